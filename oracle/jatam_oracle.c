@@ -1,0 +1,602 @@
+/*
+ * jatam_oracle.c -- plain, slow, obviously-correct CPU oracle for the JaTAM
+ * classification path.  TEST INFRASTRUCTURE ONLY: it is loaded by the test
+ * suite, by the smoke check and by the CPU-baseline leg of the benchmark, and
+ * by nothing in the product path.  It shares no code, header, table or
+ * constant with the CUDA library: everything below is written out again from
+ * the model's definitions.
+ *
+ * Model (Appendix "Modifications to Winfree's aTAM" and Section 2.1 of the
+ * paper):
+ *   - tiles are unit squares with four edge colours, ordered N, E, S, W;
+ *   - temperature 1: a single bond suffices to attach a tile;
+ *   - interaction matrix M_ij = (1 - i mod 2) d_{i,j+1} + (i mod 2) d_{i,j-1},
+ *     i.e. colours bind in adjacent pairs 1-2, 3-4, 5-6, colour 0 is inert and
+ *     all non-bonding pairs are neutral;
+ *   - tiles may be rotated by multiples of 90 degrees but never mirrored;
+ *   - the first tile of the set (the seed) starts at the centre of an empty
+ *     grid; every tile type, the seed type included, is available without
+ *     limit;
+ *   - configurations are equal iff type and orientation agree everywhere;
+ *     shapes are equal iff the occupied positions agree;
+ *   - a configuration with a tile outside the origin-centred square of
+ *     dimension d is unbounded by d.
+ * Genome encoding (Appendix "Encoding genome information"): tiles seed first,
+ * each tile N, E, S, W, log2(c) bits per colour.
+ * Hash (Section 2.5 "Classifying self-assembled shapes" and the appendix
+ * "One-at-a-time Hash"): Jenkins' 32-bit one-at-a-time hash over the
+ * positions of the occupied sites relative to the cropped grid.
+ *
+ * Where the paper is silent the readings used here are:
+ *   [R1]  the literal M: with c even the top odd colour has no partner;
+ *   [R2]  a packed genotype is read MSB-first (first tile, N edge = top bits);
+ *   [R4]  rotation r turns a tile clockwise: side d of (t, r) is colour
+ *         col[t][(d - r) mod 4];
+ *   [R5]  the seed is placed in orientation 0 at (L/2, L/2);
+ *   [R7]  ambiguity counts distinct rotated colour tuples, so repeated tile
+ *         types and symmetric tiles are not non-determinism (Section 2.4);
+ *         a placed tile is recorded by the lowest (t, r) carrying its tuple;
+ *   [R8]  after each placement (and after the seed) the empty neighbours of
+ *         the new tile are (re)evaluated; >= 2 distinct candidates anywhere
+ *         -> local non-determinism; else a candidate outside the grid ->
+ *         unbounded; else an empty frontier -> terminated;
+ *   [R9]  step s of replicate j draws word (s mod 4) of
+ *         Philox4x32-10(ctr = (s >> 2, j, id_lo, id_hi), key = seed), and
+ *         picks frontier site floor(u * |F| / 2^32) in row-major order;
+ *   [R10] replicates run in order; the first one that is unbounded, locally
+ *         non-deterministic, or terminates in a configuration different from
+ *         replicate 0's decides the class; otherwise the genotype is
+ *         deterministic and bounded;
+ *   [R11] the shape of replicate 0 is canonicalised over the 8 symmetries of
+ *         the square (minimum of (height, width, row-major bits)) and hashed
+ *         as the bytes height, width, then x, y per occupied cell in
+ *         row-major order.
+ */
+#include <pthread.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define ORC_MAXL 32
+#define ORC_MAXN 4
+
+enum { ORC_DET_BOUNDED = 0, ORC_ND_LOCAL = 1, ORC_ND_STERIC = 2, ORC_UNBOUNDED = 3 };
+enum { OUT_TERMINATED = 0, OUT_ND_LOCAL = 1, OUT_UNBOUNDED = 2 };
+
+/* direction d: 0 = N, 1 = E, 2 = S, 3 = W; x grows to the east, y to the south */
+static const int DX[4] = {0, 1, 0, -1};
+static const int DY[4] = {-1, 0, 1, 0};
+
+typedef struct {
+    uint8_t cls;
+    uint8_t decided_rep;
+    uint16_t size;
+    uint32_t shape_hash;
+} orc_result;
+
+/* ---------------------------------------------------------------------------
+ * Philox4x32-10 (Salmon, Moraes, Dror, Shaw, "Parallel random numbers: as easy
+ * as 1, 2, 3", SC'11): ten rounds of the 4x32 Philox S-box with multipliers
+ * 0xD2511F53 / 0xCD9E8D57 and Weyl key increments 0x9E3779B9 / 0xBB67AE85.
+ * ------------------------------------------------------------------------- */
+void orc_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4])
+{
+    uint32_t x0 = ctr[0], x1 = ctr[1], x2 = ctr[2], x3 = ctr[3];
+    uint32_t k0 = key[0], k1 = key[1];
+    for (int round = 0; round < 10; round++) {
+        if (round > 0) {
+            k0 += 0x9E3779B9u;
+            k1 += 0xBB67AE85u;
+        }
+        uint64_t prod0 = (uint64_t)0xD2511F53u * (uint64_t)x0;
+        uint64_t prod1 = (uint64_t)0xCD9E8D57u * (uint64_t)x2;
+        uint32_t hi0 = (uint32_t)(prod0 >> 32), lo0 = (uint32_t)prod0;
+        uint32_t hi1 = (uint32_t)(prod1 >> 32), lo1 = (uint32_t)prod1;
+        uint32_t y0 = hi1 ^ x1 ^ k0;
+        uint32_t y1 = lo1;
+        uint32_t y2 = hi0 ^ x3 ^ k1;
+        uint32_t y3 = lo0;
+        x0 = y0; x1 = y1; x2 = y2; x3 = y3;
+    }
+    out[0] = x0; out[1] = x1; out[2] = x2; out[3] = x3;
+}
+
+/* ---------------------------------------------------------------------------
+ * Jenkins one-at-a-time hash (Jenkins 1997; the paper's appendix "One-at-a-
+ * time Hash"): start from 0; per byte add it, add the value shifted left by
+ * 10, xor the value shifted right by 6; finish with add <<3, xor >>11,
+ * add <<15.  All arithmetic modulo 2^32.  Bytes are taken unsigned; the
+ * coordinates hashed here are < 32 so the paper's signed-char argument makes
+ * no difference.
+ * ------------------------------------------------------------------------- */
+uint32_t orc_oaat(const uint8_t *bytes, uint64_t len)
+{
+    uint32_t h = 0;
+    for (uint64_t i = 0; i < len; i++) {
+        h += bytes[i];
+        h += h << 10;
+        h ^= h >> 6;
+    }
+    h += h << 3;
+    h ^= h >> 11;
+    h += h << 15;
+    return h;
+}
+
+/* The interaction matrix M of the appendix: colours i and j bind iff
+ * (i even and i = j + 1) or (i odd and i = j - 1). */
+int orc_bind(int i, int j)
+{
+    if ((i % 2) == 0) return i == j + 1;
+    return i == j - 1;
+}
+
+/* Decode a packed genotype: tiles seed first, each N, E, S, W, b = log2(c)
+ * bits per colour, most significant bits first (reading [R2]). */
+int orc_decode(uint64_t g, int n, int c, uint8_t col[16])
+{
+    int b = 0;
+    while ((1 << b) < c) b++;
+    if ((1 << b) != c || n < 1 || n > ORC_MAXN) return -1;
+    memset(col, 0, 16);
+    for (int t = 0; t < n; t++)
+        for (int e = 0; e < 4; e++) {
+            int pos = b * (4 * (n - 1 - t) + (3 - e));
+            col[4 * t + e] = (uint8_t)((g >> pos) & (uint64_t)(c - 1));
+        }
+    return 0;
+}
+
+/* Genotype sampled uniformly from the packed space: words 0 and 1 of
+ * Philox4x32-10(ctr = (0, 1 << 24, i_lo, i_hi), key = seed), masked to the
+ * genome length. */
+uint64_t orc_sample_genotype(uint64_t i, int n, int c, uint64_t seed)
+{
+    int b = 0;
+    while ((1 << b) < c) b++;
+    int bits = 4 * n * b;
+    uint32_t ctr[4] = {0u, 1u << 24, (uint32_t)i, (uint32_t)(i >> 32)};
+    uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+    uint32_t w[4];
+    orc_philox4x32_10(ctr, key, w);
+    uint64_t v = ((uint64_t)w[1] << 32) | w[0];
+    if (bits < 64) v &= (((uint64_t)1) << bits) - 1;
+    return v;
+}
+
+/* ---------------------------------------------------------------------------
+ * Tile set with rotations
+ * ------------------------------------------------------------------------- */
+typedef struct {
+    int n, c, L, k;
+    uint64_t seed;
+    int col[ORC_MAXN][4];
+    int side[4 * ORC_MAXN][4]; /* side[4t + r][d] */
+    int rep[4 * ORC_MAXN];     /* lowest (t, r) with the same rotated tuple */
+} tileset;
+
+static void make_tileset(tileset *T, int n, int c, int L, int k, uint64_t seed, const uint8_t col[16])
+{
+    T->n = n; T->c = c; T->L = L; T->k = k; T->seed = seed;
+    for (int t = 0; t < n; t++)
+        for (int e = 0; e < 4; e++) T->col[t][e] = col[4 * t + e];
+    /* clockwise rotation by r quarter turns: the colour that was on side
+       (d - r) mod 4 now faces direction d (reading [R4]) */
+    for (int t = 0; t < n; t++)
+        for (int r = 0; r < 4; r++)
+            for (int d = 0; d < 4; d++) T->side[4 * t + r][d] = T->col[t][(d - r + 4) % 4];
+    for (int a = 0; a < 4 * n; a++) {
+        T->rep[a] = a;
+        for (int b = 0; b < a; b++) {
+            if (memcmp(T->side[a], T->side[b], sizeof T->side[a]) == 0) {
+                T->rep[a] = b;
+                break;
+            }
+        }
+    }
+}
+
+/* ---------------------------------------------------------------------------
+ * One assembly grid
+ * ------------------------------------------------------------------------- */
+typedef struct {
+    int L;
+    int cell[ORC_MAXL][ORC_MAXL];  /* -1 empty, else the recorded tuple id */
+    int ncand[ORC_MAXL][ORC_MAXL]; /* |D(s)| of an empty site, as last evaluated */
+    int cand[ORC_MAXL][ORC_MAXL];  /* the single candidate when ncand == 1 */
+    int size;
+} grid;
+
+static int inside(const grid *G, int x, int y) { return x >= 0 && y >= 0 && x < G->L && y < G->L; }
+
+/* D(q): the distinct rotated tuples that can attach at the empty site q,
+ * i.e. those (t, r) for which some occupied neighbour offers a bond
+ * (temperature 1, non-bonding faces neutral).  Returns |D(q)|; *only receives
+ * the tuple when |D(q)| == 1. */
+static int candidates(const tileset *T, const grid *G, int qx, int qy, int *only)
+{
+    int seen[4 * ORC_MAXN];
+    int m = 0;
+    memset(seen, 0, sizeof seen);
+    for (int t = 0; t < T->n; t++) {
+        for (int r = 0; r < 4; r++) {
+            int a = 4 * t + r;
+            int bonds = 0;
+            for (int d = 0; d < 4; d++) {
+                int nx = qx + DX[d], ny = qy + DY[d];
+                if (!inside(G, nx, ny)) continue;
+                int u = G->cell[ny][nx];
+                if (u < 0) continue;
+                /* the neighbour in direction d shows us its side (d + 2) mod 4 */
+                if (orc_bind(T->side[a][d], T->side[u][(d + 2) % 4])) bonds = 1;
+            }
+            if (bonds && !seen[T->rep[a]]) {
+                seen[T->rep[a]] = 1;
+                m++;
+                *only = T->rep[a];
+            }
+        }
+    }
+    return m;
+}
+
+static uint32_t draw(const tileset *T, uint64_t stream_id, int rep, int step)
+{
+    uint32_t ctr[4] = {(uint32_t)step >> 2, (uint32_t)rep, (uint32_t)stream_id, (uint32_t)(stream_id >> 32)};
+    uint32_t key[2] = {(uint32_t)T->seed, (uint32_t)(T->seed >> 32)};
+    uint32_t w[4];
+    orc_philox4x32_10(ctr, key, w);
+    return w[step & 3];
+}
+
+/* Optional per-step trace of a replicate, used by the tests to re-derive every
+ * draw independently. */
+typedef struct {
+    int32_t nfront;  /* |F| before the draw */
+    uint32_t u;      /* the Philox word */
+    int32_t index;   /* chosen rank in F */
+    int32_t x, y;    /* chosen site */
+    int32_t tuple;   /* tuple placed */
+} orc_trace_step;
+
+/* Grow one replicate from the seed until it is decided. */
+static int run_replicate(const tileset *T, uint64_t stream_id, int rep, grid *G, uint64_t *placements,
+                         orc_trace_step *trace, int trace_cap, int *trace_len)
+{
+    int L = T->L;
+    G->L = L;
+    for (int y = 0; y < L; y++)
+        for (int x = 0; x < L; x++) {
+            G->cell[y][x] = -1;
+            G->ncand[y][x] = 0;
+            G->cand[y][x] = -1;
+        }
+    int px = L / 2, py = L / 2;
+    G->cell[py][px] = T->rep[0];
+    G->size = 1;
+    int step = 0;
+    int fx[ORC_MAXL * ORC_MAXL], fy[ORC_MAXL * ORC_MAXL];
+    for (;;) {
+        int nd = 0, unb = 0;
+        for (int d = 0; d < 4; d++) {
+            int qx = px + DX[d], qy = py + DY[d];
+            int in = inside(G, qx, qy);
+            if (in && G->cell[qy][qx] >= 0) continue;
+            int only = -1;
+            int m = candidates(T, G, qx, qy, &only);
+            if (in) {
+                G->ncand[qy][qx] = m;
+                G->cand[qy][qx] = (m == 1) ? only : -1;
+            }
+            if (m >= 2) nd = 1;
+            else if (!in && m >= 1) unb = 1;
+        }
+        if (nd) return OUT_ND_LOCAL;
+        if (unb) return OUT_UNBOUNDED;
+        int nf = 0;
+        for (int y = 0; y < L; y++)
+            for (int x = 0; x < L; x++)
+                if (G->cell[y][x] < 0 && G->ncand[y][x] == 1) {
+                    fx[nf] = x;
+                    fy[nf] = y;
+                    nf++;
+                }
+        if (nf == 0) return OUT_TERMINATED;
+        uint32_t u = draw(T, stream_id, rep, step);
+        int i = (int)(((uint64_t)u * (uint64_t)nf) >> 32);
+        int sx = fx[i], sy = fy[i];
+        if (trace && *trace_len < trace_cap) {
+            orc_trace_step *ts = &trace[*trace_len];
+            ts->nfront = nf; ts->u = u; ts->index = i; ts->x = sx; ts->y = sy; ts->tuple = G->cand[sy][sx];
+            (*trace_len)++;
+        }
+        G->cell[sy][sx] = G->cand[sy][sx];
+        G->size++;
+        step++;
+        (*placements)++;
+        px = sx;
+        py = sy;
+    }
+}
+
+static int same_configuration(const grid *A, const grid *B)
+{
+    for (int y = 0; y < A->L; y++)
+        for (int x = 0; x < A->L; x++)
+            if (A->cell[y][x] != B->cell[y][x]) return 0;
+    return 1;
+}
+
+/* ---------------------------------------------------------------------------
+ * Canonical form under the 8 symmetries of the square, and its hash
+ * ------------------------------------------------------------------------- */
+
+/* Image of (x, y) under symmetry s (4 rotations, then the 4 mirror images). */
+static void symmetry(int s, int x, int y, int *ox, int *oy)
+{
+    switch (s) {
+    case 0: *ox = x;  *oy = y;  break;
+    case 1: *ox = -y; *oy = x;  break;
+    case 2: *ox = -x; *oy = -y; break;
+    case 3: *ox = y;  *oy = -x; break;
+    case 4: *ox = -x; *oy = y;  break;
+    case 5: *ox = x;  *oy = -y; break;
+    case 6: *ox = y;  *oy = x;  break;
+    default: *ox = -y; *oy = -x; break;
+    }
+}
+
+/* Canonical form of a set of m cells: for every symmetry, translate the image
+ * so that its minimum x and y are 0, giving an h x w bitmap; keep the image
+ * with the smallest (h, w, row-major bit sequence), 0 before 1.  Writes the
+ * bitmap (row-major, 1 byte per cell) to out[h * w]; returns 0. */
+int orc_canonical(const int32_t *xs, const int32_t *ys, int m, uint8_t *out, int32_t *out_h, int32_t *out_w)
+{
+    static const int CAP = 2 * ORC_MAXL + 1;
+    int best_h = 0, best_w = 0, have = 0;
+    uint8_t best[(2 * ORC_MAXL + 1) * (2 * ORC_MAXL + 1)];
+    uint8_t img[(2 * ORC_MAXL + 1) * (2 * ORC_MAXL + 1)];
+    if (m <= 0) {
+        *out_h = 0;
+        *out_w = 0;
+        return 0;
+    }
+    for (int s = 0; s < 8; s++) {
+        int minx = 1 << 30, miny = 1 << 30, maxx = -(1 << 30), maxy = -(1 << 30);
+        for (int i = 0; i < m; i++) {
+            int tx, ty;
+            symmetry(s, xs[i], ys[i], &tx, &ty);
+            if (tx < minx) minx = tx;
+            if (ty < miny) miny = ty;
+            if (tx > maxx) maxx = tx;
+            if (ty > maxy) maxy = ty;
+        }
+        int h = maxy - miny + 1, w = maxx - minx + 1;
+        if (h > CAP || w > CAP) return -1;
+        memset(img, 0, (size_t)h * (size_t)w);
+        for (int i = 0; i < m; i++) {
+            int tx, ty;
+            symmetry(s, xs[i], ys[i], &tx, &ty);
+            img[(ty - miny) * w + (tx - minx)] = 1;
+        }
+        int better = 0;
+        if (!have) better = 1;
+        else if (h != best_h) better = h < best_h;
+        else if (w != best_w) better = w < best_w;
+        else better = memcmp(img, best, (size_t)h * (size_t)w) < 0;
+        if (better) {
+            have = 1;
+            best_h = h;
+            best_w = w;
+            memcpy(best, img, (size_t)h * (size_t)w);
+        }
+    }
+    memcpy(out, best, (size_t)best_h * (size_t)best_w);
+    *out_h = best_h;
+    *out_w = best_w;
+    return 0;
+}
+
+/* Hash of a canonical bitmap through one-at-a-time: first the height and the
+ * width of the cropped grid, then bytes x, y of every occupied cell in
+ * row-major order.  (Starting from state 0, a zero byte leaves the state at 0,
+ * so without the non-zero dimension bytes a leading cell at (0, 0) would not
+ * count and, e.g., the 2 x 2 square would hash like the L-tromino.) */
+uint32_t orc_shape_hash(const uint8_t *bitmap, int h, int w)
+{
+    uint8_t bytes[2 + 2 * (2 * ORC_MAXL + 1) * (2 * ORC_MAXL + 1)];
+    uint64_t nb = 0;
+    bytes[nb++] = (uint8_t)h;
+    bytes[nb++] = (uint8_t)w;
+    for (int y = 0; y < h; y++)
+        for (int x = 0; x < w; x++)
+            if (bitmap[y * w + x]) {
+                bytes[nb++] = (uint8_t)x;
+                bytes[nb++] = (uint8_t)y;
+            }
+    return orc_oaat(bytes, nb);
+}
+
+static uint32_t hash_of_grid(const grid *G)
+{
+    int32_t xs[ORC_MAXL * ORC_MAXL], ys[ORC_MAXL * ORC_MAXL];
+    uint8_t bm[(2 * ORC_MAXL + 1) * (2 * ORC_MAXL + 1)];
+    int m = 0;
+    for (int y = 0; y < G->L; y++)
+        for (int x = 0; x < G->L; x++)
+            if (G->cell[y][x] >= 0) {
+                xs[m] = x;
+                ys[m] = y;
+                m++;
+            }
+    int32_t h, w;
+    orc_canonical(xs, ys, m, bm, &h, &w);
+    return orc_shape_hash(bm, h, w);
+}
+
+/* ---------------------------------------------------------------------------
+ * Classification of one genotype (reading [R10] / [R11])
+ * ------------------------------------------------------------------------- */
+static int valid_params(int n, int c, int L, int k)
+{
+    return n >= 1 && n <= ORC_MAXN && c >= 1 && c <= 8 && L >= 1 && L <= ORC_MAXL && k >= 1 && k <= 255;
+}
+
+/* Classify one genotype given its colours col[4t + e].  When rep0_cells is not
+ * NULL it receives replicate 0's final grid (L*L ints, row-major, -1 empty).
+ * When trace is not NULL it receives the steps of replicate trace_rep. */
+int orc_classify_ex(int n, int c, int L, int k, uint64_t seed, const uint8_t col[16], uint64_t stream_id,
+                    orc_result *res, uint64_t *placements, int32_t *rep0_cells, int trace_rep,
+                    orc_trace_step *trace, int trace_cap, int *trace_len)
+{
+    if (!valid_params(n, c, L, k)) return -1;
+    for (int i = 0; i < 4 * n; i++)
+        if (col[i] >= c) return -1;
+    tileset T;
+    make_tileset(&T, n, c, L, k, seed, col);
+    grid *A0 = (grid *)malloc(sizeof(grid));
+    grid *Aj = (grid *)malloc(sizeof(grid));
+    if (!A0 || !Aj) {
+        free(A0);
+        free(Aj);
+        return -2;
+    }
+    uint64_t placed = 0;
+    int cls = ORC_DET_BOUNDED, decided = k;
+    int tl = 0;
+    for (int j = 0; j < k; j++) {
+        grid *G = (j == 0) ? A0 : Aj;
+        int want = (trace && j == trace_rep);
+        int out = run_replicate(&T, stream_id, j, G, &placed, want ? trace : NULL, trace_cap, &tl);
+        if (out == OUT_UNBOUNDED) { cls = ORC_UNBOUNDED; decided = j; break; }
+        if (out == OUT_ND_LOCAL) { cls = ORC_ND_LOCAL; decided = j; break; }
+        if (j > 0 && !same_configuration(A0, Aj)) { cls = ORC_ND_STERIC; decided = j; break; }
+    }
+    res->cls = (uint8_t)cls;
+    res->decided_rep = (uint8_t)decided;
+    res->size = 0;
+    res->shape_hash = 0;
+    if (cls == ORC_DET_BOUNDED || cls == ORC_ND_STERIC) {
+        res->size = (uint16_t)A0->size;
+        res->shape_hash = hash_of_grid(A0);
+    }
+    if (rep0_cells) {
+        for (int y = 0; y < L; y++)
+            for (int x = 0; x < L; x++) rep0_cells[y * L + x] = A0->cell[y][x];
+    }
+    if (placements) *placements += placed;
+    if (trace_len) *trace_len = tl;
+    free(A0);
+    free(Aj);
+    return 0;
+}
+
+int orc_classify(int n, int c, int L, int k, uint64_t seed, const uint8_t col[16], uint64_t stream_id,
+                 orc_result *res, uint64_t *placements)
+{
+    return orc_classify_ex(n, c, L, k, seed, col, stream_id, res, placements, NULL, -1, NULL, 0, NULL);
+}
+
+/* ---------------------------------------------------------------------------
+ * Batch drivers (one POSIX thread per core over contiguous ranges)
+ * ------------------------------------------------------------------------- */
+typedef struct {
+    int n, c, L, k, sampled;
+    uint64_t seed, first, count;
+    const uint8_t *cols;    /* explicit colours [count][16] or NULL */
+    const uint8_t *shapes;  /* per-item (n, c, L, k) [count][4] or NULL */
+    const uint64_t *ids;    /* stream ids or NULL */
+    orc_result *out;
+    uint64_t lo, hi;        /* this thread's range of items */
+    uint64_t placements;
+    int status;
+} job;
+
+static void *worker(void *arg)
+{
+    job *J = (job *)arg;
+    for (uint64_t i = J->lo; i < J->hi; i++) {
+        uint8_t col[16];
+        int n = J->n, c = J->c, L = J->L, k = J->k;
+        uint64_t sid;
+        if (J->cols) {
+            memcpy(col, J->cols + 16 * i, 16);
+            if (J->shapes) {
+                n = J->shapes[4 * i + 0];
+                c = J->shapes[4 * i + 1];
+                L = J->shapes[4 * i + 2];
+                k = J->shapes[4 * i + 3];
+            }
+            sid = J->ids ? J->ids[i] : i;
+        } else {
+            uint64_t idx = J->first + i;
+            uint64_t g = J->sampled ? orc_sample_genotype(idx, n, c, J->seed) : idx;
+            if (orc_decode(g, n, c, col) != 0) {
+                J->status = -1;
+                return NULL;
+            }
+            sid = g;
+        }
+        int rc = orc_classify(n, c, L, k, J->seed, col, sid, &J->out[i], &J->placements);
+        if (rc != 0) {
+            J->status = rc;
+            return NULL;
+        }
+    }
+    return NULL;
+}
+
+static int run_jobs(job *proto, uint64_t count, int nthreads, uint64_t *placements)
+{
+    if (nthreads < 1) nthreads = 1;
+    if (nthreads > 256) nthreads = 256;
+    if ((uint64_t)nthreads > count && count > 0) nthreads = (int)count;
+    job jobs[256];
+    pthread_t th[256];
+    for (int t = 0; t < nthreads; t++) {
+        jobs[t] = *proto;
+        jobs[t].lo = count * (uint64_t)t / (uint64_t)nthreads;
+        jobs[t].hi = count * (uint64_t)(t + 1) / (uint64_t)nthreads;
+        jobs[t].placements = 0;
+        jobs[t].status = 0;
+    }
+    for (int t = 1; t < nthreads; t++) pthread_create(&th[t], NULL, worker, &jobs[t]);
+    worker(&jobs[0]);
+    for (int t = 1; t < nthreads; t++) pthread_join(th[t], NULL);
+    uint64_t total = 0;
+    int status = 0;
+    for (int t = 0; t < nthreads; t++) {
+        total += jobs[t].placements;
+        if (jobs[t].status) status = jobs[t].status;
+    }
+    if (placements) *placements = total;
+    return status;
+}
+
+/* Classify genotype indices first .. first+count-1 of the packed space
+ * (in order, or sampled when sampled != 0).  The stream id of each genotype
+ * is its packed value. */
+int orc_enumerate(int n, int c, int L, int k, uint64_t seed, int sampled, uint64_t first, uint64_t count,
+                  orc_result *out, int nthreads, uint64_t *placements)
+{
+    if (!valid_params(n, c, L, k)) return -1;
+    job proto;
+    memset(&proto, 0, sizeof proto);
+    proto.n = n; proto.c = c; proto.L = L; proto.k = k; proto.sampled = sampled;
+    proto.seed = seed; proto.first = first; proto.count = count; proto.out = out;
+    return run_jobs(&proto, count, nthreads, placements);
+}
+
+/* Classify explicit colour records cols[count][16]; shapes[count][4] gives
+ * per-item (n, c, L, k) or is NULL (then n, c, L, k apply to all); ids gives
+ * stream ids or is NULL (then the item index is the stream id). */
+int orc_classify_batch(const uint8_t *cols, const uint8_t *shapes, int n, int c, int L, int k, uint64_t seed,
+                       const uint64_t *ids, uint64_t count, orc_result *out, int nthreads, uint64_t *placements)
+{
+    job proto;
+    memset(&proto, 0, sizeof proto);
+    proto.n = n; proto.c = c; proto.L = L; proto.k = k;
+    proto.seed = seed; proto.count = count; proto.cols = cols; proto.shapes = shapes; proto.ids = ids;
+    proto.out = out;
+    return run_jobs(&proto, count, nthreads, placements);
+}
