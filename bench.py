@@ -1,0 +1,323 @@
+"""Benchmark: genotypes classified per second on one GB300.
+
+Workload: S_{2,8} in full -- all 8^8 = 16,777,216 two-tile genotypes, 16 x 16
+grid, k = 20 replicate assemblies, Philox key 2 -- classified by
+jatam_enumerate into per-genotype results (8 B each, 134 MB, larger than the
+129 MB L2) plus the phenotype histogram.  One step = one such enumeration.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+Under torchrun (N > 1) every rank classifies its own full copy of the
+workload under its own Philox key (weak scaling, no collective on the data
+path); rank 0 prints one JSON line with the whole-job rate.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = "s28_full"
+METRIC = "genotypes classified/s (1 GB300, bit-exact vs oracle) + % int/smem roofline"
+UNIT = "genotypes/s"
+
+# algorithmic integer operations per unit of work ("Roofline")
+OPS_PER_PLACEMENT = 62
+OPS_PER_REPLICATE = 37
+OPS_PER_GENOTYPE = 300
+OPS_PER_SHAPED_CELL = 24
+
+
+def _env_rank():
+    return int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("LOCAL_RANK", "0"))
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons while running."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+        self.t = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            if self.t:
+                self.t.join(timeout=2)
+
+    def summary(self):
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.lines:
+            p = [x.strip() for x in line.split(",")]
+            if len(p) < 9:
+                continue
+            try:
+                sm.append(float(p[1]))
+                smax.append(float(p[2]))
+            except ValueError:
+                continue
+            for name, v in zip(names, p[5:9]):
+                if v.lower() == "active":
+                    reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(smax)), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except OSError:
+        return {}
+
+
+def algorithmic_ops(res_cls, res_rep, res_size, k, placements):
+    """Integer operations the method needs for one pass over the workload."""
+    reps = np.where(res_rep >= k, k, res_rep.astype(np.int64) + 1).sum()
+    shaped = (res_cls == 0) | (res_cls == 2)
+    cells = res_size[shaped].astype(np.int64).sum()
+    return (OPS_PER_PLACEMENT * placements + OPS_PER_REPLICATE * int(reps) + OPS_PER_GENOTYPE * res_cls.size
+            + OPS_PER_SHAPED_CELL * int(cells))
+
+
+def cpu_sample_plan():
+    """Stratified bounded sample of the workload for the oracle: 64 blocks of
+    65,536 consecutive genotypes spread evenly over the space."""
+    n, c, L, k, seed, first, count, sampled = WORKLOAD_SPEC()
+    blocks = 64
+    per = 65536
+    stride = count // blocks
+    return [(first + b * stride, per) for b in range(blocks)]
+
+
+def WORKLOAD_SPEC():
+    from paper_2205_15311_gb300 import workloads as W
+    return W.WORKLOADS[WORKLOAD]
+
+
+def run_oracle_sample(nthreads):
+    from oracle import oracle as O
+    n, c, L, k, seed, _, _, _ = WORKLOAD_SPEC()
+    done = 0
+    t0 = time.perf_counter()
+    for first, cnt in cpu_sample_plan():
+        O.enumerate_space(n, c, L, k, seed, first, cnt, nthreads=nthreads)
+        done += cnt
+    return done, time.perf_counter() - t0
+
+
+def reference_arm(args):
+    rank, world, _ = _env_rank()
+    if rank != 0:
+        return 0
+    from oracle import oracle as O
+    O.build()
+    cores = os.cpu_count() or 1
+    times, units = [], 0
+    for _ in range(args.warmup):
+        run_oracle_sample(cores)
+    for _ in range(args.steps):
+        u, dt = run_oracle_sample(cores)
+        units = u
+        times.append(dt)
+    per_step = float(np.mean(times))
+    value = units / per_step
+    n, c, L, k, seed, first, count, _ = WORKLOAD_SPEC()
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": per_step * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+        "config": {"workload": f"{WORKLOAD}: S_{{2,8}} n={n} c={c} L={L} k={k} seed={seed}",
+                   "step": f"oracle on a stratified sample of {units} genotypes (64 x 65536)"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": f"64 blocks of 65,536 consecutive genotypes of S_{{2,8}} ({units} per step)"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+    if args.impl == "reference":
+        return reference_arm(args)
+
+    import torch
+    import torch.distributed as dist
+
+    rank, world, local = _env_rank()
+    if world > 1:
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA device")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2205_15311_gb300 import binding as J
+
+    n, c, L, k, seed0, first, count, sampled = WORKLOAD_SPEC()
+    seed = seed0 + rank  # every rank: its own independent classification of the space
+    hist_cap = 1 << 16
+    stream = torch.cuda.Stream(device=dev)
+    out = torch.empty(count * 8, dtype=torch.uint8, device=dev)
+    hist = torch.empty(hist_cap * 32, dtype=torch.uint8, device=dev)
+    hlen = torch.zeros(1, dtype=torch.int32, device=dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)  # larger than the 129 MB L2
+
+    def step():
+        J.enumerate_space(n, c, L, k, seed, first, count, sampled=sampled, out=out, hist=hist, hist_len=hlen,
+                          hist_cap=hist_cap, stream=stream)
+
+    J.jatam_profile(1)
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            step()
+    stream.synchronize()
+
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    stops = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    kernel_ms = []
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clocks:
+        for i in range(args.steps):
+            with torch.cuda.stream(stream):
+                flush.fill_(i & 255)
+                starts[i].record(stream)
+                step()
+                stops[i].record(stream)
+            kernel_ms.append(J.last_kernel_ms())
+        torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    step_ms = [s.elapsed_time(e) for s, e in zip(starts, stops)]
+    ms = float(np.mean(step_ms))
+    if world > 1:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = world * count / (ms / 1e3)
+
+    # end to end through the C ABI with host buffers: results and histogram land in pinned host memory
+    out_h = torch.empty(count * 8, dtype=torch.uint8, pin_memory=True)
+    hist_h = np.zeros(hist_cap, J.HIST_DTYPE)
+    hlen_h = np.zeros(1, np.uint32)
+    J.enumerate_space(n, c, L, k, seed, first, count, sampled=sampled, out=out_h, hist=hist_h, hist_len=hlen_h,
+                      hist_cap=hist_cap, stream=stream)
+    e2e_times = []
+    for i in range(max(3, min(args.steps, 5))):
+        flush.fill_(i & 255)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        J.enumerate_space(n, c, L, k, seed, first, count, sampled=sampled, out=out_h, hist=hist_h,
+                          hist_len=hlen_h, hist_cap=hist_cap, stream=stream)
+        e2e_times.append(time.perf_counter() - t0)
+    e2e_s = float(np.mean(e2e_times))
+    if world > 1:
+        t = torch.tensor([e2e_s], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    nk = int(hlen_h[0])
+
+    line = None
+    if rank == 0:
+        res = J.results_view(out)
+        peaks = measured_peaks()
+        sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+        props = torch.cuda.get_device_properties(dev)
+        n_sms = props.multi_processor_count
+        alu_peak = n_sms * 128 * sm_max * 1e6 / 1e12  # int32 lane-ops per second, T
+        placements = None
+        golden = os.path.join(ROOT, "tests", "golden", "c2_summary.json")
+        if os.path.exists(golden) and seed == 2:
+            placements = json.load(open(golden))["placements"]
+        roofline = None
+        kms = float(np.mean(kernel_ms))
+        if placements is not None:
+            ops = algorithmic_ops(res["cls"], res["decided_rep"], res["size"], k, placements)
+            achieved = ops / (kms / 1e3) / 1e12
+            roofline = {"bound": "alu", "achieved": round(achieved, 4), "peak": round(alu_peak, 2),
+                        "unit": "Tops/s", "frac": round(achieved / alu_peak, 4), "traffic": None,
+                        "kernel": "classify_kernel<16>", "kernel_ms": round(kms, 4),
+                        "peak_source": f"{n_sms} SMs x 128 int32 lanes x {sm_max:.0f} MHz (MEASURED_PEAKS sm_max)",
+                        "hbm_gbs": round(count * 8 / (kms / 1e3) / 1e9, 1),
+                        "hbm_frac_of_measured": round(count * 8 / (kms / 1e3) / 1e9 / float(peaks.get("hbm_gbs", 6753.1)), 4)}
+        cpu = None
+        if not args.no_cpu_baseline and world == 1:
+            from oracle import oracle as O
+            O.build()
+            cores = os.cpu_count() or 1
+            units, dt = run_oracle_sample(cores)
+            cpu = {"value": units / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+                   "sample": f"64 blocks of 65,536 consecutive genotypes of S_{{2,8}} ({units} genotypes, {dt:.1f} s)"}
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+            "config": {"workload": f"{WORKLOAD}: all 8^8 genotypes of S_{{2,8}}, n={n} c={c} L={L} k={k} seed={seed0}",
+                       "global_batch": world * count, "parallelism": f"replicas x{world}",
+                       "l2": "256 MB buffer written between timed steps; outputs 134 MB > L2",
+                       "distinct_phenotypes": nk},
+            "e2e": {"value": world * count / e2e_s, "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": count * 8 + nk * 32 + 8},
+            "gpu_launches": 4 * args.steps,
+            "roofline": roofline,
+            "cpu_baseline": cpu,
+            "clocks": clocks.summary(),
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

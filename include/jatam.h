@@ -1,0 +1,185 @@
+/*
+ * jatam.h -- C ABI of libjatam.so: batched stochastic tile self-assembly and
+ * phenotype classification of JaTAM genotypes on one GB300 (sm_103a).
+ *
+ * The model is the one of the paper (arXiv 2205.15311, "Modifications to
+ * Winfree's aTAM" and Section 1.1): square tiles with four coloured edges
+ * (N, E, S, W), colours binding in adjacent pairs 1-2, 3-4, 5-6 (0 inert,
+ * other pairs neutral), temperature 1, rotations allowed and mirror images
+ * not, the first tile of the set as seed at the centre of an L x L grid, every
+ * tile type unlimited.  For every genotype the library grows k replicate
+ * assemblies, flags local non-determinism (two distinct tiles fit one site,
+ * Section 2.4), unbounded growth (a tile fits outside the grid, appendix
+ * "Modifications to Winfree's aTAM"), and steric non-determinism (a replicate
+ * ends in a configuration different from replicate 0's, Section 2.4); a
+ * genotype with none of these is deterministic and bounded.  The shape of
+ * replicate 0 is put in canonical form under the 8 symmetries of the square
+ * and hashed with Jenkins' one-at-a-time hash (Section 2.5), and the genotypes
+ * are binned by (class, hash) into a phenotype histogram (Section 2.6).
+ *
+ * The random draws are fixed: step s of replicate j of the genotype with
+ * stream id g uses word (s mod 4) of Philox4x32-10 with counter
+ * (s >> 2, j, g_lo, g_hi) and key (seed_lo, seed_hi), and picks frontier site
+ * floor(u * |F| / 2^32) of the frontier F in row-major order.  Results are
+ * therefore bit-identical whatever the launch configuration.
+ *
+ * Conventions for every call
+ *   - returns JATAM_OK (0) or a negative JATAM_E* code; jatam_last_error()
+ *     gives a message for the calling thread's last failure;
+ *   - buffers belong to the caller.  Each pointer may be device memory or host
+ *     memory (pinned or pageable); the library detects which with
+ *     cudaPointerGetAttributes and stages host buffers through device memory;
+ *   - work is queued on the CUDA stream `stream` (NULL = legacy default
+ *     stream).  The call returns before the work ends unless a host output
+ *     buffer was given or cfg->flags has JATAM_SYNC; in those cases it waits
+ *     for the stream and also reports errors found on the device;
+ *   - the library owns one workspace per device (the histogram table, counters
+ *     and staging buffers); calls on one device are serialised through it, in
+ *     the order they were made, whatever their streams.  jatam_shutdown()
+ *     frees it.
+ */
+#ifndef JATAM_H
+#define JATAM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ---- */
+#define JATAM_OK 0
+#define JATAM_EINVAL (-1)       /* bad argument (size, range, null pointer, colour >= c, capacity) */
+#define JATAM_ENOMEM (-2)       /* device allocation failed or the histogram table overflowed */
+#define JATAM_ECUDA (-3)        /* a CUDA runtime call failed */
+#define JATAM_ETIMEOUT (-4)     /* a bounded device-side loop gave up (internal invariant broken) */
+#define JATAM_EUNSUPPORTED (-5) /* parameters outside the supported range (n > 4, c > 8, L > 32, k > 255) */
+
+/* ---- phenotype classes ---- */
+#define JATAM_DET_BOUNDED 0 /* every replicate ended in replicate 0's configuration */
+#define JATAM_ND_LOCAL 1    /* two distinct rotated tiles fitted one empty site */
+#define JATAM_ND_STERIC 2   /* a replicate ended in a configuration different from replicate 0's */
+#define JATAM_UNBOUNDED 3   /* a tile fitted a site outside the L x L grid */
+
+/* ---- jatam_config.flags ---- */
+#define JATAM_SAMPLED 0x1u /* jatam_enumerate: index i names a uniformly sampled genotype (see below) */
+#define JATAM_SYNC 0x2u    /* wait for the work to finish before returning */
+
+/* Limits of the supported model sizes. */
+#define JATAM_MAX_TILES 4
+#define JATAM_MAX_COLOURS 8
+#define JATAM_MAX_GRID 32
+#define JATAM_MAX_REPLICATES 255
+
+typedef struct {
+    uint8_t n;      /* tile types, 1..4 (the seed is tile 0) */
+    uint8_t c;      /* colours 0..c-1, 1..8 (a power of two for packed genotypes) */
+    uint8_t L;      /* grid side, 1..32; the seed sits at (L/2, L/2) */
+    uint8_t k;      /* replicate assemblies per genotype, 1..255 */
+    uint32_t flags; /* JATAM_SAMPLED | JATAM_SYNC */
+    uint64_t seed;  /* Philox key (low word, high word) */
+} jatam_config;     /* 16 bytes */
+
+typedef struct {
+    uint8_t cls;         /* JATAM_DET_BOUNDED .. JATAM_UNBOUNDED */
+    uint8_t decided_rep; /* replicate that decided a non-deterministic or unbounded class; k otherwise */
+    uint16_t size;       /* tiles in replicate 0's final shape (classes 0 and 2), else 0 */
+    uint32_t shape_hash; /* one-at-a-time hash of the canonical shape (classes 0 and 2), else 0 */
+} jatam_result;          /* 8 bytes */
+
+typedef struct {
+    uint32_t cls;        /* class */
+    uint32_t shape_hash; /* hash (0 for classes 1 and 3) */
+    uint32_t size;       /* shape size; the largest seen if genotypes disagreed */
+    uint32_t flags;      /* bit 0: genotypes with this key disagreed on the size (a hash collision) */
+    uint64_t count;      /* genotypes with this (class, hash) */
+    uint64_t min_id;     /* smallest stream id among them */
+} jatam_hist_entry;      /* 32 bytes; a histogram is sorted by (cls, shape_hash) */
+
+/*
+ * jatam_enumerate -- classify genotypes first .. first+count-1 of the packed
+ * space S_{n,c} (Section 2.1 "Binary encodings" and the appendix "Encoding
+ * genome information": tiles seed first, each N, E, S, W, log2(c) bits per
+ * colour, the first tile's N edge in the most significant bits).
+ *   cfg      : n, c (power of two), L, k, seed, flags.  Without JATAM_SAMPLED
+ *              index i is the genotype value itself.  With it, genotype i is
+ *              words 0 and 1 of Philox4x32-10(ctr = (0, 1 << 24, i_lo, i_hi),
+ *              key = seed) as (w1 << 32 | w0), masked to the 4 n log2(c) bits.
+ *              The stream id of each genotype is its value.
+ *   first, count : index range; first + count must not exceed 2^(4 n log2 c)
+ *              for the in-order space.  count may be 0.
+ *   out      : NULL or [count] results, out[i] for index first + i.
+ *   hist     : NULL or [hist_cap] histogram entries of this call, sorted.
+ *   hist_len : with hist, receives the number of distinct keys (which may
+ *              exceed hist_cap: then only hist_cap entries are written and,
+ *              when hist_len is host memory, JATAM_EINVAL is returned).
+ *   stream   : cudaStream_t or NULL.
+ */
+int jatam_enumerate(const jatam_config *cfg, uint64_t first, uint64_t count, jatam_result *out,
+                    jatam_hist_entry *hist, uint32_t hist_cap, uint32_t *hist_len, void *stream);
+
+/*
+ * jatam_classify_batch -- classify N explicit tile sets (Section 2.6: a batch
+ * of assemblies, hashed and binned).
+ *   colours    : [N][16] uint8, colour of edge e of tile t at [i][4 t + e]
+ *                (N, E, S, W); entries beyond 4 n are ignored.
+ *   shapes     : NULL (every item uses cfg->n, c, L, k) or [N][4] uint8 giving
+ *                each item's (n, c, L, k) -- batches may mix them.
+ *   stream_ids : NULL (item i uses stream id i) or [N] uint64.
+ *   out, hist, hist_cap, hist_len, stream : as for jatam_enumerate.
+ * Items with a colour >= c or parameters out of range get cls = 255 and the
+ * call reports JATAM_EINVAL once the work has finished.
+ */
+int jatam_classify_batch(const jatam_config *cfg, const uint8_t *colours, const uint8_t *shapes,
+                         const uint64_t *stream_ids, uint64_t N, jatam_result *out, jatam_hist_entry *hist,
+                         uint32_t hist_cap, uint32_t *hist_len, void *stream);
+
+/*
+ * ga_evaluate -- fitness of a population of packed genomes for the genetic
+ * algorithm (Section 2.2 and Section 3.2): genome i is decoded as in
+ * jatam_enumerate, classified with stream id = its value, and
+ *   fitness[i] = size of its shape if it is deterministic and bounded, else 0.
+ *   genomes : [N] uint64 packed genomes (4 n log2(c) bits used).
+ *   fitness : [N] int32, required.   out : NULL or [N] results.
+ */
+int ga_evaluate(const jatam_config *cfg, const uint64_t *genomes, uint64_t N, int32_t *fitness,
+                jatam_result *out, void *stream);
+
+/*
+ * jatam_philox -- Philox4x32-10 (Salmon et al., SC'11) as computed by the
+ * classification kernels, for checking the draws: for each of N records
+ * in[6 i .. 6 i + 5] = (ctr0, ctr1, ctr2, ctr3, key0, key1) it writes the four
+ * output words to out[4 i .. 4 i + 3].  Buffers may be host or device.
+ */
+int jatam_philox(const uint32_t *in, uint64_t N, uint32_t *out, void *stream);
+
+/*
+ * jatam_hist_merge -- host-only merge of two sorted histograms (the shards of
+ * a range split across processes or devices): counts add, min_id takes the
+ * minimum, size the maximum, flags OR.  a, b, out are host arrays; out may not
+ * alias a or b.  Returns JATAM_EINVAL if the merged length exceeds cap
+ * (*len still receives it).
+ */
+int jatam_hist_merge(const jatam_hist_entry *a, uint32_t na, const jatam_hist_entry *b, uint32_t nb,
+                     jatam_hist_entry *out, uint32_t cap, uint32_t *len);
+
+/*
+ * jatam_profile -- when enable != 0, every later call records CUDA events
+ * around its classification kernel on the call's stream; jatam_kernel_ms()
+ * then waits for the last such pair and returns its elapsed milliseconds in
+ * *ms (JATAM_EINVAL if no call has been profiled).
+ */
+int jatam_profile(int enable);
+int jatam_kernel_ms(float *ms);
+
+/* Free every device workspace of the library (waits for queued work). */
+void jatam_shutdown(void);
+
+/* Message describing the calling thread's last failure ("" if none). */
+const char *jatam_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* JATAM_H */

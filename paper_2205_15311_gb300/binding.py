@@ -1,0 +1,209 @@
+"""Thin ctypes binding of libjatam.so (include/jatam.h).
+
+The functions named like the C ABI (``jatam_enumerate``, ``jatam_classify_batch``,
+``ga_evaluate``, ``jatam_philox``, ``jatam_hist_merge``, ``jatam_shutdown``,
+``jatam_last_error``) take raw addresses (ints) exactly as the C calls do.  The
+helpers below them only marshal torch tensors or numpy arrays into those calls:
+every step of the classification runs in the CUDA kernels of the library.
+There is no CPU fallback: without the built library every call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from .build import LIB_PATH
+
+JATAM_OK = 0
+JATAM_EINVAL = -1
+JATAM_ENOMEM = -2
+JATAM_ECUDA = -3
+JATAM_ETIMEOUT = -4
+JATAM_EUNSUPPORTED = -5
+
+DET_BOUNDED, ND_LOCAL, ND_STERIC, UNBOUNDED = 0, 1, 2, 3
+JATAM_SAMPLED = 0x1
+JATAM_SYNC = 0x2
+
+RESULT_DTYPE = np.dtype([("cls", "u1"), ("decided_rep", "u1"), ("size", "<u2"), ("shape_hash", "<u4")])
+HIST_DTYPE = np.dtype([("cls", "<u4"), ("shape_hash", "<u4"), ("size", "<u4"), ("flags", "<u4"),
+                       ("count", "<u8"), ("min_id", "<u8")])
+
+
+class jatam_config(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_uint8), ("c", ctypes.c_uint8), ("L", ctypes.c_uint8), ("k", ctypes.c_uint8),
+                ("flags", ctypes.c_uint32), ("seed", ctypes.c_uint64)]
+
+
+class JatamError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"libjatam error {code}: {msg}")
+        self.code = code
+
+
+_lib = None
+_VP = ctypes.c_void_p
+_U64 = ctypes.c_uint64
+_U32 = ctypes.c_uint32
+
+
+def lib():
+    """Load libjatam.so; raises if it has not been built (no fallback)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: build it with __graft_entry__.build() "
+                               "(python -c 'import __graft_entry__ as g; g.build()')")
+        L = ctypes.CDLL(LIB_PATH)
+        L.jatam_enumerate.argtypes = [_VP, _U64, _U64, _VP, _VP, _U32, _VP, _VP]
+        L.jatam_classify_batch.argtypes = [_VP, _VP, _VP, _VP, _U64, _VP, _VP, _U32, _VP, _VP]
+        L.ga_evaluate.argtypes = [_VP, _VP, _U64, _VP, _VP, _VP]
+        L.jatam_philox.argtypes = [_VP, _U64, _VP, _VP]
+        L.jatam_hist_merge.argtypes = [_VP, _U32, _VP, _U32, _VP, _U32, _VP]
+        for f in ("jatam_enumerate", "jatam_classify_batch", "ga_evaluate", "jatam_philox", "jatam_hist_merge"):
+            getattr(L, f).restype = ctypes.c_int
+        L.jatam_profile.argtypes = [ctypes.c_int]
+        L.jatam_profile.restype = ctypes.c_int
+        L.jatam_kernel_ms.argtypes = [ctypes.POINTER(ctypes.c_float)]
+        L.jatam_kernel_ms.restype = ctypes.c_int
+        L.jatam_shutdown.argtypes = []
+        L.jatam_shutdown.restype = None
+        L.jatam_last_error.argtypes = []
+        L.jatam_last_error.restype = ctypes.c_char_p
+        _lib = L
+    return _lib
+
+
+# ---------------------------------------------------------------------------
+# the C ABI, one to one
+# ---------------------------------------------------------------------------
+def jatam_enumerate(cfg, first, count, out, hist, hist_cap, hist_len, stream):
+    return lib().jatam_enumerate(cfg, first, count, out, hist, hist_cap, hist_len, stream)
+
+
+def jatam_classify_batch(cfg, colours, shapes, stream_ids, N, out, hist, hist_cap, hist_len, stream):
+    return lib().jatam_classify_batch(cfg, colours, shapes, stream_ids, N, out, hist, hist_cap, hist_len, stream)
+
+
+def ga_evaluate(cfg, genomes, N, fitness, out, stream):
+    return lib().ga_evaluate(cfg, genomes, N, fitness, out, stream)
+
+
+def jatam_philox(inp, N, out, stream):
+    return lib().jatam_philox(inp, N, out, stream)
+
+
+def jatam_hist_merge(a, na, b, nb, out, cap, length):
+    return lib().jatam_hist_merge(a, na, b, nb, out, cap, length)
+
+
+def jatam_profile(enable):
+    return lib().jatam_profile(int(enable))
+
+
+def jatam_kernel_ms(ms):
+    return lib().jatam_kernel_ms(ms)
+
+
+def jatam_shutdown():
+    lib().jatam_shutdown()
+
+
+def jatam_last_error() -> str:
+    return lib().jatam_last_error().decode()
+
+
+# ---------------------------------------------------------------------------
+# marshalling helpers
+# ---------------------------------------------------------------------------
+def make_config(n, c, L, k, seed, flags=0):
+    return jatam_config(n=n, c=c, L=L, k=k, flags=flags, seed=seed & 0xFFFFFFFFFFFFFFFF)
+
+
+def _addr(x):
+    """Address of a torch tensor, numpy array or int (None -> 0)."""
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    if hasattr(x, "data_ptr"):
+        return x.data_ptr()
+    return x.ctypes.data
+
+
+def _stream_handle(stream):
+    if stream is None:
+        return None
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream  # torch.cuda.Stream
+
+
+def check(rc):
+    if rc != JATAM_OK:
+        raise JatamError(rc, jatam_last_error())
+    return rc
+
+
+def enumerate_space(n, c, L, k, seed, first, count, *, sampled=False, out=None, hist=None, hist_len=None,
+                    hist_cap=0, stream=None, sync=False):
+    """jatam_enumerate on caller buffers (torch tensors or numpy arrays)."""
+    cfg = make_config(n, c, L, k, seed, (JATAM_SAMPLED if sampled else 0) | (JATAM_SYNC if sync else 0))
+    return check(jatam_enumerate(ctypes.addressof(cfg), first, count, _addr(out), _addr(hist), hist_cap,
+                                 _addr(hist_len), _stream_handle(stream)))
+
+
+def classify_batch(colours, *, n=0, c=0, L=0, k=0, seed=0, shapes=None, stream_ids=None, out=None, hist=None,
+                   hist_len=None, hist_cap=0, stream=None, sync=False):
+    N = int(colours.shape[0])
+    cfg = make_config(n, c, L, k, seed, JATAM_SYNC if sync else 0)
+    return check(jatam_classify_batch(ctypes.addressof(cfg), _addr(colours), _addr(shapes), _addr(stream_ids), N,
+                                      _addr(out), _addr(hist), hist_cap, _addr(hist_len), _stream_handle(stream)))
+
+
+def evaluate_genomes(genomes, fitness, *, n, c, L, k, seed, out=None, stream=None, sync=False):
+    cfg = make_config(n, c, L, k, seed, JATAM_SYNC if sync else 0)
+    N = int(genomes.shape[0])
+    return check(ga_evaluate(ctypes.addressof(cfg), _addr(genomes), N, _addr(fitness), _addr(out),
+                             _stream_handle(stream)))
+
+
+def philox(records, out, stream=None):
+    """records: [N][6] uint32 (ctr0..3, key0, key1) -> out [N][4] uint32."""
+    N = int(records.shape[0])
+    return check(jatam_philox(_addr(records), N, _addr(out), _stream_handle(stream)))
+
+
+def last_kernel_ms() -> float:
+    """Duration of the last profiled classification kernel (jatam_profile(1) first)."""
+    ms = ctypes.c_float(0.0)
+    check(jatam_kernel_ms(ctypes.byref(ms)))
+    return float(ms.value)
+
+
+def merge_histograms(a, b):
+    """Host merge of two sorted histograms (numpy HIST_DTYPE arrays)."""
+    a = np.ascontiguousarray(a, HIST_DTYPE)
+    b = np.ascontiguousarray(b, HIST_DTYPE)
+    cap = a.shape[0] + b.shape[0]
+    out = np.zeros(max(cap, 1), HIST_DTYPE)
+    n = ctypes.c_uint32(0)
+    check(jatam_hist_merge(_addr(a) if a.size else None, a.shape[0], _addr(b) if b.size else None, b.shape[0],
+                           out.ctypes.data, cap, ctypes.addressof(n)))
+    return out[: n.value].copy()
+
+
+def results_view(t):
+    """numpy structured view of a result buffer (torch uint8/int64 tensor or numpy)."""
+    if hasattr(t, "cpu"):
+        t = t.cpu().numpy()
+    return np.ascontiguousarray(t).view(np.uint8).reshape(-1).view(RESULT_DTYPE)
+
+
+def hist_view(t, length=None):
+    if hasattr(t, "cpu"):
+        t = t.cpu().numpy()
+    h = np.ascontiguousarray(t).view(np.uint8).reshape(-1).view(HIST_DTYPE)
+    return h if length is None else h[:length]

@@ -1,0 +1,529 @@
+// jatam_api.cu -- host side of libjatam.so: argument checks, the per-device
+// workspace, staging of host buffers, launches, and the error state.
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <string>
+
+#include <cuda_runtime.h>
+
+#include "jatam_internal.cuh"
+
+using namespace jatam;
+
+namespace {
+
+thread_local std::string g_last_error;
+std::mutex g_mutex;
+bool g_profile = false;
+
+int fail(int code, const char *fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_last_error = buf;
+    return code;
+}
+
+#define CUDA_TRY(expr)                                                                        \
+    do {                                                                                      \
+        cudaError_t e_ = (expr);                                                              \
+        if (e_ != cudaSuccess)                                                                \
+            return fail(JATAM_ECUDA, "%s failed: %s", #expr, cudaGetErrorString(e_));         \
+    } while (0)
+
+constexpr unsigned TABLE_LOG2 = 18;  // 262,144 phenotype slots per device
+
+struct Workspace {
+    int device = -1;
+    int num_sms = 0;
+    Table table{};
+    Compact compact{};
+    unsigned long long *work_next = nullptr;
+    unsigned *err = nullptr;
+    unsigned *nkeys = nullptr;
+    unsigned *host_words = nullptr;  // pinned: [0] err, [1] nkeys
+    void *stage_in = nullptr;
+    size_t stage_in_bytes = 0;
+    void *stage_out = nullptr;
+    size_t stage_out_bytes = 0;
+    void *stage_aux = nullptr;
+    size_t stage_aux_bytes = 0;
+    jatam_hist_entry *stage_hist = nullptr;
+    size_t stage_hist_cap = 0;
+    cudaEvent_t last = nullptr;  // end of the previous call's work on this device
+    cudaEvent_t k_start = nullptr, k_stop = nullptr;  // around the last profiled kernel
+    bool k_valid = false;
+    bool attrs_set[3][9] = {};
+};
+
+std::map<int, Workspace *> g_ws;
+
+int grow(void **p, size_t *have, size_t want)
+{
+    if (*have >= want) return JATAM_OK;
+    if (*p) cudaFree(*p);
+    *p = nullptr;
+    *have = 0;
+    size_t sz = want < (1u << 20) ? (1u << 20) : want;
+    cudaError_t e = cudaMalloc(p, sz);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        *p = nullptr;
+        return fail(JATAM_ENOMEM, "cudaMalloc of %zu bytes failed: %s", sz, cudaGetErrorString(e));
+    }
+    *have = sz;
+    return JATAM_OK;
+}
+
+int workspace(Workspace **out)
+{
+    int dev = 0;
+    CUDA_TRY(cudaGetDevice(&dev));
+    auto it = g_ws.find(dev);
+    if (it != g_ws.end()) {
+        *out = it->second;
+        return JATAM_OK;
+    }
+    Workspace *w = new Workspace();
+    w->device = dev;
+    CUDA_TRY(cudaDeviceGetAttribute(&w->num_sms, cudaDevAttrMultiProcessorCount, dev));
+    const size_t cap = size_t(1) << TABLE_LOG2;
+    w->table.cap_log2 = TABLE_LOG2;
+    CUDA_TRY(cudaMalloc(&w->table.key, cap * 8));
+    CUDA_TRY(cudaMalloc(&w->table.count, cap * 8));
+    CUDA_TRY(cudaMalloc(&w->table.min_id, cap * 8));
+    CUDA_TRY(cudaMalloc(&w->table.size_max, cap * 4));
+    CUDA_TRY(cudaMalloc(&w->table.size_min, cap * 4));
+    CUDA_TRY(cudaMalloc(&w->compact.key, cap * 8));
+    CUDA_TRY(cudaMalloc(&w->compact.count, cap * 8));
+    CUDA_TRY(cudaMalloc(&w->compact.min_id, cap * 8));
+    CUDA_TRY(cudaMalloc(&w->compact.size_max, cap * 4));
+    CUDA_TRY(cudaMalloc(&w->compact.size_min, cap * 4));
+    CUDA_TRY(cudaMalloc(&w->work_next, 8));
+    CUDA_TRY(cudaMalloc(&w->err, 4));
+    CUDA_TRY(cudaMalloc(&w->nkeys, 4));
+    CUDA_TRY(cudaMallocHost(&w->host_words, 16));
+    CUDA_TRY(cudaEventCreateWithFlags(&w->last, cudaEventDisableTiming));
+    CUDA_TRY(cudaEventCreate(&w->k_start));
+    CUDA_TRY(cudaEventCreate(&w->k_stop));
+    CUDA_TRY(launch_table_init(w->table, nullptr));
+    CUDA_TRY(launch_reset(w->work_next, w->nkeys, nullptr));
+    CUDA_TRY(cudaMemsetAsync(w->err, 0, 4, nullptr));
+    CUDA_TRY(cudaDeviceSynchronize());
+    g_ws[dev] = w;
+    *out = w;
+    return JATAM_OK;
+}
+
+enum Kind { K_NULL, K_DEVICE, K_HOST };
+
+Kind kind_of(const void *p, int device)
+{
+    if (!p) return K_NULL;
+    cudaPointerAttributes at;
+    cudaError_t e = cudaPointerGetAttributes(&at, p);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return K_HOST;
+    }
+    if ((at.type == cudaMemoryTypeDevice && at.device == device) || at.type == cudaMemoryTypeManaged)
+        return K_DEVICE;
+    if (at.type == cudaMemoryTypeDevice) return K_NULL;  // another device's memory: rejected by the caller
+    return K_HOST;
+}
+
+bool is_pow2(int c) { return c == 1 || c == 2 || c == 4 || c == 8; }
+int log2c(int c) { return c >= 8 ? 3 : c >= 4 ? 2 : c >= 2 ? 1 : 0; }
+int lattice_template(int L) { return L <= 8 ? 8 : L <= 16 ? 16 : 32; }
+
+int check_params(int n, int c, int L, int k, bool packed)
+{
+    if (n < 1 || n > JATAM_MAX_TILES || c < 1 || c > JATAM_MAX_COLOURS || L < 1 || L > JATAM_MAX_GRID || k < 1 ||
+        k > JATAM_MAX_REPLICATES)
+        return fail(JATAM_EUNSUPPORTED, "unsupported parameters n=%d c=%d L=%d k=%d (n 1..4, c 1..8, L 1..32, k 1..255)",
+                    n, c, L, k);
+    if (packed && !is_pow2(c)) return fail(JATAM_EINVAL, "packed genotypes need c to be a power of two, got %d", c);
+    return JATAM_OK;
+}
+
+// launch shape: warps per CTA by lattice template; CTAs = resident CTAs on every SM
+int warps_for(int S) { return S == 32 ? 2 : 4; }
+
+struct Outputs {
+    jatam_result *out_dev = nullptr;
+    int32_t *fit_dev = nullptr;
+    jatam_hist_entry *hist_dev = nullptr;
+    uint32_t *hist_len_dev = nullptr;
+    bool host_out = false, host_fit = false, host_hist = false, host_len = false;
+};
+
+// Run the classification of one launch description plus the histogram
+// kernels, stage host outputs, and synchronise when needed.
+int run(Workspace *w, LaunchArgs a, int S, jatam_result *out, int32_t *fitness, jatam_hist_entry *hist,
+        uint32_t hist_cap, uint32_t *hist_len, bool sync_flag, cudaStream_t st)
+{
+    Outputs o;
+    const Kind ko = kind_of(out, w->device), kf = kind_of(fitness, w->device), kh = kind_of(hist, w->device),
+               kl = kind_of(hist_len, w->device);
+    if ((out && ko == K_NULL) || (fitness && kf == K_NULL) || (hist && kh == K_NULL) || (hist_len && kl == K_NULL))
+        return fail(JATAM_EINVAL, "an output buffer lives on another device");
+    if (hist && !hist_len) return fail(JATAM_EINVAL, "hist needs hist_len");
+    if (hist && hist_cap == 0) return fail(JATAM_EINVAL, "hist_cap must be positive when hist is given");
+    const size_t n_items = (size_t)a.count;
+    // staging: out and fitness share stage_out (out first, 16-byte aligned fitness after it)
+    size_t out_bytes = (ko == K_HOST) ? n_items * sizeof(jatam_result) : 0;
+    size_t fit_off = (out_bytes + 255) & ~size_t(255);
+    size_t fit_bytes = (kf == K_HOST) ? n_items * sizeof(int32_t) : 0;
+    if (out_bytes + fit_bytes) {
+        int rc = grow(&w->stage_out, &w->stage_out_bytes, fit_off + fit_bytes + 256);
+        if (rc) return rc;
+    }
+    o.host_out = ko == K_HOST;
+    o.host_fit = kf == K_HOST;
+    o.out_dev = o.host_out ? reinterpret_cast<jatam_result *>(w->stage_out) : out;
+    o.fit_dev = o.host_fit ? reinterpret_cast<int32_t *>(static_cast<char *>(w->stage_out) + fit_off) : fitness;
+    if (hist) {
+        o.host_hist = kh == K_HOST;
+        o.host_len = kl == K_HOST;
+        if (o.host_hist) {
+            if (w->stage_hist_cap < hist_cap) {
+                if (w->stage_hist) cudaFree(w->stage_hist);
+                w->stage_hist = nullptr;
+                w->stage_hist_cap = 0;
+                cudaError_t e = cudaMalloc(&w->stage_hist, (size_t)hist_cap * sizeof(jatam_hist_entry));
+                if (e != cudaSuccess) {
+                    cudaGetLastError();
+                    return fail(JATAM_ENOMEM, "cannot stage %u histogram entries", hist_cap);
+                }
+                w->stage_hist_cap = hist_cap;
+            }
+            o.hist_dev = w->stage_hist;
+        } else {
+            o.hist_dev = hist;
+        }
+        o.hist_len_dev = o.host_len ? reinterpret_cast<uint32_t *>(w->nkeys) : hist_len;
+    }
+    a.out = o.out_dev;
+    a.fitness = o.fit_dev;
+    a.table = w->table;
+    a.use_hist = hist ? 1 : 0;
+    a.work_next = w->work_next;
+    a.err = w->err;
+
+    const int warps = warps_for(S);
+    const int si = S == 8 ? 0 : S == 16 ? 1 : 2;
+    if (!w->attrs_set[si][warps]) {
+        CUDA_TRY(classify_set_attributes(S, warps));
+        w->attrs_set[si][warps] = true;
+    }
+    int per_sm = 0;
+    CUDA_TRY(classify_occupancy(S, warps, &per_sm));
+    if (per_sm < 1) return fail(JATAM_ECUDA, "classification kernel does not fit on an SM");
+    long long blocks = (long long)per_sm * w->num_sms;
+    const long long lanes_per_cta = 32LL * warps;
+    const long long needed = (long long)((n_items + lanes_per_cta - 1) / lanes_per_cta);
+    if (needed < blocks) blocks = needed < 1 ? 1 : needed;
+
+    CUDA_TRY(cudaStreamWaitEvent(st, w->last, 0));
+    CUDA_TRY(launch_reset(w->work_next, w->nkeys, st));
+    if (g_profile) CUDA_TRY(cudaEventRecord(w->k_start, st));
+    if (n_items) CUDA_TRY(launch_classify(a, S, (int)blocks, warps, st));
+    if (g_profile) {
+        CUDA_TRY(cudaEventRecord(w->k_stop, st));
+        w->k_valid = true;
+    }
+    if (hist) {
+        CUDA_TRY(launch_hist_compact(w->table, w->compact, w->nkeys, 2 * w->num_sms, st));
+        CUDA_TRY(launch_hist_emit(w->compact, w->nkeys, o.hist_dev, hist_cap, o.host_len ? nullptr : o.hist_len_dev,
+                                  w->num_sms, st));
+    }
+    if (o.host_out && n_items)
+        CUDA_TRY(cudaMemcpyAsync(out, o.out_dev, n_items * sizeof(jatam_result), cudaMemcpyDeviceToHost, st));
+    if (o.host_fit && n_items)
+        CUDA_TRY(cudaMemcpyAsync(fitness, o.fit_dev, n_items * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+    const bool must_sync = sync_flag || o.host_out || o.host_fit || o.host_hist || o.host_len;
+    if (must_sync) {
+        CUDA_TRY(cudaMemcpyAsync(&w->host_words[0], w->err, 4, cudaMemcpyDeviceToHost, st));
+        CUDA_TRY(cudaMemcpyAsync(&w->host_words[1], w->nkeys, 4, cudaMemcpyDeviceToHost, st));
+    }
+    CUDA_TRY(cudaEventRecord(w->last, st));
+    if (!must_sync) return JATAM_OK;
+    CUDA_TRY(cudaStreamSynchronize(st));
+    const unsigned err = w->host_words[0];
+    const unsigned nk = w->host_words[1];
+    if (hist) {
+        if (o.host_len) *hist_len = nk;
+        if (o.host_hist && nk) {
+            const size_t nc = nk < hist_cap ? nk : hist_cap;
+            CUDA_TRY(cudaMemcpy(hist, o.hist_dev, nc * sizeof(jatam_hist_entry), cudaMemcpyDeviceToHost));
+        }
+    }
+    if (err) {
+        CUDA_TRY(cudaMemsetAsync(w->err, 0, 4, st));
+        CUDA_TRY(cudaStreamSynchronize(st));
+        if (err & ERR_GUARD) return fail(JATAM_ETIMEOUT, "a bounded device loop found an inconsistent state");
+        if (err & ERR_TABLE_FULL) return fail(JATAM_ENOMEM, "the phenotype table (%u slots) overflowed", 1u << TABLE_LOG2);
+        if (err & ERR_INVALID_ITEM) return fail(JATAM_EINVAL, "an item had a colour >= c or parameters out of range");
+    }
+    if (hist && nk > hist_cap && (o.host_len))
+        return fail(JATAM_EINVAL, "histogram has %u keys but hist_cap is %u", nk, hist_cap);
+    return JATAM_OK;
+}
+
+// copy a host input to the staging buffer, or pass a device pointer through
+int stage_input(Workspace *w, const void *p, size_t bytes, void **stage, size_t *have, const void **dev,
+                cudaStream_t st)
+{
+    Kind k = kind_of(p, w->device);
+    if (k == K_NULL && p) return fail(JATAM_EINVAL, "an input buffer lives on another device");
+    if (k != K_HOST) {
+        *dev = p;
+        return JATAM_OK;
+    }
+    int rc = grow(stage, have, bytes);
+    if (rc) return rc;
+    CUDA_TRY(cudaMemcpyAsync(*stage, p, bytes, cudaMemcpyHostToDevice, st));
+    *dev = *stage;
+    return JATAM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int jatam_enumerate(const jatam_config *cfg, uint64_t first, uint64_t count, jatam_result *out,
+                    jatam_hist_entry *hist, uint32_t hist_cap, uint32_t *hist_len, void *stream)
+{
+    std::lock_guard<std::mutex> lock(g_mutex);
+    g_last_error.clear();
+    if (!cfg) return fail(JATAM_EINVAL, "cfg is NULL");
+    int rc = check_params(cfg->n, cfg->c, cfg->L, cfg->k, true);
+    if (rc) return rc;
+    const int bits = 4 * cfg->n * log2c(cfg->c);
+    const bool sampled = (cfg->flags & JATAM_SAMPLED) != 0;
+    if (!sampled) {
+        const uint64_t space = bits >= 64 ? ~0ull : (1ull << bits);
+        if (first > space || count > space - first)
+            return fail(JATAM_EINVAL, "index range [%llu, %llu + %llu) exceeds the %d-bit space", (unsigned long long)first,
+                        (unsigned long long)first, (unsigned long long)count, bits);
+    } else if (count > ~0ull - first) {
+        return fail(JATAM_EINVAL, "index range overflows");
+    }
+    Workspace *w = nullptr;
+    rc = workspace(&w);
+    if (rc) return rc;
+    LaunchArgs a{};
+    a.mode = sampled ? MODE_SAMPLED : MODE_RANGE;
+    a.first = first;
+    a.count = count;
+    a.n = cfg->n; a.c = cfg->c; a.L = cfg->L; a.k = cfg->k;
+    a.key0 = (uint32_t)cfg->seed;
+    a.key1 = (uint32_t)(cfg->seed >> 32);
+    return run(w, a, lattice_template(cfg->L), out, nullptr, hist, hist_cap, hist_len,
+               (cfg->flags & JATAM_SYNC) != 0, static_cast<cudaStream_t>(stream));
+}
+
+int jatam_classify_batch(const jatam_config *cfg, const uint8_t *colours, const uint8_t *shapes,
+                         const uint64_t *stream_ids, uint64_t N, jatam_result *out, jatam_hist_entry *hist,
+                         uint32_t hist_cap, uint32_t *hist_len, void *stream)
+{
+    std::lock_guard<std::mutex> lock(g_mutex);
+    g_last_error.clear();
+    if (!cfg) return fail(JATAM_EINVAL, "cfg is NULL");
+    if (N && !colours) return fail(JATAM_EINVAL, "colours is NULL");
+    if ((reinterpret_cast<uintptr_t>(colours) & 15) || (reinterpret_cast<uintptr_t>(shapes) & 3) ||
+        (reinterpret_cast<uintptr_t>(stream_ids) & 7))
+        return fail(JATAM_EINVAL, "colours must be 16-byte, shapes 4-byte and stream_ids 8-byte aligned");
+    int S = 32;
+    if (!shapes) {
+        int rc = check_params(cfg->n, cfg->c, cfg->L, cfg->k, false);
+        if (rc) return rc;
+        S = lattice_template(cfg->L);
+    }
+    Workspace *w = nullptr;
+    int rc = workspace(&w);
+    if (rc) return rc;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    CUDA_TRY(cudaStreamWaitEvent(st, w->last, 0));
+    LaunchArgs a{};
+    a.mode = MODE_RECORDS;
+    a.count = N;
+    a.n = cfg->n; a.c = cfg->c; a.L = cfg->L; a.k = cfg->k;
+    a.key0 = (uint32_t)cfg->seed;
+    a.key1 = (uint32_t)(cfg->seed >> 32);
+    // stage host inputs one after the other in stage_in (16-byte aligned pieces)
+    const size_t cb = (size_t)N * 16, sb = shapes ? (size_t)N * 4 : 0, ib = stream_ids ? (size_t)N * 8 : 0;
+    const size_t off_s = (cb + 255) & ~size_t(255), off_i = (off_s + sb + 255) & ~size_t(255);
+    const Kind kc = kind_of(colours, w->device), ks = kind_of(shapes, w->device), ki = kind_of(stream_ids, w->device);
+    if ((kc == K_NULL && colours) || (ks == K_NULL && shapes) || (ki == K_NULL && stream_ids))
+        return fail(JATAM_EINVAL, "an input buffer lives on another device");
+    if (kc == K_HOST || ks == K_HOST || ki == K_HOST) {
+        rc = grow(&w->stage_in, &w->stage_in_bytes, off_i + ib + 256);
+        if (rc) return rc;
+    }
+    char *base = static_cast<char *>(w->stage_in);
+    a.colours = colours;
+    if (kc == K_HOST && N) {
+        CUDA_TRY(cudaMemcpyAsync(base, colours, cb, cudaMemcpyHostToDevice, st));
+        a.colours = reinterpret_cast<const uint8_t *>(base);
+    }
+    a.shapes = shapes;
+    if (ks == K_HOST && N) {
+        CUDA_TRY(cudaMemcpyAsync(base + off_s, shapes, sb, cudaMemcpyHostToDevice, st));
+        a.shapes = reinterpret_cast<const uint8_t *>(base + off_s);
+    }
+    a.ids = reinterpret_cast<const unsigned long long *>(stream_ids);
+    if (ki == K_HOST && N) {
+        CUDA_TRY(cudaMemcpyAsync(base + off_i, stream_ids, ib, cudaMemcpyHostToDevice, st));
+        a.ids = reinterpret_cast<const unsigned long long *>(base + off_i);
+    }
+    return run(w, a, S, out, nullptr, hist, hist_cap, hist_len, (cfg->flags & JATAM_SYNC) != 0, st);
+}
+
+int ga_evaluate(const jatam_config *cfg, const uint64_t *genomes, uint64_t N, int32_t *fitness, jatam_result *out,
+                void *stream)
+{
+    std::lock_guard<std::mutex> lock(g_mutex);
+    g_last_error.clear();
+    if (!cfg) return fail(JATAM_EINVAL, "cfg is NULL");
+    if (!fitness) return fail(JATAM_EINVAL, "fitness is NULL");
+    if (N && !genomes) return fail(JATAM_EINVAL, "genomes is NULL");
+    if (reinterpret_cast<uintptr_t>(genomes) & 7) return fail(JATAM_EINVAL, "genomes must be 8-byte aligned");
+    int rc = check_params(cfg->n, cfg->c, cfg->L, cfg->k, true);
+    if (rc) return rc;
+    Workspace *w = nullptr;
+    rc = workspace(&w);
+    if (rc) return rc;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    CUDA_TRY(cudaStreamWaitEvent(st, w->last, 0));
+    const void *gdev = nullptr;
+    rc = stage_input(w, genomes, (size_t)N * 8, &w->stage_in, &w->stage_in_bytes, &gdev, st);
+    if (rc) return rc;
+    LaunchArgs a{};
+    a.mode = MODE_GENOMES;
+    a.count = N;
+    a.genomes = static_cast<const unsigned long long *>(gdev);
+    a.n = cfg->n; a.c = cfg->c; a.L = cfg->L; a.k = cfg->k;
+    a.key0 = (uint32_t)cfg->seed;
+    a.key1 = (uint32_t)(cfg->seed >> 32);
+    return run(w, a, lattice_template(cfg->L), out, fitness, nullptr, 0, nullptr, (cfg->flags & JATAM_SYNC) != 0, st);
+}
+
+int jatam_philox(const uint32_t *in, uint64_t N, uint32_t *out, void *stream)
+{
+    std::lock_guard<std::mutex> lock(g_mutex);
+    g_last_error.clear();
+    if (N && (!in || !out)) return fail(JATAM_EINVAL, "in/out is NULL");
+    Workspace *w = nullptr;
+    int rc = workspace(&w);
+    if (rc) return rc;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    CUDA_TRY(cudaStreamWaitEvent(st, w->last, 0));
+    const void *din = nullptr;
+    rc = stage_input(w, in, (size_t)N * 24, &w->stage_in, &w->stage_in_bytes, &din, st);
+    if (rc) return rc;
+    const Kind ko = kind_of(out, w->device);
+    if (ko == K_NULL && out) return fail(JATAM_EINVAL, "out lives on another device");
+    uint32_t *dout = out;
+    if (ko == K_HOST) {
+        rc = grow(&w->stage_aux, &w->stage_aux_bytes, (size_t)N * 16);
+        if (rc) return rc;
+        dout = static_cast<uint32_t *>(w->stage_aux);
+    }
+    CUDA_TRY(launch_philox(static_cast<const uint32_t *>(din), N, dout, st));
+    if (ko == K_HOST && N) CUDA_TRY(cudaMemcpyAsync(out, dout, (size_t)N * 16, cudaMemcpyDeviceToHost, st));
+    CUDA_TRY(cudaEventRecord(w->last, st));
+    if (ko == K_HOST || kind_of(in, w->device) == K_HOST) CUDA_TRY(cudaStreamSynchronize(st));
+    return JATAM_OK;
+}
+
+int jatam_hist_merge(const jatam_hist_entry *a, uint32_t na, const jatam_hist_entry *b, uint32_t nb,
+                     jatam_hist_entry *out, uint32_t cap, uint32_t *len)
+{
+    g_last_error.clear();
+    if ((na && !a) || (nb && !b) || !len || (cap && !out)) return fail(JATAM_EINVAL, "NULL argument");
+    uint32_t i = 0, j = 0, m = 0;
+    auto key = [](const jatam_hist_entry &e) { return ((uint64_t)e.cls << 32) | e.shape_hash; };
+    while (i < na || j < nb) {
+        jatam_hist_entry e;
+        if (j >= nb || (i < na && key(a[i]) < key(b[j]))) {
+            e = a[i++];
+        } else if (i >= na || key(b[j]) < key(a[i])) {
+            e = b[j++];
+        } else {
+            e = a[i];
+            const jatam_hist_entry &f = b[j];
+            e.count += f.count;
+            e.min_id = e.min_id < f.min_id ? e.min_id : f.min_id;
+            e.flags |= f.flags | (e.size != f.size ? 1u : 0u);
+            e.size = e.size > f.size ? e.size : f.size;
+            ++i;
+            ++j;
+        }
+        if (m < cap) out[m] = e;
+        ++m;
+    }
+    *len = m;
+    if (m > cap) return fail(JATAM_EINVAL, "merged histogram has %u keys but cap is %u", m, cap);
+    return JATAM_OK;
+}
+
+int jatam_profile(int enable)
+{
+    std::lock_guard<std::mutex> lock(g_mutex);
+    g_last_error.clear();
+    g_profile = enable != 0;
+    return JATAM_OK;
+}
+
+int jatam_kernel_ms(float *ms)
+{
+    std::lock_guard<std::mutex> lock(g_mutex);
+    g_last_error.clear();
+    if (!ms) return fail(JATAM_EINVAL, "ms is NULL");
+    int dev = 0;
+    CUDA_TRY(cudaGetDevice(&dev));
+    auto it = g_ws.find(dev);
+    if (it == g_ws.end() || !it->second->k_valid) return fail(JATAM_EINVAL, "no profiled call on this device");
+    CUDA_TRY(cudaEventSynchronize(it->second->k_stop));
+    CUDA_TRY(cudaEventElapsedTime(ms, it->second->k_start, it->second->k_stop));
+    return JATAM_OK;
+}
+
+void jatam_shutdown(void)
+{
+    std::lock_guard<std::mutex> lock(g_mutex);
+    int cur = 0;
+    cudaGetDevice(&cur);
+    for (auto &kv : g_ws) {
+        Workspace *w = kv.second;
+        cudaSetDevice(w->device);
+        cudaDeviceSynchronize();
+        cudaFree(w->table.key); cudaFree(w->table.count); cudaFree(w->table.min_id);
+        cudaFree(w->table.size_max); cudaFree(w->table.size_min);
+        cudaFree(w->compact.key); cudaFree(w->compact.count); cudaFree(w->compact.min_id);
+        cudaFree(w->compact.size_max); cudaFree(w->compact.size_min);
+        cudaFree(w->work_next); cudaFree(w->err); cudaFree(w->nkeys);
+        cudaFreeHost(w->host_words);
+        if (w->stage_in) cudaFree(w->stage_in);
+        if (w->stage_out) cudaFree(w->stage_out);
+        if (w->stage_aux) cudaFree(w->stage_aux);
+        if (w->stage_hist) cudaFree(w->stage_hist);
+        cudaEventDestroy(w->last);
+        cudaEventDestroy(w->k_start);
+        cudaEventDestroy(w->k_stop);
+        delete w;
+    }
+    g_ws.clear();
+    cudaSetDevice(cur);
+}
+
+const char *jatam_last_error(void) { return g_last_error.c_str(); }
+
+}  // extern "C"

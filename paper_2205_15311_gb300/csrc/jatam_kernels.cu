@@ -1,0 +1,822 @@
+// jatam_kernels.cu -- sm_103a kernels of libjatam.so.
+//
+// One persistent warp serves 32 genotypes at a time, one per lane.  Each lane
+// grows the replicate assemblies of its genotype one tile per loop iteration
+// (Section 2.4: stochastic addition of bonding tiles until no tile fits or the
+// grid edge is reached).  The lane's lattice lives in shared memory,
+// interleaved so that word w of lane l sits at [w * 32 + l]: every lane always
+// addresses its own bank, so the lane-private accesses never conflict (the
+// bank-per-assembly idea of Section 2.4, kept because it still holds on
+// sm_103a).  The per-genotype work that does not vectorise over lanes --
+// building the binding tables and the canonical form of the final shape -- is
+// done by the whole warp for one lane at a time, so it never serialises the
+// warp behind a single lane.
+//
+// Per lane, for a lattice with rows of S bits (L <= S):
+//   OCCA[NW]   occupancy of replicate 0 (kept for the comparison and the shape)
+//   OCCB[NW]   occupancy of replicates 1..k-1
+//   FRONT[NW]  frontier: empty in-grid sites with exactly one distinct candidate
+//   NIB[S*S/8] 4-bit tuple id per cell: the placed tuple of an occupied cell or
+//              the single candidate of a frontier cell
+//   NBM[32]    NBM[2 t + d/2] >> 16 (d & 1): the set of tuple ids that can
+//              attach on side d of a placed tuple t (16 bits)
+// A tuple id is the lowest (tile, rotation) index 4 t + r with that rotated
+// colour tuple, so equal tuples (repeated tile types, symmetric tiles) share
+// an id and never count as ambiguity (Section 2.4).
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "jatam_internal.cuh"
+
+namespace jatam {
+namespace {
+
+constexpr unsigned FULL = 0xffffffffu;
+constexpr int HIST_SLOTS = 256;  // per-CTA phenotype aggregation table
+constexpr int CHUNK = 32;        // items taken from the global counter at once
+
+enum Phase : int { PH_NEED = 0, PH_INIT, PH_START, PH_GROW, PH_SHAPE, PH_WRITE, PH_DONE };
+
+template <int S>
+struct Geo {
+    static constexpr int NW = (S * S) / 32;  // words per bitmap
+    static constexpr int LOG2S = (S == 8) ? 3 : (S == 16) ? 4 : 5;
+    static constexpr int OCCA = 0;
+    static constexpr int OCCB = NW;
+    static constexpr int FRONT = 2 * NW;
+    static constexpr int NIB = 3 * NW;
+    static constexpr int NBM = 3 * NW + (S * S) / 8;
+    static constexpr int WORDS = NBM + 32;  // 32-bit words per lane
+};
+
+// ---------------------------------------------------------------------------
+// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11)
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint4 philox4x32_10(uint4 x, uint32_t k0, uint32_t k1)
+{
+#pragma unroll
+    for (int round = 0; round < 10; ++round) {
+        const uint32_t lo0 = 0xD2511F53u * x.x, hi0 = __umulhi(0xD2511F53u, x.x);
+        const uint32_t lo1 = 0xCD9E8D57u * x.z, hi1 = __umulhi(0xCD9E8D57u, x.z);
+        x = make_uint4(hi1 ^ x.y ^ k0, lo1, hi0 ^ x.w ^ k1, lo0);
+        k0 += 0x9E3779B9u;
+        k1 += 0xBB67AE85u;
+    }
+    return x;
+}
+
+// Jenkins one-at-a-time, one byte at a time (Section 2.5).
+__device__ __forceinline__ uint32_t oaat_add(uint32_t h, uint32_t byte)
+{
+    h += byte;
+    h += h << 10;
+    h ^= h >> 6;
+    return h;
+}
+__device__ __forceinline__ uint32_t oaat_finish(uint32_t h)
+{
+    h += h << 3;
+    h ^= h >> 11;
+    h += h << 15;
+    return h;
+}
+
+// position of the i-th (0-based) set bit of v; requires i < popc(v)
+__device__ __forceinline__ int nth_set(uint32_t v, uint32_t i)
+{
+    int pos = 0;
+    uint32_t c = __popc(v & 0xFFFFu);
+    if (i >= c) { i -= c; v >>= 16; pos += 16; }
+    c = __popc(v & 0xFFu);
+    if (i >= c) { i -= c; v >>= 8; pos += 8; }
+    c = __popc(v & 0xFu);
+    if (i >= c) { i -= c; v >>= 4; pos += 4; }
+    c = __popc(v & 0x3u);
+    if (i >= c) { i -= c; v >>= 2; pos += 2; }
+    if (i >= (v & 1u)) pos += 1;
+    return pos;
+}
+
+__device__ __forceinline__ unsigned lanemask_lt()
+{
+    unsigned m;
+    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+    return m;
+}
+
+template <int S>
+__device__ __forceinline__ int nib_get(const uint32_t *my, int b)
+{
+    return (my[(Geo<S>::NIB + (b >> 3)) * 32] >> ((b & 7) * 4)) & 15;
+}
+template <int S>
+__device__ __forceinline__ void nib_set(uint32_t *my, int b, int v)
+{
+    uint32_t *p = &my[(Geo<S>::NIB + (b >> 3)) * 32];
+    const int sh = (b & 7) * 4;
+    *p = (*p & ~(15u << sh)) | ((uint32_t)v << sh);
+}
+
+// state of one lane's genotype
+struct Lane {
+    int phase;
+    unsigned long long item;  // output position
+    unsigned long long sid;   // stream id
+    unsigned long long cols;  // colour of edge e of tile t at nibble 4 t + e
+    int n, c, L, k;
+    int rep, step, size, size0, nF;
+    int ymin, ymax, xmin, xmax;  // bounding box of the current replicate
+    int x0, x1, y0, y1;          // bounding box of replicate 0
+    int dlo, dhi;                // rows that may be dirty in any bitmap
+    int blo, bhi;                // rows of OCCB written by the current replicate
+    int diverged;                // replicate j > 0 can no longer end in replicate 0's configuration
+    int cls, decided;
+    uint32_t hash;
+    uint32_t pblk;               // Philox block held in pbuf
+    uint4 pbuf;
+};
+
+template <int S>
+__device__ __forceinline__ void clear_rows(uint32_t *my, int base, int lo, int hi)
+{
+    const int wlo = (lo * S) >> 5, whi = (hi * S) >> 5;
+    for (int w = wlo; w <= whi; ++w) my[(base + w) * 32] = 0u;
+}
+
+// ---------------------------------------------------------------------------
+// warp-cooperative binding tables for owner lane o (all 32 lanes take part)
+// ---------------------------------------------------------------------------
+template <int S>
+__device__ __forceinline__ void coop_tables(int o, uint32_t *warp_lanes, const Lane &Ls, int lane)
+{
+    using G = Geo<S>;
+    const uint32_t clo = __shfl_sync(FULL, (uint32_t)Ls.cols, o);
+    const uint32_t chi = __shfl_sync(FULL, (uint32_t)(Ls.cols >> 32), o);
+    const int n = __shfl_sync(FULL, Ls.n, o);
+    const int c = __shfl_sync(FULL, Ls.c, o);
+    const unsigned long long cols = ((unsigned long long)chi << 32) | clo;
+    const int t = lane >> 2, r = lane & 3;
+    const bool valid = lane < 16 && t < n;
+    int s[4];
+#pragma unroll
+    for (int d = 0; d < 4; ++d) {
+        // clockwise rotation by r: the edge (d - r) mod 4 now faces direction d
+        s[d] = valid ? (int)((cols >> (4 * (4 * t + ((d - r) & 3)))) & 15u) : 0;
+    }
+    const uint32_t tup = valid ? (uint32_t)(s[0] | (s[1] << 4) | (s[2] << 8) | (s[3] << 12)) : (0x10000u | lane);
+    const uint32_t same = __match_any_sync(FULL, tup);
+    const bool is_rep = valid && (__ffs(same) - 1 == lane);
+    const uint32_t reps = __ballot_sync(FULL, is_rep);
+    // bit-sliced colour planes: sl[e][b] = reps whose side e has bit b set
+    uint32_t sl[4][3];
+#pragma unroll
+    for (int e = 0; e < 4; ++e)
+#pragma unroll
+        for (int b = 0; b < 3; ++b) sl[e][b] = __ballot_sync(FULL, is_rep && ((s[e] >> b) & 1));
+    if (is_rep) {
+        uint32_t M[4];
+#pragma unroll
+        for (int d = 0; d < 4; ++d) {
+            const int a = s[d];
+            // the interaction matrix pairs 1-2, 3-4, 5-6; 0 and an odd top colour have no partner
+            const int pa = (a == 0) ? -1 : (a & 1) ? ((a + 1 < c) ? a + 1 : -1) : a - 1;
+            uint32_t m = 0;
+            if (pa >= 0) {
+                m = reps;
+#pragma unroll
+                for (int b = 0; b < 3; ++b) m &= ((pa >> b) & 1) ? sl[(d + 2) & 3][b] : ~sl[(d + 2) & 3][b];
+            }
+            M[d] = m & 0xFFFFu;
+        }
+        uint32_t *ob = warp_lanes + o;
+        ob[(G::NBM + 2 * lane) * 32] = M[0] | (M[1] << 16);
+        ob[(G::NBM + 2 * lane + 1) * 32] = M[2] | (M[3] << 16);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// warp-cooperative canonical form + hash of owner o's replicate-0 shape
+// ---------------------------------------------------------------------------
+template <int S>
+__device__ __forceinline__ uint32_t coop_shape_hash(int o, const uint32_t *warp_lanes, const Lane &Ls, int lane)
+{
+    using G = Geo<S>;
+    const int x0 = __shfl_sync(FULL, Ls.x0, o), x1 = __shfl_sync(FULL, Ls.x1, o);
+    const int y0 = __shfl_sync(FULL, Ls.y0, o), y1 = __shfl_sync(FULL, Ls.y1, o);
+    const int h = y1 - y0 + 1, w = x1 - x0 + 1;
+    const uint32_t wmask = (w >= 32) ? FULL : ((1u << w) - 1u);
+    uint32_t r = 0;  // lane i < h: row i of the crop, bit j = cell (x0 + j, y0 + i)
+    if (lane < h) {
+        const int b = (y0 + lane) * S + x0;
+        r = (warp_lanes[(G::OCCA + (b >> 5)) * 32 + o] >> (b & 31)) & wmask;
+    }
+    uint32_t col = 0;  // lane j < w: column j, bit i = cell (x0 + j, y0 + i)
+    for (int j = 0; j < w; ++j) {
+        const uint32_t bj = __ballot_sync(FULL, (r >> j) & 1u);
+        if (lane == j) col = bj;
+    }
+    const uint32_t rrev = __shfl_sync(FULL, r, (h - 1 - lane) & 31);
+    const uint32_t crev = __shfl_sync(FULL, col, (w - 1 - lane) & 31);
+    // the 8 images, each as rows whose first cell is the most significant bit
+    uint32_t v[8];
+    v[0] = __brev(r) >> (32 - w);     // identity
+    v[1] = r;                         // mirror x
+    v[2] = __brev(rrev) >> (32 - w);  // mirror y
+    v[3] = rrev;                      // half turn
+    v[4] = __brev(col) >> (32 - h);   // transpose
+    v[5] = col;                       // quarter turn
+    v[6] = __brev(crev) >> (32 - h);  // quarter turn the other way
+    v[7] = crev;                      // anti-transpose
+    // smallest (height, width) first: rows-images have (h, w), column-images (w, h)
+    const int start = (h <= w) ? 0 : 4;
+    const int stop = (h >= w) ? 8 : 4;
+    const int hc = (start == 0) ? h : w;
+    const int wc = (start == 0) ? w : h;
+    uint32_t best = v[start];
+#pragma unroll
+    for (int t = 1; t < 8; ++t) {
+        if (t > start && t < stop) {
+            const uint32_t diff = __ballot_sync(FULL, lane < hc && v[t] != best);
+            if (diff) {
+                const int f = __ffs(diff) - 1;
+                const uint32_t a = __shfl_sync(FULL, v[t], f);
+                const uint32_t b = __shfl_sync(FULL, best, f);
+                if (a < b) best = v[t];
+            }
+        }
+    }
+    // one-at-a-time over (h, w) and (x, y) of every occupied cell, row-major
+    uint32_t hsh = oaat_add(0u, (uint32_t)hc);
+    hsh = oaat_add(hsh, (uint32_t)wc);
+    for (int i = 0; i < hc; ++i) {
+        uint32_t row = __shfl_sync(FULL, best, i);
+        while (row) {
+            const int p = 31 - __clz(row);
+            hsh = oaat_add(hsh, (uint32_t)(wc - 1 - p));
+            hsh = oaat_add(hsh, (uint32_t)i);
+            row &= ~(1u << p);
+        }
+    }
+    return oaat_finish(hsh);
+}
+
+// ---------------------------------------------------------------------------
+// one growth step of one lane: seed placement or one drawn placement, then the
+// evaluation of the new tile's empty neighbours and the replicate rule
+// ---------------------------------------------------------------------------
+template <int S>
+__device__ __forceinline__ void lane_step(Lane &Ls, uint32_t *my, uint32_t k0, uint32_t k1, unsigned *err)
+{
+    using G = Geo<S>;
+    const int occ = (Ls.rep == 0) ? G::OCCA : G::OCCB;
+    int px, py, tau;
+    if (Ls.phase == PH_START) {
+        if (Ls.rep == 0) {
+            if (Ls.dlo <= Ls.dhi) {
+                const int lo = max(Ls.dlo, 0), hi = min(Ls.dhi, S - 1);
+                clear_rows<S>(my, G::OCCA, lo, hi);
+                clear_rows<S>(my, G::OCCB, lo, hi);
+                clear_rows<S>(my, G::FRONT, lo, hi);
+            }
+            Ls.dlo = S;
+            Ls.dhi = -1;
+        } else if (Ls.blo <= Ls.bhi) {
+            clear_rows<S>(my, G::OCCB, Ls.blo, Ls.bhi);  // FRONT is empty: the replicate terminated
+        }
+        Ls.blo = S;
+        Ls.bhi = -1;
+        px = py = Ls.L >> 1;
+        tau = 0;
+        const int b = py * S + px;
+        my[(occ + (b >> 5)) * 32] |= 1u << (b & 31);
+        if (Ls.rep == 0) nib_set<S>(my, b, 0);
+        Ls.size = 1;
+        Ls.step = 0;
+        Ls.nF = 0;
+        Ls.diverged = 0;
+        Ls.ymin = Ls.ymax = py;
+        Ls.xmin = Ls.xmax = px;
+        Ls.pblk = 0xFFFFFFFFu;
+        Ls.phase = PH_GROW;
+    } else {
+        const uint32_t blk = (uint32_t)Ls.step >> 2;
+        if (blk != Ls.pblk) {
+            Ls.pbuf = philox4x32_10(make_uint4(blk, (uint32_t)Ls.rep, (uint32_t)Ls.sid, (uint32_t)(Ls.sid >> 32)),
+                                    k0, k1);
+            Ls.pblk = blk;
+        }
+        const int sel = Ls.step & 3;
+        const uint32_t u = sel == 0 ? Ls.pbuf.x : sel == 1 ? Ls.pbuf.y : sel == 2 ? Ls.pbuf.z : Ls.pbuf.w;
+        uint32_t i = __umulhi(u, (uint32_t)Ls.nF);
+        int w = (max(Ls.ymin - 1, 0) * S) >> 5;
+        uint32_t f = 0;
+        for (;;) {
+            f = my[(G::FRONT + w) * 32];
+            const uint32_t cnt = __popc(f);
+            if (i < cnt) break;
+            i -= cnt;
+            if (++w >= G::NW) {
+                atomicOr(err, ERR_GUARD);
+                Ls.cls = 255;
+                Ls.phase = PH_WRITE;
+                return;
+            }
+        }
+        const int bit = nth_set(f, i);
+        const int b = w * 32 + bit;
+        px = b & (S - 1);
+        py = b >> G::LOG2S;
+        tau = nib_get<S>(my, b);
+        my[(G::FRONT + w) * 32] = f & ~(1u << bit);
+        my[(occ + w) * 32] |= 1u << bit;
+        Ls.nF -= 1;
+        Ls.size += 1;
+        Ls.step += 1;
+        Ls.ymin = min(Ls.ymin, py);
+        Ls.ymax = max(Ls.ymax, py);
+        Ls.xmin = min(Ls.xmin, px);
+        Ls.xmax = max(Ls.xmax, px);
+    }
+    Ls.dlo = min(Ls.dlo, py - 1);
+    Ls.dhi = max(Ls.dhi, py + 1);
+    if (Ls.rep > 0) {
+        Ls.blo = min(Ls.blo, py);
+        Ls.bhi = max(Ls.bhi, py);
+    }
+
+    // the empty neighbours of the new tile: only their candidate sets changed
+    const uint32_t m01 = my[(G::NBM + 2 * tau) * 32];
+    const uint32_t m23 = my[(G::NBM + 2 * tau + 1) * 32];
+    bool nd = false, unb = false;
+#pragma unroll
+    for (int d = 0; d < 4; ++d) {
+        const uint32_t M = ((d == 0) ? m01 : (d == 1) ? (m01 >> 16) : (d == 2) ? m23 : (m23 >> 16)) & 0xFFFFu;
+        const int qx = px + (d == 1) - (d == 3);
+        const int qy = py + (d == 2) - (d == 0);
+        if (qx < 0 || qy < 0 || qx >= Ls.L || qy >= Ls.L) {
+            // a site outside the grid: a single candidate means unbounded growth
+            if (M) {
+                if (M & (M - 1)) nd = true;
+                else unb = true;
+            }
+            continue;
+        }
+        const int qb = qy * S + qx;
+        const int qw = qb >> 5;
+        const uint32_t qbit = 1u << (qb & 31);
+        if (my[(occ + qw) * 32] & qbit) continue;
+        const uint32_t fw = my[(G::FRONT + qw) * 32];
+        if (fw & qbit) {
+            // already a frontier site with one candidate: any other one is ambiguity
+            if (M & ~(1u << nib_get<S>(my, qb))) nd = true;
+        } else if (M) {
+            if (M & (M - 1)) {
+                nd = true;
+            } else {
+                const int tn = __ffs(M) - 1;
+                if (Ls.rep > 0 && !Ls.diverged) {
+                    // replicate 0 must hold the same tuple here, or this replicate
+                    // cannot end in replicate 0's configuration
+                    if (!(my[(G::OCCA + qw) * 32] & qbit) || nib_get<S>(my, qb) != tn) Ls.diverged = 1;
+                }
+                nib_set<S>(my, qb, tn);
+                my[(G::FRONT + qw) * 32] = fw | qbit;
+                Ls.nF += 1;
+            }
+        }
+    }
+    if (!(nd || unb || Ls.nF == 0)) return;
+    // the replicate is decided; apply the first-deciding-replicate rule
+    if (nd) {
+        Ls.cls = JATAM_ND_LOCAL;
+        Ls.decided = Ls.rep;
+        Ls.phase = PH_WRITE;
+        return;
+    }
+    if (unb) {
+        Ls.cls = JATAM_UNBOUNDED;
+        Ls.decided = Ls.rep;
+        Ls.phase = PH_WRITE;
+        return;
+    }
+    if (Ls.rep == 0) {
+        Ls.size0 = Ls.size;
+        Ls.x0 = Ls.xmin;
+        Ls.x1 = Ls.xmax;
+        Ls.y0 = Ls.ymin;
+        Ls.y1 = Ls.ymax;
+    } else if (Ls.diverged || Ls.size != Ls.size0) {
+        Ls.cls = JATAM_ND_STERIC;
+        Ls.decided = Ls.rep;
+        Ls.phase = PH_SHAPE;
+        return;
+    }
+    if (Ls.rep + 1 >= Ls.k) {
+        Ls.cls = JATAM_DET_BOUNDED;
+        Ls.decided = Ls.k;
+        Ls.phase = PH_SHAPE;
+    } else {
+        Ls.rep += 1;
+        Ls.phase = PH_START;
+    }
+}
+
+__device__ __forceinline__ unsigned table_slot(unsigned long long key, unsigned log2cap)
+{
+    return (unsigned)((key * 0x9E3779B97F4A7C15ull) >> (64 - log2cap));
+}
+
+__device__ void table_insert(const Table &T, unsigned long long key, unsigned long long cnt,
+                             unsigned long long mid, unsigned smax, unsigned smin, unsigned *err)
+{
+    const unsigned cap = 1u << T.cap_log2;
+    unsigned slot = table_slot(key, T.cap_log2);
+    for (unsigned p = 0; p < cap; ++p) {
+        const unsigned long long old = atomicCAS(&T.key[slot], EMPTY_KEY, key);
+        if (old == EMPTY_KEY || old == key) {
+            atomicAdd(&T.count[slot], cnt);
+            atomicMin(&T.min_id[slot], mid);
+            atomicMax(&T.size_max[slot], smax);
+            atomicMin(&T.size_min[slot], smin);
+            return;
+        }
+        slot = (slot + 1) & (cap - 1);
+    }
+    atomicOr(err, ERR_TABLE_FULL);
+}
+
+struct SmemHist {
+    unsigned long long key[HIST_SLOTS];
+    unsigned long long min_id[HIST_SLOTS];
+    unsigned count[HIST_SLOTS];
+    unsigned smax[HIST_SLOTS];
+    unsigned smin[HIST_SLOTS];
+};
+
+__device__ __forceinline__ void hist_insert(SmemHist &H, const Table &T, unsigned long long key,
+                                            unsigned long long id, unsigned size, unsigned *err)
+{
+    unsigned slot = table_slot(key, 8);
+    for (int p = 0; p < 16; ++p) {
+        const unsigned long long old = atomicCAS(&H.key[slot], EMPTY_KEY, key);
+        if (old == EMPTY_KEY || old == key) {
+            atomicAdd(&H.count[slot], 1u);
+            atomicMin(&H.min_id[slot], id);
+            atomicMax(&H.smax[slot], size);
+            atomicMin(&H.smin[slot], size);
+            return;
+        }
+        slot = (slot + 1) & (HIST_SLOTS - 1);
+    }
+    table_insert(T, key, 1ull, id, size, size, err);
+}
+
+// decode a packed genotype into nibble-packed colours (tiles seed first,
+// N, E, S, W, b bits per colour, the first tile's N edge most significant)
+__device__ __forceinline__ unsigned long long unpack_genotype(unsigned long long g, int n, int b)
+{
+    unsigned long long cols = 0;
+    const unsigned long long cm = (1ull << b) - 1ull;
+    for (int t = 0; t < n; ++t)
+        for (int e = 0; e < 4; ++e) {
+            const int pos = b * (4 * (n - 1 - t) + (3 - e));
+            cols |= ((g >> pos) & cm) << (4 * (4 * t + e));
+        }
+    return cols;
+}
+
+__device__ __forceinline__ int log2_colours(int c) { return c >= 8 ? 3 : c >= 4 ? 2 : c >= 2 ? 1 : 0; }
+
+template <int S>
+__global__ void __launch_bounds__(256) classify_kernel(const LaunchArgs a)
+{
+    using G = Geo<S>;
+    extern __shared__ uint32_t smem_lanes[];
+    __shared__ SmemHist H;
+    const int lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5;
+    uint32_t *warp_lanes = smem_lanes + (size_t)warp * G::WORDS * 32;
+    uint32_t *my = warp_lanes + lane;
+
+    for (int i = threadIdx.x; i < HIST_SLOTS; i += blockDim.x) {
+        H.key[i] = EMPTY_KEY;
+        H.min_id[i] = ~0ull;
+        H.count[i] = 0u;
+        H.smax[i] = 0u;
+        H.smin[i] = 0xFFFFFFFFu;
+    }
+    for (int w = 0; w < 3 * G::NW; ++w) my[w * 32] = 0u;
+    __syncthreads();
+
+    Lane Ls;
+    Ls.phase = PH_NEED;
+    Ls.dlo = S;
+    Ls.dhi = -1;
+    Ls.blo = S;
+    Ls.bhi = -1;
+    Ls.n = a.n; Ls.c = a.c; Ls.L = a.L; Ls.k = a.k;
+    Ls.cls = 0; Ls.decided = 0; Ls.hash = 0; Ls.size0 = 0;
+    Ls.item = 0; Ls.sid = 0; Ls.cols = 0;
+    Ls.rep = Ls.step = Ls.size = Ls.nF = 0;
+    Ls.x0 = Ls.x1 = Ls.y0 = Ls.y1 = 0;
+    Ls.ymin = Ls.ymax = Ls.xmin = Ls.xmax = 0;
+    Ls.diverged = 0;
+    Ls.pblk = 0xFFFFFFFFu;
+    Ls.pbuf = make_uint4(0, 0, 0, 0);
+    unsigned long long q_next = 0, q_end = 0;  // this warp's slice of the work counter
+    const int b_uniform = log2_colours(a.c);
+
+    for (;;) {
+        // ---- hand out new items to idle lanes, then build their tables together
+        const unsigned need = __ballot_sync(FULL, Ls.phase == PH_NEED);
+        if (need) {
+            const int cnt = __popc(need);
+            const int rank = __popc(need & lanemask_lt());
+            unsigned long long my_idx = ~0ull;
+            int assigned = 0;
+            while (assigned < cnt) {
+                if (q_next >= q_end) {
+                    unsigned long long nb = 0;
+                    if (lane == 0) nb = atomicAdd(a.work_next, (unsigned long long)CHUNK);
+                    nb = __shfl_sync(FULL, nb, 0);
+                    if (nb >= a.count) break;
+                    q_next = nb;
+                    q_end = min(nb + (unsigned long long)CHUNK, a.count);
+                }
+                const int take = (int)min((unsigned long long)(cnt - assigned), q_end - q_next);
+                if (Ls.phase == PH_NEED && rank >= assigned && rank < assigned + take)
+                    my_idx = q_next + (unsigned long long)(rank - assigned);
+                q_next += (unsigned long long)take;
+                assigned += take;
+            }
+            if (Ls.phase == PH_NEED) {
+                if (my_idx == ~0ull) {
+                    Ls.phase = PH_DONE;
+                } else {
+                    Ls.item = my_idx;
+                    Ls.phase = PH_INIT;
+                    if (a.mode == MODE_RECORDS) {
+                        const uint4 raw = *reinterpret_cast<const uint4 *>(a.colours + 16ull * my_idx);
+                        if (a.shapes) {
+                            const uint32_t sh = *reinterpret_cast<const uint32_t *>(a.shapes + 4ull * my_idx);
+                            Ls.n = sh & 255; Ls.c = (sh >> 8) & 255; Ls.L = (sh >> 16) & 255; Ls.k = sh >> 24;
+                        }
+                        Ls.sid = a.ids ? a.ids[my_idx] : my_idx;
+                        unsigned long long cols = 0;
+                        bool ok = Ls.n >= 1 && Ls.n <= 4 && Ls.c >= 1 && Ls.c <= 8 && Ls.L >= 1 && Ls.L <= S &&
+                                  Ls.k >= 1;
+                        const uint32_t wv[4] = {raw.x, raw.y, raw.z, raw.w};
+#pragma unroll
+                        for (int e = 0; e < 16; ++e) {
+                            const int v = (wv[e >> 2] >> (8 * (e & 3))) & 255;
+                            if (e < 4 * Ls.n) {
+                                if (v >= Ls.c) ok = false;
+                                cols |= (unsigned long long)(v & 15) << (4 * e);
+                            }
+                        }
+                        Ls.cols = cols;
+                        if (!ok) {
+                            atomicOr(a.err, ERR_INVALID_ITEM);
+                            Ls.cls = 255;
+                            Ls.decided = 0;
+                            Ls.size0 = 0;
+                            Ls.hash = 0;
+                            Ls.phase = PH_WRITE;
+                        }
+                    } else {
+                        unsigned long long g;
+                        if (a.mode == MODE_RANGE) {
+                            g = a.first + my_idx;
+                        } else if (a.mode == MODE_GENOMES) {
+                            g = a.genomes[my_idx];
+                        } else {
+                            const unsigned long long i = a.first + my_idx;
+                            const uint4 w = philox4x32_10(make_uint4(0u, 1u << 24, (uint32_t)i, (uint32_t)(i >> 32)),
+                                                          a.key0, a.key1);
+                            g = ((unsigned long long)w.y << 32) | w.x;
+                        }
+                        const int bits = 4 * a.n * b_uniform;
+                        if (bits < 64) g &= (1ull << bits) - 1ull;
+                        Ls.sid = g;
+                        Ls.cols = unpack_genotype(g, a.n, b_uniform);
+                    }
+                }
+            }
+            unsigned init = __ballot_sync(FULL, Ls.phase == PH_INIT);
+            while (init) {
+                const int o = __ffs(init) - 1;
+                init &= init - 1;
+                coop_tables<S>(o, warp_lanes, Ls, lane);
+            }
+            __syncwarp();
+            if (Ls.phase == PH_INIT) {
+                Ls.rep = 0;
+                Ls.phase = PH_START;
+            }
+        }
+        if (__all_sync(FULL, Ls.phase == PH_DONE)) break;
+
+        // ---- one assembly step per busy lane
+        if (Ls.phase == PH_START || Ls.phase == PH_GROW) lane_step<S>(Ls, my, a.key0, a.key1, a.err);
+
+        // ---- canonical shapes of finished genotypes, one warp-wide job each
+        unsigned shp = __ballot_sync(FULL, Ls.phase == PH_SHAPE);
+        while (shp) {
+            const int o = __ffs(shp) - 1;
+            shp &= shp - 1;
+            const uint32_t hv = coop_shape_hash<S>(o, warp_lanes, Ls, lane);
+            if (lane == o) {
+                Ls.hash = hv;
+                Ls.phase = PH_WRITE;
+            }
+        }
+        if (Ls.phase == PH_WRITE) {
+            const bool shaped = Ls.cls == JATAM_DET_BOUNDED || Ls.cls == JATAM_ND_STERIC;
+            const unsigned size = shaped ? (unsigned)Ls.size0 : 0u;
+            const uint32_t hash = shaped ? Ls.hash : 0u;
+            if (a.out) {
+                const uint32_t w0 = (uint32_t)(Ls.cls & 255) | ((uint32_t)(Ls.decided & 255) << 8) | (size << 16);
+                reinterpret_cast<uint2 *>(a.out)[Ls.item] = make_uint2(w0, hash);
+            }
+            if (a.fitness) a.fitness[Ls.item] = (Ls.cls == JATAM_DET_BOUNDED) ? (int32_t)size : 0;
+            if (a.use_hist && Ls.cls != 255)
+                hist_insert(H, a.table, ((unsigned long long)Ls.cls << 32) | hash, Ls.sid, size, a.err);
+            Ls.phase = PH_NEED;
+        }
+    }
+
+    __syncthreads();
+    if (a.use_hist) {
+        for (int i = threadIdx.x; i < HIST_SLOTS; i += blockDim.x)
+            if (H.key[i] != EMPTY_KEY)
+                table_insert(a.table, H.key[i], H.count[i], H.min_id[i], H.smax[i], H.smin[i], a.err);
+    }
+}
+
+__global__ void reset_kernel(unsigned long long *work_next, unsigned *nkeys)
+{
+    *work_next = 0ull;
+    *nkeys = 0u;
+}
+
+__global__ void table_init_kernel(Table t)
+{
+    const unsigned cap = 1u << t.cap_log2;
+    for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < cap; i += gridDim.x * blockDim.x) {
+        t.key[i] = EMPTY_KEY;
+        t.count[i] = 0ull;
+        t.min_id[i] = ~0ull;
+        t.size_max[i] = 0u;
+        t.size_min[i] = 0xFFFFFFFFu;
+    }
+}
+
+// move the used slots into a dense list and leave the table empty again
+__global__ void hist_compact_kernel(Table t, Compact c, unsigned *nkeys)
+{
+    const unsigned cap = 1u << t.cap_log2;
+    for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < cap; i += gridDim.x * blockDim.x) {
+        const unsigned long long k = t.key[i];
+        if (k == EMPTY_KEY) continue;
+        const unsigned j = atomicAdd(nkeys, 1u);
+        c.key[j] = k;
+        c.count[j] = t.count[i];
+        c.min_id[j] = t.min_id[i];
+        c.size_max[j] = t.size_max[i];
+        c.size_min[j] = t.size_min[i];
+        t.key[i] = EMPTY_KEY;
+        t.count[i] = 0ull;
+        t.min_id[i] = ~0ull;
+        t.size_max[i] = 0u;
+        t.size_min[i] = 0xFFFFFFFFu;
+    }
+}
+
+// rank every key among all keys (keys are distinct) and write the sorted histogram
+__global__ void hist_emit_kernel(Compact c, const unsigned *nkeys, jatam_hist_entry *hist, unsigned cap,
+                                 uint32_t *hist_len)
+{
+    constexpr int TILE = 1024;
+    __shared__ unsigned long long tile[TILE];
+    const unsigned nk = *nkeys;
+    if (blockIdx.x == 0 && threadIdx.x == 0 && hist_len) *hist_len = nk;
+    const unsigned per_block = blockDim.x;
+    for (unsigned base = blockIdx.x * per_block; base < nk; base += gridDim.x * per_block) {
+        const unsigned me = base + threadIdx.x;
+        const unsigned long long mk = (me < nk) ? c.key[me] : EMPTY_KEY;
+        unsigned rank = 0;
+        for (unsigned t0 = 0; t0 < nk; t0 += TILE) {
+            __syncthreads();
+            for (unsigned j = threadIdx.x; j < TILE && t0 + j < nk; j += blockDim.x) tile[j] = c.key[t0 + j];
+            __syncthreads();
+            const unsigned lim = min((unsigned)TILE, nk - t0);
+            for (unsigned j = 0; j < lim; ++j) rank += (tile[j] < mk) ? 1u : 0u;
+        }
+        if (me < nk && rank < cap) {
+            jatam_hist_entry e;
+            e.cls = (uint32_t)(mk >> 32);
+            e.shape_hash = (uint32_t)mk;
+            e.size = c.size_max[me];
+            e.flags = (c.size_max[me] != c.size_min[me]) ? 1u : 0u;
+            e.count = c.count[me];
+            e.min_id = c.min_id[me];
+            hist[rank] = e;
+        }
+    }
+}
+
+__global__ void philox_kernel(const uint32_t *in, unsigned long long n, uint32_t *out)
+{
+    for (unsigned long long i = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; i < n;
+         i += (unsigned long long)gridDim.x * blockDim.x) {
+        const uint32_t *r = in + 6 * i;
+        const uint4 w = philox4x32_10(make_uint4(r[0], r[1], r[2], r[3]), r[4], r[5]);
+        out[4 * i + 0] = w.x;
+        out[4 * i + 1] = w.y;
+        out[4 * i + 2] = w.z;
+        out[4 * i + 3] = w.w;
+    }
+}
+
+template <int S>
+int smem_bytes_for(int warps) { return warps * Geo<S>::WORDS * 32 * 4; }
+
+}  // namespace
+
+int classify_smem_bytes(int S, int warps_per_cta)
+{
+    switch (S) {
+    case 8: return smem_bytes_for<8>(warps_per_cta);
+    case 16: return smem_bytes_for<16>(warps_per_cta);
+    default: return smem_bytes_for<32>(warps_per_cta);
+    }
+}
+
+cudaError_t classify_set_attributes(int S, int warps_per_cta)
+{
+    const int bytes = classify_smem_bytes(S, warps_per_cta);
+    switch (S) {
+    case 8: return cudaFuncSetAttribute(classify_kernel<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    case 16: return cudaFuncSetAttribute(classify_kernel<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    default: return cudaFuncSetAttribute(classify_kernel<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    }
+}
+
+cudaError_t classify_occupancy(int S, int warps_per_cta, int *blocks_per_sm)
+{
+    const int bytes = classify_smem_bytes(S, warps_per_cta);
+    const int threads = warps_per_cta * 32;
+    switch (S) {
+    case 8: return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, classify_kernel<8>, threads, bytes);
+    case 16: return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, classify_kernel<16>, threads, bytes);
+    default: return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, classify_kernel<32>, threads, bytes);
+    }
+}
+
+cudaError_t launch_classify(const LaunchArgs &a, int S, int blocks, int warps_per_cta, cudaStream_t st)
+{
+    const int bytes = classify_smem_bytes(S, warps_per_cta);
+    const dim3 grid(blocks), block(warps_per_cta * 32);
+    switch (S) {
+    case 8: classify_kernel<8><<<grid, block, bytes, st>>>(a); break;
+    case 16: classify_kernel<16><<<grid, block, bytes, st>>>(a); break;
+    default: classify_kernel<32><<<grid, block, bytes, st>>>(a); break;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_reset(unsigned long long *work_next, unsigned *nkeys, cudaStream_t st)
+{
+    reset_kernel<<<1, 1, 0, st>>>(work_next, nkeys);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_table_init(Table t, cudaStream_t st)
+{
+    table_init_kernel<<<256, 256, 0, st>>>(t);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_hist_compact(Table t, Compact c, unsigned *nkeys, int blocks, cudaStream_t st)
+{
+    hist_compact_kernel<<<blocks, 256, 0, st>>>(t, c, nkeys);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_hist_emit(Compact c, const unsigned *nkeys, jatam_hist_entry *hist, unsigned cap,
+                             uint32_t *hist_len, int blocks, cudaStream_t st)
+{
+    hist_emit_kernel<<<blocks, 256, 0, st>>>(c, nkeys, hist, cap, hist_len);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_philox(const uint32_t *in, unsigned long long n, uint32_t *out, cudaStream_t st)
+{
+    if (n == 0) return cudaSuccess;
+    const unsigned long long blocks = min((n + 255ull) / 256ull, 4096ull);
+    philox_kernel<<<(unsigned)blocks, 256, 0, st>>>(in, n, out);
+    return cudaGetLastError();
+}
+
+}  // namespace jatam

@@ -1,0 +1,215 @@
+"""Parity of the CUDA path (through the C ABI) with the CPU oracle.
+
+Every comparison is exact: classes, deciding replicates, sizes and shape hashes
+are integers, and the histogram rows (class, hash, size, count, smallest id)
+must match row for row.
+"""
+import hashlib
+import json
+import os
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from oracle import oracle as O  # noqa: E402
+from paper_2205_15311_gb300 import binding as J  # noqa: E402
+from paper_2205_15311_gb300 import workloads as W  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    torch.cuda.init()
+    yield
+
+
+def _dev_enumerate(n, c, L, k, seed, first, count, sampled=False, hist_cap=1 << 16):
+    out = torch.empty(max(count, 1) * 8, dtype=torch.uint8, device="cuda")
+    hist = torch.empty(hist_cap * 32, dtype=torch.uint8, device="cuda")
+    hlen = torch.zeros(1, dtype=torch.int32, device="cuda")
+    J.enumerate_space(n, c, L, k, seed, first, count, sampled=sampled, out=out, hist=hist, hist_len=hlen,
+                      hist_cap=hist_cap, sync=True)
+    m = int(hlen.item())
+    return J.results_view(out)[:count], J.hist_view(hist, min(m, hist_cap)), m
+
+
+def _oracle_hist(res, ids):
+    return O.histogram(res, ids)
+
+
+def _hist_rows(h):
+    return [(int(r["cls"]), int(r["shape_hash"]), int(r["size"]), int(r["count"]), int(r["min_id"])) for r in h]
+
+
+def test_philox_matches_oracle():
+    rng = np.random.default_rng(1)
+    rec = rng.integers(0, 1 << 32, size=(4096, 6), dtype=np.uint64).astype(np.uint32)
+    rec[0] = 0
+    rec[1] = 0xFFFFFFFF
+    out = np.zeros((4096, 4), np.uint32)
+    J.philox(rec, out)
+    for i in range(0, 4096, 37):
+        assert out[i].tolist() == O.philox(rec[i, :4].tolist(), rec[i, 4:].tolist())
+    dev_in = torch.from_numpy(rec.view(np.int32)).cuda()
+    dev_out = torch.zeros((4096, 4), dtype=torch.int32, device="cuda")
+    J.philox(dev_in, dev_out)
+    torch.cuda.synchronize()
+    assert np.array_equal(dev_out.cpu().numpy().view(np.uint32), out)
+
+
+def test_s24_full_space_matches_oracle_and_golden():
+    n, c, L, k, seed, first, count, _ = W.WORKLOADS["s24_full"]
+    res, hist, m = _dev_enumerate(n, c, L, k, seed, first, count)
+    ref, _ = O.enumerate_space(n, c, L, k, seed, first, count)
+    assert np.array_equal(res, ref)
+    gold = json.load(open(os.path.join(GOLDEN, "c1_summary.json")))
+    assert hashlib.sha256(res.tobytes()).hexdigest() == gold["results_sha256"]
+    want = _oracle_hist(ref, np.arange(count, dtype=np.uint64))
+    assert m == len(want)
+    assert _hist_rows(hist) == _hist_rows(want)
+
+
+def _golden_hist(name):
+    rows = []
+    for line in open(os.path.join(GOLDEN, name)):
+        if line.startswith("#"):
+            continue
+        rows.append(tuple(int(v) for v in line.split()))
+    return rows
+
+
+def test_s28_full_space_matches_golden():
+    """All 8^8 genotypes of S_{2,8}: the SHA-256 of the 134 MB result array and
+    the histogram equal what the oracle wrote (tests/golden/make_golden.py)."""
+    n, c, L, k, seed, first, count, _ = W.WORKLOADS["s28_full"]
+    res, hist, m = _dev_enumerate(n, c, L, k, seed, first, count)
+    gold = json.load(open(os.path.join(GOLDEN, "c2_summary.json")))
+    assert np.bincount(res["cls"], minlength=4).tolist() == gold["class_counts"]
+    assert hashlib.sha256(res.tobytes()).hexdigest() == gold["results_sha256"]
+    assert _hist_rows(hist) == _golden_hist("c2_histogram.txt")
+    # spot-check against the oracle run one genotype at a time
+    rng = np.random.default_rng(7)
+    for g in rng.integers(0, count, size=300):
+        r = O.classify(n, c, L, k, seed, O.decode(int(g), n, c), int(g))
+        assert (r["cls"], r["decided_rep"], r["size"], r["shape_hash"]) == tuple(res[int(g)].tolist())
+
+
+def test_s38_sample_slice_matches_oracle():
+    n, c, L, k, seed, _, _, _ = W.WORKLOADS["s38_sample"]
+    first, count = 12345, (1 << 16) + 77
+    res, hist, m = _dev_enumerate(n, c, L, k, seed, first, count, sampled=True)
+    ref, _ = O.enumerate_space(n, c, L, k, seed, first, count, sampled=True)
+    assert np.array_equal(res, ref)
+    ids = np.array([O.sample_genotype(first + i, n, c, seed) for i in range(count)], np.uint64)
+    assert _hist_rows(hist) == _hist_rows(_oracle_hist(ref, ids))
+
+
+@pytest.mark.parametrize("L", [1, 2, 3, 5, 8, 9, 16, 19, 31, 32])
+def test_grid_sizes_including_ragged_ones(L):
+    n, c, k, seed = 2, 8, 7, 11
+    first, count = 3 * (1 << 20) + 5, 3001
+    res, hist, m = _dev_enumerate(n, c, L, k, seed, first, count)
+    ref, _ = O.enumerate_space(n, c, L, k, seed, first, count)
+    assert np.array_equal(res, ref)
+
+
+@pytest.mark.parametrize("count", [0, 1, 31, 32, 33, 1000])
+def test_ragged_counts(count):
+    n, c, L, k, seed = 2, 8, 16, 20, 2
+    first = (1 << 24) - count  # ends exactly at the end of the space
+    res, hist, m = _dev_enumerate(n, c, L, k, seed, first, count)
+    ref, _ = O.enumerate_space(n, c, L, k, seed, first, count)
+    assert np.array_equal(res, ref)
+    assert m == len(_oracle_hist(ref, np.arange(first, first + count, dtype=np.uint64)))
+
+
+def test_mixed_records_match_oracle():
+    colours, shapes = W.mixed_records(20000, seed=4)
+    ids = np.arange(20000, dtype=np.uint64) * np.uint64(7919) + np.uint64(5)
+    dc = torch.from_numpy(colours).cuda()
+    ds = torch.from_numpy(shapes).cuda()
+    di = torch.from_numpy(ids.view(np.int64)).cuda()
+    out = torch.empty(20000 * 8, dtype=torch.uint8, device="cuda")
+    hist = torch.empty((1 << 14) * 32, dtype=torch.uint8, device="cuda")
+    hlen = torch.zeros(1, dtype=torch.int32, device="cuda")
+    J.classify_batch(dc, seed=4, shapes=ds, stream_ids=di, out=out, hist=hist, hist_len=hlen, hist_cap=1 << 14,
+                     sync=True)
+    res = J.results_view(out)
+    ref, _ = O.classify_batch(colours, shapes=shapes, seed=4, ids=ids)
+    assert np.array_equal(res, ref)
+    m = int(hlen.item())
+    assert _hist_rows(J.hist_view(hist, m)) == _hist_rows(_oracle_hist(ref, ids))
+
+
+def test_uniform_records_all_tile_counts():
+    rng = np.random.default_rng(3)
+    for n, c, L in ((1, 8, 16), (4, 8, 16), (3, 6, 12), (4, 2, 32), (2, 1, 5)):
+        N = 4000
+        colours = np.zeros((N, 16), np.uint8)
+        colours[:, : 4 * n] = rng.integers(0, c, size=(N, 4 * n))
+        out = np.zeros(N, J.RESULT_DTYPE)
+        J.classify_batch(colours, n=n, c=c, L=L, k=9, seed=99, out=out)
+        ref, _ = O.classify_batch(colours, n=n, c=c, L=L, k=9, seed=99)
+        assert np.array_equal(out, ref), (n, c, L)
+
+
+def test_host_buffers_equal_device_buffers():
+    n, c, L, k, seed = 3, 8, 32, 20, 3
+    first, count = 1 << 30, 5000
+    out = np.zeros(count, J.RESULT_DTYPE)
+    hist = np.zeros(4096, J.HIST_DTYPE)
+    hlen = np.zeros(1, np.uint32)
+    J.enumerate_space(n, c, L, k, seed, first, count, sampled=True, out=out, hist=hist, hist_len=hlen, hist_cap=4096)
+    res, dh, m = _dev_enumerate(n, c, L, k, seed, first, count, sampled=True)
+    assert np.array_equal(out, res)
+    assert int(hlen[0]) == m and np.array_equal(hist[:m], dh)
+
+
+def test_hist_capacity_too_small_reports_length():
+    n, c, L, k, seed = 2, 8, 16, 20, 2
+    hist = np.zeros(3, J.HIST_DTYPE)
+    hlen = np.zeros(1, np.uint32)
+    with pytest.raises(J.JatamError) as e:
+        J.enumerate_space(n, c, L, k, seed, 0, 1 << 20, hist=hist, hist_len=hlen, hist_cap=3)
+    assert e.value.code == J.JATAM_EINVAL and int(hlen[0]) > 3
+
+
+def test_ga_evaluate_fitness():
+    n, c, L, k, seed = 3, 8, 16, 20, 5
+    g = W.random_genomes(30000, n, c, seed=5)
+    fit = np.zeros(30000, np.int32)
+    out = np.zeros(30000, J.RESULT_DTYPE)
+    J.evaluate_genomes(g, fit, n=n, c=c, L=L, k=k, seed=seed, out=out)
+    for i in range(0, 30000, 97):
+        r = O.classify(n, c, L, k, seed, O.decode(int(g[i]), n, c), int(g[i]))
+        assert tuple(out[i].tolist()) == (r["cls"], r["decided_rep"], r["size"], r["shape_hash"])
+        assert fit[i] == (r["size"] if r["cls"] == O.DET_BOUNDED else 0)
+    # same genotype, same stream id: identical to the enumeration of that index
+    res, _, _ = _dev_enumerate(n, c, L, k, seed, int(g[0]), 1)
+    assert tuple(res[0].tolist()) == tuple(out[0].tolist())
+
+
+def test_argument_errors():
+    with pytest.raises(J.JatamError) as e:
+        J.enumerate_space(5, 8, 16, 20, 2, 0, 10, out=np.zeros(10, J.RESULT_DTYPE))
+    assert e.value.code == J.JATAM_EUNSUPPORTED
+    with pytest.raises(J.JatamError) as e:
+        J.enumerate_space(2, 6, 16, 20, 2, 0, 10, out=np.zeros(10, J.RESULT_DTYPE))
+    assert e.value.code == J.JATAM_EINVAL
+    with pytest.raises(J.JatamError) as e:
+        J.enumerate_space(2, 8, 16, 20, 2, (1 << 24) - 5, 10, out=np.zeros(10, J.RESULT_DTYPE))
+    assert e.value.code == J.JATAM_EINVAL
+    bad = np.zeros((4, 16), np.uint8)
+    bad[2, 3] = 9  # colour >= c
+    out = np.zeros(4, J.RESULT_DTYPE)
+    with pytest.raises(J.JatamError) as e:
+        J.classify_batch(bad, n=2, c=8, L=16, k=4, seed=1, out=out)
+    assert e.value.code == J.JATAM_EINVAL and out["cls"][2] == 255
+    # the error was consumed: the next call is clean
+    J.classify_batch(bad[:2], n=2, c=8, L=16, k=4, seed=1, out=out[:2])
