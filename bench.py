@@ -181,6 +181,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end leg")
+    ap.add_argument("--count", type=int, default=0,
+                    help="classify only the first COUNT genotypes (small profiling cases; not a bench line)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     if args.impl == "reference":
@@ -202,6 +205,8 @@ def main():
     from paper_2205_15311_gb300 import binding as J
 
     n, c, L, k, seed0, first, count, sampled = WORKLOAD_SPEC()
+    if args.count:
+        count = min(count, args.count)
     seed = seed0 + rank  # every rank: its own independent classification of the space
     hist_cap = 1 << 16
     stream = torch.cuda.Stream(device=dev)
@@ -249,22 +254,23 @@ def main():
     out_h = torch.empty(count * 8, dtype=torch.uint8, pin_memory=True)
     hist_h = np.zeros(hist_cap, J.HIST_DTYPE)
     hlen_h = np.zeros(1, np.uint32)
-    J.enumerate_space(n, c, L, k, seed, first, count, sampled=sampled, out=out_h, hist=hist_h, hist_len=hlen_h,
-                      hist_cap=hist_cap, stream=stream)
+    if not args.no_e2e:
+        J.enumerate_space(n, c, L, k, seed, first, count, sampled=sampled, out=out_h, hist=hist_h,
+                          hist_len=hlen_h, hist_cap=hist_cap, stream=stream)
     e2e_times = []
-    for i in range(max(3, min(args.steps, 5))):
+    for i in range(0 if args.no_e2e else max(3, min(args.steps, 5))):
         flush.fill_(i & 255)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         J.enumerate_space(n, c, L, k, seed, first, count, sampled=sampled, out=out_h, hist=hist_h,
                           hist_len=hlen_h, hist_cap=hist_cap, stream=stream)
         e2e_times.append(time.perf_counter() - t0)
-    e2e_s = float(np.mean(e2e_times))
+    e2e_s = float(np.mean(e2e_times)) if e2e_times else float("nan")
     if world > 1:
         t = torch.tensor([e2e_s], device=dev)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         e2e_s = float(t.item())
-    nk = int(hlen_h[0])
+    nk = int(hlen_h[0]) if e2e_times else int(hlen.item())
 
     line = None
     if rank == 0:
@@ -276,7 +282,7 @@ def main():
         alu_peak = n_sms * 128 * sm_max * 1e6 / 1e12  # int32 lane-ops per second, T
         placements = None
         golden = os.path.join(ROOT, "tests", "golden", "c2_summary.json")
-        if os.path.exists(golden) and seed == 2:
+        if os.path.exists(golden) and seed == 2 and not args.count:
             placements = json.load(open(golden))["placements"]
         roofline = None
         kms = float(np.mean(kernel_ms))
@@ -305,8 +311,9 @@ def main():
                        "global_batch": world * count, "parallelism": f"replicas x{world}",
                        "l2": "256 MB buffer written between timed steps; outputs 134 MB > L2",
                        "distinct_phenotypes": nk},
-            "e2e": {"value": world * count / e2e_s, "unit": UNIT, "h2d_bytes_per_step": 0,
-                    "d2h_bytes_per_step": count * 8 + nk * 32 + 8},
+            "e2e": None if not e2e_times else {"value": world * count / e2e_s, "unit": UNIT,
+                                               "h2d_bytes_per_step": 0,
+                                               "d2h_bytes_per_step": count * 8 + nk * 32 + 8},
             "gpu_launches": 4 * args.steps,
             "roofline": roofline,
             "cpu_baseline": cpu,
