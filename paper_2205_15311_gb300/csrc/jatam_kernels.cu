@@ -47,7 +47,8 @@ struct Geo {
     static constexpr int FRONT = 2 * NW;
     static constexpr int NIB = 3 * NW;
     static constexpr int NBM = 3 * NW + (S * S) / 8;
-    static constexpr int WORDS = NBM + 32;  // 32-bit words per lane
+    static constexpr int CACHE = NBM + 32;  // per-warp shape cache: entry j in "lane" j's bank
+    static constexpr int WORDS = CACHE + 3;  // 32-bit words per lane
 };
 
 // ---------------------------------------------------------------------------
@@ -131,6 +132,7 @@ struct Lane {
     int dlo, dhi;                // rows that may be dirty in any bitmap
     int blo, bhi;                // rows of OCCB written by the current replicate
     int diverged;                // replicate j > 0 can no longer end in replicate 0's configuration
+    int forced;                  // replicate 0 so far never had more than one frontier site to choose from
     int cls, decided;
     uint32_t hash;
     uint32_t pblk;               // Philox block held in pbuf
@@ -261,6 +263,50 @@ __device__ __forceinline__ uint32_t coop_shape_hash(int o, const uint32_t *warp_
     return oaat_finish(hsh);
 }
 
+// The seed step of replicate 0, evaluated straight from the colours: for each
+// side d of the seed (tile 0, orientation 0) the candidates are the rotated
+// tuples whose side facing the seed has the partner colour of the seed's side
+// d.  Returns 1 (local ambiguity), 3 (unbounded), 0 (terminated: nothing can
+// attach, every replicate ends as the lone seed) or -1 (the assembly grows).
+__device__ __forceinline__ int seed_outcome(unsigned long long cols, int n, int c, int L)
+{
+    const unsigned long long ones = 0x1111111111111111ull;
+    const unsigned long long valid = (n >= 4) ? ~0ull : ((1ull << (16 * n)) - 1ull);
+    const int cx = L >> 1;
+    bool nd = false, unb = false, grows = false;
+#pragma unroll
+    for (int d = 0; d < 4; ++d) {
+        const int a = (int)((cols >> (4 * d)) & 15u);
+        const int pa = (a == 0) ? -1 : (a & 1) ? ((a + 1 < c) ? a + 1 : -1) : a - 1;
+        if (pa < 0) continue;
+        const unsigned long long x = cols ^ ((unsigned long long)pa * ones);
+        const unsigned long long nz = (x | (x >> 1) | (x >> 2) | (x >> 3)) & ones;
+        unsigned long long eq = ~nz & ones & valid;  // bit 4 m set: edge m carries colour pa
+        if (!eq) continue;
+        const int e = (d + 2) & 3;  // the candidate's side that faces the seed
+        uint32_t first = 0xFFFFFFFFu;
+        bool multi = false;
+        while (eq) {
+            const int m = (__ffsll((long long)eq) - 1) >> 2;
+            eq &= eq - 1;
+            const int t = m >> 2, i = m & 3;
+            const uint32_t tile = (uint32_t)(cols >> (16 * t)) & 0xFFFFu;
+            const int r = (e - i) & 3;  // turn that brings edge i to side e
+            const uint32_t tup = ((tile << (4 * r)) | (tile >> (16 - 4 * r))) & 0xFFFFu;
+            if (first == 0xFFFFFFFFu) first = tup;
+            else if (tup != first) multi = true;
+        }
+        const int qx = cx + (d == 1) - (d == 3), qy = cx + (d == 2) - (d == 0);
+        const bool inside = qx >= 0 && qy >= 0 && qx < L && qy < L;
+        if (multi) nd = true;
+        else if (!inside) unb = true;
+        grows = true;
+    }
+    if (nd) return JATAM_ND_LOCAL;
+    if (unb) return JATAM_UNBOUNDED;
+    return grows ? -1 : 0;
+}
+
 // ---------------------------------------------------------------------------
 // one growth step of one lane: seed placement or one drawn placement, then the
 // evaluation of the new tile's empty neighbours and the replicate rule
@@ -295,6 +341,7 @@ __device__ __forceinline__ void lane_step(Lane &Ls, uint32_t *my, uint32_t k0, u
         Ls.step = 0;
         Ls.nF = 0;
         Ls.diverged = 0;
+        Ls.forced = 1;
         Ls.ymin = Ls.ymax = py;
         Ls.xmin = Ls.xmax = px;
         Ls.pblk = 0xFFFFFFFFu;
@@ -306,6 +353,7 @@ __device__ __forceinline__ void lane_step(Lane &Ls, uint32_t *my, uint32_t k0, u
                                     k0, k1);
             Ls.pblk = blk;
         }
+        if (Ls.nF > 1) Ls.forced = 0;
         const int sel = Ls.step & 3;
         const uint32_t u = sel == 0 ? Ls.pbuf.x : sel == 1 ? Ls.pbuf.y : sel == 2 ? Ls.pbuf.z : Ls.pbuf.w;
         uint32_t i = __umulhi(u, (uint32_t)Ls.nF);
@@ -406,6 +454,15 @@ __device__ __forceinline__ void lane_step(Lane &Ls, uint32_t *my, uint32_t k0, u
         Ls.x1 = Ls.xmax;
         Ls.y0 = Ls.ymin;
         Ls.y1 = Ls.ymax;
+        if (Ls.forced) {
+            // every draw of replicate 0 had a single frontier site: every other
+            // replicate starts from the same seed and is forced along the same
+            // path, so all k replicates end in this configuration
+            Ls.cls = JATAM_DET_BOUNDED;
+            Ls.decided = Ls.k;
+            Ls.phase = PH_SHAPE;
+            return;
+        }
     } else if (Ls.diverged || Ls.size != Ls.size0) {
         Ls.cls = JATAM_ND_STERIC;
         Ls.decided = Ls.rep;
@@ -507,6 +564,8 @@ __global__ void __launch_bounds__(256) classify_kernel(const LaunchArgs a)
         H.smin[i] = 0xFFFFFFFFu;
     }
     for (int w = 0; w < 3 * G::NW; ++w) my[w * 32] = 0u;
+    my[G::CACHE * 32] = 0u;  // key with h = 0: never matches a crop
+    my[(G::CACHE + 1) * 32] = 0u;
     __syncthreads();
 
     Lane Ls;
@@ -522,9 +581,12 @@ __global__ void __launch_bounds__(256) classify_kernel(const LaunchArgs a)
     Ls.x0 = Ls.x1 = Ls.y0 = Ls.y1 = 0;
     Ls.ymin = Ls.ymax = Ls.xmin = Ls.xmax = 0;
     Ls.diverged = 0;
+    Ls.forced = 0;
     Ls.pblk = 0xFFFFFFFFu;
     Ls.pbuf = make_uint4(0, 0, 0, 0);
     unsigned long long q_next = 0, q_end = 0;  // this warp's slice of the work counter
+    // the lone seed: a 1 x 1 crop with its cell at (0, 0)
+    const uint32_t monomer_hash = oaat_finish(oaat_add(oaat_add(oaat_add(oaat_add(0u, 1u), 1u), 0u), 0u));
     const int b_uniform = log2_colours(a.c);
 
     for (;;) {
@@ -603,6 +665,16 @@ __global__ void __launch_bounds__(256) classify_kernel(const LaunchArgs a)
                     }
                 }
             }
+            if (Ls.phase == PH_INIT) {
+                const int so = seed_outcome(Ls.cols, Ls.n, Ls.c, Ls.L);
+                if (so >= 0) {
+                    Ls.cls = (so == 0) ? JATAM_DET_BOUNDED : so;
+                    Ls.decided = (so == 0) ? Ls.k : 0;
+                    Ls.size0 = 1;
+                    Ls.hash = monomer_hash;
+                    Ls.phase = PH_WRITE;
+                }
+            }
             unsigned init = __ballot_sync(FULL, Ls.phase == PH_INIT);
             while (init) {
                 const int o = __ffs(init) - 1;
@@ -620,7 +692,30 @@ __global__ void __launch_bounds__(256) classify_kernel(const LaunchArgs a)
         // ---- one assembly step per busy lane
         if (Ls.phase == PH_START || Ls.phase == PH_GROW) lane_step<S>(Ls, my, a.key0, a.key1, a.err);
 
-        // ---- canonical shapes of finished genotypes, one warp-wide job each
+        // ---- canonical shapes of finished genotypes: a per-warp cache keyed by
+        // the exact crop (when it has at most 32 cells), else one warp-wide job each
+        unsigned long long ckey = 0ull;
+        int cslot = -1;
+        if (Ls.phase == PH_SHAPE) {
+            const int h = Ls.y1 - Ls.y0 + 1, w = Ls.x1 - Ls.x0 + 1;
+            if (h * w <= 32) {
+                const uint32_t wmask = (w >= 32) ? FULL : ((1u << w) - 1u);
+                uint32_t bits = 0;
+                for (int i = 0; i < h; ++i) {
+                    const int b = (Ls.y0 + i) * S + Ls.x0;
+                    bits |= ((my[(G::OCCA + (b >> 5)) * 32] >> (b & 31)) & wmask) << (i * w);
+                }
+                ckey = ((unsigned long long)h << 40) | ((unsigned long long)w << 32) | bits;
+                cslot = (int)((uint32_t)((ckey * 0x9E3779B97F4A7C15ull) >> 32) >> 27);
+                const uint32_t *ce = warp_lanes + cslot;
+                const unsigned long long have =
+                    ((unsigned long long)ce[(G::CACHE + 1) * 32] << 32) | ce[G::CACHE * 32];
+                if (have == ckey) {
+                    Ls.hash = ce[(G::CACHE + 2) * 32];
+                    Ls.phase = PH_WRITE;
+                }
+            }
+        }
         unsigned shp = __ballot_sync(FULL, Ls.phase == PH_SHAPE);
         while (shp) {
             const int o = __ffs(shp) - 1;
@@ -629,7 +724,14 @@ __global__ void __launch_bounds__(256) classify_kernel(const LaunchArgs a)
             if (lane == o) {
                 Ls.hash = hv;
                 Ls.phase = PH_WRITE;
+                if (cslot >= 0) {
+                    uint32_t *ce = warp_lanes + cslot;
+                    ce[G::CACHE * 32] = (uint32_t)ckey;
+                    ce[(G::CACHE + 1) * 32] = (uint32_t)(ckey >> 32);
+                    ce[(G::CACHE + 2) * 32] = hv;
+                }
             }
+            __syncwarp();
         }
         if (Ls.phase == PH_WRITE) {
             const bool shaped = Ls.cls == JATAM_DET_BOUNDED || Ls.cls == JATAM_ND_STERIC;
