@@ -182,6 +182,9 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end leg")
+    ap.add_argument("--profile-genomes", type=int, default=0,
+                    help="instead of the bench: ga_evaluate on this many uniform random genomes of the "
+                         "workload's space (a representative small case for ncu); prints timings only")
     ap.add_argument("--count", type=int, default=0,
                     help="classify only the first COUNT genotypes (small profiling cases; not a bench line)")
     args = ap.parse_args()
@@ -205,6 +208,16 @@ def main():
     from paper_2205_15311_gb300 import binding as J
 
     n, c, L, k, seed0, first, count, sampled = WORKLOAD_SPEC()
+    if args.profile_genomes:
+        from paper_2205_15311_gb300 import workloads as W
+        g = torch.from_numpy(W.random_genomes(args.profile_genomes, n, c, seed=7).view(np.int64)).to(dev)
+        fit = torch.empty(args.profile_genomes, dtype=torch.int32, device=dev)
+        J.jatam_profile(1)
+        for i in range(args.warmup + args.steps):
+            J.evaluate_genomes(g, fit, n=n, c=c, L=L, k=k, seed=seed0, sync=True)
+            if i >= args.warmup:
+                print(json.dumps({"profile_genomes": args.profile_genomes, "kernel_ms": J.last_kernel_ms()}))
+        return 0
     if args.count:
         count = min(count, args.count)
     seed = seed0 + rank  # every rank: its own independent classification of the space

@@ -2,6 +2,7 @@
 // workspace, staging of host buffers, launches, and the error state.
 #include <cstdarg>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <map>
 #include <mutex>
@@ -18,6 +19,24 @@ namespace {
 thread_local std::string g_last_error;
 std::mutex g_mutex;
 bool g_profile = false;
+int g_stop_at = 16;  // lanes that must finish before a warp leaves its growth rounds
+int g_warps_override = 0;
+
+// optional overrides of the launch shape (for tuning sweeps)
+void read_env_overrides()
+{
+    static bool done = false;
+    if (done) return;
+    done = true;
+    if (const char *v = getenv("JATAM_STOP_AT")) {
+        int x = atoi(v);
+        if (x >= 1 && x <= 32) g_stop_at = x;
+    }
+    if (const char *v = getenv("JATAM_WARPS_PER_CTA")) {
+        int x = atoi(v);
+        if (x >= 1 && x <= 8) g_warps_override = x;
+    }
+}
 
 int fail(int code, const char *fmt, ...)
 {
@@ -83,6 +102,7 @@ int grow(void **p, size_t *have, size_t want)
 
 int workspace(Workspace **out)
 {
+    read_env_overrides();
     int dev = 0;
     CUDA_TRY(cudaGetDevice(&dev));
     auto it = g_ws.find(dev);
@@ -153,7 +173,7 @@ int check_params(int n, int c, int L, int k, bool packed)
 }
 
 // launch shape: warps per CTA by lattice template; CTAs = resident CTAs on every SM
-int warps_for(int S) { return S == 32 ? 2 : 4; }
+int warps_for(int S) { return g_warps_override ? g_warps_override : (S == 32 ? 2 : S == 16 ? 8 : 8); }
 
 struct Outputs {
     jatam_result *out_dev = nullptr;
@@ -215,6 +235,7 @@ int run(Workspace *w, LaunchArgs a, int S, jatam_result *out, int32_t *fitness, 
     a.use_hist = hist ? 1 : 0;
     a.work_next = w->work_next;
     a.err = w->err;
+    a.stop_at = g_stop_at;
 
     const int warps = warps_for(S);
     const int si = S == 8 ? 0 : S == 16 ? 1 : 2;

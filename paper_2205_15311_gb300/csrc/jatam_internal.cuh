@@ -59,6 +59,7 @@ struct LaunchArgs {
     int32_t *fitness;             // [count] or null
     Table table;
     int use_hist;
+    int stop_at;                    // finished lanes that end a growth round (1..32)
     unsigned long long *work_next;  // work counter, zeroed before the launch
     unsigned *err;                  // sticky error bits
 };

@@ -590,9 +590,24 @@ __global__ void __launch_bounds__(256) classify_kernel(const LaunchArgs a)
     const int b_uniform = log2_colours(a.c);
 
     for (;;) {
-        // ---- hand out new items to idle lanes, then build their tables together
-        const unsigned need = __ballot_sync(FULL, Ls.phase == PH_NEED);
-        if (need) {
+        // ---- service: write finished genotypes, hand out new ones and pre-check
+        // them, until every lane is growing or out of work (all lanes together)
+        for (;;) {
+            if (Ls.phase == PH_WRITE) {
+                const bool shaped = Ls.cls == JATAM_DET_BOUNDED || Ls.cls == JATAM_ND_STERIC;
+                const unsigned size = shaped ? (unsigned)Ls.size0 : 0u;
+                const uint32_t hash = shaped ? Ls.hash : 0u;
+                if (a.out) {
+                    const uint32_t w0 = (uint32_t)(Ls.cls & 255) | ((uint32_t)(Ls.decided & 255) << 8) | (size << 16);
+                    reinterpret_cast<uint2 *>(a.out)[Ls.item] = make_uint2(w0, hash);
+                }
+                if (a.fitness) a.fitness[Ls.item] = (Ls.cls == JATAM_DET_BOUNDED) ? (int32_t)size : 0;
+                if (a.use_hist && Ls.cls != 255)
+                    hist_insert(H, a.table, ((unsigned long long)Ls.cls << 32) | hash, Ls.sid, size, a.err);
+                Ls.phase = PH_NEED;
+            }
+            const unsigned need = __ballot_sync(FULL, Ls.phase == PH_NEED);
+            if (!need) break;
             const int cnt = __popc(need);
             const int rank = __popc(need & lanemask_lt());
             unsigned long long my_idx = ~0ull;
@@ -675,22 +690,31 @@ __global__ void __launch_bounds__(256) classify_kernel(const LaunchArgs a)
                     Ls.phase = PH_WRITE;
                 }
             }
-            unsigned init = __ballot_sync(FULL, Ls.phase == PH_INIT);
-            while (init) {
-                const int o = __ffs(init) - 1;
-                init &= init - 1;
-                coop_tables<S>(o, warp_lanes, Ls, lane);
-            }
-            __syncwarp();
-            if (Ls.phase == PH_INIT) {
-                Ls.rep = 0;
-                Ls.phase = PH_START;
-            }
+            if (!__any_sync(FULL, Ls.phase == PH_WRITE)) break;
+        }
+        // ---- binding tables of the genotypes that grow, one warp-wide job each
+        unsigned init = __ballot_sync(FULL, Ls.phase == PH_INIT);
+        while (init) {
+            const int o = __ffs(init) - 1;
+            init &= init - 1;
+            coop_tables<S>(o, warp_lanes, Ls, lane);
+        }
+        __syncwarp();
+        if (Ls.phase == PH_INIT) {
+            Ls.rep = 0;
+            Ls.phase = PH_START;
         }
         if (__all_sync(FULL, Ls.phase == PH_DONE)) break;
 
-        // ---- one assembly step per busy lane
-        if (Ls.phase == PH_START || Ls.phase == PH_GROW) lane_step<S>(Ls, my, a.key0, a.key1, a.err);
+        // ---- growth: one step per busy lane per round, until a.stop_at lanes
+        // have finished their genotype or no lane is left growing
+        for (;;) {
+            if (Ls.phase == PH_START || Ls.phase == PH_GROW) lane_step<S>(Ls, my, a.key0, a.key1, a.err);
+            const unsigned busy = __ballot_sync(FULL, Ls.phase == PH_START || Ls.phase == PH_GROW);
+            if (!busy) break;
+            const unsigned fin = __ballot_sync(FULL, Ls.phase == PH_SHAPE || Ls.phase == PH_WRITE);
+            if (__popc(fin) >= a.stop_at) break;
+        }
 
         // ---- canonical shapes of finished genotypes: a per-warp cache keyed by
         // the exact crop (when it has at most 32 cells), else one warp-wide job each
@@ -732,19 +756,6 @@ __global__ void __launch_bounds__(256) classify_kernel(const LaunchArgs a)
                 }
             }
             __syncwarp();
-        }
-        if (Ls.phase == PH_WRITE) {
-            const bool shaped = Ls.cls == JATAM_DET_BOUNDED || Ls.cls == JATAM_ND_STERIC;
-            const unsigned size = shaped ? (unsigned)Ls.size0 : 0u;
-            const uint32_t hash = shaped ? Ls.hash : 0u;
-            if (a.out) {
-                const uint32_t w0 = (uint32_t)(Ls.cls & 255) | ((uint32_t)(Ls.decided & 255) << 8) | (size << 16);
-                reinterpret_cast<uint2 *>(a.out)[Ls.item] = make_uint2(w0, hash);
-            }
-            if (a.fitness) a.fitness[Ls.item] = (Ls.cls == JATAM_DET_BOUNDED) ? (int32_t)size : 0;
-            if (a.use_hist && Ls.cls != 255)
-                hist_insert(H, a.table, ((unsigned long long)Ls.cls << 32) | hash, Ls.sid, size, a.err);
-            Ls.phase = PH_NEED;
         }
     }
 
