@@ -327,7 +327,7 @@ def main():
             "e2e": None if not e2e_times else {"value": world * count / e2e_s, "unit": UNIT,
                                                "h2d_bytes_per_step": 0,
                                                "d2h_bytes_per_step": count * 8 + nk * 32 + 8},
-            "gpu_launches": 4 * args.steps,
+            "gpu_launches": 5 * args.steps,
             "roofline": roofline,
             "cpu_baseline": cpu,
             "clocks": clocks.summary(),

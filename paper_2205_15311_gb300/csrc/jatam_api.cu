@@ -66,6 +66,9 @@ struct Workspace {
     unsigned long long *work_next = nullptr;
     unsigned *err = nullptr;
     unsigned *nkeys = nullptr;
+    unsigned long long *list_count = nullptr;
+    void *list = nullptr;  // items left to grow after the pre-filter (8 B each)
+    size_t list_bytes = 0;
     unsigned *host_words = nullptr;  // pinned: [0] err, [1] nkeys
     void *stage_in = nullptr;
     size_t stage_in_bytes = 0;
@@ -128,12 +131,13 @@ int workspace(Workspace **out)
     CUDA_TRY(cudaMalloc(&w->work_next, 8));
     CUDA_TRY(cudaMalloc(&w->err, 4));
     CUDA_TRY(cudaMalloc(&w->nkeys, 4));
+    CUDA_TRY(cudaMalloc(&w->list_count, 8));
     CUDA_TRY(cudaMallocHost(&w->host_words, 16));
     CUDA_TRY(cudaEventCreateWithFlags(&w->last, cudaEventDisableTiming));
     CUDA_TRY(cudaEventCreate(&w->k_start));
     CUDA_TRY(cudaEventCreate(&w->k_stop));
     CUDA_TRY(launch_table_init(w->table, nullptr));
-    CUDA_TRY(launch_reset(w->work_next, w->nkeys, nullptr));
+    CUDA_TRY(launch_reset(w->work_next, w->nkeys, w->list_count, nullptr));
     CUDA_TRY(cudaMemsetAsync(w->err, 0, 4, nullptr));
     CUDA_TRY(cudaDeviceSynchronize());
     g_ws[dev] = w;
@@ -236,6 +240,12 @@ int run(Workspace *w, LaunchArgs a, int S, jatam_result *out, int32_t *fitness, 
     a.work_next = w->work_next;
     a.err = w->err;
     a.stop_at = g_stop_at;
+    if (n_items) {
+        int rc = grow(&w->list, &w->list_bytes, n_items * 8);
+        if (rc) return rc;
+    }
+    a.list = static_cast<unsigned long long *>(w->list);
+    a.list_count = w->list_count;
 
     const int warps = warps_for(S);
     const int si = S == 8 ? 0 : S == 16 ? 1 : 2;
@@ -252,7 +262,12 @@ int run(Workspace *w, LaunchArgs a, int S, jatam_result *out, int32_t *fitness, 
     if (needed < blocks) blocks = needed < 1 ? 1 : needed;
 
     CUDA_TRY(cudaStreamWaitEvent(st, w->last, 0));
-    CUDA_TRY(launch_reset(w->work_next, w->nkeys, st));
+    CUDA_TRY(launch_reset(w->work_next, w->nkeys, w->list_count, st));
+    if (n_items) {
+        long long pblocks = (long long)(n_items + 255) / 256;
+        if (pblocks > 8LL * w->num_sms) pblocks = 8LL * w->num_sms;
+        CUDA_TRY(launch_prefilter(a, S, (int)pblocks, st));
+    }
     if (g_profile) CUDA_TRY(cudaEventRecord(w->k_start, st));
     if (n_items) CUDA_TRY(launch_classify(a, S, (int)blocks, warps, st));
     if (g_profile) {
@@ -530,7 +545,8 @@ void jatam_shutdown(void)
         cudaFree(w->table.size_max); cudaFree(w->table.size_min);
         cudaFree(w->compact.key); cudaFree(w->compact.count); cudaFree(w->compact.min_id);
         cudaFree(w->compact.size_max); cudaFree(w->compact.size_min);
-        cudaFree(w->work_next); cudaFree(w->err); cudaFree(w->nkeys);
+        cudaFree(w->work_next); cudaFree(w->err); cudaFree(w->nkeys); cudaFree(w->list_count);
+        if (w->list) cudaFree(w->list);
         cudaFreeHost(w->host_words);
         if (w->stage_in) cudaFree(w->stage_in);
         if (w->stage_out) cudaFree(w->stage_out);

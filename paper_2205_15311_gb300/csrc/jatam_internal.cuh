@@ -60,6 +60,8 @@ struct LaunchArgs {
     Table table;
     int use_hist;
     int stop_at;                    // finished lanes that end a growth round (1..32)
+    unsigned long long *list;        // items left to grow, written by the pre-filter
+    unsigned long long *list_count;  // their number
     unsigned long long *work_next;  // work counter, zeroed before the launch
     unsigned *err;                  // sticky error bits
 };
@@ -70,7 +72,9 @@ cudaError_t classify_set_attributes(int S, int warps_per_cta);
 cudaError_t classify_occupancy(int S, int warps_per_cta, int *blocks_per_sm);
 cudaError_t launch_classify(const LaunchArgs &a, int S, int blocks, int warps_per_cta, cudaStream_t st);
 
-cudaError_t launch_reset(unsigned long long *work_next, unsigned *nkeys, cudaStream_t st);
+cudaError_t launch_reset(unsigned long long *work_next, unsigned *nkeys, unsigned long long *list_count,
+                         cudaStream_t st);
+cudaError_t launch_prefilter(const LaunchArgs &a, int smax, int blocks, cudaStream_t st);
 cudaError_t launch_table_init(Table t, cudaStream_t st);
 cudaError_t launch_hist_compact(Table t, Compact c, unsigned *nkeys, int blocks, cudaStream_t st);
 cudaError_t launch_hist_emit(Compact c, const unsigned *nkeys, jatam_hist_entry *hist, unsigned cap,

@@ -135,9 +135,17 @@ struct Lane {
     int forced;                  // replicate 0 so far never had more than one frontier site to choose from
     int cls, decided;
     uint32_t hash;
-    uint32_t pblk;               // Philox block held in pbuf
-    uint4 pbuf;
+    uint32_t ka, kb;             // Philox blocks held: key = replicate * 512 + block (NO_BLOCK if none)
+    uint4 pa, pb;                // pa: the block in use; pb: a block fetched ahead
 };
+
+constexpr uint32_t NO_BLOCK = 0xFFFFFFFFu;
+
+// Philox block `key` (replicate key >> 9, block key & 511) of stream id sid
+__device__ __forceinline__ uint4 philox_block(uint32_t key, unsigned long long sid, uint32_t k0, uint32_t k1)
+{
+    return philox4x32_10(make_uint4(key & 511u, key >> 9, (uint32_t)sid, (uint32_t)(sid >> 32)), k0, k1);
+}
 
 template <int S>
 __device__ __forceinline__ void clear_rows(uint32_t *my, int base, int lo, int hi)
@@ -344,18 +352,21 @@ __device__ __forceinline__ void lane_step(Lane &Ls, uint32_t *my, uint32_t k0, u
         Ls.forced = 1;
         Ls.ymin = Ls.ymax = py;
         Ls.xmin = Ls.xmax = px;
-        Ls.pblk = 0xFFFFFFFFu;
         Ls.phase = PH_GROW;
     } else {
-        const uint32_t blk = (uint32_t)Ls.step >> 2;
-        if (blk != Ls.pblk) {
-            Ls.pbuf = philox4x32_10(make_uint4(blk, (uint32_t)Ls.rep, (uint32_t)Ls.sid, (uint32_t)(Ls.sid >> 32)),
-                                    k0, k1);
-            Ls.pblk = blk;
+        const uint32_t key = (uint32_t)Ls.rep * 512u + ((uint32_t)Ls.step >> 2);
+        if (Ls.ka != key) {
+            if (Ls.kb == key) {
+                Ls.pa = Ls.pb;
+                Ls.kb = NO_BLOCK;
+            } else {
+                Ls.pa = philox_block(key, Ls.sid, k0, k1);
+            }
+            Ls.ka = key;
         }
         if (Ls.nF > 1) Ls.forced = 0;
         const int sel = Ls.step & 3;
-        const uint32_t u = sel == 0 ? Ls.pbuf.x : sel == 1 ? Ls.pbuf.y : sel == 2 ? Ls.pbuf.z : Ls.pbuf.w;
+        const uint32_t u = sel == 0 ? Ls.pa.x : sel == 1 ? Ls.pa.y : sel == 2 ? Ls.pa.z : Ls.pa.w;
         uint32_t i = __umulhi(u, (uint32_t)Ls.nF);
         int w = (max(Ls.ymin - 1, 0) * S) >> 5;
         uint32_t f = 0;
@@ -545,6 +556,156 @@ __device__ __forceinline__ unsigned long long unpack_genotype(unsigned long long
 
 __device__ __forceinline__ int log2_colours(int c) { return c >= 8 ? 3 : c >= 4 ? 2 : c >= 2 ? 1 : 0; }
 
+// One item of a launch: its colours (nibble-packed), size parameters and
+// stream id.  ok is false for a record with a colour >= c or a parameter out
+// of range (L must also fit the lattice template smax).
+struct Item {
+    unsigned long long sid, cols;
+    int n, c, L, k;
+    bool ok;
+};
+
+__device__ __forceinline__ Item load_item(const LaunchArgs &a, unsigned long long idx, int b_uniform, int smax)
+{
+    Item it;
+    it.n = a.n; it.c = a.c; it.L = a.L; it.k = a.k;
+    it.ok = true;
+    if (a.mode == MODE_RECORDS) {
+        const uint4 raw = *reinterpret_cast<const uint4 *>(a.colours + 16ull * idx);
+        if (a.shapes) {
+            const uint32_t sh = *reinterpret_cast<const uint32_t *>(a.shapes + 4ull * idx);
+            it.n = sh & 255; it.c = (sh >> 8) & 255; it.L = (sh >> 16) & 255; it.k = sh >> 24;
+        }
+        it.sid = a.ids ? a.ids[idx] : idx;
+        unsigned long long cols = 0;
+        bool ok = it.n >= 1 && it.n <= 4 && it.c >= 1 && it.c <= 8 && it.L >= 1 && it.L <= smax && it.k >= 1;
+        const uint32_t wv[4] = {raw.x, raw.y, raw.z, raw.w};
+#pragma unroll
+        for (int e = 0; e < 16; ++e) {
+            const int v = (wv[e >> 2] >> (8 * (e & 3))) & 255;
+            if (e < 4 * it.n) {
+                if (v >= it.c) ok = false;
+                cols |= (unsigned long long)(v & 15) << (4 * e);
+            }
+        }
+        it.cols = cols;
+        it.ok = ok;
+    } else {
+        unsigned long long g;
+        if (a.mode == MODE_RANGE) {
+            g = a.first + idx;
+        } else if (a.mode == MODE_GENOMES) {
+            g = a.genomes[idx];
+        } else {
+            const unsigned long long i = a.first + idx;
+            const uint4 w = philox4x32_10(make_uint4(0u, 1u << 24, (uint32_t)i, (uint32_t)(i >> 32)), a.key0, a.key1);
+            g = ((unsigned long long)w.y << 32) | w.x;
+        }
+        const int bits = 4 * a.n * b_uniform;
+        if (bits < 64) g &= (1ull << bits) - 1ull;
+        it.sid = g;
+        it.cols = unpack_genotype(g, a.n, b_uniform);
+    }
+    return it;
+}
+
+__device__ __forceinline__ uint32_t monomer_shape_hash()
+{
+    // the lone seed: a 1 x 1 crop with its cell at (0, 0)
+    return oaat_finish(oaat_add(oaat_add(oaat_add(oaat_add(0u, 1u), 1u), 0u), 0u));
+}
+
+__device__ __forceinline__ void write_result(const LaunchArgs &a, unsigned long long item, int cls, int decided,
+                                             unsigned size, uint32_t hash)
+{
+    if (a.out) {
+        const uint32_t w0 = (uint32_t)(cls & 255) | ((uint32_t)(decided & 255) << 8) | (size << 16);
+        reinterpret_cast<uint2 *>(a.out)[item] = make_uint2(w0, hash);
+    }
+    if (a.fitness) a.fitness[item] = (cls == JATAM_DET_BOUNDED) ? (int32_t)size : 0;
+}
+
+// ---------------------------------------------------------------------------
+// Pre-filter: one thread per item evaluates the seed step of replicate 0 (a
+// lone seed, or local ambiguity / unboundedness right at the seed), writes the
+// result of every item it decides, counts them into the histogram, and appends
+// every other item to the list that the growth kernel consumes.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) prefilter_kernel(const LaunchArgs a, int smax)
+{
+    // keys decided here: 0 = (ND_LOCAL, 0), 1 = (UNBOUNDED, 0), 2 = (DET_BOUNDED, monomer)
+    __shared__ unsigned s_cnt[3];
+    __shared__ unsigned long long s_min[3];
+    if (threadIdx.x < 3) {
+        s_cnt[threadIdx.x] = 0u;
+        s_min[threadIdx.x] = ~0ull;
+    }
+    __syncthreads();
+    const int lane = threadIdx.x & 31;
+    const int b_uniform = log2_colours(a.c);
+    const uint32_t mono = monomer_shape_hash();
+    const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
+    for (unsigned long long base = (unsigned long long)blockIdx.x * blockDim.x; base < a.count; base += stride) {
+        const unsigned long long idx = base + threadIdx.x;
+        int key = -1;
+        bool grow = false;
+        unsigned long long sid = 0;
+        if (idx < a.count) {
+            const Item it = load_item(a, idx, b_uniform, smax);
+            sid = it.sid;
+            if (!it.ok) {
+                atomicOr(a.err, ERR_INVALID_ITEM);
+                write_result(a, idx, 255, 0, 0u, 0u);
+            } else {
+                const int so = seed_outcome(it.cols, it.n, it.c, it.L);
+                if (so < 0) {
+                    grow = true;
+                } else if (so == 0) {
+                    write_result(a, idx, JATAM_DET_BOUNDED, it.k, 1u, mono);
+                    key = 2;
+                } else {
+                    write_result(a, idx, so, 0, 0u, 0u);
+                    key = (so == JATAM_ND_LOCAL) ? 0 : 1;
+                }
+            }
+        }
+        const unsigned gm = __ballot_sync(FULL, grow);
+        if (gm) {
+            unsigned long long slot = 0;
+            if (lane == 0) slot = atomicAdd(a.list_count, (unsigned long long)__popc(gm));
+            slot = __shfl_sync(FULL, slot, 0);
+            if (grow) a.list[slot + __popc(gm & lanemask_lt())] = idx;
+        }
+        if (a.use_hist) {
+#pragma unroll
+            for (int q = 0; q < 3; ++q) {
+                const unsigned m = __ballot_sync(FULL, key == q);
+                if (m) {
+                    unsigned long long v = (key == q) ? sid : ~0ull;
+#pragma unroll
+                    for (int off = 16; off > 0; off >>= 1) {
+                        const unsigned long long o = __shfl_xor_sync(FULL, v, off);
+                        v = o < v ? o : v;
+                    }
+                    if (lane == 0) {
+                        atomicAdd(&s_cnt[q], (unsigned)__popc(m));
+                        atomicMin(&s_min[q], v);
+                    }
+                }
+            }
+        }
+    }
+    __syncthreads();
+    if (a.use_hist && threadIdx.x < 3 && s_cnt[threadIdx.x]) {
+        const int q = threadIdx.x;
+        const unsigned long long key = (q == 0) ? ((unsigned long long)JATAM_ND_LOCAL << 32)
+                                     : (q == 1) ? ((unsigned long long)JATAM_UNBOUNDED << 32)
+                                                : (unsigned long long)mono;
+        const unsigned sz = (q == 2) ? 1u : 0u;
+        table_insert(a.table, key, s_cnt[q], s_min[q], sz, sz, a.err);
+    }
+}
+
 template <int S>
 __global__ void __launch_bounds__(256) classify_kernel(const LaunchArgs a)
 {
@@ -582,26 +743,21 @@ __global__ void __launch_bounds__(256) classify_kernel(const LaunchArgs a)
     Ls.ymin = Ls.ymax = Ls.xmin = Ls.xmax = 0;
     Ls.diverged = 0;
     Ls.forced = 0;
-    Ls.pblk = 0xFFFFFFFFu;
-    Ls.pbuf = make_uint4(0, 0, 0, 0);
+    Ls.ka = Ls.kb = NO_BLOCK;
+    Ls.pa = Ls.pb = make_uint4(0, 0, 0, 0);
     unsigned long long q_next = 0, q_end = 0;  // this warp's slice of the work counter
-    // the lone seed: a 1 x 1 crop with its cell at (0, 0)
-    const uint32_t monomer_hash = oaat_finish(oaat_add(oaat_add(oaat_add(oaat_add(0u, 1u), 1u), 0u), 0u));
     const int b_uniform = log2_colours(a.c);
+    const unsigned long long total = *a.list_count;  // items the pre-filter left to grow
 
     for (;;) {
-        // ---- service: write finished genotypes, hand out new ones and pre-check
-        // them, until every lane is growing or out of work (all lanes together)
+        // ---- service: write finished genotypes and hand out new ones from the
+        // pre-filter's list (all lanes together)
         for (;;) {
             if (Ls.phase == PH_WRITE) {
                 const bool shaped = Ls.cls == JATAM_DET_BOUNDED || Ls.cls == JATAM_ND_STERIC;
                 const unsigned size = shaped ? (unsigned)Ls.size0 : 0u;
                 const uint32_t hash = shaped ? Ls.hash : 0u;
-                if (a.out) {
-                    const uint32_t w0 = (uint32_t)(Ls.cls & 255) | ((uint32_t)(Ls.decided & 255) << 8) | (size << 16);
-                    reinterpret_cast<uint2 *>(a.out)[Ls.item] = make_uint2(w0, hash);
-                }
-                if (a.fitness) a.fitness[Ls.item] = (Ls.cls == JATAM_DET_BOUNDED) ? (int32_t)size : 0;
+                write_result(a, Ls.item, Ls.cls, Ls.decided, size, hash);
                 if (a.use_hist && Ls.cls != 255)
                     hist_insert(H, a.table, ((unsigned long long)Ls.cls << 32) | hash, Ls.sid, size, a.err);
                 Ls.phase = PH_NEED;
@@ -610,87 +766,37 @@ __global__ void __launch_bounds__(256) classify_kernel(const LaunchArgs a)
             if (!need) break;
             const int cnt = __popc(need);
             const int rank = __popc(need & lanemask_lt());
-            unsigned long long my_idx = ~0ull;
+            unsigned long long my_pos = ~0ull;
             int assigned = 0;
             while (assigned < cnt) {
                 if (q_next >= q_end) {
                     unsigned long long nb = 0;
                     if (lane == 0) nb = atomicAdd(a.work_next, (unsigned long long)CHUNK);
                     nb = __shfl_sync(FULL, nb, 0);
-                    if (nb >= a.count) break;
+                    if (nb >= total) break;
                     q_next = nb;
-                    q_end = min(nb + (unsigned long long)CHUNK, a.count);
+                    q_end = min(nb + (unsigned long long)CHUNK, total);
                 }
                 const int take = (int)min((unsigned long long)(cnt - assigned), q_end - q_next);
                 if (Ls.phase == PH_NEED && rank >= assigned && rank < assigned + take)
-                    my_idx = q_next + (unsigned long long)(rank - assigned);
+                    my_pos = q_next + (unsigned long long)(rank - assigned);
                 q_next += (unsigned long long)take;
                 assigned += take;
             }
             if (Ls.phase == PH_NEED) {
-                if (my_idx == ~0ull) {
+                if (my_pos == ~0ull) {
                     Ls.phase = PH_DONE;
                 } else {
-                    Ls.item = my_idx;
+                    const unsigned long long item = a.list[my_pos];
+                    const Item it = load_item(a, item, b_uniform, S);
+                    Ls.item = item;
+                    Ls.sid = it.sid;
+                    Ls.cols = it.cols;
+                    Ls.n = it.n; Ls.c = it.c; Ls.L = it.L; Ls.k = it.k;
                     Ls.phase = PH_INIT;
-                    if (a.mode == MODE_RECORDS) {
-                        const uint4 raw = *reinterpret_cast<const uint4 *>(a.colours + 16ull * my_idx);
-                        if (a.shapes) {
-                            const uint32_t sh = *reinterpret_cast<const uint32_t *>(a.shapes + 4ull * my_idx);
-                            Ls.n = sh & 255; Ls.c = (sh >> 8) & 255; Ls.L = (sh >> 16) & 255; Ls.k = sh >> 24;
-                        }
-                        Ls.sid = a.ids ? a.ids[my_idx] : my_idx;
-                        unsigned long long cols = 0;
-                        bool ok = Ls.n >= 1 && Ls.n <= 4 && Ls.c >= 1 && Ls.c <= 8 && Ls.L >= 1 && Ls.L <= S &&
-                                  Ls.k >= 1;
-                        const uint32_t wv[4] = {raw.x, raw.y, raw.z, raw.w};
-#pragma unroll
-                        for (int e = 0; e < 16; ++e) {
-                            const int v = (wv[e >> 2] >> (8 * (e & 3))) & 255;
-                            if (e < 4 * Ls.n) {
-                                if (v >= Ls.c) ok = false;
-                                cols |= (unsigned long long)(v & 15) << (4 * e);
-                            }
-                        }
-                        Ls.cols = cols;
-                        if (!ok) {
-                            atomicOr(a.err, ERR_INVALID_ITEM);
-                            Ls.cls = 255;
-                            Ls.decided = 0;
-                            Ls.size0 = 0;
-                            Ls.hash = 0;
-                            Ls.phase = PH_WRITE;
-                        }
-                    } else {
-                        unsigned long long g;
-                        if (a.mode == MODE_RANGE) {
-                            g = a.first + my_idx;
-                        } else if (a.mode == MODE_GENOMES) {
-                            g = a.genomes[my_idx];
-                        } else {
-                            const unsigned long long i = a.first + my_idx;
-                            const uint4 w = philox4x32_10(make_uint4(0u, 1u << 24, (uint32_t)i, (uint32_t)(i >> 32)),
-                                                          a.key0, a.key1);
-                            g = ((unsigned long long)w.y << 32) | w.x;
-                        }
-                        const int bits = 4 * a.n * b_uniform;
-                        if (bits < 64) g &= (1ull << bits) - 1ull;
-                        Ls.sid = g;
-                        Ls.cols = unpack_genotype(g, a.n, b_uniform);
-                    }
                 }
             }
-            if (Ls.phase == PH_INIT) {
-                const int so = seed_outcome(Ls.cols, Ls.n, Ls.c, Ls.L);
-                if (so >= 0) {
-                    Ls.cls = (so == 0) ? JATAM_DET_BOUNDED : so;
-                    Ls.decided = (so == 0) ? Ls.k : 0;
-                    Ls.size0 = 1;
-                    Ls.hash = monomer_hash;
-                    Ls.phase = PH_WRITE;
-                }
-            }
-            if (!__any_sync(FULL, Ls.phase == PH_WRITE)) break;
+            break;  // every listed item grows: one round hands out work to all idle lanes
         }
         // ---- binding tables of the genotypes that grow, one warp-wide job each
         unsigned init = __ballot_sync(FULL, Ls.phase == PH_INIT);
@@ -703,12 +809,45 @@ __global__ void __launch_bounds__(256) classify_kernel(const LaunchArgs a)
         if (Ls.phase == PH_INIT) {
             Ls.rep = 0;
             Ls.phase = PH_START;
+            Ls.ka = NO_BLOCK;
+            Ls.pb = philox_block(0u, Ls.sid, a.key0, a.key1);
+            Ls.kb = 0u;
         }
         if (__all_sync(FULL, Ls.phase == PH_DONE)) break;
 
         // ---- growth: one step per busy lane per round, until a.stop_at lanes
         // have finished their genotype or no lane is left growing
         for (;;) {
+            // Philox blocks are computed for all lanes at once: when some lane
+            // lacks the block of its current draw, every lane that will need a
+            // block soon (its current one, or block 0 of its next replicate)
+            // computes it in the same pass
+            {
+                uint32_t want = NO_BLOCK;
+                bool now = false;
+                if (Ls.phase == PH_GROW) {
+                    const uint32_t key = (uint32_t)Ls.rep * 512u + ((uint32_t)Ls.step >> 2);
+                    if (Ls.ka != key && Ls.kb != key) {
+                        want = key;
+                        now = true;
+                    } else if (Ls.kb == NO_BLOCK && Ls.rep + 1 < Ls.k) {
+                        want = (uint32_t)(Ls.rep + 1) * 512u;
+                    }
+                } else if (Ls.phase == PH_START) {
+                    const uint32_t key = (uint32_t)Ls.rep * 512u;
+                    if (Ls.ka != key && Ls.kb != key) want = key;
+                }
+                if (__any_sync(FULL, now) && want != NO_BLOCK) {
+                    const uint4 w = philox_block(want, Ls.sid, a.key0, a.key1);
+                    if (now) {
+                        Ls.pa = w;
+                        Ls.ka = want;
+                    } else {
+                        Ls.pb = w;
+                        Ls.kb = want;
+                    }
+                }
+            }
             if (Ls.phase == PH_START || Ls.phase == PH_GROW) lane_step<S>(Ls, my, a.key0, a.key1, a.err);
             const unsigned busy = __ballot_sync(FULL, Ls.phase == PH_START || Ls.phase == PH_GROW);
             if (!busy) break;
@@ -767,10 +906,11 @@ __global__ void __launch_bounds__(256) classify_kernel(const LaunchArgs a)
     }
 }
 
-__global__ void reset_kernel(unsigned long long *work_next, unsigned *nkeys)
+__global__ void reset_kernel(unsigned long long *work_next, unsigned *nkeys, unsigned long long *list_count)
 {
     *work_next = 0ull;
     *nkeys = 0u;
+    *list_count = 0ull;
 }
 
 __global__ void table_init_kernel(Table t)
@@ -899,9 +1039,16 @@ cudaError_t launch_classify(const LaunchArgs &a, int S, int blocks, int warps_pe
     return cudaGetLastError();
 }
 
-cudaError_t launch_reset(unsigned long long *work_next, unsigned *nkeys, cudaStream_t st)
+cudaError_t launch_reset(unsigned long long *work_next, unsigned *nkeys, unsigned long long *list_count,
+                         cudaStream_t st)
 {
-    reset_kernel<<<1, 1, 0, st>>>(work_next, nkeys);
+    reset_kernel<<<1, 1, 0, st>>>(work_next, nkeys, list_count);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_prefilter(const LaunchArgs &a, int smax, int blocks, cudaStream_t st)
+{
+    prefilter_kernel<<<blocks, 256, 0, st>>>(a, smax);
     return cudaGetLastError();
 }
 

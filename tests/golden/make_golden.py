@@ -40,7 +40,7 @@ def write(name):
     res, placements = O.enumerate_space(n, c, L, k, seed, first, count, sampled=sampled)
     dt = time.time() - t0
     ids = (np.array([O.sample_genotype(i, n, c, seed) for i in range(first, first + count)], np.uint64)
-           if sampled and count <= (1 << 16) else None)
+           if sampled else None)
     digest = hashlib.sha256(res.tobytes()).hexdigest()
     hist = O.histogram(res, ids if ids is not None else (None if sampled else np.arange(first, first + count,
                                                                                           dtype=np.uint64)))
@@ -58,7 +58,7 @@ def write(name):
         json.dump(meta, f, indent=1)
         f.write("\n")
     with open(os.path.join(HERE, f"{name}_histogram.txt"), "w") as f:
-        f.write("# cls shape_hash size count min_id" + ("" if not sampled else "  (min_id: sample index)") + "\n")
+        f.write("# cls shape_hash size count min_id\n")
         for h in hist:
             f.write(f"{int(h['cls'])} {int(h['shape_hash'])} {int(h['size'])} {int(h['count'])} {int(h['min_id'])}\n")
     print(name, meta, flush=True)

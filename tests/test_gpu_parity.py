@@ -213,3 +213,14 @@ def test_argument_errors():
     assert e.value.code == J.JATAM_EINVAL and out["cls"][2] == 255
     # the error was consumed: the next call is clean
     J.classify_batch(bad[:2], n=2, c=8, L=16, k=4, seed=1, out=out[:2])
+
+
+def test_s38_sample_2e20_matches_golden():
+    """2^20 genotypes sampled from S_{3,8} on the 32 x 32 grid: SHA-256 of the
+    results and the histogram equal what the oracle wrote."""
+    n, c, L, k, seed, _, _, _ = W.WORKLOADS["s38_sample"]
+    res, hist, m = _dev_enumerate(n, c, L, k, seed, 0, 1 << 20, sampled=True)
+    gold = json.load(open(os.path.join(GOLDEN, "c3s_summary.json")))
+    assert np.bincount(res["cls"], minlength=4).tolist() == gold["class_counts"]
+    assert hashlib.sha256(res.tobytes()).hexdigest() == gold["results_sha256"]
+    assert _hist_rows(hist) == _golden_hist("c3s_histogram.txt")
