@@ -164,6 +164,30 @@ int jatam_hist_merge(const jatam_hist_entry *a, uint32_t na, const jatam_hist_en
                      jatam_hist_entry *out, uint32_t cap, uint32_t *len);
 
 /*
+ * jatam_autotune -- pick the launch shape of the classification kernel for
+ * each of n_shapes configurations (Section 2.6 batches the space by device
+ * capacity; the best batch shape depends on the grid size and tile count).
+ * For every configuration it times the kernel on a sample of its space
+ * (the first min(2^18, |space|) genotypes, or 2^18 sampled ones when
+ * cfg.flags has JATAM_SAMPLED) for every candidate (warps per CTA in
+ * {2, 4, 8}, growth-round threshold in {4, 8, 12, 16, 20, 24, 28}) and keeps
+ * the fastest for the key (lattice template, n, c) of that configuration;
+ * later calls with the same key use it.  The choice never changes results:
+ * the draws depend only on the genotype, the replicate and the step.
+ * Synchronises `stream`.
+ */
+int jatam_autotune(const jatam_config *shapes, uint32_t n_shapes, void *stream);
+
+/*
+ * jatam_set_tuning / jatam_get_tuning -- set or read the launch shape used for
+ * cfg's key: warps_per_cta 1..8, stop_at 1..32 (lanes that must have finished
+ * their genotype before a warp leaves a growth round).  A key never tuned or
+ * set uses the defaults (8 warps, 16).
+ */
+int jatam_set_tuning(const jatam_config *cfg, int warps_per_cta, int stop_at);
+int jatam_get_tuning(const jatam_config *cfg, int *warps_per_cta, int *stop_at);
+
+/*
  * jatam_profile -- when enable != 0, every later call records CUDA events
  * around its classification kernel on the call's stream; jatam_kernel_ms()
  * then waits for the last such pair and returns its elapsed milliseconds in

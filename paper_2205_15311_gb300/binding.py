@@ -64,6 +64,12 @@ def lib():
         L.jatam_hist_merge.argtypes = [_VP, _U32, _VP, _U32, _VP, _U32, _VP]
         for f in ("jatam_enumerate", "jatam_classify_batch", "ga_evaluate", "jatam_philox", "jatam_hist_merge"):
             getattr(L, f).restype = ctypes.c_int
+        L.jatam_autotune.argtypes = [_VP, _U32, _VP]
+        L.jatam_autotune.restype = ctypes.c_int
+        L.jatam_set_tuning.argtypes = [_VP, ctypes.c_int, ctypes.c_int]
+        L.jatam_set_tuning.restype = ctypes.c_int
+        L.jatam_get_tuning.argtypes = [_VP, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]
+        L.jatam_get_tuning.restype = ctypes.c_int
         L.jatam_profile.argtypes = [ctypes.c_int]
         L.jatam_profile.restype = ctypes.c_int
         L.jatam_kernel_ms.argtypes = [ctypes.POINTER(ctypes.c_float)]
@@ -97,6 +103,18 @@ def jatam_philox(inp, N, out, stream):
 
 def jatam_hist_merge(a, na, b, nb, out, cap, length):
     return lib().jatam_hist_merge(a, na, b, nb, out, cap, length)
+
+
+def jatam_autotune(shapes, n_shapes, stream):
+    return lib().jatam_autotune(shapes, n_shapes, stream)
+
+
+def jatam_set_tuning(cfg, warps_per_cta, stop_at):
+    return lib().jatam_set_tuning(cfg, warps_per_cta, stop_at)
+
+
+def jatam_get_tuning(cfg, warps_per_cta, stop_at):
+    return lib().jatam_get_tuning(cfg, warps_per_cta, stop_at)
 
 
 def jatam_profile(enable):
@@ -174,6 +192,26 @@ def philox(records, out, stream=None):
     """records: [N][6] uint32 (ctr0..3, key0, key1) -> out [N][4] uint32."""
     N = int(records.shape[0])
     return check(jatam_philox(_addr(records), N, _addr(out), _stream_handle(stream)))
+
+
+def autotune(configs, stream=None):
+    """configs: list of dicts with n, c, L, k, seed (and optional sampled)."""
+    arr = (jatam_config * len(configs))()
+    for i, d in enumerate(configs):
+        arr[i] = make_config(d["n"], d["c"], d["L"], d["k"], d.get("seed", 0), JATAM_SAMPLED if d.get("sampled") else 0)
+    return check(jatam_autotune(ctypes.addressof(arr), len(configs), _stream_handle(stream)))
+
+
+def set_tuning(n, c, L, warps_per_cta, stop_at):
+    cfg = make_config(n, c, L, 1, 0)
+    return check(jatam_set_tuning(ctypes.addressof(cfg), warps_per_cta, stop_at))
+
+
+def get_tuning(n, c, L):
+    cfg = make_config(n, c, L, 1, 0)
+    w, s = ctypes.c_int(0), ctypes.c_int(0)
+    check(jatam_get_tuning(ctypes.addressof(cfg), ctypes.byref(w), ctypes.byref(s)))
+    return w.value, s.value
 
 
 def last_kernel_ms() -> float:

@@ -5,6 +5,7 @@
 #include <cstdlib>
 #include <cstring>
 #include <map>
+#include <tuple>
 #include <mutex>
 #include <string>
 
@@ -19,8 +20,15 @@ namespace {
 thread_local std::string g_last_error;
 std::mutex g_mutex;
 bool g_profile = false;
-int g_stop_at = 16;  // lanes that must finish before a warp leaves its growth rounds
+int g_stop_override = 0;
 int g_warps_override = 0;
+
+struct Tuning {
+    int warps = 8;
+    int stop_at = 16;
+};
+// launch shape per key (lattice template, n, c); n = c = 0 for mixed batches
+std::map<std::tuple<int, int, int>, Tuning> g_tuned;
 
 // optional overrides of the launch shape (for tuning sweeps)
 void read_env_overrides()
@@ -30,7 +38,7 @@ void read_env_overrides()
     done = true;
     if (const char *v = getenv("JATAM_STOP_AT")) {
         int x = atoi(v);
-        if (x >= 1 && x <= 32) g_stop_at = x;
+        if (x >= 1 && x <= 32) g_stop_override = x;
     }
     if (const char *v = getenv("JATAM_WARPS_PER_CTA")) {
         int x = atoi(v);
@@ -176,8 +184,16 @@ int check_params(int n, int c, int L, int k, bool packed)
     return JATAM_OK;
 }
 
-// launch shape: warps per CTA by lattice template; CTAs = resident CTAs on every SM
-int warps_for(int S) { return g_warps_override ? g_warps_override : (S == 32 ? 2 : S == 16 ? 8 : 8); }
+Tuning tuning_for(int S, int n, int c)
+{
+    Tuning t;
+    auto it = g_tuned.find(std::make_tuple(S, n, c));
+    if (it != g_tuned.end()) t = it->second;
+    if (S == 32 && it == g_tuned.end()) t.warps = 2;  // the 32 x 32 lattice takes 33 KB of shared memory per warp
+    if (g_warps_override) t.warps = g_warps_override;
+    if (g_stop_override) t.stop_at = g_stop_override;
+    return t;
+}
 
 struct Outputs {
     jatam_result *out_dev = nullptr;
@@ -190,7 +206,8 @@ struct Outputs {
 // Run the classification of one launch description plus the histogram
 // kernels, stage host outputs, and synchronise when needed.
 int run(Workspace *w, LaunchArgs a, int S, jatam_result *out, int32_t *fitness, jatam_hist_entry *hist,
-        uint32_t hist_cap, uint32_t *hist_len, bool sync_flag, cudaStream_t st)
+        uint32_t hist_cap, uint32_t *hist_len, bool sync_flag, cudaStream_t st, const Tuning *force = nullptr,
+        float *kernel_ms = nullptr)
 {
     Outputs o;
     const Kind ko = kind_of(out, w->device), kf = kind_of(fitness, w->device), kh = kind_of(hist, w->device),
@@ -239,7 +256,9 @@ int run(Workspace *w, LaunchArgs a, int S, jatam_result *out, int32_t *fitness, 
     a.use_hist = hist ? 1 : 0;
     a.work_next = w->work_next;
     a.err = w->err;
-    a.stop_at = g_stop_at;
+    const Tuning tune = force ? *force : tuning_for(S, a.mode == MODE_RECORDS && a.shapes ? 0 : a.n,
+                                                    a.mode == MODE_RECORDS && a.shapes ? 0 : a.c);
+    a.stop_at = tune.stop_at;
     if (n_items) {
         int rc = grow(&w->list, &w->list_bytes, n_items * 8);
         if (rc) return rc;
@@ -247,7 +266,7 @@ int run(Workspace *w, LaunchArgs a, int S, jatam_result *out, int32_t *fitness, 
     a.list = static_cast<unsigned long long *>(w->list);
     a.list_count = w->list_count;
 
-    const int warps = warps_for(S);
+    const int warps = tune.warps;
     const int si = S == 8 ? 0 : S == 16 ? 1 : 2;
     if (!w->attrs_set[si][warps]) {
         CUDA_TRY(classify_set_attributes(S, warps));
@@ -268,9 +287,10 @@ int run(Workspace *w, LaunchArgs a, int S, jatam_result *out, int32_t *fitness, 
         if (pblocks > 8LL * w->num_sms) pblocks = 8LL * w->num_sms;
         CUDA_TRY(launch_prefilter(a, S, (int)pblocks, st));
     }
-    if (g_profile) CUDA_TRY(cudaEventRecord(w->k_start, st));
+    const bool timed = g_profile || kernel_ms;
+    if (timed) CUDA_TRY(cudaEventRecord(w->k_start, st));
     if (n_items) CUDA_TRY(launch_classify(a, S, (int)blocks, warps, st));
-    if (g_profile) {
+    if (timed) {
         CUDA_TRY(cudaEventRecord(w->k_stop, st));
         w->k_valid = true;
     }
@@ -289,6 +309,10 @@ int run(Workspace *w, LaunchArgs a, int S, jatam_result *out, int32_t *fitness, 
         CUDA_TRY(cudaMemcpyAsync(&w->host_words[1], w->nkeys, 4, cudaMemcpyDeviceToHost, st));
     }
     CUDA_TRY(cudaEventRecord(w->last, st));
+    if (kernel_ms) {
+        CUDA_TRY(cudaEventSynchronize(w->k_stop));
+        CUDA_TRY(cudaEventElapsedTime(kernel_ms, w->k_start, w->k_stop));
+    }
     if (!must_sync) return JATAM_OK;
     CUDA_TRY(cudaStreamSynchronize(st));
     const unsigned err = w->host_words[0];
@@ -507,6 +531,87 @@ int jatam_hist_merge(const jatam_hist_entry *a, uint32_t na, const jatam_hist_en
     }
     *len = m;
     if (m > cap) return fail(JATAM_EINVAL, "merged histogram has %u keys but cap is %u", m, cap);
+    return JATAM_OK;
+}
+
+int jatam_autotune(const jatam_config *shapes, uint32_t n_shapes, void *stream)
+{
+    std::lock_guard<std::mutex> lock(g_mutex);
+    g_last_error.clear();
+    if (n_shapes && !shapes) return fail(JATAM_EINVAL, "shapes is NULL");
+    Workspace *w = nullptr;
+    int rc = workspace(&w);
+    if (rc) return rc;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    for (uint32_t i = 0; i < n_shapes; ++i) {
+        const jatam_config &cfg = shapes[i];
+        rc = check_params(cfg.n, cfg.c, cfg.L, cfg.k, true);
+        if (rc) return rc;
+        const int S = lattice_template(cfg.L);
+        const int bits = 4 * cfg.n * log2c(cfg.c);
+        const bool sampled = (cfg.flags & JATAM_SAMPLED) != 0;
+        unsigned long long count = 1ull << 18;
+        if (!sampled && bits < 18) count = 1ull << bits;
+        LaunchArgs a{};
+        a.mode = sampled ? MODE_SAMPLED : MODE_RANGE;
+        a.first = 0;
+        a.count = count;
+        a.n = cfg.n; a.c = cfg.c; a.L = cfg.L; a.k = cfg.k;
+        a.key0 = (uint32_t)cfg.seed;
+        a.key1 = (uint32_t)(cfg.seed >> 32);
+        Tuning best;
+        float best_ms = 1e30f;
+        for (int warps : {2, 4, 8}) {
+            const int bytes = classify_smem_bytes(S, warps);
+            if (bytes > 200 * 1024) continue;
+            for (int stop : {4, 8, 12, 16, 20, 24, 28}) {
+                Tuning t;
+                t.warps = warps;
+                t.stop_at = stop;
+                float ms_min = 1e30f;
+                for (int rep = 0; rep < 2; ++rep) {
+                    float ms = 0.f;
+                    rc = run(w, a, S, nullptr, nullptr, nullptr, 0, nullptr, true, st, &t, &ms);
+                    if (rc) return rc;
+                    ms_min = ms < ms_min ? ms : ms_min;
+                }
+                if (ms_min < best_ms) {
+                    best_ms = ms_min;
+                    best = t;
+                }
+            }
+        }
+        g_tuned[std::make_tuple(S, (int)cfg.n, (int)cfg.c)] = best;
+    }
+    return JATAM_OK;
+}
+
+int jatam_set_tuning(const jatam_config *cfg, int warps_per_cta, int stop_at)
+{
+    std::lock_guard<std::mutex> lock(g_mutex);
+    g_last_error.clear();
+    if (!cfg) return fail(JATAM_EINVAL, "cfg is NULL");
+    if (warps_per_cta < 1 || warps_per_cta > 8 || stop_at < 1 || stop_at > 32)
+        return fail(JATAM_EINVAL, "warps_per_cta must be 1..8 and stop_at 1..32");
+    if (cfg->L < 1 || cfg->L > JATAM_MAX_GRID) return fail(JATAM_EUNSUPPORTED, "L must be 1..32");
+    const int S = lattice_template(cfg->L);
+    if (classify_smem_bytes(S, warps_per_cta) > 200 * 1024)
+        return fail(JATAM_EINVAL, "%d warps of a %dx%d lattice do not fit in shared memory", warps_per_cta, S, S);
+    Tuning t;
+    t.warps = warps_per_cta;
+    t.stop_at = stop_at;
+    g_tuned[std::make_tuple(S, (int)cfg->n, (int)cfg->c)] = t;
+    return JATAM_OK;
+}
+
+int jatam_get_tuning(const jatam_config *cfg, int *warps_per_cta, int *stop_at)
+{
+    std::lock_guard<std::mutex> lock(g_mutex);
+    g_last_error.clear();
+    if (!cfg || !warps_per_cta || !stop_at) return fail(JATAM_EINVAL, "NULL argument");
+    const Tuning t = tuning_for(lattice_template(cfg->L), cfg->n, cfg->c);
+    *warps_per_cta = t.warps;
+    *stop_at = t.stop_at;
     return JATAM_OK;
 }
 

@@ -324,34 +324,17 @@ __device__ __forceinline__ void lane_step(Lane &Ls, uint32_t *my, uint32_t k0, u
 {
     using G = Geo<S>;
     const int occ = (Ls.rep == 0) ? G::OCCA : G::OCCB;
-    int px, py, tau;
-    if (Ls.phase == PH_START) {
-        if (Ls.rep == 0) {
-            if (Ls.dlo <= Ls.dhi) {
-                const int lo = max(Ls.dlo, 0), hi = min(Ls.dhi, S - 1);
-                clear_rows<S>(my, G::OCCA, lo, hi);
-                clear_rows<S>(my, G::OCCB, lo, hi);
-                clear_rows<S>(my, G::FRONT, lo, hi);
-            }
-            Ls.dlo = S;
-            Ls.dhi = -1;
-        } else if (Ls.blo <= Ls.bhi) {
-            clear_rows<S>(my, G::OCCB, Ls.blo, Ls.bhi);  // FRONT is empty: the replicate terminated
-        }
-        Ls.blo = S;
-        Ls.bhi = -1;
-        px = py = Ls.L >> 1;
+    const bool seed = Ls.phase == PH_START;
+    int b, tau;
+    if (seed) {
+        // a new replicate: the seed, tile 0 in orientation 0, at the centre
+        b = (Ls.L >> 1) * S + (Ls.L >> 1);
         tau = 0;
-        const int b = py * S + px;
-        my[(occ + (b >> 5)) * 32] |= 1u << (b & 31);
-        if (Ls.rep == 0) nib_set<S>(my, b, 0);
-        Ls.size = 1;
+        Ls.size = 0;
         Ls.step = 0;
         Ls.nF = 0;
         Ls.diverged = 0;
         Ls.forced = 1;
-        Ls.ymin = Ls.ymax = py;
-        Ls.xmin = Ls.xmax = px;
         Ls.phase = PH_GROW;
     } else {
         const uint32_t key = (uint32_t)Ls.rep * 512u + ((uint32_t)Ls.step >> 2);
@@ -383,20 +366,20 @@ __device__ __forceinline__ void lane_step(Lane &Ls, uint32_t *my, uint32_t k0, u
             }
         }
         const int bit = nth_set(f, i);
-        const int b = w * 32 + bit;
-        px = b & (S - 1);
-        py = b >> G::LOG2S;
+        b = w * 32 + bit;
         tau = nib_get<S>(my, b);
         my[(G::FRONT + w) * 32] = f & ~(1u << bit);
-        my[(occ + w) * 32] |= 1u << bit;
         Ls.nF -= 1;
-        Ls.size += 1;
         Ls.step += 1;
-        Ls.ymin = min(Ls.ymin, py);
-        Ls.ymax = max(Ls.ymax, py);
-        Ls.xmin = min(Ls.xmin, px);
-        Ls.xmax = max(Ls.xmax, px);
     }
+    const int px = b & (S - 1), py = b >> G::LOG2S;
+    my[(occ + (b >> 5)) * 32] |= 1u << (b & 31);
+    if (seed && Ls.rep == 0) nib_set<S>(my, b, 0);
+    Ls.size += 1;
+    Ls.ymin = seed ? py : min(Ls.ymin, py);
+    Ls.ymax = seed ? py : max(Ls.ymax, py);
+    Ls.xmin = seed ? px : min(Ls.xmin, px);
+    Ls.xmax = seed ? px : max(Ls.xmax, px);
     Ls.dlo = min(Ls.dlo, py - 1);
     Ls.dhi = max(Ls.dhi, py + 1);
     if (Ls.rep > 0) {
@@ -404,7 +387,9 @@ __device__ __forceinline__ void lane_step(Lane &Ls, uint32_t *my, uint32_t k0, u
         Ls.bhi = max(Ls.bhi, py);
     }
 
-    // the empty neighbours of the new tile: only their candidate sets changed
+    // the empty neighbours of the new tile: only their candidate sets changed.
+    // Straight-line code: every lane evaluates all four sides, whatever their
+    // case, so the warp stays converged.
     const uint32_t m01 = my[(G::NBM + 2 * tau) * 32];
     const uint32_t m23 = my[(G::NBM + 2 * tau + 1) * 32];
     bool nd = false, unb = false;
@@ -413,36 +398,31 @@ __device__ __forceinline__ void lane_step(Lane &Ls, uint32_t *my, uint32_t k0, u
         const uint32_t M = ((d == 0) ? m01 : (d == 1) ? (m01 >> 16) : (d == 2) ? m23 : (m23 >> 16)) & 0xFFFFu;
         const int qx = px + (d == 1) - (d == 3);
         const int qy = py + (d == 2) - (d == 0);
-        if (qx < 0 || qy < 0 || qx >= Ls.L || qy >= Ls.L) {
-            // a site outside the grid: a single candidate means unbounded growth
-            if (M) {
-                if (M & (M - 1)) nd = true;
-                else unb = true;
-            }
-            continue;
-        }
-        const int qb = qy * S + qx;
+        const bool in = (unsigned)qx < (unsigned)Ls.L && (unsigned)qy < (unsigned)Ls.L;
+        const int qb = in ? qy * S + qx : b;  // outside the grid: read the new tile's own cell, write nothing
         const int qw = qb >> 5;
         const uint32_t qbit = 1u << (qb & 31);
-        if (my[(occ + qw) * 32] & qbit) continue;
+        const int sh = (qb & 7) * 4;
+        const uint32_t ow = my[(occ + qw) * 32];
         const uint32_t fw = my[(G::FRONT + qw) * 32];
-        if (fw & qbit) {
-            // already a frontier site with one candidate: any other one is ambiguity
-            if (M & ~(1u << nib_get<S>(my, qb))) nd = true;
-        } else if (M) {
-            if (M & (M - 1)) {
-                nd = true;
-            } else {
-                const int tn = __ffs(M) - 1;
-                if (Ls.rep > 0 && !Ls.diverged) {
-                    // replicate 0 must hold the same tuple here, or this replicate
-                    // cannot end in replicate 0's configuration
-                    if (!(my[(G::OCCA + qw) * 32] & qbit) || nib_get<S>(my, qb) != tn) Ls.diverged = 1;
-                }
-                nib_set<S>(my, qb, tn);
-                my[(G::FRONT + qw) * 32] = fw | qbit;
-                Ls.nF += 1;
-            }
+        const uint32_t nw = my[(G::NIB + (qb >> 3)) * 32];
+        const int tq = (nw >> sh) & 15;
+        const bool empty = in && !(ow & qbit);
+        const bool isf = (fw & qbit) != 0;
+        const bool multi = (M & (M - 1)) != 0;
+        // two distinct candidates at one site (inside or outside the grid), or a
+        // frontier site whose single candidate is contradicted
+        nd = nd || (!in && multi) || (empty && (isf ? (M & ~(1u << tq)) != 0 : multi));
+        // one candidate outside the grid: growth past the cap
+        unb = unb || (!in && M != 0 && !multi);
+        if (empty && !isf && M != 0 && !multi) {
+            const int tn = __ffs(M) - 1;
+            // replicate 0 must hold the same tuple here, or this replicate can
+            // no longer end in replicate 0's configuration
+            if (Ls.rep > 0 && !Ls.diverged && (!(my[(G::OCCA + qw) * 32] & qbit) || tq != tn)) Ls.diverged = 1;
+            my[(G::NIB + (qb >> 3)) * 32] = (nw & ~(15u << sh)) | ((uint32_t)tn << sh);
+            my[(G::FRONT + qw) * 32] = fw | qbit;
+            Ls.nF += 1;
         }
     }
     if (!(nd || unb || Ls.nF == 0)) return;
@@ -485,6 +465,11 @@ __device__ __forceinline__ void lane_step(Lane &Ls, uint32_t *my, uint32_t k0, u
         Ls.decided = Ls.k;
         Ls.phase = PH_SHAPE;
     } else {
+        // next replicate: its occupancy starts empty (the frontier of a
+        // terminated replicate is already empty)
+        if (Ls.blo <= Ls.bhi) clear_rows<S>(my, G::OCCB, Ls.blo, Ls.bhi);
+        Ls.blo = S;
+        Ls.bhi = -1;
         Ls.rep += 1;
         Ls.phase = PH_START;
     }
@@ -807,6 +792,17 @@ __global__ void __launch_bounds__(256) classify_kernel(const LaunchArgs a)
         }
         __syncwarp();
         if (Ls.phase == PH_INIT) {
+            // a new genotype: clear whatever the previous one left in the bitmaps
+            if (Ls.dlo <= Ls.dhi) {
+                const int lo = max(Ls.dlo, 0), hi = min(Ls.dhi, S - 1);
+                clear_rows<S>(my, G::OCCA, lo, hi);
+                clear_rows<S>(my, G::OCCB, lo, hi);
+                clear_rows<S>(my, G::FRONT, lo, hi);
+            }
+            Ls.dlo = S;
+            Ls.dhi = -1;
+            Ls.blo = S;
+            Ls.bhi = -1;
             Ls.rep = 0;
             Ls.phase = PH_START;
             Ls.ka = NO_BLOCK;

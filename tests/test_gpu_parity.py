@@ -224,3 +224,25 @@ def test_s38_sample_2e20_matches_golden():
     assert np.bincount(res["cls"], minlength=4).tolist() == gold["class_counts"]
     assert hashlib.sha256(res.tobytes()).hexdigest() == gold["results_sha256"]
     assert _hist_rows(hist) == _golden_hist("c3s_histogram.txt")
+
+
+def test_results_do_not_depend_on_the_launch_shape():
+    """The draws depend only on (genotype, replicate, step): every launch shape
+    gives bit-identical results; jatam_autotune picks one of them."""
+    n, c, L, k, seed = 2, 8, 16, 20, 2
+    first, count = 5 << 20, 200000
+    base, hbase, _ = _dev_enumerate(n, c, L, k, seed, first, count)
+    try:
+        for warps, stop in ((1, 1), (2, 32), (4, 8), (8, 3)):
+            J.set_tuning(n, c, L, warps, stop)
+            assert J.get_tuning(n, c, L) == (warps, stop)
+            res, hist, _ = _dev_enumerate(n, c, L, k, seed, first, count)
+            assert np.array_equal(res, base)
+            assert np.array_equal(hist, hbase)
+        J.autotune([{"n": n, "c": c, "L": L, "k": k, "seed": seed}])
+        w, s = J.get_tuning(n, c, L)
+        assert 1 <= w <= 8 and 1 <= s <= 32
+        res, _, _ = _dev_enumerate(n, c, L, k, seed, first, count)
+        assert np.array_equal(res, base)
+    finally:
+        J.set_tuning(n, c, L, 8, 16)
