@@ -175,11 +175,14 @@ def reference_arm(args):
 
 
 def main():
+    global WORKLOAD
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--workload", default="s28_full",
+                    help="s28_full (the bench line), or s24_full / s28_paper / s38_sample for measurements")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end leg")
     ap.add_argument("--profile-genomes", type=int, default=0,
@@ -189,6 +192,7 @@ def main():
                     help="classify only the first COUNT genotypes (small profiling cases; not a bench line)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
+    WORKLOAD = args.workload
     if args.impl == "reference":
         return reference_arm(args)
 
@@ -294,8 +298,9 @@ def main():
         n_sms = props.multi_processor_count
         alu_peak = n_sms * 128 * sm_max * 1e6 / 1e12  # int32 lane-ops per second, T
         placements = None
-        golden = os.path.join(ROOT, "tests", "golden", "c2_summary.json")
-        if os.path.exists(golden) and seed == 2 and not args.count:
+        golden = os.path.join(ROOT, "tests", "golden",
+                              {"s28_full": "c2_summary.json", "s24_full": "c1_summary.json"}.get(WORKLOAD, "-"))
+        if os.path.exists(golden) and rank == 0 and not args.count:
             placements = json.load(open(golden))["placements"]
         roofline = None
         kms = float(np.mean(kernel_ms))
@@ -304,7 +309,8 @@ def main():
             achieved = ops / (kms / 1e3) / 1e12
             roofline = {"bound": "alu", "achieved": round(achieved, 4), "peak": round(alu_peak, 2),
                         "unit": "Tops/s", "frac": round(achieved / alu_peak, 4), "traffic": None,
-                        "kernel": "classify_kernel<16>", "kernel_ms": round(kms, 4),
+                        "kernel": f"classify_kernel<{8 if L <= 8 else 16 if L <= 16 else 32}>",
+                        "kernel_ms": round(kms, 4),
                         "peak_source": f"{n_sms} SMs x 128 int32 lanes x {sm_max:.0f} MHz (MEASURED_PEAKS sm_max)",
                         "hbm_gbs": round(count * 8 / (kms / 1e3) / 1e9, 1),
                         "hbm_frac_of_measured": round(count * 8 / (kms / 1e3) / 1e9 / float(peaks.get("hbm_gbs", 6753.1)), 4)}
@@ -320,7 +326,8 @@ def main():
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "u32", "data": "synthetic",
-            "config": {"workload": f"{WORKLOAD}: all 8^8 genotypes of S_{{2,8}}, n={n} c={c} L={L} k={k} seed={seed0}",
+            "config": {"workload": f"{WORKLOAD}: {'sampled' if sampled else 'all'} {count} genotypes of "
+                                   f"S_{{{n},{c}}}, n={n} c={c} L={L} k={k} seed={seed0}",
                        "global_batch": world * count, "parallelism": f"replicas x{world}",
                        "l2": "256 MB buffer written between timed steps; outputs 134 MB > L2",
                        "distinct_phenotypes": nk},

@@ -89,7 +89,7 @@ struct Workspace {
     cudaEvent_t last = nullptr;  // end of the previous call's work on this device
     cudaEvent_t k_start = nullptr, k_stop = nullptr;  // around the last profiled kernel
     bool k_valid = false;
-    bool attrs_set[3][9] = {};
+    int max_dyn_smem[3] = {0, 0, 0};  // the kernel attribute only ever grows
 };
 
 std::map<int, Workspace *> g_ws;
@@ -268,9 +268,9 @@ int run(Workspace *w, LaunchArgs a, int S, jatam_result *out, int32_t *fitness, 
 
     const int warps = tune.warps;
     const int si = S == 8 ? 0 : S == 16 ? 1 : 2;
-    if (!w->attrs_set[si][warps]) {
+    if (classify_smem_bytes(S, warps) > w->max_dyn_smem[si]) {
         CUDA_TRY(classify_set_attributes(S, warps));
-        w->attrs_set[si][warps] = true;
+        w->max_dyn_smem[si] = classify_smem_bytes(S, warps);
     }
     int per_sm = 0;
     CUDA_TRY(classify_occupancy(S, warps, &per_sm));
