@@ -315,118 +315,12 @@ __device__ __forceinline__ int seed_outcome(unsigned long long cols, int n, int 
     return grows ? -1 : 0;
 }
 
-// ---------------------------------------------------------------------------
-// one growth step of one lane: seed placement or one drawn placement, then the
-// evaluation of the new tile's empty neighbours and the replicate rule
-// ---------------------------------------------------------------------------
+// The replicate just ended (local ambiguity, unbounded growth, or an empty
+// frontier): apply the first-deciding-replicate rule.
 template <int S>
-__device__ __forceinline__ void lane_step(Lane &Ls, uint32_t *my, uint32_t k0, uint32_t k1, unsigned *err)
+__device__ __forceinline__ void replicate_end(Lane &Ls, uint32_t *my, bool nd, bool unb)
 {
     using G = Geo<S>;
-    const int occ = (Ls.rep == 0) ? G::OCCA : G::OCCB;
-    const bool seed = Ls.phase == PH_START;
-    int b, tau;
-    if (seed) {
-        // a new replicate: the seed, tile 0 in orientation 0, at the centre
-        b = (Ls.L >> 1) * S + (Ls.L >> 1);
-        tau = 0;
-        Ls.size = 0;
-        Ls.step = 0;
-        Ls.nF = 0;
-        Ls.diverged = 0;
-        Ls.forced = 1;
-        Ls.phase = PH_GROW;
-    } else {
-        const uint32_t key = (uint32_t)Ls.rep * 512u + ((uint32_t)Ls.step >> 2);
-        if (Ls.ka != key) {
-            if (Ls.kb == key) {
-                Ls.pa = Ls.pb;
-                Ls.kb = NO_BLOCK;
-            } else {
-                Ls.pa = philox_block(key, Ls.sid, k0, k1);
-            }
-            Ls.ka = key;
-        }
-        if (Ls.nF > 1) Ls.forced = 0;
-        const int sel = Ls.step & 3;
-        const uint32_t u = sel == 0 ? Ls.pa.x : sel == 1 ? Ls.pa.y : sel == 2 ? Ls.pa.z : Ls.pa.w;
-        uint32_t i = __umulhi(u, (uint32_t)Ls.nF);
-        int w = (max(Ls.ymin - 1, 0) * S) >> 5;
-        uint32_t f = 0;
-        for (;;) {
-            f = my[(G::FRONT + w) * 32];
-            const uint32_t cnt = __popc(f);
-            if (i < cnt) break;
-            i -= cnt;
-            if (++w >= G::NW) {
-                atomicOr(err, ERR_GUARD);
-                Ls.cls = 255;
-                Ls.phase = PH_WRITE;
-                return;
-            }
-        }
-        const int bit = nth_set(f, i);
-        b = w * 32 + bit;
-        tau = nib_get<S>(my, b);
-        my[(G::FRONT + w) * 32] = f & ~(1u << bit);
-        Ls.nF -= 1;
-        Ls.step += 1;
-    }
-    const int px = b & (S - 1), py = b >> G::LOG2S;
-    my[(occ + (b >> 5)) * 32] |= 1u << (b & 31);
-    if (seed && Ls.rep == 0) nib_set<S>(my, b, 0);
-    Ls.size += 1;
-    Ls.ymin = seed ? py : min(Ls.ymin, py);
-    Ls.ymax = seed ? py : max(Ls.ymax, py);
-    Ls.xmin = seed ? px : min(Ls.xmin, px);
-    Ls.xmax = seed ? px : max(Ls.xmax, px);
-    Ls.dlo = min(Ls.dlo, py - 1);
-    Ls.dhi = max(Ls.dhi, py + 1);
-    if (Ls.rep > 0) {
-        Ls.blo = min(Ls.blo, py);
-        Ls.bhi = max(Ls.bhi, py);
-    }
-
-    // the empty neighbours of the new tile: only their candidate sets changed.
-    // Straight-line code: every lane evaluates all four sides, whatever their
-    // case, so the warp stays converged.
-    const uint32_t m01 = my[(G::NBM + 2 * tau) * 32];
-    const uint32_t m23 = my[(G::NBM + 2 * tau + 1) * 32];
-    bool nd = false, unb = false;
-#pragma unroll
-    for (int d = 0; d < 4; ++d) {
-        const uint32_t M = ((d == 0) ? m01 : (d == 1) ? (m01 >> 16) : (d == 2) ? m23 : (m23 >> 16)) & 0xFFFFu;
-        const int qx = px + (d == 1) - (d == 3);
-        const int qy = py + (d == 2) - (d == 0);
-        const bool in = (unsigned)qx < (unsigned)Ls.L && (unsigned)qy < (unsigned)Ls.L;
-        const int qb = in ? qy * S + qx : b;  // outside the grid: read the new tile's own cell, write nothing
-        const int qw = qb >> 5;
-        const uint32_t qbit = 1u << (qb & 31);
-        const int sh = (qb & 7) * 4;
-        const uint32_t ow = my[(occ + qw) * 32];
-        const uint32_t fw = my[(G::FRONT + qw) * 32];
-        const uint32_t nw = my[(G::NIB + (qb >> 3)) * 32];
-        const int tq = (nw >> sh) & 15;
-        const bool empty = in && !(ow & qbit);
-        const bool isf = (fw & qbit) != 0;
-        const bool multi = (M & (M - 1)) != 0;
-        // two distinct candidates at one site (inside or outside the grid), or a
-        // frontier site whose single candidate is contradicted
-        nd = nd || (!in && multi) || (empty && (isf ? (M & ~(1u << tq)) != 0 : multi));
-        // one candidate outside the grid: growth past the cap
-        unb = unb || (!in && M != 0 && !multi);
-        if (empty && !isf && M != 0 && !multi) {
-            const int tn = __ffs(M) - 1;
-            // replicate 0 must hold the same tuple here, or this replicate can
-            // no longer end in replicate 0's configuration
-            if (Ls.rep > 0 && !Ls.diverged && (!(my[(G::OCCA + qw) * 32] & qbit) || tq != tn)) Ls.diverged = 1;
-            my[(G::NIB + (qb >> 3)) * 32] = (nw & ~(15u << sh)) | ((uint32_t)tn << sh);
-            my[(G::FRONT + qw) * 32] = fw | qbit;
-            Ls.nF += 1;
-        }
-    }
-    if (!(nd || unb || Ls.nF == 0)) return;
-    // the replicate is decided; apply the first-deciding-replicate rule
     if (nd) {
         Ls.cls = JATAM_ND_LOCAL;
         Ls.decided = Ls.rep;
@@ -473,6 +367,132 @@ __device__ __forceinline__ void lane_step(Lane &Ls, uint32_t *my, uint32_t k0, u
         Ls.rep += 1;
         Ls.phase = PH_START;
     }
+}
+
+// ---------------------------------------------------------------------------
+// one growth step of one lane: seed placement or one drawn placement, then the
+// evaluation of the new tile's empty neighbours and the replicate rule
+// ---------------------------------------------------------------------------
+template <int S>
+__device__ __forceinline__ void lane_step(Lane &Ls, uint32_t *my, uint32_t k0, uint32_t k1, unsigned *err)
+{
+    // Called by all 32 lanes; lanes that are not growing do the arithmetic on
+    // harmless addresses of their own region and write nothing.  __syncwarp()
+    // brings the warp back together after each data-dependent part.
+    using G = Geo<S>;
+    const bool active = Ls.phase == PH_START || Ls.phase == PH_GROW;
+    const bool seed = Ls.phase == PH_START;
+    const int occ = (Ls.rep == 0) ? G::OCCA : G::OCCB;
+    int b = 0, tau = 0;
+    bool placing = active;
+    if (active && !seed) {
+        const uint32_t key = (uint32_t)Ls.rep * 512u + ((uint32_t)Ls.step >> 2);
+        if (Ls.ka != key) {
+            if (Ls.kb == key) {
+                Ls.pa = Ls.pb;
+                Ls.kb = NO_BLOCK;
+            } else {
+                Ls.pa = philox_block(key, Ls.sid, k0, k1);
+            }
+            Ls.ka = key;
+        }
+        if (Ls.nF > 1) Ls.forced = 0;
+        const int sel = Ls.step & 3;
+        const uint32_t u = sel == 0 ? Ls.pa.x : sel == 1 ? Ls.pa.y : sel == 2 ? Ls.pa.z : Ls.pa.w;
+        uint32_t i = __umulhi(u, (uint32_t)Ls.nF);
+        int w = (max(Ls.ymin - 1, 0) * S) >> 5;
+        uint32_t f = my[(G::FRONT + w) * 32];
+        uint32_t cnt = __popc(f);
+        while (i >= cnt) {
+            i -= cnt;
+            if (++w >= G::NW) break;
+            f = my[(G::FRONT + w) * 32];
+            cnt = __popc(f);
+        }
+        if (w >= G::NW) {
+            atomicOr(err, ERR_GUARD);
+            Ls.cls = 255;
+            Ls.phase = PH_WRITE;
+            placing = false;
+        } else {
+            const int bit = nth_set(f, i);
+            b = w * 32 + bit;
+            tau = nib_get<S>(my, b);
+            my[(G::FRONT + w) * 32] = f & ~(1u << bit);
+            Ls.nF -= 1;
+            Ls.step += 1;
+        }
+    }
+    if (seed) {
+        // a new replicate: the seed, tile 0 in orientation 0, at the centre
+        b = (Ls.L >> 1) * S + (Ls.L >> 1);
+        tau = 0;
+        Ls.size = 0;
+        Ls.step = 0;
+        Ls.nF = 0;
+        Ls.diverged = 0;
+        Ls.forced = 1;
+        Ls.phase = PH_GROW;
+    }
+    __syncwarp();
+    const int px = b & (S - 1), py = b >> G::LOG2S;
+    if (placing) {
+        my[(occ + (b >> 5)) * 32] |= 1u << (b & 31);
+        if (seed && Ls.rep == 0) nib_set<S>(my, b, 0);
+        Ls.size += 1;
+        Ls.ymin = seed ? py : min(Ls.ymin, py);
+        Ls.ymax = seed ? py : max(Ls.ymax, py);
+        Ls.xmin = seed ? px : min(Ls.xmin, px);
+        Ls.xmax = seed ? px : max(Ls.xmax, px);
+        Ls.dlo = min(Ls.dlo, py - 1);
+        Ls.dhi = max(Ls.dhi, py + 1);
+        if (Ls.rep > 0) {
+            Ls.blo = min(Ls.blo, py);
+            Ls.bhi = max(Ls.bhi, py);
+        }
+    }
+
+    // the empty neighbours of the new tile: only their candidate sets changed.
+    // Straight-line code: every lane evaluates all four sides, whatever their
+    // case, so the warp stays converged.
+    const uint32_t m01 = my[(G::NBM + 2 * tau) * 32];
+    const uint32_t m23 = my[(G::NBM + 2 * tau + 1) * 32];
+    bool nd = false, unb = false;
+#pragma unroll
+    for (int d = 0; d < 4; ++d) {
+        const uint32_t M = ((d == 0) ? m01 : (d == 1) ? (m01 >> 16) : (d == 2) ? m23 : (m23 >> 16)) & 0xFFFFu;
+        const int qx = px + (d == 1) - (d == 3);
+        const int qy = py + (d == 2) - (d == 0);
+        const bool in = (unsigned)qx < (unsigned)Ls.L && (unsigned)qy < (unsigned)Ls.L;
+        const int qb = in ? qy * S + qx : b;  // outside the grid: read the new tile's own cell, write nothing
+        const int qw = qb >> 5;
+        const uint32_t qbit = 1u << (qb & 31);
+        const int sh = (qb & 7) * 4;
+        const uint32_t ow = my[(occ + qw) * 32];
+        const uint32_t fw = my[(G::FRONT + qw) * 32];
+        const uint32_t nw = my[(G::NIB + (qb >> 3)) * 32];
+        const int tq = (nw >> sh) & 15;
+        const bool empty = in && !(ow & qbit);
+        const bool isf = (fw & qbit) != 0;
+        const bool multi = (M & (M - 1)) != 0;
+        // two distinct candidates at one site (inside or outside the grid), or a
+        // frontier site whose single candidate is contradicted
+        nd = nd || (!in && multi) || (empty && (isf ? (M & ~(1u << tq)) != 0 : multi));
+        // one candidate outside the grid: growth past the cap
+        unb = unb || (!in && M != 0 && !multi);
+        if (placing && empty && !isf && M != 0 && !multi) {
+            const int tn = __ffs(M) - 1;
+            // replicate 0 must hold the same tuple here, or this replicate can
+            // no longer end in replicate 0's configuration
+            if (Ls.rep > 0 && !Ls.diverged && (!(my[(G::OCCA + qw) * 32] & qbit) || tq != tn)) Ls.diverged = 1;
+            my[(G::NIB + (qb >> 3)) * 32] = (nw & ~(15u << sh)) | ((uint32_t)tn << sh);
+            my[(G::FRONT + qw) * 32] = fw | qbit;
+            Ls.nF += 1;
+        }
+    }
+    __syncwarp();
+    if (placing && (nd || unb || Ls.nF == 0)) replicate_end<S>(Ls, my, nd, unb);
+    __syncwarp();
 }
 
 __device__ __forceinline__ unsigned table_slot(unsigned long long key, unsigned log2cap)
@@ -844,7 +864,7 @@ __global__ void __launch_bounds__(256) classify_kernel(const LaunchArgs a)
                     }
                 }
             }
-            if (Ls.phase == PH_START || Ls.phase == PH_GROW) lane_step<S>(Ls, my, a.key0, a.key1, a.err);
+            lane_step<S>(Ls, my, a.key0, a.key1, a.err);
             const unsigned busy = __ballot_sync(FULL, Ls.phase == PH_START || Ls.phase == PH_GROW);
             if (!busy) break;
             const unsigned fin = __ballot_sync(FULL, Ls.phase == PH_SHAPE || Ls.phase == PH_WRITE);
