@@ -182,7 +182,7 @@ int jatam_autotune(const jatam_config *shapes, uint32_t n_shapes, void *stream);
  * jatam_set_tuning / jatam_get_tuning -- set or read the launch shape used for
  * cfg's key: warps_per_cta 1..8, stop_at 1..32 (lanes that must have finished
  * their genotype before a warp leaves a growth round).  A key never tuned or
- * set uses the defaults (8 warps, 16).
+ * set uses the defaults (8 warps, 8).
  */
 int jatam_set_tuning(const jatam_config *cfg, int warps_per_cta, int stop_at);
 int jatam_get_tuning(const jatam_config *cfg, int *warps_per_cta, int *stop_at);

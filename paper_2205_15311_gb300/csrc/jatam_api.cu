@@ -25,7 +25,7 @@ int g_warps_override = 0;
 
 struct Tuning {
     int warps = 8;
-    int stop_at = 16;
+    int stop_at = 8;
 };
 // launch shape per key (lattice template, n, c); n = c = 0 for mixed batches
 std::map<std::tuple<int, int, int>, Tuning> g_tuned;

@@ -155,40 +155,50 @@ __device__ __forceinline__ void clear_rows(uint32_t *my, int base, int lo, int h
 }
 
 // ---------------------------------------------------------------------------
-// warp-cooperative binding tables for owner lane o (all 32 lanes take part)
+// warp-cooperative binding tables: each group of GL lanes (GL = 8 for at most
+// two tiles, 16 for up to four) builds the tables of one new genotype, so one
+// pass serves 32 / GL genotypes.  Lane l of a group handles (tile, rotation)
+// = (l / 4, l % 4).  The owners served are removed from `pending`.
 // ---------------------------------------------------------------------------
-template <int S>
-__device__ __forceinline__ void coop_tables(int o, uint32_t *warp_lanes, const Lane &Ls, int lane)
+template <int S, int GL>
+__device__ __forceinline__ void coop_tables(unsigned &pending, uint32_t *warp_lanes, const Lane &Ls, int lane)
 {
     using G = Geo<S>;
-    const uint32_t clo = __shfl_sync(FULL, (uint32_t)Ls.cols, o);
-    const uint32_t chi = __shfl_sync(FULL, (uint32_t)(Ls.cols >> 32), o);
-    const int n = __shfl_sync(FULL, Ls.n, o);
-    const int c = __shfl_sync(FULL, Ls.c, o);
-    const unsigned long long cols = ((unsigned long long)chi << 32) | clo;
-    const int t = lane >> 2, r = lane & 3;
-    const bool valid = lane < 16 && t < n;
-    int s[4];
+    constexpr int NG = 32 / GL;
+    const int g = lane / GL, l = lane % GL;
+    const int o = (g < __popc(pending)) ? nth_set(pending, (uint32_t)g) : -1;
 #pragma unroll
-    for (int d = 0; d < 4; ++d) {
-        // clockwise rotation by r: the edge (d - r) mod 4 now faces direction d
-        s[d] = valid ? (int)((cols >> (4 * (4 * t + ((d - r) & 3)))) & 15u) : 0;
-    }
-    const uint32_t tup = valid ? (uint32_t)(s[0] | (s[1] << 4) | (s[2] << 8) | (s[3] << 12)) : (0x10000u | lane);
-    const uint32_t same = __match_any_sync(FULL, tup);
+    for (int q = 0; q < NG; ++q) pending &= pending - 1;
+    const int src = (o < 0) ? lane : o;
+    const uint32_t clo = __shfl_sync(FULL, (uint32_t)Ls.cols, src);
+    const uint32_t chi = __shfl_sync(FULL, (uint32_t)(Ls.cols >> 32), src);
+    const int n = __shfl_sync(FULL, Ls.n, src);
+    const int c = __shfl_sync(FULL, Ls.c, src);
+    const int t = l >> 2, r = l & 3;
+    const bool valid = o >= 0 && t < n;
+    // tile t as 16 bits (nibble e = colour of edge e); a clockwise turn by r
+    // moves the colour of edge (d - r) mod 4 to side d: a 4r-bit rotation
+    const uint32_t tile = ((t < 2 ? clo : chi) >> (16 * (t & 1))) & 0xFFFFu;
+    const uint32_t rot = ((tile << (4 * r)) | (tile >> ((16 - 4 * r) & 15))) & 0xFFFFu;
+    const uint32_t rotv = (r == 0) ? tile : rot;
+    const uint32_t tag = valid ? (rotv | ((uint32_t)g << 16)) : (0x100000u | (uint32_t)lane);
+    const uint32_t same = __match_any_sync(FULL, tag);
     const bool is_rep = valid && (__ffs(same) - 1 == lane);
-    const uint32_t reps = __ballot_sync(FULL, is_rep);
+    const int shift = g * GL;
+    const uint32_t gmask = (GL == 32) ? FULL : ((1u << GL) - 1u);
+    const uint32_t reps = (__ballot_sync(FULL, is_rep) >> shift) & gmask;
     // bit-sliced colour planes: sl[e][b] = reps whose side e has bit b set
     uint32_t sl[4][3];
 #pragma unroll
     for (int e = 0; e < 4; ++e)
 #pragma unroll
-        for (int b = 0; b < 3; ++b) sl[e][b] = __ballot_sync(FULL, is_rep && ((s[e] >> b) & 1));
+        for (int b = 0; b < 3; ++b)
+            sl[e][b] = (__ballot_sync(FULL, is_rep && ((rotv >> (4 * e + b)) & 1)) >> shift) & gmask;
     if (is_rep) {
         uint32_t M[4];
 #pragma unroll
         for (int d = 0; d < 4; ++d) {
-            const int a = s[d];
+            const int a = (rotv >> (4 * d)) & 15;
             // the interaction matrix pairs 1-2, 3-4, 5-6; 0 and an odd top colour have no partner
             const int pa = (a == 0) ? -1 : (a & 1) ? ((a + 1 < c) ? a + 1 : -1) : a - 1;
             uint32_t m = 0;
@@ -200,8 +210,8 @@ __device__ __forceinline__ void coop_tables(int o, uint32_t *warp_lanes, const L
             M[d] = m & 0xFFFFu;
         }
         uint32_t *ob = warp_lanes + o;
-        ob[(G::NBM + 2 * lane) * 32] = M[0] | (M[1] << 16);
-        ob[(G::NBM + 2 * lane + 1) * 32] = M[2] | (M[3] << 16);
+        ob[(G::NBM + 2 * l) * 32] = M[0] | (M[1] << 16);
+        ob[(G::NBM + 2 * l + 1) * 32] = M[2] | (M[3] << 16);
     }
 }
 
@@ -805,10 +815,10 @@ __global__ void __launch_bounds__(256) classify_kernel(const LaunchArgs a)
         }
         // ---- binding tables of the genotypes that grow, one warp-wide job each
         unsigned init = __ballot_sync(FULL, Ls.phase == PH_INIT);
-        while (init) {
-            const int o = __ffs(init) - 1;
-            init &= init - 1;
-            coop_tables<S>(o, warp_lanes, Ls, lane);
+        if (a.n <= 2 && !(a.mode == MODE_RECORDS && a.shapes)) {
+            while (init) coop_tables<S, 8>(init, warp_lanes, Ls, lane);
+        } else {
+            while (init) coop_tables<S, 16>(init, warp_lanes, Ls, lane);
         }
         __syncwarp();
         if (Ls.phase == PH_INIT) {

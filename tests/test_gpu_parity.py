@@ -245,4 +245,4 @@ def test_results_do_not_depend_on_the_launch_shape():
         res, _, _ = _dev_enumerate(n, c, L, k, seed, first, count)
         assert np.array_equal(res, base)
     finally:
-        J.set_tuning(n, c, L, 8, 16)
+        J.set_tuning(n, c, L, 8, 8)
