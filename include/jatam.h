@@ -196,6 +196,33 @@ int jatam_get_tuning(const jatam_config *cfg, int *warps_per_cta, int *stop_at);
 int jatam_profile(int enable);
 int jatam_kernel_ms(float *ms);
 
+/*
+ * jatam_enumerate_noalloc -- jatam_enumerate without any device allocation,
+ * for callers that cannot allocate: code whose application owns every byte of
+ * device memory through its own pool, code that runs where a cudaMalloc (or
+ * the device-wide synchronisation a cudaFree implies) is not allowed, or code
+ * that must not let a library grow a hidden workspace.  The paper has no
+ * counterpart: it is an integration variant of the same classification.
+ *   Its scratch (three counters and the list of genotypes left to grow after
+ *   the seed-step pre-filter) lives in one fixed array of device memory that
+ *   is part of the library (8 B per genotype for JATAM_NOALLOC_MAX_COUNT
+ *   genotypes, about 8 MB); every GPU that loads the library holds it until
+ *   the process exits.
+ *   cfg   : as for jatam_enumerate (JATAM_SAMPLED honoured; with JATAM_SYNC the
+ *           call waits for the stream and reports device-side errors).
+ *   first, count : index range, count <= JATAM_NOALLOC_MAX_COUNT, else
+ *           JATAM_EINVAL with a message naming the limit.
+ *   out   : [count] results in DEVICE memory (required; host memory is
+ *           rejected, as staging it would need an allocation).  No histogram.
+ *   stream: cudaStream_t or NULL.
+ * The first call on each device looks up the scratch array's device address
+ * and sets the kernel's launch limits; make that first call before any stream
+ * capture.  All calls share the one array and start by clearing its counters:
+ * calls whose work overlaps on the GPU (unordered streams) race on it.
+ */
+#define JATAM_NOALLOC_MAX_COUNT 1048576u
+int jatam_enumerate_noalloc(const jatam_config *cfg, uint64_t first, uint64_t count, jatam_result *out, void *stream);
+
 /* Free every device workspace of the library (waits for queued work). */
 void jatam_shutdown(void);
 

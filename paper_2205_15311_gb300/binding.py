@@ -26,6 +26,7 @@ JATAM_EUNSUPPORTED = -5
 DET_BOUNDED, ND_LOCAL, ND_STERIC, UNBOUNDED = 0, 1, 2, 3
 JATAM_SAMPLED = 0x1
 JATAM_SYNC = 0x2
+JATAM_NOALLOC_MAX_COUNT = 1048576
 
 RESULT_DTYPE = np.dtype([("cls", "u1"), ("decided_rep", "u1"), ("size", "<u2"), ("shape_hash", "<u4")])
 HIST_DTYPE = np.dtype([("cls", "<u4"), ("shape_hash", "<u4"), ("size", "<u4"), ("flags", "<u4"),
@@ -64,6 +65,8 @@ def lib():
         L.jatam_hist_merge.argtypes = [_VP, _U32, _VP, _U32, _VP, _U32, _VP]
         for f in ("jatam_enumerate", "jatam_classify_batch", "ga_evaluate", "jatam_philox", "jatam_hist_merge"):
             getattr(L, f).restype = ctypes.c_int
+        L.jatam_enumerate_noalloc.argtypes = [_VP, _U64, _U64, _VP, _VP]
+        L.jatam_enumerate_noalloc.restype = ctypes.c_int
         L.jatam_autotune.argtypes = [_VP, _U32, _VP]
         L.jatam_autotune.restype = ctypes.c_int
         L.jatam_set_tuning.argtypes = [_VP, ctypes.c_int, ctypes.c_int]
@@ -103,6 +106,10 @@ def jatam_philox(inp, N, out, stream):
 
 def jatam_hist_merge(a, na, b, nb, out, cap, length):
     return lib().jatam_hist_merge(a, na, b, nb, out, cap, length)
+
+
+def jatam_enumerate_noalloc(cfg, first, count, out, stream):
+    return lib().jatam_enumerate_noalloc(cfg, first, count, out, stream)
 
 
 def jatam_autotune(shapes, n_shapes, stream):
@@ -171,6 +178,12 @@ def enumerate_space(n, c, L, k, seed, first, count, *, sampled=False, out=None, 
     cfg = make_config(n, c, L, k, seed, (JATAM_SAMPLED if sampled else 0) | (JATAM_SYNC if sync else 0))
     return check(jatam_enumerate(ctypes.addressof(cfg), first, count, _addr(out), _addr(hist), hist_cap,
                                  _addr(hist_len), _stream_handle(stream)))
+
+
+def enumerate_noalloc(n, c, L, k, seed, first, count, out, *, sampled=False, stream=None, sync=False):
+    """jatam_enumerate_noalloc into a device buffer `out` (no library allocation)."""
+    cfg = make_config(n, c, L, k, seed, (JATAM_SAMPLED if sampled else 0) | (JATAM_SYNC if sync else 0))
+    return check(jatam_enumerate_noalloc(ctypes.addressof(cfg), first, count, _addr(out), _stream_handle(stream)))
 
 
 def classify_batch(colours, *, n=0, c=0, L=0, k=0, seed=0, shapes=None, stream_ids=None, out=None, hist=None,

@@ -355,6 +355,8 @@ int stage_input(Workspace *w, const void *p, size_t bytes, void **stage, size_t 
 
 }  // namespace
 
+void jatam::set_last_error(const char *msg) { g_last_error = msg; }
+
 extern "C" {
 
 int jatam_enumerate(const jatam_config *cfg, uint64_t first, uint64_t count, jatam_result *out,

@@ -81,4 +81,7 @@ cudaError_t launch_hist_emit(Compact c, const unsigned *nkeys, jatam_hist_entry 
                              uint32_t *hist_len, int blocks, cudaStream_t st);
 cudaError_t launch_philox(const uint32_t *in, unsigned long long n, uint32_t *out, cudaStream_t st);
 
+// the message returned by jatam_last_error() for the calling thread
+void set_last_error(const char *msg);
+
 }  // namespace jatam

@@ -1,0 +1,174 @@
+// jatam_noalloc.cu -- jatam_enumerate_noalloc: classification of an index
+// range without any device allocation by the library.
+//
+// Who needs this: code that runs where cudaMalloc is not an option -- for
+// example a host callback or a library that must not touch the CUDA allocator
+// because the application owns all device memory through its own pool, or
+// code that must not trigger the implicit device synchronisation cudaFree
+// performs.  jatam_enumerate allocates a per-device workspace on first use and
+// grows it for larger calls; this entry point instead keeps its scratch in
+// one fixed array in device memory that is part of the loaded library.
+//
+// The scratch array below (NOALLOC_BYTES) is reserved on every GPU where the
+// library's module is loaded, for as long as the process lives.  It holds
+// three counters and the list of genotypes left to grow after the seed-step
+// pre-filter, so a call may classify at most JATAM_NOALLOC_MAX_COUNT
+// genotypes.  Every call reuses the same array: two calls that overlap on the
+// GPU (different streams, no ordering between them) race on it and give
+// wrong results.
+#include <cstdint>
+#include <mutex>
+
+#include <cuda_runtime.h>
+
+#include "jatam_internal.cuh"
+
+using namespace jatam;
+
+namespace {
+
+constexpr size_t NOALLOC_HEADER = 256;  // work counter, list length, error word
+constexpr size_t NOALLOC_BYTES = NOALLOC_HEADER + (size_t)JATAM_NOALLOC_MAX_COUNT * 8;
+
+// The scratch itself.  Host code must not use this name as an address: on the
+// host it is only a stand-in, so the device address is looked up once per
+// device with cudaGetSymbolAddress.
+static __device__ __align__(256) unsigned char g_noalloc_scratch[NOALLOC_BYTES];
+
+constexpr int MAX_DEVICES = 64;
+struct DeviceState {
+    bool ready = false;
+    unsigned char *scratch = nullptr;  // device address of g_noalloc_scratch on this device
+    int num_sms = 0;
+    int smem_set[3] = {0, 0, 0};
+};
+DeviceState g_dev[MAX_DEVICES];
+std::mutex g_noalloc_mutex;
+
+int noalloc_fail(int code, const char *msg)
+{
+    jatam::set_last_error(msg);  // read back with jatam_last_error()
+    return code;
+}
+
+int lattice_template_of(int L) { return L <= 8 ? 8 : L <= 16 ? 16 : 32; }
+int colour_bits(int c) { return c >= 8 ? 3 : c >= 4 ? 2 : c >= 2 ? 1 : 0; }
+
+// set-up of the calling thread's current device: the scratch address and the
+// launch limits of the classification kernel
+int device_setup(DeviceState **out)
+{
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return noalloc_fail(JATAM_ECUDA, "cudaGetDevice failed");
+    if (dev < 0 || dev >= MAX_DEVICES) return noalloc_fail(JATAM_EUNSUPPORTED, "device ordinal out of range");
+    DeviceState &d = g_dev[dev];
+    if (!d.ready) {
+        void *p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess || p == nullptr) {
+            cudaGetLastError();
+            return noalloc_fail(JATAM_ECUDA, "cudaGetSymbolAddress of the scratch array failed");
+        }
+        if (cudaDeviceGetAttribute(&d.num_sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+            return noalloc_fail(JATAM_ECUDA, "cudaDeviceGetAttribute failed");
+        d.scratch = static_cast<unsigned char *>(p);
+        d.ready = true;
+    }
+    *out = &d;
+    return JATAM_OK;
+}
+
+}  // namespace
+
+extern "C" int jatam_enumerate_noalloc(const jatam_config *cfg, uint64_t first, uint64_t count, jatam_result *out,
+                                       void *stream)
+{
+    std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+    jatam::set_last_error("");
+    if (!cfg || !out) return noalloc_fail(JATAM_EINVAL, "cfg and out are required");
+    const int n = cfg->n, c = cfg->c, L = cfg->L, k = cfg->k;
+    if (n < 1 || n > JATAM_MAX_TILES || L < 1 || L > JATAM_MAX_GRID || k < 1 || k > JATAM_MAX_REPLICATES ||
+        !(c == 1 || c == 2 || c == 4 || c == 8))
+        return noalloc_fail(JATAM_EUNSUPPORTED, "n 1..4, c in {1, 2, 4, 8}, L 1..32, k 1..255");
+    if (count > JATAM_NOALLOC_MAX_COUNT)
+        return noalloc_fail(JATAM_EINVAL, "count exceeds JATAM_NOALLOC_MAX_COUNT (the fixed scratch holds "
+                                          "1,048,576 genotypes per call)");
+    const bool sampled = (cfg->flags & JATAM_SAMPLED) != 0;
+    const int bits = 4 * n * colour_bits(c);
+    if (!sampled) {
+        const uint64_t space = bits >= 64 ? ~0ull : (1ull << bits);
+        if (first > space || count > space - first) return noalloc_fail(JATAM_EINVAL, "index range exceeds the space");
+    }
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, out) != cudaSuccess ||
+        !(at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged)) {
+        cudaGetLastError();
+        return noalloc_fail(JATAM_EINVAL, "out must be device memory");
+    }
+    DeviceState *d = nullptr;
+    int rc = device_setup(&d);
+    if (rc) return rc;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+
+    unsigned char *base = d->scratch;
+    unsigned long long *work_next = reinterpret_cast<unsigned long long *>(base);
+    unsigned long long *list_count = reinterpret_cast<unsigned long long *>(base + 8);
+    unsigned *err = reinterpret_cast<unsigned *>(base + 16);
+    unsigned *nkeys = reinterpret_cast<unsigned *>(base + 20);
+    unsigned long long *list = reinterpret_cast<unsigned long long *>(base + NOALLOC_HEADER);
+
+    LaunchArgs a{};
+    a.mode = sampled ? MODE_SAMPLED : MODE_RANGE;
+    a.first = first;
+    a.count = count;
+    a.n = n; a.c = c; a.L = L; a.k = k;
+    a.key0 = (uint32_t)cfg->seed;
+    a.key1 = (uint32_t)(cfg->seed >> 32);
+    a.out = out;
+    a.fitness = nullptr;
+    a.use_hist = 0;
+    a.stop_at = 8;
+    a.list = list;
+    a.list_count = list_count;
+    a.work_next = work_next;
+    a.err = err;
+
+    const int S = lattice_template_of(L);
+    const int warps = (S == 32) ? 2 : 8;
+    const int si = S == 8 ? 0 : S == 16 ? 1 : 2;
+    const int bytes = classify_smem_bytes(S, warps);
+    if (bytes > d->smem_set[si]) {
+        if (classify_set_attributes(S, warps) != cudaSuccess) {
+            cudaGetLastError();
+            return noalloc_fail(JATAM_ECUDA, "cudaFuncSetAttribute failed");
+        }
+        d->smem_set[si] = bytes;
+    }
+    int per_sm = 0;
+    if (classify_occupancy(S, warps, &per_sm) != cudaSuccess || per_sm < 1) {
+        cudaGetLastError();
+        return noalloc_fail(JATAM_ECUDA, "classification kernel does not fit on an SM");
+    }
+    long long blocks = (long long)per_sm * d->num_sms;
+    const long long needed = (long long)((count + 32ull * warps - 1) / (32ull * warps));
+    if (needed < blocks) blocks = needed < 1 ? 1 : needed;
+
+    // the counters and the error word start at zero in every call
+    if (launch_reset(work_next, nkeys, list_count, st) != cudaSuccess) return noalloc_fail(JATAM_ECUDA, "launch failed");
+    if (cudaMemsetAsync(err, 0, 4, st) != cudaSuccess) return noalloc_fail(JATAM_ECUDA, "cudaMemsetAsync failed");
+    if (count) {
+        long long pblocks = (long long)((count + 255) / 256);
+        if (pblocks > 8LL * d->num_sms) pblocks = 8LL * d->num_sms;
+        if (launch_prefilter(a, S, (int)pblocks, st) != cudaSuccess) return noalloc_fail(JATAM_ECUDA, "launch failed");
+        if (launch_classify(a, S, (int)blocks, warps, st) != cudaSuccess)
+            return noalloc_fail(JATAM_ECUDA, "launch failed");
+    }
+    if (cfg->flags & JATAM_SYNC) {
+        unsigned h_err = 0;
+        if (cudaMemcpyAsync(&h_err, err, 4, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+            cudaStreamSynchronize(st) != cudaSuccess)
+            return noalloc_fail(JATAM_ECUDA, "synchronisation failed");
+        if (h_err) return noalloc_fail(JATAM_ETIMEOUT, "a bounded device loop found an inconsistent state");
+    }
+    return JATAM_OK;
+}
