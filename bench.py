@@ -117,6 +117,28 @@ def algorithmic_ops(res_cls, res_rep, res_size, k, placements):
             + OPS_PER_SHAPED_CELL * int(cells))
 
 
+def measured_traffic(kernel_file):
+    """DRAM bytes per launch of the dominant kernel from the committed ncu summary,
+    or None when the kernel source changed since those counters were taken."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", "classify_kernel_s28_full_traffic.md")
+    try:
+        text = open(path).read()
+        src = open(kernel_file, "rb").read()
+    except OSError:
+        return None
+    want = None
+    traffic = None
+    for line in text.splitlines():
+        if line.startswith("kernel_source_sha256_prefix:"):
+            want = line.split(":", 1)[1].strip()
+        if line.startswith("traffic_bytes_per_launch:"):
+            traffic = int(line.split(":", 1)[1].strip())
+    if want is None or traffic is None or hashlib.sha256(src).hexdigest()[: len(want)] != want:
+        return None
+    return traffic
+
+
 def cpu_sample_plan():
     """Stratified bounded sample of the workload for the oracle: 64 blocks of
     65,536 consecutive genotypes spread evenly over the space."""
@@ -178,7 +200,7 @@ def main():
     global WORKLOAD
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--workload", default="s28_full",
@@ -307,8 +329,11 @@ def main():
         if placements is not None:
             ops = algorithmic_ops(res["cls"], res["decided_rep"], res["size"], k, placements)
             achieved = ops / (kms / 1e3) / 1e12
+            traffic = measured_traffic(os.path.join(ROOT, "paper_2205_15311_gb300", "csrc", "jatam_kernels.cu"))
+            if WORKLOAD != "s28_full":
+                traffic = None
             roofline = {"bound": "alu", "achieved": round(achieved, 4), "peak": round(alu_peak, 2),
-                        "unit": "Tops/s", "frac": round(achieved / alu_peak, 4), "traffic": None,
+                        "unit": "Tops/s", "frac": round(achieved / alu_peak, 4), "traffic": traffic,
                         "kernel": f"classify_kernel<{8 if L <= 8 else 16 if L <= 16 else 32}>",
                         "kernel_ms": round(kms, 4),
                         "peak_source": f"{n_sms} SMs x 128 int32 lanes x {sm_max:.0f} MHz (MEASURED_PEAKS sm_max)",
