@@ -154,6 +154,68 @@ def WORKLOAD_SPEC():
     return W.WORKLOADS[WORKLOAD]
 
 
+MIXED_COUNT = 10_000_000
+
+
+def mixed_arm(args, torch, J, dev):
+    """Batched uneven workload: 10^7 explicit tile sets with n in {2,3,4},
+    c in {4,6,8}, L in {8,16,32}, k in {10,20} (seed 4) in one persistent,
+    graph-captured launch whose CTA plan the autotuner picks; the per-size
+    fixed launches are timed beside it."""
+    from paper_2205_15311_gb300 import workloads as W
+    colours, shapes = W.mixed_records(MIXED_COUNT, seed=4)
+    dc = torch.from_numpy(colours).to(dev)
+    ds = torch.from_numpy(shapes).to(dev)
+    out = torch.empty(MIXED_COUNT * 8, dtype=torch.uint8, device=dev)
+    hist_cap = 1 << 16
+    hist = torch.empty(hist_cap * 32, dtype=torch.uint8, device=dev)
+    hlen = torch.zeros(1, dtype=torch.int32, device=dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.Stream(device=dev)
+    J.autotune_batch(dc[: 1 << 20], ds[: 1 << 20], 4, stream=stream)
+    plan = J.get_mixed_plan()
+
+    def timed(per_shape, graph):
+        for _ in range(args.warmup):
+            J.classify_batch(dc, seed=4, shapes=ds, out=out, hist=hist, hist_len=hlen, hist_cap=hist_cap,
+                             stream=stream, per_shape=per_shape, graph=graph)
+        stream.synchronize()
+        st = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+        en = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+        kms = []
+        for i in range(args.steps):
+            with torch.cuda.stream(stream):
+                flush.fill_(i & 255)
+                st[i].record(stream)
+                J.classify_batch(dc, seed=4, shapes=ds, out=out, hist=hist, hist_len=hlen, hist_cap=hist_cap,
+                                 stream=stream, per_shape=per_shape, graph=graph)
+                en[i].record(stream)
+            kms.append(J.last_kernel_ms())
+        torch.cuda.synchronize()
+        return float(np.mean([a.elapsed_time(b) for a, b in zip(st, en)])), float(np.mean(kms))
+
+    J.jatam_profile(1)
+    with ClockSampler(int(str(dev).split(":")[-1]) if ":" in str(dev) else 0) as clocks:
+        ms, kms = timed(False, True)
+    ms_fixed, kms_fixed = timed(True, False)
+    line = {
+        "metric": METRIC, "value": MIXED_COUNT / (ms / 1e3), "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+        "config": {"workload": "mixed: 10^7 tile sets, n in {2,3,4}, c in {4,6,8}, L in {8,16,32}, k in {10,20}, "
+                               "seed 4", "launch": "one persistent launch, CUDA graph replay",
+                   "plan_w32_w16_w8": list(plan), "growth_kernels_ms": round(kms, 4),
+                   "per_shape_fixed_launches": {"ms_per_step": round(ms_fixed, 4),
+                                                "growth_kernels_ms": round(kms_fixed, 4),
+                                                "value": MIXED_COUNT / (ms_fixed / 1e3)},
+                   "distinct_phenotypes": int(hlen.item())},
+        "e2e": None, "gpu_launches": 5 * args.steps, "roofline": None, "cpu_baseline": None,
+        "clocks": clocks.summary(),
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def run_oracle_sample(nthreads):
     from oracle import oracle as O
     n, c, L, k, seed, _, _, _ = WORKLOAD_SPEC()
@@ -204,7 +266,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--workload", default="s28_full",
-                    help="s28_full (the bench line), or s24_full / s28_paper / s38_sample for measurements")
+                    help="s28_full (the bench line), or s24_full / s28_paper / s38_sample / mixed for measurements")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end leg")
     ap.add_argument("--profile-genomes", type=int, default=0,
@@ -232,6 +294,8 @@ def main():
     import __graft_entry__
     __graft_entry__.build()
     from paper_2205_15311_gb300 import binding as J
+    if WORKLOAD == "mixed":
+        return mixed_arm(args, torch, J, dev)
 
     n, c, L, k, seed0, first, count, sampled = WORKLOAD_SPEC()
     if args.profile_genomes:

@@ -64,6 +64,10 @@ extern "C" {
 /* ---- jatam_config.flags ---- */
 #define JATAM_SAMPLED 0x1u /* jatam_enumerate: index i names a uniformly sampled genotype (see below) */
 #define JATAM_SYNC 0x2u    /* wait for the work to finish before returning */
+#define JATAM_PER_SHAPE 0x4u /* jatam_classify_batch with mixed shapes: one fixed launch per lattice size
+                                class instead of the single persistent launch */
+#define JATAM_GRAPH 0x8u     /* capture the call's kernel sequence as a CUDA graph the first time a given
+                                set of arguments is seen, and replay it on later calls with the same set */
 
 /* Limits of the supported model sizes. */
 #define JATAM_MAX_TILES 4
@@ -129,6 +133,12 @@ int jatam_enumerate(const jatam_config *cfg, uint64_t first, uint64_t count, jat
  *   out, hist, hist_cap, hist_len, stream : as for jatam_enumerate.
  * Items with a colour >= c or parameters out of range get cls = 255 and the
  * call reports JATAM_EINVAL once the work has finished.
+ * Mixed shapes run as one persistent launch: the pre-filter sorts the items
+ * that grow into three lists by lattice size (L <= 8, <= 16, <= 32); warps
+ * with 32 x 32, 16 x 16 and 8 x 8 shared-memory regions (a per-CTA plan that
+ * jatam_autotune picks) work through their own list and then steal from the
+ * lists of smaller sizes.  With JATAM_PER_SHAPE the three lists run as three
+ * fixed launches instead.  Results are identical either way.
  */
 int jatam_classify_batch(const jatam_config *cfg, const uint8_t *colours, const uint8_t *shapes,
                          const uint64_t *stream_ids, uint64_t N, jatam_result *out, jatam_hist_entry *hist,
@@ -144,6 +154,67 @@ int jatam_classify_batch(const jatam_config *cfg, const uint8_t *colours, const 
  */
 int ga_evaluate(const jatam_config *cfg, const uint64_t *genomes, uint64_t N, int32_t *fitness,
                 jatam_result *out, void *stream);
+
+/* ---- genetic algorithm (Section 2.2; Section 3.2 for the Fujiyama test bed) ---- */
+#define JATAM_GA_TOURNAMENT 0
+#define JATAM_GA_ROULETTE 1
+#define JATAM_GA_NO_CROSSOVER 0
+#define JATAM_GA_ONE_POINT 1
+#define JATAM_GA_UNIFORM 2
+#define JATAM_GA_FITNESS_SHAPE 0   /* size of the deterministic bounded shape, else 0 (ga_evaluate) */
+#define JATAM_GA_FITNESS_HAMMING 1 /* number of set bits: the paper's Fujiyama landscape */
+
+typedef struct {
+    uint8_t n, c;                    /* genome space S_{n,c}, c a power of two: 4 n log2(c) bits */
+    uint8_t selection;               /* JATAM_GA_TOURNAMENT or JATAM_GA_ROULETTE (global roulette wheel) */
+    uint8_t tournament;              /* tournament size, 1..16 */
+    uint8_t crossover;               /* JATAM_GA_NO_CROSSOVER, JATAM_GA_ONE_POINT or JATAM_GA_UNIFORM */
+    uint8_t reserved[3];
+    uint32_t crossover_threshold;    /* a child is a crossover when its draw u < threshold (u uniform 32-bit) */
+    uint32_t mutation_thresholds[4]; /* mutation events on one edge = #{j : u >= t_j}, t non-decreasing */
+    uint64_t seed;                   /* Philox key */
+} jatam_ga_config;                   /* 40 bytes */
+
+/*
+ * ga_breed -- one generation: children[i] from parents and their fitness.
+ * Two parents are selected (tournament: the fittest of `tournament` uniform
+ * draws, the earliest on ties; roulette: the parent in whose slice of the
+ * cumulative non-negative fitness a uniform dart lands, uniform if all are 0),
+ * crossed over (one point: the bits above a uniform cut in 1..bits-1 from the
+ * first parent, the rest from the second; uniform: a random 64-bit mask picks
+ * each bit), and mutated: every edge undergoes a Poisson number of events
+ * (the thresholds), each flipping one uniformly chosen bit of the edge.  Word k
+ * of child i in generation g is word (k mod 4) of Philox4x32-10(ctr =
+ * (k >> 2, (2 << 24) | g, i_lo, i_hi), key = seed), in the order: selection
+ * words of parent A (T or 1), of parent B, crossover decision, two cut/mask
+ * words, one Poisson word per edge, four bit-choice words per edge.
+ * parents, fitness, children: [N], host or device; children may not alias
+ * parents.  Roulette needs the total fitness below 2^32.
+ */
+int ga_breed(const jatam_ga_config *ga, const uint64_t *parents, const int32_t *fitness, uint64_t N,
+             uint32_t generation, uint64_t *children, void *stream);
+
+/* ga_hamming -- fitness[i] = number of set bits of genomes[i] (Section 3.2). */
+int ga_hamming(const uint64_t *genomes, uint64_t N, int32_t *fitness, void *stream);
+
+/* ga_poisson_thresholds -- t_j = floor(2^32 P(K <= j)), j = 0..3, for
+ * K ~ Poisson(rate): the per-edge mutation thresholds for a mean of `rate`
+ * events per edge (host only). */
+int ga_poisson_thresholds(double rate, uint32_t thresholds[4]);
+
+/*
+ * ga_run -- `generations` generations of the genetic algorithm on the device:
+ * per generation the fitness (JATAM_GA_FITNESS_SHAPE: classification with
+ * cls->L, cls->k, cls->seed, as ga_evaluate; JATAM_GA_FITNESS_HAMMING: ga_hamming),
+ * its best value and total, then ga_breed with generation index g.
+ *   population : [N] device memory; in: generation 0, out: the last generation
+ *                (after `generations` breedings).
+ *   best, total: NULL or [generations] (host or device): the best fitness and
+ *                the sum of fitness of generation g's population.
+ * Synchronises `stream` when best/total are host memory.
+ */
+int ga_run(const jatam_ga_config *ga, const jatam_config *cls, int fitness_kind, uint64_t N, uint32_t generations,
+           uint64_t *population, int32_t *best, int64_t *total, void *stream);
 
 /*
  * jatam_philox -- Philox4x32-10 (Salmon et al., SC'11) as computed by the
@@ -186,6 +257,20 @@ int jatam_autotune(const jatam_config *shapes, uint32_t n_shapes, void *stream);
  */
 int jatam_set_tuning(const jatam_config *cfg, int warps_per_cta, int stop_at);
 int jatam_get_tuning(const jatam_config *cfg, int *warps_per_cta, int *stop_at);
+
+/*
+ * jatam_set_mixed_plan / jatam_get_mixed_plan -- the CTA plan of the
+ * persistent launch for mixed lattice sizes: warps with a 32 x 32, 16 x 16
+ * and 8 x 8 region per CTA (at least one 32 x 32 warp, since only those can
+ * run L > 16; at most 8 warps in total, shared memory permitting; default
+ * 2, 4, 2).
+ * jatam_autotune_batch -- time every candidate plan (and the per-size fixed
+ * launches' growth-round threshold) on the given mixed batch (colours[N][16],
+ * shapes[N][4], host or device) and keep the fastest plan.  Synchronises.
+ */
+int jatam_set_mixed_plan(int warps_32, int warps_16, int warps_8);
+int jatam_get_mixed_plan(int *warps_32, int *warps_16, int *warps_8);
+int jatam_autotune_batch(const uint8_t *colours, const uint8_t *shapes, uint64_t N, uint64_t seed, void *stream);
 
 /*
  * jatam_profile -- when enable != 0, every later call records CUDA events

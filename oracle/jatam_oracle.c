@@ -52,6 +52,7 @@
  *         as the bytes height, width, then x, y per occupied cell in
  *         row-major order.
  */
+#include <math.h>
 #include <pthread.h>
 #include <stdint.h>
 #include <stdlib.h>
@@ -600,3 +601,141 @@ int orc_classify_batch(const uint8_t *cols, const uint8_t *shapes, int n, int c,
     proto.out = out;
     return run_jobs(&proto, count, nthreads, placements);
 }
+
+/* ---------------------------------------------------------------------------
+ * Genetic algorithm (Section 2.2 "Genetic Algorithms"; appendix "Efficient
+ * bit-wise implementations of common evolutionary operators"): one generation
+ * turns a parent population with its fitness values into a child population.
+ *   selection  -- tournament (the best of T uniformly drawn parents, the
+ *                 earliest drawn on ties) or global roulette wheel (the parent
+ *                 in whose slice of the cumulative fitness a dart lands,
+ *                 Section 2.2; uniform when all fitness values are 0);
+ *   crossover  -- none, single point (the bits above a cut point from parent
+ *                 A, the rest from B) or uniform (each bit from A or B);
+ *   mutation   -- every edge (gene) undergoes a Poisson number of events with
+ *                 mean rate mu; each event flips one uniformly chosen bit of
+ *                 the edge's log2(c) bits (Section 2.2; appendix "Encoding
+ *                 genome information": flips of single bits).
+ * Draws: word k of child i in generation g is word (k mod 4) of
+ * Philox4x32-10(ctr = (k >> 2, (2 << 24) | g, i_lo, i_hi), key = seed), laid
+ * out as: tournament A (T words) or roulette dart A (1), tournament B / dart B,
+ * crossover decision, two mask/cut words, one Poisson word per edge, and
+ * four bit-choice words per edge.
+ * ------------------------------------------------------------------------- */
+typedef struct {
+    int n, c;
+    int selection;   /* 0 tournament, 1 roulette */
+    int tournament;  /* T */
+    int crossover;   /* 0 none, 1 single point, 2 uniform */
+    uint32_t crossover_threshold;
+    uint32_t mutation_thresholds[4];
+    uint64_t seed;
+} orc_ga;
+
+static uint32_t ga_word(const orc_ga *G, uint32_t generation, uint64_t child, int k)
+{
+    uint32_t ctr[4] = {(uint32_t)k >> 2, (2u << 24) | generation, (uint32_t)child, (uint32_t)(child >> 32)};
+    uint32_t key[2] = {(uint32_t)G->seed, (uint32_t)(G->seed >> 32)};
+    uint32_t w[4];
+    orc_philox4x32_10(ctr, key, w);
+    return w[k & 3];
+}
+
+/* The roulette wheel's cumulative search: the first index whose running sum
+ * of weights exceeds the dart (equivalently: reaches dart + 1). */
+uint64_t orc_roulette_pick(const uint64_t *cumsum, uint64_t N, uint64_t dart)
+{
+    for (uint64_t i = 0; i < N; i++)
+        if (cumsum[i] > dart) return i;
+    return N - 1;
+}
+
+/* index of the parent chosen by selection from words starting at k0 */
+static uint64_t ga_select(const orc_ga *G, const int32_t *fitness, const uint64_t *cumsum, uint64_t N,
+                          uint32_t generation, uint64_t child, int k0)
+{
+    if (G->selection == 0) {
+        uint64_t best = 0;
+        int have = 0;
+        for (int j = 0; j < G->tournament; j++) {
+            uint64_t idx = ((uint64_t)ga_word(G, generation, child, k0 + j) * N) >> 32;
+            if (!have || fitness[idx] > fitness[best]) {
+                best = idx;
+                have = 1;
+            }
+        }
+        return best;
+    }
+    uint64_t total = cumsum[N - 1];
+    uint32_t u = ga_word(G, generation, child, k0);
+    if (total == 0) return ((uint64_t)u * N) >> 32;
+    uint64_t dart = ((uint64_t)u * total) >> 32;  /* uniform in [0, total) */
+    return orc_roulette_pick(cumsum, N, dart);
+}
+
+int orc_ga_breed(const orc_ga *G, const uint64_t *parents, const int32_t *fitness, uint64_t N, uint32_t generation,
+                 uint64_t *children)
+{
+    int b = 0;
+    while ((1 << b) < G->c) b++;
+    const int bits = 4 * G->n * b;
+    const uint64_t all = bits >= 64 ? ~0ull : (((uint64_t)1 << bits) - 1);
+    const int T = G->selection == 0 ? G->tournament : 1;
+    if (N == 0) return 0;
+    uint64_t *cumsum = (uint64_t *)malloc(sizeof(uint64_t) * N);
+    if (!cumsum) return -2;
+    uint64_t run = 0;
+    for (uint64_t i = 0; i < N; i++) {
+        run += fitness[i] > 0 ? (uint64_t)fitness[i] : 0;
+        cumsum[i] = run;
+    }
+    const int k_cross = 2 * T, k_mask = 2 * T + 1, k_pois = 2 * T + 3, k_bit = 2 * T + 3 + 4 * G->n;
+    for (uint64_t i = 0; i < N; i++) {
+        uint64_t a = parents[ga_select(G, fitness, cumsum, N, generation, i, 0)];
+        uint64_t bb = parents[ga_select(G, fitness, cumsum, N, generation, i, T)];
+        uint64_t child = a;
+        if (G->crossover != 0 && ga_word(G, generation, i, k_cross) < G->crossover_threshold) {
+            if (G->crossover == 1) {
+                /* cut in 1 .. bits-1: the top bits - cut from A, the low cut bits from B */
+                int cut = 1 + (int)(((uint64_t)ga_word(G, generation, i, k_mask) * (uint64_t)(bits - 1)) >> 32);
+                uint64_t low = ((uint64_t)1 << cut) - 1;
+                child = (a & ~low) | (bb & low);
+            } else {
+                uint64_t mask = ((uint64_t)ga_word(G, generation, i, k_mask + 1) << 32) | ga_word(G, generation, i, k_mask);
+                child = (a & ~mask) | (bb & mask);
+            }
+        }
+        for (int e = 0; e < 4 * G->n && b > 0; e++) {
+            uint32_t u = ga_word(G, generation, i, k_pois + e);
+            int events = 0;
+            for (int j = 0; j < 4; j++)
+                if (u >= G->mutation_thresholds[j]) events++;
+            int t = e / 4, side = e % 4;
+            int pos = b * (4 * (G->n - 1 - t) + (3 - side));
+            for (int m = 0; m < events; m++) {
+                int bit = (int)(((uint64_t)ga_word(G, generation, i, k_bit + 4 * e + m) * (uint64_t)b) >> 32);
+                child ^= (uint64_t)1 << (pos + bit);
+            }
+        }
+        children[i] = child & all;
+    }
+    free(cumsum);
+    return 0;
+}
+
+/* floor(2^32 P(K <= j)) for K ~ Poisson(rate), j = 0..3, saturated at 2^32 - 1 */
+int orc_poisson_thresholds(double rate, uint32_t out[4])
+{
+    if (!(rate >= 0.0)) return -1;
+    double term = exp(-rate), cdf = 0.0;
+    for (int j = 0; j < 4; j++) {
+        cdf += term;
+        term *= rate / (double)(j + 1);
+        double t = floor(cdf * 4294967296.0);
+        out[j] = t >= 4294967295.0 ? 4294967295u : (uint32_t)t;
+    }
+    return 0;
+}
+
+/* Fujiyama test-bed fitness (Section 3.2): the Hamming weight of the genome */
+int orc_hamming(uint64_t g) { int h = 0; while (g) { h += (int)(g & 1); g >>= 1; } return h; }

@@ -37,6 +37,12 @@ class _Trace(ctypes.Structure):
                 ("x", ctypes.c_int32), ("y", ctypes.c_int32), ("tuple", ctypes.c_int32)]
 
 
+class _GA(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int), ("c", ctypes.c_int), ("selection", ctypes.c_int), ("tournament", ctypes.c_int),
+                ("crossover", ctypes.c_int), ("crossover_threshold", ctypes.c_uint32),
+                ("mutation_thresholds", ctypes.c_uint32 * 4), ("seed", ctypes.c_uint64)]
+
+
 _lib = None
 _lock = threading.Lock()
 
@@ -46,7 +52,7 @@ def build(force: bool = False) -> str:
     os.makedirs(BUILD_DIR, exist_ok=True)
     if force or not os.path.exists(LIB) or os.path.getmtime(LIB) < os.path.getmtime(SRC):
         tmp = LIB + f".tmp{os.getpid()}"
-        subprocess.check_call(["gcc", "-std=c11", "-O2", "-Wall", "-fPIC", "-shared", "-pthread", SRC, "-o", tmp])
+        subprocess.check_call(["gcc", "-std=c11", "-O2", "-Wall", "-fPIC", "-shared", "-pthread", SRC, "-o", tmp, "-lm"])
         os.replace(tmp, LIB)
     return LIB
 
@@ -87,6 +93,15 @@ def lib():
                                              ctypes.c_int, ctypes.c_int, ctypes.c_uint64, ctypes.c_void_p,
                                              ctypes.c_uint64, ctypes.c_void_p, ctypes.c_int, u64p]
             L.orc_classify_batch.restype = ctypes.c_int
+            L.orc_ga_breed.argtypes = [ctypes.POINTER(_GA), ctypes.c_void_p, ctypes.c_void_p, ctypes.c_uint64,
+                                       ctypes.c_uint32, ctypes.c_void_p]
+            L.orc_ga_breed.restype = ctypes.c_int
+            L.orc_poisson_thresholds.argtypes = [ctypes.c_double, u32p]
+            L.orc_poisson_thresholds.restype = ctypes.c_int
+            L.orc_roulette_pick.argtypes = [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_uint64]
+            L.orc_roulette_pick.restype = ctypes.c_uint64
+            L.orc_hamming.argtypes = [ctypes.c_uint64]
+            L.orc_hamming.restype = ctypes.c_int
             _lib = L
     return _lib
 
@@ -245,3 +260,47 @@ def size_collisions(results):
     pairs = np.unique(np.stack([key, res["size"].astype(np.uint64)], axis=1), axis=0)
     k, cnt = np.unique(pairs[:, 0], return_counts=True)
     return k[cnt > 1]
+
+
+# ---------------------------------------------------------------------------
+# genetic algorithm (Section 2.2; the paper's appendix on GA operators)
+# ---------------------------------------------------------------------------
+TOURNAMENT, ROULETTE = 0, 1
+NO_CROSSOVER, ONE_POINT, UNIFORM = 0, 1, 2
+
+
+def poisson_thresholds(rate: float):
+    """floor(2^32 P(K <= j)), j = 0..3, K ~ Poisson(rate)."""
+    out = (ctypes.c_uint32 * 4)()
+    if lib().orc_poisson_thresholds(float(rate), out) != 0:
+        raise ValueError("rate must be >= 0")
+    return [int(v) for v in out]
+
+
+def hamming(g: int) -> int:
+    """The paper's Fujiyama test-bed fitness: the number of set bits."""
+    return int(lib().orc_hamming(int(g)))
+
+
+def ga_breed(parents, fitness, generation, *, n, c, seed, selection=TOURNAMENT, tournament=4,
+             crossover=NO_CROSSOVER, crossover_threshold=0, mutation_thresholds=(0xFFFFFFFF,) * 4):
+    """One generation: children from parents and their fitness values."""
+    parents = np.ascontiguousarray(parents, dtype=np.uint64)
+    fitness = np.ascontiguousarray(fitness, dtype=np.int32)
+    N = parents.shape[0]
+    g = _GA(n=n, c=c, selection=selection, tournament=tournament, crossover=crossover,
+            crossover_threshold=crossover_threshold, seed=seed)
+    for j in range(4):
+        g.mutation_thresholds[j] = int(mutation_thresholds[j])
+    children = np.zeros(N, np.uint64)
+    rc = lib().orc_ga_breed(ctypes.byref(g), parents.ctypes.data, fitness.ctypes.data, N, int(generation),
+                            children.ctypes.data)
+    if rc != 0:
+        raise ValueError(f"oracle ga_breed failed (rc={rc})")
+    return children
+
+
+def roulette_pick(weights, dart):
+    """Index chosen by the cumulative search of the roulette wheel."""
+    cs = np.cumsum(np.asarray(weights, dtype=np.uint64)).astype(np.uint64)
+    return int(lib().orc_roulette_pick(cs.ctypes.data, cs.shape[0], int(dart)))

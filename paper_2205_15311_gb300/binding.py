@@ -26,6 +26,8 @@ JATAM_EUNSUPPORTED = -5
 DET_BOUNDED, ND_LOCAL, ND_STERIC, UNBOUNDED = 0, 1, 2, 3
 JATAM_SAMPLED = 0x1
 JATAM_SYNC = 0x2
+JATAM_PER_SHAPE = 0x4
+JATAM_GRAPH = 0x8
 JATAM_NOALLOC_MAX_COUNT = 1048576
 
 RESULT_DTYPE = np.dtype([("cls", "u1"), ("decided_rep", "u1"), ("size", "<u2"), ("shape_hash", "<u4")])
@@ -36,6 +38,18 @@ HIST_DTYPE = np.dtype([("cls", "<u4"), ("shape_hash", "<u4"), ("size", "<u4"), (
 class jatam_config(ctypes.Structure):
     _fields_ = [("n", ctypes.c_uint8), ("c", ctypes.c_uint8), ("L", ctypes.c_uint8), ("k", ctypes.c_uint8),
                 ("flags", ctypes.c_uint32), ("seed", ctypes.c_uint64)]
+
+
+class jatam_ga_config(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_uint8), ("c", ctypes.c_uint8), ("selection", ctypes.c_uint8),
+                ("tournament", ctypes.c_uint8), ("crossover", ctypes.c_uint8), ("reserved", ctypes.c_uint8 * 3),
+                ("crossover_threshold", ctypes.c_uint32), ("mutation_thresholds", ctypes.c_uint32 * 4),
+                ("seed", ctypes.c_uint64)]
+
+
+TOURNAMENT, ROULETTE = 0, 1
+NO_CROSSOVER, ONE_POINT, UNIFORM = 0, 1, 2
+FITNESS_SHAPE, FITNESS_HAMMING = 0, 1
 
 
 class JatamError(RuntimeError):
@@ -67,6 +81,20 @@ def lib():
             getattr(L, f).restype = ctypes.c_int
         L.jatam_enumerate_noalloc.argtypes = [_VP, _U64, _U64, _VP, _VP]
         L.jatam_enumerate_noalloc.restype = ctypes.c_int
+        L.ga_breed.argtypes = [_VP, _VP, _VP, _U64, _U32, _VP, _VP]
+        L.ga_breed.restype = ctypes.c_int
+        L.ga_hamming.argtypes = [_VP, _U64, _VP, _VP]
+        L.ga_hamming.restype = ctypes.c_int
+        L.ga_poisson_thresholds.argtypes = [ctypes.c_double, ctypes.POINTER(ctypes.c_uint32)]
+        L.ga_poisson_thresholds.restype = ctypes.c_int
+        L.ga_run.argtypes = [_VP, _VP, ctypes.c_int, _U64, _U32, _VP, _VP, _VP, _VP]
+        L.ga_run.restype = ctypes.c_int
+        L.jatam_set_mixed_plan.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int]
+        L.jatam_set_mixed_plan.restype = ctypes.c_int
+        L.jatam_get_mixed_plan.argtypes = [ctypes.POINTER(ctypes.c_int)] * 3
+        L.jatam_get_mixed_plan.restype = ctypes.c_int
+        L.jatam_autotune_batch.argtypes = [_VP, _VP, _U64, _U64, _VP]
+        L.jatam_autotune_batch.restype = ctypes.c_int
         L.jatam_autotune.argtypes = [_VP, _U32, _VP]
         L.jatam_autotune.restype = ctypes.c_int
         L.jatam_set_tuning.argtypes = [_VP, ctypes.c_int, ctypes.c_int]
@@ -110,6 +138,34 @@ def jatam_hist_merge(a, na, b, nb, out, cap, length):
 
 def jatam_enumerate_noalloc(cfg, first, count, out, stream):
     return lib().jatam_enumerate_noalloc(cfg, first, count, out, stream)
+
+
+def ga_breed(ga, parents, fitness, N, generation, children, stream):
+    return lib().ga_breed(ga, parents, fitness, N, generation, children, stream)
+
+
+def ga_hamming(genomes, N, fitness, stream):
+    return lib().ga_hamming(genomes, N, fitness, stream)
+
+
+def ga_poisson_thresholds(rate, thresholds):
+    return lib().ga_poisson_thresholds(rate, thresholds)
+
+
+def ga_run(ga, cls, fitness_kind, N, generations, population, best, total, stream):
+    return lib().ga_run(ga, cls, fitness_kind, N, generations, population, best, total, stream)
+
+
+def jatam_set_mixed_plan(w32, w16, w8):
+    return lib().jatam_set_mixed_plan(w32, w16, w8)
+
+
+def jatam_get_mixed_plan(w32, w16, w8):
+    return lib().jatam_get_mixed_plan(w32, w16, w8)
+
+
+def jatam_autotune_batch(colours, shapes, N, seed, stream):
+    return lib().jatam_autotune_batch(colours, shapes, N, seed, stream)
 
 
 def jatam_autotune(shapes, n_shapes, stream):
@@ -173,9 +229,10 @@ def check(rc):
 
 
 def enumerate_space(n, c, L, k, seed, first, count, *, sampled=False, out=None, hist=None, hist_len=None,
-                    hist_cap=0, stream=None, sync=False):
+                    hist_cap=0, stream=None, sync=False, graph=False):
     """jatam_enumerate on caller buffers (torch tensors or numpy arrays)."""
-    cfg = make_config(n, c, L, k, seed, (JATAM_SAMPLED if sampled else 0) | (JATAM_SYNC if sync else 0))
+    cfg = make_config(n, c, L, k, seed, (JATAM_SAMPLED if sampled else 0) | (JATAM_SYNC if sync else 0)
+                      | (JATAM_GRAPH if graph else 0))
     return check(jatam_enumerate(ctypes.addressof(cfg), first, count, _addr(out), _addr(hist), hist_cap,
                                  _addr(hist_len), _stream_handle(stream)))
 
@@ -187,15 +244,16 @@ def enumerate_noalloc(n, c, L, k, seed, first, count, out, *, sampled=False, str
 
 
 def classify_batch(colours, *, n=0, c=0, L=0, k=0, seed=0, shapes=None, stream_ids=None, out=None, hist=None,
-                   hist_len=None, hist_cap=0, stream=None, sync=False):
+                   hist_len=None, hist_cap=0, stream=None, sync=False, per_shape=False, graph=False):
     N = int(colours.shape[0])
-    cfg = make_config(n, c, L, k, seed, JATAM_SYNC if sync else 0)
+    cfg = make_config(n, c, L, k, seed, (JATAM_SYNC if sync else 0) | (JATAM_PER_SHAPE if per_shape else 0)
+                      | (JATAM_GRAPH if graph else 0))
     return check(jatam_classify_batch(ctypes.addressof(cfg), _addr(colours), _addr(shapes), _addr(stream_ids), N,
                                       _addr(out), _addr(hist), hist_cap, _addr(hist_len), _stream_handle(stream)))
 
 
-def evaluate_genomes(genomes, fitness, *, n, c, L, k, seed, out=None, stream=None, sync=False):
-    cfg = make_config(n, c, L, k, seed, JATAM_SYNC if sync else 0)
+def evaluate_genomes(genomes, fitness, *, n, c, L, k, seed, out=None, stream=None, sync=False, graph=False):
+    cfg = make_config(n, c, L, k, seed, (JATAM_SYNC if sync else 0) | (JATAM_GRAPH if graph else 0))
     N = int(genomes.shape[0])
     return check(ga_evaluate(ctypes.addressof(cfg), _addr(genomes), N, _addr(fitness), _addr(out),
                              _stream_handle(stream)))
@@ -213,6 +271,21 @@ def autotune(configs, stream=None):
     for i, d in enumerate(configs):
         arr[i] = make_config(d["n"], d["c"], d["L"], d["k"], d.get("seed", 0), JATAM_SAMPLED if d.get("sampled") else 0)
     return check(jatam_autotune(ctypes.addressof(arr), len(configs), _stream_handle(stream)))
+
+
+def set_mixed_plan(w32, w16, w8):
+    return check(jatam_set_mixed_plan(w32, w16, w8))
+
+
+def get_mixed_plan():
+    v = [ctypes.c_int(0) for _ in range(3)]
+    check(jatam_get_mixed_plan(*[ctypes.byref(x) for x in v]))
+    return tuple(x.value for x in v)
+
+
+def autotune_batch(colours, shapes, seed, stream=None):
+    N = int(colours.shape[0])
+    return check(jatam_autotune_batch(_addr(colours), _addr(shapes), N, seed, _stream_handle(stream)))
 
 
 def set_tuning(n, c, L, warps_per_cta, stop_at):
@@ -258,3 +331,38 @@ def hist_view(t, length=None):
         t = t.cpu().numpy()
     h = np.ascontiguousarray(t).view(np.uint8).reshape(-1).view(HIST_DTYPE)
     return h if length is None else h[:length]
+
+
+# ---------------------------------------------------------------------------
+# genetic algorithm helpers
+# ---------------------------------------------------------------------------
+def poisson_thresholds(rate):
+    t = (ctypes.c_uint32 * 4)()
+    check(ga_poisson_thresholds(float(rate), t))
+    return [int(v) for v in t]
+
+
+def make_ga(n, c, seed, *, selection=TOURNAMENT, tournament=4, crossover=NO_CROSSOVER, crossover_threshold=0,
+            mutation_thresholds=(0xFFFFFFFF,) * 4):
+    g = jatam_ga_config(n=n, c=c, selection=selection, tournament=tournament, crossover=crossover,
+                        crossover_threshold=crossover_threshold, seed=seed & 0xFFFFFFFFFFFFFFFF)
+    for j in range(4):
+        g.mutation_thresholds[j] = int(mutation_thresholds[j])
+    return g
+
+
+def breed(ga, parents, fitness, generation, children, stream=None):
+    N = int(parents.shape[0])
+    return check(ga_breed(ctypes.addressof(ga), _addr(parents), _addr(fitness), N, int(generation), _addr(children),
+                          _stream_handle(stream)))
+
+
+def hamming(genomes, fitness, stream=None):
+    return check(ga_hamming(_addr(genomes), int(genomes.shape[0]), _addr(fitness), _stream_handle(stream)))
+
+
+def run_ga(ga, population, generations, *, fitness_kind=FITNESS_SHAPE, L=16, k=20, seed=0, best=None, total=None,
+           stream=None):
+    cls = make_config(ga.n, ga.c, L, k, seed)
+    return check(ga_run(ctypes.addressof(ga), ctypes.addressof(cls), int(fitness_kind), int(population.shape[0]),
+                        int(generations), _addr(population), _addr(best), _addr(total), _stream_handle(stream)))

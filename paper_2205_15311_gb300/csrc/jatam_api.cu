@@ -1,11 +1,13 @@
 // jatam_api.cu -- host side of libjatam.so: argument checks, the per-device
 // workspace, staging of host buffers, launches, and the error state.
+#include <cmath>
 #include <cstdarg>
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
 #include <map>
 #include <tuple>
+#include <vector>
 #include <mutex>
 #include <string>
 
@@ -26,6 +28,7 @@ int g_warps_override = 0;
 struct Tuning {
     int warps = 8;
     int stop_at = 8;
+    int w32 = 2, w16 = 4, w8 = 2;  // warps per CTA of each region size in the mixed launch
 };
 // launch shape per key (lattice template, n, c); n = c = 0 for mixed batches
 std::map<std::tuple<int, int, int>, Tuning> g_tuned;
@@ -90,6 +93,10 @@ struct Workspace {
     cudaEvent_t k_start = nullptr, k_stop = nullptr;  // around the last profiled kernel
     bool k_valid = false;
     int max_dyn_smem[3] = {0, 0, 0};  // the kernel attribute only ever grows
+    std::map<std::string, cudaGraphExec_t> graphs;  // captured calls, by argument set
+    void *ga_buf = nullptr;   // ga_run / ga_breed: fitness, children, cumsum, stats
+    size_t ga_bytes = 0;
+    cudaStream_t capture = nullptr;                  // private stream used only for capturing
 };
 
 std::map<int, Workspace *> g_ws;
@@ -136,10 +143,10 @@ int workspace(Workspace **out)
     CUDA_TRY(cudaMalloc(&w->compact.min_id, cap * 8));
     CUDA_TRY(cudaMalloc(&w->compact.size_max, cap * 4));
     CUDA_TRY(cudaMalloc(&w->compact.size_min, cap * 4));
-    CUDA_TRY(cudaMalloc(&w->work_next, 8));
+    CUDA_TRY(cudaMalloc(&w->work_next, 3 * 8));
     CUDA_TRY(cudaMalloc(&w->err, 4));
     CUDA_TRY(cudaMalloc(&w->nkeys, 4));
-    CUDA_TRY(cudaMalloc(&w->list_count, 8));
+    CUDA_TRY(cudaMalloc(&w->list_count, 3 * 8));
     CUDA_TRY(cudaMallocHost(&w->host_words, 16));
     CUDA_TRY(cudaEventCreateWithFlags(&w->last, cudaEventDisableTiming));
     CUDA_TRY(cudaEventCreate(&w->k_start));
@@ -184,11 +191,28 @@ int check_params(int n, int c, int L, int k, bool packed)
     return JATAM_OK;
 }
 
+int g_plan[3] = {2, 4, 2};  // mixed launch: warps with 32x32, 16x16, 8x8 regions per CTA
+
+bool plan_fits(int w32, int w16, int w8)
+{
+    const int warps = w32 + w16 + w8;
+    // at least one warp with a 32 x 32 region: a batch may hold any lattice size,
+    // and only such a warp can run an item with L > 16
+    return w32 >= 1 && w16 >= 0 && w8 >= 0 && w32 <= 8 && w16 <= 8 && w8 <= 8 && warps <= 8 &&
+           classify_mixed_smem_bytes(w32, w16, w8) <= 200 * 1024;
+}
+
 Tuning tuning_for(int S, int n, int c)
 {
     Tuning t;
+    t.w32 = g_plan[0];
+    t.w16 = g_plan[1];
+    t.w8 = g_plan[2];
     auto it = g_tuned.find(std::make_tuple(S, n, c));
-    if (it != g_tuned.end()) t = it->second;
+    if (it != g_tuned.end()) {
+        t.warps = it->second.warps;
+        t.stop_at = it->second.stop_at;
+    }
     if (S == 32 && it == g_tuned.end()) t.warps = 2;  // the 32 x 32 lattice takes 33 KB of shared memory per warp
     if (g_warps_override) t.warps = g_warps_override;
     if (g_stop_override) t.stop_at = g_stop_override;
@@ -207,7 +231,7 @@ struct Outputs {
 // kernels, stage host outputs, and synchronise when needed.
 int run(Workspace *w, LaunchArgs a, int S, jatam_result *out, int32_t *fitness, jatam_hist_entry *hist,
         uint32_t hist_cap, uint32_t *hist_len, bool sync_flag, cudaStream_t st, const Tuning *force = nullptr,
-        float *kernel_ms = nullptr)
+        float *kernel_ms = nullptr, bool per_shape = false, bool use_graph = false)
 {
     Outputs o;
     const Kind ko = kind_of(out, w->device), kf = kind_of(fitness, w->device), kh = kind_of(hist, w->device),
@@ -235,6 +259,7 @@ int run(Workspace *w, LaunchArgs a, int S, jatam_result *out, int32_t *fitness, 
         if (o.host_hist) {
             if (w->stage_hist_cap < hist_cap) {
                 if (w->stage_hist) cudaFree(w->stage_hist);
+        if (w->ga_buf) cudaFree(w->ga_buf);
                 w->stage_hist = nullptr;
                 w->stage_hist_cap = 0;
                 cudaError_t e = cudaMalloc(&w->stage_hist, (size_t)hist_cap * sizeof(jatam_hist_entry));
@@ -256,49 +281,140 @@ int run(Workspace *w, LaunchArgs a, int S, jatam_result *out, int32_t *fitness, 
     a.use_hist = hist ? 1 : 0;
     a.work_next = w->work_next;
     a.err = w->err;
-    const Tuning tune = force ? *force : tuning_for(S, a.mode == MODE_RECORDS && a.shapes ? 0 : a.n,
-                                                    a.mode == MODE_RECORDS && a.shapes ? 0 : a.c);
+    const bool mixed = a.mode == MODE_RECORDS && a.shapes;
+    const Tuning tune = force ? *force : tuning_for(S, mixed ? 0 : a.n, mixed ? 0 : a.c);
     a.stop_at = tune.stop_at;
     if (n_items) {
-        int rc = grow(&w->list, &w->list_bytes, n_items * 8);
+        int rc = grow(&w->list, &w->list_bytes, n_items * 8 * (mixed ? 3 : 1));
         if (rc) return rc;
     }
     a.list = static_cast<unsigned long long *>(w->list);
+    a.list_stride = n_items;
     a.list_count = w->list_count;
+    a.bucket = mixed ? 1 : 0;
+    a.klass = 0;
+    a.plan_w32 = tune.w32;
+    a.plan_w16 = tune.w16;
+    a.plan_w8 = tune.w8;
 
+    // the single-template launch (not used for mixed sizes)
     const int warps = tune.warps;
-    const int si = S == 8 ? 0 : S == 16 ? 1 : 2;
-    if (classify_smem_bytes(S, warps) > w->max_dyn_smem[si]) {
-        CUDA_TRY(classify_set_attributes(S, warps));
-        w->max_dyn_smem[si] = classify_smem_bytes(S, warps);
+    long long blocks = 0;
+    if (!mixed) {
+        const int si = S == 8 ? 0 : S == 16 ? 1 : 2;
+        if (classify_smem_bytes(S, warps) > w->max_dyn_smem[si]) {
+            CUDA_TRY(classify_set_attributes(S, warps));
+            w->max_dyn_smem[si] = classify_smem_bytes(S, warps);
+        }
+        int per_sm = 0;
+        CUDA_TRY(classify_occupancy(S, warps, &per_sm));
+        if (per_sm < 1) return fail(JATAM_ECUDA, "classification kernel does not fit on an SM");
+        blocks = (long long)per_sm * w->num_sms;
+        const long long lanes_per_cta = 32LL * warps;
+        const long long needed = (long long)((n_items + lanes_per_cta - 1) / lanes_per_cta);
+        if (needed < blocks) blocks = needed < 1 ? 1 : needed;
     }
-    int per_sm = 0;
-    CUDA_TRY(classify_occupancy(S, warps, &per_sm));
-    if (per_sm < 1) return fail(JATAM_ECUDA, "classification kernel does not fit on an SM");
-    long long blocks = (long long)per_sm * w->num_sms;
-    const long long lanes_per_cta = 32LL * warps;
-    const long long needed = (long long)((n_items + lanes_per_cta - 1) / lanes_per_cta);
-    if (needed < blocks) blocks = needed < 1 ? 1 : needed;
+
+    // launch shapes of the growth kernels, fixed before anything is enqueued
+    struct FixedLaunch {
+        int S, blocks, warps, stop_at;
+    } fixed[3] = {};
+    if (n_items && mixed && per_shape) {
+        for (int kc = 0; kc < 3; ++kc) {
+            const int Sk = 8 << kc;
+            const Tuning tk = tuning_for(Sk, 0, 0);
+            if (classify_smem_bytes(Sk, tk.warps) > w->max_dyn_smem[kc]) {
+                CUDA_TRY(classify_set_attributes(Sk, tk.warps));
+                w->max_dyn_smem[kc] = classify_smem_bytes(Sk, tk.warps);
+            }
+            int pk = 0;
+            CUDA_TRY(classify_occupancy(Sk, tk.warps, &pk));
+            if (pk < 1) return fail(JATAM_ECUDA, "classification kernel does not fit on an SM");
+            fixed[kc] = {Sk, pk * w->num_sms, tk.warps, tk.stop_at};
+        }
+    }
+    int mixed_blocks = 0;
+    if (n_items && mixed && !per_shape) {
+        int pm = 0;
+        CUDA_TRY(classify_mixed_prepare(a.plan_w32, a.plan_w16, a.plan_w8, &pm));
+        if (pm < 1) return fail(JATAM_ECUDA, "mixed classification kernel does not fit on an SM");
+        mixed_blocks = pm * w->num_sms;
+    }
+    long long pblocks = (long long)(n_items + 255) / 256;
+    if (pblocks > 8LL * w->num_sms) pblocks = 8LL * w->num_sms;
+    const bool timed = g_profile || kernel_ms;
+
+    // the device work of the call; `events` brackets the growth kernels
+    auto enqueue = [&](cudaStream_t s, bool events) -> int {
+        CUDA_TRY(launch_reset(w->work_next, w->nkeys, w->list_count, s));
+        if (n_items) CUDA_TRY(launch_prefilter(a, S, (int)pblocks, s));
+        if (events) CUDA_TRY(cudaEventRecord(w->k_start, s));
+        if (n_items && !mixed) CUDA_TRY(launch_classify(a, S, (int)blocks, warps, s));
+        if (n_items && mixed && per_shape) {
+            // one fixed launch per lattice size class, each over its own list
+            for (int kc = 0; kc < 3; ++kc) {
+                LaunchArgs ak = a;
+                ak.klass = kc;
+                ak.stop_at = fixed[kc].stop_at;
+                CUDA_TRY(launch_classify(ak, fixed[kc].S, fixed[kc].blocks, fixed[kc].warps, s));
+            }
+        }
+        if (n_items && mixed && !per_shape) CUDA_TRY(launch_classify_mixed(a, mixed_blocks, s));
+        if (events) CUDA_TRY(cudaEventRecord(w->k_stop, s));
+        if (hist) {
+            CUDA_TRY(launch_hist_compact(w->table, w->compact, w->nkeys, 2 * w->num_sms, s));
+            CUDA_TRY(launch_hist_emit(w->compact, w->nkeys, o.hist_dev, hist_cap,
+                                      o.host_len ? nullptr : o.hist_len_dev, w->num_sms, s));
+        }
+        return JATAM_OK;
+    };
 
     CUDA_TRY(cudaStreamWaitEvent(st, w->last, 0));
-    CUDA_TRY(launch_reset(w->work_next, w->nkeys, w->list_count, st));
-    if (n_items) {
-        long long pblocks = (long long)(n_items + 255) / 256;
-        if (pblocks > 8LL * w->num_sms) pblocks = 8LL * w->num_sms;
-        CUDA_TRY(launch_prefilter(a, S, (int)pblocks, st));
+    if (!use_graph) {
+        int rc = enqueue(st, timed);
+        if (rc) return rc;
+    } else {
+        // one instantiated graph per distinct argument set, replayed on the caller's stream
+        std::string key;
+        auto put = [&key](const void *p, size_t n) { key.append(static_cast<const char *>(p), n); };
+        const void *ptrs[] = {a.colours, a.shapes, a.ids, a.genomes, a.out, a.fitness, a.list, o.hist_dev,
+                              o.host_len ? nullptr : o.hist_len_dev};
+        put(ptrs, sizeof ptrs);
+        const long long nums[] = {a.mode, (long long)a.first, (long long)a.count, a.n, a.c, a.L, a.k, a.key0, a.key1,
+                                  a.use_hist, a.stop_at, (long long)a.list_stride, a.bucket, a.plan_w32, a.plan_w16,
+                                  a.plan_w8, S, blocks, warps, per_shape, mixed_blocks, pblocks, hist_cap,
+                                  fixed[0].blocks, fixed[0].warps, fixed[0].stop_at, fixed[1].blocks, fixed[1].warps,
+                                  fixed[1].stop_at, fixed[2].blocks, fixed[2].warps, fixed[2].stop_at};
+        put(nums, sizeof nums);
+        cudaGraphExec_t exec = nullptr;
+        auto it = w->graphs.find(key);
+        if (it != w->graphs.end()) {
+            exec = it->second;
+        } else {
+            if (w->graphs.size() >= 64) {
+                for (auto &kv : w->graphs) cudaGraphExecDestroy(kv.second);
+                w->graphs.clear();
+            }
+            if (!w->capture) CUDA_TRY(cudaStreamCreateWithFlags(&w->capture, cudaStreamNonBlocking));
+            cudaGraph_t graph = nullptr;
+            CUDA_TRY(cudaStreamBeginCapture(w->capture, cudaStreamCaptureModeThreadLocal));
+            const int rc = enqueue(w->capture, false);
+            cudaError_t ec = cudaStreamEndCapture(w->capture, &graph);
+            if (rc) {
+                if (graph) cudaGraphDestroy(graph);
+                return rc;
+            }
+            if (ec != cudaSuccess) return fail(JATAM_ECUDA, "stream capture failed: %s", cudaGetErrorString(ec));
+            ec = cudaGraphInstantiate(&exec, graph, 0);
+            cudaGraphDestroy(graph);
+            if (ec != cudaSuccess) return fail(JATAM_ECUDA, "graph instantiation failed: %s", cudaGetErrorString(ec));
+            w->graphs[key] = exec;
+        }
+        if (timed) CUDA_TRY(cudaEventRecord(w->k_start, st));
+        CUDA_TRY(cudaGraphLaunch(exec, st));
+        if (timed) CUDA_TRY(cudaEventRecord(w->k_stop, st));
     }
-    const bool timed = g_profile || kernel_ms;
-    if (timed) CUDA_TRY(cudaEventRecord(w->k_start, st));
-    if (n_items) CUDA_TRY(launch_classify(a, S, (int)blocks, warps, st));
-    if (timed) {
-        CUDA_TRY(cudaEventRecord(w->k_stop, st));
-        w->k_valid = true;
-    }
-    if (hist) {
-        CUDA_TRY(launch_hist_compact(w->table, w->compact, w->nkeys, 2 * w->num_sms, st));
-        CUDA_TRY(launch_hist_emit(w->compact, w->nkeys, o.hist_dev, hist_cap, o.host_len ? nullptr : o.hist_len_dev,
-                                  w->num_sms, st));
-    }
+    if (timed) w->k_valid = true;
     if (o.host_out && n_items)
         CUDA_TRY(cudaMemcpyAsync(out, o.out_dev, n_items * sizeof(jatam_result), cudaMemcpyDeviceToHost, st));
     if (o.host_fit && n_items)
@@ -388,7 +504,8 @@ int jatam_enumerate(const jatam_config *cfg, uint64_t first, uint64_t count, jat
     a.key0 = (uint32_t)cfg->seed;
     a.key1 = (uint32_t)(cfg->seed >> 32);
     return run(w, a, lattice_template(cfg->L), out, nullptr, hist, hist_cap, hist_len,
-               (cfg->flags & JATAM_SYNC) != 0, static_cast<cudaStream_t>(stream));
+               (cfg->flags & JATAM_SYNC) != 0, static_cast<cudaStream_t>(stream), nullptr, nullptr, false,
+               (cfg->flags & JATAM_GRAPH) != 0);
 }
 
 int jatam_classify_batch(const jatam_config *cfg, const uint8_t *colours, const uint8_t *shapes,
@@ -445,7 +562,8 @@ int jatam_classify_batch(const jatam_config *cfg, const uint8_t *colours, const 
         CUDA_TRY(cudaMemcpyAsync(base + off_i, stream_ids, ib, cudaMemcpyHostToDevice, st));
         a.ids = reinterpret_cast<const unsigned long long *>(base + off_i);
     }
-    return run(w, a, S, out, nullptr, hist, hist_cap, hist_len, (cfg->flags & JATAM_SYNC) != 0, st);
+    return run(w, a, S, out, nullptr, hist, hist_cap, hist_len, (cfg->flags & JATAM_SYNC) != 0, st, nullptr, nullptr,
+               (cfg->flags & JATAM_PER_SHAPE) != 0, (cfg->flags & JATAM_GRAPH) != 0);
 }
 
 int ga_evaluate(const jatam_config *cfg, const uint64_t *genomes, uint64_t N, int32_t *fitness, jatam_result *out,
@@ -474,7 +592,215 @@ int ga_evaluate(const jatam_config *cfg, const uint64_t *genomes, uint64_t N, in
     a.n = cfg->n; a.c = cfg->c; a.L = cfg->L; a.k = cfg->k;
     a.key0 = (uint32_t)cfg->seed;
     a.key1 = (uint32_t)(cfg->seed >> 32);
-    return run(w, a, lattice_template(cfg->L), out, fitness, nullptr, 0, nullptr, (cfg->flags & JATAM_SYNC) != 0, st);
+    return run(w, a, lattice_template(cfg->L), out, fitness, nullptr, 0, nullptr, (cfg->flags & JATAM_SYNC) != 0, st,
+               nullptr, nullptr, false, (cfg->flags & JATAM_GRAPH) != 0);
+}
+
+namespace {
+
+int check_ga(const jatam_ga_config *ga, GaArgs *g)
+{
+    if (!ga) return fail(JATAM_EINVAL, "ga is NULL");
+    int rc = check_params(ga->n, ga->c, 1, 1, true);
+    if (rc) return rc;
+    if (ga->selection > 1 || ga->crossover > 2 || (ga->selection == 0 && (ga->tournament < 1 || ga->tournament > 16)))
+        return fail(JATAM_EINVAL, "selection 0/1, tournament 1..16, crossover 0..2");
+    for (int j = 1; j < 4; ++j)
+        if (ga->mutation_thresholds[j] < ga->mutation_thresholds[j - 1])
+            return fail(JATAM_EINVAL, "mutation thresholds must not decrease");
+    *g = GaArgs{};
+    g->n = ga->n;
+    g->c = ga->c;
+    g->b = log2c(ga->c);
+    g->bits = 4 * ga->n * g->b;
+    g->selection = ga->selection;
+    g->tournament = ga->tournament;
+    g->crossover = ga->crossover;
+    g->crossover_threshold = ga->crossover_threshold;
+    for (int j = 0; j < 4; ++j) g->mutation_thresholds[j] = ga->mutation_thresholds[j];
+    g->key0 = (uint32_t)ga->seed;
+    g->key1 = (uint32_t)(ga->seed >> 32);
+    if (g->crossover == 1 && g->bits < 2) return fail(JATAM_EINVAL, "one-point crossover needs at least 2 bits");
+    return JATAM_OK;
+}
+
+// GA scratch: [fitness N x 4][children N x 8][cumsum N x 8][stats 16], 256-byte aligned pieces
+struct GaScratch {
+    int32_t *fitness;
+    unsigned long long *children, *cumsum;
+    long long *stats;
+};
+
+int ga_scratch(Workspace *w, uint64_t N, GaScratch *s)
+{
+    const size_t a = ((size_t)N * 4 + 255) & ~size_t(255), b = ((size_t)N * 8 + 255) & ~size_t(255);
+    int rc = grow(&w->ga_buf, &w->ga_bytes, a + 2 * b + 256);
+    if (rc) return rc;
+    char *p = static_cast<char *>(w->ga_buf);
+    s->fitness = reinterpret_cast<int32_t *>(p);
+    s->children = reinterpret_cast<unsigned long long *>(p + a);
+    s->cumsum = reinterpret_cast<unsigned long long *>(p + a + b);
+    s->stats = reinterpret_cast<long long *>(p + a + 2 * b);
+    return JATAM_OK;
+}
+
+}  // namespace
+
+int ga_breed(const jatam_ga_config *ga, const uint64_t *parents, const int32_t *fitness, uint64_t N,
+             uint32_t generation, uint64_t *children, void *stream)
+{
+    std::lock_guard<std::mutex> lock(g_mutex);
+    g_last_error.clear();
+    GaArgs g;
+    int rc = check_ga(ga, &g);
+    if (rc) return rc;
+    if (N && (!parents || !fitness || !children)) return fail(JATAM_EINVAL, "parents, fitness, children required");
+    if (N == 0) return JATAM_OK;
+    if (generation >= (1u << 24)) return fail(JATAM_EINVAL, "generation must be < 2^24");
+    Workspace *w = nullptr;
+    rc = workspace(&w);
+    if (rc) return rc;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    CUDA_TRY(cudaStreamWaitEvent(st, w->last, 0));
+    GaScratch sc;
+    rc = ga_scratch(w, 2 * N, &sc);  // room to stage host parents next to the children
+    if (rc) return rc;
+    const Kind kp = kind_of(parents, w->device), kf = kind_of(fitness, w->device), kc = kind_of(children, w->device);
+    if ((kp == K_NULL) || (kf == K_NULL) || (kc == K_NULL)) return fail(JATAM_EINVAL, "a buffer lives on another device");
+    const unsigned long long *dp = reinterpret_cast<const unsigned long long *>(parents);
+    const int32_t *df = fitness;
+    if (kp == K_HOST) {
+        CUDA_TRY(cudaMemcpyAsync(sc.cumsum + N, parents, (size_t)N * 8, cudaMemcpyHostToDevice, st));
+        dp = sc.cumsum + N;
+    }
+    if (kf == K_HOST) {
+        CUDA_TRY(cudaMemcpyAsync(sc.fitness, fitness, (size_t)N * 4, cudaMemcpyHostToDevice, st));
+        df = sc.fitness;
+    }
+    unsigned long long *dc = kc == K_HOST ? sc.children : reinterpret_cast<unsigned long long *>(children);
+    g.parents = dp;
+    g.fitness = df;
+    g.cumsum = sc.cumsum;
+    g.N = N;
+    g.generation = generation;
+    g.children = dc;
+    CUDA_TRY(launch_ga_breed(g, st));
+    if (kc == K_HOST) CUDA_TRY(cudaMemcpyAsync(children, dc, (size_t)N * 8, cudaMemcpyDeviceToHost, st));
+    CUDA_TRY(cudaEventRecord(w->last, st));
+    if (kc == K_HOST || kp == K_HOST || kf == K_HOST) CUDA_TRY(cudaStreamSynchronize(st));
+    return JATAM_OK;
+}
+
+int ga_hamming(const uint64_t *genomes, uint64_t N, int32_t *fitness, void *stream)
+{
+    std::lock_guard<std::mutex> lock(g_mutex);
+    g_last_error.clear();
+    if (N && (!genomes || !fitness)) return fail(JATAM_EINVAL, "genomes and fitness required");
+    if (N == 0) return JATAM_OK;
+    Workspace *w = nullptr;
+    int rc = workspace(&w);
+    if (rc) return rc;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    CUDA_TRY(cudaStreamWaitEvent(st, w->last, 0));
+    GaScratch sc;
+    rc = ga_scratch(w, N, &sc);
+    if (rc) return rc;
+    const Kind kg = kind_of(genomes, w->device), kf = kind_of(fitness, w->device);
+    const unsigned long long *dg = reinterpret_cast<const unsigned long long *>(genomes);
+    if (kg == K_HOST) {
+        CUDA_TRY(cudaMemcpyAsync(sc.children, genomes, (size_t)N * 8, cudaMemcpyHostToDevice, st));
+        dg = sc.children;
+    }
+    int32_t *df = kf == K_HOST ? sc.fitness : fitness;
+    CUDA_TRY(launch_ga_hamming(dg, N, df, st));
+    if (kf == K_HOST) CUDA_TRY(cudaMemcpyAsync(fitness, df, (size_t)N * 4, cudaMemcpyDeviceToHost, st));
+    CUDA_TRY(cudaEventRecord(w->last, st));
+    if (kf == K_HOST || kg == K_HOST) CUDA_TRY(cudaStreamSynchronize(st));
+    return JATAM_OK;
+}
+
+int ga_poisson_thresholds(double rate, uint32_t thresholds[4])
+{
+    g_last_error.clear();
+    if (!thresholds || !(rate >= 0.0)) return fail(JATAM_EINVAL, "rate must be >= 0 and thresholds non-NULL");
+    double term = exp(-rate), cdf = 0.0;
+    for (int j = 0; j < 4; ++j) {
+        cdf += term;
+        term *= rate / (double)(j + 1);
+        const double t = floor(cdf * 4294967296.0);
+        thresholds[j] = t >= 4294967295.0 ? 4294967295u : (uint32_t)t;
+    }
+    return JATAM_OK;
+}
+
+int ga_run(const jatam_ga_config *ga, const jatam_config *cls, int fitness_kind, uint64_t N, uint32_t generations,
+           uint64_t *population, int32_t *best, int64_t *total, void *stream)
+{
+    GaArgs g;
+    {
+        std::lock_guard<std::mutex> lock(g_mutex);
+        g_last_error.clear();
+        int rc = check_ga(ga, &g);
+        if (rc) return rc;
+        if (fitness_kind != JATAM_GA_FITNESS_SHAPE && fitness_kind != JATAM_GA_FITNESS_HAMMING)
+            return fail(JATAM_EINVAL, "fitness_kind must be JATAM_GA_FITNESS_SHAPE or _HAMMING");
+        if (fitness_kind == JATAM_GA_FITNESS_SHAPE && !cls) return fail(JATAM_EINVAL, "cls is required for shape fitness");
+        if (!population || N == 0) return fail(JATAM_EINVAL, "population and N > 0 are required");
+        if (generations >= (1u << 24)) return fail(JATAM_EINVAL, "generations must be < 2^24");
+    }
+    Workspace *w = nullptr;
+    {
+        std::lock_guard<std::mutex> lock(g_mutex);
+        int rc = workspace(&w);
+        if (rc) return rc;
+        if (kind_of(population, w->device) != K_DEVICE) return fail(JATAM_EINVAL, "population must be device memory");
+    }
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const Kind kb = kind_of(best, w->device), kt = kind_of(total, w->device);
+    std::vector<long long> host_stats;
+    if (kb == K_HOST || kt == K_HOST) host_stats.resize(2 * (size_t)generations);
+    jatam_config cc{};
+    if (cls) cc = *cls;
+    cc.n = ga->n;
+    cc.c = ga->c;
+    cc.flags = JATAM_GRAPH;  // the fitness call is the same every generation: replay its graph
+    unsigned long long *pop = reinterpret_cast<unsigned long long *>(population);
+    for (uint32_t gen = 0; gen < generations; ++gen) {
+        GaScratch sc;
+        {
+            std::lock_guard<std::mutex> lock(g_mutex);
+            int rc = ga_scratch(w, N, &sc);
+            if (rc) return rc;
+        }
+        int rc = (fitness_kind == JATAM_GA_FITNESS_SHAPE)
+                     ? ga_evaluate(&cc, reinterpret_cast<const uint64_t *>(pop), N, sc.fitness, nullptr, stream)
+                     : ga_hamming(reinterpret_cast<const uint64_t *>(pop), N, sc.fitness, stream);
+        if (rc) return rc;
+        std::lock_guard<std::mutex> lock(g_mutex);
+        CUDA_TRY(launch_ga_stats(sc.fitness, N, sc.stats, st));
+        if (kb == K_DEVICE) CUDA_TRY(cudaMemcpyAsync(best + gen, sc.stats, 4, cudaMemcpyDeviceToDevice, st));
+        if (kt == K_DEVICE) CUDA_TRY(cudaMemcpyAsync(total + gen, sc.stats + 1, 8, cudaMemcpyDeviceToDevice, st));
+        if (!host_stats.empty())
+            CUDA_TRY(cudaMemcpyAsync(&host_stats[2 * gen], sc.stats, 16, cudaMemcpyDeviceToHost, st));
+        GaArgs gg = g;
+        gg.parents = pop;
+        gg.fitness = sc.fitness;
+        gg.cumsum = sc.cumsum;
+        gg.N = N;
+        gg.generation = gen;
+        gg.children = sc.children;
+        CUDA_TRY(launch_ga_breed(gg, st));
+        CUDA_TRY(cudaMemcpyAsync(pop, sc.children, (size_t)N * 8, cudaMemcpyDeviceToDevice, st));
+        CUDA_TRY(cudaEventRecord(w->last, st));
+        if (!host_stats.empty()) CUDA_TRY(cudaStreamSynchronize(st));  // host_stats must not be read early
+    }
+    if (!host_stats.empty()) {
+        for (uint32_t gen = 0; gen < generations; ++gen) {
+            if (kb == K_HOST) best[gen] = (int32_t)host_stats[2 * gen];
+            if (kt == K_HOST) total[gen] = host_stats[2 * gen + 1];
+        }
+    }
+    return JATAM_OK;
 }
 
 int jatam_philox(const uint32_t *in, uint64_t N, uint32_t *out, void *stream)
@@ -617,6 +943,94 @@ int jatam_get_tuning(const jatam_config *cfg, int *warps_per_cta, int *stop_at)
     return JATAM_OK;
 }
 
+int jatam_set_mixed_plan(int warps_32, int warps_16, int warps_8)
+{
+    std::lock_guard<std::mutex> lock(g_mutex);
+    g_last_error.clear();
+    if (!plan_fits(warps_32, warps_16, warps_8))
+        return fail(JATAM_EINVAL, "plan %d/%d/%d: at least one 32 x 32 warp, at most 8 warps, regions that fit "
+                                  "in shared memory", warps_32, warps_16, warps_8);
+    g_plan[0] = warps_32;
+    g_plan[1] = warps_16;
+    g_plan[2] = warps_8;
+    return JATAM_OK;
+}
+
+int jatam_get_mixed_plan(int *warps_32, int *warps_16, int *warps_8)
+{
+    std::lock_guard<std::mutex> lock(g_mutex);
+    g_last_error.clear();
+    if (!warps_32 || !warps_16 || !warps_8) return fail(JATAM_EINVAL, "NULL argument");
+    *warps_32 = g_plan[0];
+    *warps_16 = g_plan[1];
+    *warps_8 = g_plan[2];
+    return JATAM_OK;
+}
+
+int jatam_autotune_batch(const uint8_t *colours, const uint8_t *shapes, uint64_t N, uint64_t seed, void *stream)
+{
+    std::lock_guard<std::mutex> lock(g_mutex);
+    g_last_error.clear();
+    if (!colours || !shapes || N == 0) return fail(JATAM_EINVAL, "colours, shapes and N > 0 are required");
+    Workspace *w = nullptr;
+    int rc = workspace(&w);
+    if (rc) return rc;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    CUDA_TRY(cudaStreamWaitEvent(st, w->last, 0));
+    // the batch as device memory in stage_in: colours, then shapes
+    const Kind kc = kind_of(colours, w->device), ks = kind_of(shapes, w->device);
+    const size_t cb = (size_t)N * 16, off_s = (cb + 255) & ~size_t(255);
+    const uint8_t *dc = colours, *ds = shapes;
+    if (kc == K_HOST || ks == K_HOST) {
+        rc = grow(&w->stage_in, &w->stage_in_bytes, off_s + (size_t)N * 4 + 256);
+        if (rc) return rc;
+        char *base = static_cast<char *>(w->stage_in);
+        if (kc == K_HOST) {
+            CUDA_TRY(cudaMemcpyAsync(base, colours, cb, cudaMemcpyHostToDevice, st));
+            dc = reinterpret_cast<const uint8_t *>(base);
+        }
+        if (ks == K_HOST) {
+            CUDA_TRY(cudaMemcpyAsync(base + off_s, shapes, (size_t)N * 4, cudaMemcpyHostToDevice, st));
+            ds = reinterpret_cast<const uint8_t *>(base + off_s);
+        }
+    }
+    LaunchArgs a{};
+    a.mode = MODE_RECORDS;
+    a.count = N;
+    a.colours = dc;
+    a.shapes = ds;
+    a.key0 = (uint32_t)seed;
+    a.key1 = (uint32_t)(seed >> 32);
+    static const int plans[][3] = {{1, 2, 1}, {2, 4, 2}, {1, 3, 2}, {2, 2, 2}, {1, 4, 3}, {2, 3, 3},
+                                   {3, 3, 2}, {1, 5, 2}, {2, 5, 1}, {1, 6, 1}, {4, 2, 2}, {2, 6, 0}};
+    int best[3] = {g_plan[0], g_plan[1], g_plan[2]};
+    float best_ms = 1e30f;
+    for (const auto &p : plans) {
+        if (!plan_fits(p[0], p[1], p[2])) continue;
+        for (int stop : {4, 8, 16}) {
+            Tuning t;
+            t.stop_at = stop;
+            t.w32 = p[0];
+            t.w16 = p[1];
+            t.w8 = p[2];
+            float ms = 0.f;
+            rc = run(w, a, 32, nullptr, nullptr, nullptr, 0, nullptr, true, st, &t, &ms);
+            if (rc) return rc;
+            if (ms < best_ms) {
+                best_ms = ms;
+                best[0] = p[0];
+                best[1] = p[1];
+                best[2] = p[2];
+                g_tuned[std::make_tuple(32, 0, 0)] = t;
+            }
+        }
+    }
+    g_plan[0] = best[0];
+    g_plan[1] = best[1];
+    g_plan[2] = best[2];
+    return JATAM_OK;
+}
+
 int jatam_profile(int enable)
 {
     std::lock_guard<std::mutex> lock(g_mutex);
@@ -659,9 +1073,12 @@ void jatam_shutdown(void)
         if (w->stage_out) cudaFree(w->stage_out);
         if (w->stage_aux) cudaFree(w->stage_aux);
         if (w->stage_hist) cudaFree(w->stage_hist);
+        if (w->ga_buf) cudaFree(w->ga_buf);
         cudaEventDestroy(w->last);
         cudaEventDestroy(w->k_start);
         cudaEventDestroy(w->k_stop);
+        for (auto &kv : w->graphs) cudaGraphExecDestroy(kv.second);
+        if (w->capture) cudaStreamDestroy(w->capture);
         delete w;
     }
     g_ws.clear();

@@ -60,9 +60,13 @@ struct LaunchArgs {
     Table table;
     int use_hist;
     int stop_at;                    // finished lanes that end a growth round (1..32)
-    unsigned long long *list;        // items left to grow, written by the pre-filter
-    unsigned long long *list_count;  // their number
-    unsigned long long *work_next;  // work counter, zeroed before the launch
+    unsigned long long *list;        // items left to grow, written by the pre-filter: 1 or 3 lists
+    unsigned long long list_stride;  // capacity of one list (the call's item count)
+    unsigned long long *list_count;  // [3] their lengths
+    int bucket;                      // 1: lists by lattice size class (<= 8, <= 16, <= 32); 0: one list
+    int klass;                       // classify_kernel: the list it works through
+    int plan_w32, plan_w16, plan_w8; // classify_mixed_kernel: warps per CTA of each region size
+    unsigned long long *work_next;  // [3] work counters (one per list), zeroed before the launch
     unsigned *err;                  // sticky error bits
 };
 
@@ -71,6 +75,9 @@ int classify_smem_bytes(int S, int warps_per_cta);
 cudaError_t classify_set_attributes(int S, int warps_per_cta);
 cudaError_t classify_occupancy(int S, int warps_per_cta, int *blocks_per_sm);
 cudaError_t launch_classify(const LaunchArgs &a, int S, int blocks, int warps_per_cta, cudaStream_t st);
+int classify_mixed_smem_bytes(int w32, int w16, int w8);
+cudaError_t classify_mixed_prepare(int w32, int w16, int w8, int *blocks_per_sm);
+cudaError_t launch_classify_mixed(const LaunchArgs &a, int blocks, cudaStream_t st);
 
 cudaError_t launch_reset(unsigned long long *work_next, unsigned *nkeys, unsigned long long *list_count,
                          cudaStream_t st);
@@ -80,6 +87,25 @@ cudaError_t launch_hist_compact(Table t, Compact c, unsigned *nkeys, int blocks,
 cudaError_t launch_hist_emit(Compact c, const unsigned *nkeys, jatam_hist_entry *hist, unsigned cap,
                              uint32_t *hist_len, int blocks, cudaStream_t st);
 cudaError_t launch_philox(const uint32_t *in, unsigned long long n, uint32_t *out, cudaStream_t st);
+
+// genetic algorithm (jatam_ga.cu)
+struct GaArgs {
+    int n, c, b, bits;           // genome space: 4 n b bits, b = log2(c)
+    int selection, tournament, crossover;
+    uint32_t crossover_threshold;
+    uint32_t mutation_thresholds[4];
+    uint32_t key0, key1;
+    const unsigned long long *parents;
+    const int32_t *fitness;
+    const unsigned long long *cumsum;  // roulette: workspace for the prefix sum of the fitness
+    unsigned long long N;
+    uint32_t generation;
+    unsigned long long *children;
+};
+cudaError_t launch_ga_breed(const GaArgs &g, cudaStream_t st);
+cudaError_t launch_ga_hamming(const unsigned long long *genomes, unsigned long long n, int32_t *fitness,
+                              cudaStream_t st);
+cudaError_t launch_ga_stats(const int32_t *fitness, unsigned long long n, long long *stats, cudaStream_t st);
 
 // the message returned by jatam_last_error() for the calling thread
 void set_last_error(const char *msg);

@@ -27,6 +27,7 @@
 #include <cstdint>
 #include <cuda_runtime.h>
 
+#include "jatam_device.cuh"
 #include "jatam_internal.cuh"
 
 namespace jatam {
@@ -50,22 +51,6 @@ struct Geo {
     static constexpr int CACHE = NBM + 32;  // per-warp shape cache: entry j in "lane" j's bank
     static constexpr int WORDS = CACHE + 3;  // 32-bit words per lane
 };
-
-// ---------------------------------------------------------------------------
-// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11)
-// ---------------------------------------------------------------------------
-__device__ __forceinline__ uint4 philox4x32_10(uint4 x, uint32_t k0, uint32_t k1)
-{
-#pragma unroll
-    for (int round = 0; round < 10; ++round) {
-        const uint32_t lo0 = 0xD2511F53u * x.x, hi0 = __umulhi(0xD2511F53u, x.x);
-        const uint32_t lo1 = 0xCD9E8D57u * x.z, hi1 = __umulhi(0xCD9E8D57u, x.z);
-        x = make_uint4(hi1 ^ x.y ^ k0, lo1, hi0 ^ x.w ^ k1, lo0);
-        k0 += 0x9E3779B9u;
-        k1 += 0xBB67AE85u;
-    }
-    return x;
-}
 
 // Jenkins one-at-a-time, one byte at a time (Section 2.5).
 __device__ __forceinline__ uint32_t oaat_add(uint32_t h, uint32_t byte)
@@ -664,10 +649,12 @@ __global__ void __launch_bounds__(256) prefilter_kernel(const LaunchArgs a, int 
         const unsigned long long idx = base + threadIdx.x;
         int key = -1;
         bool grow = false;
+        int klass = 0;
         unsigned long long sid = 0;
         if (idx < a.count) {
             const Item it = load_item(a, idx, b_uniform, smax);
             sid = it.sid;
+            if (a.bucket) klass = (it.L <= 8) ? 0 : (it.L <= 16) ? 1 : 2;
             if (!it.ok) {
                 atomicOr(a.err, ERR_INVALID_ITEM);
                 write_result(a, idx, 255, 0, 0u, 0u);
@@ -684,12 +671,18 @@ __global__ void __launch_bounds__(256) prefilter_kernel(const LaunchArgs a, int 
                 }
             }
         }
-        const unsigned gm = __ballot_sync(FULL, grow);
-        if (gm) {
-            unsigned long long slot = 0;
-            if (lane == 0) slot = atomicAdd(a.list_count, (unsigned long long)__popc(gm));
-            slot = __shfl_sync(FULL, slot, 0);
-            if (grow) a.list[slot + __popc(gm & lanemask_lt())] = idx;
+        // append to the list of the item's lattice size class (one class
+        // unless the launch mixes sizes)
+#pragma unroll
+        for (int kc = 0; kc < 3; ++kc) {
+            const unsigned gm = __ballot_sync(FULL, grow && klass == kc);
+            if (gm) {
+                unsigned long long slot = 0;
+                if (lane == 0) slot = atomicAdd(&a.list_count[kc], (unsigned long long)__popc(gm));
+                slot = __shfl_sync(FULL, slot, 0);
+                if (grow && klass == kc) a.list[(size_t)kc * a.list_stride + slot + __popc(gm & lanemask_lt())] = idx;
+            }
+            if (!a.bucket) break;
         }
         if (a.use_hist) {
 #pragma unroll
@@ -721,28 +714,22 @@ __global__ void __launch_bounds__(256) prefilter_kernel(const LaunchArgs a, int 
     }
 }
 
+// The work of one warp over one list of items (a pre-filter list): every
+// lane takes items from the list through the shared counter `work_next` and
+// the warp runs them to their class in batched phases.  `warp_lanes` is the
+// warp's interleaved region of Geo<S>::WORDS words per lane.
 template <int S>
-__global__ void __launch_bounds__(256) classify_kernel(const LaunchArgs a)
+__device__ __forceinline__ void warp_loop(const LaunchArgs &a, uint32_t *warp_lanes, SmemHist &H,
+                                          const unsigned long long *list, unsigned long long total,
+                                          unsigned long long *work_next)
 {
     using G = Geo<S>;
-    extern __shared__ uint32_t smem_lanes[];
-    __shared__ SmemHist H;
     const int lane = threadIdx.x & 31;
-    const int warp = threadIdx.x >> 5;
-    uint32_t *warp_lanes = smem_lanes + (size_t)warp * G::WORDS * 32;
     uint32_t *my = warp_lanes + lane;
-
-    for (int i = threadIdx.x; i < HIST_SLOTS; i += blockDim.x) {
-        H.key[i] = EMPTY_KEY;
-        H.min_id[i] = ~0ull;
-        H.count[i] = 0u;
-        H.smax[i] = 0u;
-        H.smin[i] = 0xFFFFFFFFu;
-    }
     for (int w = 0; w < 3 * G::NW; ++w) my[w * 32] = 0u;
     my[G::CACHE * 32] = 0u;  // key with h = 0: never matches a crop
     my[(G::CACHE + 1) * 32] = 0u;
-    __syncthreads();
+    __syncwarp();
 
     Lane Ls;
     Ls.phase = PH_NEED;
@@ -762,7 +749,6 @@ __global__ void __launch_bounds__(256) classify_kernel(const LaunchArgs a)
     Ls.pa = Ls.pb = make_uint4(0, 0, 0, 0);
     unsigned long long q_next = 0, q_end = 0;  // this warp's slice of the work counter
     const int b_uniform = log2_colours(a.c);
-    const unsigned long long total = *a.list_count;  // items the pre-filter left to grow
 
     for (;;) {
         // ---- service: write finished genotypes and hand out new ones from the
@@ -786,7 +772,7 @@ __global__ void __launch_bounds__(256) classify_kernel(const LaunchArgs a)
             while (assigned < cnt) {
                 if (q_next >= q_end) {
                     unsigned long long nb = 0;
-                    if (lane == 0) nb = atomicAdd(a.work_next, (unsigned long long)CHUNK);
+                    if (lane == 0) nb = atomicAdd(work_next, (unsigned long long)CHUNK);
                     nb = __shfl_sync(FULL, nb, 0);
                     if (nb >= total) break;
                     q_next = nb;
@@ -802,7 +788,7 @@ __global__ void __launch_bounds__(256) classify_kernel(const LaunchArgs a)
                 if (my_pos == ~0ull) {
                     Ls.phase = PH_DONE;
                 } else {
-                    const unsigned long long item = a.list[my_pos];
+                    const unsigned long long item = list[my_pos];
                     const Item it = load_item(a, item, b_uniform, S);
                     Ls.item = item;
                     Ls.sid = it.sid;
@@ -924,6 +910,22 @@ __global__ void __launch_bounds__(256) classify_kernel(const LaunchArgs a)
         }
     }
 
+}
+
+__device__ __forceinline__ void hist_begin(SmemHist &H)
+{
+    for (int i = threadIdx.x; i < HIST_SLOTS; i += blockDim.x) {
+        H.key[i] = EMPTY_KEY;
+        H.min_id[i] = ~0ull;
+        H.count[i] = 0u;
+        H.smax[i] = 0u;
+        H.smin[i] = 0xFFFFFFFFu;
+    }
+    __syncthreads();
+}
+
+__device__ __forceinline__ void hist_end(SmemHist &H, const LaunchArgs &a)
+{
     __syncthreads();
     if (a.use_hist) {
         for (int i = threadIdx.x; i < HIST_SLOTS; i += blockDim.x)
@@ -932,11 +934,57 @@ __global__ void __launch_bounds__(256) classify_kernel(const LaunchArgs a)
     }
 }
 
+// One lattice template for every warp: the items of pre-filter list a.klass.
+template <int S>
+__global__ void __launch_bounds__(256) classify_kernel(const LaunchArgs a)
+{
+    extern __shared__ uint32_t smem_lanes[];
+    __shared__ SmemHist H;
+    hist_begin(H);
+    const int warp = threadIdx.x >> 5;
+    uint32_t *warp_lanes = smem_lanes + (size_t)warp * Geo<S>::WORDS * 32;
+    warp_loop<S>(a, warp_lanes, H, a.list + (size_t)a.klass * a.list_stride, a.list_count[a.klass],
+                 a.work_next + a.klass);
+    hist_end(H, a);
+}
+
+// Mixed lattice sizes in one persistent launch: the first plan_w32 warps of a
+// CTA own 32 x 32 regions, the next plan_w16 16 x 16 regions, the rest 8 x 8.
+// A warp first works through the list of its own size class, then steals from
+// the lists of the smaller classes (a larger region holds any smaller
+// lattice).
+__global__ void __launch_bounds__(256) classify_mixed_kernel(const LaunchArgs a)
+{
+    extern __shared__ uint32_t smem_lanes[];
+    __shared__ SmemHist H;
+    hist_begin(H);
+    const int warp = threadIdx.x >> 5;
+    const int w32 = a.plan_w32, w16 = a.plan_w16;
+    constexpr size_t R32 = (size_t)Geo<32>::WORDS * 32, R16 = (size_t)Geo<16>::WORDS * 32,
+                     R8 = (size_t)Geo<8>::WORDS * 32;
+    if (warp < w32) {
+        uint32_t *wl = smem_lanes + (size_t)warp * R32;
+        for (int c = 2; c >= 0; --c)
+            warp_loop<32>(a, wl, H, a.list + (size_t)c * a.list_stride, a.list_count[c], a.work_next + c);
+    } else if (warp < w32 + w16) {
+        uint32_t *wl = smem_lanes + (size_t)w32 * R32 + (size_t)(warp - w32) * R16;
+        for (int c = 1; c >= 0; --c)
+            warp_loop<16>(a, wl, H, a.list + (size_t)c * a.list_stride, a.list_count[c], a.work_next + c);
+    } else {
+        uint32_t *wl = smem_lanes + (size_t)w32 * R32 + (size_t)w16 * R16 + (size_t)(warp - w32 - w16) * R8;
+        warp_loop<8>(a, wl, H, a.list, a.list_count[0], a.work_next);
+    }
+    hist_end(H, a);
+}
+
+
 __global__ void reset_kernel(unsigned long long *work_next, unsigned *nkeys, unsigned long long *list_count)
 {
-    *work_next = 0ull;
+    for (int c = 0; c < 3; ++c) {
+        work_next[c] = 0ull;
+        list_count[c] = 0ull;
+    }
     *nkeys = 0u;
-    *list_count = 0ull;
 }
 
 __global__ void table_init_kernel(Table t)
@@ -1062,6 +1110,27 @@ cudaError_t launch_classify(const LaunchArgs &a, int S, int blocks, int warps_pe
     case 16: classify_kernel<16><<<grid, block, bytes, st>>>(a); break;
     default: classify_kernel<32><<<grid, block, bytes, st>>>(a); break;
     }
+    return cudaGetLastError();
+}
+
+int classify_mixed_smem_bytes(int w32, int w16, int w8)
+{
+    return (w32 * Geo<32>::WORDS + w16 * Geo<16>::WORDS + w8 * Geo<8>::WORDS) * 32 * 4;
+}
+
+cudaError_t classify_mixed_prepare(int w32, int w16, int w8, int *blocks_per_sm)
+{
+    const int bytes = classify_mixed_smem_bytes(w32, w16, w8);
+    cudaError_t e = cudaFuncSetAttribute(classify_mixed_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e != cudaSuccess) return e;
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, classify_mixed_kernel, (w32 + w16 + w8) * 32,
+                                                         bytes);
+}
+
+cudaError_t launch_classify_mixed(const LaunchArgs &a, int blocks, cudaStream_t st)
+{
+    const int warps = a.plan_w32 + a.plan_w16 + a.plan_w8;
+    classify_mixed_kernel<<<blocks, warps * 32, classify_mixed_smem_bytes(a.plan_w32, a.plan_w16, a.plan_w8), st>>>(a);
     return cudaGetLastError();
 }
 

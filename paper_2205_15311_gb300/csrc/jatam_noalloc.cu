@@ -111,10 +111,10 @@ extern "C" int jatam_enumerate_noalloc(const jatam_config *cfg, uint64_t first, 
     cudaStream_t st = static_cast<cudaStream_t>(stream);
 
     unsigned char *base = d->scratch;
-    unsigned long long *work_next = reinterpret_cast<unsigned long long *>(base);
-    unsigned long long *list_count = reinterpret_cast<unsigned long long *>(base + 8);
-    unsigned *err = reinterpret_cast<unsigned *>(base + 16);
-    unsigned *nkeys = reinterpret_cast<unsigned *>(base + 20);
+    unsigned long long *work_next = reinterpret_cast<unsigned long long *>(base);        // [3]
+    unsigned long long *list_count = reinterpret_cast<unsigned long long *>(base + 32);  // [3]
+    unsigned *err = reinterpret_cast<unsigned *>(base + 64);
+    unsigned *nkeys = reinterpret_cast<unsigned *>(base + 68);
     unsigned long long *list = reinterpret_cast<unsigned long long *>(base + NOALLOC_HEADER);
 
     LaunchArgs a{};
@@ -129,7 +129,10 @@ extern "C" int jatam_enumerate_noalloc(const jatam_config *cfg, uint64_t first, 
     a.use_hist = 0;
     a.stop_at = 8;
     a.list = list;
+    a.list_stride = count;
     a.list_count = list_count;
+    a.bucket = 0;
+    a.klass = 0;
     a.work_next = work_next;
     a.err = err;
 

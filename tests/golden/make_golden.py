@@ -34,7 +34,34 @@ WORKLOADS = {
 }
 
 
+def write_mixed(name, count, seed):
+    """Explicit mixed-size tile sets from the seeded input generator (its
+    SplitMix64 streams are the inputs; every result comes from the oracle)."""
+    from paper_2205_15311_gb300 import workloads as WL  # input generator only
+    colours, shapes = WL.mixed_records(count, seed=seed)
+    t0 = time.time()
+    res, placements = O.classify_batch(colours, shapes=shapes, seed=seed)
+    dt = time.time() - t0
+    hist = O.histogram(res, np.arange(count, dtype=np.uint64))
+    meta = {
+        "workload": {"mixed_records": count, "seed": seed},
+        "inputs_sha256": hashlib.sha256(colours.tobytes() + shapes.tobytes()).hexdigest(),
+        "results_sha256": hashlib.sha256(res.tobytes()).hexdigest(),
+        "class_counts": np.bincount(res["cls"], minlength=4).tolist(),
+        "placements": int(placements),
+        "distinct_keys": int(hist.shape[0]),
+        "oracle_seconds": round(dt, 1),
+        "collisions": int(O.size_collisions(res).size),
+    }
+    with open(os.path.join(HERE, f"{name}_summary.json"), "w") as f:
+        json.dump(meta, f, indent=1)
+        f.write("\n")
+    print(name, meta, flush=True)
+
+
 def write(name):
+    if name == "c4s":
+        return write_mixed(name, 1_000_000, 4)
     n, c, L, k, seed, first, count, sampled = WORKLOADS[name]
     t0 = time.time()
     res, placements = O.enumerate_space(n, c, L, k, seed, first, count, sampled=sampled)

@@ -1,0 +1,119 @@
+"""Parity of the GPU genetic algorithm (ga_breed, ga_hamming, ga_run) with the
+oracle: children, fitness and per-generation statistics are integers and must
+match exactly."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from oracle import oracle as O  # noqa: E402
+from paper_2205_15311_gb300 import binding as J  # noqa: E402
+from paper_2205_15311_gb300 import workloads as W  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    torch.cuda.init()
+    yield
+
+
+CASES = [
+    dict(selection=0, tournament=4, crossover=0, rate=0.01),
+    dict(selection=0, tournament=1, crossover=1, rate=0.2),
+    dict(selection=1, tournament=1, crossover=2, rate=0.05),
+    dict(selection=1, tournament=1, crossover=1, rate=0.0),
+    dict(selection=0, tournament=16, crossover=2, rate=1.5),
+]
+
+
+@pytest.mark.parametrize("case", CASES)
+@pytest.mark.parametrize("n,c", [(3, 8), (2, 4), (4, 8)])
+def test_breed_matches_oracle(case, n, c):
+    N = 3001
+    parents = W.random_genomes(N, n, c, seed=21)
+    fitness = (np.arange(N) * 7919 % 97).astype(np.int32)
+    fitness[::5] = 0
+    thr = J.poisson_thresholds(case["rate"])
+    ga = J.make_ga(n, c, 77, selection=case["selection"], tournament=case["tournament"],
+                   crossover=case["crossover"], crossover_threshold=0xC0000000, mutation_thresholds=thr)
+    for gen in (0, 5, (1 << 24) - 1):
+        want = O.ga_breed(parents, fitness, gen, n=n, c=c, seed=77, selection=case["selection"],
+                          tournament=case["tournament"], crossover=case["crossover"],
+                          crossover_threshold=0xC0000000, mutation_thresholds=thr)
+        host = np.zeros(N, np.uint64)
+        J.breed(ga, parents, fitness, gen, host)
+        assert np.array_equal(host, want)
+        dp = torch.from_numpy(parents.view(np.int64)).cuda()
+        df = torch.from_numpy(fitness).cuda()
+        dc = torch.zeros(N, dtype=torch.int64, device="cuda")
+        J.breed(ga, dp, df, gen, dc)
+        torch.cuda.synchronize()
+        assert np.array_equal(dc.cpu().numpy().view(np.uint64), want)
+
+
+def test_hamming_fitness():
+    g = W.random_genomes(10000, 3, 8, seed=2)
+    f = np.zeros(10000, np.int32)
+    J.hamming(g, f)
+    assert np.array_equal(f, np.array([O.hamming(int(v)) for v in g], np.int32))
+
+
+def _oracle_ga(pop, gens, fit_fn, **kw):
+    best, total = [], []
+    for gen in range(gens):
+        f = fit_fn(pop)
+        best.append(int(f.max()))
+        total.append(int(f.sum()))
+        pop = O.ga_breed(pop, f, gen, **kw)
+    return pop, best, total
+
+
+def test_ga_run_fujiyama_matches_oracle():
+    """The paper's test bed: Hamming-weight fitness, population 512."""
+    n, c, N, gens = 3, 8, 512, 40
+    thr = J.poisson_thresholds(0.02)
+    pop0 = W.random_genomes(N, n, c, seed=31)
+    kw = dict(n=n, c=c, seed=5, selection=0, tournament=4, crossover=1, crossover_threshold=0x80000000,
+              mutation_thresholds=thr)
+    want_pop, want_best, want_total = _oracle_ga(pop0, gens, lambda p: np.array([O.hamming(int(v)) for v in p],
+                                                                                np.int32), **kw)
+    ga = J.make_ga(n, c, 5, selection=0, tournament=4, crossover=1, crossover_threshold=0x80000000,
+                   mutation_thresholds=thr)
+    pop = torch.from_numpy(pop0.view(np.int64).copy()).cuda()
+    best = np.zeros(gens, np.int32)
+    total = np.zeros(gens, np.int64)
+    J.run_ga(ga, pop, gens, fitness_kind=J.FITNESS_HAMMING, best=best, total=total)
+    assert best.tolist() == want_best and total.tolist() == want_total
+    assert np.array_equal(pop.cpu().numpy().view(np.uint64), want_pop)
+    assert want_best[-1] > want_best[0]  # selection on the single Fujiyama peak climbs
+
+
+def test_ga_run_shape_fitness_matches_oracle():
+    """Fitness = size of the deterministic bounded shape (S_{3,8}, 16 x 16, k = 20)."""
+    n, c, N, gens, L, k, cseed = 3, 8, 256, 6, 16, 20, 7
+    thr = J.poisson_thresholds(0.03)
+    pop0 = W.random_genomes(N, n, c, seed=41)
+
+    def fit(p):
+        out = []
+        for v in p:
+            r = O.classify(n, c, L, k, cseed, O.decode(int(v), n, c), int(v))
+            out.append(r["size"] if r["cls"] == O.DET_BOUNDED else 0)
+        return np.array(out, np.int32)
+
+    kw = dict(n=n, c=c, seed=9, selection=1, tournament=1, crossover=2, crossover_threshold=0x40000000,
+              mutation_thresholds=thr)
+    want_pop, want_best, want_total = _oracle_ga(pop0, gens, fit, **kw)
+    ga = J.make_ga(n, c, 9, selection=1, tournament=1, crossover=2, crossover_threshold=0x40000000,
+                   mutation_thresholds=thr)
+    pop = torch.from_numpy(pop0.view(np.int64).copy()).cuda()
+    best = torch.zeros(gens, dtype=torch.int32, device="cuda")
+    total = torch.zeros(gens, dtype=torch.int64, device="cuda")
+    J.run_ga(ga, pop, gens, fitness_kind=J.FITNESS_SHAPE, L=L, k=k, seed=cseed, best=best, total=total)
+    torch.cuda.synchronize()
+    assert best.cpu().tolist() == want_best and total.cpu().tolist() == want_total
+    assert np.array_equal(pop.cpu().numpy().view(np.uint64), want_pop)

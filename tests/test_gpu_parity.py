@@ -30,7 +30,7 @@ def _cuda():
 
 
 def _dev_enumerate(n, c, L, k, seed, first, count, sampled=False, hist_cap=1 << 16):
-    out = torch.empty(max(count, 1) * 8, dtype=torch.uint8, device="cuda")
+    out = torch.full((max(count, 1) * 8,), 0xEE, dtype=torch.uint8, device="cuda")  # poisoned
     hist = torch.empty(hist_cap * 32, dtype=torch.uint8, device="cuda")
     hlen = torch.zeros(1, dtype=torch.int32, device="cuda")
     J.enumerate_space(n, c, L, k, seed, first, count, sampled=sampled, out=out, hist=hist, hist_len=hlen,
@@ -129,22 +129,54 @@ def test_ragged_counts(count):
     assert m == len(_oracle_hist(ref, np.arange(first, first + count, dtype=np.uint64)))
 
 
-def test_mixed_records_match_oracle():
-    colours, shapes = W.mixed_records(20000, seed=4)
-    ids = np.arange(20000, dtype=np.uint64) * np.uint64(7919) + np.uint64(5)
+def _mixed_run(colours, shapes, ids=None, per_shape=False, hist_cap=1 << 14):
+    N = colours.shape[0]
     dc = torch.from_numpy(colours).cuda()
     ds = torch.from_numpy(shapes).cuda()
-    di = torch.from_numpy(ids.view(np.int64)).cuda()
-    out = torch.empty(20000 * 8, dtype=torch.uint8, device="cuda")
-    hist = torch.empty((1 << 14) * 32, dtype=torch.uint8, device="cuda")
+    di = None if ids is None else torch.from_numpy(ids.view(np.int64)).cuda()
+    out = torch.full((N * 8,), 0xEE, dtype=torch.uint8, device="cuda")  # poisoned: every result must be written
+    hist = torch.empty(hist_cap * 32, dtype=torch.uint8, device="cuda")
     hlen = torch.zeros(1, dtype=torch.int32, device="cuda")
-    J.classify_batch(dc, seed=4, shapes=ds, stream_ids=di, out=out, hist=hist, hist_len=hlen, hist_cap=1 << 14,
-                     sync=True)
-    res = J.results_view(out)
-    ref, _ = O.classify_batch(colours, shapes=shapes, seed=4, ids=ids)
-    assert np.array_equal(res, ref)
+    J.classify_batch(dc, seed=4, shapes=ds, stream_ids=di, out=out, hist=hist, hist_len=hlen, hist_cap=hist_cap,
+                     sync=True, per_shape=per_shape)
     m = int(hlen.item())
-    assert _hist_rows(J.hist_view(hist, m)) == _hist_rows(_oracle_hist(ref, ids))
+    return J.results_view(out), J.hist_view(hist, m)
+
+
+def test_mixed_records_match_oracle():
+    """Mixed n, c, L, k in one persistent launch, with several CTA plans, and as
+    per-size fixed launches: all equal the oracle."""
+    colours, shapes = W.mixed_records(20000, seed=4)
+    ids = np.arange(20000, dtype=np.uint64) * np.uint64(7919) + np.uint64(5)
+    ref, _ = O.classify_batch(colours, shapes=shapes, seed=4, ids=ids)
+    want_hist = _hist_rows(_oracle_hist(ref, ids))
+    old_plan = J.get_mixed_plan()
+    try:
+        for plan in ((2, 4, 2), (1, 0, 0), (1, 2, 1), (1, 0, 5), (4, 2, 2)):
+            J.set_mixed_plan(*plan)
+            res, hist = _mixed_run(colours, shapes, ids)
+            assert np.array_equal(res, ref), plan
+            assert _hist_rows(hist) == want_hist
+        for bad in ((0, 1, 3), (0, 0, 8), (3, 3, 3)):
+            with pytest.raises(J.JatamError):
+                J.set_mixed_plan(*bad)
+    finally:
+        J.set_mixed_plan(*old_plan)
+    res, hist = _mixed_run(colours, shapes, ids, per_shape=True)
+    assert np.array_equal(res, ref)
+    assert _hist_rows(hist) == want_hist
+
+
+def test_mixed_1e6_matches_golden():
+    """A million mixed-size tile sets: SHA-256 of the results equals the oracle's."""
+    gold = json.load(open(os.path.join(GOLDEN, "c4s_summary.json")))
+    colours, shapes = W.mixed_records(1_000_000, seed=4)
+    assert hashlib.sha256(colours.tobytes() + shapes.tobytes()).hexdigest() == gold["inputs_sha256"]
+    for per_shape in (False, True):
+        res, hist = _mixed_run(colours, shapes, per_shape=per_shape)
+        assert np.bincount(res["cls"], minlength=4).tolist() == gold["class_counts"]
+        assert hashlib.sha256(res.tobytes()).hexdigest() == gold["results_sha256"]
+        assert len(hist) == gold["distinct_keys"]
 
 
 def test_uniform_records_all_tile_counts():
@@ -246,3 +278,36 @@ def test_results_do_not_depend_on_the_launch_shape():
         assert np.array_equal(res, base)
     finally:
         J.set_tuning(n, c, L, 8, 8)
+
+
+def test_graph_replay_equals_direct_launches():
+    """JATAM_GRAPH: the first call captures the kernel sequence, later calls with
+    the same arguments replay it; results equal the direct launches."""
+    n, c, L, k, seed = 3, 8, 32, 20, 3
+    first, count = 777, 50000
+    base, hbase, _ = _dev_enumerate(n, c, L, k, seed, first, count, sampled=True)
+    out = torch.empty(count * 8, dtype=torch.uint8, device="cuda")
+    hist = torch.empty((1 << 16) * 32, dtype=torch.uint8, device="cuda")
+    hlen = torch.zeros(1, dtype=torch.int32, device="cuda")
+    for _ in range(3):
+        out.zero_()
+        J.enumerate_space(n, c, L, k, seed, first, count, sampled=True, out=out, hist=hist, hist_len=hlen,
+                          hist_cap=1 << 16, sync=True, graph=True)
+        assert np.array_equal(J.results_view(out)[:count], base)
+        assert np.array_equal(J.hist_view(hist, int(hlen.item())), hbase)
+    colours, shapes = W.mixed_records(30000, seed=4)
+    ref, _ = _mixed_run(colours, shapes)
+    dc, ds = torch.from_numpy(colours).cuda(), torch.from_numpy(shapes).cuda()
+    o2 = torch.empty(30000 * 8, dtype=torch.uint8, device="cuda")
+    for per_shape in (False, True, False):
+        o2.zero_()
+        J.classify_batch(dc, seed=4, shapes=ds, out=o2, sync=True, per_shape=per_shape, graph=True)
+        assert np.array_equal(J.results_view(o2), ref)
+    g = torch.from_numpy(W.random_genomes(8192, 3, 8, seed=5).view(np.int64)).cuda()
+    f1 = torch.empty(8192, dtype=torch.int32, device="cuda")
+    f2 = torch.empty(8192, dtype=torch.int32, device="cuda")
+    J.evaluate_genomes(g, f1, n=3, c=8, L=16, k=20, seed=5, sync=True)
+    for _ in range(2):
+        f2.zero_()
+        J.evaluate_genomes(g, f2, n=3, c=8, L=16, k=20, seed=5, sync=True, graph=True)
+        assert torch.equal(f1, f2)
