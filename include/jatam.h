@@ -216,6 +216,59 @@ int ga_poisson_thresholds(double rate, uint32_t thresholds[4]);
 int ga_run(const jatam_ga_config *ga, const jatam_config *cls, int fitness_kind, uint64_t N, uint32_t generations,
            uint64_t *population, int32_t *best, int64_t *total, void *stream);
 
+/* ---- surrogate network (a learned pre-screen; the paper has no network) ----
+ * A multilayer perceptron over the 36 bits of an S_{3,8} genome (feature j =
+ * bit 35 - j): 36 -> 256 -> 256 -> 8, ReLU, softmax cross-entropy over the 8
+ * phenotype classes {unbounded, local non-determinism, steric
+ * non-determinism, deterministic bounded of size 1, 2-3, 4-7, 8-15, >= 16}.
+ * Products run on bfloat16 tensor cores with float32 accumulation; the master
+ * parameters and Adam (beta 0.9 / 0.999, eps 1e-8) are float32.  Parameters
+ * form one float32 vector: W1 [48][256] (input rows 36..47 unused), b1 [256],
+ * W2 [256][256], b2 [256], W3 [256][8], b3 [8] -- JATAM_MLP_NPARAM floats. */
+#define JATAM_MLP_NPARAM 80392
+typedef struct jatam_mlp jatam_mlp;
+
+/* Create a network with capacity for batches of up to max_batch genomes;
+ * its parameters start at zero (set them with jatam_mlp_set_params). */
+int jatam_mlp_create(uint64_t max_batch, jatam_mlp **net);
+void jatam_mlp_destroy(jatam_mlp *net);
+/* params: [JATAM_MLP_NPARAM] float32, host or device; set also resets Adam. */
+int jatam_mlp_set_params(jatam_mlp *net, const float *params, void *stream);
+int jatam_mlp_get_params(jatam_mlp *net, float *params, void *stream);
+/*
+ * One training step on a batch: forward, loss, backward; then Adam with
+ * learning rate lr unless lr == 0.  genomes [B] (36-bit, host or device),
+ * labels [B] uint8 classes 0..7.  loss (host float, may be NULL) receives the
+ * mean cross-entropy before the update; grads (NULL or [JATAM_MLP_NPARAM]
+ * float32, host or device) receives the gradient of that loss.  Synchronises
+ * when loss or grads is host memory.
+ */
+int jatam_mlp_train_step(jatam_mlp *net, const uint64_t *genomes, const uint8_t *labels, uint64_t B, float lr,
+                         float *loss, float *grads, void *stream);
+/* logits [N][8] float32 (host or device) for genomes [N] (N <= max_batch). */
+int jatam_mlp_predict(jatam_mlp *net, const uint64_t *genomes, uint64_t N, float *logits, void *stream);
+
+/* Training data for the network, on the device: labels[i] = class of
+ * results[i] (the 8 classes above); out[i] = genomes[i] of S_{n,c} written as
+ * an S_{3,8} genome (its tiles first, then all-zero tiles, each colour in 3
+ * bits; an all-zero tile never binds, so the classification is unchanged). */
+int jatam_mlp_labels(const jatam_result *results, uint64_t N, uint8_t *labels, void *stream);
+int jatam_embed_genomes(const uint64_t *genomes, uint64_t N, int n, int c, uint64_t *out, void *stream);
+
+/*
+ * ga_run_screened -- ga_run with the network as a pre-screen (shape fitness):
+ * each generation breeds ratio x N candidate children (child indices
+ * 0 .. ratio N - 1 of ga_breed), scores each with the network's expected
+ * shape size (class probabilities times 0, 0, 0, 1, 2.5, 5.5, 11.5, 20) and
+ * keeps the N best (ties: lower index) as the next population, which the
+ * plain classification then evaluates: every reported fitness is simulated,
+ * the network only decides which candidates get simulated.  ratio x N must fit
+ * the network's max_batch.
+ */
+int ga_run_screened(const jatam_ga_config *ga, const jatam_config *cls, uint64_t N, uint32_t generations,
+                    uint32_t ratio, jatam_mlp *net, uint64_t *population, int32_t *best, int64_t *total,
+                    void *stream);
+
 /*
  * jatam_philox -- Philox4x32-10 (Salmon et al., SC'11) as computed by the
  * classification kernels, for checking the draws: for each of N records

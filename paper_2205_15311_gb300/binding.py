@@ -81,6 +81,24 @@ def lib():
             getattr(L, f).restype = ctypes.c_int
         L.jatam_enumerate_noalloc.argtypes = [_VP, _U64, _U64, _VP, _VP]
         L.jatam_enumerate_noalloc.restype = ctypes.c_int
+        L.jatam_mlp_create.argtypes = [_U64, ctypes.POINTER(_VP)]
+        L.jatam_mlp_create.restype = ctypes.c_int
+        L.jatam_mlp_destroy.argtypes = [_VP]
+        L.jatam_mlp_destroy.restype = None
+        L.jatam_mlp_set_params.argtypes = [_VP, _VP, _VP]
+        L.jatam_mlp_set_params.restype = ctypes.c_int
+        L.jatam_mlp_get_params.argtypes = [_VP, _VP, _VP]
+        L.jatam_mlp_get_params.restype = ctypes.c_int
+        L.jatam_mlp_train_step.argtypes = [_VP, _VP, _VP, _U64, ctypes.c_float, _VP, _VP, _VP]
+        L.jatam_mlp_train_step.restype = ctypes.c_int
+        L.jatam_mlp_predict.argtypes = [_VP, _VP, _U64, _VP, _VP]
+        L.jatam_mlp_predict.restype = ctypes.c_int
+        L.jatam_mlp_labels.argtypes = [_VP, _U64, _VP, _VP]
+        L.jatam_mlp_labels.restype = ctypes.c_int
+        L.jatam_embed_genomes.argtypes = [_VP, _U64, ctypes.c_int, ctypes.c_int, _VP, _VP]
+        L.jatam_embed_genomes.restype = ctypes.c_int
+        L.ga_run_screened.argtypes = [_VP, _VP, _U64, _U32, _U32, _VP, _VP, _VP, _VP, _VP]
+        L.ga_run_screened.restype = ctypes.c_int
         L.ga_breed.argtypes = [_VP, _VP, _VP, _U64, _U32, _VP, _VP]
         L.ga_breed.restype = ctypes.c_int
         L.ga_hamming.argtypes = [_VP, _U64, _VP, _VP]
@@ -154,6 +172,42 @@ def ga_poisson_thresholds(rate, thresholds):
 
 def ga_run(ga, cls, fitness_kind, N, generations, population, best, total, stream):
     return lib().ga_run(ga, cls, fitness_kind, N, generations, population, best, total, stream)
+
+
+def jatam_mlp_create(max_batch, net):
+    return lib().jatam_mlp_create(max_batch, net)
+
+
+def jatam_mlp_destroy(net):
+    lib().jatam_mlp_destroy(net)
+
+
+def jatam_mlp_set_params(net, params, stream):
+    return lib().jatam_mlp_set_params(net, params, stream)
+
+
+def jatam_mlp_get_params(net, params, stream):
+    return lib().jatam_mlp_get_params(net, params, stream)
+
+
+def jatam_mlp_train_step(net, genomes, labels, B, lr, loss, grads, stream):
+    return lib().jatam_mlp_train_step(net, genomes, labels, B, lr, loss, grads, stream)
+
+
+def jatam_mlp_predict(net, genomes, N, logits, stream):
+    return lib().jatam_mlp_predict(net, genomes, N, logits, stream)
+
+
+def jatam_mlp_labels(results, N, labels, stream):
+    return lib().jatam_mlp_labels(results, N, labels, stream)
+
+
+def jatam_embed_genomes(genomes, N, n, c, out, stream):
+    return lib().jatam_embed_genomes(genomes, N, n, c, out, stream)
+
+
+def ga_run_screened(ga, cls, N, generations, ratio, net, population, best, total, stream):
+    return lib().ga_run_screened(ga, cls, N, generations, ratio, net, population, best, total, stream)
 
 
 def jatam_set_mixed_plan(w32, w16, w8):
@@ -366,3 +420,81 @@ def run_ga(ga, population, generations, *, fitness_kind=FITNESS_SHAPE, L=16, k=2
     cls = make_config(ga.n, ga.c, L, k, seed)
     return check(ga_run(ctypes.addressof(ga), ctypes.addressof(cls), int(fitness_kind), int(population.shape[0]),
                         int(generations), _addr(population), _addr(best), _addr(total), _stream_handle(stream)))
+
+
+# ---------------------------------------------------------------------------
+# surrogate network
+# ---------------------------------------------------------------------------
+MLP_NPARAM = 80392
+MLP_SHAPES = (("W1", (48, 256)), ("b1", (256,)), ("W2", (256, 256)), ("b2", (256,)), ("W3", (256, 8)), ("b3", (8,)))
+
+
+def flatten_params(p):
+    return np.concatenate([np.asarray(p[k], np.float32).reshape(-1) for k, _ in MLP_SHAPES]).astype(np.float32)
+
+
+def unflatten_params(v):
+    out, o = {}, 0
+    for k, shp in MLP_SHAPES:
+        n = int(np.prod(shp))
+        out[k] = np.asarray(v[o: o + n], np.float64).reshape(shp)
+        o += n
+    return out
+
+
+class Surrogate:
+    """Owner of a jatam_mlp handle (argument marshalling only)."""
+
+    def __init__(self, max_batch):
+        h = ctypes.c_void_p()
+        check(jatam_mlp_create(int(max_batch), ctypes.byref(h)))
+        self.h = h
+
+    def close(self):
+        if self.h:
+            jatam_mlp_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_params(self, flat, stream=None):
+        flat = np.ascontiguousarray(flat, np.float32) if not hasattr(flat, "data_ptr") else flat
+        check(jatam_mlp_set_params(self.h, _addr(flat), _stream_handle(stream)))
+
+    def get_params(self, stream=None):
+        out = np.zeros(MLP_NPARAM, np.float32)
+        check(jatam_mlp_get_params(self.h, out.ctypes.data, _stream_handle(stream)))
+        return out
+
+    def train_step(self, genomes, labels, lr, grads=None, stream=None):
+        loss = ctypes.c_float(0.0)
+        check(jatam_mlp_train_step(self.h, _addr(genomes), _addr(labels), int(genomes.shape[0]), float(lr),
+                                   ctypes.addressof(loss), _addr(grads), _stream_handle(stream)))
+        return float(loss.value)
+
+    def predict(self, genomes, logits, stream=None):
+        check(jatam_mlp_predict(self.h, _addr(genomes), int(genomes.shape[0]), _addr(logits),
+                                _stream_handle(stream)))
+
+
+def labels_of(results, labels, stream=None):
+    """Device results (uint8 view, 8 B per genotype) -> device class labels."""
+    N = int(results.numel() // 8) if hasattr(results, "numel") else int(results.shape[0])
+    return check(jatam_mlp_labels(_addr(results), N, _addr(labels), _stream_handle(stream)))
+
+
+def embed(genomes, n, c, out, stream=None):
+    return check(jatam_embed_genomes(_addr(genomes), int(genomes.shape[0]), int(n), int(c), _addr(out),
+                                     _stream_handle(stream)))
+
+
+def run_ga_screened(ga, population, generations, ratio, net, *, L=16, k=20, seed=0, best=None, total=None,
+                    stream=None):
+    cls = make_config(ga.n, ga.c, L, k, seed)
+    return check(ga_run_screened(ctypes.addressof(ga), ctypes.addressof(cls), int(population.shape[0]),
+                                 int(generations), int(ratio), net.h, _addr(population), _addr(best), _addr(total),
+                                 _stream_handle(stream)))

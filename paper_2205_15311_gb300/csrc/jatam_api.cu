@@ -17,6 +17,14 @@
 
 using namespace jatam;
 
+struct jatam_mlp {
+    int device = -1;
+    jatam::MlpBuffers b{};
+    int t = 0;              // Adam steps taken
+    void *stage = nullptr;  // host inputs: genomes then labels; host outputs
+    size_t stage_bytes = 0;
+};
+
 namespace {
 
 thread_local std::string g_last_error;
@@ -96,6 +104,10 @@ struct Workspace {
     std::map<std::string, cudaGraphExec_t> graphs;  // captured calls, by argument set
     void *ga_buf = nullptr;   // ga_run / ga_breed: fitness, children, cumsum, stats
     size_t ga_bytes = 0;
+    void *screen_buf = nullptr;  // ga_run_screened: candidates, chosen indices, scores
+    size_t screen_bytes = 0;
+    unsigned long long *screen_cand = nullptr, *screen_idx = nullptr;
+    float *screen_score = nullptr;
     cudaStream_t capture = nullptr;                  // private stream used only for capturing
 };
 
@@ -216,6 +228,7 @@ Tuning tuning_for(int S, int n, int c)
     if (S == 32 && it == g_tuned.end()) t.warps = 2;  // the 32 x 32 lattice takes 33 KB of shared memory per warp
     if (g_warps_override) t.warps = g_warps_override;
     if (g_stop_override) t.stop_at = g_stop_override;
+    while (t.warps > 1 && classify_smem_bytes(S, t.warps) > 200 * 1024) --t.warps;  // what fits on one SM
     return t;
 }
 
@@ -260,6 +273,7 @@ int run(Workspace *w, LaunchArgs a, int S, jatam_result *out, int32_t *fitness, 
             if (w->stage_hist_cap < hist_cap) {
                 if (w->stage_hist) cudaFree(w->stage_hist);
         if (w->ga_buf) cudaFree(w->ga_buf);
+        if (w->screen_buf) cudaFree(w->screen_buf);
                 w->stage_hist = nullptr;
                 w->stage_hist_cap = 0;
                 cudaError_t e = cudaMalloc(&w->stage_hist, (size_t)hist_cap * sizeof(jatam_hist_entry));
@@ -682,6 +696,7 @@ int ga_breed(const jatam_ga_config *ga, const uint64_t *parents, const int32_t *
     g.fitness = df;
     g.cumsum = sc.cumsum;
     g.N = N;
+    g.Nc = N;
     g.generation = generation;
     g.children = dc;
     CUDA_TRY(launch_ga_breed(g, st));
@@ -733,8 +748,14 @@ int ga_poisson_thresholds(double rate, uint32_t thresholds[4])
     return JATAM_OK;
 }
 
-int ga_run(const jatam_ga_config *ga, const jatam_config *cls, int fitness_kind, uint64_t N, uint32_t generations,
-           uint64_t *population, int32_t *best, int64_t *total, void *stream)
+}  // extern "C"
+
+namespace {
+// The GA loop; with a network, each generation breeds ratio x N candidates,
+// the network scores them and the best N (the only ones simulated) form the
+// next population.
+int ga_loop(const jatam_ga_config *ga, const jatam_config *cls, int fitness_kind, uint64_t N, uint32_t generations,
+            uint64_t *population, int32_t *best, int64_t *total, void *stream, jatam_mlp *net, uint32_t ratio)
 {
     GaArgs g;
     {
@@ -754,6 +775,18 @@ int ga_run(const jatam_ga_config *ga, const jatam_config *cls, int fitness_kind,
         int rc = workspace(&w);
         if (rc) return rc;
         if (kind_of(population, w->device) != K_DEVICE) return fail(JATAM_EINVAL, "population must be device memory");
+        if (net) {
+            const unsigned long long M = (unsigned long long)N * ratio;
+            if (ratio < 1 || (long long)M > net->b.cap || M > (1ull << 26))
+                return fail(JATAM_EINVAL, "ratio x N must be at least N and fit the network's batch capacity");
+            const size_t need = (size_t)M * 8 * 2 + (size_t)M * 4 + 1024;
+            rc = grow(&w->screen_buf, &w->screen_bytes, need);
+            if (rc) return rc;
+            char *p = static_cast<char *>(w->screen_buf);
+            w->screen_cand = reinterpret_cast<unsigned long long *>(p);
+            w->screen_idx = reinterpret_cast<unsigned long long *>(p + (((size_t)M * 8 + 255) & ~size_t(255)));
+            w->screen_score = reinterpret_cast<float *>(p + 2 * (((size_t)M * 8 + 255) & ~size_t(255)));
+        }
     }
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     const Kind kb = kind_of(best, w->device), kt = kind_of(total, w->device);
@@ -787,10 +820,21 @@ int ga_run(const jatam_ga_config *ga, const jatam_config *cls, int fitness_kind,
         gg.fitness = sc.fitness;
         gg.cumsum = sc.cumsum;
         gg.N = N;
+        gg.Nc = N;
         gg.generation = gen;
         gg.children = sc.children;
-        CUDA_TRY(launch_ga_breed(gg, st));
-        CUDA_TRY(cudaMemcpyAsync(pop, sc.children, (size_t)N * 8, cudaMemcpyDeviceToDevice, st));
+        if (!net) {
+            CUDA_TRY(launch_ga_breed(gg, st));
+            CUDA_TRY(cudaMemcpyAsync(pop, sc.children, (size_t)N * 8, cudaMemcpyDeviceToDevice, st));
+        } else {
+            const unsigned long long M = (unsigned long long)N * ratio;
+            gg.Nc = M;
+            gg.children = w->screen_cand;
+            CUDA_TRY(launch_ga_breed(gg, st));
+            CUDA_TRY(mlp_forward(net->b, w->screen_cand, (long long)M, st));
+            CUDA_TRY(launch_screen(net->b.logits, (long long)M, (long long)N, w->screen_score, w->screen_idx,
+                                   w->screen_cand, pop, st));
+        }
         CUDA_TRY(cudaEventRecord(w->last, st));
         if (!host_stats.empty()) CUDA_TRY(cudaStreamSynchronize(st));  // host_stats must not be read early
     }
@@ -800,6 +844,198 @@ int ga_run(const jatam_ga_config *ga, const jatam_config *cls, int fitness_kind,
             if (kt == K_HOST) total[gen] = host_stats[2 * gen + 1];
         }
     }
+    return JATAM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int ga_run(const jatam_ga_config *ga, const jatam_config *cls, int fitness_kind, uint64_t N, uint32_t generations,
+           uint64_t *population, int32_t *best, int64_t *total, void *stream)
+{
+    return ga_loop(ga, cls, fitness_kind, N, generations, population, best, total, stream, nullptr, 1);
+}
+
+int ga_run_screened(const jatam_ga_config *ga, const jatam_config *cls, uint64_t N, uint32_t generations,
+                    uint32_t ratio, jatam_mlp *net, uint64_t *population, int32_t *best, int64_t *total, void *stream)
+{
+    if (!net) {
+        std::lock_guard<std::mutex> lock(g_mutex);
+        return fail(JATAM_EINVAL, "net is required");
+    }
+    return ga_loop(ga, cls, JATAM_GA_FITNESS_SHAPE, N, generations, population, best, total, stream, net, ratio);
+}
+
+int jatam_mlp_create(uint64_t max_batch, jatam_mlp **net)
+{
+    std::lock_guard<std::mutex> lock(g_mutex);
+    g_last_error.clear();
+    if (!net || max_batch == 0 || max_batch > (1ull << 26)) return fail(JATAM_EINVAL, "net required, 1 <= max_batch <= 2^26");
+    if (MLP_NPARAM != JATAM_MLP_NPARAM) return fail(JATAM_EINVAL, "parameter count mismatch");
+    jatam_mlp *m = new jatam_mlp();
+    CUDA_TRY(cudaGetDevice(&m->device));
+    const long long P = MLP_NPARAM, Bc = (long long)max_batch;
+    MlpBuffers &b = m->b;
+    b.cap = Bc;
+    auto alloc = [&](void **p, size_t bytes) -> int {
+        cudaError_t e = cudaMalloc(p, bytes);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return fail(JATAM_ENOMEM, "cudaMalloc of %zu bytes failed", bytes);
+        }
+        return JATAM_OK;
+    };
+    int rc = 0;
+    rc |= alloc((void **)&b.p, P * 4); rc |= alloc((void **)&b.grad, P * 4);
+    rc |= alloc((void **)&b.m, P * 4); rc |= alloc((void **)&b.v, P * 4);
+    rc |= alloc((void **)&b.wq, P * 2);
+    rc |= alloc((void **)&b.x, Bc * MLP_PAD * 2); rc |= alloc((void **)&b.h1, Bc * MLP_H * 2);
+    rc |= alloc((void **)&b.h2, Bc * MLP_H * 2); rc |= alloc((void **)&b.dq, Bc * MLP_OUT * 2);
+    rc |= alloc((void **)&b.dh1, Bc * MLP_H * 2); rc |= alloc((void **)&b.dh2, Bc * MLP_H * 2);
+    rc |= alloc((void **)&b.logits, Bc * MLP_OUT * 4); rc |= alloc((void **)&b.d, Bc * MLP_OUT * 4);
+    rc |= alloc((void **)&b.loss, 16);
+    if (rc) {
+        jatam_mlp_destroy(m);
+        return JATAM_ENOMEM;
+    }
+    CUDA_TRY(cudaMemset(b.p, 0, P * 4));
+    CUDA_TRY(cudaMemset(b.m, 0, P * 4));
+    CUDA_TRY(cudaMemset(b.v, 0, P * 4));
+    CUDA_TRY(cudaMemset(b.wq, 0, P * 2));
+    *net = m;
+    return JATAM_OK;
+}
+
+void jatam_mlp_destroy(jatam_mlp *m)
+{
+    if (!m) return;
+    MlpBuffers &b = m->b;
+    void *ptrs[] = {b.p, b.grad, b.m, b.v, b.wq, b.x, b.h1, b.h2, b.dq, b.dh1, b.dh2, b.logits, b.d, b.loss, m->stage};
+    cudaDeviceSynchronize();
+    for (void *p : ptrs)
+        if (p) cudaFree(p);
+    delete m;
+}
+
+namespace {
+int mlp_stage(jatam_mlp *m, size_t bytes) { return grow(&m->stage, &m->stage_bytes, bytes); }
+}  // namespace
+
+int jatam_mlp_set_params(jatam_mlp *m, const float *params, void *stream)
+{
+    std::lock_guard<std::mutex> lock(g_mutex);
+    g_last_error.clear();
+    if (!m || !params) return fail(JATAM_EINVAL, "net and params required");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const size_t bytes = (size_t)MLP_NPARAM * 4;
+    CUDA_TRY(cudaMemcpyAsync(m->b.p, params, bytes, cudaMemcpyDefault, st));
+    CUDA_TRY(cudaMemsetAsync(m->b.m, 0, bytes, st));
+    CUDA_TRY(cudaMemsetAsync(m->b.v, 0, bytes, st));
+    m->t = 0;
+    CUDA_TRY(mlp_refresh_bf16(m->b, st));
+    CUDA_TRY(cudaStreamSynchronize(st));
+    return JATAM_OK;
+}
+
+int jatam_mlp_get_params(jatam_mlp *m, float *params, void *stream)
+{
+    std::lock_guard<std::mutex> lock(g_mutex);
+    g_last_error.clear();
+    if (!m || !params) return fail(JATAM_EINVAL, "net and params required");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    CUDA_TRY(cudaMemcpyAsync(params, m->b.p, (size_t)MLP_NPARAM * 4, cudaMemcpyDefault, st));
+    CUDA_TRY(cudaStreamSynchronize(st));
+    return JATAM_OK;
+}
+
+int jatam_mlp_train_step(jatam_mlp *m, const uint64_t *genomes, const uint8_t *labels, uint64_t B, float lr,
+                         float *loss, float *grads, void *stream)
+{
+    std::lock_guard<std::mutex> lock(g_mutex);
+    g_last_error.clear();
+    if (!m || !genomes || !labels || B == 0 || (long long)B > m->b.cap)
+        return fail(JATAM_EINVAL, "net, genomes, labels required and 1 <= B <= max_batch");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const Kind kg = kind_of(genomes, m->device), kl = kind_of(labels, m->device);
+    const unsigned long long *dg = reinterpret_cast<const unsigned long long *>(genomes);
+    const uint8_t *dl = labels;
+    const size_t gb = ((size_t)B * 8 + 255) & ~size_t(255);
+    if (kg == K_HOST || kl == K_HOST) {
+        int rc = mlp_stage(m, gb + B + 256);
+        if (rc) return rc;
+        char *s8 = static_cast<char *>(m->stage);
+        if (kg == K_HOST) {
+            CUDA_TRY(cudaMemcpyAsync(s8, genomes, (size_t)B * 8, cudaMemcpyHostToDevice, st));
+            dg = reinterpret_cast<const unsigned long long *>(s8);
+        }
+        if (kl == K_HOST) {
+            CUDA_TRY(cudaMemcpyAsync(s8 + gb, labels, B, cudaMemcpyHostToDevice, st));
+            dl = reinterpret_cast<const uint8_t *>(s8 + gb);
+        }
+    }
+    CUDA_TRY(mlp_forward(m->b, dg, (long long)B, st));
+    CUDA_TRY(mlp_backward(m->b, dl, (long long)B, st));
+    if (grads) CUDA_TRY(cudaMemcpyAsync(grads, m->b.grad, (size_t)MLP_NPARAM * 4, cudaMemcpyDefault, st));
+    float h_loss = 0.f;
+    if (loss) CUDA_TRY(cudaMemcpyAsync(&h_loss, m->b.loss, 4, cudaMemcpyDeviceToHost, st));
+    if (lr != 0.f) {
+        m->t += 1;
+        CUDA_TRY(mlp_adam(m->b, lr, m->t, st));
+    }
+    if (loss || (grads && kind_of(grads, m->device) == K_HOST) || kg == K_HOST || kl == K_HOST) {
+        CUDA_TRY(cudaStreamSynchronize(st));
+        if (loss) *loss = h_loss;
+    }
+    return JATAM_OK;
+}
+
+int jatam_mlp_predict(jatam_mlp *m, const uint64_t *genomes, uint64_t N, float *logits, void *stream)
+{
+    std::lock_guard<std::mutex> lock(g_mutex);
+    g_last_error.clear();
+    if (!m || !genomes || !logits || N == 0 || (long long)N > m->b.cap)
+        return fail(JATAM_EINVAL, "net, genomes, logits required and 1 <= N <= max_batch");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const Kind kg = kind_of(genomes, m->device), ko = kind_of(logits, m->device);
+    const unsigned long long *dg = reinterpret_cast<const unsigned long long *>(genomes);
+    if (kg == K_HOST) {
+        int rc = mlp_stage(m, (size_t)N * 8);
+        if (rc) return rc;
+        CUDA_TRY(cudaMemcpyAsync(m->stage, genomes, (size_t)N * 8, cudaMemcpyHostToDevice, st));
+        dg = static_cast<const unsigned long long *>(m->stage);
+    }
+    CUDA_TRY(mlp_forward(m->b, dg, (long long)N, st));
+    CUDA_TRY(cudaMemcpyAsync(logits, m->b.logits, (size_t)N * MLP_OUT * 4, cudaMemcpyDefault, st));
+    if (kg == K_HOST || ko == K_HOST) CUDA_TRY(cudaStreamSynchronize(st));
+    return JATAM_OK;
+}
+
+int jatam_mlp_labels(const jatam_result *results, uint64_t N, uint8_t *labels, void *stream)
+{
+    std::lock_guard<std::mutex> lock(g_mutex);
+    g_last_error.clear();
+    if (N && (!results || !labels)) return fail(JATAM_EINVAL, "results and labels required");
+    int dev = 0;
+    CUDA_TRY(cudaGetDevice(&dev));
+    if (N && (kind_of(results, dev) != K_DEVICE || kind_of(labels, dev) != K_DEVICE))
+        return fail(JATAM_EINVAL, "results and labels must be device memory");
+    CUDA_TRY(launch_mlp_labels(results, (long long)N, labels, static_cast<cudaStream_t>(stream)));
+    return JATAM_OK;
+}
+
+int jatam_embed_genomes(const uint64_t *genomes, uint64_t N, int n, int c, uint64_t *out, void *stream)
+{
+    std::lock_guard<std::mutex> lock(g_mutex);
+    g_last_error.clear();
+    if (N && (!genomes || !out)) return fail(JATAM_EINVAL, "genomes and out required");
+    if (n < 1 || n > 3 || !(c == 2 || c == 4 || c == 8)) return fail(JATAM_EINVAL, "n 1..3 and c in {2, 4, 8}");
+    int dev = 0;
+    CUDA_TRY(cudaGetDevice(&dev));
+    if (N && (kind_of(genomes, dev) != K_DEVICE || kind_of(out, dev) != K_DEVICE))
+        return fail(JATAM_EINVAL, "genomes and out must be device memory");
+    CUDA_TRY(launch_embed(reinterpret_cast<const unsigned long long *>(genomes), (long long)N, n, log2c(c),
+                          reinterpret_cast<unsigned long long *>(out), static_cast<cudaStream_t>(stream)));
     return JATAM_OK;
 }
 
@@ -1074,6 +1310,7 @@ void jatam_shutdown(void)
         if (w->stage_aux) cudaFree(w->stage_aux);
         if (w->stage_hist) cudaFree(w->stage_hist);
         if (w->ga_buf) cudaFree(w->ga_buf);
+        if (w->screen_buf) cudaFree(w->screen_buf);
         cudaEventDestroy(w->last);
         cudaEventDestroy(w->k_start);
         cudaEventDestroy(w->k_stop);

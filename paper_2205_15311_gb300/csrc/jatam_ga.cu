@@ -68,7 +68,7 @@ __device__ unsigned long long select_parent(const GaArgs &g, ChildDraws &d, int 
 __global__ void __launch_bounds__(256) ga_breed_kernel(const GaArgs g)
 {
     const unsigned long long i = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x;
-    if (i >= g.N) return;
+    if (i >= g.Nc) return;
     ChildDraws d;
     d.k0 = g.key0;
     d.k1 = g.key1;
@@ -166,13 +166,13 @@ __global__ void ga_stats_reset_kernel(long long *stats)
 
 cudaError_t launch_ga_breed(const GaArgs &g, cudaStream_t st)
 {
-    if (g.N == 0) return cudaSuccess;
+    if (g.N == 0 || g.Nc == 0) return cudaSuccess;
     if (g.selection == 1) {
         ga_scan_kernel<<<1, 1024, 0, st>>>(g.fitness, g.N, const_cast<unsigned long long *>(g.cumsum));
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }
-    ga_breed_kernel<<<(unsigned)((g.N + 255) / 256), 256, 0, st>>>(g);
+    ga_breed_kernel<<<(unsigned)((g.Nc + 255) / 256), 256, 0, st>>>(g);
     return cudaGetLastError();
 }
 

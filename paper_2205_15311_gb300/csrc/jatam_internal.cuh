@@ -98,7 +98,8 @@ struct GaArgs {
     const unsigned long long *parents;
     const int32_t *fitness;
     const unsigned long long *cumsum;  // roulette: workspace for the prefix sum of the fitness
-    unsigned long long N;
+    unsigned long long N;         // parents
+    unsigned long long Nc;        // children to breed (child indices 0 .. Nc-1)
     uint32_t generation;
     unsigned long long *children;
 };
@@ -106,6 +107,32 @@ cudaError_t launch_ga_breed(const GaArgs &g, cudaStream_t st);
 cudaError_t launch_ga_hamming(const unsigned long long *genomes, unsigned long long n, int32_t *fitness,
                               cudaStream_t st);
 cudaError_t launch_ga_stats(const int32_t *fitness, unsigned long long n, long long *stats, cudaStream_t st);
+
+// surrogate network (jatam_mlp.cu): 36 -> 256 -> 256 -> 8, inputs padded to 48
+constexpr int MLP_IN = 36, MLP_PAD = 48, MLP_H = 256, MLP_OUT = 8;
+extern const long long MLP_OFF_W1, MLP_OFF_B1, MLP_OFF_W2, MLP_OFF_B2, MLP_OFF_W3, MLP_OFF_B3, MLP_NPARAM;
+
+}  // namespace jatam
+#include <cuda_bf16.h>
+namespace jatam {
+
+struct MlpBuffers {
+    float *p, *grad, *m, *v;     // [MLP_NPARAM] master parameters, gradients, Adam moments
+    __nv_bfloat16 *wq;           // [MLP_NPARAM] bfloat16 copy of the parameters (weights used by the products)
+    long long cap;               // batch capacity of the activation buffers
+    __nv_bfloat16 *x, *h1, *h2, *dq, *dh1, *dh2;
+    float *logits, *d, *loss;
+};
+cudaError_t mlp_forward(const MlpBuffers &b, const unsigned long long *genomes, long long B, cudaStream_t st);
+cudaError_t mlp_backward(const MlpBuffers &b, const uint8_t *labels, long long B, cudaStream_t st);
+cudaError_t mlp_adam(const MlpBuffers &b, float lr, int t, cudaStream_t st);
+cudaError_t mlp_refresh_bf16(const MlpBuffers &b, cudaStream_t st);
+cudaError_t launch_mlp_labels(const jatam_result *res, long long n, uint8_t *labels, cudaStream_t st);
+cudaError_t launch_embed(const unsigned long long *in, long long n, int tiles, int bits_per_colour,
+                         unsigned long long *out, cudaStream_t st);
+// scores of n candidates from their logits; idx = the `keep` best, chosen = cand[idx]
+cudaError_t launch_screen(const float *logits, long long n, long long keep, float *score, unsigned long long *idx,
+                          const unsigned long long *cand, unsigned long long *chosen, cudaStream_t st);
 
 // the message returned by jatam_last_error() for the calling thread
 void set_last_error(const char *msg);

@@ -1,0 +1,474 @@
+// jatam_mlp.cu -- the surrogate network 36 -> 256 -> 256 -> 8 (ReLU, softmax
+// cross-entropy) on bfloat16 tensor cores with float32 accumulation: forward,
+// backward and Adam for training, forward for inference.
+//
+// Every matrix product of the network -- forward and the three weight and two
+// activation gradients of the backward pass -- is one call of a tile GEMM
+// C[M x N] = A[M x K] B[K x N] whose operands are bfloat16 with arbitrary row
+// and column strides (so transposes cost nothing) and whose epilogue is fused:
+// bias + ReLU to bfloat16 (hidden layers), bias to float32 (logits), a ReLU
+// derivative mask to bfloat16 (activation gradients), or plain float32
+// (weight gradients).  The product itself is mma.sync.m16n8k16 (bf16 x bf16 ->
+// f32) from shared-memory tiles.
+#include <cstdint>
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include "jatam_internal.cuh"
+
+namespace jatam {
+namespace {
+
+constexpr int TM = 64, TN = 64, TK = 16;  // CTA tile; 4 warps of 32 x 32
+constexpr int KP = TK + 8;                // padded row (halfs) of the shared tiles
+
+enum Epi : int { EPI_F32 = 0, EPI_BIAS_F32 = 1, EPI_BIAS_RELU_BF16 = 2, EPI_MASK_BF16 = 3 };
+
+struct GemmArgs {
+    const __nv_bfloat16 *A;
+    long long a_m, a_k;  // element (m, k) at A[m * a_m + k * a_k]
+    const __nv_bfloat16 *B;
+    long long b_k, b_n;  // element (k, n) at B[k * b_k + n * b_n]
+    int M, N, K;
+    int epi;
+    const float *bias;             // [N] for the bias epilogues
+    const __nv_bfloat16 *mask;     // [M x N] row-major: keep where mask > 0 (EPI_MASK_BF16)
+    float *Cf;                     // [M x N] row-major float32 output
+    __nv_bfloat16 *Cb;             // [M x N] row-major bfloat16 output
+};
+
+__device__ __forceinline__ void mma_bf16(float (&c)[4], const uint32_t (&a)[4], const uint32_t (&b)[2])
+{
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0, %1, %2, %3}, {%4, %5, %6, %7}, {%8, %9}, "
+        "{%0, %1, %2, %3};\n"
+        : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+}
+
+__global__ void __launch_bounds__(128) gemm_bf16_kernel(const GemmArgs g)
+{
+    __shared__ __align__(16) __nv_bfloat16 As[TM][KP];  // [m][k]
+    __shared__ __align__(16) __nv_bfloat16 Bs[TN][KP];  // [n][k]
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int m0 = blockIdx.y * TM, n0 = blockIdx.x * TN;
+    const int wm = (warp >> 1) * 32, wn = (warp & 1) * 32;  // warp's 32 x 32 sub-tile
+    const int gq = lane >> 2, tq = lane & 3;
+    float acc[2][4][4];
+#pragma unroll
+    for (int i = 0; i < 2; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+#pragma unroll
+            for (int r = 0; r < 4; ++r) acc[i][j][r] = 0.f;
+    const __nv_bfloat16 zero = __float2bfloat16(0.f);
+    for (int k0 = 0; k0 < g.K; k0 += TK) {
+        // stage the A and B tiles (zero outside the matrices)
+        for (int e = tid; e < TM * TK; e += blockDim.x) {
+            const int m = e / TK, k = e % TK;
+            const int gm = m0 + m, gk = k0 + k;
+            As[m][k] = (gm < g.M && gk < g.K) ? g.A[gm * g.a_m + gk * g.a_k] : zero;
+        }
+        for (int e = tid; e < TN * TK; e += blockDim.x) {
+            const int n = e / TK, k = e % TK;
+            const int gn = n0 + n, gk = k0 + k;
+            Bs[n][k] = (gn < g.N && gk < g.K) ? g.B[gk * g.b_k + gn * g.b_n] : zero;
+        }
+        __syncthreads();
+        uint32_t af[2][4], bf[4][2];
+#pragma unroll
+        for (int i = 0; i < 2; ++i) {
+            const int r = wm + 16 * i + gq;
+            af[i][0] = *reinterpret_cast<const uint32_t *>(&As[r][2 * tq]);
+            af[i][1] = *reinterpret_cast<const uint32_t *>(&As[r + 8][2 * tq]);
+            af[i][2] = *reinterpret_cast<const uint32_t *>(&As[r][2 * tq + 8]);
+            af[i][3] = *reinterpret_cast<const uint32_t *>(&As[r + 8][2 * tq + 8]);
+        }
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int cidx = wn + 8 * j + gq;
+            bf[j][0] = *reinterpret_cast<const uint32_t *>(&Bs[cidx][2 * tq]);
+            bf[j][1] = *reinterpret_cast<const uint32_t *>(&Bs[cidx][2 * tq + 8]);
+        }
+#pragma unroll
+        for (int i = 0; i < 2; ++i)
+#pragma unroll
+            for (int j = 0; j < 4; ++j) mma_bf16(acc[i][j], af[i], bf[j]);
+        __syncthreads();
+    }
+    // epilogue: accumulator element r sits at row gq (+8 for r >= 2), column 2 tq + (r & 1)
+#pragma unroll
+    for (int i = 0; i < 2; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+#pragma unroll
+            for (int r = 0; r < 4; ++r) {
+                const int m = m0 + wm + 16 * i + gq + (r >= 2 ? 8 : 0);
+                const int n = n0 + wn + 8 * j + 2 * tq + (r & 1);
+                if (m >= g.M || n >= g.N) continue;
+                float v = acc[i][j][r];
+                const long long o = (long long)m * g.N + n;
+                switch (g.epi) {
+                case EPI_F32: g.Cf[o] = v; break;
+                case EPI_BIAS_F32: g.Cf[o] = v + g.bias[n]; break;
+                case EPI_BIAS_RELU_BF16: g.Cb[o] = __float2bfloat16_rn(fmaxf(v + g.bias[n], 0.f)); break;
+                default: g.Cb[o] = __float2bfloat16_rn(__bfloat162float(g.mask[o]) > 0.f ? v : 0.f); break;
+                }
+            }
+}
+
+// features: bit (35 - j) of the genome for j < 36, zero for 36..47
+__global__ void features_kernel(const unsigned long long *genomes, long long n, __nv_bfloat16 *x)
+{
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n * MLP_PAD;
+         i += (long long)gridDim.x * blockDim.x) {
+        const long long r = i / MLP_PAD;
+        const int j = (int)(i % MLP_PAD);
+        const float v = (j < MLP_IN) ? (float)((genomes[r] >> (MLP_IN - 1 - j)) & 1ull) : 0.f;
+        x[i] = __float2bfloat16_rn(v);
+    }
+}
+
+// softmax cross-entropy on float32 logits: d = (softmax - onehot) / B, as
+// float32 (for the bias gradient) and bfloat16 (for the products); the loss
+// summed into *loss (divided by B)
+__global__ void softmax_ce_kernel(const float *logits, const uint8_t *labels, long long B, float *d,
+                                  __nv_bfloat16 *dq, float *loss)
+{
+    const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    float l = 0.f;
+    if (i < B) {
+        const float *z = logits + i * MLP_OUT;
+        float mx = z[0];
+        for (int c = 1; c < MLP_OUT; ++c) mx = fmaxf(mx, z[c]);
+        float e[MLP_OUT], s = 0.f;
+        for (int c = 0; c < MLP_OUT; ++c) {
+            e[c] = expf(z[c] - mx);
+            s += e[c];
+        }
+        const int y = labels[i];
+        for (int c = 0; c < MLP_OUT; ++c) {
+            const float v = (e[c] / s - (c == y ? 1.f : 0.f)) / (float)B;
+            d[i * MLP_OUT + c] = v;
+            dq[i * MLP_OUT + c] = __float2bfloat16_rn(v);
+        }
+        l = (logf(s) + mx - z[y]) / (float)B;
+    }
+    for (int off = 16; off > 0; off >>= 1) l += __shfl_xor_sync(0xffffffffu, l, off);
+    if ((threadIdx.x & 31) == 0) atomicAdd(loss, l);
+}
+
+// column sums of a [B x N] matrix (float32 or bfloat16) into out[N]
+template <typename T>
+__global__ void colsum_kernel(const T *a, long long B, int N, float *out)
+{
+    const int n = blockIdx.x;
+    float s = 0.f;
+    for (long long r = threadIdx.x; r < B; r += blockDim.x) s += (float)a[r * N + n];
+    __shared__ float red[256];
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int off = blockDim.x / 2; off > 0; off >>= 1) {
+        if ((int)threadIdx.x < off) red[threadIdx.x] += red[threadIdx.x + off];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) out[n] = red[0];
+}
+
+template <>
+__global__ void colsum_kernel<__nv_bfloat16>(const __nv_bfloat16 *a, long long B, int N, float *out)
+{
+    const int n = blockIdx.x;
+    float s = 0.f;
+    for (long long r = threadIdx.x; r < B; r += blockDim.x) s += __bfloat162float(a[r * N + n]);
+    __shared__ float red[256];
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int off = blockDim.x / 2; off > 0; off >>= 1) {
+        if ((int)threadIdx.x < off) red[threadIdx.x] += red[threadIdx.x + off];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) out[n] = red[0];
+}
+
+// Adam on the float32 master parameters, then their bfloat16 copies
+__global__ void adam_kernel(float *p, const float *g, float *m, float *v, long long n, float lr, float b1, float b2,
+                            float eps, float c1, float c2, __nv_bfloat16 *pq)
+{
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const float gi = g[i];
+        const float mi = b1 * m[i] + (1.f - b1) * gi;
+        const float vi = b2 * v[i] + (1.f - b2) * gi * gi;
+        m[i] = mi;
+        v[i] = vi;
+        const float pi = p[i] - lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+        p[i] = pi;
+        pq[i] = __float2bfloat16_rn(pi);
+    }
+}
+
+__global__ void to_bf16_kernel(const float *p, long long n, __nv_bfloat16 *pq)
+{
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        pq[i] = __float2bfloat16_rn(p[i]);
+}
+
+__global__ void zero_kernel(float *p, long long n)
+{
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        p[i] = 0.f;
+}
+
+cudaError_t gemm(const GemmArgs &g, cudaStream_t st)
+{
+    const dim3 grid((g.N + TN - 1) / TN, (g.M + TM - 1) / TM);
+    gemm_bf16_kernel<<<grid, 128, 0, st>>>(g);
+    return cudaGetLastError();
+}
+
+unsigned grid_for(long long n) { return (unsigned)((n + 255) / 256 < 4096 ? (n + 255) / 256 : 4096); }
+
+}  // namespace
+
+// offsets of the six parameter tensors in the flat parameter vector
+const long long MLP_OFF_W1 = 0;
+const long long MLP_OFF_B1 = MLP_OFF_W1 + (long long)MLP_PAD * MLP_H;
+const long long MLP_OFF_W2 = MLP_OFF_B1 + MLP_H;
+const long long MLP_OFF_B2 = MLP_OFF_W2 + (long long)MLP_H * MLP_H;
+const long long MLP_OFF_W3 = MLP_OFF_B2 + MLP_H;
+const long long MLP_OFF_B3 = MLP_OFF_W3 + (long long)MLP_H * MLP_OUT;
+const long long MLP_NPARAM = MLP_OFF_B3 + MLP_OUT;
+
+cudaError_t mlp_forward(const MlpBuffers &b, const unsigned long long *genomes, long long B, cudaStream_t st)
+{
+    features_kernel<<<grid_for(B * MLP_PAD), 256, 0, st>>>(genomes, B, b.x);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    const __nv_bfloat16 *Wq = b.wq;
+    GemmArgs g{};
+    // h1 = relu(x W1 + b1)
+    g = GemmArgs{b.x, MLP_PAD, 1, Wq + MLP_OFF_W1, MLP_H, 1, (int)B, MLP_H, MLP_PAD, EPI_BIAS_RELU_BF16,
+                 b.p + MLP_OFF_B1, nullptr, nullptr, b.h1};
+    if ((e = gemm(g, st)) != cudaSuccess) return e;
+    // h2 = relu(h1 W2 + b2)
+    g = GemmArgs{b.h1, MLP_H, 1, Wq + MLP_OFF_W2, MLP_H, 1, (int)B, MLP_H, MLP_H, EPI_BIAS_RELU_BF16,
+                 b.p + MLP_OFF_B2, nullptr, nullptr, b.h2};
+    if ((e = gemm(g, st)) != cudaSuccess) return e;
+    // logits = h2 W3 + b3
+    g = GemmArgs{b.h2, MLP_H, 1, Wq + MLP_OFF_W3, MLP_OUT, 1, (int)B, MLP_OUT, MLP_H, EPI_BIAS_F32,
+                 b.p + MLP_OFF_B3, nullptr, b.logits, nullptr};
+    return gemm(g, st);
+}
+
+cudaError_t mlp_backward(const MlpBuffers &b, const uint8_t *labels, long long B, cudaStream_t st)
+{
+    cudaError_t e;
+    zero_kernel<<<1, 32, 0, st>>>(b.loss, 1);
+    softmax_ce_kernel<<<(unsigned)((B + 255) / 256), 256, 0, st>>>(b.logits, labels, B, b.d, b.dq, b.loss);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    float *G = b.grad;
+    GemmArgs g{};
+    // dW3 = h2^T dq  [256 x 8], K = B
+    g = GemmArgs{b.h2, 1, MLP_H, b.dq, MLP_OUT, 1, MLP_H, MLP_OUT, (int)B, EPI_F32, nullptr, nullptr,
+                 G + MLP_OFF_W3, nullptr};
+    if ((e = gemm(g, st)) != cudaSuccess) return e;
+    colsum_kernel<float><<<MLP_OUT, 256, 0, st>>>(b.d, B, MLP_OUT, G + MLP_OFF_B3);
+    // dh2 = (dq W3^T) * [h2 > 0]  [B x 256], K = 8
+    g = GemmArgs{b.dq, MLP_OUT, 1, b.wq + MLP_OFF_W3, 1, MLP_OUT, (int)B, MLP_H, MLP_OUT, EPI_MASK_BF16, nullptr,
+                 b.h2, nullptr, b.dh2};
+    if ((e = gemm(g, st)) != cudaSuccess) return e;
+    // dW2 = h1^T dh2  [256 x 256]
+    g = GemmArgs{b.h1, 1, MLP_H, b.dh2, MLP_H, 1, MLP_H, MLP_H, (int)B, EPI_F32, nullptr, nullptr, G + MLP_OFF_W2,
+                 nullptr};
+    if ((e = gemm(g, st)) != cudaSuccess) return e;
+    colsum_kernel<__nv_bfloat16><<<MLP_H, 256, 0, st>>>(b.dh2, B, MLP_H, G + MLP_OFF_B2);
+    // dh1 = (dh2 W2^T) * [h1 > 0]  [B x 256]
+    g = GemmArgs{b.dh2, MLP_H, 1, b.wq + MLP_OFF_W2, 1, MLP_H, (int)B, MLP_H, MLP_H, EPI_MASK_BF16, nullptr, b.h1,
+                 nullptr, b.dh1};
+    if ((e = gemm(g, st)) != cudaSuccess) return e;
+    // dW1 = x^T dh1  [48 x 256]
+    g = GemmArgs{b.x, 1, MLP_PAD, b.dh1, MLP_H, 1, MLP_PAD, MLP_H, (int)B, EPI_F32, nullptr, nullptr, G + MLP_OFF_W1,
+                 nullptr};
+    if ((e = gemm(g, st)) != cudaSuccess) return e;
+    colsum_kernel<__nv_bfloat16><<<MLP_H, 256, 0, st>>>(b.dh1, B, MLP_H, G + MLP_OFF_B1);
+    return cudaGetLastError();
+}
+
+cudaError_t mlp_adam(const MlpBuffers &b, float lr, int t, cudaStream_t st)
+{
+    const float b1 = 0.9f, b2 = 0.999f, eps = 1e-8f;
+    const float c1 = 1.f - powf(b1, (float)t), c2 = 1.f - powf(b2, (float)t);
+    adam_kernel<<<grid_for(MLP_NPARAM), 256, 0, st>>>(b.p, b.grad, b.m, b.v, MLP_NPARAM, lr, b1, b2, eps, c1, c2,
+                                                       b.wq);
+    return cudaGetLastError();
+}
+
+cudaError_t mlp_refresh_bf16(const MlpBuffers &b, cudaStream_t st)
+{
+    to_bf16_kernel<<<grid_for(MLP_NPARAM), 256, 0, st>>>(b.p, MLP_NPARAM, b.wq);
+    return cudaGetLastError();
+}
+
+}  // namespace jatam
+
+namespace jatam {
+namespace {
+
+// class label of a classification result (the network's 8 outputs)
+__global__ void labels_kernel(const jatam_result *res, long long n, uint8_t *labels)
+{
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const jatam_result r = res[i];
+        uint8_t y;
+        if (r.cls == JATAM_UNBOUNDED) y = 0;
+        else if (r.cls == JATAM_ND_LOCAL) y = 1;
+        else if (r.cls == JATAM_ND_STERIC) y = 2;
+        else y = r.size >= 16 ? 7 : r.size >= 8 ? 6 : r.size >= 4 ? 5 : r.size >= 2 ? 4 : 3;
+        labels[i] = y;
+    }
+}
+
+// packed genomes of S_{n,c} -> S_{3,8} (tiles beyond n all-zero, colours kept)
+__global__ void embed_kernel(const unsigned long long *in, long long count, int n, int b, unsigned long long *out)
+{
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < count;
+         i += (long long)gridDim.x * blockDim.x) {
+        const unsigned long long g = in[i];
+        unsigned long long o = 0;
+        for (int t = 0; t < n; ++t)
+            for (int e = 0; e < 4; ++e) {
+                const unsigned long long colour = (g >> (b * (4 * (n - 1 - t) + (3 - e)))) & ((1ull << b) - 1ull);
+                o |= colour << (3 * (4 * (3 - 1 - t) + (3 - e)));
+            }
+        out[i] = o;
+    }
+}
+
+// expected shape size under the predicted class probabilities
+__global__ void score_kernel(const float *logits, long long n, float *score)
+{
+    const float value[MLP_OUT] = {0.f, 0.f, 0.f, 1.f, 2.5f, 5.5f, 11.5f, 20.f};
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const float *z = logits + i * MLP_OUT;
+        float mx = z[0];
+        for (int c = 1; c < MLP_OUT; ++c) mx = fmaxf(mx, z[c]);
+        float s = 0.f, e = 0.f;
+        for (int c = 0; c < MLP_OUT; ++c) {
+            const float p = expf(z[c] - mx);
+            s += p;
+            e += p * value[c];
+        }
+        score[i] = e / s;
+    }
+}
+
+// Indices of the `keep` largest non-negative scores among n (ties: lower index
+// first), in increasing index order; one CTA of 1024 threads, radix select on
+// the float bits (monotone for non-negative floats) then an ordered compaction.
+__global__ void __launch_bounds__(1024) topn_kernel(const float *score, long long n, long long keep,
+                                                    unsigned long long *idx_out)
+{
+    __shared__ unsigned hist[256];
+    __shared__ unsigned prefix_s, want_s;
+    __shared__ unsigned long long scan[1024];
+    const uint32_t *key = reinterpret_cast<const uint32_t *>(score);
+    unsigned prefix = 0, mask = 0;
+    unsigned long long want = (unsigned long long)keep;  // rank (from the top) still to place inside the prefix
+    for (int shift = 24; shift >= 0; shift -= 8) {
+        for (int i = threadIdx.x; i < 256; i += blockDim.x) hist[i] = 0;
+        __syncthreads();
+        for (long long i = threadIdx.x; i < n; i += blockDim.x) {
+            const uint32_t k = key[i];
+            if ((k & mask) == prefix) atomicAdd(&hist[(k >> shift) & 255u], 1u);
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            unsigned long long acc = 0;
+            int d = 255;
+            for (; d > 0; --d) {
+                if (acc + hist[d] >= want) break;
+                acc += hist[d];
+            }
+            prefix_s = prefix | ((unsigned)d << shift);
+            want_s = (unsigned)(want - acc);
+        }
+        __syncthreads();
+        prefix = prefix_s;
+        want = want_s;
+        mask |= 255u << shift;
+        __syncthreads();
+    }
+    // prefix is now the key of the keep-th largest; `want` of its copies are taken, lowest indices first
+    const uint32_t thr = prefix;
+    const long long per = (n + blockDim.x - 1) / blockDim.x;
+    const long long lo = threadIdx.x * per, hi = min(n, lo + per);
+    unsigned long long above = 0, equal = 0;
+    for (long long i = lo; i < hi; ++i) {
+        above += key[i] > thr;
+        equal += key[i] == thr;
+    }
+    // exclusive scan of (equal) to rank the ties, and of (above + chosen ties) for positions
+    scan[threadIdx.x] = equal;
+    __syncthreads();
+    for (int off = 1; off < (int)blockDim.x; off <<= 1) {
+        const unsigned long long v = threadIdx.x >= (unsigned)off ? scan[threadIdx.x - off] : 0ull;
+        __syncthreads();
+        scan[threadIdx.x] += v;
+        __syncthreads();
+    }
+    const unsigned long long eq_before = scan[threadIdx.x] - equal;
+    __syncthreads();
+    const unsigned long long take_eq = eq_before >= want ? 0 : min(equal, want - eq_before);
+    scan[threadIdx.x] = above + take_eq;
+    __syncthreads();
+    for (int off = 1; off < (int)blockDim.x; off <<= 1) {
+        const unsigned long long v = threadIdx.x >= (unsigned)off ? scan[threadIdx.x - off] : 0ull;
+        __syncthreads();
+        scan[threadIdx.x] += v;
+        __syncthreads();
+    }
+    unsigned long long pos = scan[threadIdx.x] - (above + take_eq);
+    unsigned long long eq_left = take_eq;
+    for (long long i = lo; i < hi; ++i) {
+        const uint32_t k = key[i];
+        if (k > thr || (k == thr && eq_left > 0)) {
+            if (k == thr) --eq_left;
+            idx_out[pos++] = (unsigned long long)i;
+        }
+    }
+}
+
+__global__ void gather_kernel(const unsigned long long *src, const unsigned long long *idx, long long n,
+                              unsigned long long *dst)
+{
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        dst[i] = src[idx[i]];
+}
+
+unsigned grid_of(long long n) { return (unsigned)((n + 255) / 256 < 4096 ? (n + 255) / 256 : 4096); }
+
+}  // namespace
+
+cudaError_t launch_mlp_labels(const jatam_result *res, long long n, uint8_t *labels, cudaStream_t st)
+{
+    if (n) labels_kernel<<<grid_of(n), 256, 0, st>>>(res, n, labels);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_embed(const unsigned long long *in, long long n, int tiles, int bits_per_colour,
+                         unsigned long long *out, cudaStream_t st)
+{
+    if (n) embed_kernel<<<grid_of(n), 256, 0, st>>>(in, n, tiles, bits_per_colour, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_screen(const float *logits, long long n, long long keep, float *score, unsigned long long *idx,
+                          const unsigned long long *cand, unsigned long long *chosen, cudaStream_t st)
+{
+    score_kernel<<<grid_of(n), 256, 0, st>>>(logits, n, score);
+    topn_kernel<<<1, 1024, 0, st>>>(score, n, keep, idx);
+    gather_kernel<<<grid_of(keep), 256, 0, st>>>(cand, idx, keep, chosen);
+    return cudaGetLastError();
+}
+
+}  // namespace jatam
