@@ -418,6 +418,51 @@ uint32_t orc_shape_hash(const uint8_t *bitmap, int h, int w)
     return orc_oaat(bytes, nb);
 }
 
+/* The rotation-invariant variant of Section 2.5: hash each of the four
+ * rotations of the shape (each cropped, hashed as orc_shape_hash hashes a
+ * bitmap), sort the four hashes numerically, and hash the sorted hashes again
+ * (their 16 bytes, little endian) with one-at-a-time.  Mirror images are not
+ * identified. */
+uint32_t orc_c4_hash(const int32_t *xs, const int32_t *ys, int m)
+{
+    uint32_t hs[4];
+    uint8_t img[(2 * ORC_MAXL + 1) * (2 * ORC_MAXL + 1)];
+    for (int s = 0; s < 4; s++) {
+        int minx = 1 << 30, miny = 1 << 30, maxx = -(1 << 30), maxy = -(1 << 30);
+        for (int i = 0; i < m; i++) {
+            int tx, ty;
+            symmetry(s, xs[i], ys[i], &tx, &ty);
+            if (tx < minx) minx = tx;
+            if (ty < miny) miny = ty;
+            if (tx > maxx) maxx = tx;
+            if (ty > maxy) maxy = ty;
+        }
+        int h = maxy - miny + 1, w = maxx - minx + 1;
+        if (h < 1 || w < 1 || h > 2 * ORC_MAXL + 1 || w > 2 * ORC_MAXL + 1) return 0;
+        memset(img, 0, (size_t)h * (size_t)w);
+        for (int i = 0; i < m; i++) {
+            int tx, ty;
+            symmetry(s, xs[i], ys[i], &tx, &ty);
+            img[(ty - miny) * w + (tx - minx)] = 1;
+        }
+        hs[s] = orc_shape_hash(img, h, w);
+    }
+    for (int i = 1; i < 4; i++)
+        for (int j = i; j > 0 && hs[j - 1] > hs[j]; j--) {
+            uint32_t t = hs[j];
+            hs[j] = hs[j - 1];
+            hs[j - 1] = t;
+        }
+    uint8_t bytes[16];
+    for (int i = 0; i < 4; i++)
+        for (int b = 0; b < 4; b++) bytes[4 * i + b] = (uint8_t)(hs[i] >> (8 * b));
+    return orc_oaat(bytes, 16);
+}
+
+static int g_c4_hash = 0; /* hash mode of the classification calls below (0: D4 canonical form, 1: C4) */
+
+void orc_set_hash_mode(int c4) { g_c4_hash = c4 ? 1 : 0; }
+
 static uint32_t hash_of_grid(const grid *G)
 {
     int32_t xs[ORC_MAXL * ORC_MAXL], ys[ORC_MAXL * ORC_MAXL];
@@ -430,6 +475,7 @@ static uint32_t hash_of_grid(const grid *G)
                 ys[m] = y;
                 m++;
             }
+    if (g_c4_hash) return orc_c4_hash(xs, ys, m);
     int32_t h, w;
     orc_canonical(xs, ys, m, bm, &h, &w);
     return orc_shape_hash(bm, h, w);

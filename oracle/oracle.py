@@ -100,6 +100,10 @@ def lib():
             L.orc_poisson_thresholds.restype = ctypes.c_int
             L.orc_roulette_pick.argtypes = [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_uint64]
             L.orc_roulette_pick.restype = ctypes.c_uint64
+            L.orc_c4_hash.argtypes = [i32p, i32p, ctypes.c_int]
+            L.orc_c4_hash.restype = ctypes.c_uint32
+            L.orc_set_hash_mode.argtypes = [ctypes.c_int]
+            L.orc_set_hash_mode.restype = None
             L.orc_hamming.argtypes = [ctypes.c_uint64]
             L.orc_hamming.restype = ctypes.c_int
             _lib = L
@@ -304,3 +308,27 @@ def roulette_pick(weights, dart):
     """Index chosen by the cumulative search of the roulette wheel."""
     cs = np.cumsum(np.asarray(weights, dtype=np.uint64)).astype(np.uint64)
     return int(lib().orc_roulette_pick(cs.ctypes.data, cs.shape[0], int(dart)))
+
+
+def c4_hash(cells) -> int:
+    """The rotation-invariant hash variant of Section 2.5 (mirror images differ)."""
+    cells = list(cells)
+    xs = np.array([c[0] for c in cells] or [0], np.int32)
+    ys = np.array([c[1] for c in cells] or [0], np.int32)
+    return int(lib().orc_c4_hash(xs.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
+                                 ys.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), len(cells)))
+
+
+class hash_mode:
+    """Context manager: classify with the C4 hash variant (Section 2.5) instead
+    of the canonical form under the 8 symmetries."""
+
+    def __init__(self, c4: bool):
+        self.c4 = bool(c4)
+
+    def __enter__(self):
+        lib().orc_set_hash_mode(int(self.c4))
+        return self
+
+    def __exit__(self, *exc):
+        lib().orc_set_hash_mode(0)

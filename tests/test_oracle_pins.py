@@ -446,3 +446,30 @@ def test_edge_sizes():
         O.classify(2, 8, 33, 1, 1, [0] * 8, 0)
     with pytest.raises(ValueError):
         O.classify(2, 4, 16, 1, 1, [0, 0, 0, 4, 0, 0, 0, 0], 0)
+
+
+def test_c4_hash_counts_one_sided_polyominoes():
+    """The rotation-only variant of Section 2.5 identifies the four rotations of
+    a shape but not its mirror image: over the fixed polyominoes of size 1..7
+    it takes 1, 1, 2, 7, 18, 60, 196 values (one-sided polyominoes)."""
+    fixed = _fixed_polyominoes(7)
+    for m in range(1, 8):
+        hashes = {O.c4_hash(sorted(s)) for s in fixed[m]}
+        assert len(hashes) == [1, 1, 2, 7, 18, 60, 196][m - 1]
+    s_tet = [(1, 0), (2, 0), (0, 1), (1, 1)]
+    z_tet = [(0, 0), (1, 0), (1, 1), (2, 1)]
+    assert O.c4_hash(s_tet) != O.c4_hash(z_tet)
+    assert O.c4_hash(s_tet) == O.c4_hash([(-y, x) for (x, y) in s_tet])
+
+
+def test_c4_hash_mode_changes_only_the_hash():
+    n, c, L, k, seed = 2, 8, 12, 6, 2
+    first, count = 5 << 20, 3000
+    d4, _ = O.enumerate_space(n, c, L, k, seed, first, count)
+    with O.hash_mode(True):
+        c4, _ = O.enumerate_space(n, c, L, k, seed, first, count)
+    for f in ("cls", "decided_rep", "size"):
+        assert np.array_equal(d4[f], c4[f])
+    shaped = (d4["cls"] == O.DET_BOUNDED) | (d4["cls"] == O.ND_STERIC)
+    assert shaped.any() and not np.array_equal(d4["shape_hash"][shaped], c4["shape_hash"][shaped])
+    assert not c4["shape_hash"][~shaped].any()
