@@ -109,12 +109,23 @@ def measured_peaks():
 
 
 def algorithmic_ops(res_cls, res_rep, res_size, k, placements):
-    """Integer operations the method needs for one pass over the workload."""
+    """Integer operations the method as stated needs for one pass over the
+    workload: every replicate of every genotype simulated (the oracle's count)."""
     reps = np.where(res_rep >= k, k, res_rep.astype(np.int64) + 1).sum()
     shaped = (res_cls == 0) | (res_cls == 2)
     cells = res_size[shaped].astype(np.int64).sum()
     return (OPS_PER_PLACEMENT * placements + OPS_PER_REPLICATE * int(reps) + OPS_PER_GENOTYPE * res_cls.size
             + OPS_PER_SHAPED_CELL * int(cells))
+
+
+def executed_ops(work, res_cls, res_size):
+    """Integer operations of the work the growth kernel itself executed (its
+    counters): drawn and seed placements, genotypes taken by warps, and the
+    cells of the shapes it canonicalised (the pre-filter settles lone seeds)."""
+    shaped = ((res_cls == 0) | (res_cls == 2)) & (res_size > 1)
+    cells = res_size[shaped].astype(np.int64).sum()
+    return (OPS_PER_PLACEMENT * work["placements"] + OPS_PER_REPLICATE * work["seeds"]
+            + OPS_PER_GENOTYPE * work["genotypes"] + OPS_PER_SHAPED_CELL * int(cells))
 
 
 def measured_traffic(kernel_file):
@@ -327,6 +338,13 @@ def main():
         for _ in range(args.warmup):
             step()
     stream.synchronize()
+    # one untimed counted pass: the work the growth kernel executes per step
+    J.jatam_profile(3)
+    with torch.cuda.stream(stream):
+        step()
+    stream.synchronize()
+    work = J.work_counters()
+    J.jatam_profile(1)
 
     starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     stops = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
@@ -390,19 +408,26 @@ def main():
             placements = json.load(open(golden))["placements"]
         roofline = None
         kms = float(np.mean(kernel_ms))
+        ops = executed_ops(work, res["cls"], res["size"])
+        achieved = ops / (kms / 1e3) / 1e12
+        traffic = measured_traffic(os.path.join(ROOT, "paper_2205_15311_gb300", "csrc", "jatam_kernels.cu"))
+        if WORKLOAD != "s28_full":
+            traffic = None
+        roofline = {"bound": "alu", "achieved": round(achieved, 4), "peak": round(alu_peak, 2),
+                    "unit": "Tops/s", "frac": round(achieved / alu_peak, 4), "traffic": traffic,
+                    "kernel": f"classify_kernel<{8 if L <= 8 else 16 if L <= 16 else 32}>",
+                    "kernel_ms": round(kms, 4),
+                    "peak_source": f"{n_sms} SMs x 128 int32 lanes x {sm_max:.0f} MHz (MEASURED_PEAKS sm_max)",
+                    "executed": work,
+                    "lane_utilisation": round((work["placements"] + work["seeds"]) / max(work["lane_slots"], 1), 4),
+                    "hbm_gbs": round(count * 8 / (kms / 1e3) / 1e9, 1),
+                    "hbm_frac_of_measured": round(count * 8 / (kms / 1e3) / 1e9 / float(peaks.get("hbm_gbs", 6753.1)), 4)}
         if placements is not None:
-            ops = algorithmic_ops(res["cls"], res["decided_rep"], res["size"], k, placements)
-            achieved = ops / (kms / 1e3) / 1e12
-            traffic = measured_traffic(os.path.join(ROOT, "paper_2205_15311_gb300", "csrc", "jatam_kernels.cu"))
-            if WORKLOAD != "s28_full":
-                traffic = None
-            roofline = {"bound": "alu", "achieved": round(achieved, 4), "peak": round(alu_peak, 2),
-                        "unit": "Tops/s", "frac": round(achieved / alu_peak, 4), "traffic": traffic,
-                        "kernel": f"classify_kernel<{8 if L <= 8 else 16 if L <= 16 else 32}>",
-                        "kernel_ms": round(kms, 4),
-                        "peak_source": f"{n_sms} SMs x 128 int32 lanes x {sm_max:.0f} MHz (MEASURED_PEAKS sm_max)",
-                        "hbm_gbs": round(count * 8 / (kms / 1e3) / 1e9, 1),
-                        "hbm_frac_of_measured": round(count * 8 / (kms / 1e3) / 1e9 / float(peaks.get("hbm_gbs", 6753.1)), 4)}
+            # the same rate counted in the work of the process as the paper states it
+            # (all k replicates of every genotype, the oracle's placement count)
+            mops = algorithmic_ops(res["cls"], res["decided_rep"], res["size"], k, placements)
+            roofline["method_placements"] = placements
+            roofline["method_ops_frac"] = round(mops / (kms / 1e3) / 1e12 / alu_peak, 4)
         cpu = None
         if not args.no_cpu_baseline and world == 1:
             from oracle import oracle as O

@@ -66,6 +66,10 @@ extern "C" {
 #define JATAM_SYNC 0x2u    /* wait for the work to finish before returning */
 #define JATAM_PER_SHAPE 0x4u /* jatam_classify_batch with mixed shapes: one fixed launch per lattice size
                                 class instead of the single persistent launch */
+#define JATAM_C4_HASH 0x10u  /* the paper's rotation-only hash (Section 2.5): hash the 4 rotations of the
+                                cropped shape, sort the 4 hashes, hash them again (16 bytes, little endian);
+                                mirror images stay distinct.  Default: the canonical form under all 8
+                                symmetries of the square */
 #define JATAM_GRAPH 0x8u     /* capture the call's kernel sequence as a CUDA graph the first time a given
                                 set of arguments is seen, and replay it on later calls with the same set */
 
@@ -326,13 +330,23 @@ int jatam_get_mixed_plan(int *warps_32, int *warps_16, int *warps_8);
 int jatam_autotune_batch(const uint8_t *colours, const uint8_t *shapes, uint64_t N, uint64_t seed, void *stream);
 
 /*
- * jatam_profile -- when enable != 0, every later call records CUDA events
- * around its classification kernel on the call's stream; jatam_kernel_ms()
- * then waits for the last such pair and returns its elapsed milliseconds in
- * *ms (JATAM_EINVAL if no call has been profiled).
+ * jatam_profile -- enable is a bit set for every later call:
+ *   bit 0 (1): record CUDA events around the classification kernels on the
+ *              call's stream; jatam_kernel_ms() then waits for the last such
+ *              pair and returns its elapsed milliseconds in *ms
+ *              (JATAM_EINVAL if no call has been profiled);
+ *   bit 1 (2): count the work the classification kernels executed;
+ *              jatam_work_counters() waits for the last call and returns
+ *              [0] drawn placements, [1] seed placements (replicates grown),
+ *              [2] lane slots of the growth rounds (32 per warp round; the
+ *              lanes not placing are the SIMT idle share), [3] genotypes grown
+ *              by warps (those the seed-step pre-filter did not settle).
+ *              JATAM_EINVAL if the last call on the device was not counted.
+ * enable outside 0..3: JATAM_EINVAL.  The counters cost one ballot per round.
  */
 int jatam_profile(int enable);
 int jatam_kernel_ms(float *ms);
+int jatam_work_counters(uint64_t counters[4]);
 
 /*
  * jatam_enumerate_noalloc -- jatam_enumerate without any device allocation,

@@ -28,6 +28,7 @@ JATAM_SAMPLED = 0x1
 JATAM_SYNC = 0x2
 JATAM_PER_SHAPE = 0x4
 JATAM_GRAPH = 0x8
+JATAM_C4_HASH = 0x10
 JATAM_NOALLOC_MAX_COUNT = 1048576
 
 RESULT_DTYPE = np.dtype([("cls", "u1"), ("decided_rep", "u1"), ("size", "<u2"), ("shape_hash", "<u4")])
@@ -123,6 +124,8 @@ def lib():
         L.jatam_profile.restype = ctypes.c_int
         L.jatam_kernel_ms.argtypes = [ctypes.POINTER(ctypes.c_float)]
         L.jatam_kernel_ms.restype = ctypes.c_int
+        L.jatam_work_counters.argtypes = [ctypes.POINTER(ctypes.c_uint64)]
+        L.jatam_work_counters.restype = ctypes.c_int
         L.jatam_shutdown.argtypes = []
         L.jatam_shutdown.restype = None
         L.jatam_last_error.argtypes = []
@@ -242,6 +245,10 @@ def jatam_kernel_ms(ms):
     return lib().jatam_kernel_ms(ms)
 
 
+def jatam_work_counters(counters):
+    return lib().jatam_work_counters(counters)
+
+
 def jatam_shutdown():
     lib().jatam_shutdown()
 
@@ -283,10 +290,10 @@ def check(rc):
 
 
 def enumerate_space(n, c, L, k, seed, first, count, *, sampled=False, out=None, hist=None, hist_len=None,
-                    hist_cap=0, stream=None, sync=False, graph=False):
+                    hist_cap=0, stream=None, sync=False, graph=False, c4_hash=False):
     """jatam_enumerate on caller buffers (torch tensors or numpy arrays)."""
     cfg = make_config(n, c, L, k, seed, (JATAM_SAMPLED if sampled else 0) | (JATAM_SYNC if sync else 0)
-                      | (JATAM_GRAPH if graph else 0))
+                      | (JATAM_GRAPH if graph else 0) | (JATAM_C4_HASH if c4_hash else 0))
     return check(jatam_enumerate(ctypes.addressof(cfg), first, count, _addr(out), _addr(hist), hist_cap,
                                  _addr(hist_len), _stream_handle(stream)))
 
@@ -359,6 +366,15 @@ def last_kernel_ms() -> float:
     ms = ctypes.c_float(0.0)
     check(jatam_kernel_ms(ctypes.byref(ms)))
     return float(ms.value)
+
+
+def work_counters():
+    """Executed work of the last counted call (jatam_profile(2) first): drawn
+    placements, seed placements, lane slots of the growth rounds, genotypes
+    grown by warps."""
+    c = (ctypes.c_uint64 * 4)()
+    check(jatam_work_counters(c))
+    return {"placements": int(c[0]), "seeds": int(c[1]), "lane_slots": int(c[2]), "genotypes": int(c[3])}
 
 
 def merge_histograms(a, b):

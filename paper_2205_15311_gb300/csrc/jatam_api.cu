@@ -29,7 +29,7 @@ namespace {
 
 thread_local std::string g_last_error;
 std::mutex g_mutex;
-bool g_profile = false;
+int g_profile = 0;  // bit 0: events around the growth kernels; bit 1: executed-work counters
 int g_stop_override = 0;
 int g_warps_override = 0;
 
@@ -83,6 +83,8 @@ struct Workspace {
     Table table{};
     Compact compact{};
     unsigned long long *work_next = nullptr;
+    unsigned long long *stats = nullptr;  // [4] executed-work counters of the last counted call
+    bool stats_valid = false;
     unsigned *err = nullptr;
     unsigned *nkeys = nullptr;
     unsigned long long *list_count = nullptr;
@@ -156,6 +158,7 @@ int workspace(Workspace **out)
     CUDA_TRY(cudaMalloc(&w->compact.size_max, cap * 4));
     CUDA_TRY(cudaMalloc(&w->compact.size_min, cap * 4));
     CUDA_TRY(cudaMalloc(&w->work_next, 3 * 8));
+    CUDA_TRY(cudaMalloc(&w->stats, 4 * 8));
     CUDA_TRY(cudaMalloc(&w->err, 4));
     CUDA_TRY(cudaMalloc(&w->nkeys, 4));
     CUDA_TRY(cudaMalloc(&w->list_count, 3 * 8));
@@ -294,6 +297,7 @@ int run(Workspace *w, LaunchArgs a, int S, jatam_result *out, int32_t *fitness, 
     a.table = w->table;
     a.use_hist = hist ? 1 : 0;
     a.work_next = w->work_next;
+    a.stats = (g_profile & 2) ? w->stats : nullptr;
     a.err = w->err;
     const bool mixed = a.mode == MODE_RECORDS && a.shapes;
     const Tuning tune = force ? *force : tuning_for(S, mixed ? 0 : a.n, mixed ? 0 : a.c);
@@ -356,11 +360,12 @@ int run(Workspace *w, LaunchArgs a, int S, jatam_result *out, int32_t *fitness, 
     }
     long long pblocks = (long long)(n_items + 255) / 256;
     if (pblocks > 8LL * w->num_sms) pblocks = 8LL * w->num_sms;
-    const bool timed = g_profile || kernel_ms;
+    const bool timed = (g_profile & 1) || kernel_ms;
 
     // the device work of the call; `events` brackets the growth kernels
     auto enqueue = [&](cudaStream_t s, bool events) -> int {
         CUDA_TRY(launch_reset(w->work_next, w->nkeys, w->list_count, s));
+        if (a.stats) CUDA_TRY(cudaMemsetAsync(a.stats, 0, 4 * 8, s));
         if (n_items) CUDA_TRY(launch_prefilter(a, S, (int)pblocks, s));
         if (events) CUDA_TRY(cudaEventRecord(w->k_start, s));
         if (n_items && !mixed) CUDA_TRY(launch_classify(a, S, (int)blocks, warps, s));
@@ -398,7 +403,8 @@ int run(Workspace *w, LaunchArgs a, int S, jatam_result *out, int32_t *fitness, 
                                   a.use_hist, a.stop_at, (long long)a.list_stride, a.bucket, a.plan_w32, a.plan_w16,
                                   a.plan_w8, S, blocks, warps, per_shape, mixed_blocks, pblocks, hist_cap,
                                   fixed[0].blocks, fixed[0].warps, fixed[0].stop_at, fixed[1].blocks, fixed[1].warps,
-                                  fixed[1].stop_at, fixed[2].blocks, fixed[2].warps, fixed[2].stop_at};
+                                  fixed[1].stop_at, fixed[2].blocks, fixed[2].warps, fixed[2].stop_at,
+                                  a.stats ? 1 : 0};
         put(nums, sizeof nums);
         cudaGraphExec_t exec = nullptr;
         auto it = w->graphs.find(key);
@@ -429,6 +435,7 @@ int run(Workspace *w, LaunchArgs a, int S, jatam_result *out, int32_t *fitness, 
         if (timed) CUDA_TRY(cudaEventRecord(w->k_stop, st));
     }
     if (timed) w->k_valid = true;
+    w->stats_valid = a.stats != nullptr;
     if (o.host_out && n_items)
         CUDA_TRY(cudaMemcpyAsync(out, o.out_dev, n_items * sizeof(jatam_result), cudaMemcpyDeviceToHost, st));
     if (o.host_fit && n_items)
@@ -514,6 +521,7 @@ int jatam_enumerate(const jatam_config *cfg, uint64_t first, uint64_t count, jat
     a.mode = sampled ? MODE_SAMPLED : MODE_RANGE;
     a.first = first;
     a.count = count;
+    a.c4 = (cfg->flags & JATAM_C4_HASH) ? 1 : 0;
     a.n = cfg->n; a.c = cfg->c; a.L = cfg->L; a.k = cfg->k;
     a.key0 = (uint32_t)cfg->seed;
     a.key1 = (uint32_t)(cfg->seed >> 32);
@@ -547,6 +555,7 @@ int jatam_classify_batch(const jatam_config *cfg, const uint8_t *colours, const 
     LaunchArgs a{};
     a.mode = MODE_RECORDS;
     a.count = N;
+    a.c4 = (cfg->flags & JATAM_C4_HASH) ? 1 : 0;
     a.n = cfg->n; a.c = cfg->c; a.L = cfg->L; a.k = cfg->k;
     a.key0 = (uint32_t)cfg->seed;
     a.key1 = (uint32_t)(cfg->seed >> 32);
@@ -602,6 +611,7 @@ int ga_evaluate(const jatam_config *cfg, const uint64_t *genomes, uint64_t N, in
     LaunchArgs a{};
     a.mode = MODE_GENOMES;
     a.count = N;
+    a.c4 = (cfg->flags & JATAM_C4_HASH) ? 1 : 0;
     a.genomes = static_cast<const unsigned long long *>(gdev);
     a.n = cfg->n; a.c = cfg->c; a.L = cfg->L; a.k = cfg->k;
     a.key0 = (uint32_t)cfg->seed;
@@ -894,6 +904,7 @@ int jatam_mlp_create(uint64_t max_batch, jatam_mlp **net)
     rc |= alloc((void **)&b.h2, Bc * MLP_H * 2); rc |= alloc((void **)&b.dq, Bc * MLP_OUT * 2);
     rc |= alloc((void **)&b.dh1, Bc * MLP_H * 2); rc |= alloc((void **)&b.dh2, Bc * MLP_H * 2);
     rc |= alloc((void **)&b.logits, Bc * MLP_OUT * 4); rc |= alloc((void **)&b.d, Bc * MLP_OUT * 4);
+    rc |= alloc((void **)&b.lrow, Bc * 4);
     rc |= alloc((void **)&b.loss, 16);
     if (rc) {
         jatam_mlp_destroy(m);
@@ -911,7 +922,8 @@ void jatam_mlp_destroy(jatam_mlp *m)
 {
     if (!m) return;
     MlpBuffers &b = m->b;
-    void *ptrs[] = {b.p, b.grad, b.m, b.v, b.wq, b.x, b.h1, b.h2, b.dq, b.dh1, b.dh2, b.logits, b.d, b.loss, m->stage};
+    void *ptrs[] = {b.p, b.grad, b.m, b.v, b.wq, b.x, b.h1, b.h2, b.dq, b.dh1, b.dh2, b.logits, b.d, b.lrow, b.loss,
+                    m->stage};
     cudaDeviceSynchronize();
     for (void *p : ptrs)
         if (p) cudaFree(p);
@@ -1271,7 +1283,22 @@ int jatam_profile(int enable)
 {
     std::lock_guard<std::mutex> lock(g_mutex);
     g_last_error.clear();
-    g_profile = enable != 0;
+    if (enable < 0 || enable > 3) return fail(JATAM_EINVAL, "enable must be 0..3");
+    g_profile = enable;
+    return JATAM_OK;
+}
+
+int jatam_work_counters(uint64_t counters[4])
+{
+    std::lock_guard<std::mutex> lock(g_mutex);
+    g_last_error.clear();
+    if (!counters) return fail(JATAM_EINVAL, "counters is NULL");
+    int dev = 0;
+    CUDA_TRY(cudaGetDevice(&dev));
+    auto it = g_ws.find(dev);
+    if (it == g_ws.end() || !it->second->stats_valid) return fail(JATAM_EINVAL, "no counted call on this device");
+    CUDA_TRY(cudaEventSynchronize(it->second->last));
+    CUDA_TRY(cudaMemcpy(counters, it->second->stats, 4 * 8, cudaMemcpyDeviceToHost));
     return JATAM_OK;
 }
 
@@ -1302,7 +1329,7 @@ void jatam_shutdown(void)
         cudaFree(w->table.size_max); cudaFree(w->table.size_min);
         cudaFree(w->compact.key); cudaFree(w->compact.count); cudaFree(w->compact.min_id);
         cudaFree(w->compact.size_max); cudaFree(w->compact.size_min);
-        cudaFree(w->work_next); cudaFree(w->err); cudaFree(w->nkeys); cudaFree(w->list_count);
+        cudaFree(w->work_next); cudaFree(w->stats); cudaFree(w->err); cudaFree(w->nkeys); cudaFree(w->list_count);
         if (w->list) cudaFree(w->list);
         cudaFreeHost(w->host_words);
         if (w->stage_in) cudaFree(w->stage_in);

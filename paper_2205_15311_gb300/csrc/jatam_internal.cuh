@@ -59,6 +59,7 @@ struct LaunchArgs {
     int32_t *fitness;             // [count] or null
     Table table;
     int use_hist;
+    int c4;                       // 1: the rotation-only hash variant instead of the canonical form
     int stop_at;                    // finished lanes that end a growth round (1..32)
     unsigned long long *list;        // items left to grow, written by the pre-filter: 1 or 3 lists
     unsigned long long list_stride;  // capacity of one list (the call's item count)
@@ -67,6 +68,8 @@ struct LaunchArgs {
     int klass;                       // classify_kernel: the list it works through
     int plan_w32, plan_w16, plan_w8; // classify_mixed_kernel: warps per CTA of each region size
     unsigned long long *work_next;  // [3] work counters (one per list), zeroed before the launch
+    unsigned long long *stats;      // null, or [4] executed work: drawn placements, seed placements,
+                                    // lane slots of the growth rounds, genotypes grown by warps
     unsigned *err;                  // sticky error bits
 };
 
@@ -121,7 +124,7 @@ struct MlpBuffers {
     __nv_bfloat16 *wq;           // [MLP_NPARAM] bfloat16 copy of the parameters (weights used by the products)
     long long cap;               // batch capacity of the activation buffers
     __nv_bfloat16 *x, *h1, *h2, *dq, *dh1, *dh2;
-    float *logits, *d, *loss;
+    float *logits, *d, *lrow, *loss;
 };
 cudaError_t mlp_forward(const MlpBuffers &b, const unsigned long long *genomes, long long B, cudaStream_t st);
 cudaError_t mlp_backward(const MlpBuffers &b, const uint8_t *labels, long long B, cudaStream_t st);

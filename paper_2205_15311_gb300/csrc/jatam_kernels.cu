@@ -118,6 +118,8 @@ struct Lane {
     int blo, bhi;                // rows of OCCB written by the current replicate
     int diverged;                // replicate j > 0 can no longer end in replicate 0's configuration
     int forced;                  // replicate 0 so far never had more than one frontier site to choose from
+    int cert;                    // replicate 0 so far: every occupied neighbour of a placed tile can only
+                                 // receive, from that tile, the tuple it holds (or nothing)
     int cls, decided;
     uint32_t hash;
     uint32_t ka, kb;             // Philox blocks held: key = replicate * 512 + block (NO_BLOCK if none)
@@ -200,11 +202,51 @@ __device__ __forceinline__ void coop_tables(unsigned &pending, uint32_t *warp_la
     }
 }
 
+// one-at-a-time over (h, w) and (x, y) of every occupied cell of an image held
+// as rows in lanes (row i in lane i, its first cell the most significant of wc bits)
+__device__ __forceinline__ uint32_t image_hash(uint32_t v, int hc, int wc)
+{
+    uint32_t hsh = oaat_add(0u, (uint32_t)hc);
+    hsh = oaat_add(hsh, (uint32_t)wc);
+    for (int i = 0; i < hc; ++i) {
+        uint32_t row = __shfl_sync(FULL, v, i);
+        while (row) {
+            const int p = 31 - __clz(row);
+            hsh = oaat_add(hsh, (uint32_t)(wc - 1 - p));
+            hsh = oaat_add(hsh, (uint32_t)i);
+            row &= ~(1u << p);
+        }
+    }
+    return oaat_finish(hsh);
+}
+
+// four image hashes sorted and hashed again, byte by byte (little endian)
+__device__ __forceinline__ uint32_t c4_combine(uint32_t a, uint32_t b, uint32_t c, uint32_t d)
+{
+    uint32_t x[4] = {a, b, c, d};
+#pragma unroll
+    for (int i = 1; i < 4; ++i)
+#pragma unroll
+        for (int j = i; j > 0; --j)
+            if (x[j - 1] > x[j]) {
+                const uint32_t t = x[j];
+                x[j] = x[j - 1];
+                x[j - 1] = t;
+            }
+    uint32_t hsh = 0u;
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int byte = 0; byte < 4; ++byte) hsh = oaat_add(hsh, (x[i] >> (8 * byte)) & 255u);
+    return oaat_finish(hsh);
+}
+
 // ---------------------------------------------------------------------------
 // warp-cooperative canonical form + hash of owner o's replicate-0 shape
 // ---------------------------------------------------------------------------
 template <int S>
-__device__ __forceinline__ uint32_t coop_shape_hash(int o, const uint32_t *warp_lanes, const Lane &Ls, int lane)
+__device__ __forceinline__ uint32_t coop_shape_hash(int o, const uint32_t *warp_lanes, const Lane &Ls, int lane,
+                                                    bool c4)
 {
     using G = Geo<S>;
     const int x0 = __shfl_sync(FULL, Ls.x0, o), x1 = __shfl_sync(FULL, Ls.x1, o);
@@ -251,19 +293,15 @@ __device__ __forceinline__ uint32_t coop_shape_hash(int o, const uint32_t *warp_
             }
         }
     }
-    // one-at-a-time over (h, w) and (x, y) of every occupied cell, row-major
-    uint32_t hsh = oaat_add(0u, (uint32_t)hc);
-    hsh = oaat_add(hsh, (uint32_t)wc);
-    for (int i = 0; i < hc; ++i) {
-        uint32_t row = __shfl_sync(FULL, best, i);
-        while (row) {
-            const int p = 31 - __clz(row);
-            hsh = oaat_add(hsh, (uint32_t)(wc - 1 - p));
-            hsh = oaat_add(hsh, (uint32_t)i);
-            row &= ~(1u << p);
-        }
+    if (c4) {
+        // the rotation-only variant of Section 2.5: the images under the four
+        // rotations (identity, half turn, and the two quarter turns), each
+        // hashed, sorted, and hashed again
+        const uint32_t h0 = image_hash(v[0], h, w), h3 = image_hash(v[3], h, w);
+        const uint32_t h5 = image_hash(v[5], w, h), h6 = image_hash(v[6], w, h);
+        return c4_combine(h0, h3, h5, h6);
     }
-    return oaat_finish(hsh);
+    return image_hash(best, hc, wc);
 }
 
 // The seed step of replicate 0, evaluated straight from the colours: for each
@@ -334,10 +372,17 @@ __device__ __forceinline__ void replicate_end(Lane &Ls, uint32_t *my, bool nd, b
         Ls.x1 = Ls.xmax;
         Ls.y0 = Ls.ymin;
         Ls.y1 = Ls.ymax;
-        if (Ls.forced) {
-            // every draw of replicate 0 had a single frontier site: every other
-            // replicate starts from the same seed and is forced along the same
-            // path, so all k replicates end in this configuration
+        if (Ls.forced || Ls.cert) {
+            // The outcome of every later replicate is fixed: either every draw
+            // of replicate 0 had a single frontier site, so every replicate
+            // follows the same path; or the final configuration A0 is closed:
+            // for every two adjacent tiles of A0, what either one offers the
+            // other's cell is that cell's tuple or nothing, and replicate 0
+            // ended with no candidate outside A0.  Then, in any order, every
+            // site a replicate can reach receives only A0's tuple there, no
+            // site ever sees two distinct candidates, nothing attaches outside
+            // A0, and the frontier empties only when all of A0 (connected
+            // through its bonds) is placed: all k replicates end in A0.
             Ls.cls = JATAM_DET_BOUNDED;
             Ls.decided = Ls.k;
             Ls.phase = PH_SHAPE;
@@ -381,30 +426,36 @@ __device__ __forceinline__ void lane_step(Lane &Ls, uint32_t *my, uint32_t k0, u
     int b = 0, tau = 0;
     bool placing = active;
     if (active && !seed) {
+        // the growth loop's batched fetch-ahead has computed this block (in pa,
+        // or in pb when it was fetched as the next replicate's first block)
         const uint32_t key = (uint32_t)Ls.rep * 512u + ((uint32_t)Ls.step >> 2);
         if (Ls.ka != key) {
             if (Ls.kb == key) {
                 Ls.pa = Ls.pb;
                 Ls.kb = NO_BLOCK;
+                Ls.ka = key;
             } else {
-                Ls.pa = philox_block(key, Ls.sid, k0, k1);
+                atomicOr(err, ERR_GUARD);  // unreachable: the fetch-ahead supplies every current block
+                Ls.cls = 255;
+                Ls.phase = PH_WRITE;
+                placing = false;
             }
-            Ls.ka = key;
         }
         if (Ls.nF > 1) Ls.forced = 0;
         const int sel = Ls.step & 3;
         const uint32_t u = sel == 0 ? Ls.pa.x : sel == 1 ? Ls.pa.y : sel == 2 ? Ls.pa.z : Ls.pa.w;
-        uint32_t i = __umulhi(u, (uint32_t)Ls.nF);
+        uint32_t i = placing ? __umulhi(u, (uint32_t)Ls.nF) : 0u;
         int w = (max(Ls.ymin - 1, 0) * S) >> 5;
         uint32_t f = my[(G::FRONT + w) * 32];
-        uint32_t cnt = __popc(f);
+        uint32_t cnt = placing ? __popc(f) : 1u;
         while (i >= cnt) {
             i -= cnt;
             if (++w >= G::NW) break;
             f = my[(G::FRONT + w) * 32];
             cnt = __popc(f);
         }
-        if (w >= G::NW) {
+        if (!placing) {
+        } else if (w >= G::NW) {
             atomicOr(err, ERR_GUARD);
             Ls.cls = 255;
             Ls.phase = PH_WRITE;
@@ -427,6 +478,7 @@ __device__ __forceinline__ void lane_step(Lane &Ls, uint32_t *my, uint32_t k0, u
         Ls.nF = 0;
         Ls.diverged = 0;
         Ls.forced = 1;
+        Ls.cert = 1;
         Ls.phase = PH_GROW;
     }
     __syncwarp();
@@ -475,6 +527,9 @@ __device__ __forceinline__ void lane_step(Lane &Ls, uint32_t *my, uint32_t k0, u
         nd = nd || (!in && multi) || (empty && (isf ? (M & ~(1u << tq)) != 0 : multi));
         // one candidate outside the grid: growth past the cap
         unb = unb || (!in && M != 0 && !multi);
+        // replicate 0: an occupied neighbour that could receive from the new
+        // tile a tuple other than its own breaks the closure of the final shape
+        if (placing && Ls.rep == 0 && in && (ow & qbit) && (M & ~(1u << tq)) != 0) Ls.cert = 0;
         if (placing && empty && !isf && M != 0 && !multi) {
             const int tn = __ffs(M) - 1;
             // replicate 0 must hold the same tuple here, or this replicate can
@@ -609,10 +664,11 @@ __device__ __forceinline__ Item load_item(const LaunchArgs &a, unsigned long lon
     return it;
 }
 
-__device__ __forceinline__ uint32_t monomer_shape_hash()
+__device__ __forceinline__ uint32_t monomer_shape_hash(bool c4)
 {
-    // the lone seed: a 1 x 1 crop with its cell at (0, 0)
-    return oaat_finish(oaat_add(oaat_add(oaat_add(oaat_add(0u, 1u), 1u), 0u), 0u));
+    // the lone seed: a 1 x 1 crop with its cell at (0, 0), the same under every rotation
+    const uint32_t h = oaat_finish(oaat_add(oaat_add(oaat_add(oaat_add(0u, 1u), 1u), 0u), 0u));
+    return c4 ? c4_combine(h, h, h, h) : h;
 }
 
 __device__ __forceinline__ void write_result(const LaunchArgs &a, unsigned long long item, int cls, int decided,
@@ -643,7 +699,7 @@ __global__ void __launch_bounds__(256) prefilter_kernel(const LaunchArgs a, int 
     __syncthreads();
     const int lane = threadIdx.x & 31;
     const int b_uniform = log2_colours(a.c);
-    const uint32_t mono = monomer_shape_hash();
+    const uint32_t mono = monomer_shape_hash(a.c4 != 0);
     const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
     for (unsigned long long base = (unsigned long long)blockIdx.x * blockDim.x; base < a.count; base += stride) {
         const unsigned long long idx = base + threadIdx.x;
@@ -742,9 +798,11 @@ __device__ __forceinline__ void warp_loop(const LaunchArgs &a, uint32_t *warp_la
     Ls.item = 0; Ls.sid = 0; Ls.cols = 0;
     Ls.rep = Ls.step = Ls.size = Ls.nF = 0;
     Ls.x0 = Ls.x1 = Ls.y0 = Ls.y1 = 0;
+    unsigned long long st_draw = 0, st_seed = 0, st_slots = 0, st_geno = 0;  // executed work (a.stats)
     Ls.ymin = Ls.ymax = Ls.xmin = Ls.xmax = 0;
     Ls.diverged = 0;
     Ls.forced = 0;
+    Ls.cert = 0;
     Ls.ka = Ls.kb = NO_BLOCK;
     Ls.pa = Ls.pb = make_uint4(0, 0, 0, 0);
     unsigned long long q_next = 0, q_end = 0;  // this warp's slice of the work counter
@@ -821,6 +879,7 @@ __device__ __forceinline__ void warp_loop(const LaunchArgs &a, uint32_t *warp_la
             Ls.bhi = -1;
             Ls.rep = 0;
             Ls.phase = PH_START;
+            st_geno += 1;
             Ls.ka = NO_BLOCK;
             Ls.pb = philox_block(0u, Ls.sid, a.key0, a.key1);
             Ls.kb = 0u;
@@ -860,6 +919,11 @@ __device__ __forceinline__ void warp_loop(const LaunchArgs &a, uint32_t *warp_la
                     }
                 }
             }
+            if (a.stats) {
+                st_draw += __popc(__ballot_sync(FULL, Ls.phase == PH_GROW));
+                st_seed += __popc(__ballot_sync(FULL, Ls.phase == PH_START));
+                st_slots += 32;
+            }
             lane_step<S>(Ls, my, a.key0, a.key1, a.err);
             const unsigned busy = __ballot_sync(FULL, Ls.phase == PH_START || Ls.phase == PH_GROW);
             if (!busy) break;
@@ -895,7 +959,7 @@ __device__ __forceinline__ void warp_loop(const LaunchArgs &a, uint32_t *warp_la
         while (shp) {
             const int o = __ffs(shp) - 1;
             shp &= shp - 1;
-            const uint32_t hv = coop_shape_hash<S>(o, warp_lanes, Ls, lane);
+            const uint32_t hv = coop_shape_hash<S>(o, warp_lanes, Ls, lane, a.c4 != 0);
             if (lane == o) {
                 Ls.hash = hv;
                 Ls.phase = PH_WRITE;
@@ -909,7 +973,15 @@ __device__ __forceinline__ void warp_loop(const LaunchArgs &a, uint32_t *warp_la
             __syncwarp();
         }
     }
-
+    if (a.stats) {
+        st_geno = __reduce_add_sync(FULL, (unsigned)st_geno);
+        if (lane == 0) {
+            atomicAdd(&a.stats[0], st_draw);
+            atomicAdd(&a.stats[1], st_seed);
+            atomicAdd(&a.stats[2], st_slots);
+            atomicAdd(&a.stats[3], st_geno);
+        }
+    }
 }
 
 __device__ __forceinline__ void hist_begin(SmemHist &H)

@@ -133,7 +133,7 @@ __global__ void features_kernel(const unsigned long long *genomes, long long n, 
 // float32 (for the bias gradient) and bfloat16 (for the products); the loss
 // summed into *loss (divided by B)
 __global__ void softmax_ce_kernel(const float *logits, const uint8_t *labels, long long B, float *d,
-                                  __nv_bfloat16 *dq, float *loss)
+                                  __nv_bfloat16 *dq, float *lrow)
 {
     const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     float l = 0.f;
@@ -153,9 +153,24 @@ __global__ void softmax_ce_kernel(const float *logits, const uint8_t *labels, lo
             dq[i * MLP_OUT + c] = __float2bfloat16_rn(v);
         }
         l = (logf(s) + mx - z[y]) / (float)B;
+        lrow[i] = l;
     }
-    for (int off = 16; off > 0; off >>= 1) l += __shfl_xor_sync(0xffffffffu, l, off);
-    if ((threadIdx.x & 31) == 0) atomicAdd(loss, l);
+}
+
+// the loss: the per-row losses summed in a fixed order (one CTA), so repeated
+// runs give the same bits
+__global__ void __launch_bounds__(256) loss_sum_kernel(const float *lrow, long long B, float *loss)
+{
+    __shared__ float red[256];
+    float s = 0.f;
+    for (long long r = threadIdx.x; r < B; r += blockDim.x) s += lrow[r];
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int off = blockDim.x / 2; off > 0; off >>= 1) {
+        if ((int)threadIdx.x < off) red[threadIdx.x] += red[threadIdx.x + off];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *loss = red[0];
 }
 
 // column sums of a [B x N] matrix (float32 or bfloat16) into out[N]
@@ -213,12 +228,6 @@ __global__ void to_bf16_kernel(const float *p, long long n, __nv_bfloat16 *pq)
         pq[i] = __float2bfloat16_rn(p[i]);
 }
 
-__global__ void zero_kernel(float *p, long long n)
-{
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
-        p[i] = 0.f;
-}
-
 cudaError_t gemm(const GemmArgs &g, cudaStream_t st)
 {
     const dim3 grid((g.N + TN - 1) / TN, (g.M + TM - 1) / TM);
@@ -263,8 +272,8 @@ cudaError_t mlp_forward(const MlpBuffers &b, const unsigned long long *genomes, 
 cudaError_t mlp_backward(const MlpBuffers &b, const uint8_t *labels, long long B, cudaStream_t st)
 {
     cudaError_t e;
-    zero_kernel<<<1, 32, 0, st>>>(b.loss, 1);
-    softmax_ce_kernel<<<(unsigned)((B + 255) / 256), 256, 0, st>>>(b.logits, labels, B, b.d, b.dq, b.loss);
+    softmax_ce_kernel<<<(unsigned)((B + 255) / 256), 256, 0, st>>>(b.logits, labels, B, b.d, b.dq, b.lrow);
+    loss_sum_kernel<<<1, 256, 0, st>>>(b.lrow, B, b.loss);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     float *G = b.grad;
     GemmArgs g{};

@@ -29,12 +29,12 @@ def _cuda():
     yield
 
 
-def _dev_enumerate(n, c, L, k, seed, first, count, sampled=False, hist_cap=1 << 16):
+def _dev_enumerate(n, c, L, k, seed, first, count, sampled=False, hist_cap=1 << 16, c4_hash=False):
     out = torch.full((max(count, 1) * 8,), 0xEE, dtype=torch.uint8, device="cuda")  # poisoned
     hist = torch.empty(hist_cap * 32, dtype=torch.uint8, device="cuda")
     hlen = torch.zeros(1, dtype=torch.int32, device="cuda")
     J.enumerate_space(n, c, L, k, seed, first, count, sampled=sampled, out=out, hist=hist, hist_len=hlen,
-                      hist_cap=hist_cap, sync=True)
+                      hist_cap=hist_cap, sync=True, c4_hash=c4_hash)
     m = int(hlen.item())
     return J.results_view(out)[:count], J.hist_view(hist, min(m, hist_cap)), m
 
@@ -108,6 +108,37 @@ def test_s38_sample_slice_matches_oracle():
     assert np.array_equal(res, ref)
     ids = np.array([O.sample_genotype(first + i, n, c, seed) for i in range(count)], np.uint64)
     assert _hist_rows(hist) == _hist_rows(_oracle_hist(ref, ids))
+
+
+@pytest.mark.parametrize("case", ["s24_full", "s28_slice", "s38_sample"])
+def test_c4_hash_variant_matches_oracle(case):
+    """The rotation-only hash of Section 2.5: every field but the hash equals
+    the default run, the hashes equal the oracle's C4 hashes, and chiral pairs
+    now land in different histogram rows."""
+    if case == "s24_full":
+        n, c, L, k, seed, first, count, _ = W.WORKLOADS["s24_full"]
+        sampled = False
+    elif case == "s28_slice":
+        n, c, L, k, seed, sampled = 2, 8, 16, 20, 2, False
+        first, count = 5 * (1 << 20) + 3, 40000
+    else:
+        n, c, L, k, seed, _, _, _ = W.WORKLOADS["s38_sample"]
+        first, count, sampled = 777, 40000, True
+    res, hist, m = _dev_enumerate(n, c, L, k, seed, first, count, sampled=sampled, c4_hash=True)
+    base, _, m8 = _dev_enumerate(n, c, L, k, seed, first, count, sampled=sampled)
+    with O.hash_mode(True):
+        ref, _ = O.enumerate_space(n, c, L, k, seed, first, count, sampled=sampled)
+    assert np.array_equal(res, ref)
+    for f in ("cls", "decided_rep", "size"):
+        assert np.array_equal(res[f], base[f])
+    if sampled:
+        ids = np.array([O.sample_genotype(first + i, n, c, seed) for i in range(count)], np.uint64)
+    else:
+        ids = np.arange(first, first + count, dtype=np.uint64)
+    with O.hash_mode(True):
+        want = _oracle_hist(ref, ids)
+    assert _hist_rows(hist) == _hist_rows(want)
+    assert m >= m8  # a free shape splits into at most two one-sided shapes
 
 
 @pytest.mark.parametrize("L", [1, 2, 3, 5, 8, 9, 16, 19, 31, 32])
@@ -311,3 +342,69 @@ def test_graph_replay_equals_direct_launches():
         f2.zero_()
         J.evaluate_genomes(g, f2, n=3, c=8, L=16, k=20, seed=5, sync=True, graph=True)
         assert torch.equal(f1, f2)
+
+
+_DX, _DY = (0, 1, 0, -1), (-1, 0, 1, 0)
+
+
+def _closed(col, n, c, grid):
+    """The closure test of a final replicate-0 configuration, written out from
+    the binding rule: for every two adjacent tiles, the tuples the one offers
+    the other's cell are that cell's tuple or none."""
+    def bind(a, b):
+        return a != 0 and b != 0 and min(a, b) % 2 == 1 and max(a, b) == min(a, b) + 1 and max(a, b) < c
+    side = {4 * t + r: [col[4 * t + (d - r) % 4] for d in range(4)] for t in range(n) for r in range(4)}
+    rep = {a: min(b for b in range(a + 1) if side[b] == side[a]) for a in side}
+    L = grid.shape[0]
+    for y in range(L):
+        for x in range(L):
+            u = grid[y, x]
+            if u < 0:
+                continue
+            for d in range(4):
+                qx, qy = x + _DX[d], y + _DY[d]
+                if not (0 <= qx < L and 0 <= qy < L) or grid[qy, qx] < 0:
+                    continue
+                offered = {rep[a] for a in side if bind(side[a][(d + 2) % 4], side[u][d])}
+                if offered and offered != {grid[qy, qx]}:
+                    return False
+    return True
+
+
+def test_work_counters_count_the_executed_process():
+    """jatam_profile(2) counts exactly the placements the kernel performs: every
+    replicate of every genotype the pre-filter left, except that a DET genotype
+    whose replicate 0 was forced (a single frontier site at every draw) or
+    closed stops after replicate 0 (both fix the outcome of all replicates)."""
+    n, c, L, k, seed = 2, 8, 16, 20, 2
+    genomes = W.random_genomes(3000, n, c, seed=21)  # stream id = the genome itself
+    want = {"placements": 0, "seeds": 0, "genotypes": 0}
+    ref = []
+    for g in genomes.tolist():
+        col = O.decode(g, n, c)
+        r = O.classify(n, c, L, k, seed, col, g, want_grid=True, trace_rep=0)
+        ref.append((r["cls"], r["decided_rep"], r["size"], r["shape_hash"]))
+        at_seed = r["placements"] == 0 and r["decided_rep"] == 0 and r["cls"] in (1, 3)
+        lone = r["cls"] == 0 and r["size"] == 1
+        if at_seed or lone:
+            continue
+        want["genotypes"] += 1
+        if r["cls"] == 0 and (all(t[0] <= 1 for t in r["trace"]) or _closed(list(col), n, c, r["grid"])):
+            want["placements"] += r["size"] - 1
+            want["seeds"] += 1
+        else:
+            want["placements"] += r["placements"]
+            want["seeds"] += min(r["decided_rep"] + 1, k)
+    dg = torch.from_numpy(genomes.view(np.int64)).cuda()
+    out = torch.full((len(genomes) * 8,), 0xEE, dtype=torch.uint8, device="cuda")
+    fit = torch.empty(len(genomes), dtype=torch.int32, device="cuda")
+    J.jatam_profile(2)
+    try:
+        J.evaluate_genomes(dg, fit, n=n, c=c, L=L, k=k, seed=seed, out=out, sync=True)
+        got = J.work_counters()
+    finally:
+        J.jatam_profile(0)
+    res = J.results_view(out)
+    assert [tuple(x) for x in res.tolist()] == ref
+    assert {key: got[key] for key in want} == want
+    assert got["lane_slots"] % 32 == 0 and got["lane_slots"] >= got["placements"] + got["seeds"]
