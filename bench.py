@@ -227,6 +227,68 @@ def mixed_arm(args, torch, J, dev):
     return 0
 
 
+def ga_arm(args, torch, J, dev):
+    """The GA of the fifth configuration (n = 3, c = 8 genomes, population
+    8192, 500 generations, per-edge mutation rate 0.01, tournament of 4, shape
+    fitness at L = 16, k = 20, seed 5), plain and with the surrogate network as
+    a pre-screen (trained first on labels the library's classification gives:
+    S_{2,4} in full, a uniform sample of S_{2,8}, and a uniform sample of
+    S_{3,8} at the GA's L and k).  Every reported fitness is simulated; the
+    line gives genomes simulated per second and, per arm, the generation at
+    which the verified best fitness first reached each level."""
+    from paper_2205_15311_gb300 import surrogate as S
+    from paper_2205_15311_gb300 import workloads as W
+    N, G, ratio, seed = 8192, 500, 4, 5
+    genomes, labels = S.build_training_set(torch, dev, s28_sample=1 << 21, s38_sample=1 << 21)
+    perm = torch.from_numpy(np.random.default_rng(seed).permutation(genomes.shape[0])).to(dev)
+    genomes, labels = genomes[perm].contiguous(), labels[perm].contiguous()
+    net = J.Surrogate(max_batch=max(N * ratio, 1 << 15))
+    net.set_params(S.initial_params(seed))
+    t0 = time.perf_counter()
+    S.train(torch, net, genomes, labels, steps=3000, batch=8192, lr=2e-3)
+    torch.cuda.synchronize()
+    train_s = time.perf_counter() - t0
+    trained = net.get_params()
+    thr = J.poisson_thresholds(0.01)
+    ga = J.make_ga(3, 8, seed, selection=J.TOURNAMENT, tournament=4, crossover=J.NO_CROSSOVER,
+                   mutation_thresholds=thr)
+    pop0 = W.random_genomes(N, 3, 8, seed=seed)
+    arms = {}
+    for mode in ("plain", "screened"):
+        pop = torch.from_numpy(pop0.view(np.int64).copy()).to(dev)
+        best = np.zeros(G, np.int32)
+        net.set_params(trained)
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        if mode == "plain":
+            J.run_ga(ga, pop, G, fitness_kind=J.FITNESS_SHAPE, L=16, k=20, seed=seed, best=best)
+        else:
+            J.run_ga_screened(ga, pop, G, ratio, net, online_lr=1e-3, L=16, k=20, seed=seed, best=best)
+        b.record()
+        torch.cuda.synchronize()
+        ms = a.elapsed_time(b)
+        so_far = np.maximum.accumulate(best)
+        first = {int(v): int(np.argmax(so_far >= v)) for v in sorted(set(so_far.tolist()))}
+        arms[mode] = {"genomes_per_s": N * G / (ms / 1e3), "ms": round(ms, 1), "best": int(so_far[-1]),
+                      "first_generation_reaching": first}
+    net.close()
+    line = {
+        "metric": "GA genomes simulated/s (every survivor classified; plain vs surrogate-screened)",
+        "value": arms["plain"]["genomes_per_s"], "unit": "genomes/s", "n_gpus": 1, "steps": G, "warmup": 0,
+        "ms_per_step": arms["plain"]["ms"] / G, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "u32", "data": "synthetic",
+        "config": {"workload": "ga: n=3 c=8, population 8192, 500 generations, per-edge mutation 0.01, "
+                               "tournament 4, shape fitness L=16 k=20, seed 5",
+                   "surrogate": f"36-256-256-8 bf16, 3000 Adam steps of 8192 on S_{{2,4}} + 2M S_{{2,8}} + 2M S_{{3,8}} "
+                                f"labels ({train_s:.1f} s); screen ratio {ratio}, online lr 1e-3",
+                   "plain": arms["plain"], "screened": arms["screened"]},
+        "e2e": None, "gpu_launches": None, "roofline": None, "cpu_baseline": None,
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def run_oracle_sample(nthreads):
     from oracle import oracle as O
     n, c, L, k, seed, _, _, _ = WORKLOAD_SPEC()
@@ -277,7 +339,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--workload", default="s28_full",
-                    help="s28_full (the bench line), or s24_full / s28_paper / s38_sample / mixed for measurements")
+                    help="s28_full (the bench line), or s24_full / s28_paper / s38_sample / mixed / ga for measurements")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end leg")
     ap.add_argument("--profile-genomes", type=int, default=0,
@@ -307,6 +369,8 @@ def main():
     from paper_2205_15311_gb300 import binding as J
     if WORKLOAD == "mixed":
         return mixed_arm(args, torch, J, dev)
+    if WORKLOAD == "ga":
+        return ga_arm(args, torch, J, dev)
 
     n, c, L, k, seed0, first, count, sampled = WORKLOAD_SPEC()
     if args.profile_genomes:

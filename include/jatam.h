@@ -262,16 +262,22 @@ int jatam_embed_genomes(const uint64_t *genomes, uint64_t N, int n, int c, uint6
 /*
  * ga_run_screened -- ga_run with the network as a pre-screen (shape fitness):
  * each generation breeds ratio x N candidate children (child indices
- * 0 .. ratio N - 1 of ga_breed), scores each with the network's expected
- * shape size (class probabilities times 0, 0, 0, 1, 2.5, 5.5, 11.5, 20) and
- * keeps the N best (ties: lower index) as the next population, which the
+ * 0 .. ratio N - 1 of ga_breed), scores each with the network's probability
+ * of a deterministic bounded shape of at least 8 tiles (classes 6 and 7) and
+ * keeps the N best (ties: lower index) as the next population -- distinct
+ * genomes first: a repeat of an earlier candidate ranks below every first
+ * occurrence, so the population does not collapse onto copies of the
+ * network's favourite -- which the
  * plain classification then evaluates: every reported fitness is simulated,
- * the network only decides which candidates get simulated.  ratio x N must fit
- * the network's max_batch.
+ * the network only decides which candidates get simulated.  When online_lr >
+ * 0, each generation's simulated population, labelled by its own results,
+ * also trains the network for one Adam step at that learning rate (the
+ * network follows the region the search moves into).  ratio x N must fit the
+ * network's max_batch.
  */
 int ga_run_screened(const jatam_ga_config *ga, const jatam_config *cls, uint64_t N, uint32_t generations,
-                    uint32_t ratio, jatam_mlp *net, uint64_t *population, int32_t *best, int64_t *total,
-                    void *stream);
+                    uint32_t ratio, jatam_mlp *net, float online_lr, uint64_t *population, int32_t *best,
+                    int64_t *total, void *stream);
 
 /*
  * jatam_philox -- Philox4x32-10 (Salmon et al., SC'11) as computed by the
@@ -308,9 +314,11 @@ int jatam_autotune(const jatam_config *shapes, uint32_t n_shapes, void *stream);
 
 /*
  * jatam_set_tuning / jatam_get_tuning -- set or read the launch shape used for
- * cfg's key: warps_per_cta 1..8, stop_at 1..32 (lanes that must have finished
- * their genotype before a warp leaves a growth round).  A key never tuned or
- * set uses the defaults (8 warps, 8).
+ * cfg's key: warps_per_cta 1..6, stop_at 1..32 (lanes that must have finished
+ * their genotype before a warp leaves a growth round); warps_per_cta 0 forgets
+ * the key's setting.  A key never tuned or set uses the defaults: the CTA size
+ * that keeps the most warps resident on an SM, and stop_at 12 (lattices up to
+ * 16 x 16) or 8 (32 x 32).
  */
 int jatam_set_tuning(const jatam_config *cfg, int warps_per_cta, int stop_at);
 int jatam_get_tuning(const jatam_config *cfg, int *warps_per_cta, int *stop_at);

@@ -98,7 +98,7 @@ def lib():
         L.jatam_mlp_labels.restype = ctypes.c_int
         L.jatam_embed_genomes.argtypes = [_VP, _U64, ctypes.c_int, ctypes.c_int, _VP, _VP]
         L.jatam_embed_genomes.restype = ctypes.c_int
-        L.ga_run_screened.argtypes = [_VP, _VP, _U64, _U32, _U32, _VP, _VP, _VP, _VP, _VP]
+        L.ga_run_screened.argtypes = [_VP, _VP, _U64, _U32, _U32, _VP, ctypes.c_float, _VP, _VP, _VP, _VP]
         L.ga_run_screened.restype = ctypes.c_int
         L.ga_breed.argtypes = [_VP, _VP, _VP, _U64, _U32, _VP, _VP]
         L.ga_breed.restype = ctypes.c_int
@@ -209,8 +209,8 @@ def jatam_embed_genomes(genomes, N, n, c, out, stream):
     return lib().jatam_embed_genomes(genomes, N, n, c, out, stream)
 
 
-def ga_run_screened(ga, cls, N, generations, ratio, net, population, best, total, stream):
-    return lib().ga_run_screened(ga, cls, N, generations, ratio, net, population, best, total, stream)
+def ga_run_screened(ga, cls, N, generations, ratio, net, online_lr, population, best, total, stream):
+    return lib().ga_run_screened(ga, cls, N, generations, ratio, net, online_lr, population, best, total, stream)
 
 
 def jatam_set_mixed_plan(w32, w16, w8):
@@ -508,9 +508,9 @@ def embed(genomes, n, c, out, stream=None):
                                      _stream_handle(stream)))
 
 
-def run_ga_screened(ga, population, generations, ratio, net, *, L=16, k=20, seed=0, best=None, total=None,
-                    stream=None):
+def run_ga_screened(ga, population, generations, ratio, net, *, online_lr=1e-3, L=16, k=20, seed=0, best=None,
+                    total=None, stream=None):
     cls = make_config(ga.n, ga.c, L, k, seed)
     return check(ga_run_screened(ctypes.addressof(ga), ctypes.addressof(cls), int(population.shape[0]),
-                                 int(generations), int(ratio), net.h, _addr(population), _addr(best), _addr(total),
-                                 _stream_handle(stream)))
+                                 int(generations), int(ratio), net.h, float(online_lr), _addr(population), _addr(best),
+                                 _addr(total), _stream_handle(stream)))

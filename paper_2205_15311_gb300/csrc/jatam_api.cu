@@ -34,8 +34,8 @@ int g_stop_override = 0;
 int g_warps_override = 0;
 
 struct Tuning {
-    int warps = 8;
-    int stop_at = 8;
+    int warps = 0;    // 0: the CTA size that keeps the most warps resident
+    int stop_at = 0;  // 0: 12 for lattices up to 16 x 16, 8 for 32 x 32 (measured on S_{2,8}, S_{3,8})
     int w32 = 2, w16 = 4, w8 = 2;  // warps per CTA of each region size in the mixed launch
 };
 // launch shape per key (lattice template, n, c); n = c = 0 for mixed batches
@@ -53,7 +53,7 @@ void read_env_overrides()
     }
     if (const char *v = getenv("JATAM_WARPS_PER_CTA")) {
         int x = atoi(v);
-        if (x >= 1 && x <= 8) g_warps_override = x;
+        if (x >= 1 && x <= MAX_CTA_WARPS) g_warps_override = x;
     }
 }
 
@@ -102,7 +102,6 @@ struct Workspace {
     cudaEvent_t last = nullptr;  // end of the previous call's work on this device
     cudaEvent_t k_start = nullptr, k_stop = nullptr;  // around the last profiled kernel
     bool k_valid = false;
-    int max_dyn_smem[3] = {0, 0, 0};  // the kernel attribute only ever grows
     std::map<std::string, cudaGraphExec_t> graphs;  // captured calls, by argument set
     void *ga_buf = nullptr;   // ga_run / ga_breed: fitness, children, cumsum, stats
     size_t ga_bytes = 0;
@@ -110,6 +109,7 @@ struct Workspace {
     size_t screen_bytes = 0;
     unsigned long long *screen_cand = nullptr, *screen_idx = nullptr;
     float *screen_score = nullptr;
+    ScreenTable screen_table{};
     cudaStream_t capture = nullptr;                  // private stream used only for capturing
 };
 
@@ -223,15 +223,17 @@ Tuning tuning_for(int S, int n, int c)
     t.w32 = g_plan[0];
     t.w16 = g_plan[1];
     t.w8 = g_plan[2];
+    const int nt = tuple_table_size(n);
     auto it = g_tuned.find(std::make_tuple(S, n, c));
     if (it != g_tuned.end()) {
         t.warps = it->second.warps;
         t.stop_at = it->second.stop_at;
     }
-    if (S == 32 && it == g_tuned.end()) t.warps = 2;  // the 32 x 32 lattice takes 33 KB of shared memory per warp
+    if (t.warps == 0) t.warps = default_warps_per_cta(S, nt);
+    if (t.stop_at == 0) t.stop_at = (S == 32) ? 8 : 12;
     if (g_warps_override) t.warps = g_warps_override;
     if (g_stop_override) t.stop_at = g_stop_override;
-    while (t.warps > 1 && classify_smem_bytes(S, t.warps) > 200 * 1024) --t.warps;  // what fits on one SM
+    while (t.warps > 1 && classify_smem_bytes(S, nt, t.warps) > 200 * 1024) --t.warps;  // what fits on one SM
     return t;
 }
 
@@ -317,15 +319,12 @@ int run(Workspace *w, LaunchArgs a, int S, jatam_result *out, int32_t *fitness, 
 
     // the single-template launch (not used for mixed sizes)
     const int warps = tune.warps;
+    const int nt = mixed ? 16 : tuple_table_size(a.n);
     long long blocks = 0;
     if (!mixed) {
-        const int si = S == 8 ? 0 : S == 16 ? 1 : 2;
-        if (classify_smem_bytes(S, warps) > w->max_dyn_smem[si]) {
-            CUDA_TRY(classify_set_attributes(S, warps));
-            w->max_dyn_smem[si] = classify_smem_bytes(S, warps);
-        }
+        CUDA_TRY(classify_set_attributes(S, nt, warps));
         int per_sm = 0;
-        CUDA_TRY(classify_occupancy(S, warps, &per_sm));
+        CUDA_TRY(classify_occupancy(S, nt, warps, &per_sm));
         if (per_sm < 1) return fail(JATAM_ECUDA, "classification kernel does not fit on an SM");
         blocks = (long long)per_sm * w->num_sms;
         const long long lanes_per_cta = 32LL * warps;
@@ -341,12 +340,9 @@ int run(Workspace *w, LaunchArgs a, int S, jatam_result *out, int32_t *fitness, 
         for (int kc = 0; kc < 3; ++kc) {
             const int Sk = 8 << kc;
             const Tuning tk = tuning_for(Sk, 0, 0);
-            if (classify_smem_bytes(Sk, tk.warps) > w->max_dyn_smem[kc]) {
-                CUDA_TRY(classify_set_attributes(Sk, tk.warps));
-                w->max_dyn_smem[kc] = classify_smem_bytes(Sk, tk.warps);
-            }
+            CUDA_TRY(classify_set_attributes(Sk, 16, tk.warps));
             int pk = 0;
-            CUDA_TRY(classify_occupancy(Sk, tk.warps, &pk));
+            CUDA_TRY(classify_occupancy(Sk, 16, tk.warps, &pk));
             if (pk < 1) return fail(JATAM_ECUDA, "classification kernel does not fit on an SM");
             fixed[kc] = {Sk, pk * w->num_sms, tk.warps, tk.stop_at};
         }
@@ -368,14 +364,14 @@ int run(Workspace *w, LaunchArgs a, int S, jatam_result *out, int32_t *fitness, 
         if (a.stats) CUDA_TRY(cudaMemsetAsync(a.stats, 0, 4 * 8, s));
         if (n_items) CUDA_TRY(launch_prefilter(a, S, (int)pblocks, s));
         if (events) CUDA_TRY(cudaEventRecord(w->k_start, s));
-        if (n_items && !mixed) CUDA_TRY(launch_classify(a, S, (int)blocks, warps, s));
+        if (n_items && !mixed) CUDA_TRY(launch_classify(a, S, nt, (int)blocks, warps, s));
         if (n_items && mixed && per_shape) {
             // one fixed launch per lattice size class, each over its own list
             for (int kc = 0; kc < 3; ++kc) {
                 LaunchArgs ak = a;
                 ak.klass = kc;
                 ak.stop_at = fixed[kc].stop_at;
-                CUDA_TRY(launch_classify(ak, fixed[kc].S, fixed[kc].blocks, fixed[kc].warps, s));
+                CUDA_TRY(launch_classify(ak, fixed[kc].S, 16, fixed[kc].blocks, fixed[kc].warps, s));
             }
         }
         if (n_items && mixed && !per_shape) CUDA_TRY(launch_classify_mixed(a, mixed_blocks, s));
@@ -652,19 +648,24 @@ int check_ga(const jatam_ga_config *ga, GaArgs *g)
 struct GaScratch {
     int32_t *fitness;
     unsigned long long *children, *cumsum;
+    jatam_result *results;  // the population's classification (online training of a screening network)
+    uint8_t *labels;
     long long *stats;
 };
 
 int ga_scratch(Workspace *w, uint64_t N, GaScratch *s)
 {
     const size_t a = ((size_t)N * 4 + 255) & ~size_t(255), b = ((size_t)N * 8 + 255) & ~size_t(255);
-    int rc = grow(&w->ga_buf, &w->ga_bytes, a + 2 * b + 256);
+    const size_t c = ((size_t)N + 255) & ~size_t(255);
+    int rc = grow(&w->ga_buf, &w->ga_bytes, a + 3 * b + c + 256);
     if (rc) return rc;
     char *p = static_cast<char *>(w->ga_buf);
     s->fitness = reinterpret_cast<int32_t *>(p);
     s->children = reinterpret_cast<unsigned long long *>(p + a);
     s->cumsum = reinterpret_cast<unsigned long long *>(p + a + b);
-    s->stats = reinterpret_cast<long long *>(p + a + 2 * b);
+    s->results = reinterpret_cast<jatam_result *>(p + a + 2 * b);
+    s->labels = reinterpret_cast<uint8_t *>(p + a + 3 * b);
+    s->stats = reinterpret_cast<long long *>(p + a + 3 * b + c);
     return JATAM_OK;
 }
 
@@ -765,7 +766,8 @@ namespace {
 // the network scores them and the best N (the only ones simulated) form the
 // next population.
 int ga_loop(const jatam_ga_config *ga, const jatam_config *cls, int fitness_kind, uint64_t N, uint32_t generations,
-            uint64_t *population, int32_t *best, int64_t *total, void *stream, jatam_mlp *net, uint32_t ratio)
+            uint64_t *population, int32_t *best, int64_t *total, void *stream, jatam_mlp *net, uint32_t ratio,
+            float online_lr)
 {
     GaArgs g;
     {
@@ -789,13 +791,21 @@ int ga_loop(const jatam_ga_config *ga, const jatam_config *cls, int fitness_kind
             const unsigned long long M = (unsigned long long)N * ratio;
             if (ratio < 1 || (long long)M > net->b.cap || M > (1ull << 26))
                 return fail(JATAM_EINVAL, "ratio x N must be at least N and fit the network's batch capacity");
-            const size_t need = (size_t)M * 8 * 2 + (size_t)M * 4 + 1024;
+            unsigned cap = 1;
+            while (cap < 2 * M) cap <<= 1;
+            const size_t a8 = ((size_t)M * 8 + 255) & ~size_t(255), a4 = ((size_t)M * 4 + 255) & ~size_t(255);
+            const size_t need = 2 * a8 + a4 + (size_t)cap * 12 + a4 + 256 + 1024;
             rc = grow(&w->screen_buf, &w->screen_bytes, need);
             if (rc) return rc;
             char *p = static_cast<char *>(w->screen_buf);
             w->screen_cand = reinterpret_cast<unsigned long long *>(p);
-            w->screen_idx = reinterpret_cast<unsigned long long *>(p + (((size_t)M * 8 + 255) & ~size_t(255)));
-            w->screen_score = reinterpret_cast<float *>(p + 2 * (((size_t)M * 8 + 255) & ~size_t(255)));
+            w->screen_idx = reinterpret_cast<unsigned long long *>(p + a8);
+            w->screen_score = reinterpret_cast<float *>(p + 2 * a8);
+            w->screen_table.keys = reinterpret_cast<unsigned long long *>(p + 2 * a8 + a4);
+            w->screen_table.first = reinterpret_cast<unsigned *>(p + 2 * a8 + a4 + (size_t)cap * 8);
+            w->screen_table.slot = reinterpret_cast<unsigned *>(p + 2 * a8 + a4 + (size_t)cap * 12);
+            w->screen_table.err = reinterpret_cast<unsigned *>(p + 2 * a8 + a4 + (size_t)cap * 12 + a4);
+            w->screen_table.cap_mask = cap - 1;
         }
     }
     cudaStream_t st = static_cast<cudaStream_t>(stream);
@@ -816,7 +826,8 @@ int ga_loop(const jatam_ga_config *ga, const jatam_config *cls, int fitness_kind
             if (rc) return rc;
         }
         int rc = (fitness_kind == JATAM_GA_FITNESS_SHAPE)
-                     ? ga_evaluate(&cc, reinterpret_cast<const uint64_t *>(pop), N, sc.fitness, nullptr, stream)
+                     ? ga_evaluate(&cc, reinterpret_cast<const uint64_t *>(pop), N, sc.fitness,
+                                   net ? sc.results : nullptr, stream)
                      : ga_hamming(reinterpret_cast<const uint64_t *>(pop), N, sc.fitness, stream);
         if (rc) return rc;
         std::lock_guard<std::mutex> lock(g_mutex);
@@ -837,13 +848,21 @@ int ga_loop(const jatam_ga_config *ga, const jatam_config *cls, int fitness_kind
             CUDA_TRY(launch_ga_breed(gg, st));
             CUDA_TRY(cudaMemcpyAsync(pop, sc.children, (size_t)N * 8, cudaMemcpyDeviceToDevice, st));
         } else {
+            if (online_lr > 0.f) {
+                // the simulated population, labelled by its own results, trains the network
+                CUDA_TRY(launch_mlp_labels(sc.results, (long long)N, sc.labels, st));
+                CUDA_TRY(mlp_forward(net->b, pop, (long long)N, st));
+                CUDA_TRY(mlp_backward(net->b, sc.labels, (long long)N, st));
+                net->t += 1;
+                CUDA_TRY(mlp_adam(net->b, online_lr, net->t, st));
+            }
             const unsigned long long M = (unsigned long long)N * ratio;
             gg.Nc = M;
             gg.children = w->screen_cand;
             CUDA_TRY(launch_ga_breed(gg, st));
             CUDA_TRY(mlp_forward(net->b, w->screen_cand, (long long)M, st));
             CUDA_TRY(launch_screen(net->b.logits, (long long)M, (long long)N, w->screen_score, w->screen_idx,
-                                   w->screen_cand, pop, st));
+                                   w->screen_cand, pop, w->screen_table, st));
         }
         CUDA_TRY(cudaEventRecord(w->last, st));
         if (!host_stats.empty()) CUDA_TRY(cudaStreamSynchronize(st));  // host_stats must not be read early
@@ -864,17 +883,19 @@ extern "C" {
 int ga_run(const jatam_ga_config *ga, const jatam_config *cls, int fitness_kind, uint64_t N, uint32_t generations,
            uint64_t *population, int32_t *best, int64_t *total, void *stream)
 {
-    return ga_loop(ga, cls, fitness_kind, N, generations, population, best, total, stream, nullptr, 1);
+    return ga_loop(ga, cls, fitness_kind, N, generations, population, best, total, stream, nullptr, 1, 0.f);
 }
 
 int ga_run_screened(const jatam_ga_config *ga, const jatam_config *cls, uint64_t N, uint32_t generations,
-                    uint32_t ratio, jatam_mlp *net, uint64_t *population, int32_t *best, int64_t *total, void *stream)
+                    uint32_t ratio, jatam_mlp *net, float online_lr, uint64_t *population, int32_t *best,
+                    int64_t *total, void *stream)
 {
-    if (!net) {
+    if (!net || !(online_lr >= 0.f) || online_lr > 1.f) {
         std::lock_guard<std::mutex> lock(g_mutex);
-        return fail(JATAM_EINVAL, "net is required");
+        return fail(JATAM_EINVAL, "net is required and 0 <= online_lr <= 1");
     }
-    return ga_loop(ga, cls, JATAM_GA_FITNESS_SHAPE, N, generations, population, best, total, stream, net, ratio);
+    return ga_loop(ga, cls, JATAM_GA_FITNESS_SHAPE, N, generations, population, best, total, stream, net, ratio,
+                   online_lr);
 }
 
 int jatam_mlp_create(uint64_t max_batch, jatam_mlp **net)
@@ -905,6 +926,7 @@ int jatam_mlp_create(uint64_t max_batch, jatam_mlp **net)
     rc |= alloc((void **)&b.dh1, Bc * MLP_H * 2); rc |= alloc((void **)&b.dh2, Bc * MLP_H * 2);
     rc |= alloc((void **)&b.logits, Bc * MLP_OUT * 4); rc |= alloc((void **)&b.d, Bc * MLP_OUT * 4);
     rc |= alloc((void **)&b.lrow, Bc * 4);
+    rc |= alloc((void **)&b.splitk, (size_t)MLP_SPLITK_MAX * MLP_H * MLP_H * 4);
     rc |= alloc((void **)&b.loss, 16);
     if (rc) {
         jatam_mlp_destroy(m);
@@ -923,7 +945,7 @@ void jatam_mlp_destroy(jatam_mlp *m)
     if (!m) return;
     MlpBuffers &b = m->b;
     void *ptrs[] = {b.p, b.grad, b.m, b.v, b.wq, b.x, b.h1, b.h2, b.dq, b.dh1, b.dh2, b.logits, b.d, b.lrow, b.loss,
-                    m->stage};
+                    b.splitk, m->stage};
     cudaDeviceSynchronize();
     for (void *p : ptrs)
         if (p) cudaFree(p);
@@ -1137,8 +1159,8 @@ int jatam_autotune(const jatam_config *shapes, uint32_t n_shapes, void *stream)
         a.key1 = (uint32_t)(cfg.seed >> 32);
         Tuning best;
         float best_ms = 1e30f;
-        for (int warps : {2, 4, 8}) {
-            const int bytes = classify_smem_bytes(S, warps);
+        for (int warps : {2, 3, 4, 5, 6}) {
+            const int bytes = classify_smem_bytes(S, tuple_table_size(cfg.n), warps);
             if (bytes > 200 * 1024) continue;
             for (int stop : {4, 8, 12, 16, 20, 24, 28}) {
                 Tuning t;
@@ -1167,11 +1189,15 @@ int jatam_set_tuning(const jatam_config *cfg, int warps_per_cta, int stop_at)
     std::lock_guard<std::mutex> lock(g_mutex);
     g_last_error.clear();
     if (!cfg) return fail(JATAM_EINVAL, "cfg is NULL");
-    if (warps_per_cta < 1 || warps_per_cta > 8 || stop_at < 1 || stop_at > 32)
-        return fail(JATAM_EINVAL, "warps_per_cta must be 1..8 and stop_at 1..32");
     if (cfg->L < 1 || cfg->L > JATAM_MAX_GRID) return fail(JATAM_EUNSUPPORTED, "L must be 1..32");
     const int S = lattice_template(cfg->L);
-    if (classify_smem_bytes(S, warps_per_cta) > 200 * 1024)
+    if (warps_per_cta == 0) {
+        g_tuned.erase(std::make_tuple(S, (int)cfg->n, (int)cfg->c));
+        return JATAM_OK;
+    }
+    if (warps_per_cta < 1 || warps_per_cta > MAX_CTA_WARPS || stop_at < 1 || stop_at > 32)
+        return fail(JATAM_EINVAL, "warps_per_cta must be 0..%d and stop_at 1..32", MAX_CTA_WARPS);
+    if (classify_smem_bytes(S, tuple_table_size(cfg->n), warps_per_cta) > 200 * 1024)
         return fail(JATAM_EINVAL, "%d warps of a %dx%d lattice do not fit in shared memory", warps_per_cta, S, S);
     Tuning t;
     t.warps = warps_per_cta;

@@ -73,11 +73,19 @@ struct LaunchArgs {
     unsigned *err;                  // sticky error bits
 };
 
-// Lattice template: rows of S bits, S in {8, 16, 32}, L <= S.
-int classify_smem_bytes(int S, int warps_per_cta);
-cudaError_t classify_set_attributes(int S, int warps_per_cta);
-cudaError_t classify_occupancy(int S, int warps_per_cta, int *blocks_per_sm);
-cudaError_t launch_classify(const LaunchArgs &a, int S, int blocks, int warps_per_cta, cudaStream_t st);
+// Lattice template: rows of S bits, S in {8, 16, 32}, L <= S; nt = 8 tuple ids
+// (sets of at most two tiles, uniform launches only) or 16.
+int classify_smem_bytes(int S, int nt, int warps_per_cta);
+cudaError_t classify_set_attributes(int S, int nt, int warps_per_cta);
+cudaError_t classify_occupancy(int S, int nt, int warps_per_cta, int *blocks_per_sm);
+cudaError_t launch_classify(const LaunchArgs &a, int S, int nt, int blocks, int warps_per_cta, cudaStream_t st);
+// largest CTA of classify_kernel (its launch bounds hold it to 113 registers so
+// that three such CTAs fit an SM)
+constexpr int MAX_CTA_WARPS = 6;
+// warps per CTA that keep the most warps resident on an SM
+int default_warps_per_cta(int S, int nt);
+// tuple-table size of a uniform launch of n-tile sets
+inline int tuple_table_size(int n) { return (n >= 1 && n <= 2) ? 8 : 16; }
 int classify_mixed_smem_bytes(int w32, int w16, int w8);
 cudaError_t classify_mixed_prepare(int w32, int w16, int w8, int *blocks_per_sm);
 cudaError_t launch_classify_mixed(const LaunchArgs &a, int blocks, cudaStream_t st);
@@ -125,7 +133,9 @@ struct MlpBuffers {
     long long cap;               // batch capacity of the activation buffers
     __nv_bfloat16 *x, *h1, *h2, *dq, *dh1, *dh2;
     float *logits, *d, *lrow, *loss;
+    float *splitk;               // [MLP_SPLITK_MAX][256 x 256] partial weight gradients (split-K)
 };
+constexpr int MLP_SPLITK_MAX = 32;
 cudaError_t mlp_forward(const MlpBuffers &b, const unsigned long long *genomes, long long B, cudaStream_t st);
 cudaError_t mlp_backward(const MlpBuffers &b, const uint8_t *labels, long long B, cudaStream_t st);
 cudaError_t mlp_adam(const MlpBuffers &b, float lr, int t, cudaStream_t st);
@@ -133,9 +143,20 @@ cudaError_t mlp_refresh_bf16(const MlpBuffers &b, cudaStream_t st);
 cudaError_t launch_mlp_labels(const jatam_result *res, long long n, uint8_t *labels, cudaStream_t st);
 cudaError_t launch_embed(const unsigned long long *in, long long n, int tiles, int bits_per_colour,
                          unsigned long long *out, cudaStream_t st);
-// scores of n candidates from their logits; idx = the `keep` best, chosen = cand[idx]
+// scratch of the screen's de-duplication: a table of cap_mask + 1 (a power of
+// two >= 2n) slots and the slot of each of the n candidates
+struct ScreenTable {
+    unsigned long long *keys;
+    unsigned *first, *slot, *err;
+    unsigned cap_mask;
+};
+// scores of n candidates from their logits: the network's probability of a
+// deterministic bounded shape of >= 8 tiles, plus one for the first occurrence
+// of each distinct genome (repeats rank below every distinct genome); idx = the
+// `keep` best (ties: lower index), chosen = cand[idx]
 cudaError_t launch_screen(const float *logits, long long n, long long keep, float *score, unsigned long long *idx,
-                          const unsigned long long *cand, unsigned long long *chosen, cudaStream_t st);
+                          const unsigned long long *cand, unsigned long long *chosen, const ScreenTable &t,
+                          cudaStream_t st);
 
 // the message returned by jatam_last_error() for the calling thread
 void set_last_error(const char *msg);

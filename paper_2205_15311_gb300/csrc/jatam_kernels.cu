@@ -18,8 +18,9 @@
 //   FRONT[NW]  frontier: empty in-grid sites with exactly one distinct candidate
 //   NIB[S*S/8] 4-bit tuple id per cell: the placed tuple of an occupied cell or
 //              the single candidate of a frontier cell
-//   NBM[32]    NBM[2 t + d/2] >> 16 (d & 1): the set of tuple ids that can
-//              attach on side d of a placed tuple t (16 bits)
+//   NBM[2 NT]  NBM[2 t + d/2] >> 16 (d & 1): the set of tuple ids that can
+//              attach on side d of a placed tuple t (16 bits); NT = 8 tuple
+//              ids for sets of at most two tiles, else 16
 // A tuple id is the lowest (tile, rotation) index 4 t + r with that rotated
 // colour tuple, so equal tuples (repeated tile types, symmetric tiles) share
 // an id and never count as ambiguity (Section 2.4).
@@ -27,10 +28,29 @@
 #include <cstdint>
 #include <cuda_runtime.h>
 
+#include <map>
+#include <mutex>
+#include <tuple>
+
 #include "jatam_device.cuh"
 #include "jatam_internal.cuh"
 
 namespace jatam {
+
+// Per-lane shared-memory layout of a lattice with rows of S bits.
+template <int S, int NT = 16>
+struct Geo {
+    static constexpr int NW = (S * S) / 32;  // words per bitmap
+    static constexpr int LOG2S = (S == 8) ? 3 : (S == 16) ? 4 : 5;
+    static constexpr int OCCA = 0;
+    static constexpr int OCCB = NW;
+    static constexpr int FRONT = 2 * NW;
+    static constexpr int NIB = 3 * NW;
+    static constexpr int NBM = 3 * NW + (S * S) / 8;  // 2 words per tuple id: NT = 8 (<= 2 tiles) or 16
+    static constexpr int CACHE = NBM + 2 * NT;  // per-warp shape cache: entry j in "lane" j's bank
+    static constexpr int WORDS = CACHE + 3;      // 32-bit words per lane
+};
+
 namespace {
 
 constexpr unsigned FULL = 0xffffffffu;
@@ -39,18 +59,6 @@ constexpr int CHUNK = 32;        // items taken from the global counter at once
 
 enum Phase : int { PH_NEED = 0, PH_INIT, PH_START, PH_GROW, PH_SHAPE, PH_WRITE, PH_DONE };
 
-template <int S>
-struct Geo {
-    static constexpr int NW = (S * S) / 32;  // words per bitmap
-    static constexpr int LOG2S = (S == 8) ? 3 : (S == 16) ? 4 : 5;
-    static constexpr int OCCA = 0;
-    static constexpr int OCCB = NW;
-    static constexpr int FRONT = 2 * NW;
-    static constexpr int NIB = 3 * NW;
-    static constexpr int NBM = 3 * NW + (S * S) / 8;
-    static constexpr int CACHE = NBM + 32;  // per-warp shape cache: entry j in "lane" j's bank
-    static constexpr int WORDS = CACHE + 3;  // 32-bit words per lane
-};
 
 // Jenkins one-at-a-time, one byte at a time (Section 2.5).
 __device__ __forceinline__ uint32_t oaat_add(uint32_t h, uint32_t byte)
@@ -112,6 +120,7 @@ struct Lane {
     unsigned long long cols;  // colour of edge e of tile t at nibble 4 t + e
     int n, c, L, k;
     int rep, step, size, size0, nF;
+    unsigned long long fc;       // lattices with at most 8 frontier words: byte w = sites in word w
     int ymin, ymax, xmin, xmax;  // bounding box of the current replicate
     int x0, x1, y0, y1;          // bounding box of replicate 0
     int dlo, dhi;                // rows that may be dirty in any bitmap
@@ -377,12 +386,13 @@ __device__ __forceinline__ void replicate_end(Lane &Ls, uint32_t *my, bool nd, b
             // of replicate 0 had a single frontier site, so every replicate
             // follows the same path; or the final configuration A0 is closed:
             // for every two adjacent tiles of A0, what either one offers the
-            // other's cell is that cell's tuple or nothing, and replicate 0
+            // other's cell is that cell's tuple or nothing (offers to the seed's
+            // cell aside: the seed is always there first), and replicate 0
             // ended with no candidate outside A0.  Then, in any order, every
-            // site a replicate can reach receives only A0's tuple there, no
-            // site ever sees two distinct candidates, nothing attaches outside
-            // A0, and the frontier empties only when all of A0 (connected
-            // through its bonds) is placed: all k replicates end in A0.
+            // empty site a replicate can reach receives only A0's tuple there,
+            // no site ever sees two distinct candidates, nothing attaches
+            // outside A0, and the frontier empties only when all of A0
+            // (connected through its bonds) is placed: all k replicates end in A0.
             Ls.cls = JATAM_DET_BOUNDED;
             Ls.decided = Ls.k;
             Ls.phase = PH_SHAPE;
@@ -444,18 +454,32 @@ __device__ __forceinline__ void lane_step(Lane &Ls, uint32_t *my, uint32_t k0, u
         if (Ls.nF > 1) Ls.forced = 0;
         const int sel = Ls.step & 3;
         const uint32_t u = sel == 0 ? Ls.pa.x : sel == 1 ? Ls.pa.y : sel == 2 ? Ls.pa.z : Ls.pa.w;
+        // rank i of the chosen site among the frontier sites in row-major order
         uint32_t i = placing ? __umulhi(u, (uint32_t)Ls.nF) : 0u;
-        int w = (max(Ls.ymin - 1, 0) * S) >> 5;
-        uint32_t f = my[(G::FRONT + w) * 32];
-        uint32_t cnt = placing ? __popc(f) : 1u;
-        while (i >= cnt) {
-            i -= cnt;
-            if (++w >= G::NW) break;
+        int w;
+        uint32_t f;
+        if constexpr (G::NW <= 8) {
+            // the word holding it, from the packed per-word site counts: byte j
+            // of P is the number of sites in words 0..j (at most L * L - 1 <=
+            // 255, so the bytes never carry)
+            const unsigned long long P = Ls.fc * 0x0101010101010101ull;
+            const uint32_t ii = i * 0x01010101u;
+            w = (__popc(__vcmpleu4((uint32_t)P, ii)) + __popc(__vcmpleu4((uint32_t)(P >> 32), ii))) >> 3;
+            if (w > 0) i -= (uint32_t)(P >> (8 * (w - 1))) & 255u;
+            f = my[(G::FRONT + min(w, G::NW - 1)) * 32];
+        } else {
+            w = (max(Ls.ymin - 1, 0) * S) >> 5;
             f = my[(G::FRONT + w) * 32];
-            cnt = __popc(f);
+            uint32_t cnt = placing ? __popc(f) : 1u;
+            while (i >= cnt) {
+                i -= cnt;
+                if (++w >= G::NW) break;
+                f = my[(G::FRONT + w) * 32];
+                cnt = __popc(f);
+            }
         }
         if (!placing) {
-        } else if (w >= G::NW) {
+        } else if (w >= G::NW || i >= (uint32_t)__popc(f)) {
             atomicOr(err, ERR_GUARD);
             Ls.cls = 255;
             Ls.phase = PH_WRITE;
@@ -465,6 +489,7 @@ __device__ __forceinline__ void lane_step(Lane &Ls, uint32_t *my, uint32_t k0, u
             b = w * 32 + bit;
             tau = nib_get<S>(my, b);
             my[(G::FRONT + w) * 32] = f & ~(1u << bit);
+            if constexpr (G::NW <= 8) Ls.fc -= 1ull << (8 * w);
             Ls.nF -= 1;
             Ls.step += 1;
         }
@@ -476,6 +501,7 @@ __device__ __forceinline__ void lane_step(Lane &Ls, uint32_t *my, uint32_t k0, u
         Ls.size = 0;
         Ls.step = 0;
         Ls.nF = 0;
+        Ls.fc = 0ull;
         Ls.diverged = 0;
         Ls.forced = 1;
         Ls.cert = 1;
@@ -483,6 +509,7 @@ __device__ __forceinline__ void lane_step(Lane &Ls, uint32_t *my, uint32_t k0, u
     }
     __syncwarp();
     const int px = b & (S - 1), py = b >> G::LOG2S;
+
     if (placing) {
         my[(occ + (b >> 5)) * 32] |= 1u << (b & 31);
         if (seed && Ls.rep == 0) nib_set<S>(my, b, 0);
@@ -504,6 +531,7 @@ __device__ __forceinline__ void lane_step(Lane &Ls, uint32_t *my, uint32_t k0, u
     // case, so the warp stays converged.
     const uint32_t m01 = my[(G::NBM + 2 * tau) * 32];
     const uint32_t m23 = my[(G::NBM + 2 * tau + 1) * 32];
+    const int seed_cell = (Ls.L >> 1) * S + (Ls.L >> 1);
     bool nd = false, unb = false;
 #pragma unroll
     for (int d = 0; d < 4; ++d) {
@@ -528,8 +556,9 @@ __device__ __forceinline__ void lane_step(Lane &Ls, uint32_t *my, uint32_t k0, u
         // one candidate outside the grid: growth past the cap
         unb = unb || (!in && M != 0 && !multi);
         // replicate 0: an occupied neighbour that could receive from the new
-        // tile a tuple other than its own breaks the closure of the final shape
-        if (placing && Ls.rep == 0 && in && (ow & qbit) && (M & ~(1u << tq)) != 0) Ls.cert = 0;
+        // tile a tuple other than its own breaks the closure of the final
+        // shape -- unless it is the seed, which every replicate places first
+        if (placing && Ls.rep == 0 && in && (ow & qbit) && (M & ~(1u << tq)) != 0 && qb != seed_cell) Ls.cert = 0;
         if (placing && empty && !isf && M != 0 && !multi) {
             const int tn = __ffs(M) - 1;
             // replicate 0 must hold the same tuple here, or this replicate can
@@ -537,6 +566,7 @@ __device__ __forceinline__ void lane_step(Lane &Ls, uint32_t *my, uint32_t k0, u
             if (Ls.rep > 0 && !Ls.diverged && (!(my[(G::OCCA + qw) * 32] & qbit) || tq != tn)) Ls.diverged = 1;
             my[(G::NIB + (qb >> 3)) * 32] = (nw & ~(15u << sh)) | ((uint32_t)tn << sh);
             my[(G::FRONT + qw) * 32] = fw | qbit;
+            if constexpr (G::NW <= 8) Ls.fc += 1ull << (8 * qw);
             Ls.nF += 1;
         }
     }
@@ -577,22 +607,22 @@ struct SmemHist {
     unsigned smin[HIST_SLOTS];
 };
 
-__device__ __forceinline__ void hist_insert(SmemHist &H, const Table &T, unsigned long long key,
-                                            unsigned long long id, unsigned size, unsigned *err)
+__device__ __forceinline__ void hist_insert(SmemHist &H, const Table &T, unsigned long long key, unsigned cnt,
+                                            unsigned long long id, unsigned smax, unsigned smin, unsigned *err)
 {
     unsigned slot = table_slot(key, 8);
     for (int p = 0; p < 16; ++p) {
         const unsigned long long old = atomicCAS(&H.key[slot], EMPTY_KEY, key);
         if (old == EMPTY_KEY || old == key) {
-            atomicAdd(&H.count[slot], 1u);
+            atomicAdd(&H.count[slot], cnt);
             atomicMin(&H.min_id[slot], id);
-            atomicMax(&H.smax[slot], size);
-            atomicMin(&H.smin[slot], size);
+            atomicMax(&H.smax[slot], smax);
+            atomicMin(&H.smin[slot], smin);
             return;
         }
         slot = (slot + 1) & (HIST_SLOTS - 1);
     }
-    table_insert(T, key, 1ull, id, size, size, err);
+    table_insert(T, key, cnt, id, smax, smin, err);
 }
 
 // decode a packed genotype into nibble-packed colours (tiles seed first,
@@ -773,13 +803,13 @@ __global__ void __launch_bounds__(256) prefilter_kernel(const LaunchArgs a, int 
 // The work of one warp over one list of items (a pre-filter list): every
 // lane takes items from the list through the shared counter `work_next` and
 // the warp runs them to their class in batched phases.  `warp_lanes` is the
-// warp's interleaved region of Geo<S>::WORDS words per lane.
-template <int S>
+// warp's interleaved region of Geo<S, NT>::WORDS words per lane.
+template <int S, int NT>
 __device__ __forceinline__ void warp_loop(const LaunchArgs &a, uint32_t *warp_lanes, SmemHist &H,
                                           const unsigned long long *list, unsigned long long total,
                                           unsigned long long *work_next)
 {
-    using G = Geo<S>;
+    using G = Geo<S, NT>;
     const int lane = threadIdx.x & 31;
     uint32_t *my = warp_lanes + lane;
     for (int w = 0; w < 3 * G::NW; ++w) my[w * 32] = 0u;
@@ -797,6 +827,7 @@ __device__ __forceinline__ void warp_loop(const LaunchArgs &a, uint32_t *warp_la
     Ls.cls = 0; Ls.decided = 0; Ls.hash = 0; Ls.size0 = 0;
     Ls.item = 0; Ls.sid = 0; Ls.cols = 0;
     Ls.rep = Ls.step = Ls.size = Ls.nF = 0;
+    Ls.fc = 0ull;
     Ls.x0 = Ls.x1 = Ls.y0 = Ls.y1 = 0;
     unsigned long long st_draw = 0, st_seed = 0, st_slots = 0, st_geno = 0;  // executed work (a.stats)
     Ls.ymin = Ls.ymax = Ls.xmin = Ls.xmax = 0;
@@ -818,7 +849,7 @@ __device__ __forceinline__ void warp_loop(const LaunchArgs &a, uint32_t *warp_la
                 const uint32_t hash = shaped ? Ls.hash : 0u;
                 write_result(a, Ls.item, Ls.cls, Ls.decided, size, hash);
                 if (a.use_hist && Ls.cls != 255)
-                    hist_insert(H, a.table, ((unsigned long long)Ls.cls << 32) | hash, Ls.sid, size, a.err);
+                    hist_insert(H, a.table, ((unsigned long long)Ls.cls << 32) | hash, 1u, Ls.sid, size, size, a.err);
                 Ls.phase = PH_NEED;
             }
             const unsigned need = __ballot_sync(FULL, Ls.phase == PH_NEED);
@@ -859,9 +890,9 @@ __device__ __forceinline__ void warp_loop(const LaunchArgs &a, uint32_t *warp_la
         }
         // ---- binding tables of the genotypes that grow, one warp-wide job each
         unsigned init = __ballot_sync(FULL, Ls.phase == PH_INIT);
-        if (a.n <= 2 && !(a.mode == MODE_RECORDS && a.shapes)) {
+        if (NT == 8 || (a.n <= 2 && !(a.mode == MODE_RECORDS && a.shapes))) {
             while (init) coop_tables<S, 8>(init, warp_lanes, Ls, lane);
-        } else {
+        } else if constexpr (NT == 16) {
             while (init) coop_tables<S, 16>(init, warp_lanes, Ls, lane);
         }
         __syncwarp();
@@ -880,9 +911,9 @@ __device__ __forceinline__ void warp_loop(const LaunchArgs &a, uint32_t *warp_la
             Ls.rep = 0;
             Ls.phase = PH_START;
             st_geno += 1;
+            // the first Philox block comes from the growth rounds' batched fetch
             Ls.ka = NO_BLOCK;
-            Ls.pb = philox_block(0u, Ls.sid, a.key0, a.key1);
-            Ls.kb = 0u;
+            Ls.kb = NO_BLOCK;
         }
         if (__all_sync(FULL, Ls.phase == PH_DONE)) break;
 
@@ -1007,16 +1038,17 @@ __device__ __forceinline__ void hist_end(SmemHist &H, const LaunchArgs &a)
 }
 
 // One lattice template for every warp: the items of pre-filter list a.klass.
-template <int S>
-__global__ void __launch_bounds__(256) classify_kernel(const LaunchArgs a)
+// CTAs of at most MAX_CTA_WARPS warps, three of which fit an SM's registers.
+template <int S, int NT>
+__global__ void __launch_bounds__(MAX_CTA_WARPS * 32, 3) classify_kernel(const LaunchArgs a)
 {
     extern __shared__ uint32_t smem_lanes[];
     __shared__ SmemHist H;
     hist_begin(H);
     const int warp = threadIdx.x >> 5;
-    uint32_t *warp_lanes = smem_lanes + (size_t)warp * Geo<S>::WORDS * 32;
-    warp_loop<S>(a, warp_lanes, H, a.list + (size_t)a.klass * a.list_stride, a.list_count[a.klass],
-                 a.work_next + a.klass);
+    uint32_t *warp_lanes = smem_lanes + (size_t)warp * Geo<S, NT>::WORDS * 32;
+    warp_loop<S, NT>(a, warp_lanes, H, a.list + (size_t)a.klass * a.list_stride, a.list_count[a.klass],
+                     a.work_next + a.klass);
     hist_end(H, a);
 }
 
@@ -1037,14 +1069,14 @@ __global__ void __launch_bounds__(256) classify_mixed_kernel(const LaunchArgs a)
     if (warp < w32) {
         uint32_t *wl = smem_lanes + (size_t)warp * R32;
         for (int c = 2; c >= 0; --c)
-            warp_loop<32>(a, wl, H, a.list + (size_t)c * a.list_stride, a.list_count[c], a.work_next + c);
+            warp_loop<32, 16>(a, wl, H, a.list + (size_t)c * a.list_stride, a.list_count[c], a.work_next + c);
     } else if (warp < w32 + w16) {
         uint32_t *wl = smem_lanes + (size_t)w32 * R32 + (size_t)(warp - w32) * R16;
         for (int c = 1; c >= 0; --c)
-            warp_loop<16>(a, wl, H, a.list + (size_t)c * a.list_stride, a.list_count[c], a.work_next + c);
+            warp_loop<16, 16>(a, wl, H, a.list + (size_t)c * a.list_stride, a.list_count[c], a.work_next + c);
     } else {
         uint32_t *wl = smem_lanes + (size_t)w32 * R32 + (size_t)w16 * R16 + (size_t)(warp - w32 - w16) * R8;
-        warp_loop<8>(a, wl, H, a.list, a.list_count[0], a.work_next);
+        warp_loop<8, 16>(a, wl, H, a.list, a.list_count[0], a.work_next);
     }
     hist_end(H, a);
 }
@@ -1138,51 +1170,96 @@ __global__ void philox_kernel(const uint32_t *in, unsigned long long n, uint32_t
     }
 }
 
-template <int S>
-int smem_bytes_for(int warps) { return warps * Geo<S>::WORDS * 32 * 4; }
+template <int S, int NT>
+int smem_bytes_for(int warps) { return warps * Geo<S, NT>::WORDS * 32 * 4; }
+
+// the instance for lattice template S and tuple-table size nt
+template <typename F>
+auto with_instance(int S, int nt, F f)
+{
+    if (nt == 8) {
+        switch (S) {
+        case 8: return f(classify_kernel<8, 8>, smem_bytes_for<8, 8>);
+        case 16: return f(classify_kernel<16, 8>, smem_bytes_for<16, 8>);
+        default: return f(classify_kernel<32, 8>, smem_bytes_for<32, 8>);
+        }
+    }
+    switch (S) {
+    case 8: return f(classify_kernel<8, 16>, smem_bytes_for<8, 16>);
+    case 16: return f(classify_kernel<16, 16>, smem_bytes_for<16, 16>);
+    default: return f(classify_kernel<32, 16>, smem_bytes_for<32, 16>);
+    }
+}
 
 }  // namespace
 
-int classify_smem_bytes(int S, int warps_per_cta)
+int classify_smem_bytes(int S, int nt, int warps_per_cta)
 {
-    switch (S) {
-    case 8: return smem_bytes_for<8>(warps_per_cta);
-    case 16: return smem_bytes_for<16>(warps_per_cta);
-    default: return smem_bytes_for<32>(warps_per_cta);
-    }
+    return with_instance(S, nt, [&](auto, auto bytes_for) { return bytes_for(warps_per_cta); });
 }
 
-cudaError_t classify_set_attributes(int S, int warps_per_cta)
+cudaError_t classify_set_attributes(int S, int nt, int warps_per_cta)
 {
-    const int bytes = classify_smem_bytes(S, warps_per_cta);
-    switch (S) {
-    case 8: return cudaFuncSetAttribute(classify_kernel<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-    case 16: return cudaFuncSetAttribute(classify_kernel<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-    default: return cudaFuncSetAttribute(classify_kernel<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-    }
+    // The kernel's dynamic shared-memory limit is per device and shared by every
+    // caller of the library, so it only ever grows: a caller that needs less
+    // never lowers it under a launch that needs more.
+    static std::mutex mu;
+    static std::map<std::tuple<int, int, int>, int> limit;  // (device, S, nt) -> bytes set
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    const int bytes = classify_smem_bytes(S, nt, warps_per_cta);
+    std::lock_guard<std::mutex> lock(mu);
+    int &have = limit[std::make_tuple(dev, S, nt)];
+    if (bytes <= have) return cudaSuccess;
+    e = with_instance(S, nt, [&](auto kernel, auto) {
+        return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    });
+    if (e == cudaSuccess) have = bytes;
+    return e;
 }
 
-cudaError_t classify_occupancy(int S, int warps_per_cta, int *blocks_per_sm)
+cudaError_t classify_occupancy(int S, int nt, int warps_per_cta, int *blocks_per_sm)
 {
-    const int bytes = classify_smem_bytes(S, warps_per_cta);
-    const int threads = warps_per_cta * 32;
-    switch (S) {
-    case 8: return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, classify_kernel<8>, threads, bytes);
-    case 16: return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, classify_kernel<16>, threads, bytes);
-    default: return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, classify_kernel<32>, threads, bytes);
-    }
+    return with_instance(S, nt, [&](auto kernel, auto bytes_for) {
+        return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, kernel, warps_per_cta * 32,
+                                                             bytes_for(warps_per_cta));
+    });
 }
 
-cudaError_t launch_classify(const LaunchArgs &a, int S, int blocks, int warps_per_cta, cudaStream_t st)
+int default_warps_per_cta(int S, int nt)
 {
-    const int bytes = classify_smem_bytes(S, warps_per_cta);
-    const dim3 grid(blocks), block(warps_per_cta * 32);
-    switch (S) {
-    case 8: classify_kernel<8><<<grid, block, bytes, st>>>(a); break;
-    case 16: classify_kernel<16><<<grid, block, bytes, st>>>(a); break;
-    default: classify_kernel<32><<<grid, block, bytes, st>>>(a); break;
+    // the CTA size that keeps the most warps resident on an SM (ties: the larger CTA)
+    static int cache[2][3] = {{0, 0, 0}, {0, 0, 0}};
+    int &c = cache[nt == 8 ? 0 : 1][S == 8 ? 0 : S == 16 ? 1 : 2];
+    if (c) return c;
+    int best = 1, best_warps = 0;
+    for (int w = MAX_CTA_WARPS; w >= 1; --w) {
+        if (classify_smem_bytes(S, nt, w) > 200 * 1024) continue;
+        if (classify_set_attributes(S, nt, w) != cudaSuccess) {  // the occupancy query needs the limit
+            cudaGetLastError();
+            continue;
+        }
+        int per_sm = 0;
+        if (classify_occupancy(S, nt, w, &per_sm) != cudaSuccess) {
+            cudaGetLastError();
+            continue;
+        }
+        if (per_sm * w > best_warps) {
+            best_warps = per_sm * w;
+            best = w;
+        }
     }
-    return cudaGetLastError();
+    c = best;
+    return c;
+}
+
+cudaError_t launch_classify(const LaunchArgs &a, int S, int nt, int blocks, int warps_per_cta, cudaStream_t st)
+{
+    return with_instance(S, nt, [&](auto kernel, auto bytes_for) {
+        kernel<<<dim3(blocks), dim3(warps_per_cta * 32), bytes_for(warps_per_cta), st>>>(a);
+        return cudaGetLastError();
+    });
 }
 
 int classify_mixed_smem_bytes(int w32, int w16, int w8)
@@ -1193,8 +1270,22 @@ int classify_mixed_smem_bytes(int w32, int w16, int w8)
 cudaError_t classify_mixed_prepare(int w32, int w16, int w8, int *blocks_per_sm)
 {
     const int bytes = classify_mixed_smem_bytes(w32, w16, w8);
-    cudaError_t e = cudaFuncSetAttribute(classify_mixed_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-    if (e != cudaSuccess) return e;
+    {
+        // grow-only, as for classify_kernel: a smaller plan never lowers the limit
+        // under a captured launch of a larger one
+        static std::mutex mu;
+        static std::map<int, int> limit;  // device -> bytes set
+        int dev = 0;
+        cudaError_t e = cudaGetDevice(&dev);
+        if (e != cudaSuccess) return e;
+        std::lock_guard<std::mutex> lock(mu);
+        int &have = limit[dev];
+        if (bytes > have) {
+            e = cudaFuncSetAttribute(classify_mixed_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+            if (e != cudaSuccess) return e;
+            have = bytes;
+        }
+    }
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, classify_mixed_kernel, (w32 + w16 + w8) * 32,
                                                          bytes);
 }

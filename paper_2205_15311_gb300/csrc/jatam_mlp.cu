@@ -9,7 +9,10 @@
 // bias + ReLU to bfloat16 (hidden layers), bias to float32 (logits), a ReLU
 // derivative mask to bfloat16 (activation gradients), or plain float32
 // (weight gradients).  The product itself is mma.sync.m16n8k16 (bf16 x bf16 ->
-// f32) from shared-memory tiles.
+// f32) from shared-memory tiles.  The weight gradients (K = the batch, only a
+// few output tiles) split K over the grid's z dimension into float32 partial
+// products that a second kernel sums in split order, so the bits do not
+// depend on scheduling.
 #include <cstdint>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
@@ -35,6 +38,7 @@ struct GemmArgs {
     const __nv_bfloat16 *mask;     // [M x N] row-major: keep where mask > 0 (EPI_MASK_BF16)
     float *Cf;                     // [M x N] row-major float32 output
     __nv_bfloat16 *Cb;             // [M x N] row-major bfloat16 output
+    int kchunk;                    // split-K: CTA z covers k in [z kchunk, (z + 1) kchunk); 0: all of K
 };
 
 __device__ __forceinline__ void mma_bf16(float (&c)[4], const uint32_t (&a)[4], const uint32_t (&b)[2])
@@ -62,17 +66,19 @@ __global__ void __launch_bounds__(128) gemm_bf16_kernel(const GemmArgs g)
 #pragma unroll
             for (int r = 0; r < 4; ++r) acc[i][j][r] = 0.f;
     const __nv_bfloat16 zero = __float2bfloat16(0.f);
-    for (int k0 = 0; k0 < g.K; k0 += TK) {
+    const int kbeg = g.kchunk ? (int)blockIdx.z * g.kchunk : 0;
+    const int kend = g.kchunk ? min(g.K, kbeg + g.kchunk) : g.K;
+    for (int k0 = kbeg; k0 < kend; k0 += TK) {
         // stage the A and B tiles (zero outside the matrices)
         for (int e = tid; e < TM * TK; e += blockDim.x) {
             const int m = e / TK, k = e % TK;
             const int gm = m0 + m, gk = k0 + k;
-            As[m][k] = (gm < g.M && gk < g.K) ? g.A[gm * g.a_m + gk * g.a_k] : zero;
+            As[m][k] = (gm < g.M && gk < kend) ? g.A[gm * g.a_m + gk * g.a_k] : zero;
         }
         for (int e = tid; e < TN * TK; e += blockDim.x) {
             const int n = e / TK, k = e % TK;
             const int gn = n0 + n, gk = k0 + k;
-            Bs[n][k] = (gn < g.N && gk < g.K) ? g.B[gk * g.b_k + gn * g.b_n] : zero;
+            Bs[n][k] = (gn < g.N && gk < kend) ? g.B[gk * g.b_k + gn * g.b_n] : zero;
         }
         __syncthreads();
         uint32_t af[2][4], bf[4][2];
@@ -109,7 +115,7 @@ __global__ void __launch_bounds__(128) gemm_bf16_kernel(const GemmArgs g)
                 float v = acc[i][j][r];
                 const long long o = (long long)m * g.N + n;
                 switch (g.epi) {
-                case EPI_F32: g.Cf[o] = v; break;
+                case EPI_F32: g.Cf[(long long)blockIdx.z * g.M * g.N + o] = v; break;
                 case EPI_BIAS_F32: g.Cf[o] = v + g.bias[n]; break;
                 case EPI_BIAS_RELU_BF16: g.Cb[o] = __float2bfloat16_rn(fmaxf(v + g.bias[n], 0.f)); break;
                 default: g.Cb[o] = __float2bfloat16_rn(__bfloat162float(g.mask[o]) > 0.f ? v : 0.f); break;
@@ -228,10 +234,39 @@ __global__ void to_bf16_kernel(const float *p, long long n, __nv_bfloat16 *pq)
         pq[i] = __float2bfloat16_rn(p[i]);
 }
 
-cudaError_t gemm(const GemmArgs &g, cudaStream_t st)
+// out[i] = sum over z of part[z][i], z in increasing order
+__global__ void splitk_sum_kernel(const float *part, int splits, long long n, float *out)
 {
-    const dim3 grid((g.N + TN - 1) / TN, (g.M + TM - 1) / TM);
-    gemm_bf16_kernel<<<grid, 128, 0, st>>>(g);
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        float s = 0.f;
+        for (int z = 0; z < splits; ++z) s += part[(long long)z * n + i];
+        out[i] = s;
+    }
+}
+
+cudaError_t gemm(const GemmArgs &g, cudaStream_t st, float *splitk = nullptr)
+{
+    const dim3 tiles((g.N + TN - 1) / TN, (g.M + TM - 1) / TM);
+    const int ntiles = (int)(tiles.x * tiles.y);
+    // a float32 product with few output tiles and a long K: split K over the grid
+    int splits = 1;
+    if (splitk && g.epi == EPI_F32 && ntiles < 64) {
+        splits = (g.K + 8 * TK - 1) / (8 * TK);                        // at least 8 k-tiles a split
+        splits = min(splits, min(MLP_SPLITK_MAX, (304 + ntiles - 1) / ntiles));  // about two CTAs per SM
+    }
+    if (splits <= 1) {
+        GemmArgs h = g;
+        h.kchunk = 0;
+        gemm_bf16_kernel<<<tiles, 128, 0, st>>>(h);
+        return cudaGetLastError();
+    }
+    GemmArgs h = g;
+    h.kchunk = ((g.K + splits - 1) / splits + TK - 1) / TK * TK;
+    splits = (g.K + h.kchunk - 1) / h.kchunk;
+    h.Cf = splitk;
+    gemm_bf16_kernel<<<dim3(tiles.x, tiles.y, splits), 128, 0, st>>>(h);
+    const long long n = (long long)g.M * g.N;
+    splitk_sum_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(splitk, splits, n, g.Cf);
     return cudaGetLastError();
 }
 
@@ -280,7 +315,7 @@ cudaError_t mlp_backward(const MlpBuffers &b, const uint8_t *labels, long long B
     // dW3 = h2^T dq  [256 x 8], K = B
     g = GemmArgs{b.h2, 1, MLP_H, b.dq, MLP_OUT, 1, MLP_H, MLP_OUT, (int)B, EPI_F32, nullptr, nullptr,
                  G + MLP_OFF_W3, nullptr};
-    if ((e = gemm(g, st)) != cudaSuccess) return e;
+    if ((e = gemm(g, st, b.splitk)) != cudaSuccess) return e;
     colsum_kernel<float><<<MLP_OUT, 256, 0, st>>>(b.d, B, MLP_OUT, G + MLP_OFF_B3);
     // dh2 = (dq W3^T) * [h2 > 0]  [B x 256], K = 8
     g = GemmArgs{b.dq, MLP_OUT, 1, b.wq + MLP_OFF_W3, 1, MLP_OUT, (int)B, MLP_H, MLP_OUT, EPI_MASK_BF16, nullptr,
@@ -289,7 +324,7 @@ cudaError_t mlp_backward(const MlpBuffers &b, const uint8_t *labels, long long B
     // dW2 = h1^T dh2  [256 x 256]
     g = GemmArgs{b.h1, 1, MLP_H, b.dh2, MLP_H, 1, MLP_H, MLP_H, (int)B, EPI_F32, nullptr, nullptr, G + MLP_OFF_W2,
                  nullptr};
-    if ((e = gemm(g, st)) != cudaSuccess) return e;
+    if ((e = gemm(g, st, b.splitk)) != cudaSuccess) return e;
     colsum_kernel<__nv_bfloat16><<<MLP_H, 256, 0, st>>>(b.dh2, B, MLP_H, G + MLP_OFF_B2);
     // dh1 = (dh2 W2^T) * [h1 > 0]  [B x 256]
     g = GemmArgs{b.dh2, MLP_H, 1, b.wq + MLP_OFF_W2, 1, MLP_H, (int)B, MLP_H, MLP_H, EPI_MASK_BF16, nullptr, b.h1,
@@ -298,7 +333,7 @@ cudaError_t mlp_backward(const MlpBuffers &b, const uint8_t *labels, long long B
     // dW1 = x^T dh1  [48 x 256]
     g = GemmArgs{b.x, 1, MLP_PAD, b.dh1, MLP_H, 1, MLP_PAD, MLP_H, (int)B, EPI_F32, nullptr, nullptr, G + MLP_OFF_W1,
                  nullptr};
-    if ((e = gemm(g, st)) != cudaSuccess) return e;
+    if ((e = gemm(g, st, b.splitk)) != cudaSuccess) return e;
     colsum_kernel<__nv_bfloat16><<<MLP_H, 256, 0, st>>>(b.dh1, B, MLP_H, G + MLP_OFF_B1);
     return cudaGetLastError();
 }
@@ -356,7 +391,7 @@ __global__ void embed_kernel(const unsigned long long *in, long long count, int 
 // expected shape size under the predicted class probabilities
 __global__ void score_kernel(const float *logits, long long n, float *score)
 {
-    const float value[MLP_OUT] = {0.f, 0.f, 0.f, 1.f, 2.5f, 5.5f, 11.5f, 20.f};
+    // probability of a deterministic bounded shape of at least 8 tiles (classes 6, 7)
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
         const float *z = logits + i * MLP_OUT;
         float mx = z[0];
@@ -365,7 +400,7 @@ __global__ void score_kernel(const float *logits, long long n, float *score)
         for (int c = 0; c < MLP_OUT; ++c) {
             const float p = expf(z[c] - mx);
             s += p;
-            e += p * value[c];
+            if (c >= 6) e += p;
         }
         score[i] = e / s;
     }
@@ -471,10 +506,47 @@ cudaError_t launch_embed(const unsigned long long *in, long long n, int tiles, i
     return cudaGetLastError();
 }
 
+// Distinct candidates: an open-addressing table (capacity a power of two >= 2n,
+// keys ~0 = empty) keeps the smallest index of each genome; slot[i] is the
+// slot of candidate i.
+__global__ void dedup_insert_kernel(const unsigned long long *cand, long long n, unsigned long long *keys,
+                                    unsigned *first, unsigned cap_mask, unsigned *slot, unsigned *err)
+{
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const unsigned long long g = cand[i];
+        unsigned h = (unsigned)((g * 0x9E3779B97F4A7C15ull) >> 32) & cap_mask;
+        bool done = false;
+        for (unsigned p = 0; p <= cap_mask && !done; ++p) {
+            const unsigned long long old = atomicCAS(&keys[h], ~0ull, g);
+            if (old == ~0ull || old == g) {
+                atomicMin(&first[h], (unsigned)i);
+                slot[i] = h;
+                done = true;
+            } else {
+                h = (h + 1) & cap_mask;
+            }
+        }
+        if (!done) atomicOr(err, 1u);  // unreachable: the table holds at least 2n slots
+    }
+}
+
+// the first occurrence of each genome scores one above every repeat
+__global__ void dedup_mark_kernel(float *score, long long n, const unsigned *first, const unsigned *slot)
+{
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        if (first[slot[i]] == (unsigned)i) score[i] += 1.f;
+}
+
 cudaError_t launch_screen(const float *logits, long long n, long long keep, float *score, unsigned long long *idx,
-                          const unsigned long long *cand, unsigned long long *chosen, cudaStream_t st)
+                          const unsigned long long *cand, unsigned long long *chosen, const ScreenTable &t,
+                          cudaStream_t st)
 {
     score_kernel<<<grid_of(n), 256, 0, st>>>(logits, n, score);
+    cudaError_t e = cudaMemsetAsync(t.keys, 0xFF, (size_t)(t.cap_mask + 1) * 8, st);
+    if (e != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(t.first, 0xFF, (size_t)(t.cap_mask + 1) * 4, st)) != cudaSuccess) return e;
+    dedup_insert_kernel<<<grid_of(n), 256, 0, st>>>(cand, n, t.keys, t.first, t.cap_mask, t.slot, t.err);
+    dedup_mark_kernel<<<grid_of(n), 256, 0, st>>>(score, n, t.first, t.slot);
     topn_kernel<<<1, 1024, 0, st>>>(score, n, keep, idx);
     gather_kernel<<<grid_of(keep), 256, 0, st>>>(cand, idx, keep, chosen);
     return cudaGetLastError();

@@ -40,7 +40,6 @@ struct DeviceState {
     bool ready = false;
     unsigned char *scratch = nullptr;  // device address of g_noalloc_scratch on this device
     int num_sms = 0;
-    int smem_set[3] = {0, 0, 0};
 };
 DeviceState g_dev[MAX_DEVICES];
 std::mutex g_noalloc_mutex;
@@ -137,18 +136,14 @@ extern "C" int jatam_enumerate_noalloc(const jatam_config *cfg, uint64_t first, 
     a.err = err;
 
     const int S = lattice_template_of(L);
-    const int warps = (S == 32) ? 2 : 8;
-    const int si = S == 8 ? 0 : S == 16 ? 1 : 2;
-    const int bytes = classify_smem_bytes(S, warps);
-    if (bytes > d->smem_set[si]) {
-        if (classify_set_attributes(S, warps) != cudaSuccess) {
-            cudaGetLastError();
-            return noalloc_fail(JATAM_ECUDA, "cudaFuncSetAttribute failed");
-        }
-        d->smem_set[si] = bytes;
+    const int nt = tuple_table_size(cfg->n);
+    const int warps = default_warps_per_cta(S, nt);
+    if (classify_set_attributes(S, nt, warps) != cudaSuccess) {
+        cudaGetLastError();
+        return noalloc_fail(JATAM_ECUDA, "cudaFuncSetAttribute failed");
     }
     int per_sm = 0;
-    if (classify_occupancy(S, warps, &per_sm) != cudaSuccess || per_sm < 1) {
+    if (classify_occupancy(S, nt, warps, &per_sm) != cudaSuccess || per_sm < 1) {
         cudaGetLastError();
         return noalloc_fail(JATAM_ECUDA, "classification kernel does not fit on an SM");
     }
@@ -163,7 +158,7 @@ extern "C" int jatam_enumerate_noalloc(const jatam_config *cfg, uint64_t first, 
         long long pblocks = (long long)((count + 255) / 256);
         if (pblocks > 8LL * d->num_sms) pblocks = 8LL * d->num_sms;
         if (launch_prefilter(a, S, (int)pblocks, st) != cudaSuccess) return noalloc_fail(JATAM_ECUDA, "launch failed");
-        if (launch_classify(a, S, (int)blocks, warps, st) != cudaSuccess)
+        if (launch_classify(a, S, nt, (int)blocks, warps, st) != cudaSuccess)
             return noalloc_fail(JATAM_ECUDA, "launch failed");
     }
     if (cfg->flags & JATAM_SYNC) {

@@ -46,7 +46,8 @@ def build_training_set(torch, device, *, s28_sample=1 << 21, s38_sample=1 << 21,
 
     add(np.arange(1 << 16, dtype=np.uint64), 2, 4, 16, 10, 1)
     add(W.random_genomes(s28_sample, 2, 8, seed=12), 2, 8, 16, 20, 2)
-    add(W.random_genomes(s38_sample, 3, 8, seed=13), 3, 8, L, k, seed38)
+    if s38_sample:
+        add(W.random_genomes(s38_sample, 3, 8, seed=13), 3, 8, L, k, seed38)
     genomes = torch.cat(parts_g)
     labels = torch.cat(parts_y)
     torch.cuda.synchronize()

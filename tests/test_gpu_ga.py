@@ -117,3 +117,42 @@ def test_ga_run_shape_fitness_matches_oracle():
     torch.cuda.synchronize()
     assert best.cpu().tolist() == want_best and total.cpu().tolist() == want_total
     assert np.array_equal(pop.cpu().numpy().view(np.uint64), want_pop)
+
+
+def test_screened_ga_reaches_the_best_shape_with_fewer_simulations():
+    """The network as a pre-screen pays: at the same number
+    of simulations, 5 generations of N = 2048 survivors (every survivor
+    simulated by the plain classification), the screened GA reaches a verified
+    best fitness of 32 in more of 12 independent runs than the plain GA, and its
+    mean verified best is higher."""
+    from paper_2205_15311_gb300 import surrogate as S
+    dev = torch.device("cuda")
+    genomes, labels = S.build_training_set(torch, dev, s28_sample=1 << 21, s38_sample=1 << 21)
+    perm = torch.from_numpy(np.random.default_rng(1).permutation(genomes.shape[0])).to(dev)
+    genomes, labels = genomes[perm].contiguous(), labels[perm].contiguous()
+    net = J.Surrogate(max_batch=1 << 17)
+    net.set_params(S.initial_params(0))
+    S.train(torch, net, genomes, labels, steps=3000, batch=8192, lr=2e-3)
+    trained = net.get_params()
+    N, G, ratio = 2048, 5, 4
+    thr = J.poisson_thresholds(0.03)
+    best_plain, best_screened = [], []
+    for sd in range(12):
+        pop0 = W.random_genomes(N, 3, 8, seed=100 + sd)
+        ga = J.make_ga(3, 8, 500 + sd, selection=J.TOURNAMENT, tournament=4, crossover=J.ONE_POINT,
+                       crossover_threshold=0x80000000, mutation_thresholds=thr)
+        for mode, out in (("plain", best_plain), ("screened", best_screened)):
+            pop = torch.from_numpy(pop0.view(np.int64).copy()).to(dev)
+            best = np.zeros(G, np.int32)
+            if mode == "plain":
+                J.run_ga(ga, pop, G, fitness_kind=J.FITNESS_SHAPE, L=16, k=20, seed=7, best=best)
+            else:
+                net.set_params(trained)  # every run starts from the same network
+                J.run_ga_screened(ga, pop, G, ratio, net, online_lr=1e-3, L=16, k=20, seed=7, best=best)
+            out.append(int(best.max()))
+    net.close()
+    reach_plain = sum(b >= 32 for b in best_plain)
+    reach_screened = sum(b >= 32 for b in best_screened)
+    print("best after 5 generations: plain", best_plain, "screened", best_screened)
+    assert reach_screened >= reach_plain + 3
+    assert np.mean(best_screened) > np.mean(best_plain) + 2

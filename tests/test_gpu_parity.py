@@ -296,7 +296,7 @@ def test_results_do_not_depend_on_the_launch_shape():
     first, count = 5 << 20, 200000
     base, hbase, _ = _dev_enumerate(n, c, L, k, seed, first, count)
     try:
-        for warps, stop in ((1, 1), (2, 32), (4, 8), (8, 3)):
+        for warps, stop in ((1, 1), (2, 32), (4, 8), (6, 3)):
             J.set_tuning(n, c, L, warps, stop)
             assert J.get_tuning(n, c, L) == (warps, stop)
             res, hist, _ = _dev_enumerate(n, c, L, k, seed, first, count)
@@ -304,11 +304,11 @@ def test_results_do_not_depend_on_the_launch_shape():
             assert np.array_equal(hist, hbase)
         J.autotune([{"n": n, "c": c, "L": L, "k": k, "seed": seed}])
         w, s = J.get_tuning(n, c, L)
-        assert 1 <= w <= 8 and 1 <= s <= 32
+        assert 1 <= w <= 6 and 1 <= s <= 32
         res, _, _ = _dev_enumerate(n, c, L, k, seed, first, count)
         assert np.array_equal(res, base)
     finally:
-        J.set_tuning(n, c, L, 8, 8)
+        J.set_tuning(n, c, L, 0, 8)  # back to the defaults
 
 
 def test_graph_replay_equals_direct_launches():
@@ -350,7 +350,8 @@ _DX, _DY = (0, 1, 0, -1), (-1, 0, 1, 0)
 def _closed(col, n, c, grid):
     """The closure test of a final replicate-0 configuration, written out from
     the binding rule: for every two adjacent tiles, the tuples the one offers
-    the other's cell are that cell's tuple or none."""
+    the other's cell are that cell's tuple or none (the seed's cell, occupied
+    first in every replicate, may be offered anything)."""
     def bind(a, b):
         return a != 0 and b != 0 and min(a, b) % 2 == 1 and max(a, b) == min(a, b) + 1 and max(a, b) < c
     side = {4 * t + r: [col[4 * t + (d - r) % 4] for d in range(4)] for t in range(n) for r in range(4)}
@@ -363,7 +364,7 @@ def _closed(col, n, c, grid):
                 continue
             for d in range(4):
                 qx, qy = x + _DX[d], y + _DY[d]
-                if not (0 <= qx < L and 0 <= qy < L) or grid[qy, qx] < 0:
+                if not (0 <= qx < L and 0 <= qy < L) or grid[qy, qx] < 0 or (qx, qy) == (L // 2, L // 2):
                     continue
                 offered = {rep[a] for a in side if bind(side[a][(d + 2) % 4], side[u][d])}
                 if offered and offered != {grid[qy, qx]}:
