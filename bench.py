@@ -289,6 +289,44 @@ def ga_arm(args, torch, J, dev):
     return 0
 
 
+KSWEEP = (1, 2, 4, 8, 16, 20, 32, 64, 128)
+
+
+def ksweep_arm(args, torch, J, dev):
+    """The k sweep of the paper's S_{2,8} result (Section 3.1): all 8^8
+    genotypes classified at each k, for the lattice of the bench (L = 16) and
+    the paper's (L = 19).  With one seed the first k replicates of a run at k'
+    > k are the run at k, so DET(k') is a subset of DET(k); the genotypes
+    called DET at k but not at the largest k are non-deterministic genotypes
+    misclassified at k.  Reports their share of DET(k) and the GPU time."""
+    n, c, seed, count = 2, 8, 2, 8 ** 8
+    out = torch.empty(count * 8, dtype=torch.uint8, device=dev)
+    J.jatam_profile(1)
+    lines = {}
+    for L in (16, 19):
+        rows = {}
+        for k in KSWEEP:
+            for _ in range(2):  # the first call of a shape pays for its set-up
+                J.enumerate_space(n, c, L, k, seed, 0, count, out=out, sync=True)
+            kms = J.last_kernel_ms()
+            cls = J.results_view(out)["cls"]
+            counts = np.bincount(cls.astype(np.int64), minlength=4)
+            rows[k] = {"det": int(counts[0]), "nd_local": int(counts[1]), "nd_steric": int(counts[2]),
+                       "unbounded": int(counts[3]), "growth_kernels_ms": round(kms, 3)}
+        det_ref = rows[KSWEEP[-1]]["det"]
+        for k in KSWEEP:
+            d = rows[k]["det"]
+            rows[k]["misclassified_share_of_det"] = round((d - det_ref) / d, 6) if d else 0.0
+        lines[f"L{L}"] = rows
+    line = {"metric": "k sweep of S_{2,8}: genotypes called DET at k that are not DET at k = 128",
+            "value": lines["L19"][8]["misclassified_share_of_det"], "unit": "share of DET(k=8) at L=19",
+            "n_gpus": 1, "higher_is_better": False, "data": "synthetic",
+            "config": {"workload": f"ksweep: all 8^8 genotypes of S_{{2,8}}, seed {seed}, k in {list(KSWEEP)}, "
+                                   "L in {16, 19}", "sweep": lines}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def run_oracle_sample(nthreads):
     from oracle import oracle as O
     n, c, L, k, seed, _, _, _ = WORKLOAD_SPEC()
@@ -339,7 +377,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--workload", default="s28_full",
-                    help="s28_full (the bench line), or s24_full / s28_paper / s38_sample / mixed / ga for measurements")
+                    help="s28_full (the bench line), or s24_full / s28_paper / s38_sample / mixed / ga / ksweep "
+                         "for measurements")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end leg")
     ap.add_argument("--profile-genomes", type=int, default=0,
@@ -371,6 +410,8 @@ def main():
         return mixed_arm(args, torch, J, dev)
     if WORKLOAD == "ga":
         return ga_arm(args, torch, J, dev)
+    if WORKLOAD == "ksweep":
+        return ksweep_arm(args, torch, J, dev)
 
     n, c, L, k, seed0, first, count, sampled = WORKLOAD_SPEC()
     if args.profile_genomes:
@@ -479,7 +520,7 @@ def main():
             traffic = None
         roofline = {"bound": "alu", "achieved": round(achieved, 4), "peak": round(alu_peak, 2),
                     "unit": "Tops/s", "frac": round(achieved / alu_peak, 4), "traffic": traffic,
-                    "kernel": f"classify_kernel<{8 if L <= 8 else 16 if L <= 16 else 32}>",
+                    "kernel": f"classify_kernel<{8 if L <= 8 else 16 if L <= 16 else 32}, {8 if n <= 2 else 16}>",
                     "kernel_ms": round(kms, 4),
                     "peak_source": f"{n_sms} SMs x 128 int32 lanes x {sm_max:.0f} MHz (MEASURED_PEAKS sm_max)",
                     "executed": work,
