@@ -152,12 +152,19 @@ def measured_traffic(kernel_file):
 
 def cpu_sample_plan():
     """Stratified bounded sample of the workload for the oracle: 64 blocks of
-    65,536 consecutive genotypes spread evenly over the space."""
+    up to 65,536 consecutive genotypes spread evenly over the workload."""
     n, c, L, k, seed, first, count, sampled = WORKLOAD_SPEC()
     blocks = 64
-    per = 65536
     stride = count // blocks
+    per = min(65536, stride)
     return [(first + b * stride, per) for b in range(blocks)]
+
+
+def cpu_sample_text():
+    n, c, L, k, seed, first, count, sampled = WORKLOAD_SPEC()
+    per = cpu_sample_plan()[0][1]
+    what = "sample indices" if sampled else "consecutive genotypes"
+    return f"64 blocks of {per:,} {what} of S_{{{n},{c}}} spread evenly over the workload"
 
 
 def WORKLOAD_SPEC():
@@ -183,8 +190,9 @@ def mixed_arm(args, torch, J, dev):
     hlen = torch.zeros(1, dtype=torch.int32, device=dev)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
     stream = torch.cuda.Stream(device=dev)
-    J.autotune_batch(dc[: 1 << 20], ds[: 1 << 20], 4, stream=stream)
+    J.autotune_batch(dc, ds, 4, stream=stream)
     plan = J.get_mixed_plan()
+    choice = J.get_mixed_launch()
 
     def timed(per_shape, graph):
         for _ in range(args.warmup):
@@ -216,6 +224,7 @@ def mixed_arm(args, torch, J, dev):
         "config": {"workload": "mixed: 10^7 tile sets, n in {2,3,4}, c in {4,6,8}, L in {8,16,32}, k in {10,20}, "
                                "seed 4", "launch": "one persistent launch, CUDA graph replay",
                    "plan_w32_w16_w8": list(plan), "growth_kernels_ms": round(kms, 4),
+                   "autotuner_default_launch": choice,
                    "per_shape_fixed_launches": {"ms_per_step": round(ms_fixed, 4),
                                                 "growth_kernels_ms": round(kms_fixed, 4),
                                                 "value": MIXED_COUNT / (ms_fixed / 1e3)},
@@ -344,7 +353,7 @@ def reference_arm(args):
         return 0
     from oracle import oracle as O
     O.build()
-    cores = os.cpu_count() or 1
+    cores = getattr(args, "cpu_threads", 0) or os.cpu_count() or 1
     times, units = [], 0
     for _ in range(args.warmup):
         run_oracle_sample(cores)
@@ -359,10 +368,10 @@ def reference_arm(args):
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": per_step * 1e3, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
-        "config": {"workload": f"{WORKLOAD}: S_{{2,8}} n={n} c={c} L={L} k={k} seed={seed}",
+        "config": {"workload": f"{WORKLOAD}: S_{{{n},{c}}} n={n} c={c} L={L} k={k} seed={seed}",
                    "step": f"oracle on a stratified sample of {units} genotypes (64 x 65536)"},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
-                         "sample": f"64 blocks of 65,536 consecutive genotypes of S_{{2,8}} ({units} per step)"},
+                         "sample": f"{cpu_sample_text()} ({units} per step)"},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -380,6 +389,7 @@ def main():
                     help="s28_full (the bench line), or s24_full / s28_paper / s38_sample / mixed / ga / ksweep "
                          "for measurements")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-threads", type=int, default=0, help="threads of the oracle arm (default: all cores)")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end leg")
     ap.add_argument("--profile-genomes", type=int, default=0,
                     help="instead of the bench: ga_evaluate on this many uniform random genomes of the "
@@ -537,10 +547,10 @@ def main():
         if not args.no_cpu_baseline and world == 1:
             from oracle import oracle as O
             O.build()
-            cores = os.cpu_count() or 1
+            cores = getattr(args, "cpu_threads", 0) or os.cpu_count() or 1
             units, dt = run_oracle_sample(cores)
             cpu = {"value": units / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
-                   "sample": f"64 blocks of 65,536 consecutive genotypes of S_{{2,8}} ({units} genotypes, {dt:.1f} s)"}
+                   "sample": f"{cpu_sample_text()} ({units} genotypes, {dt:.1f} s)"}
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",

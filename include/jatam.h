@@ -66,6 +66,9 @@ extern "C" {
 #define JATAM_SYNC 0x2u    /* wait for the work to finish before returning */
 #define JATAM_PER_SHAPE 0x4u /* jatam_classify_batch with mixed shapes: one fixed launch per lattice size
                                 class instead of the single persistent launch */
+#define JATAM_PERSISTENT 0x20u /* jatam_classify_batch with mixed shapes: the single persistent launch.
+                                  Neither flag: the launch jatam_autotune_batch found faster
+                                  (the persistent one until it has run) */
 #define JATAM_C4_HASH 0x10u  /* the paper's rotation-only hash (Section 2.5): hash the 4 rotations of the
                                 cropped shape, sort the 4 hashes, hash them again (16 bytes, little endian);
                                 mirror images stay distinct.  Default: the canonical form under all 8
@@ -142,7 +145,8 @@ int jatam_enumerate(const jatam_config *cfg, uint64_t first, uint64_t count, jat
  * with 32 x 32, 16 x 16 and 8 x 8 shared-memory regions (a per-CTA plan that
  * jatam_autotune picks) work through their own list and then steal from the
  * lists of smaller sizes.  With JATAM_PER_SHAPE the three lists run as three
- * fixed launches instead.  Results are identical either way.
+ * fixed launches instead; without either flag, as the autotuner chose.
+ * Results are identical either way.
  */
 int jatam_classify_batch(const jatam_config *cfg, const uint8_t *colours, const uint8_t *shapes,
                          const uint64_t *stream_ids, uint64_t N, jatam_result *out, jatam_hist_entry *hist,
@@ -233,7 +237,10 @@ int ga_run(const jatam_ga_config *ga, const jatam_config *cls, int fitness_kind,
 typedef struct jatam_mlp jatam_mlp;
 
 /* Create a network with capacity for batches of up to max_batch genomes;
- * its parameters start at zero (set them with jatam_mlp_set_params). */
+ * its parameters start at zero (set them with jatam_mlp_set_params).  Its
+ * products with 256 output columns run on tcgen05 (accumulator in tensor
+ * memory), the others on mma.sync; the environment variable
+ * JATAM_MLP_PRODUCTS=mma, read here, keeps all of them on mma.sync. */
 int jatam_mlp_create(uint64_t max_batch, jatam_mlp **net);
 void jatam_mlp_destroy(jatam_mlp *net);
 /* params: [JATAM_MLP_NPARAM] float32, host or device; set also resets Adam. */
@@ -329,12 +336,16 @@ int jatam_get_tuning(const jatam_config *cfg, int *warps_per_cta, int *stop_at);
  * and 8 x 8 region per CTA (at least one 32 x 32 warp, since only those can
  * run L > 16; at most 8 warps in total, shared memory permitting; default
  * 2, 4, 2).
- * jatam_autotune_batch -- time every candidate plan (and the per-size fixed
- * launches' growth-round threshold) on the given mixed batch (colours[N][16],
- * shapes[N][4], host or device) and keep the fastest plan.  Synchronises.
+ * jatam_autotune_batch -- time every candidate plan of the persistent launch
+ * and the per-size fixed launches on the given mixed batch (colours[N][16],
+ * shapes[N][4], host or device); keep the fastest plan, and make the faster
+ * of the two launch forms the default of mixed batches.  Synchronises.
  */
 int jatam_set_mixed_plan(int warps_32, int warps_16, int warps_8);
 int jatam_get_mixed_plan(int *warps_32, int *warps_16, int *warps_8);
+/* *per_shape = 1 if mixed batches without a launch-form flag use the per-size
+ * fixed launches, 0 if the persistent launch. */
+int jatam_get_mixed_launch(int *per_shape);
 int jatam_autotune_batch(const uint8_t *colours, const uint8_t *shapes, uint64_t N, uint64_t seed, void *stream);
 
 /*

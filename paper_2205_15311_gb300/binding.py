@@ -29,6 +29,7 @@ JATAM_SYNC = 0x2
 JATAM_PER_SHAPE = 0x4
 JATAM_GRAPH = 0x8
 JATAM_C4_HASH = 0x10
+JATAM_PERSISTENT = 0x20
 JATAM_NOALLOC_MAX_COUNT = 1048576
 
 RESULT_DTYPE = np.dtype([("cls", "u1"), ("decided_rep", "u1"), ("size", "<u2"), ("shape_hash", "<u4")])
@@ -112,6 +113,8 @@ def lib():
         L.jatam_set_mixed_plan.restype = ctypes.c_int
         L.jatam_get_mixed_plan.argtypes = [ctypes.POINTER(ctypes.c_int)] * 3
         L.jatam_get_mixed_plan.restype = ctypes.c_int
+        L.jatam_get_mixed_launch.argtypes = [ctypes.POINTER(ctypes.c_int)]
+        L.jatam_get_mixed_launch.restype = ctypes.c_int
         L.jatam_autotune_batch.argtypes = [_VP, _VP, _U64, _U64, _VP]
         L.jatam_autotune_batch.restype = ctypes.c_int
         L.jatam_autotune.argtypes = [_VP, _U32, _VP]
@@ -155,6 +158,10 @@ def jatam_philox(inp, N, out, stream):
 
 def jatam_hist_merge(a, na, b, nb, out, cap, length):
     return lib().jatam_hist_merge(a, na, b, nb, out, cap, length)
+
+
+def jatam_get_mixed_launch(per_shape):
+    return lib().jatam_get_mixed_launch(per_shape)
 
 
 def jatam_enumerate_noalloc(cfg, first, count, out, stream):
@@ -305,10 +312,12 @@ def enumerate_noalloc(n, c, L, k, seed, first, count, out, *, sampled=False, str
 
 
 def classify_batch(colours, *, n=0, c=0, L=0, k=0, seed=0, shapes=None, stream_ids=None, out=None, hist=None,
-                   hist_len=None, hist_cap=0, stream=None, sync=False, per_shape=False, graph=False):
+                   hist_len=None, hist_cap=0, stream=None, sync=False, per_shape=None, graph=False):
+    """per_shape: True -> per-size fixed launches, False -> the persistent launch,
+    None -> the form jatam_autotune_batch found faster."""
     N = int(colours.shape[0])
-    cfg = make_config(n, c, L, k, seed, (JATAM_SYNC if sync else 0) | (JATAM_PER_SHAPE if per_shape else 0)
-                      | (JATAM_GRAPH if graph else 0))
+    form = 0 if per_shape is None else (JATAM_PER_SHAPE if per_shape else JATAM_PERSISTENT)
+    cfg = make_config(n, c, L, k, seed, (JATAM_SYNC if sync else 0) | form | (JATAM_GRAPH if graph else 0))
     return check(jatam_classify_batch(ctypes.addressof(cfg), _addr(colours), _addr(shapes), _addr(stream_ids), N,
                                       _addr(out), _addr(hist), hist_cap, _addr(hist_len), _stream_handle(stream)))
 
@@ -342,6 +351,13 @@ def get_mixed_plan():
     v = [ctypes.c_int(0) for _ in range(3)]
     check(jatam_get_mixed_plan(*[ctypes.byref(x) for x in v]))
     return tuple(x.value for x in v)
+
+
+def get_mixed_launch():
+    """'per_shape' or 'persistent': the launch form of mixed batches without a flag."""
+    v = ctypes.c_int(0)
+    check(jatam_get_mixed_launch(ctypes.byref(v)))
+    return "per_shape" if v.value else "persistent"
 
 
 def autotune_batch(colours, shapes, seed, stream=None):

@@ -10,7 +10,7 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD_DIR = os.path.join(PKG, "_build")
 LIB_PATH = os.path.join(BUILD_DIR, "libjatam.so")
-SOURCES = ["jatam_kernels.cu", "jatam_api.cu", "jatam_noalloc.cu", "jatam_ga.cu", "jatam_mlp.cu"]
+SOURCES = ["jatam_kernels.cu", "jatam_api.cu", "jatam_noalloc.cu", "jatam_ga.cu", "jatam_mlp.cu", "jatam_tc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 

@@ -31,6 +31,7 @@ thread_local std::string g_last_error;
 std::mutex g_mutex;
 int g_profile = 0;  // bit 0: events around the growth kernels; bit 1: executed-work counters
 int g_stop_override = 0;
+bool g_mixed_per_shape = false;  // the default launch form of mixed batches (set by jatam_autotune_batch)
 int g_warps_override = 0;
 
 struct Tuning {
@@ -582,7 +583,8 @@ int jatam_classify_batch(const jatam_config *cfg, const uint8_t *colours, const 
         a.ids = reinterpret_cast<const unsigned long long *>(base + off_i);
     }
     return run(w, a, S, out, nullptr, hist, hist_cap, hist_len, (cfg->flags & JATAM_SYNC) != 0, st, nullptr, nullptr,
-               (cfg->flags & JATAM_PER_SHAPE) != 0, (cfg->flags & JATAM_GRAPH) != 0);
+               (cfg->flags & JATAM_PER_SHAPE) != 0 || (!(cfg->flags & JATAM_PERSISTENT) && g_mixed_per_shape),
+               (cfg->flags & JATAM_GRAPH) != 0);
 }
 
 int ga_evaluate(const jatam_config *cfg, const uint64_t *genomes, uint64_t N, int32_t *fitness, jatam_result *out,
@@ -876,6 +878,17 @@ int ga_loop(const jatam_ga_config *ga, const jatam_config *cls, int fitness_kind
     return JATAM_OK;
 }
 
+// after a synchronisation: a bounded wait of the tcgen05 products that ran out
+int mlp_tc_status(jatam_mlp *m)
+{
+    if (!m->b.tc) return JATAM_OK;
+    unsigned e = 0;
+    CUDA_TRY(cudaMemcpy(&e, m->b.tc_err, 4, cudaMemcpyDeviceToHost));
+    if (!e) return JATAM_OK;
+    CUDA_TRY(cudaMemset(m->b.tc_err, 0, 4));
+    return fail(JATAM_ETIMEOUT, "a tensor-core product gave up waiting for its result");
+}
+
 }  // namespace
 
 extern "C" {
@@ -927,6 +940,8 @@ int jatam_mlp_create(uint64_t max_batch, jatam_mlp **net)
     rc |= alloc((void **)&b.logits, Bc * MLP_OUT * 4); rc |= alloc((void **)&b.d, Bc * MLP_OUT * 4);
     rc |= alloc((void **)&b.lrow, Bc * 4);
     rc |= alloc((void **)&b.splitk, (size_t)MLP_SPLITK_MAX * MLP_H * MLP_H * 4);
+    rc |= alloc((void **)&b.tc_err, 4);
+    rc |= alloc((void **)&b.wqt, (size_t)(MLP_PAD * MLP_H + MLP_H * MLP_H) * 2);
     rc |= alloc((void **)&b.loss, 16);
     if (rc) {
         jatam_mlp_destroy(m);
@@ -936,6 +951,13 @@ int jatam_mlp_create(uint64_t max_batch, jatam_mlp **net)
     CUDA_TRY(cudaMemset(b.m, 0, P * 4));
     CUDA_TRY(cudaMemset(b.v, 0, P * 4));
     CUDA_TRY(cudaMemset(b.wq, 0, P * 2));
+    CUDA_TRY(cudaMemset(b.tc_err, 0, 4));
+    CUDA_TRY(cudaMemset(b.wqt, 0, (size_t)(MLP_PAD * MLP_H + MLP_H * MLP_H) * 2));
+    {
+        // JATAM_MLP_PRODUCTS=mma keeps every product on mma.sync (for comparisons)
+        const char *v = getenv("JATAM_MLP_PRODUCTS");
+        b.tc = (v && strcmp(v, "mma") == 0) ? 0 : 1;
+    }
     *net = m;
     return JATAM_OK;
 }
@@ -945,7 +967,7 @@ void jatam_mlp_destroy(jatam_mlp *m)
     if (!m) return;
     MlpBuffers &b = m->b;
     void *ptrs[] = {b.p, b.grad, b.m, b.v, b.wq, b.x, b.h1, b.h2, b.dq, b.dh1, b.dh2, b.logits, b.d, b.lrow, b.loss,
-                    b.splitk, m->stage};
+                    b.splitk, b.tc_err, b.wqt, m->stage};
     cudaDeviceSynchronize();
     for (void *p : ptrs)
         if (p) cudaFree(p);
@@ -1020,6 +1042,7 @@ int jatam_mlp_train_step(jatam_mlp *m, const uint64_t *genomes, const uint8_t *l
     if (loss || (grads && kind_of(grads, m->device) == K_HOST) || kg == K_HOST || kl == K_HOST) {
         CUDA_TRY(cudaStreamSynchronize(st));
         if (loss) *loss = h_loss;
+        return mlp_tc_status(m);
     }
     return JATAM_OK;
 }
@@ -1041,7 +1064,10 @@ int jatam_mlp_predict(jatam_mlp *m, const uint64_t *genomes, uint64_t N, float *
     }
     CUDA_TRY(mlp_forward(m->b, dg, (long long)N, st));
     CUDA_TRY(cudaMemcpyAsync(logits, m->b.logits, (size_t)N * MLP_OUT * 4, cudaMemcpyDefault, st));
-    if (kg == K_HOST || ko == K_HOST) CUDA_TRY(cudaStreamSynchronize(st));
+    if (kg == K_HOST || ko == K_HOST) {
+        CUDA_TRY(cudaStreamSynchronize(st));
+        return mlp_tc_status(m);
+    }
     return JATAM_OK;
 }
 
@@ -1241,6 +1267,15 @@ int jatam_get_mixed_plan(int *warps_32, int *warps_16, int *warps_8)
     return JATAM_OK;
 }
 
+int jatam_get_mixed_launch(int *per_shape)
+{
+    std::lock_guard<std::mutex> lock(g_mutex);
+    g_last_error.clear();
+    if (!per_shape) return fail(JATAM_EINVAL, "per_shape is NULL");
+    *per_shape = g_mixed_per_shape ? 1 : 0;
+    return JATAM_OK;
+}
+
 int jatam_autotune_batch(const uint8_t *colours, const uint8_t *shapes, uint64_t N, uint64_t seed, void *stream)
 {
     std::lock_guard<std::mutex> lock(g_mutex);
@@ -1302,6 +1337,15 @@ int jatam_autotune_batch(const uint8_t *colours, const uint8_t *shapes, uint64_t
     g_plan[0] = best[0];
     g_plan[1] = best[1];
     g_plan[2] = best[2];
+    // the per-size fixed launches on the same batch
+    float fixed_ms = 1e30f;
+    for (int rep = 0; rep < 2; ++rep) {
+        float ms = 0.f;
+        rc = run(w, a, 32, nullptr, nullptr, nullptr, 0, nullptr, true, st, nullptr, &ms, true);
+        if (rc) return rc;
+        fixed_ms = ms < fixed_ms ? ms : fixed_ms;
+    }
+    g_mixed_per_shape = fixed_ms < best_ms;
     return JATAM_OK;
 }
 

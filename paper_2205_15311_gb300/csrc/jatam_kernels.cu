@@ -722,6 +722,8 @@ __global__ void __launch_bounds__(256) prefilter_kernel(const LaunchArgs a, int 
     // keys decided here: 0 = (ND_LOCAL, 0), 1 = (UNBOUNDED, 0), 2 = (DET_BOUNDED, monomer)
     __shared__ unsigned s_cnt[3];
     __shared__ unsigned long long s_min[3];
+    __shared__ unsigned s_fill[3];               // this iteration's items per list
+    __shared__ unsigned long long s_base[3];     // where they go in the lists
     if (threadIdx.x < 3) {
         s_cnt[threadIdx.x] = 0u;
         s_min[threadIdx.x] = ~0ull;
@@ -730,6 +732,11 @@ __global__ void __launch_bounds__(256) prefilter_kernel(const LaunchArgs a, int 
     const int lane = threadIdx.x & 31;
     const int b_uniform = log2_colours(a.c);
     const uint32_t mono = monomer_shape_hash(a.c4 != 0);
+    // stream ids that grow with the item index (an index range: the genotype
+    // itself; records without ids: the index): the lowest lane of a warp holds
+    // the smallest.  Sampled genotypes and GA genomes need the reduction.
+    const bool sid_is_index = a.mode == MODE_RANGE || (a.mode == MODE_RECORDS && !a.ids);
+    const int nlists = a.bucket ? 3 : 1;
     const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
     for (unsigned long long base = (unsigned long long)blockIdx.x * blockDim.x; base < a.count; base += stride) {
         const unsigned long long idx = base + threadIdx.x;
@@ -757,29 +764,39 @@ __global__ void __launch_bounds__(256) prefilter_kernel(const LaunchArgs a, int 
                 }
             }
         }
-        // append to the list of the item's lattice size class (one class
-        // unless the launch mixes sizes)
-#pragma unroll
-        for (int kc = 0; kc < 3; ++kc) {
+        // append to the list of the item's lattice size class (one class unless
+        // the launch mixes sizes): warp offsets from shared counters, then one
+        // global atomic per list and CTA iteration
+        if (threadIdx.x < 3) s_fill[threadIdx.x] = 0u;
+        __syncthreads();
+        unsigned my_off = 0;
+        for (int kc = 0; kc < nlists; ++kc) {
             const unsigned gm = __ballot_sync(FULL, grow && klass == kc);
-            if (gm) {
-                unsigned long long slot = 0;
-                if (lane == 0) slot = atomicAdd(&a.list_count[kc], (unsigned long long)__popc(gm));
-                slot = __shfl_sync(FULL, slot, 0);
-                if (grow && klass == kc) a.list[(size_t)kc * a.list_stride + slot + __popc(gm & lanemask_lt())] = idx;
-            }
-            if (!a.bucket) break;
+            unsigned woff = 0;
+            if (gm && lane == 0) woff = atomicAdd(&s_fill[kc], (unsigned)__popc(gm));
+            woff = __shfl_sync(FULL, woff, 0);
+            if (grow && klass == kc) my_off = woff + __popc(gm & lanemask_lt());
         }
+        __syncthreads();
+        if (threadIdx.x < nlists && s_fill[threadIdx.x])
+            s_base[threadIdx.x] = atomicAdd(&a.list_count[threadIdx.x], (unsigned long long)s_fill[threadIdx.x]);
+        __syncthreads();
+        if (grow) a.list[(size_t)klass * a.list_stride + s_base[klass] + my_off] = idx;
         if (a.use_hist) {
 #pragma unroll
             for (int q = 0; q < 3; ++q) {
                 const unsigned m = __ballot_sync(FULL, key == q);
                 if (m) {
-                    unsigned long long v = (key == q) ? sid : ~0ull;
+                    unsigned long long v;
+                    if (sid_is_index) {
+                        v = __shfl_sync(FULL, sid, __ffs(m) - 1);
+                    } else {
+                        v = (key == q) ? sid : ~0ull;
 #pragma unroll
-                    for (int off = 16; off > 0; off >>= 1) {
-                        const unsigned long long o = __shfl_xor_sync(FULL, v, off);
-                        v = o < v ? o : v;
+                        for (int off = 16; off > 0; off >>= 1) {
+                            const unsigned long long o = __shfl_xor_sync(FULL, v, off);
+                            v = o < v ? o : v;
+                        }
                     }
                     if (lane == 0) {
                         atomicAdd(&s_cnt[q], (unsigned)__popc(m));

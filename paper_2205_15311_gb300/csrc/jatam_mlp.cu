@@ -9,7 +9,9 @@
 // bias + ReLU to bfloat16 (hidden layers), bias to float32 (logits), a ReLU
 // derivative mask to bfloat16 (activation gradients), or plain float32
 // (weight gradients).  The product itself is mma.sync.m16n8k16 (bf16 x bf16 ->
-// f32) from shared-memory tiles.  The weight gradients (K = the batch, only a
+// f32) from shared-memory tiles, except the products with 256 output columns
+// (both hidden layers and the first layer's activation gradient), which run on
+// tcgen05 with the accumulator in tensor memory (jatam_tc.cu).  The weight gradients (K = the batch, only a
 // few output tiles) split K over the grid's z dimension into float32 partial
 // products that a second kernel sums in split order, so the bits do not
 // depend on scheduling.
@@ -39,6 +41,7 @@ struct GemmArgs {
     float *Cf;                     // [M x N] row-major float32 output
     __nv_bfloat16 *Cb;             // [M x N] row-major bfloat16 output
     int kchunk;                    // split-K: CTA z covers k in [z kchunk, (z + 1) kchunk); 0: all of K
+    const __nv_bfloat16 *Bt;       // the same B with K contiguous (element (k, n) at Bt[n * K + k]), or null
 };
 
 __device__ __forceinline__ void mma_bf16(float (&c)[4], const uint32_t (&a)[4], const uint32_t (&b)[2])
@@ -213,8 +216,22 @@ __global__ void colsum_kernel<__nv_bfloat16>(const __nv_bfloat16 *a, long long B
 }
 
 // Adam on the float32 master parameters, then their bfloat16 copies
+// the K-contiguous copies of W1 and W2 that the tcgen05 products read as their
+// B operand: W1T [256 x 48] (W1T[n][k] = W1[k][n]) then W2T [256 x 256]
+__device__ __forceinline__ void store_transposed(__nv_bfloat16 *pqt, long long i, __nv_bfloat16 v)
+{
+    if (i < MLP_PAD * MLP_H) {
+        const long long k = i / MLP_H, n = i % MLP_H;
+        pqt[n * MLP_PAD + k] = v;
+    } else if (i >= MLP_PAD * MLP_H + MLP_H && i < MLP_PAD * MLP_H + MLP_H + MLP_H * MLP_H) {
+        const long long j = i - (MLP_PAD * MLP_H + MLP_H);
+        const long long k = j / MLP_H, n = j % MLP_H;
+        pqt[MLP_PAD * MLP_H + n * MLP_H + k] = v;
+    }
+}
+
 __global__ void adam_kernel(float *p, const float *g, float *m, float *v, long long n, float lr, float b1, float b2,
-                            float eps, float c1, float c2, __nv_bfloat16 *pq)
+                            float eps, float c1, float c2, __nv_bfloat16 *pq, __nv_bfloat16 *pqt)
 {
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
         const float gi = g[i];
@@ -225,13 +242,16 @@ __global__ void adam_kernel(float *p, const float *g, float *m, float *v, long l
         const float pi = p[i] - lr * (mi / c1) / (sqrtf(vi / c2) + eps);
         p[i] = pi;
         pq[i] = __float2bfloat16_rn(pi);
+        if (pqt) store_transposed(pqt, i, pq[i]);
     }
 }
 
-__global__ void to_bf16_kernel(const float *p, long long n, __nv_bfloat16 *pq)
+__global__ void to_bf16_kernel(const float *p, long long n, __nv_bfloat16 *pq, __nv_bfloat16 *pqt)
 {
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
         pq[i] = __float2bfloat16_rn(p[i]);
+        if (pqt) store_transposed(pqt, i, pq[i]);
+    }
 }
 
 // out[i] = sum over z of part[z][i], z in increasing order
@@ -244,8 +264,15 @@ __global__ void splitk_sum_kernel(const float *part, int splits, long long n, fl
     }
 }
 
-cudaError_t gemm(const GemmArgs &g, cudaStream_t st, float *splitk = nullptr)
+cudaError_t gemm(const GemmArgs &g, cudaStream_t st, float *splitk = nullptr, const MlpBuffers *tcb = nullptr)
 {
+    // the products with 256 output columns and K a multiple of 16 on tcgen05
+    if (tcb && tcb->tc && g.N == 256 && g.M >= 128 && g.K % 16 == 0 &&
+        (g.epi == EPI_BIAS_RELU_BF16 || g.epi == EPI_MASK_BF16)) {
+        const bool bt = g.Bt != nullptr;
+        return tc_gemm_n256(g.A, g.a_m, g.a_k, bt ? g.Bt : g.B, bt ? 1 : g.b_k, bt ? g.K : g.b_n, g.M, g.K,
+                            g.epi == EPI_BIAS_RELU_BF16 ? 0 : 1, g.bias, g.mask, g.Cb, tcb->tc_err, st);
+    }
     const dim3 tiles((g.N + TN - 1) / TN, (g.M + TM - 1) / TM);
     const int ntiles = (int)(tiles.x * tiles.y);
     // a float32 product with few output tiles and a long K: split K over the grid
@@ -292,12 +319,12 @@ cudaError_t mlp_forward(const MlpBuffers &b, const unsigned long long *genomes, 
     GemmArgs g{};
     // h1 = relu(x W1 + b1)
     g = GemmArgs{b.x, MLP_PAD, 1, Wq + MLP_OFF_W1, MLP_H, 1, (int)B, MLP_H, MLP_PAD, EPI_BIAS_RELU_BF16,
-                 b.p + MLP_OFF_B1, nullptr, nullptr, b.h1};
-    if ((e = gemm(g, st)) != cudaSuccess) return e;
+                 b.p + MLP_OFF_B1, nullptr, nullptr, b.h1, 0, b.wqt};
+    if ((e = gemm(g, st, nullptr, &b)) != cudaSuccess) return e;
     // h2 = relu(h1 W2 + b2)
     g = GemmArgs{b.h1, MLP_H, 1, Wq + MLP_OFF_W2, MLP_H, 1, (int)B, MLP_H, MLP_H, EPI_BIAS_RELU_BF16,
-                 b.p + MLP_OFF_B2, nullptr, nullptr, b.h2};
-    if ((e = gemm(g, st)) != cudaSuccess) return e;
+                 b.p + MLP_OFF_B2, nullptr, nullptr, b.h2, 0, b.wqt + MLP_PAD * MLP_H};
+    if ((e = gemm(g, st, nullptr, &b)) != cudaSuccess) return e;
     // logits = h2 W3 + b3
     g = GemmArgs{b.h2, MLP_H, 1, Wq + MLP_OFF_W3, MLP_OUT, 1, (int)B, MLP_OUT, MLP_H, EPI_BIAS_F32,
                  b.p + MLP_OFF_B3, nullptr, b.logits, nullptr};
@@ -329,7 +356,7 @@ cudaError_t mlp_backward(const MlpBuffers &b, const uint8_t *labels, long long B
     // dh1 = (dh2 W2^T) * [h1 > 0]  [B x 256]
     g = GemmArgs{b.dh2, MLP_H, 1, b.wq + MLP_OFF_W2, 1, MLP_H, (int)B, MLP_H, MLP_H, EPI_MASK_BF16, nullptr, b.h1,
                  nullptr, b.dh1};
-    if ((e = gemm(g, st)) != cudaSuccess) return e;
+    if ((e = gemm(g, st, nullptr, &b)) != cudaSuccess) return e;
     // dW1 = x^T dh1  [48 x 256]
     g = GemmArgs{b.x, 1, MLP_PAD, b.dh1, MLP_H, 1, MLP_PAD, MLP_H, (int)B, EPI_F32, nullptr, nullptr, G + MLP_OFF_W1,
                  nullptr};
@@ -343,13 +370,13 @@ cudaError_t mlp_adam(const MlpBuffers &b, float lr, int t, cudaStream_t st)
     const float b1 = 0.9f, b2 = 0.999f, eps = 1e-8f;
     const float c1 = 1.f - powf(b1, (float)t), c2 = 1.f - powf(b2, (float)t);
     adam_kernel<<<grid_for(MLP_NPARAM), 256, 0, st>>>(b.p, b.grad, b.m, b.v, MLP_NPARAM, lr, b1, b2, eps, c1, c2,
-                                                       b.wq);
+                                                       b.wq, b.wqt);
     return cudaGetLastError();
 }
 
 cudaError_t mlp_refresh_bf16(const MlpBuffers &b, cudaStream_t st)
 {
-    to_bf16_kernel<<<grid_for(MLP_NPARAM), 256, 0, st>>>(b.p, MLP_NPARAM, b.wq);
+    to_bf16_kernel<<<grid_for(MLP_NPARAM), 256, 0, st>>>(b.p, MLP_NPARAM, b.wq, b.wqt);
     return cudaGetLastError();
 }
 

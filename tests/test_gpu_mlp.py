@@ -81,3 +81,34 @@ def test_predict_matches_oracle_and_training_lowers_the_loss():
     after = J.unflatten_params(net.get_params())
     assert not np.allclose(after["W1"], params["W1"])
     net.close()
+
+
+@pytest.mark.parametrize("B", [200, 1000, 4096])
+def test_tensor_core_products_match_mma_sync(B, monkeypatch):
+    """The tcgen05 products (the 256-column ones: both hidden layers and the
+    first layer's activation gradient) against the mma.sync kernel on the same
+    bfloat16 operands: only float32 summation order and bfloat16 rounding of
+    the stored activations differ."""
+    params = J.flatten_params(M.init_params(11))
+    genomes = W.random_genomes(B, 3, 8, seed=B + 1)
+    labels = np.random.default_rng(B).integers(0, 8, size=B).astype(np.uint8)
+    out = {}
+    for mode in ("mma", "tc"):
+        monkeypatch.setenv("JATAM_MLP_PRODUCTS", mode)
+        net = J.Surrogate(max_batch=4096)
+        net.set_params(params)
+        logits = np.zeros((B, 8), np.float32)
+        net.predict(genomes, logits)
+        grads = np.zeros(J.MLP_NPARAM, np.float32)
+        loss = net.train_step(genomes, labels, lr=0.0, grads=grads)
+        out[mode] = (logits, grads, loss)
+        net.close()
+    assert _rel(out["tc"][0], out["mma"][0]) < 1e-2
+    assert _rel(out["tc"][1], out["mma"][1]) < 1e-2
+    assert abs(out["tc"][2] - out["mma"][2]) <= 1e-3 * abs(out["mma"][2])
+    # and against the oracle
+    want_loss, want, _ = M.forward_backward(J.unflatten_params(params), M.genome_bits(genomes),
+                                            labels.astype(np.int64), bf16=True)
+    got = J.unflatten_params(out["tc"][1])
+    for k in ("W1", "b1", "W2", "b2", "W3", "b3"):
+        assert _rel(got[k], want[k]) < 1e-2, k
