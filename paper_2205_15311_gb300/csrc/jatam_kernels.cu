@@ -177,9 +177,20 @@ __device__ __forceinline__ void coop_tables(unsigned &pending, uint32_t *warp_la
     const uint32_t tile = ((t < 2 ? clo : chi) >> (16 * (t & 1))) & 0xFFFFu;
     const uint32_t rot = ((tile << (4 * r)) | (tile >> ((16 - 4 * r) & 15))) & 0xFFFFu;
     const uint32_t rotv = (r == 0) ? tile : rot;
-    const uint32_t tag = valid ? (rotv | ((uint32_t)g << 16)) : (0x100000u | (uint32_t)lane);
-    const uint32_t same = __match_any_sync(FULL, tag);
-    const bool is_rep = valid && (__ffs(same) - 1 == lane);
+    // (t, r) is the representative of its rotated tuple -- the lowest (tile,
+    // rotation) index with that tuple -- unless a lower rotation of the same
+    // tile gives the same tuple (r = 1: the tile is symmetric under a quarter
+    // turn; r = 2, 3: under a half turn, which a quarter-turn symmetry implies)
+    // or an earlier tile is a rotation of this one.  Decided from the colours
+    // alone, without comparing lanes.
+    const uint32_t q1 = ((tile << 4) | (tile >> 12)) & 0xFFFFu, q2 = ((tile << 8) | (tile >> 8)) & 0xFFFFu;
+    bool is_rep = valid && (r == 0 || (r == 1 ? q1 != tile : q2 != tile));
+    for (int u = 0; u < t; ++u) {
+        const uint32_t tu = ((u < 2 ? clo : chi) >> (16 * (u & 1))) & 0xFFFFu;
+        const uint32_t u1 = ((tu << 4) | (tu >> 12)) & 0xFFFFu, u2 = ((tu << 8) | (tu >> 8)) & 0xFFFFu;
+        const uint32_t u3 = ((tu << 12) | (tu >> 4)) & 0xFFFFu;
+        if (tile == tu || tile == u1 || tile == u2 || tile == u3) is_rep = false;
+    }
     const int shift = g * GL;
     const uint32_t gmask = (GL == 32) ? FULL : ((1u << GL) - 1u);
     const uint32_t reps = (__ballot_sync(FULL, is_rep) >> shift) & gmask;
@@ -313,15 +324,13 @@ __device__ __forceinline__ uint32_t coop_shape_hash(int o, const uint32_t *warp_
     return image_hash(best, hc, wc);
 }
 
-// The seed step of replicate 0, evaluated straight from the colours: for each
-// side d of the seed (tile 0, orientation 0) the candidates are the rotated
-// tuples whose side facing the seed has the partner colour of the seed's side
-// d.  Returns 1 (local ambiguity), 3 (unbounded), 0 (terminated: nothing can
-// attach, every replicate ends as the lone seed) or -1 (the assembly grows).
-__device__ __forceinline__ int seed_outcome(unsigned long long cols, int n, int c, int L)
+// W: the unsigned type that holds the colours (32 bits for at most two tiles).
+template <typename W>
+__device__ __forceinline__ int seed_outcome_w(W cols, int n, int c, int L)
 {
-    const unsigned long long ones = 0x1111111111111111ull;
-    const unsigned long long valid = (n >= 4) ? ~0ull : ((1ull << (16 * n)) - 1ull);
+    constexpr int BITS = 8 * (int)sizeof(W);
+    const W ones = (W)0x1111111111111111ull;
+    const W valid = (16 * n >= BITS) ? ~(W)0 : (W)(((W)1 << (16 * n)) - (W)1);
     const int cx = L >> 1;
     bool nd = false, unb = false, grows = false;
 #pragma unroll
@@ -329,15 +338,15 @@ __device__ __forceinline__ int seed_outcome(unsigned long long cols, int n, int 
         const int a = (int)((cols >> (4 * d)) & 15u);
         const int pa = (a == 0) ? -1 : (a & 1) ? ((a + 1 < c) ? a + 1 : -1) : a - 1;
         if (pa < 0) continue;
-        const unsigned long long x = cols ^ ((unsigned long long)pa * ones);
-        const unsigned long long nz = (x | (x >> 1) | (x >> 2) | (x >> 3)) & ones;
-        unsigned long long eq = ~nz & ones & valid;  // bit 4 m set: edge m carries colour pa
+        const W x = cols ^ ((W)pa * ones);
+        const W nz = (x | (x >> 1) | (x >> 2) | (x >> 3)) & ones;
+        W eq = ~nz & ones & valid;  // bit 4 m set: edge m carries colour pa
         if (!eq) continue;
         const int e = (d + 2) & 3;  // the candidate's side that faces the seed
         uint32_t first = 0xFFFFFFFFu;
         bool multi = false;
         while (eq) {
-            const int m = (__ffsll((long long)eq) - 1) >> 2;
+            const int m = ((BITS == 32 ? __ffs((int)eq) : __ffsll((long long)eq)) - 1) >> 2;
             eq &= eq - 1;
             const int t = m >> 2, i = m & 3;
             const uint32_t tile = (uint32_t)(cols >> (16 * t)) & 0xFFFFu;
@@ -355,6 +364,17 @@ __device__ __forceinline__ int seed_outcome(unsigned long long cols, int n, int 
     if (nd) return JATAM_ND_LOCAL;
     if (unb) return JATAM_UNBOUNDED;
     return grows ? -1 : 0;
+}
+
+// The seed step of replicate 0, evaluated straight from the colours: for each
+// side d of the seed (tile 0, orientation 0) the candidates are the rotated
+// tuples whose side facing the seed has the partner colour of the seed's side
+// d.  Returns 1 (local ambiguity), 3 (unbounded), 0 (terminated: nothing can
+// attach, every replicate ends as the lone seed) or -1 (the assembly grows).
+__device__ __forceinline__ int seed_outcome(unsigned long long cols, int n, int c, int L)
+{
+    if (n <= 2) return seed_outcome_w<uint32_t>((uint32_t)cols, n, c, L);
+    return seed_outcome_w<unsigned long long>(cols, n, c, L);
 }
 
 // The replicate just ended (local ambiguity, unbounded growth, or an empty
@@ -629,6 +649,16 @@ __device__ __forceinline__ void hist_insert(SmemHist &H, const Table &T, unsigne
 // N, E, S, W, b bits per colour, the first tile's N edge most significant)
 __device__ __forceinline__ unsigned long long unpack_genotype(unsigned long long g, int n, int b)
 {
+    if (n <= 2) {
+        // at most 8 colours of at most 4 bits: 32-bit arithmetic
+        const uint32_t g32 = (uint32_t)g, cm = (1u << b) - 1u;
+        uint32_t cols = 0;
+        for (int m = 0; m < 4 * n; ++m) {
+            const int pos = b * (4 * n - 1 - m);  // edge e of tile t is m = 4 t + e
+            cols |= ((g32 >> pos) & cm) << (4 * m);
+        }
+        return cols;
+    }
     unsigned long long cols = 0;
     const unsigned long long cm = (1ull << b) - 1ull;
     for (int t = 0; t < n; ++t)
