@@ -60,6 +60,7 @@
 
 #define ORC_MAXL 32
 #define ORC_MAXN 4
+#define ORC_MAXC 8
 
 enum { ORC_DET_BOUNDED = 0, ORC_ND_LOCAL = 1, ORC_ND_STERIC = 2, ORC_UNBOUNDED = 3 };
 enum { OUT_TERMINATED = 0, OUT_ND_LOCAL = 1, OUT_UNBOUNDED = 2 };
@@ -320,6 +321,108 @@ static int run_replicate(const tileset *T, uint64_t stream_id, int rep, grid *G,
     }
 }
 
+/* ---------------------------------------------------------------------------
+ * The movelist process of Section 2.4 (reading L1), the alternative draw order:
+ * the frontier is kept as a last-in-first-out stack.  After each placement
+ * (and after the seed) the sites that have just become frontier sites, taken
+ * in the order N, E, S, W of the placed tile, are pushed in a random order --
+ * permutation number floor(u m! / 2^32) of the m sites, u the Philox word
+ * whose index is the number of placements after the seed so far, decoded in
+ * the factorial number system (digit i picks among the sites not yet taken,
+ * the first pick is pushed first) -- and the next tile goes on the site at the
+ * top.  Candidates, ambiguity and growth past the grid are judged as in the
+ * row-major process.
+ * ------------------------------------------------------------------------- */
+static int g_lifo = 0; /* process of the classification calls below (0: row-major frontier, 1: movelist) */
+
+void orc_set_process(int lifo) { g_lifo = lifo ? 1 : 0; }
+
+/* the order in which permutation number idx of m items is pushed: out[i] = item pushed i-th */
+void orc_lifo_permutation(uint32_t idx, int m, int out[4])
+{
+    int pool[4] = {0, 1, 2, 3};
+    int left = m;
+    for (int i = 0; i < m; i++) {
+        int f = 1;
+        for (int q = 2; q <= m - 1 - i; q++) f *= q;
+        const int sel = (int)(idx / (uint32_t)f);
+        idx %= (uint32_t)f;
+        out[i] = pool[sel];
+        for (int q = sel; q < left - 1; q++) pool[q] = pool[q + 1];
+        left--;
+    }
+}
+
+static int run_replicate_lifo(const tileset *T, uint64_t stream_id, int rep, grid *G, uint64_t *placements,
+                              orc_trace_step *trace, int trace_cap, int *trace_len)
+{
+    int L = T->L;
+    G->L = L;
+    for (int y = 0; y < L; y++)
+        for (int x = 0; x < L; x++) {
+            G->cell[y][x] = -1;
+            G->ncand[y][x] = 0;
+            G->cand[y][x] = -1;
+        }
+    int px = L / 2, py = L / 2;
+    G->cell[py][px] = T->rep[0];
+    G->size = 1;
+    int placed = 0; /* placements after the seed */
+    int sx_stack[ORC_MAXL * ORC_MAXL], sy_stack[ORC_MAXL * ORC_MAXL];
+    int sp = 0;
+    for (;;) {
+        int nd = 0, unb = 0;
+        int newx[4], newy[4], m = 0;
+        for (int d = 0; d < 4; d++) {
+            int qx = px + DX[d], qy = py + DY[d];
+            int in = inside(G, qx, qy);
+            if (in && G->cell[qy][qx] >= 0) continue;
+            int only = -1;
+            int mm = candidates(T, G, qx, qy, &only);
+            if (in) {
+                const int was_frontier = G->ncand[qy][qx] == 1;
+                G->ncand[qy][qx] = mm;
+                G->cand[qy][qx] = (mm == 1) ? only : -1;
+                if (mm == 1 && !was_frontier) {
+                    newx[m] = qx;
+                    newy[m] = qy;
+                    m++;
+                }
+            }
+            if (mm >= 2) nd = 1;
+            else if (!in && mm >= 1) unb = 1;
+        }
+        if (nd) return OUT_ND_LOCAL;
+        if (unb) return OUT_UNBOUNDED;
+        /* push the new sites in the drawn order */
+        uint32_t u = draw(T, stream_id, rep, placed);
+        int fact = 1;
+        for (int q = 2; q <= m; q++) fact *= q;
+        const uint32_t idx = (uint32_t)(((uint64_t)u * (uint64_t)fact) >> 32);
+        int order[4];
+        orc_lifo_permutation(idx, m, order);
+        for (int i = 0; i < m; i++) {
+            sx_stack[sp] = newx[order[i]];
+            sy_stack[sp] = newy[order[i]];
+            sp++;
+        }
+        if (sp == 0) return OUT_TERMINATED;
+        sp--;
+        const int sx = sx_stack[sp], sy = sy_stack[sp];
+        if (trace && *trace_len < trace_cap) {
+            orc_trace_step *ts = &trace[*trace_len];
+            ts->nfront = m; ts->u = u; ts->index = (int32_t)idx; ts->x = sx; ts->y = sy; ts->tuple = G->cand[sy][sx];
+            (*trace_len)++;
+        }
+        G->cell[sy][sx] = G->cand[sy][sx];
+        G->size++;
+        placed++;
+        (*placements)++;
+        px = sx;
+        py = sy;
+    }
+}
+
 static int same_configuration(const grid *A, const grid *B)
 {
     for (int y = 0; y < A->L; y++)
@@ -514,7 +617,7 @@ int orc_classify_ex(int n, int c, int L, int k, uint64_t seed, const uint8_t col
     for (int j = 0; j < k; j++) {
         grid *G = (j == 0) ? A0 : Aj;
         int want = (trace && j == trace_rep);
-        int out = run_replicate(&T, stream_id, j, G, &placed, want ? trace : NULL, trace_cap, &tl);
+        int out = (g_lifo ? run_replicate_lifo : run_replicate)(&T, stream_id, j, G, &placed, want ? trace : NULL, trace_cap, &tl);
         if (out == OUT_UNBOUNDED) { cls = ORC_UNBOUNDED; decided = j; break; }
         if (out == OUT_ND_LOCAL) { cls = ORC_ND_LOCAL; decided = j; break; }
         if (j > 0 && !same_configuration(A0, Aj)) { cls = ORC_ND_STERIC; decided = j; break; }
@@ -785,3 +888,115 @@ int orc_poisson_thresholds(double rate, uint32_t out[4])
 
 /* Fujiyama test-bed fitness (Section 3.2): the Hamming weight of the genome */
 int orc_hamming(uint64_t g) { int h = 0; while (g) { h += (int)(g & 1); g >>= 1; } return h; }
+
+/* ---------------------------------------------------------------------------
+ * Orbits of the exact symmetries of the process (the orbit mode of the
+ * enumeration): a permutation of the c colours that preserves M, turning any
+ * non-seed tile, and permuting the non-seed tiles.  With the draws fixed every
+ * genotype of an orbit assembles identically (the process sees only which
+ * rotated tuples bind, never the labels, and the seed is untouched).  The
+ * representative of an orbit is its smallest packed genotype, found here by
+ * applying every element of the group.
+ * ------------------------------------------------------------------------- */
+static pthread_mutex_t g_aut_mutex = PTHREAD_MUTEX_INITIALIZER;
+static int g_aut_ready[ORC_MAXC + 1];
+static int g_aut_count[ORC_MAXC + 1];
+static uint8_t g_aut[ORC_MAXC + 1][128][ORC_MAXC];
+
+/* every permutation p of 0 .. c-1 with M(p[i], p[j]) == M(i, j), by brute force */
+static void colour_automorphisms(int c)
+{
+    pthread_mutex_lock(&g_aut_mutex);
+    if (!g_aut_ready[c]) {
+        int p[ORC_MAXC];
+        for (int i = 0; i < c; i++) p[i] = i;
+        int count = 0;
+        for (;;) {
+            int ok = 1;
+            for (int i = 0; i < c && ok; i++)
+                for (int j = 0; j < c && ok; j++)
+                    if (orc_bind(p[i], p[j]) != orc_bind(i, j)) ok = 0;
+            if (ok && count < 128) {
+                for (int i = 0; i < c; i++) g_aut[c][count][i] = (uint8_t)p[i];
+                count++;
+            }
+            /* next permutation in lexicographic order */
+            int i = c - 2;
+            while (i >= 0 && p[i] >= p[i + 1]) i--;
+            if (i < 0) break;
+            int j = c - 1;
+            while (p[j] <= p[i]) j--;
+            int t = p[i]; p[i] = p[j]; p[j] = t;
+            for (int a = i + 1, b2 = c - 1; a < b2; a++, b2--) { t = p[a]; p[a] = p[b2]; p[b2] = t; }
+        }
+        g_aut_count[c] = count;
+        g_aut_ready[c] = 1;
+    }
+    pthread_mutex_unlock(&g_aut_mutex);
+}
+
+int orc_colour_automorphism_count(int c)
+{
+    if (c < 1 || c > ORC_MAXC) return -1;
+    colour_automorphisms(c);
+    return g_aut_count[c];
+}
+
+static uint64_t encode_genotype(const uint8_t col[16], int n, int c)
+{
+    int b = 0;
+    while ((1 << b) < c) b++;
+    uint64_t g = 0;
+    for (int t = 0; t < n; t++)
+        for (int e = 0; e < 4; e++) g |= (uint64_t)col[4 * t + e] << (b * (4 * (n - 1 - t) + (3 - e)));
+    return g;
+}
+
+uint64_t orc_orbit_rep(uint64_t g, int n, int c)
+{
+    uint8_t col[16], img[16];
+    if (orc_decode(g, n, c, col) != 0) return g;
+    colour_automorphisms(c);
+    const int m = n - 1;                        /* non-seed tiles */
+    int nperm = 1, nrot = 1;
+    for (int i = 2; i <= m; i++) nperm *= i;
+    for (int i = 0; i < m; i++) nrot *= 4;
+    uint64_t best = g;
+    for (int a = 0; a < g_aut_count[c]; a++) {
+        const uint8_t *pi = g_aut[c][a];
+        for (int pk = 0; pk < nperm; pk++) {
+            /* the pk-th permutation of the non-seed slots (factorial number system) */
+            int perm[ORC_MAXN], pool[ORC_MAXN], np = m, code = pk;
+            for (int i = 0; i < m; i++) pool[i] = i + 1;
+            for (int i = 0; i < m; i++) {
+                int f = 1;
+                for (int q = 2; q <= m - 1 - i; q++) f *= q;
+                int sel = code / f;
+                code %= f;
+                perm[i] = pool[sel];
+                for (int q = sel; q < np - 1; q++) pool[q] = pool[q + 1];
+                np--;
+            }
+            for (int rk = 0; rk < nrot; rk++) {
+                for (int e = 0; e < 4; e++) img[e] = pi[col[e]];
+                int code_r = rk;
+                for (int s = 0; s < m; s++) {
+                    const int r = code_r % 4;
+                    code_r /= 4;
+                    const int t = perm[s];
+                    for (int e = 0; e < 4; e++) img[4 * (s + 1) + e] = pi[col[4 * t + ((e - r + 4) % 4)]];
+                }
+                const uint64_t v = encode_genotype(img, n, c);
+                if (v < best) best = v;
+            }
+        }
+    }
+    return best;
+}
+
+/* representatives of genotypes first .. first + count - 1 */
+int orc_orbit_reps(int n, int c, uint64_t first, uint64_t count, uint64_t *out)
+{
+    for (uint64_t i = 0; i < count; i++) out[i] = orc_orbit_rep(first + i, n, c);
+    return 0;
+}

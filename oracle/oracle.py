@@ -104,6 +104,17 @@ def lib():
             L.orc_c4_hash.restype = ctypes.c_uint32
             L.orc_set_hash_mode.argtypes = [ctypes.c_int]
             L.orc_set_hash_mode.restype = None
+            L.orc_colour_automorphism_count.argtypes = [ctypes.c_int]
+            L.orc_colour_automorphism_count.restype = ctypes.c_int
+            L.orc_orbit_rep.argtypes = [ctypes.c_uint64, ctypes.c_int, ctypes.c_int]
+            L.orc_orbit_rep.restype = ctypes.c_uint64
+            L.orc_orbit_reps.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_uint64, ctypes.c_uint64,
+                                         ctypes.POINTER(ctypes.c_uint64)]
+            L.orc_orbit_reps.restype = ctypes.c_int
+            L.orc_set_process.argtypes = [ctypes.c_int]
+            L.orc_set_process.restype = None
+            L.orc_lifo_permutation.argtypes = [ctypes.c_uint32, ctypes.c_int, ctypes.POINTER(ctypes.c_int)]
+            L.orc_lifo_permutation.restype = None
             L.orc_hamming.argtypes = [ctypes.c_uint64]
             L.orc_hamming.restype = ctypes.c_int
             _lib = L
@@ -332,3 +343,65 @@ class hash_mode:
 
     def __exit__(self, *exc):
         lib().orc_set_hash_mode(0)
+
+
+# ---------------------------------------------------------------------------
+# orbit mode (exact symmetries of the process)
+# ---------------------------------------------------------------------------
+def colour_automorphism_count(c) -> int:
+    """Permutations of the c colours that preserve the binding matrix."""
+    return int(lib().orc_colour_automorphism_count(int(c)))
+
+
+def orbit_rep(g, n, c) -> int:
+    """Smallest packed genotype of g's orbit under the colour permutations that
+    preserve the binding matrix, turns of non-seed tiles and permutations of
+    non-seed tiles (all of them applied)."""
+    return int(lib().orc_orbit_rep(int(g), int(n), int(c)))
+
+
+def orbit_reps(n, c, first, count):
+    out = np.zeros(count, np.uint64)
+    lib().orc_orbit_reps(int(n), int(c), int(first), int(count),
+                         out.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64)))
+    return out
+
+
+def enumerate_orbits(n, c, L, k, seed, count, *, nthreads=None):
+    """The orbit mode of the enumeration over genotypes 0 .. count - 1: every
+    genotype gets the result of classifying its orbit representative with the
+    representative as stream id."""
+    reps = orbit_reps(n, c, 0, count)
+    uniq = np.unique(reps)
+    cols = np.zeros((uniq.shape[0], 16), np.uint8)
+    for i, g in enumerate(uniq.tolist()):
+        cols[i, : 4 * n] = decode(g, n, c)[: 4 * n]
+    res_u, _ = classify_batch(cols, n=n, c=c, L=L, k=k, seed=seed, ids=uniq, nthreads=nthreads)
+    pos = np.searchsorted(uniq, reps)
+    return res_u[pos], reps
+
+
+# ---------------------------------------------------------------------------
+# the movelist (LIFO) process of Section 2.4
+# ---------------------------------------------------------------------------
+class process_mode:
+    """Context manager: classify with the movelist process (new frontier sites
+    pushed on a stack in a drawn order, the top one placed) instead of the
+    uniform draw over the row-major frontier."""
+
+    def __init__(self, lifo: bool):
+        self.lifo = bool(lifo)
+
+    def __enter__(self):
+        lib().orc_set_process(int(self.lifo))
+        return self
+
+    def __exit__(self, *exc):
+        lib().orc_set_process(0)
+
+
+def lifo_permutation(idx, m):
+    """Push order of permutation number idx of m items (item pushed first ...)."""
+    out = (ctypes.c_int * 4)()
+    lib().orc_lifo_permutation(int(idx), int(m), out)
+    return [out[i] for i in range(m)]
