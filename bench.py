@@ -390,6 +390,9 @@ def main():
                          "for measurements")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-threads", type=int, default=0, help="threads of the oracle arm (default: all cores)")
+    ap.add_argument("--orbits", action="store_true",
+                    help="orbit mode (JATAM_ORBITS): one classification per orbit of the exact symmetries; "
+                         "a measurement, not the bench line")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end leg")
     ap.add_argument("--profile-genomes", type=int, default=0,
                     help="instead of the bench: ga_evaluate on this many uniform random genomes of the "
@@ -446,7 +449,7 @@ def main():
 
     def step():
         J.enumerate_space(n, c, L, k, seed, first, count, sampled=sampled, out=out, hist=hist, hist_len=hlen,
-                          hist_cap=hist_cap, stream=stream)
+                          hist_cap=hist_cap, stream=stream, orbits=args.orbits)
 
     J.jatam_profile(1)
     with torch.cuda.stream(stream):
@@ -492,14 +495,14 @@ def main():
     hlen_h = np.zeros(1, np.uint32)
     if not args.no_e2e:
         J.enumerate_space(n, c, L, k, seed, first, count, sampled=sampled, out=out_h, hist=hist_h,
-                          hist_len=hlen_h, hist_cap=hist_cap, stream=stream)
+                          hist_len=hlen_h, hist_cap=hist_cap, stream=stream, orbits=args.orbits)
     e2e_times = []
     for i in range(0 if args.no_e2e else max(3, min(args.steps, 5))):
         flush.fill_(i & 255)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         J.enumerate_space(n, c, L, k, seed, first, count, sampled=sampled, out=out_h, hist=hist_h,
-                          hist_len=hlen_h, hist_cap=hist_cap, stream=stream)
+                          hist_len=hlen_h, hist_cap=hist_cap, stream=stream, orbits=args.orbits)
         e2e_times.append(time.perf_counter() - t0)
     e2e_s = float(np.mean(e2e_times)) if e2e_times else float("nan")
     if world > 1:
@@ -519,7 +522,7 @@ def main():
         placements = None
         golden = os.path.join(ROOT, "tests", "golden",
                               {"s28_full": "c2_summary.json", "s24_full": "c1_summary.json"}.get(WORKLOAD, "-"))
-        if os.path.exists(golden) and rank == 0 and not args.count:
+        if os.path.exists(golden) and rank == 0 and not args.count and not args.orbits:
             placements = json.load(open(golden))["placements"]
         roofline = None
         kms = float(np.mean(kernel_ms))
@@ -544,7 +547,7 @@ def main():
             roofline["method_placements"] = placements
             roofline["method_ops_frac"] = round(mops / (kms / 1e3) / 1e12 / alu_peak, 4)
         cpu = None
-        if not args.no_cpu_baseline and world == 1:
+        if not args.no_cpu_baseline and world == 1 and not args.orbits:
             from oracle import oracle as O
             O.build()
             cores = getattr(args, "cpu_threads", 0) or os.cpu_count() or 1
@@ -555,7 +558,8 @@ def main():
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "u32", "data": "synthetic",
-            "config": {"workload": f"{WORKLOAD}: {'sampled' if sampled else 'all'} {count} genotypes of "
+            "config": {"workload": f"{WORKLOAD}{' (orbit mode)' if args.orbits else ''}: "
+                                   f"{'sampled' if sampled else 'all'} {count} genotypes of "
                                    f"S_{{{n},{c}}}, n={n} c={c} L={L} k={k} seed={seed0}",
                        "global_batch": world * count, "parallelism": f"replicas x{world}",
                        "l2": "256 MB buffer written between timed steps; outputs 134 MB > L2",

@@ -73,6 +73,14 @@ extern "C" {
                                 cropped shape, sort the 4 hashes, hash them again (16 bytes, little endian);
                                 mirror images stay distinct.  Default: the canonical form under all 8
                                 symmetries of the square */
+#define JATAM_ORBITS 0x40u   /* jatam_enumerate over a range that starts at genotype 0: classify one
+                                genotype per orbit of the exact symmetries of the process (colour
+                                permutations that preserve the binding pairs, turns and permutations
+                                of the non-seed tiles) and give every genotype its orbit
+                                representative's result -- the smallest genotype of the orbit,
+                                classified with itself as stream id.  With the draws fixed every
+                                member assembles as the representative does, so this equals
+                                classifying each genotype with the representative's stream id. */
 #define JATAM_GRAPH 0x8u     /* capture the call's kernel sequence as a CUDA graph the first time a given
                                 set of arguments is seen, and replay it on later calls with the same set */
 
@@ -379,8 +387,9 @@ int jatam_work_counters(uint64_t counters[4]);
  *   is part of the library (8 B per genotype for JATAM_NOALLOC_MAX_COUNT
  *   genotypes, about 8 MB); every GPU that loads the library holds it until
  *   the process exits.
- *   cfg   : as for jatam_enumerate (JATAM_SAMPLED honoured; with JATAM_SYNC the
- *           call waits for the stream and reports device-side errors).
+ *   cfg   : as for jatam_enumerate (JATAM_SAMPLED and JATAM_C4_HASH honoured;
+ *           with JATAM_SYNC the call waits for the stream and reports
+ *           device-side errors; JATAM_ORBITS is rejected with JATAM_EINVAL).
  *   first, count : index range, count <= JATAM_NOALLOC_MAX_COUNT, else
  *           JATAM_EINVAL with a message naming the limit.
  *   out   : [count] results in DEVICE memory (required; host memory is

@@ -377,6 +377,7 @@ int run(Workspace *w, LaunchArgs a, int S, jatam_result *out, int32_t *fitness, 
         }
         if (n_items && mixed && !per_shape) CUDA_TRY(launch_classify_mixed(a, mixed_blocks, s));
         if (events) CUDA_TRY(cudaEventRecord(w->k_stop, s));
+        if (n_items && a.orbits) CUDA_TRY(launch_orbit_fill(a, (int)pblocks, s));
         if (hist) {
             CUDA_TRY(launch_hist_compact(w->table, w->compact, w->nkeys, 2 * w->num_sms, s));
             CUDA_TRY(launch_hist_emit(w->compact, w->nkeys, o.hist_dev, hist_cap,
@@ -401,7 +402,7 @@ int run(Workspace *w, LaunchArgs a, int S, jatam_result *out, int32_t *fitness, 
                                   a.plan_w8, S, blocks, warps, per_shape, mixed_blocks, pblocks, hist_cap,
                                   fixed[0].blocks, fixed[0].warps, fixed[0].stop_at, fixed[1].blocks, fixed[1].warps,
                                   fixed[1].stop_at, fixed[2].blocks, fixed[2].warps, fixed[2].stop_at,
-                                  a.stats ? 1 : 0};
+                                  a.stats ? 1 : 0, a.c4, a.orbits};
         put(nums, sizeof nums);
         cudaGraphExec_t exec = nullptr;
         auto it = w->graphs.find(key);
@@ -511,6 +512,9 @@ int jatam_enumerate(const jatam_config *cfg, uint64_t first, uint64_t count, jat
     } else if (count > ~0ull - first) {
         return fail(JATAM_EINVAL, "index range overflows");
     }
+    const bool orbits = (cfg->flags & JATAM_ORBITS) != 0;
+    if (orbits && (sampled || first != 0))
+        return fail(JATAM_EINVAL, "JATAM_ORBITS needs an index range that starts at genotype 0");
     Workspace *w = nullptr;
     rc = workspace(&w);
     if (rc) return rc;
@@ -518,6 +522,7 @@ int jatam_enumerate(const jatam_config *cfg, uint64_t first, uint64_t count, jat
     a.mode = sampled ? MODE_SAMPLED : MODE_RANGE;
     a.first = first;
     a.count = count;
+    a.orbits = orbits ? 1 : 0;
     a.c4 = (cfg->flags & JATAM_C4_HASH) ? 1 : 0;
     a.n = cfg->n; a.c = cfg->c; a.L = cfg->L; a.k = cfg->k;
     a.key0 = (uint32_t)cfg->seed;

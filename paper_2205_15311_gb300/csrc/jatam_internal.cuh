@@ -60,6 +60,7 @@ struct LaunchArgs {
     Table table;
     int use_hist;
     int c4;                       // 1: the rotation-only hash variant instead of the canonical form
+    int orbits;                   // 1: orbit mode (one classification per orbit of the exact symmetries)
     int stop_at;                    // finished lanes that end a growth round (1..32)
     unsigned long long *list;        // items left to grow, written by the pre-filter: 1 or 3 lists
     unsigned long long list_stride;  // capacity of one list (the call's item count)
@@ -98,6 +99,7 @@ cudaError_t launch_hist_compact(Table t, Compact c, unsigned *nkeys, int blocks,
 cudaError_t launch_hist_emit(Compact c, const unsigned *nkeys, jatam_hist_entry *hist, unsigned cap,
                              uint32_t *hist_len, int blocks, cudaStream_t st);
 cudaError_t launch_philox(const uint32_t *in, unsigned long long n, uint32_t *out, cudaStream_t st);
+cudaError_t launch_orbit_fill(const LaunchArgs &a, int blocks, cudaStream_t st);
 
 // genetic algorithm (jatam_ga.cu)
 struct GaArgs {

@@ -671,6 +671,67 @@ __device__ __forceinline__ unsigned long long unpack_genotype(unsigned long long
 
 __device__ __forceinline__ int log2_colours(int c) { return c >= 8 ? 3 : c >= 4 ? 2 : c >= 2 ? 1 : 0; }
 
+// The smallest packed genotype of g's orbit under the exact symmetries of the
+// process: colour permutations that preserve the binding pairs (any pair to
+// any pair, either order within a pair, the colours that bind nothing among
+// themselves), turns of the non-seed tiles and permutations of them.  For each
+// arrangement of the non-seed tiles the smallest relabelling is greedy: the
+// colours, read in packed order (most significant first), get the smallest
+// label still free in their class, a first-seen paired colour the odd label
+// of the next free pair and its partner the even one.
+__device__ __forceinline__ unsigned long long orbit_rep(unsigned long long g, int n, int c, int b)
+{
+    const unsigned long long cols = unpack_genotype(g, n, b);
+    const int m = n - 1;
+    const int nrot = 1 << (2 * m);
+    const int nperm = (m <= 1) ? 1 : (m == 2) ? 2 : 6;
+    const int top = (c % 2 == 0) ? c - 1 : -1;  // the top colour binds nothing when c is even
+    unsigned long long best = g;
+    for (int pk = 0; pk < nperm; ++pk) {
+        // slot order of the non-seed tiles: permutation pk of 1 .. m
+        int order[3] = {1, 2, 3};
+        if (m == 2 && pk == 1) { order[0] = 2; order[1] = 1; }
+        if (m == 3) {
+            const int perms[6][3] = {{1, 2, 3}, {1, 3, 2}, {2, 1, 3}, {2, 3, 1}, {3, 1, 2}, {3, 2, 1}};
+            order[0] = perms[pk][0]; order[1] = perms[pk][1]; order[2] = perms[pk][2];
+        }
+        for (int rk = 0; rk < nrot; ++rk) {
+            uint32_t map = 0xFFFFFFFFu;  // nibble x: the label of colour x (15: none yet)
+            int next_pair = 1, inert_seen = 0;
+            unsigned long long v = 0;
+            for (int pos = 0; pos < 4 * n; ++pos) {
+                const int s = pos >> 2, e = pos & 3;
+                int src;
+                if (s == 0) {
+                    src = e;
+                } else {
+                    const int r = (rk >> (2 * (s - 1))) & 3;
+                    src = 4 * order[s - 1] + ((e - r) & 3);
+                }
+                const int x = (int)((cols >> (4 * src)) & 15u);
+                int y = (int)((map >> (4 * x)) & 15u);
+                if (y == 15) {
+                    const bool inert = x == 0 || x == top;
+                    if (inert) {
+                        y = inert_seen == 0 ? 0 : top;
+                        ++inert_seen;
+                        map = (map & ~(15u << (4 * x))) | ((uint32_t)y << (4 * x));
+                    } else {
+                        const int partner = (x & 1) ? x + 1 : x - 1;
+                        y = next_pair;
+                        map = (map & ~(15u << (4 * x))) | ((uint32_t)next_pair << (4 * x));
+                        map = (map & ~(15u << (4 * partner))) | ((uint32_t)(next_pair + 1) << (4 * partner));
+                        next_pair += 2;
+                    }
+                }
+                v = (v << b) | (unsigned long long)y;
+            }
+            best = v < best ? v : best;
+        }
+    }
+    return best;
+}
+
 // One item of a launch: its colours (nibble-packed), size parameters and
 // stream id.  ok is false for a record with a colour >= c or a parameter out
 // of range (L must also fit the lattice template smax).
@@ -781,6 +842,8 @@ __global__ void __launch_bounds__(256) prefilter_kernel(const LaunchArgs a, int 
             if (!it.ok) {
                 atomicOr(a.err, ERR_INVALID_ITEM);
                 write_result(a, idx, 255, 0, 0u, 0u);
+            } else if (a.orbits && orbit_rep(it.sid, it.n, it.c, b_uniform) != it.sid) {
+                // not its orbit's representative: the fill pass copies the representative's result
             } else {
                 const int so = seed_outcome(it.cols, it.n, it.c, it.L);
                 if (so < 0) {
@@ -1129,6 +1192,30 @@ __global__ void __launch_bounds__(256) classify_mixed_kernel(const LaunchArgs a)
 }
 
 
+// Orbit mode, after the growth kernel: every genotype that is not its orbit's
+// representative takes the representative's result (the representative is the
+// smaller genotype, so it lies in the range, which starts at 0) and is counted
+// in the histogram under the representative's stream id.
+__global__ void __launch_bounds__(256) orbit_fill_kernel(const LaunchArgs a)
+{
+    __shared__ SmemHist H;
+    hist_begin(H);
+    const int b = log2_colours(a.c);
+    const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
+    for (unsigned long long idx = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; idx < a.count;
+         idx += stride) {
+        const unsigned long long g = a.first + idx;
+        const unsigned long long r = orbit_rep(g, a.n, a.c, b);
+        if (r == g) continue;
+        const jatam_result res = a.out[r - a.first];
+        a.out[idx] = res;
+        if (a.use_hist && res.cls != 255)
+            hist_insert(H, a.table, ((unsigned long long)res.cls << 32) | res.shape_hash, 1u, r, res.size, res.size,
+                        a.err);
+    }
+    hist_end(H, a);
+}
+
 __global__ void reset_kernel(unsigned long long *work_next, unsigned *nkeys, unsigned long long *list_count)
 {
     for (int c = 0; c < 3; ++c) {
@@ -1373,6 +1460,13 @@ cudaError_t launch_hist_emit(Compact c, const unsigned *nkeys, jatam_hist_entry 
                              uint32_t *hist_len, int blocks, cudaStream_t st)
 {
     hist_emit_kernel<<<blocks, 256, 0, st>>>(c, nkeys, hist, cap, hist_len);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_orbit_fill(const LaunchArgs &a, int blocks, cudaStream_t st)
+{
+    if (a.count == 0) return cudaSuccess;
+    orbit_fill_kernel<<<blocks, 256, 0, st>>>(a);
     return cudaGetLastError();
 }
 

@@ -93,6 +93,7 @@ extern "C" int jatam_enumerate_noalloc(const jatam_config *cfg, uint64_t first, 
         return noalloc_fail(JATAM_EINVAL, "count exceeds JATAM_NOALLOC_MAX_COUNT (the fixed scratch holds "
                                           "1,048,576 genotypes per call)");
     const bool sampled = (cfg->flags & JATAM_SAMPLED) != 0;
+    if (cfg->flags & JATAM_ORBITS) return noalloc_fail(JATAM_EINVAL, "JATAM_ORBITS needs jatam_enumerate");
     const int bits = 4 * n * colour_bits(c);
     if (!sampled) {
         const uint64_t space = bits >= 64 ? ~0ull : (1ull << bits);
@@ -121,6 +122,7 @@ extern "C" int jatam_enumerate_noalloc(const jatam_config *cfg, uint64_t first, 
     a.first = first;
     a.count = count;
     a.n = n; a.c = c; a.L = L; a.k = k;
+    a.c4 = (cfg->flags & JATAM_C4_HASH) ? 1 : 0;
     a.key0 = (uint32_t)cfg->seed;
     a.key1 = (uint32_t)(cfg->seed >> 32);
     a.out = out;

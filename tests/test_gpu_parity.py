@@ -409,3 +409,33 @@ def test_work_counters_count_the_executed_process():
     assert [tuple(x) for x in res.tolist()] == ref
     assert {key: got[key] for key in want} == want
     assert got["lane_slots"] % 32 == 0 and got["lane_slots"] >= got["placements"] + got["seeds"]
+
+
+@pytest.mark.parametrize("n,c,L,k,seed,count", [(2, 4, 16, 10, 1, 1 << 16), (2, 8, 16, 20, 2, 300000),
+                                                (3, 4, 8, 6, 5, 200000)])
+def test_orbit_mode_matches_oracle(n, c, L, k, seed, count):
+    """JATAM_ORBITS: every genotype gets its orbit representative's result
+    (classified with the representative as stream id), equal to the oracle's
+    orbit mode; the histogram counts every genotype under its representative's
+    stream id."""
+    res, hist, m = _dev_enumerate_orbits(n, c, L, k, seed, count)
+    want, reps = O.enumerate_orbits(n, c, L, k, seed, count)
+    assert np.array_equal(res, want)
+    assert _hist_rows(hist) == _hist_rows(_oracle_hist(want, reps))
+
+
+def _dev_enumerate_orbits(n, c, L, k, seed, count, hist_cap=1 << 16):
+    out = torch.full((count * 8,), 0xEE, dtype=torch.uint8, device="cuda")
+    hist = torch.empty(hist_cap * 32, dtype=torch.uint8, device="cuda")
+    hlen = torch.zeros(1, dtype=torch.int32, device="cuda")
+    J.enumerate_space(n, c, L, k, seed, 0, count, out=out, hist=hist, hist_len=hlen, hist_cap=hist_cap, sync=True,
+                      orbits=True)
+    m = int(hlen.item())
+    return J.results_view(out)[:count], J.hist_view(hist, min(m, hist_cap)), m
+
+
+def test_orbit_mode_rejects_ranges_not_starting_at_zero():
+    out = torch.empty(16 * 8, dtype=torch.uint8, device="cuda")
+    with pytest.raises(J.JatamError) as e:
+        J.enumerate_space(2, 8, 16, 20, 2, 5, 16, out=out, sync=True, orbits=True)
+    assert e.value.code == J.JATAM_EINVAL
