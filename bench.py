@@ -390,6 +390,8 @@ def main():
                          "for measurements")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-threads", type=int, default=0, help="threads of the oracle arm (default: all cores)")
+    ap.add_argument("--lifo", action="store_true",
+                    help="the movelist process (JATAM_LIFO) instead of the row-major frontier; a measurement")
     ap.add_argument("--orbits", action="store_true",
                     help="orbit mode (JATAM_ORBITS): one classification per orbit of the exact symmetries; "
                          "a measurement, not the bench line")
@@ -449,7 +451,7 @@ def main():
 
     def step():
         J.enumerate_space(n, c, L, k, seed, first, count, sampled=sampled, out=out, hist=hist, hist_len=hlen,
-                          hist_cap=hist_cap, stream=stream, orbits=args.orbits)
+                          hist_cap=hist_cap, stream=stream, orbits=args.orbits, lifo=args.lifo)
 
     J.jatam_profile(1)
     with torch.cuda.stream(stream):
@@ -495,14 +497,14 @@ def main():
     hlen_h = np.zeros(1, np.uint32)
     if not args.no_e2e:
         J.enumerate_space(n, c, L, k, seed, first, count, sampled=sampled, out=out_h, hist=hist_h,
-                          hist_len=hlen_h, hist_cap=hist_cap, stream=stream, orbits=args.orbits)
+                          hist_len=hlen_h, hist_cap=hist_cap, stream=stream, orbits=args.orbits, lifo=args.lifo)
     e2e_times = []
     for i in range(0 if args.no_e2e else max(3, min(args.steps, 5))):
         flush.fill_(i & 255)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         J.enumerate_space(n, c, L, k, seed, first, count, sampled=sampled, out=out_h, hist=hist_h,
-                          hist_len=hlen_h, hist_cap=hist_cap, stream=stream, orbits=args.orbits)
+                          hist_len=hlen_h, hist_cap=hist_cap, stream=stream, orbits=args.orbits, lifo=args.lifo)
         e2e_times.append(time.perf_counter() - t0)
     e2e_s = float(np.mean(e2e_times)) if e2e_times else float("nan")
     if world > 1:
@@ -522,7 +524,7 @@ def main():
         placements = None
         golden = os.path.join(ROOT, "tests", "golden",
                               {"s28_full": "c2_summary.json", "s24_full": "c1_summary.json"}.get(WORKLOAD, "-"))
-        if os.path.exists(golden) and rank == 0 and not args.count and not args.orbits:
+        if os.path.exists(golden) and rank == 0 and not args.count and not args.orbits and not args.lifo:
             placements = json.load(open(golden))["placements"]
         roofline = None
         kms = float(np.mean(kernel_ms))
@@ -547,7 +549,7 @@ def main():
             roofline["method_placements"] = placements
             roofline["method_ops_frac"] = round(mops / (kms / 1e3) / 1e12 / alu_peak, 4)
         cpu = None
-        if not args.no_cpu_baseline and world == 1 and not args.orbits:
+        if not args.no_cpu_baseline and world == 1 and not args.orbits and not args.lifo:
             from oracle import oracle as O
             O.build()
             cores = getattr(args, "cpu_threads", 0) or os.cpu_count() or 1
@@ -558,7 +560,8 @@ def main():
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "u32", "data": "synthetic",
-            "config": {"workload": f"{WORKLOAD}{' (orbit mode)' if args.orbits else ''}: "
+            "config": {"workload": f"{WORKLOAD}{' (orbit mode)' if args.orbits else ''}"
+                                   f"{' (movelist process)' if args.lifo else ''}: "
                                    f"{'sampled' if sampled else 'all'} {count} genotypes of "
                                    f"S_{{{n},{c}}}, n={n} c={c} L={L} k={k} seed={seed0}",
                        "global_batch": world * count, "parallelism": f"replicas x{world}",

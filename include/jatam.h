@@ -81,6 +81,14 @@ extern "C" {
                                 classified with itself as stream id.  With the draws fixed every
                                 member assembles as the representative does, so this equals
                                 classifying each genotype with the representative's stream id. */
+#define JATAM_LIFO 0x80u     /* the movelist process of Section 2.4 instead of the uniform draw over the
+                                row-major frontier: after each placement the sites that have just
+                                become frontier sites, in the order N, E, S, W of the placed tile, are
+                                pushed on a stack in a drawn order (permutation floor(u m! / 2^32) of
+                                the m sites, factorial number system, first pick pushed first; u = word
+                                s of the replicate's stream, s = placements after the seed so far) and
+                                the next tile goes on the top site.  Items of one shape only (not the
+                                mixed batches of jatam_classify_batch). */
 #define JATAM_GRAPH 0x8u     /* capture the call's kernel sequence as a CUDA graph the first time a given
                                 set of arguments is seen, and replay it on later calls with the same set */
 
@@ -389,7 +397,8 @@ int jatam_work_counters(uint64_t counters[4]);
  *   the process exits.
  *   cfg   : as for jatam_enumerate (JATAM_SAMPLED and JATAM_C4_HASH honoured;
  *           with JATAM_SYNC the call waits for the stream and reports
- *           device-side errors; JATAM_ORBITS is rejected with JATAM_EINVAL).
+ *           device-side errors; JATAM_ORBITS and JATAM_LIFO are rejected with
+ *           JATAM_EINVAL).
  *   first, count : index range, count <= JATAM_NOALLOC_MAX_COUNT, else
  *           JATAM_EINVAL with a message naming the limit.
  *   out   : [count] results in DEVICE memory (required; host memory is

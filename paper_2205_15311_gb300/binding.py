@@ -31,6 +31,7 @@ JATAM_GRAPH = 0x8
 JATAM_C4_HASH = 0x10
 JATAM_PERSISTENT = 0x20
 JATAM_ORBITS = 0x40
+JATAM_LIFO = 0x80
 JATAM_NOALLOC_MAX_COUNT = 1048576
 
 RESULT_DTYPE = np.dtype([("cls", "u1"), ("decided_rep", "u1"), ("size", "<u2"), ("shape_hash", "<u4")])
@@ -298,11 +299,11 @@ def check(rc):
 
 
 def enumerate_space(n, c, L, k, seed, first, count, *, sampled=False, out=None, hist=None, hist_len=None,
-                    hist_cap=0, stream=None, sync=False, graph=False, c4_hash=False, orbits=False):
+                    hist_cap=0, stream=None, sync=False, graph=False, c4_hash=False, orbits=False, lifo=False):
     """jatam_enumerate on caller buffers (torch tensors or numpy arrays)."""
     cfg = make_config(n, c, L, k, seed, (JATAM_SAMPLED if sampled else 0) | (JATAM_SYNC if sync else 0)
                       | (JATAM_GRAPH if graph else 0) | (JATAM_C4_HASH if c4_hash else 0)
-                      | (JATAM_ORBITS if orbits else 0))
+                      | (JATAM_ORBITS if orbits else 0) | (JATAM_LIFO if lifo else 0))
     return check(jatam_enumerate(ctypes.addressof(cfg), first, count, _addr(out), _addr(hist), hist_cap,
                                  _addr(hist_len), _stream_handle(stream)))
 

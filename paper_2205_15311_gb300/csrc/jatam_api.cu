@@ -104,6 +104,8 @@ struct Workspace {
     cudaEvent_t k_start = nullptr, k_stop = nullptr;  // around the last profiled kernel
     bool k_valid = false;
     std::map<std::string, cudaGraphExec_t> graphs;  // captured calls, by argument set
+    void *lifo_buf = nullptr;  // movelist process: one stack per thread of the growth launch
+    size_t lifo_bytes = 0;
     void *ga_buf = nullptr;   // ga_run / ga_breed: fitness, children, cumsum, stats
     size_t ga_bytes = 0;
     void *screen_buf = nullptr;  // ga_run_screened: candidates, chosen indices, scores
@@ -278,8 +280,6 @@ int run(Workspace *w, LaunchArgs a, int S, jatam_result *out, int32_t *fitness, 
         if (o.host_hist) {
             if (w->stage_hist_cap < hist_cap) {
                 if (w->stage_hist) cudaFree(w->stage_hist);
-        if (w->ga_buf) cudaFree(w->ga_buf);
-        if (w->screen_buf) cudaFree(w->screen_buf);
                 w->stage_hist = nullptr;
                 w->stage_hist_cap = 0;
                 cudaError_t e = cudaMalloc(&w->stage_hist, (size_t)hist_cap * sizeof(jatam_hist_entry));
@@ -323,14 +323,23 @@ int run(Workspace *w, LaunchArgs a, int S, jatam_result *out, int32_t *fitness, 
     const int nt = mixed ? 16 : tuple_table_size(a.n);
     long long blocks = 0;
     if (!mixed) {
-        CUDA_TRY(classify_set_attributes(S, nt, warps));
+        CUDA_TRY(classify_set_attributes(S, nt, warps, a.lifo != 0));
         int per_sm = 0;
-        CUDA_TRY(classify_occupancy(S, nt, warps, &per_sm));
+        CUDA_TRY(classify_occupancy(S, nt, warps, &per_sm, a.lifo != 0));
         if (per_sm < 1) return fail(JATAM_ECUDA, "classification kernel does not fit on an SM");
         blocks = (long long)per_sm * w->num_sms;
         const long long lanes_per_cta = 32LL * warps;
         const long long needed = (long long)((n_items + lanes_per_cta - 1) / lanes_per_cta);
         if (needed < blocks) blocks = needed < 1 ? 1 : needed;
+    }
+
+    a.lifo_stack = nullptr;
+    if (a.lifo) {
+        if (mixed) return fail(JATAM_EINVAL, "JATAM_LIFO needs items of one shape");
+        const size_t bytes = (size_t)(blocks < 1 ? 1 : blocks) * warps * 32 * (size_t)S * S * 2;
+        int rc = grow(&w->lifo_buf, &w->lifo_bytes, bytes);
+        if (rc) return rc;
+        a.lifo_stack = static_cast<uint16_t *>(w->lifo_buf);
     }
 
     // launch shapes of the growth kernels, fixed before anything is enqueued
@@ -395,7 +404,7 @@ int run(Workspace *w, LaunchArgs a, int S, jatam_result *out, int32_t *fitness, 
         std::string key;
         auto put = [&key](const void *p, size_t n) { key.append(static_cast<const char *>(p), n); };
         const void *ptrs[] = {a.colours, a.shapes, a.ids, a.genomes, a.out, a.fitness, a.list, o.hist_dev,
-                              o.host_len ? nullptr : o.hist_len_dev};
+                              o.host_len ? nullptr : o.hist_len_dev, a.lifo_stack};
         put(ptrs, sizeof ptrs);
         const long long nums[] = {a.mode, (long long)a.first, (long long)a.count, a.n, a.c, a.L, a.k, a.key0, a.key1,
                                   a.use_hist, a.stop_at, (long long)a.list_stride, a.bucket, a.plan_w32, a.plan_w16,
@@ -523,6 +532,7 @@ int jatam_enumerate(const jatam_config *cfg, uint64_t first, uint64_t count, jat
     a.first = first;
     a.count = count;
     a.orbits = orbits ? 1 : 0;
+    a.lifo = (cfg->flags & JATAM_LIFO) ? 1 : 0;
     a.c4 = (cfg->flags & JATAM_C4_HASH) ? 1 : 0;
     a.n = cfg->n; a.c = cfg->c; a.L = cfg->L; a.k = cfg->k;
     a.key0 = (uint32_t)cfg->seed;
@@ -557,6 +567,7 @@ int jatam_classify_batch(const jatam_config *cfg, const uint8_t *colours, const 
     LaunchArgs a{};
     a.mode = MODE_RECORDS;
     a.count = N;
+    a.lifo = (cfg->flags & JATAM_LIFO) ? 1 : 0;
     a.c4 = (cfg->flags & JATAM_C4_HASH) ? 1 : 0;
     a.n = cfg->n; a.c = cfg->c; a.L = cfg->L; a.k = cfg->k;
     a.key0 = (uint32_t)cfg->seed;
@@ -614,6 +625,7 @@ int ga_evaluate(const jatam_config *cfg, const uint64_t *genomes, uint64_t N, in
     LaunchArgs a{};
     a.mode = MODE_GENOMES;
     a.count = N;
+    a.lifo = (cfg->flags & JATAM_LIFO) ? 1 : 0;
     a.c4 = (cfg->flags & JATAM_C4_HASH) ? 1 : 0;
     a.genomes = static_cast<const unsigned long long *>(gdev);
     a.n = cfg->n; a.c = cfg->c; a.L = cfg->L; a.k = cfg->k;
@@ -1413,6 +1425,7 @@ void jatam_shutdown(void)
         if (w->stage_hist) cudaFree(w->stage_hist);
         if (w->ga_buf) cudaFree(w->ga_buf);
         if (w->screen_buf) cudaFree(w->screen_buf);
+        if (w->lifo_buf) cudaFree(w->lifo_buf);
         cudaEventDestroy(w->last);
         cudaEventDestroy(w->k_start);
         cudaEventDestroy(w->k_stop);

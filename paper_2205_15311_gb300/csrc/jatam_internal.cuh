@@ -61,6 +61,9 @@ struct LaunchArgs {
     int use_hist;
     int c4;                       // 1: the rotation-only hash variant instead of the canonical form
     int orbits;                   // 1: orbit mode (one classification per orbit of the exact symmetries)
+    int lifo;                     // 1: the movelist process (the host sets lifo_stack)
+    uint16_t *lifo_stack;         // movelist process: S * S cells of stack per thread of the growth launch; null:
+                                  // the row-major process
     int stop_at;                    // finished lanes that end a growth round (1..32)
     unsigned long long *list;        // items left to grow, written by the pre-filter: 1 or 3 lists
     unsigned long long list_stride;  // capacity of one list (the call's item count)
@@ -77,8 +80,8 @@ struct LaunchArgs {
 // Lattice template: rows of S bits, S in {8, 16, 32}, L <= S; nt = 8 tuple ids
 // (sets of at most two tiles, uniform launches only) or 16.
 int classify_smem_bytes(int S, int nt, int warps_per_cta);
-cudaError_t classify_set_attributes(int S, int nt, int warps_per_cta);
-cudaError_t classify_occupancy(int S, int nt, int warps_per_cta, int *blocks_per_sm);
+cudaError_t classify_set_attributes(int S, int nt, int warps_per_cta, bool lifo = false);
+cudaError_t classify_occupancy(int S, int nt, int warps_per_cta, int *blocks_per_sm, bool lifo = false);
 cudaError_t launch_classify(const LaunchArgs &a, int S, int nt, int blocks, int warps_per_cta, cudaStream_t st);
 // largest CTA of classify_kernel (its launch bounds hold it to 113 registers so
 // that three such CTAs fit an SM)

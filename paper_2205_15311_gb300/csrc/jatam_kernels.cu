@@ -121,6 +121,7 @@ struct Lane {
     int n, c, L, k;
     int rep, step, size, size0, nF;
     unsigned long long fc;       // lattices with at most 8 frontier words: byte w = sites in word w
+    int sp;                      // movelist process: sites on this lane's stack
     int ymin, ymax, xmin, xmax;  // bounding box of the current replicate
     int x0, x1, y0, y1;          // bounding box of replicate 0
     int dlo, dhi;                // rows that may be dirty in any bitmap
@@ -443,9 +444,27 @@ __device__ __forceinline__ void replicate_end(Lane &Ls, uint32_t *my, bool nd, b
 // one growth step of one lane: seed placement or one drawn placement, then the
 // evaluation of the new tile's empty neighbours and the replicate rule
 // ---------------------------------------------------------------------------
-template <int S>
-__device__ __forceinline__ void lane_step(Lane &Ls, uint32_t *my, uint32_t k0, uint32_t k1, unsigned *err)
+// the Philox word of draw index s: the fetch-ahead has put its block in pa or pb
+__device__ __forceinline__ bool current_word(Lane &Ls, uint32_t s, uint32_t &u)
 {
+    const uint32_t key = (uint32_t)Ls.rep * 512u + (s >> 2);
+    if (Ls.ka != key) {
+        if (Ls.kb != key) return false;
+        Ls.pa = Ls.pb;
+        Ls.kb = NO_BLOCK;
+        Ls.ka = key;
+    }
+    const int sel = s & 3;
+    u = sel == 0 ? Ls.pa.x : sel == 1 ? Ls.pa.y : sel == 2 ? Ls.pa.z : Ls.pa.w;
+    return true;
+}
+
+// LIFO: the movelist process; stk: this lane's stack (S * S cells, global memory)
+template <int S, bool LIFO>
+__device__ __forceinline__ void lane_step(Lane &Ls, uint32_t *my, uint32_t k0, uint32_t k1, unsigned *err,
+                                          uint16_t *stk)
+{
+    constexpr bool lifo = LIFO;
     // Called by all 32 lanes; lanes that are not growing do the arithmetic on
     // harmless addresses of their own region and write nothing.  __syncwarp()
     // brings the warp back together after each data-dependent part.
@@ -455,7 +474,22 @@ __device__ __forceinline__ void lane_step(Lane &Ls, uint32_t *my, uint32_t k0, u
     const int occ = (Ls.rep == 0) ? G::OCCA : G::OCCB;
     int b = 0, tau = 0;
     bool placing = active;
-    if (active && !seed) {
+    if (LIFO && active && !seed) {
+        // the movelist process: the site on top of the stack
+        if (Ls.sp < 1 || Ls.sp > S * S) {
+            atomicOr(err, ERR_GUARD);  // unreachable: the stack holds the frontier, which is not empty here
+            Ls.cls = 255;
+            Ls.phase = PH_WRITE;
+            placing = false;
+        } else {
+            Ls.sp -= 1;
+            b = stk[Ls.sp];
+            tau = nib_get<S>(my, b);
+            my[(G::FRONT + (b >> 5)) * 32] &= ~(1u << (b & 31));
+            Ls.nF -= 1;
+            Ls.step += 1;
+        }
+    } else if (active && !seed) {
         // the growth loop's batched fetch-ahead has computed this block (in pa,
         // or in pb when it was fetched as the next replicate's first block)
         const uint32_t key = (uint32_t)Ls.rep * 512u + ((uint32_t)Ls.step >> 2);
@@ -522,6 +556,7 @@ __device__ __forceinline__ void lane_step(Lane &Ls, uint32_t *my, uint32_t k0, u
         Ls.step = 0;
         Ls.nF = 0;
         Ls.fc = 0ull;
+        Ls.sp = 0;
         Ls.diverged = 0;
         Ls.forced = 1;
         Ls.cert = 1;
@@ -553,6 +588,8 @@ __device__ __forceinline__ void lane_step(Lane &Ls, uint32_t *my, uint32_t k0, u
     const uint32_t m23 = my[(G::NBM + 2 * tau + 1) * 32];
     const int seed_cell = (Ls.L >> 1) * S + (Ls.L >> 1);
     bool nd = false, unb = false;
+    unsigned long long newq = 0;  // movelist: the new frontier sites of this step, N, E, S, W, 16 bits each
+    int nnew = 0;
 #pragma unroll
     for (int d = 0; d < 4; ++d) {
         const uint32_t M = ((d == 0) ? m01 : (d == 1) ? (m01 >> 16) : (d == 2) ? m23 : (m23 >> 16)) & 0xFFFFu;
@@ -588,6 +625,34 @@ __device__ __forceinline__ void lane_step(Lane &Ls, uint32_t *my, uint32_t k0, u
             my[(G::FRONT + qw) * 32] = fw | qbit;
             if constexpr (G::NW <= 8) Ls.fc += 1ull << (8 * qw);
             Ls.nF += 1;
+            newq |= (unsigned long long)qb << (16 * nnew);
+            ++nnew;
+        }
+    }
+    if (LIFO && placing && !nd && !unb && nnew > 0) {
+        // push the new sites in the drawn order: permutation floor(u m! / 2^32)
+        // of the m sites in the factorial number system, the first pick first
+        uint32_t u = 0;
+        if (!current_word(Ls, (uint32_t)Ls.step, u)) {
+            atomicOr(err, ERR_GUARD);  // unreachable: the fetch-ahead supplies the block of this push
+            Ls.cls = 255;
+            Ls.phase = PH_WRITE;
+            placing = false;
+        } else {
+            if (nnew > 1) Ls.forced = 0;
+            const uint32_t fact = nnew == 4 ? 24u : nnew == 3 ? 6u : nnew == 2 ? 2u : 1u;
+            uint32_t idx = __umulhi(u, fact);
+            uint32_t pool = 0x3210u;  // the sites not yet pushed, nibble j = site index
+            for (int i = 0; i < nnew; ++i) {
+                const int left = nnew - 1 - i;
+                const uint32_t f = left == 3 ? 6u : left == 2 ? 2u : 1u;
+                const uint32_t sel = idx / f;
+                idx -= sel * f;
+                const int item = (int)((pool >> (4 * sel)) & 15u);
+                pool = (pool & ((1u << (4 * sel)) - 1u)) | ((pool >> (4 * sel + 4)) << (4 * sel));
+                if (Ls.sp < S * S) stk[Ls.sp++] = (uint16_t)((newq >> (16 * item)) & 0xFFFFu);
+                else atomicOr(err, ERR_GUARD);  // unreachable: at most S * S frontier sites
+            }
         }
     }
     __syncwarp();
@@ -914,7 +979,7 @@ __global__ void __launch_bounds__(256) prefilter_kernel(const LaunchArgs a, int 
 // lane takes items from the list through the shared counter `work_next` and
 // the warp runs them to their class in batched phases.  `warp_lanes` is the
 // warp's interleaved region of Geo<S, NT>::WORDS words per lane.
-template <int S, int NT>
+template <int S, int NT, bool LIFO>
 __device__ __forceinline__ void warp_loop(const LaunchArgs &a, uint32_t *warp_lanes, SmemHist &H,
                                           const unsigned long long *list, unsigned long long total,
                                           unsigned long long *work_next)
@@ -938,7 +1003,11 @@ __device__ __forceinline__ void warp_loop(const LaunchArgs &a, uint32_t *warp_la
     Ls.item = 0; Ls.sid = 0; Ls.cols = 0;
     Ls.rep = Ls.step = Ls.size = Ls.nF = 0;
     Ls.fc = 0ull;
+    Ls.sp = 0;
     Ls.x0 = Ls.x1 = Ls.y0 = Ls.y1 = 0;
+    // the movelist process: this lane's stack of S * S cells in the launch's scratch
+    uint16_t *stk = LIFO ? a.lifo_stack + ((size_t)blockIdx.x * blockDim.x + threadIdx.x) * (S * S) : nullptr;
+    constexpr bool lifo = LIFO;
     unsigned long long st_draw = 0, st_seed = 0, st_slots = 0, st_geno = 0;  // executed work (a.stats)
     Ls.ymin = Ls.ymax = Ls.xmin = Ls.xmax = 0;
     Ls.diverged = 0;
@@ -1038,7 +1107,10 @@ __device__ __forceinline__ void warp_loop(const LaunchArgs &a, uint32_t *warp_la
                 uint32_t want = NO_BLOCK;
                 bool now = false;
                 if (Ls.phase == PH_GROW) {
-                    const uint32_t key = (uint32_t)Ls.rep * 512u + ((uint32_t)Ls.step >> 2);
+                    // the draw of this step: the rank (row-major process) or the push
+                    // order after the pop (movelist process, one step later)
+                    const uint32_t s = (uint32_t)Ls.step + (lifo ? 1u : 0u);
+                    const uint32_t key = (uint32_t)Ls.rep * 512u + (s >> 2);
                     if (Ls.ka != key && Ls.kb != key) {
                         want = key;
                         now = true;
@@ -1046,8 +1118,12 @@ __device__ __forceinline__ void warp_loop(const LaunchArgs &a, uint32_t *warp_la
                         want = (uint32_t)(Ls.rep + 1) * 512u;
                     }
                 } else if (Ls.phase == PH_START) {
+                    // the movelist process draws the push order right after the seed
                     const uint32_t key = (uint32_t)Ls.rep * 512u;
-                    if (Ls.ka != key && Ls.kb != key) want = key;
+                    if (Ls.ka != key && Ls.kb != key) {
+                        want = key;
+                        now = lifo;
+                    }
                 }
                 if (__any_sync(FULL, now) && want != NO_BLOCK) {
                     const uint4 w = philox_block(want, Ls.sid, a.key0, a.key1);
@@ -1065,7 +1141,7 @@ __device__ __forceinline__ void warp_loop(const LaunchArgs &a, uint32_t *warp_la
                 st_seed += __popc(__ballot_sync(FULL, Ls.phase == PH_START));
                 st_slots += 32;
             }
-            lane_step<S>(Ls, my, a.key0, a.key1, a.err);
+            lane_step<S, LIFO>(Ls, my, a.key0, a.key1, a.err, stk);
             const unsigned busy = __ballot_sync(FULL, Ls.phase == PH_START || Ls.phase == PH_GROW);
             if (!busy) break;
             const unsigned fin = __ballot_sync(FULL, Ls.phase == PH_SHAPE || Ls.phase == PH_WRITE);
@@ -1149,7 +1225,7 @@ __device__ __forceinline__ void hist_end(SmemHist &H, const LaunchArgs &a)
 
 // One lattice template for every warp: the items of pre-filter list a.klass.
 // CTAs of at most MAX_CTA_WARPS warps, three of which fit an SM's registers.
-template <int S, int NT>
+template <int S, int NT, bool LIFO>
 __global__ void __launch_bounds__(MAX_CTA_WARPS * 32, 3) classify_kernel(const LaunchArgs a)
 {
     extern __shared__ uint32_t smem_lanes[];
@@ -1157,8 +1233,8 @@ __global__ void __launch_bounds__(MAX_CTA_WARPS * 32, 3) classify_kernel(const L
     hist_begin(H);
     const int warp = threadIdx.x >> 5;
     uint32_t *warp_lanes = smem_lanes + (size_t)warp * Geo<S, NT>::WORDS * 32;
-    warp_loop<S, NT>(a, warp_lanes, H, a.list + (size_t)a.klass * a.list_stride, a.list_count[a.klass],
-                     a.work_next + a.klass);
+    warp_loop<S, NT, LIFO>(a, warp_lanes, H, a.list + (size_t)a.klass * a.list_stride, a.list_count[a.klass],
+                           a.work_next + a.klass);
     hist_end(H, a);
 }
 
@@ -1179,14 +1255,14 @@ __global__ void __launch_bounds__(256) classify_mixed_kernel(const LaunchArgs a)
     if (warp < w32) {
         uint32_t *wl = smem_lanes + (size_t)warp * R32;
         for (int c = 2; c >= 0; --c)
-            warp_loop<32, 16>(a, wl, H, a.list + (size_t)c * a.list_stride, a.list_count[c], a.work_next + c);
+            warp_loop<32, 16, false>(a, wl, H, a.list + (size_t)c * a.list_stride, a.list_count[c], a.work_next + c);
     } else if (warp < w32 + w16) {
         uint32_t *wl = smem_lanes + (size_t)w32 * R32 + (size_t)(warp - w32) * R16;
         for (int c = 1; c >= 0; --c)
-            warp_loop<16, 16>(a, wl, H, a.list + (size_t)c * a.list_stride, a.list_count[c], a.work_next + c);
+            warp_loop<16, 16, false>(a, wl, H, a.list + (size_t)c * a.list_stride, a.list_count[c], a.work_next + c);
     } else {
         uint32_t *wl = smem_lanes + (size_t)w32 * R32 + (size_t)w16 * R16 + (size_t)(warp - w32 - w16) * R8;
-        warp_loop<8, 16>(a, wl, H, a.list, a.list_count[0], a.work_next);
+        warp_loop<8, 16, false>(a, wl, H, a.list, a.list_count[0], a.work_next);
     }
     hist_end(H, a);
 }
@@ -1307,21 +1383,28 @@ __global__ void philox_kernel(const uint32_t *in, unsigned long long n, uint32_t
 template <int S, int NT>
 int smem_bytes_for(int warps) { return warps * Geo<S, NT>::WORDS * 32 * 4; }
 
-// the instance for lattice template S and tuple-table size nt
+// the instance for lattice template S, tuple-table size nt and process
+template <int S, int NT, typename F>
+auto with_process(bool lifo, F f)
+{
+    if (lifo) return f(classify_kernel<S, NT, true>, smem_bytes_for<S, NT>);
+    return f(classify_kernel<S, NT, false>, smem_bytes_for<S, NT>);
+}
+
 template <typename F>
-auto with_instance(int S, int nt, F f)
+auto with_instance(int S, int nt, bool lifo, F f)
 {
     if (nt == 8) {
         switch (S) {
-        case 8: return f(classify_kernel<8, 8>, smem_bytes_for<8, 8>);
-        case 16: return f(classify_kernel<16, 8>, smem_bytes_for<16, 8>);
-        default: return f(classify_kernel<32, 8>, smem_bytes_for<32, 8>);
+        case 8: return with_process<8, 8>(lifo, f);
+        case 16: return with_process<16, 8>(lifo, f);
+        default: return with_process<32, 8>(lifo, f);
         }
     }
     switch (S) {
-    case 8: return f(classify_kernel<8, 16>, smem_bytes_for<8, 16>);
-    case 16: return f(classify_kernel<16, 16>, smem_bytes_for<16, 16>);
-    default: return f(classify_kernel<32, 16>, smem_bytes_for<32, 16>);
+    case 8: return with_process<8, 16>(lifo, f);
+    case 16: return with_process<16, 16>(lifo, f);
+    default: return with_process<32, 16>(lifo, f);
     }
 }
 
@@ -1329,33 +1412,33 @@ auto with_instance(int S, int nt, F f)
 
 int classify_smem_bytes(int S, int nt, int warps_per_cta)
 {
-    return with_instance(S, nt, [&](auto, auto bytes_for) { return bytes_for(warps_per_cta); });
+    return with_instance(S, nt, false, [&](auto, auto bytes_for) { return bytes_for(warps_per_cta); });
 }
 
-cudaError_t classify_set_attributes(int S, int nt, int warps_per_cta)
+cudaError_t classify_set_attributes(int S, int nt, int warps_per_cta, bool lifo)
 {
     // The kernel's dynamic shared-memory limit is per device and shared by every
     // caller of the library, so it only ever grows: a caller that needs less
     // never lowers it under a launch that needs more.
     static std::mutex mu;
-    static std::map<std::tuple<int, int, int>, int> limit;  // (device, S, nt) -> bytes set
+    static std::map<std::tuple<int, int, int, int>, int> limit;  // (device, S, nt, process) -> bytes set
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
     const int bytes = classify_smem_bytes(S, nt, warps_per_cta);
     std::lock_guard<std::mutex> lock(mu);
-    int &have = limit[std::make_tuple(dev, S, nt)];
+    int &have = limit[std::make_tuple(dev, S, nt, lifo ? 1 : 0)];
     if (bytes <= have) return cudaSuccess;
-    e = with_instance(S, nt, [&](auto kernel, auto) {
+    e = with_instance(S, nt, lifo, [&](auto kernel, auto) {
         return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
     });
     if (e == cudaSuccess) have = bytes;
     return e;
 }
 
-cudaError_t classify_occupancy(int S, int nt, int warps_per_cta, int *blocks_per_sm)
+cudaError_t classify_occupancy(int S, int nt, int warps_per_cta, int *blocks_per_sm, bool lifo)
 {
-    return with_instance(S, nt, [&](auto kernel, auto bytes_for) {
+    return with_instance(S, nt, lifo, [&](auto kernel, auto bytes_for) {
         return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, kernel, warps_per_cta * 32,
                                                              bytes_for(warps_per_cta));
     });
@@ -1370,12 +1453,12 @@ int default_warps_per_cta(int S, int nt)
     int best = 1, best_warps = 0;
     for (int w = MAX_CTA_WARPS; w >= 1; --w) {
         if (classify_smem_bytes(S, nt, w) > 200 * 1024) continue;
-        if (classify_set_attributes(S, nt, w) != cudaSuccess) {  // the occupancy query needs the limit
+        if (classify_set_attributes(S, nt, w, false) != cudaSuccess) {  // the occupancy query needs the limit
             cudaGetLastError();
             continue;
         }
         int per_sm = 0;
-        if (classify_occupancy(S, nt, w, &per_sm) != cudaSuccess) {
+        if (classify_occupancy(S, nt, w, &per_sm, false) != cudaSuccess) {
             cudaGetLastError();
             continue;
         }
@@ -1390,7 +1473,7 @@ int default_warps_per_cta(int S, int nt)
 
 cudaError_t launch_classify(const LaunchArgs &a, int S, int nt, int blocks, int warps_per_cta, cudaStream_t st)
 {
-    return with_instance(S, nt, [&](auto kernel, auto bytes_for) {
+    return with_instance(S, nt, a.lifo_stack != nullptr, [&](auto kernel, auto bytes_for) {
         kernel<<<dim3(blocks), dim3(warps_per_cta * 32), bytes_for(warps_per_cta), st>>>(a);
         return cudaGetLastError();
     });

@@ -93,7 +93,8 @@ extern "C" int jatam_enumerate_noalloc(const jatam_config *cfg, uint64_t first, 
         return noalloc_fail(JATAM_EINVAL, "count exceeds JATAM_NOALLOC_MAX_COUNT (the fixed scratch holds "
                                           "1,048,576 genotypes per call)");
     const bool sampled = (cfg->flags & JATAM_SAMPLED) != 0;
-    if (cfg->flags & JATAM_ORBITS) return noalloc_fail(JATAM_EINVAL, "JATAM_ORBITS needs jatam_enumerate");
+    if (cfg->flags & (JATAM_ORBITS | JATAM_LIFO))
+        return noalloc_fail(JATAM_EINVAL, "JATAM_ORBITS and JATAM_LIFO need jatam_enumerate");
     const int bits = 4 * n * colour_bits(c);
     if (!sampled) {
         const uint64_t space = bits >= 64 ? ~0ull : (1ull << bits);

@@ -156,3 +156,24 @@ def test_screened_ga_reaches_the_best_shape_with_fewer_simulations():
     print("best after 5 generations: plain", best_plain, "screened", best_screened)
     assert reach_screened >= reach_plain + 3
     assert np.mean(best_screened) > np.mean(best_plain) + 2
+
+
+def test_host_histogram_staging_keeps_the_ga_buffers():
+    """Staging a larger host histogram between two GA runs leaves the GA's own
+    device buffers alone: the second run repeats the first exactly."""
+    thr = J.poisson_thresholds(0.05)
+    ga = J.make_ga(3, 8, 9, selection=J.TOURNAMENT, tournament=4, crossover=J.ONE_POINT,
+                   crossover_threshold=0x80000000, mutation_thresholds=thr)
+    pop0 = W.random_genomes(1024, 3, 8, seed=3)
+    bests = []
+    for i in range(2):
+        pop = torch.from_numpy(pop0.view(np.int64).copy()).cuda()
+        best = np.zeros(3, np.int32)
+        J.run_ga(ga, pop, 3, fitness_kind=J.FITNESS_SHAPE, L=16, k=8, seed=2, best=best)
+        bests.append((best.copy(), pop.cpu().numpy().copy()))
+        # a host histogram with a capacity the workspace has not staged before
+        out = torch.empty(4096 * 8, dtype=torch.uint8, device="cuda")
+        hist = np.zeros(1 << (17 + i), J.HIST_DTYPE)
+        hlen = np.zeros(1, np.uint32)
+        J.enumerate_space(2, 8, 16, 20, 2, 0, 4096, out=out, hist=hist, hist_len=hlen, hist_cap=hist.shape[0])
+    assert np.array_equal(bests[0][0], bests[1][0]) and np.array_equal(bests[0][1], bests[1][1])

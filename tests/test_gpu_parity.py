@@ -439,3 +439,37 @@ def test_orbit_mode_rejects_ranges_not_starting_at_zero():
     with pytest.raises(J.JatamError) as e:
         J.enumerate_space(2, 8, 16, 20, 2, 5, 16, out=out, sync=True, orbits=True)
     assert e.value.code == J.JATAM_EINVAL
+
+
+@pytest.mark.parametrize("case", ["s24_full", "s28_slice", "s38_sample_L32"])
+def test_movelist_process_matches_oracle(case):
+    """JATAM_LIFO: the movelist process of Section 2.4 (stack of frontier sites,
+    new sites pushed in a drawn order, the top one placed) equals the oracle's
+    movelist process, results and histogram."""
+    if case == "s24_full":
+        n, c, L, k, seed, first, count, _ = W.WORKLOADS["s24_full"]
+        sampled = False
+    elif case == "s28_slice":
+        n, c, L, k, seed, sampled = 2, 8, 16, 20, 2, False
+        first, count = 7 * (1 << 20) + 11, 30000
+    else:
+        n, c, L, k, seed, _, _, _ = W.WORKLOADS["s38_sample"]
+        first, count, sampled = 4242, 20000, True
+    out = torch.full((count * 8,), 0xEE, dtype=torch.uint8, device="cuda")
+    hist = torch.empty((1 << 16) * 32, dtype=torch.uint8, device="cuda")
+    hlen = torch.zeros(1, dtype=torch.int32, device="cuda")
+    J.enumerate_space(n, c, L, k, seed, first, count, sampled=sampled, out=out, hist=hist, hist_len=hlen,
+                      hist_cap=1 << 16, sync=True, lifo=True)
+    res = J.results_view(out)[:count]
+    with O.process_mode(True):
+        ref, _ = O.enumerate_space(n, c, L, k, seed, first, count, sampled=sampled)
+    assert np.array_equal(res, ref)
+    if sampled:
+        ids = np.array([O.sample_genotype(first + i, n, c, seed) for i in range(count)], np.uint64)
+    else:
+        ids = np.arange(first, first + count, dtype=np.uint64)
+    m = int(hlen.item())
+    assert _hist_rows(J.hist_view(hist, m)) == _hist_rows(_oracle_hist(ref, ids))
+    # a different process: some results differ from the row-major one
+    plain, _ = O.enumerate_space(n, c, L, k, seed, first, count, sampled=sampled)
+    assert not np.array_equal(plain, ref)
