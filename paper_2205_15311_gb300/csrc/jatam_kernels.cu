@@ -565,8 +565,15 @@ __device__ __forceinline__ void lane_step(Lane &Ls, uint32_t *my, uint32_t k0, u
     __syncwarp();
     const int px = b & (S - 1), py = b >> G::LOG2S;
 
+    // the placed cell's occupancy and frontier words: the east and west
+    // neighbours of an in-grid cell always lie in the same words (a row never
+    // straddles two), so their sides below read their own bits from these
+    // instead of loading again (bits of other cells may be stale: no store
+    // below is built from them)
+    const uint32_t ow_b = my[(occ + (b >> 5)) * 32];
+    const uint32_t fw_b = my[(G::FRONT + (b >> 5)) * 32];
     if (placing) {
-        my[(occ + (b >> 5)) * 32] |= 1u << (b & 31);
+        my[(occ + (b >> 5)) * 32] = ow_b | (1u << (b & 31));
         if (seed && Ls.rep == 0) nib_set<S>(my, b, 0);
         Ls.size += 1;
         Ls.ymin = seed ? py : min(Ls.ymin, py);
@@ -600,8 +607,9 @@ __device__ __forceinline__ void lane_step(Lane &Ls, uint32_t *my, uint32_t k0, u
         const int qw = qb >> 5;
         const uint32_t qbit = 1u << (qb & 31);
         const int sh = (qb & 7) * 4;
-        const uint32_t ow = my[(occ + qw) * 32];
-        const uint32_t fw = my[(G::FRONT + qw) * 32];
+        const bool row = d == 1 || d == 3;  // east or west: the placed cell's words
+        const uint32_t ow = row ? ow_b : my[(occ + qw) * 32];
+        const uint32_t fw = row ? fw_b : my[(G::FRONT + qw) * 32];
         const uint32_t nw = my[(G::NIB + (qb >> 3)) * 32];
         const int tq = (nw >> sh) & 15;
         const bool empty = in && !(ow & qbit);
@@ -622,7 +630,8 @@ __device__ __forceinline__ void lane_step(Lane &Ls, uint32_t *my, uint32_t k0, u
             // no longer end in replicate 0's configuration
             if (Ls.rep > 0 && !Ls.diverged && (!(my[(G::OCCA + qw) * 32] & qbit) || tq != tn)) Ls.diverged = 1;
             my[(G::NIB + (qb >> 3)) * 32] = (nw & ~(15u << sh)) | ((uint32_t)tn << sh);
-            my[(G::FRONT + qw) * 32] = fw | qbit;
+            // a fresh read: an earlier side of this step may have set a bit of the same word
+            my[(G::FRONT + qw) * 32] |= qbit;
             if constexpr (G::NW <= 8) Ls.fc += 1ull << (8 * qw);
             Ls.nF += 1;
             newq |= (unsigned long long)qb << (16 * nnew);
