@@ -152,74 +152,103 @@ __device__ __forceinline__ void clear_rows(uint32_t *my, int base, int lo, int h
 }
 
 // ---------------------------------------------------------------------------
-// warp-cooperative binding tables: each group of GL lanes (GL = 8 for at most
-// two tiles, 16 for up to four) builds the tables of one new genotype, so one
-// pass serves 32 / GL genotypes.  Lane l of a group handles (tile, rotation)
-// = (l / 4, l % 4).  The owners served are removed from `pending`.
+// binding tables of one lane's new genotype, built by the lane alone (all new
+// lanes of a warp at once).  Tuple l = 4 t + r is tile t turned clockwise by r
+// quarter turns: side d carries the colour of edge (d - r) mod 4.  l is the
+// representative of its rotated tuple -- the lowest (tile, rotation) index with
+// that tuple -- unless a lower rotation of the same tile gives the same tuple
+// (r = 1: the tile is symmetric under a quarter turn; r = 2, 3: under a half
+// turn, which a quarter-turn symmetry implies) or an earlier tile is a rotation
+// of this one.  NBM[2 l + d / 2] >> 16 (d & 1) is the set of representatives
+// whose side d + 2 carries the partner of l's colour on side d (Section 2.2:
+// 1-2, 3-4, 5-6 bind; 0 and an odd top colour bind nothing).
 // ---------------------------------------------------------------------------
-template <int S, int GL>
-__device__ __forceinline__ void coop_tables(unsigned &pending, uint32_t *warp_lanes, const Lane &Ls, int lane)
+__device__ __forceinline__ uint32_t rot16(uint32_t x, int k)
+{
+    return ((x << k) | (x >> (16 - k))) & 0xFFFFu;
+}
+
+// Bit planes over (tile, rotation): bit 4 t + r of plane(e, b) is bit b of the
+// colour that tuple 4 t + r shows on side e, i.e. of edge (e - r) mod 4 of
+// tile t.  x holds bit b of every edge of two tiles (bit 4 j + 16 u: edge j of
+// tile u); one multiply moves edge (e - r) mod 4 of each tile to bit r of a
+// nibble (at K_e and K_e + 16).  The constants put every partial product on
+// its own bit, so no sum carries and no other product lands in the nibbles:
+//   e = 0: edges 0,3,2,1 -> x * (2^11 + 2^10 + 2^5 + 1) >> 11
+//   e = 1: edges 1,0,3,2 -> x * (2^11 + 2^6 + 2^5 + 1)  >> 10
+//   e = 2: edges 2,1,0,3 -> x * (2^11 + 2^6 + 2 + 1)    >> 9
+//   e = 3: edges 3,2,1,0 -> x * (2^15 + 2^10 + 2^5 + 1) >> 12
+template <int E>
+__device__ __forceinline__ uint32_t plane_byte(uint32_t x)
+{
+    constexpr uint32_t MUL = E == 0 ? 0xC21u : E == 1 ? 0x861u : E == 2 ? 0x843u : 0x8421u;
+    constexpr int K = E == 0 ? 11 : E == 1 ? 10 : E == 2 ? 9 : 12;
+    const uint32_t z = ((x * MUL) >> K) & 0x000F000Fu;
+    return (z | (z >> 12)) & 0xFFu;
+}
+
+template <int S, int NT>
+__device__ __forceinline__ void lane_tables(uint32_t *my, unsigned long long cols, int n, int c)
 {
     using G = Geo<S>;
-    constexpr int NG = 32 / GL;
-    const int g = lane / GL, l = lane % GL;
-    const int o = (g < __popc(pending)) ? nth_set(pending, (uint32_t)g) : -1;
+    constexpr int NTILE = NT / 4;
+    const uint32_t lo = (uint32_t)cols, hi = (uint32_t)(cols >> 32);
+    uint32_t tl[NTILE];
 #pragma unroll
-    for (int q = 0; q < NG; ++q) pending &= pending - 1;
-    const int src = (o < 0) ? lane : o;
-    const uint32_t clo = __shfl_sync(FULL, (uint32_t)Ls.cols, src);
-    const uint32_t chi = __shfl_sync(FULL, (uint32_t)(Ls.cols >> 32), src);
-    const int n = __shfl_sync(FULL, Ls.n, src);
-    const int c = __shfl_sync(FULL, Ls.c, src);
-    const int t = l >> 2, r = l & 3;
-    const bool valid = o >= 0 && t < n;
-    // tile t as 16 bits (nibble e = colour of edge e); a clockwise turn by r
-    // moves the colour of edge (d - r) mod 4 to side d: a 4r-bit rotation
-    const uint32_t tile = ((t < 2 ? clo : chi) >> (16 * (t & 1))) & 0xFFFFu;
-    const uint32_t rot = ((tile << (4 * r)) | (tile >> ((16 - 4 * r) & 15))) & 0xFFFFu;
-    const uint32_t rotv = (r == 0) ? tile : rot;
-    // (t, r) is the representative of its rotated tuple -- the lowest (tile,
-    // rotation) index with that tuple -- unless a lower rotation of the same
-    // tile gives the same tuple (r = 1: the tile is symmetric under a quarter
-    // turn; r = 2, 3: under a half turn, which a quarter-turn symmetry implies)
-    // or an earlier tile is a rotation of this one.  Decided from the colours
-    // alone, without comparing lanes.
-    const uint32_t q1 = ((tile << 4) | (tile >> 12)) & 0xFFFFu, q2 = ((tile << 8) | (tile >> 8)) & 0xFFFFu;
-    bool is_rep = valid && (r == 0 || (r == 1 ? q1 != tile : q2 != tile));
-    for (int u = 0; u < t; ++u) {
-        const uint32_t tu = ((u < 2 ? clo : chi) >> (16 * (u & 1))) & 0xFFFFu;
-        const uint32_t u1 = ((tu << 4) | (tu >> 12)) & 0xFFFFu, u2 = ((tu << 8) | (tu >> 8)) & 0xFFFFu;
-        const uint32_t u3 = ((tu << 12) | (tu >> 4)) & 0xFFFFu;
-        if (tile == tu || tile == u1 || tile == u2 || tile == u3) is_rep = false;
-    }
-    const int shift = g * GL;
-    const uint32_t gmask = (GL == 32) ? FULL : ((1u << GL) - 1u);
-    const uint32_t reps = (__ballot_sync(FULL, is_rep) >> shift) & gmask;
-    // bit-sliced colour planes: sl[e][b] = reps whose side e has bit b set
-    uint32_t sl[4][3];
+    for (int t = 0; t < NTILE; ++t) tl[t] = ((t < 2 ? lo : hi) >> (16 * (t & 1))) & 0xFFFFu;
+    uint32_t reps = 0;
 #pragma unroll
-    for (int e = 0; e < 4; ++e)
+    for (int t = 0; t < NTILE; ++t) {
+        const uint32_t tile = tl[t];
+        uint32_t m = 1u | (rot16(tile, 4) != tile ? 2u : 0u) | (rot16(tile, 8) != tile ? 12u : 0u);
 #pragma unroll
-        for (int b = 0; b < 3; ++b)
-            sl[e][b] = (__ballot_sync(FULL, is_rep && ((rotv >> (4 * e + b)) & 1)) >> shift) & gmask;
-    if (is_rep) {
-        uint32_t M[4];
-#pragma unroll
-        for (int d = 0; d < 4; ++d) {
-            const int a = (rotv >> (4 * d)) & 15;
-            // the interaction matrix pairs 1-2, 3-4, 5-6; 0 and an odd top colour have no partner
-            const int pa = (a == 0) ? -1 : (a & 1) ? ((a + 1 < c) ? a + 1 : -1) : a - 1;
-            uint32_t m = 0;
-            if (pa >= 0) {
-                m = reps;
-#pragma unroll
-                for (int b = 0; b < 3; ++b) m &= ((pa >> b) & 1) ? sl[(d + 2) & 3][b] : ~sl[(d + 2) & 3][b];
-            }
-            M[d] = m & 0xFFFFu;
+        for (int u = 0; u < t; ++u) {
+            const uint32_t tu = tl[u];
+            if (tile == tu || tile == rot16(tu, 4) || tile == rot16(tu, 8) || tile == rot16(tu, 12)) m = 0u;
         }
-        uint32_t *ob = warp_lanes + o;
-        ob[(G::NBM + 2 * l) * 32] = M[0] | (M[1] << 16);
-        ob[(G::NBM + 2 * l + 1) * 32] = M[2] | (M[3] << 16);
+        if (t < n) reps |= m << (4 * t);
+    }
+    uint32_t P[4][3];
+#pragma unroll
+    for (int b = 0; b < 3; ++b) {
+        const uint32_t xl = (lo >> b) & 0x11111111u;
+        P[0][b] = plane_byte<0>(xl);
+        P[1][b] = plane_byte<1>(xl);
+        P[2][b] = plane_byte<2>(xl);
+        P[3][b] = plane_byte<3>(xl);
+        if constexpr (NTILE > 2) {
+            const uint32_t xh = (hi >> b) & 0x11111111u;
+            P[0][b] |= plane_byte<0>(xh) << 8;
+            P[1][b] |= plane_byte<1>(xh) << 8;
+            P[2][b] |= plane_byte<2>(xh) << 8;
+            P[3][b] |= plane_byte<3>(xh) << 8;
+        }
+    }
+#pragma unroll
+    for (int t = 0; t < NTILE; ++t) {
+        if (t >= n) break;
+        uint32_t w[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) w[j] = 0u;
+#pragma unroll
+        for (int s = 0; s < 4; ++s) {
+            const int a = (int)((tl[t] >> (4 * s)) & 15u);
+            const int pa = (a == 0) ? -1 : (a & 1) ? ((a + 1 < c) ? a + 1 : -1) : a - 1;
+            const uint32_t rz = pa >= 0 ? reps : 0u;
+            const uint32_t n0 = 0u - (uint32_t)(pa & 1), n1 = 0u - (uint32_t)((pa >> 1) & 1),
+                           n2 = 0u - (uint32_t)((pa >> 2) & 1);
+            uint32_t X[4];
+#pragma unroll
+            for (int e = 0; e < 4; ++e) X[e] = rz & ~(P[e][0] ^ n0) & ~(P[e][1] ^ n1) & ~(P[e][2] ^ n2);
+            // edge s of tile t is side d = s + r of tuple 4 t + r; it binds side d + 2
+#pragma unroll
+            for (int r = 0; r < 4; ++r) {
+                const int d = (s + r) & 3;
+                w[2 * r + (d >> 1)] |= X[(d + 2) & 3] << (16 * (d & 1));
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < 8; ++j) my[(G::NBM + 8 * t + j) * 32] = w[j];
     }
 }
 
@@ -1076,15 +1105,9 @@ __device__ __forceinline__ void warp_loop(const LaunchArgs &a, uint32_t *warp_la
             }
             break;  // every listed item grows: one round hands out work to all idle lanes
         }
-        // ---- binding tables of the genotypes that grow, one warp-wide job each
-        unsigned init = __ballot_sync(FULL, Ls.phase == PH_INIT);
-        if (NT == 8 || (a.n <= 2 && !(a.mode == MODE_RECORDS && a.shapes))) {
-            while (init) coop_tables<S, 8>(init, warp_lanes, Ls, lane);
-        } else if constexpr (NT == 16) {
-            while (init) coop_tables<S, 16>(init, warp_lanes, Ls, lane);
-        }
-        __syncwarp();
+        // ---- binding tables of the genotypes that grow: every new lane builds its own
         if (Ls.phase == PH_INIT) {
+            lane_tables<S, NT>(my, Ls.cols, Ls.n, Ls.c);
             // a new genotype: clear whatever the previous one left in the bitmaps
             if (Ls.dlo <= Ls.dhi) {
                 const int lo = max(Ls.dlo, 0), hi = min(Ls.dhi, S - 1);
