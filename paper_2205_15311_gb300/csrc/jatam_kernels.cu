@@ -1133,8 +1133,13 @@ __device__ __forceinline__ void warp_loop(const LaunchArgs &a, uint32_t *warp_la
         for (;;) {
             // Philox blocks are computed for all lanes at once: when some lane
             // lacks the block of its current draw, every lane that will need a
-            // block soon (its current one, or block 0 of its next replicate)
-            // computes it in the same pass
+            // block soon computes it in the same pass -- its current one, else
+            // the one it needs after that: the next block of this replicate
+            // while the replicate still draws past the current block (known
+            // from replicate 0's size for a later replicate that has not
+            // diverged from it; assumed in replicate 0), else block 0 of the
+            // next replicate.  Keys grow along a genotype's draws, so a held
+            // block below the current key is spent.
             {
                 uint32_t want = NO_BLOCK;
                 bool now = false;
@@ -1143,11 +1148,21 @@ __device__ __forceinline__ void warp_loop(const LaunchArgs &a, uint32_t *warp_la
                     // order after the pop (movelist process, one step later)
                     const uint32_t s = (uint32_t)Ls.step + (lifo ? 1u : 0u);
                     const uint32_t key = (uint32_t)Ls.rep * 512u + (s >> 2);
-                    if (Ls.ka != key && Ls.kb != key) {
+                    if (Ls.ka != key && Ls.kb == key) {
+                        Ls.pa = Ls.pb;
+                        Ls.ka = key;
+                        Ls.kb = NO_BLOCK;
+                    }
+                    if (Ls.ka != key) {
                         want = key;
                         now = true;
-                    } else if (Ls.kb == NO_BLOCK && Ls.rep + 1 < Ls.k) {
-                        want = (uint32_t)(Ls.rep + 1) * 512u;
+                    } else if (Ls.kb == NO_BLOCK || Ls.kb < key) {
+                        // the last draw of a replicate that ends in replicate 0's
+                        // configuration: size0 - 1 placements after the seed
+                        const int last = (Ls.size0 - 2 + (lifo ? 1 : 0)) >> 2;
+                        const bool more = Ls.rep == 0 || Ls.diverged || (int)(s >> 2) < last;
+                        if (more) want = key + 1u;
+                        else if (Ls.rep + 1 < Ls.k) want = (uint32_t)(Ls.rep + 1) * 512u;
                     }
                 } else if (Ls.phase == PH_START) {
                     // the movelist process draws the push order right after the seed
