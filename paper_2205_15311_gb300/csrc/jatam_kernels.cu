@@ -57,7 +57,7 @@ constexpr unsigned FULL = 0xffffffffu;
 constexpr int HIST_SLOTS = 256;  // per-CTA phenotype aggregation table
 constexpr int CHUNK = 32;        // items taken from the global counter at once
 
-enum Phase : int { PH_NEED = 0, PH_INIT, PH_START, PH_GROW, PH_SHAPE, PH_WRITE, PH_DONE };
+enum Phase : int { PH_NEED = 0, PH_INIT, PH_START, PH_GROW, PH_DOM, PH_SHAPE, PH_WRITE, PH_DONE };
 
 
 // Jenkins one-at-a-time, one byte at a time (Section 2.5).
@@ -409,6 +409,116 @@ __device__ __forceinline__ int seed_outcome(unsigned long long cols, int n, int 
 
 // The replicate just ended (local ambiguity, unbounded growth, or an empty
 // frontier): apply the first-deciding-replicate rule.
+// ---------------------------------------------------------------------------
+// Dominance certificate of a final replicate-0 configuration A0 that is not
+// closed (warp-wide job for lane o).  Attachment graph on the cells of A0:
+// u -> v (adjacent) when u offers v's tuple of A0 to v.  A bad offer is one
+// from u to an adjacent cell q of A0 (q not the seed's cell) that contains a
+// tuple other than q's own.  If for every bad offer u -> q every path of the
+// graph from the seed to u passes through q, all k replicates end in A0:
+// before any deviation from A0 each placed cell v was attached through a
+// neighbour u -> v placed earlier, so cells are placed in an order that
+// respects the graph, u is placed after q, and no empty cell ever sees a
+// tuple other than its own in A0 (cells outside A0 receive no offers: replicate
+// 0 ended with an empty frontier); every cell of A0 is reachable, so each
+// replicate fills A0 and stops.  Lane i holds row y0 + i of A0's bounding
+// box (bit j: column x0 + j); once per distinct q, the cells with a path to
+// q's bad offerers that avoids q are flood-filled against the edges, and the
+// test fails if the seed is among them.
+// ---------------------------------------------------------------------------
+template <int S, int NT>
+__device__ __forceinline__ bool coop_dominated(int o, const uint32_t *warp_lanes, const Lane &Ls, int lane)
+{
+    using G = Geo<S>;
+    const uint32_t *ob = warp_lanes + o;
+    const int x0 = __shfl_sync(FULL, Ls.x0, o), x1 = __shfl_sync(FULL, Ls.x1, o);
+    const int y0 = __shfl_sync(FULL, Ls.y0, o), y1 = __shfl_sync(FULL, Ls.y1, o);
+    const int Lo = __shfl_sync(FULL, Ls.L, o);
+    const int h = y1 - y0 + 1, w = x1 - x0 + 1;
+    const uint32_t wmask = (w >= 32) ? FULL : ((1u << w) - 1u);
+    // the owner's binding table, word j in lane j
+    const uint32_t nbm = (lane < 2 * NT) ? ob[(G::NBM + lane) * 32] : 0u;
+    uint32_t occ = 0;
+    if (lane < h) {
+        const int b = (y0 + lane) * S + x0;
+        occ = (ob[(G::OCCA + (b >> 5)) * 32] >> (b & 31)) & wmask;
+    }
+    uint32_t occN = __shfl_up_sync(FULL, occ, 1), occS = __shfl_down_sync(FULL, occ, 1);
+    if (lane == 0) occN = 0u;
+    if (lane == 31) occS = 0u;
+    const int sx = (Lo >> 1) - x0, sy = (Lo >> 1) - y0;
+    // tuple id of column j of this lane's row (0 outside the box)
+    auto tuple_at = [&](int j) -> int {
+        if (lane >= h || j >= w) return 0;
+        const int b = (y0 + lane) * S + x0 + j;
+        return (int)((ob[(G::NIB + (b >> 3)) * 32] >> ((b & 7) * 4)) & 15u);
+    };
+    uint32_t gN = 0, gE = 0, gS = 0, gW = 0;  // good edges: cell -> its neighbour on that side
+    uint32_t bN = 0, bE = 0, bS = 0, bW = 0;  // bad offers: cell -> its neighbour on that side
+    int tW = 0, tC = tuple_at(0);
+    for (int j = 0; j < w; ++j) {
+        const int tE = tuple_at(j + 1);
+        const int tN = __shfl_up_sync(FULL, tC, 1), tS = __shfl_down_sync(FULL, tC, 1);
+        const uint32_t m01 = __shfl_sync(FULL, nbm, (2 * tC) & 31);
+        const uint32_t m23 = __shfl_sync(FULL, nbm, (2 * tC + 1) & 31);
+        if ((occ >> j) & 1u) {
+            const uint32_t bit = 1u << j;
+            const uint32_t MN = m01 & 0xFFFFu, ME = m01 >> 16, MS = m23 & 0xFFFFu, MW = m23 >> 16;
+            if ((occN >> j) & 1u) {
+                if ((MN >> tN) & 1u) gN |= bit;
+                if ((MN & ~(1u << tN)) && !(lane - 1 == sy && j == sx)) bN |= bit;
+            }
+            if (j + 1 < w && ((occ >> (j + 1)) & 1u)) {
+                if ((ME >> tE) & 1u) gE |= bit;
+                if ((ME & ~(1u << tE)) && !(lane == sy && j + 1 == sx)) bE |= bit;
+            }
+            if ((occS >> j) & 1u) {
+                if ((MS >> tS) & 1u) gS |= bit;
+                if ((MS & ~(1u << tS)) && !(lane + 1 == sy && j == sx)) bS |= bit;
+            }
+            if (j > 0 && ((occ >> (j - 1)) & 1u)) {
+                if ((MW >> tW) & 1u) gW |= bit;
+                if ((MW & ~(1u << tW)) && !(lane == sy && j - 1 == sx)) bW |= bit;
+            }
+        }
+        tW = tC;
+        tC = tE;
+    }
+    // cells that receive a bad offer
+    const uint32_t fromAbove = __shfl_up_sync(FULL, bS, 1), fromBelow = __shfl_down_sync(FULL, bN, 1);
+    uint32_t qs = (bE << 1) | (bW >> 1) | (lane > 0 ? fromAbove : 0u) | (lane < 31 ? fromBelow : 0u);
+    qs &= occ;
+    const bool seed_row = lane == sy;
+    const uint32_t seed_bit = seed_row ? (1u << sx) : 0u;
+    for (;;) {
+        const unsigned hasq = __ballot_sync(FULL, qs != 0u);
+        if (!hasq) return true;
+        const int qy = __ffs(hasq) - 1;
+        const int qx = __ffs(__shfl_sync(FULL, qs, qy)) - 1;
+        if (lane == qy) qs &= ~(1u << qx);
+        const uint32_t keep = occ & ((lane == qy) ? ~(1u << qx) : FULL);
+        // the bad offerers of q: its north neighbour offering south, its south
+        // neighbour offering north, its east one offering west, its west one east
+        uint32_t X = 0u;
+        if (lane == qy - 1) X = bS & (1u << qx);
+        if (lane == qy + 1) X = bN & (1u << qx);
+        if (lane == qy) X = (bW & ((qx + 1 < 32) ? (2u << qx) : 0u)) | (bE & ((qx > 0) ? (1u << (qx - 1)) : 0u));
+        // every cell with a path to one of them that avoids q, one
+        // breadth-first layer at a time against the edges: the seed among them
+        // means an offerer can be placed before q
+        for (;;) {
+            if (__any_sync(FULL, (X & seed_bit) != 0u)) return false;
+            const uint32_t below = __shfl_down_sync(FULL, X, 1);  // row below: this row's cells attach south
+            const uint32_t above = __shfl_up_sync(FULL, X, 1);    // row above: this row's cells attach north
+            uint32_t nX = X | (gE & (X >> 1)) | (gW & (X << 1)) | (lane < 31 ? (gS & below) : 0u) |
+                          (lane > 0 ? (gN & above) : 0u);
+            nX &= keep;
+            if (!__any_sync(FULL, nX != X)) break;
+            X = nX;
+        }
+    }
+}
+
 template <int S>
 __device__ __forceinline__ void replicate_end(Lane &Ls, uint32_t *my, bool nd, bool unb)
 {
@@ -446,6 +556,12 @@ __device__ __forceinline__ void replicate_end(Lane &Ls, uint32_t *my, bool nd, b
             Ls.cls = JATAM_DET_BOUNDED;
             Ls.decided = Ls.k;
             Ls.phase = PH_SHAPE;
+            return;
+        }
+        if (Ls.k > 1) {
+            // A0 is not closed: the warp tests whether every offending offer
+            // comes too late in every order (coop_dominated)
+            Ls.phase = PH_DOM;
             return;
         }
     } else if (Ls.diverged || Ls.size != Ls.size0) {
@@ -1191,8 +1307,28 @@ __device__ __forceinline__ void warp_loop(const LaunchArgs &a, uint32_t *warp_la
             lane_step<S, LIFO>(Ls, my, a.key0, a.key1, a.err, stk);
             const unsigned busy = __ballot_sync(FULL, Ls.phase == PH_START || Ls.phase == PH_GROW);
             if (!busy) break;
-            const unsigned fin = __ballot_sync(FULL, Ls.phase == PH_SHAPE || Ls.phase == PH_WRITE);
+            const unsigned fin = __ballot_sync(FULL, Ls.phase == PH_DOM || Ls.phase == PH_SHAPE || Ls.phase == PH_WRITE);
             if (__popc(fin) >= a.stop_at) break;
+        }
+
+        // ---- dominance certificates of replicate-0 configurations that are not closed
+        unsigned dom = __ballot_sync(FULL, Ls.phase == PH_DOM);
+        while (dom) {
+            const int o = __ffs(dom) - 1;
+            dom &= dom - 1;
+            const bool ok = coop_dominated<S, NT>(o, warp_lanes, Ls, lane);
+            if (lane == o) {
+                if (ok) {
+                    Ls.cls = JATAM_DET_BOUNDED;
+                    Ls.decided = Ls.k;
+                    Ls.phase = PH_SHAPE;
+                } else {
+                    // replicate 1 (replicate 0 wrote nothing in OCCB)
+                    Ls.rep = 1;
+                    Ls.phase = PH_START;
+                }
+            }
+            __syncwarp();
         }
 
         // ---- canonical shapes of finished genotypes: a per-warp cache keyed by

@@ -150,6 +150,20 @@ def test_grid_sizes_including_ragged_ones(L):
     assert np.array_equal(res, ref)
 
 
+@pytest.mark.parametrize("k", [1, 2, 3])
+def test_few_replicates_match_oracle(k):
+    """k = 1 (replicate 0 alone decides) to 3: the shortcuts that end a genotype
+    after replicate 0 (forced path, closed or dominated final shape) and the
+    steric comparison of later replicates at their smallest counts."""
+    n, c, L, seed = 2, 8, 16, 9
+    first, count = 5 << 20, 200000
+    res, hist, m = _dev_enumerate(n, c, L, k, seed, first, count)
+    ref, _ = O.enumerate_space(n, c, L, k, seed, first, count)
+    assert np.array_equal(res, ref)
+    if k == 1:
+        assert not np.any(ref["cls"] == O.ND_STERIC)
+
+
 @pytest.mark.parametrize("count", [0, 1, 31, 32, 33, 1000])
 def test_ragged_counts(count):
     n, c, L, k, seed = 2, 8, 16, 20, 2
@@ -344,39 +358,15 @@ def test_graph_replay_equals_direct_launches():
         assert torch.equal(f1, f2)
 
 
-_DX, _DY = (0, 1, 0, -1), (-1, 0, 1, 0)
-
-
-def _closed(col, n, c, grid):
-    """The closure test of a final replicate-0 configuration, written out from
-    the binding rule: for every two adjacent tiles, the tuples the one offers
-    the other's cell are that cell's tuple or none (the seed's cell, occupied
-    first in every replicate, may be offered anything)."""
-    def bind(a, b):
-        return a != 0 and b != 0 and min(a, b) % 2 == 1 and max(a, b) == min(a, b) + 1 and max(a, b) < c
-    side = {4 * t + r: [col[4 * t + (d - r) % 4] for d in range(4)] for t in range(n) for r in range(4)}
-    rep = {a: min(b for b in range(a + 1) if side[b] == side[a]) for a in side}
-    L = grid.shape[0]
-    for y in range(L):
-        for x in range(L):
-            u = grid[y, x]
-            if u < 0:
-                continue
-            for d in range(4):
-                qx, qy = x + _DX[d], y + _DY[d]
-                if not (0 <= qx < L and 0 <= qy < L) or grid[qy, qx] < 0 or (qx, qy) == (L // 2, L // 2):
-                    continue
-                offered = {rep[a] for a in side if bind(side[a][(d + 2) % 4], side[u][d])}
-                if offered and offered != {grid[qy, qx]}:
-                    return False
-    return True
+from certificates import closed as _closed, dominated as _dominated  # noqa: E402
 
 
 def test_work_counters_count_the_executed_process():
     """jatam_profile(2) counts exactly the placements the kernel performs: every
     replicate of every genotype the pre-filter left, except that a DET genotype
-    whose replicate 0 was forced (a single frontier site at every draw) or
-    closed stops after replicate 0 (both fix the outcome of all replicates)."""
+    whose replicate 0 was forced (a single frontier site at every draw), closed
+    or dominated stops after replicate 0 (each fixes the outcome of all
+    replicates)."""
     n, c, L, k, seed = 2, 8, 16, 20, 2
     genomes = W.random_genomes(3000, n, c, seed=21)  # stream id = the genome itself
     want = {"placements": 0, "seeds": 0, "genotypes": 0}
@@ -390,7 +380,8 @@ def test_work_counters_count_the_executed_process():
         if at_seed or lone:
             continue
         want["genotypes"] += 1
-        if r["cls"] == 0 and (all(t[0] <= 1 for t in r["trace"]) or _closed(list(col), n, c, r["grid"])):
+        if r["cls"] == 0 and (all(t[0] <= 1 for t in r["trace"]) or _closed(list(col), n, c, r["grid"])
+                              or _dominated(list(col), n, c, r["grid"])):
             want["placements"] += r["size"] - 1
             want["seeds"] += 1
         else:
