@@ -77,6 +77,7 @@ int fail(int code, const char *fmt, ...)
     } while (0)
 
 constexpr unsigned TABLE_LOG2 = 18;  // 262,144 phenotype slots per device
+constexpr unsigned CROPS_LOG2 = 12;  // 4,096 slots of the per-call crop table (64 KB)
 
 struct Workspace {
     int device = -1;
@@ -84,6 +85,7 @@ struct Workspace {
     Table table{};
     Compact compact{};
     unsigned long long *work_next = nullptr;
+    unsigned long long *crops = nullptr;  // crop -> shape hash within one call (cleared by its reset)
     unsigned long long *stats = nullptr;  // [4] executed-work counters of the last counted call
     bool stats_valid = false;
     unsigned *err = nullptr;
@@ -161,6 +163,7 @@ int workspace(Workspace **out)
     CUDA_TRY(cudaMalloc(&w->compact.size_max, cap * 4));
     CUDA_TRY(cudaMalloc(&w->compact.size_min, cap * 4));
     CUDA_TRY(cudaMalloc(&w->work_next, 3 * 8));
+    CUDA_TRY(cudaMalloc(&w->crops, (size_t(2) << CROPS_LOG2) * 8));
     CUDA_TRY(cudaMalloc(&w->stats, 4 * 8));
     CUDA_TRY(cudaMalloc(&w->err, 4));
     CUDA_TRY(cudaMalloc(&w->nkeys, 4));
@@ -170,7 +173,7 @@ int workspace(Workspace **out)
     CUDA_TRY(cudaEventCreate(&w->k_start));
     CUDA_TRY(cudaEventCreate(&w->k_stop));
     CUDA_TRY(launch_table_init(w->table, nullptr));
-    CUDA_TRY(launch_reset(w->work_next, w->nkeys, w->list_count, nullptr));
+    CUDA_TRY(launch_reset(w->work_next, w->nkeys, w->list_count, nullptr, w->crops, CROPS_LOG2));
     CUDA_TRY(cudaMemsetAsync(w->err, 0, 4, nullptr));
     CUDA_TRY(cudaDeviceSynchronize());
     g_ws[dev] = w;
@@ -300,6 +303,8 @@ int run(Workspace *w, LaunchArgs a, int S, jatam_result *out, int32_t *fitness, 
     a.table = w->table;
     a.use_hist = hist ? 1 : 0;
     a.work_next = w->work_next;
+    a.crops = w->crops;
+    a.crops_log2 = CROPS_LOG2;
     a.stats = (g_profile & 2) ? w->stats : nullptr;
     a.err = w->err;
     const bool mixed = a.mode == MODE_RECORDS && a.shapes;
@@ -370,7 +375,7 @@ int run(Workspace *w, LaunchArgs a, int S, jatam_result *out, int32_t *fitness, 
 
     // the device work of the call; `events` brackets the growth kernels
     auto enqueue = [&](cudaStream_t s, bool events) -> int {
-        CUDA_TRY(launch_reset(w->work_next, w->nkeys, w->list_count, s));
+        CUDA_TRY(launch_reset(w->work_next, w->nkeys, w->list_count, s, w->crops, CROPS_LOG2));
         if (a.stats) CUDA_TRY(cudaMemsetAsync(a.stats, 0, 4 * 8, s));
         if (n_items) CUDA_TRY(launch_prefilter(a, S, (int)pblocks, s));
         if (events) CUDA_TRY(cudaEventRecord(w->k_start, s));
@@ -1416,7 +1421,7 @@ void jatam_shutdown(void)
         cudaFree(w->table.size_max); cudaFree(w->table.size_min);
         cudaFree(w->compact.key); cudaFree(w->compact.count); cudaFree(w->compact.min_id);
         cudaFree(w->compact.size_max); cudaFree(w->compact.size_min);
-        cudaFree(w->work_next); cudaFree(w->stats); cudaFree(w->err); cudaFree(w->nkeys); cudaFree(w->list_count);
+        cudaFree(w->work_next); cudaFree(w->crops); cudaFree(w->stats); cudaFree(w->err); cudaFree(w->nkeys); cudaFree(w->list_count);
         if (w->list) cudaFree(w->list);
         cudaFreeHost(w->host_words);
         if (w->stage_in) cudaFree(w->stage_in);

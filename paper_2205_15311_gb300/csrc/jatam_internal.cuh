@@ -75,6 +75,9 @@ struct LaunchArgs {
     unsigned long long *stats;      // null, or [4] executed work: drawn placements, seed placements,
                                     // lane slots of the growth rounds, genotypes grown by warps
     unsigned *err;                  // sticky error bits
+    unsigned long long *crops;      // null, or the crop table of the launch: 2^crops_log2 slots of
+                                    // {crop bits, valid | h | w | hash}, cleared by the call's reset
+    unsigned crops_log2;
 };
 
 // Lattice template: rows of S bits, S in {8, 16, 32}, L <= S; nt = 8 tuple ids
@@ -95,7 +98,7 @@ cudaError_t classify_mixed_prepare(int w32, int w16, int w8, int *blocks_per_sm)
 cudaError_t launch_classify_mixed(const LaunchArgs &a, int blocks, cudaStream_t st);
 
 cudaError_t launch_reset(unsigned long long *work_next, unsigned *nkeys, unsigned long long *list_count,
-                         cudaStream_t st);
+                         cudaStream_t st, unsigned long long *crops = nullptr, unsigned crops_log2 = 0);
 cudaError_t launch_prefilter(const LaunchArgs &a, int smax, int blocks, cudaStream_t st);
 cudaError_t launch_table_init(Table t, cudaStream_t st);
 cudaError_t launch_hist_compact(Table t, Compact c, unsigned *nkeys, int blocks, cudaStream_t st);

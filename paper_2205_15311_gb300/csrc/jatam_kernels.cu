@@ -56,6 +56,7 @@ namespace {
 constexpr unsigned FULL = 0xffffffffu;
 constexpr int HIST_SLOTS = 256;  // per-CTA phenotype aggregation table
 constexpr int CHUNK = 32;        // items taken from the global counter at once
+constexpr int CROP_PROBES = 4;   // slots of the crop table tried per lookup
 
 enum Phase : int { PH_NEED = 0, PH_INIT, PH_START, PH_GROW, PH_DOM, PH_SHAPE, PH_WRITE, PH_DONE };
 
@@ -1332,26 +1333,62 @@ __device__ __forceinline__ void warp_loop(const LaunchArgs &a, uint32_t *warp_la
         }
 
         // ---- canonical shapes of finished genotypes: a per-warp cache keyed by
-        // the exact crop (when it has at most 32 cells), else one warp-wide job each
-        unsigned long long ckey = 0ull;
-        int cslot = -1;
+        // the exact crop (when it has at most 32 cells), then the launch's crop
+        // table (at most 64 cells), else one warp-wide job each
+        unsigned long long ckey = 0ull, gbits = 0ull;
+        int cslot = -1, gslot = -1;
         if (Ls.phase == PH_SHAPE) {
             const int h = Ls.y1 - Ls.y0 + 1, w = Ls.x1 - Ls.x0 + 1;
-            if (h * w <= 32) {
+            if (h * w <= 64) {
                 const uint32_t wmask = (w >= 32) ? FULL : ((1u << w) - 1u);
-                uint32_t bits = 0;
+                unsigned long long bits = 0;  // row i of the crop at bits i * w ..
                 for (int i = 0; i < h; ++i) {
                     const int b = (Ls.y0 + i) * S + Ls.x0;
-                    bits |= ((my[(G::OCCA + (b >> 5)) * 32] >> (b & 31)) & wmask) << (i * w);
+                    bits |= (unsigned long long)((my[(G::OCCA + (b >> 5)) * 32] >> (b & 31)) & wmask) << (i * w);
                 }
-                ckey = ((unsigned long long)h << 40) | ((unsigned long long)w << 32) | bits;
-                cslot = (int)((uint32_t)((ckey * 0x9E3779B97F4A7C15ull) >> 32) >> 27);
-                const uint32_t *ce = warp_lanes + cslot;
-                const unsigned long long have =
-                    ((unsigned long long)ce[(G::CACHE + 1) * 32] << 32) | ce[G::CACHE * 32];
-                if (have == ckey) {
-                    Ls.hash = ce[(G::CACHE + 2) * 32];
-                    Ls.phase = PH_WRITE;
+                const uint32_t hw = ((uint32_t)h << 8) | (uint32_t)w;
+                if (h * w <= 32) {
+                    ckey = ((unsigned long long)h << 40) | ((unsigned long long)w << 32) | bits;
+                    cslot = (int)((uint32_t)((ckey * 0x9E3779B97F4A7C15ull) >> 32) >> 27);
+                    const uint32_t *ce = warp_lanes + cslot;
+                    const unsigned long long have =
+                        ((unsigned long long)ce[(G::CACHE + 1) * 32] << 32) | ce[G::CACHE * 32];
+                    if (have == ckey) {
+                        Ls.hash = ce[(G::CACHE + 2) * 32];
+                        Ls.phase = PH_WRITE;
+                    }
+                }
+                if (Ls.phase == PH_SHAPE && a.crops) {
+                    // open addressing, a few probes; a slot's key and meta word are each
+                    // written once per launch (key by compare-and-swap, then the meta
+                    // word), so a matching key with a valid meta word is always right
+                    const unsigned mask = (1u << a.crops_log2) - 1u;
+                    const unsigned s0 = (unsigned)(((bits ^ ((unsigned long long)hw << 52)) *
+                                                    0x9E3779B97F4A7C15ull) >> 40) & mask;
+                    for (int p = 0; p < CROP_PROBES; ++p) {
+                        const unsigned sl = (s0 + (unsigned)p) & mask;
+                        const unsigned long long k = __ldcg(&a.crops[2 * sl]);
+                        if (k == 0ull) {
+                            gslot = (int)sl;
+                            break;
+                        }
+                        if (k == bits) {
+                            const unsigned long long meta = __ldcg(&a.crops[2 * sl + 1]);
+                            if ((meta >> 63) && (uint32_t)((meta >> 40) & 0xFFFFu) == hw) {
+                                Ls.hash = (uint32_t)meta;
+                                Ls.phase = PH_WRITE;
+                                if (cslot >= 0) {
+                                    uint32_t *ce = warp_lanes + cslot;
+                                    ce[G::CACHE * 32] = (uint32_t)ckey;
+                                    ce[(G::CACHE + 1) * 32] = (uint32_t)(ckey >> 32);
+                                    ce[(G::CACHE + 2) * 32] = Ls.hash;
+                                }
+                            }
+                            break;
+                        }
+                    }
+                    if (Ls.phase == PH_SHAPE) gbits = bits;
+                    if (gslot < 0) gslot = (int)s0;  // the probes start there again on insertion
                 }
             }
         }
@@ -1368,6 +1405,20 @@ __device__ __forceinline__ void warp_loop(const LaunchArgs &a, uint32_t *warp_la
                     ce[G::CACHE * 32] = (uint32_t)ckey;
                     ce[(G::CACHE + 1) * 32] = (uint32_t)(ckey >> 32);
                     ce[(G::CACHE + 2) * 32] = hv;
+                }
+                if (gbits) {
+                    const unsigned mask = (1u << a.crops_log2) - 1u;
+                    const unsigned long long meta = (1ull << 63) |
+                        ((unsigned long long)(((Ls.y1 - Ls.y0 + 1) << 8) | (Ls.x1 - Ls.x0 + 1)) << 40) | hv;
+                    for (int p = 0; p < CROP_PROBES; ++p) {
+                        const unsigned sl = ((unsigned)gslot + (unsigned)p) & mask;
+                        const unsigned long long old = atomicCAS(&a.crops[2 * sl], 0ull, gbits);
+                        if (old == 0ull) {
+                            __stcg(&a.crops[2 * sl + 1], meta);
+                            break;
+                        }
+                        if (old == gbits) break;
+                    }
                 }
             }
             __syncwarp();
@@ -1475,13 +1526,18 @@ __global__ void __launch_bounds__(256) orbit_fill_kernel(const LaunchArgs a)
     hist_end(H, a);
 }
 
-__global__ void reset_kernel(unsigned long long *work_next, unsigned *nkeys, unsigned long long *list_count)
+__global__ void reset_kernel(unsigned long long *work_next, unsigned *nkeys, unsigned long long *list_count,
+                             unsigned long long *crops, unsigned crop_words)
 {
-    for (int c = 0; c < 3; ++c) {
-        work_next[c] = 0ull;
-        list_count[c] = 0ull;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        for (int c = 0; c < 3; ++c) {
+            work_next[c] = 0ull;
+            list_count[c] = 0ull;
+        }
+        *nkeys = 0u;
     }
-    *nkeys = 0u;
+    for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < crop_words; i += gridDim.x * blockDim.x)
+        crops[i] = 0ull;
 }
 
 __global__ void table_init_kernel(Table t)
@@ -1698,9 +1754,10 @@ cudaError_t launch_classify_mixed(const LaunchArgs &a, int blocks, cudaStream_t 
 }
 
 cudaError_t launch_reset(unsigned long long *work_next, unsigned *nkeys, unsigned long long *list_count,
-                         cudaStream_t st)
+                         cudaStream_t st, unsigned long long *crops, unsigned crops_log2)
 {
-    reset_kernel<<<1, 1, 0, st>>>(work_next, nkeys, list_count);
+    const unsigned words = crops ? (2u << crops_log2) : 0u;
+    reset_kernel<<<crops ? 16 : 1, 256, 0, st>>>(work_next, nkeys, list_count, crops, words);
     return cudaGetLastError();
 }
 
