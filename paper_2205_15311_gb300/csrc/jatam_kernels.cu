@@ -225,15 +225,17 @@ __device__ __forceinline__ void lane_tables(uint32_t *my, unsigned long long col
             P[3][b] |= plane_byte<3>(xh) << 8;
         }
     }
-#pragma unroll
-    for (int t = 0; t < NTILE; ++t) {
-        if (t >= n) break;
+    // not unrolled over tiles: the growth kernel is sensitive to its code size
+    // (warps in different phases share the instruction cache)
+#pragma unroll 1
+    for (int t = 0; t < n; ++t) {
+        const uint32_t tile_t = (uint32_t)(cols >> (16 * t)) & 0xFFFFu;
         uint32_t w[8];
 #pragma unroll
         for (int j = 0; j < 8; ++j) w[j] = 0u;
 #pragma unroll
         for (int s = 0; s < 4; ++s) {
-            const int a = (int)((tl[t] >> (4 * s)) & 15u);
+            const int a = (int)((tile_t >> (4 * s)) & 15u);
             const int pa = (a == 0) ? -1 : (a & 1) ? ((a + 1 < c) ? a + 1 : -1) : a - 1;
             const uint32_t rz = pa >= 0 ? reps : 0u;
             const uint32_t n0 = 0u - (uint32_t)(pa & 1), n1 = 0u - (uint32_t)((pa >> 1) & 1),
