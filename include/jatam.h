@@ -340,8 +340,8 @@ int jatam_autotune(const jatam_config *shapes, uint32_t n_shapes, void *stream);
  * cfg's key: warps_per_cta 1..6, stop_at 1..32 (lanes that must have finished
  * their genotype before a warp leaves a growth round); warps_per_cta 0 forgets
  * the key's setting.  A key never tuned or set uses the defaults: the CTA size
- * that keeps the most warps resident on an SM, and stop_at 12 (lattices up to
- * 16 x 16) or 8 (32 x 32).
+ * that keeps the most warps resident on an SM, and stop_at 14 (lattices up to
+ * 16 x 16) or 12 (32 x 32).
  */
 int jatam_set_tuning(const jatam_config *cfg, int warps_per_cta, int stop_at);
 int jatam_get_tuning(const jatam_config *cfg, int *warps_per_cta, int *stop_at);

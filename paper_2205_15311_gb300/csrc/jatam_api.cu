@@ -36,7 +36,7 @@ int g_warps_override = 0;
 
 struct Tuning {
     int warps = 0;    // 0: the CTA size that keeps the most warps resident
-    int stop_at = 0;  // 0: 12 for lattices up to 16 x 16, 8 for 32 x 32 (measured on S_{2,8}, S_{3,8})
+    int stop_at = 0;  // 0: default_stop_at (14 for lattices up to 16 x 16, 12 for 32 x 32)
     int w32 = 2, w16 = 4, w8 = 2;  // warps per CTA of each region size in the mixed launch
 };
 // launch shape per key (lattice template, n, c); n = c = 0 for mixed batches
@@ -236,7 +236,7 @@ Tuning tuning_for(int S, int n, int c)
         t.stop_at = it->second.stop_at;
     }
     if (t.warps == 0) t.warps = default_warps_per_cta(S, nt);
-    if (t.stop_at == 0) t.stop_at = (S == 32) ? 8 : 12;
+    if (t.stop_at == 0) t.stop_at = default_stop_at(S);
     if (g_warps_override) t.warps = g_warps_override;
     if (g_stop_override) t.stop_at = g_stop_override;
     while (t.warps > 1 && classify_smem_bytes(S, nt, t.warps) > 200 * 1024) --t.warps;  // what fits on one SM

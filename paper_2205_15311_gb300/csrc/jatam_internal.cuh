@@ -93,6 +93,9 @@ constexpr int MAX_CTA_WARPS = 6;
 int default_warps_per_cta(int S, int nt);
 // tuple-table size of a uniform launch of n-tile sets
 inline int tuple_table_size(int n) { return (n >= 1 && n <= 2) ? 8 : 16; }
+// finished lanes that end a growth round when nothing is tuned (measured on
+// S_{2,8} at L = 16 and 19 and on S_{3,8} at L = 32)
+inline int default_stop_at(int S) { return S == 32 ? 12 : 14; }
 int classify_mixed_smem_bytes(int w32, int w16, int w8);
 cudaError_t classify_mixed_prepare(int w32, int w16, int w8, int *blocks_per_sm);
 cudaError_t launch_classify_mixed(const LaunchArgs &a, int blocks, cudaStream_t st);

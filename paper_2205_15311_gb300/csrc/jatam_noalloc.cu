@@ -129,7 +129,6 @@ extern "C" int jatam_enumerate_noalloc(const jatam_config *cfg, uint64_t first, 
     a.out = out;
     a.fitness = nullptr;
     a.use_hist = 0;
-    a.stop_at = 8;
     a.list = list;
     a.list_stride = count;
     a.list_count = list_count;
@@ -139,6 +138,7 @@ extern "C" int jatam_enumerate_noalloc(const jatam_config *cfg, uint64_t first, 
     a.err = err;
 
     const int S = lattice_template_of(L);
+    a.stop_at = default_stop_at(S);
     const int nt = tuple_table_size(cfg->n);
     const int warps = default_warps_per_cta(S, nt);
     if (classify_set_attributes(S, nt, warps) != cudaSuccess) {
