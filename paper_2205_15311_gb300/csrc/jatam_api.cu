@@ -78,6 +78,10 @@ int fail(int code, const char *fmt, ...)
 
 constexpr unsigned TABLE_LOG2 = 18;  // 262,144 phenotype slots per device
 constexpr unsigned CROPS_LOG2 = 12;  // 4,096 slots of the per-call crop table (64 KB)
+// host-buffer calls of at least 2 * PIPE_MIN_ITEMS items run in up to PIPE_MAX_CHUNKS pieces whose
+// results are copied to the host while the next piece is classified
+constexpr size_t PIPE_MIN_ITEMS = size_t(1) << 23;
+constexpr int PIPE_MAX_CHUNKS = 8;
 
 struct Workspace {
     int device = -1;
@@ -116,6 +120,18 @@ struct Workspace {
     float *screen_score = nullptr;
     ScreenTable screen_table{};
     cudaStream_t capture = nullptr;                  // private stream used only for capturing
+    // a pipelined call: pieces alternate between the caller's stream (scratch
+    // above) and `aux` (scratch `alt`), so that a piece fills the SMs that the
+    // previous piece's last genotypes leave idle; results go back on `copy`
+    struct Scratch {
+        unsigned long long *work_next = nullptr, *list_count = nullptr, *crops = nullptr;
+        unsigned *nkeys = nullptr;  // cleared by the reset, read by nobody
+        void *list = nullptr;
+        size_t list_bytes = 0;
+    } alt;
+    cudaStream_t aux = nullptr, copy = nullptr;
+    cudaEvent_t pipe_ev[PIPE_MAX_CHUNKS] = {};  // end of each piece's classification
+    cudaEvent_t pipe_start = nullptr, aux_done = nullptr, pipe_done = nullptr;
 };
 
 std::map<int, Workspace *> g_ws;
@@ -196,6 +212,18 @@ Kind kind_of(const void *p, int device)
         return K_DEVICE;
     if (at.type == cudaMemoryTypeDevice) return K_NULL;  // another device's memory: rejected by the caller
     return K_HOST;
+}
+
+// page-locked host memory (cudaMallocHost / cudaHostRegister): copies from the
+// device to it run asynchronously
+bool is_pinned(const void *p)
+{
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return at.type == cudaMemoryTypeHost;
 }
 
 bool is_pow2(int c) { return c == 1 || c == 2 || c == 4 || c == 8; }
@@ -400,8 +428,110 @@ int run(Workspace *w, LaunchArgs a, int S, jatam_result *out, int32_t *fitness, 
         return JATAM_OK;
     };
 
+    // results that go to page-locked host memory: classify the items in pieces
+    // and copy each piece's results on a second stream while the next piece is
+    // classified.  The phenotype table accumulates over the pieces and is
+    // compacted once.  Not for records without stream ids (their stream id is
+    // the item's index in the call), the orbit mode (members read their
+    // representative's result anywhere in the range), graph replay or timed calls.
+    const bool pipelined = n_items >= 2 * PIPE_MIN_ITEMS && !use_graph && !timed && !a.orbits && !a.lifo &&
+                           !(a.mode == MODE_RECORDS && !a.ids) && (o.host_out || o.host_fit) &&
+                           (!o.host_out || is_pinned(out)) && (!o.host_fit || is_pinned(fitness));
+    auto enqueue_pieces = [&](cudaStream_t s) -> int {
+        size_t pieces = n_items / PIPE_MIN_ITEMS;
+        if (pieces > (size_t)PIPE_MAX_CHUNKS) pieces = PIPE_MAX_CHUNKS;
+        const size_t per = (n_items + pieces - 1) / pieces;
+        Workspace::Scratch &alt = w->alt;
+        if (!w->copy) {
+            CUDA_TRY(cudaStreamCreateWithFlags(&w->aux, cudaStreamNonBlocking));
+            CUDA_TRY(cudaStreamCreateWithFlags(&w->copy, cudaStreamNonBlocking));
+            for (int c = 0; c < PIPE_MAX_CHUNKS; ++c)
+                CUDA_TRY(cudaEventCreateWithFlags(&w->pipe_ev[c], cudaEventDisableTiming));
+            CUDA_TRY(cudaEventCreateWithFlags(&w->pipe_start, cudaEventDisableTiming));
+            CUDA_TRY(cudaEventCreateWithFlags(&w->aux_done, cudaEventDisableTiming));
+            CUDA_TRY(cudaEventCreateWithFlags(&w->pipe_done, cudaEventDisableTiming));
+            CUDA_TRY(cudaMalloc(&alt.work_next, 3 * 8));
+            CUDA_TRY(cudaMalloc(&alt.list_count, 3 * 8));
+            CUDA_TRY(cudaMalloc(&alt.nkeys, 4));
+            CUDA_TRY(cudaMalloc(&alt.crops, (size_t(2) << CROPS_LOG2) * 8));
+        }
+        {
+            int rc = grow(&alt.list, &alt.list_bytes, per * 8 * (mixed ? 3 : 1));
+            if (rc) return rc;
+        }
+        if (a.stats) CUDA_TRY(cudaMemsetAsync(a.stats, 0, 4 * 8, s));
+        CUDA_TRY(cudaEventRecord(w->pipe_start, s));
+        CUDA_TRY(cudaStreamWaitEvent(w->aux, w->pipe_start, 0));
+        int c = 0;
+        for (size_t start = 0; start < n_items; start += per, ++c) {
+            const size_t cnt = (n_items - start < per) ? n_items - start : per;
+            const bool odd = (c & 1) != 0;
+            cudaStream_t cs = odd ? w->aux : s;
+            unsigned long long *wn = odd ? alt.work_next : w->work_next;
+            unsigned long long *lc = odd ? alt.list_count : w->list_count;
+            unsigned long long *cr = odd ? alt.crops : w->crops;
+            unsigned *nk = odd ? alt.nkeys : w->nkeys;
+            LaunchArgs ac = a;
+            ac.work_next = wn;
+            ac.list_count = lc;
+            ac.crops = cr;
+            ac.list = static_cast<unsigned long long *>(odd ? alt.list : w->list);
+            ac.list_stride = per;
+            ac.count = cnt;
+            if (a.mode == MODE_RANGE || a.mode == MODE_SAMPLED) ac.first = a.first + start;
+            if (a.mode == MODE_GENOMES) ac.genomes = a.genomes + start;
+            if (a.mode == MODE_RECORDS) {
+                ac.colours = a.colours + 16 * start;
+                if (a.shapes) ac.shapes = a.shapes + 4 * start;
+                ac.ids = a.ids + start;
+            }
+            if (a.out) ac.out = a.out + start;
+            if (a.fitness) ac.fitness = a.fitness + start;
+            CUDA_TRY(launch_reset(wn, nk, lc, cs, cr, CROPS_LOG2));
+            long long pb = (long long)(cnt + 255) / 256;
+            if (pb > 8LL * w->num_sms) pb = 8LL * w->num_sms;
+            CUDA_TRY(launch_prefilter(ac, S, (int)pb, cs));
+            if (!mixed) {
+                const long long lanes_per_cta = 32LL * warps;
+                long long bc = (long long)((cnt + lanes_per_cta - 1) / lanes_per_cta);
+                if (bc > blocks) bc = blocks;
+                CUDA_TRY(launch_classify(ac, S, nt, (int)(bc < 1 ? 1 : bc), warps, cs));
+            } else if (per_shape) {
+                for (int kc = 0; kc < 3; ++kc) {
+                    LaunchArgs ak = ac;
+                    ak.klass = kc;
+                    ak.stop_at = fixed[kc].stop_at;
+                    CUDA_TRY(launch_classify(ak, fixed[kc].S, 16, fixed[kc].blocks, fixed[kc].warps, cs));
+                }
+            } else {
+                CUDA_TRY(launch_classify_mixed(ac, mixed_blocks, cs));
+            }
+            CUDA_TRY(cudaEventRecord(w->pipe_ev[c], cs));
+            CUDA_TRY(cudaStreamWaitEvent(w->copy, w->pipe_ev[c], 0));
+            if (o.host_out)
+                CUDA_TRY(cudaMemcpyAsync(out + start, o.out_dev + start, cnt * sizeof(jatam_result),
+                                         cudaMemcpyDeviceToHost, w->copy));
+            if (o.host_fit)
+                CUDA_TRY(cudaMemcpyAsync(fitness + start, o.fit_dev + start, cnt * sizeof(int32_t),
+                                         cudaMemcpyDeviceToHost, w->copy));
+        }
+        CUDA_TRY(cudaEventRecord(w->aux_done, w->aux));
+        CUDA_TRY(cudaStreamWaitEvent(s, w->aux_done, 0));
+        if (hist) {
+            CUDA_TRY(launch_hist_compact(w->table, w->compact, w->nkeys, 2 * w->num_sms, s));
+            CUDA_TRY(launch_hist_emit(w->compact, w->nkeys, o.hist_dev, hist_cap,
+                                      o.host_len ? nullptr : o.hist_len_dev, w->num_sms, s));
+        }
+        CUDA_TRY(cudaEventRecord(w->pipe_done, w->copy));
+        CUDA_TRY(cudaStreamWaitEvent(s, w->pipe_done, 0));
+        return JATAM_OK;
+    };
+
     CUDA_TRY(cudaStreamWaitEvent(st, w->last, 0));
-    if (!use_graph) {
+    if (pipelined) {
+        int rc = enqueue_pieces(st);
+        if (rc) return rc;
+    } else if (!use_graph) {
         int rc = enqueue(st, timed);
         if (rc) return rc;
     } else {
@@ -448,9 +578,9 @@ int run(Workspace *w, LaunchArgs a, int S, jatam_result *out, int32_t *fitness, 
     }
     if (timed) w->k_valid = true;
     w->stats_valid = a.stats != nullptr;
-    if (o.host_out && n_items)
+    if (o.host_out && n_items && !pipelined)
         CUDA_TRY(cudaMemcpyAsync(out, o.out_dev, n_items * sizeof(jatam_result), cudaMemcpyDeviceToHost, st));
-    if (o.host_fit && n_items)
+    if (o.host_fit && n_items && !pipelined)
         CUDA_TRY(cudaMemcpyAsync(fitness, o.fit_dev, n_items * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
     const bool must_sync = sync_flag || o.host_out || o.host_fit || o.host_hist || o.host_len;
     if (must_sync) {
@@ -1436,6 +1566,19 @@ void jatam_shutdown(void)
         cudaEventDestroy(w->k_stop);
         for (auto &kv : w->graphs) cudaGraphExecDestroy(kv.second);
         if (w->capture) cudaStreamDestroy(w->capture);
+        if (w->copy) {
+            cudaStreamDestroy(w->copy);
+            cudaStreamDestroy(w->aux);
+            for (int c = 0; c < PIPE_MAX_CHUNKS; ++c) cudaEventDestroy(w->pipe_ev[c]);
+            cudaEventDestroy(w->pipe_start);
+            cudaEventDestroy(w->aux_done);
+            cudaEventDestroy(w->pipe_done);
+            cudaFree(w->alt.work_next);
+            cudaFree(w->alt.list_count);
+            cudaFree(w->alt.nkeys);
+            cudaFree(w->alt.crops);
+        }
+        if (w->alt.list) cudaFree(w->alt.list);
         delete w;
     }
     g_ws.clear();

@@ -248,6 +248,34 @@ def test_host_buffers_equal_device_buffers():
     assert int(hlen[0]) == m and np.array_equal(hist[:m], dh)
 
 
+def test_pinned_host_buffers_pipelined_equal_device_buffers():
+    """Calls whose results go to page-locked host memory and that hold at least
+    2^24 items run in pieces (of at least 2^23) whose copies overlap the next
+    piece's work; the results, the histogram and the fitness values equal the
+    one-pass device call."""
+    n, c, L, k, seed = 3, 8, 16, 20, 3
+    first, count = 1 << 30, (1 << 24) + 4_000_001  # a ragged last piece
+    res, dh, m = _dev_enumerate(n, c, L, k, seed, first, count, sampled=True)
+    out = torch.full((count * 8,), 0xEE, dtype=torch.uint8, pin_memory=True)
+    hist = np.zeros(1 << 16, J.HIST_DTYPE)
+    hlen = np.zeros(1, np.uint32)
+    J.enumerate_space(n, c, L, k, seed, first, count, sampled=True, out=out, hist=hist, hist_len=hlen,
+                      hist_cap=1 << 16)
+    assert np.array_equal(J.results_view(out), res)
+    assert int(hlen[0]) == m and np.array_equal(hist[:m], dh)
+    # a genome batch: staged inputs, fitness and results in page-locked memory
+    g = W.random_genomes(1 << 24, 3, 8, seed=17)
+    gd = torch.from_numpy(g.view(np.int64)).cuda()
+    fd = torch.empty(g.shape[0], dtype=torch.int32, device="cuda")
+    od = torch.empty(g.shape[0] * 8, dtype=torch.uint8, device="cuda")
+    J.evaluate_genomes(gd, fd, n=3, c=8, L=16, k=20, seed=5, out=od, sync=True)
+    gh = torch.from_numpy(g.view(np.int64)).pin_memory()
+    fh = torch.empty(g.shape[0], dtype=torch.int32, pin_memory=True)
+    oh = torch.empty(g.shape[0] * 8, dtype=torch.uint8, pin_memory=True)
+    J.evaluate_genomes(gh, fh, n=3, c=8, L=16, k=20, seed=5, out=oh, sync=True)
+    assert torch.equal(fh, fd.cpu()) and torch.equal(oh, od.cpu())
+
+
 def test_hist_capacity_too_small_reports_length():
     n, c, L, k, seed = 2, 8, 16, 20, 2
     hist = np.zeros(3, J.HIST_DTYPE)
