@@ -440,7 +440,9 @@ int run(Workspace *w, LaunchArgs a, int S, jatam_result *out, int32_t *fitness, 
     auto enqueue_pieces = [&](cudaStream_t s) -> int {
         size_t pieces = n_items / PIPE_MIN_ITEMS;
         if (pieces > (size_t)PIPE_MAX_CHUNKS) pieces = PIPE_MAX_CHUNKS;
-        const size_t per = (n_items + pieces - 1) / pieces;
+        // pieces - 1 of `per` items and a last one of about per / 4: only the last
+        // piece's copy is not hidden behind a later piece's classification
+        const size_t per = (size_t)((double)n_items / ((double)pieces - 0.75)) + 1;
         Workspace::Scratch &alt = w->alt;
         if (!w->copy) {
             CUDA_TRY(cudaStreamCreateWithFlags(&w->aux, cudaStreamNonBlocking));
@@ -465,6 +467,7 @@ int run(Workspace *w, LaunchArgs a, int S, jatam_result *out, int32_t *fitness, 
         int c = 0;
         for (size_t start = 0; start < n_items; start += per, ++c) {
             const size_t cnt = (n_items - start < per) ? n_items - start : per;
+            if (c >= PIPE_MAX_CHUNKS) return fail(JATAM_EINVAL, "internal: too many pieces");
             const bool odd = (c & 1) != 0;
             cudaStream_t cs = odd ? w->aux : s;
             unsigned long long *wn = odd ? alt.work_next : w->work_next;
