@@ -537,7 +537,8 @@ def main():
             traffic = None
         roofline = {"bound": "alu", "achieved": round(achieved, 4), "peak": round(alu_peak, 2),
                     "unit": "Tops/s", "frac": round(achieved / alu_peak, 4), "traffic": traffic,
-                    "kernel": f"classify_kernel<{8 if L <= 8 else 16 if L <= 16 else 32}, {8 if n <= 2 else 16}>",
+                    "kernel": f"classify_kernel<{8 if L <= 8 else 16 if L <= 16 else 32}, {8 if n <= 2 else 16}, "
+                              f"{1 if args.lifo else 0}>",
                     "kernel_ms": round(kms, 4),
                     "peak_source": f"{n_sms} SMs x 128 int32 lanes x {sm_max:.0f} MHz (MEASURED_PEAKS sm_max)",
                     "executed": work,
