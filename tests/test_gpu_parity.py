@@ -276,6 +276,30 @@ def test_pinned_host_buffers_pipelined_equal_device_buffers():
     assert torch.equal(fh, fd.cpu()) and torch.equal(oh, od.cpu())
 
 
+def test_pinned_records_with_ids_pipelined_equal_device_buffers():
+    """Explicit records of mixed shape with stream ids, results and histogram to
+    page-locked memory: the pieces offset the colours, the shapes and the ids."""
+    N = (1 << 24) + 5
+    colours, shapes = W.mixed_records(N, seed=6)
+    ids = W.splitmix64(6, N, 99)
+    dc, ds = torch.from_numpy(colours).cuda(), torch.from_numpy(shapes).cuda()
+    di = torch.from_numpy(ids.view(np.int64)).cuda()
+    od = torch.empty(N * 8, dtype=torch.uint8, device="cuda")
+    hd = torch.empty((1 << 16) * 32, dtype=torch.uint8, device="cuda")
+    ld = torch.zeros(1, dtype=torch.int32, device="cuda")
+    J.classify_batch(dc, seed=4, shapes=ds, stream_ids=di, out=od, hist=hd, hist_len=ld, hist_cap=1 << 16,
+                     sync=True)
+    oh = torch.empty(N * 8, dtype=torch.uint8, pin_memory=True)
+    hh = np.zeros(1 << 16, J.HIST_DTYPE)
+    lh = np.zeros(1, np.uint32)
+    J.classify_batch(torch.from_numpy(colours).pin_memory(), seed=4, shapes=torch.from_numpy(shapes).pin_memory(),
+                     stream_ids=torch.from_numpy(ids.view(np.int64)).pin_memory(), out=oh, hist=hh, hist_len=lh,
+                     hist_cap=1 << 16)
+    assert torch.equal(oh, od.cpu())
+    m = int(ld.item())
+    assert int(lh[0]) == m and np.array_equal(hh[:m], J.hist_view(hd, m))
+
+
 def test_hist_capacity_too_small_reports_length():
     n, c, L, k, seed = 2, 8, 16, 20, 2
     hist = np.zeros(3, J.HIST_DTYPE)
