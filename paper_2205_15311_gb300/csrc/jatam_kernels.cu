@@ -365,7 +365,8 @@ __device__ __forceinline__ int seed_outcome_w(W cols, int n, int c, int L)
     const W ones = (W)0x1111111111111111ull;
     const W valid = (16 * n >= BITS) ? ~(W)0 : (W)(((W)1 << (16 * n)) - (W)1);
     const int cx = L >> 1;
-    bool nd = false, unb = false, grows = false;
+    bool nd = false, unb = false;
+    int sites = 0;
 #pragma unroll
     for (int d = 0; d < 4; ++d) {
         const int a = (int)((cols >> (4 * d)) & 15u);
@@ -392,18 +393,19 @@ __device__ __forceinline__ int seed_outcome_w(W cols, int n, int c, int L)
         const bool inside = qx >= 0 && qy >= 0 && qx < L && qy < L;
         if (multi) nd = true;
         else if (!inside) unb = true;
-        grows = true;
+        ++sites;
     }
     if (nd) return JATAM_ND_LOCAL;
     if (unb) return JATAM_UNBOUNDED;
-    return grows ? -1 : 0;
+    return -sites;
 }
 
 // The seed step of replicate 0, evaluated straight from the colours: for each
 // side d of the seed (tile 0, orientation 0) the candidates are the rotated
 // tuples whose side facing the seed has the partner colour of the seed's side
 // d.  Returns 1 (local ambiguity), 3 (unbounded), 0 (terminated: nothing can
-// attach, every replicate ends as the lone seed) or -1 (the assembly grows).
+// attach, every replicate ends as the lone seed) or minus the number of
+// frontier sites after the seed (the assembly grows).
 __device__ __forceinline__ int seed_outcome(unsigned long long cols, int n, int c, int L)
 {
     if (n <= 2) return seed_outcome_w<uint32_t>((uint32_t)cols, n, c, L);
@@ -1049,13 +1051,13 @@ __global__ void __launch_bounds__(256) prefilter_kernel(const LaunchArgs a, int 
     // itself; records without ids: the index): the lowest lane of a warp holds
     // the smallest.  Sampled genotypes and GA genomes need the reduction.
     const bool sid_is_index = a.mode == MODE_RANGE || (a.mode == MODE_RECORDS && !a.ids);
-    const int nlists = a.bucket ? 3 : 1;
+    const int nlists = a.bucket ? 3 : 2;
     const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
     for (unsigned long long base = (unsigned long long)blockIdx.x * blockDim.x; base < a.count; base += stride) {
         const unsigned long long idx = base + threadIdx.x;
         int key = -1;
         bool grow = false;
-        int klass = 0;
+        int klass = 0;  // the list: the item's size class, or (one class) 0 = heavy, 1 = light
         unsigned long long sid = 0;
         if (idx < a.count) {
             const Item it = load_item(a, idx, b_uniform, smax);
@@ -1070,6 +1072,11 @@ __global__ void __launch_bounds__(256) prefilter_kernel(const LaunchArgs a, int 
                 const int so = seed_outcome(it.cols, it.n, it.c, it.L);
                 if (so < 0) {
                     grow = true;
+                    // three or four frontier sites after the seed: the genotypes that
+                    // run longest (on uniform S_{2,8}, 20 % of those that grow hold
+                    // 78 % of the slowest 1 %); they are handed out first, so that the
+                    // growth launch does not end waiting for one of them
+                    if (!a.bucket) klass = (so <= -3) ? 0 : 1;
                 } else if (so == 0) {
                     write_result(a, idx, JATAM_DET_BOUNDED, it.k, 1u, mono);
                     key = 2;
@@ -1096,7 +1103,11 @@ __global__ void __launch_bounds__(256) prefilter_kernel(const LaunchArgs a, int 
         if (threadIdx.x < nlists && s_fill[threadIdx.x])
             s_base[threadIdx.x] = atomicAdd(&a.list_count[threadIdx.x], (unsigned long long)s_fill[threadIdx.x]);
         __syncthreads();
-        if (grow) a.list[(size_t)klass * a.list_stride + s_base[klass] + my_off] = idx;
+        if (grow) {
+            const unsigned long long pos = s_base[klass] + my_off;
+            if (a.bucket) a.list[(size_t)klass * a.list_stride + pos] = idx;
+            else a.list[klass == 0 ? pos : a.list_stride - 1 - pos] = idx;  // light items from the back
+        }
         if (a.use_hist) {
 #pragma unroll
             for (int q = 0; q < 3; ++q) {
@@ -1138,9 +1149,12 @@ __global__ void __launch_bounds__(256) prefilter_kernel(const LaunchArgs a, int 
 // warp's interleaved region of Geo<S, NT>::WORDS words per lane.
 template <int S, int NT, bool LIFO>
 __device__ __forceinline__ void warp_loop(const LaunchArgs &a, uint32_t *warp_lanes, SmemHist &H,
-                                          const unsigned long long *list, unsigned long long total,
-                                          unsigned long long *work_next)
+                                          const unsigned long long *list, unsigned long long front,
+                                          unsigned long long back, unsigned long long *work_next)
 {
+    // items list[0 .. front) first, then list[a.list_stride - 1], list[a.list_stride - 2], ...
+    // (`back` of them): the pre-filter puts the longest-running genotypes in front
+    const unsigned long long total = front + back;
     using G = Geo<S, NT>;
     const int lane = threadIdx.x & 31;
     uint32_t *my = warp_lanes + lane;
@@ -1213,7 +1227,8 @@ __device__ __forceinline__ void warp_loop(const LaunchArgs &a, uint32_t *warp_la
                 if (my_pos == ~0ull) {
                     Ls.phase = PH_DONE;
                 } else {
-                    const unsigned long long item = list[my_pos];
+                    const unsigned long long item =
+                        list[my_pos < front ? my_pos : a.list_stride - 1 - (my_pos - front)];
                     const Item it = load_item(a, item, b_uniform, S);
                     Ls.item = item;
                     Ls.sid = it.sid;
@@ -1469,8 +1484,11 @@ __global__ void __launch_bounds__(MAX_CTA_WARPS * 32, 3) classify_kernel(const L
     hist_begin(H);
     const int warp = threadIdx.x >> 5;
     uint32_t *warp_lanes = smem_lanes + (size_t)warp * Geo<S, NT>::WORDS * 32;
-    warp_loop<S, NT, LIFO>(a, warp_lanes, H, a.list + (size_t)a.klass * a.list_stride, a.list_count[a.klass],
-                           a.work_next + a.klass);
+    if (a.bucket)
+        warp_loop<S, NT, LIFO>(a, warp_lanes, H, a.list + (size_t)a.klass * a.list_stride, a.list_count[a.klass],
+                               0ull, a.work_next + a.klass);
+    else
+        warp_loop<S, NT, LIFO>(a, warp_lanes, H, a.list, a.list_count[0], a.list_count[1], a.work_next);
     hist_end(H, a);
 }
 
@@ -1491,14 +1509,16 @@ __global__ void __launch_bounds__(256) classify_mixed_kernel(const LaunchArgs a)
     if (warp < w32) {
         uint32_t *wl = smem_lanes + (size_t)warp * R32;
         for (int c = 2; c >= 0; --c)
-            warp_loop<32, 16, false>(a, wl, H, a.list + (size_t)c * a.list_stride, a.list_count[c], a.work_next + c);
+            warp_loop<32, 16, false>(a, wl, H, a.list + (size_t)c * a.list_stride, a.list_count[c], 0ull,
+                                     a.work_next + c);
     } else if (warp < w32 + w16) {
         uint32_t *wl = smem_lanes + (size_t)w32 * R32 + (size_t)(warp - w32) * R16;
         for (int c = 1; c >= 0; --c)
-            warp_loop<16, 16, false>(a, wl, H, a.list + (size_t)c * a.list_stride, a.list_count[c], a.work_next + c);
+            warp_loop<16, 16, false>(a, wl, H, a.list + (size_t)c * a.list_stride, a.list_count[c], 0ull,
+                                     a.work_next + c);
     } else {
         uint32_t *wl = smem_lanes + (size_t)w32 * R32 + (size_t)w16 * R16 + (size_t)(warp - w32 - w16) * R8;
-        warp_loop<8, 16, false>(a, wl, H, a.list, a.list_count[0], a.work_next);
+        warp_loop<8, 16, false>(a, wl, H, a.list, a.list_count[0], 0ull, a.work_next);
     }
     hist_end(H, a);
 }
