@@ -614,7 +614,6 @@ template <int S, bool LIFO>
 __device__ __forceinline__ void lane_step(Lane &Ls, uint32_t *my, uint32_t k0, uint32_t k1, unsigned *err,
                                           uint16_t *stk)
 {
-    constexpr bool lifo = LIFO;
     // Called by all 32 lanes; lanes that are not growing do the arithmetic on
     // harmless addresses of their own region and write nothing.  __syncwarp()
     // brings the warp back together after each data-dependent part.
@@ -1072,11 +1071,12 @@ __global__ void __launch_bounds__(256) prefilter_kernel(const LaunchArgs a, int 
                 const int so = seed_outcome(it.cols, it.n, it.c, it.L);
                 if (so < 0) {
                     grow = true;
-                    // three or four frontier sites after the seed: the genotypes that
-                    // run longest (on uniform S_{2,8}, 20 % of those that grow hold
-                    // 78 % of the slowest 1 %); they are handed out first, so that the
-                    // growth launch does not end waiting for one of them
-                    if (!a.bucket) klass = (so <= -3) ? 0 : 1;
+                    // two or more frontier sites after the seed: the genotypes that can
+                    // run long (on uniform S_{2,8}, 57 % of those that grow, and every
+                    // one of the slowest 1 % in a sample of 7,777); they are handed out
+                    // first, so that the growth launch ends on genotypes with a single
+                    // site, which finish soon
+                    if (!a.bucket) klass = (so <= -2) ? 0 : 1;
                 } else if (so == 0) {
                     write_result(a, idx, JATAM_DET_BOUNDED, it.k, 1u, mono);
                     key = 2;
