@@ -400,6 +400,50 @@ __device__ __forceinline__ int seed_outcome_w(W cols, int n, int c, int L)
     return -sites;
 }
 
+// The seed step of replicate 0 for sets of at most two tiles, branch-free: the
+// candidates of side d of the seed are the representative tuples whose side
+// d + 2 carries the partner of the seed's colour on side d, read from the bit
+// planes of the binding tables (lane_tables); two or more is local ambiguity.
+// Same returns as seed_outcome_w.
+__device__ __forceinline__ int seed_outcome_two(uint32_t cols, int n, int c, int L)
+{
+    const uint32_t t0 = cols & 0xFFFFu, t1 = cols >> 16;
+    uint32_t reps = 1u | (rot16(t0, 4) != t0 ? 2u : 0u) | (rot16(t0, 8) != t0 ? 12u : 0u);
+    if (n == 2) {
+        uint32_t m = 1u | (rot16(t1, 4) != t1 ? 2u : 0u) | (rot16(t1, 8) != t1 ? 12u : 0u);
+        if (t1 == t0 || t1 == rot16(t0, 4) || t1 == rot16(t0, 8) || t1 == rot16(t0, 12)) m = 0u;
+        reps |= m << 4;
+    }
+    const int cx = L >> 1;
+    bool nd = false, unb = false;
+    int sites = 0;
+#pragma unroll
+    for (int d = 0; d < 4; ++d) {
+        const int a = (int)((t0 >> (4 * d)) & 15u);
+        const int pa = (a == 0) ? -1 : (a & 1) ? ((a + 1 < c) ? a + 1 : -1) : a - 1;
+        const uint32_t n0 = 0u - (uint32_t)(pa & 1), n1 = 0u - (uint32_t)((pa >> 1) & 1),
+                       n2 = 0u - (uint32_t)((pa >> 2) & 1);
+        uint32_t X = pa >= 0 ? reps : 0u;
+#pragma unroll
+        for (int b = 0; b < 3; ++b) {
+            const uint32_t x = (cols >> b) & 0x11111111u;
+            const uint32_t P = (d == 0) ? plane_byte<2>(x) : (d == 1) ? plane_byte<3>(x)
+                             : (d == 2) ? plane_byte<0>(x) : plane_byte<1>(x);  // side d + 2
+            X &= ~(P ^ (b == 0 ? n0 : b == 1 ? n1 : n2));
+        }
+        if (X) {
+            const int qx = cx + (d == 1) - (d == 3), qy = cx + (d == 2) - (d == 0);
+            const bool inside = qx >= 0 && qy >= 0 && qx < L && qy < L;
+            if (X & (X - 1)) nd = true;
+            else if (!inside) unb = true;
+            ++sites;
+        }
+    }
+    if (nd) return JATAM_ND_LOCAL;
+    if (unb) return JATAM_UNBOUNDED;
+    return -sites;
+}
+
 // The seed step of replicate 0, evaluated straight from the colours: for each
 // side d of the seed (tile 0, orientation 0) the candidates are the rotated
 // tuples whose side facing the seed has the partner colour of the seed's side
@@ -408,7 +452,7 @@ __device__ __forceinline__ int seed_outcome_w(W cols, int n, int c, int L)
 // frontier sites after the seed (the assembly grows).
 __device__ __forceinline__ int seed_outcome(unsigned long long cols, int n, int c, int L)
 {
-    if (n <= 2) return seed_outcome_w<uint32_t>((uint32_t)cols, n, c, L);
+    if (n <= 2 && c <= 8) return seed_outcome_two((uint32_t)cols, n, c, L);
     return seed_outcome_w<unsigned long long>(cols, n, c, L);
 }
 
@@ -870,8 +914,19 @@ __device__ __forceinline__ void hist_insert(SmemHist &H, const Table &T, unsigne
 
 // decode a packed genotype into nibble-packed colours (tiles seed first,
 // N, E, S, W, b bits per colour, the first tile's N edge most significant)
+// UNROLLED: constant shifts for two tiles of 3-bit colours (the pre-filter,
+// which unpacks every genotype of a call)
+template <bool UNROLLED = false>
 __device__ __forceinline__ unsigned long long unpack_genotype(unsigned long long g, int n, int b)
 {
+    if (UNROLLED && n == 2 && b == 3) {
+        // two tiles of 3-bit colours: edge m = 4 t + e sits at bits 3 (7 - m)
+        const uint32_t g32 = (uint32_t)g;
+        uint32_t cols = 0;
+#pragma unroll
+        for (int m = 0; m < 8; ++m) cols |= ((g32 >> (3 * (7 - m))) & 7u) << (4 * m);
+        return cols;
+    }
     if (n <= 2) {
         // at most 8 colours of at most 4 bits: 32-bit arithmetic
         const uint32_t g32 = (uint32_t)g, cm = (1u << b) - 1u;
@@ -964,6 +1019,7 @@ struct Item {
     bool ok;
 };
 
+template <bool UNROLLED = false>
 __device__ __forceinline__ Item load_item(const LaunchArgs &a, unsigned long long idx, int b_uniform, int smax)
 {
     Item it;
@@ -1003,7 +1059,7 @@ __device__ __forceinline__ Item load_item(const LaunchArgs &a, unsigned long lon
         const int bits = 4 * a.n * b_uniform;
         if (bits < 64) g &= (1ull << bits) - 1ull;
         it.sid = g;
-        it.cols = unpack_genotype(g, a.n, b_uniform);
+        it.cols = unpack_genotype<UNROLLED>(g, a.n, b_uniform);
     }
     return it;
 }
@@ -1059,7 +1115,7 @@ __global__ void __launch_bounds__(256) prefilter_kernel(const LaunchArgs a, int 
         int klass = 0;  // the list: the item's size class, or (one class) 0 = heavy, 1 = light
         unsigned long long sid = 0;
         if (idx < a.count) {
-            const Item it = load_item(a, idx, b_uniform, smax);
+            const Item it = load_item<true>(a, idx, b_uniform, smax);
             sid = it.sid;
             if (a.bucket) klass = (it.L <= 8) ? 0 : (it.L <= 16) ? 1 : 2;
             if (!it.ok) {
