@@ -366,6 +366,10 @@ int run(Workspace *w, LaunchArgs a, int S, jatam_result *out, int32_t *fitness, 
         if (needed < blocks) blocks = needed < 1 ? 1 : needed;
     }
 
+    // heavy genotypes first when every lane of the growth launch takes at least
+    // 8 genotypes on average (pieces of a pipelined call are at least 2^23)
+    a.heavy_first = (!mixed && n_items >= 8ull * (unsigned long long)blocks * warps * 32) ? 1 : 0;
+
     a.lifo_stack = nullptr;
     if (a.lifo) {
         if (mixed) return fail(JATAM_EINVAL, "JATAM_LIFO needs items of one shape");

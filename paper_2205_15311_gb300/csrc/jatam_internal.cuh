@@ -75,6 +75,8 @@ struct LaunchArgs {
     unsigned long long *stats;      // null, or [4] executed work: drawn placements, seed placements,
                                     // lane slots of the growth rounds, genotypes grown by warps
     unsigned *err;                  // sticky error bits
+    int heavy_first;                // 1: the pre-filter lists the genotypes with two or more frontier
+                                    // sites after the seed first (one size class only)
     unsigned long long *crops;      // null, or the crop table of the launch: 2^crops_log2 slots of
                                     // {crop bits, valid | h | w | hash}, cleared by the call's reset
     unsigned crops_log2;

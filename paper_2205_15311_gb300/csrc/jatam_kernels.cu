@@ -1131,8 +1131,10 @@ __global__ void __launch_bounds__(256) prefilter_kernel(const LaunchArgs a, int 
                     // run long (on uniform S_{2,8}, 57 % of those that grow, and every
                     // one of the slowest 1 % in a sample of 7,777); they are handed out
                     // first, so that the growth launch ends on genotypes with a single
-                    // site, which finish soon
-                    if (!a.bucket) klass = (so <= -2) ? 0 : 1;
+                    // site, which finish soon (for calls large enough that every lane
+                    // takes many genotypes: in a small call, warps given only heavy
+                    // genotypes would set its length)
+                    if (!a.bucket && a.heavy_first) klass = (so <= -2) ? 0 : 1;
                 } else if (so == 0) {
                     write_result(a, idx, JATAM_DET_BOUNDED, it.k, 1u, mono);
                     key = 2;

@@ -153,6 +153,8 @@ extern "C" int jatam_enumerate_noalloc(const jatam_config *cfg, uint64_t first, 
     long long blocks = (long long)per_sm * d->num_sms;
     const long long needed = (long long)((count + 32ull * warps - 1) / (32ull * warps));
     if (needed < blocks) blocks = needed < 1 ? 1 : needed;
+    // heavy genotypes first when every lane takes at least 8 genotypes on average
+    a.heavy_first = (count >= 8ull * (unsigned long long)blocks * warps * 32) ? 1 : 0;
 
     // the counters and the error word start at zero in every call
     if (launch_reset(work_next, nkeys, list_count, st) != cudaSuccess) return noalloc_fail(JATAM_ECUDA, "launch failed");
