@@ -30,7 +30,10 @@ WORKLOAD = "s28_full"
 METRIC = "genotypes classified/s (1 GB300, bit-exact vs oracle) + % int/smem roofline"
 UNIT = "genotypes/s"
 
-# algorithmic integer operations per unit of work ("Roofline")
+# algorithmic integer operations per unit of work of the growth kernel: a drawn placement
+# (Philox word 15, rank 1, site selection 10, placement 4, four neighbour re-evaluations 32),
+# a replicate (seed placement and its four neighbours, compare), a genotype (decode, tuples,
+# candidate masks, result), a cell of a shaped genotype (crop, 8 images, hash bytes)
 OPS_PER_PLACEMENT = 62
 OPS_PER_REPLICATE = 37
 OPS_PER_GENOTYPE = 300
