@@ -183,7 +183,7 @@ int workspace(Workspace **out)
     CUDA_TRY(cudaMalloc(&w->stats, 4 * 8));
     CUDA_TRY(cudaMalloc(&w->err, 4));
     CUDA_TRY(cudaMalloc(&w->nkeys, 4));
-    CUDA_TRY(cudaMalloc(&w->list_count, 3 * 8));
+    CUDA_TRY(cudaMalloc(&w->list_count, 6 * 8));
     CUDA_TRY(cudaMallocHost(&w->host_words, 16));
     CUDA_TRY(cudaEventCreateWithFlags(&w->last, cudaEventDisableTiming));
     CUDA_TRY(cudaEventCreate(&w->k_start));
@@ -368,7 +368,9 @@ int run(Workspace *w, LaunchArgs a, int S, jatam_result *out, int32_t *fitness, 
 
     // heavy genotypes first when every lane of the growth launch takes at least
     // 8 genotypes on average (pieces of a pipelined call are at least 2^23)
-    a.heavy_first = (!mixed && n_items >= 8ull * (unsigned long long)blocks * warps * 32) ? 1 : 0;
+    const unsigned long long lanes = mixed ? 4ull * 160ull * (unsigned long long)w->num_sms  // about 4 CTAs of 5 warps an SM
+                                           : (unsigned long long)blocks * warps * 32;
+    a.heavy_first = (n_items >= 8ull * lanes) ? 1 : 0;
 
     a.lifo_stack = nullptr;
     if (a.lifo) {
@@ -457,7 +459,7 @@ int run(Workspace *w, LaunchArgs a, int S, jatam_result *out, int32_t *fitness, 
             CUDA_TRY(cudaEventCreateWithFlags(&w->aux_done, cudaEventDisableTiming));
             CUDA_TRY(cudaEventCreateWithFlags(&w->pipe_done, cudaEventDisableTiming));
             CUDA_TRY(cudaMalloc(&alt.work_next, 3 * 8));
-            CUDA_TRY(cudaMalloc(&alt.list_count, 3 * 8));
+            CUDA_TRY(cudaMalloc(&alt.list_count, 6 * 8));
             CUDA_TRY(cudaMalloc(&alt.nkeys, 4));
             CUDA_TRY(cudaMalloc(&alt.crops, (size_t(2) << CROPS_LOG2) * 8));
         }

@@ -67,7 +67,7 @@ struct LaunchArgs {
     int stop_at;                    // finished lanes that end a growth round (1..32)
     unsigned long long *list;        // items left to grow, written by the pre-filter: 1 or 3 lists
     unsigned long long list_stride;  // capacity of one list (the call's item count)
-    unsigned long long *list_count;  // [3] their lengths
+    unsigned long long *list_count;  // [6]: items at the front of regions 0..2 of `list`, then items stored from their ends
     int bucket;                      // 1: lists by lattice size class (<= 8, <= 16, <= 32); 0: one list
     int klass;                       // classify_kernel: the list it works through
     int plan_w32, plan_w16, plan_w8; // classify_mixed_kernel: warps per CTA of each region size

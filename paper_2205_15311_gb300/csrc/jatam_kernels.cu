@@ -1092,8 +1092,8 @@ __global__ void __launch_bounds__(256) prefilter_kernel(const LaunchArgs a, int 
     // keys decided here: 0 = (ND_LOCAL, 0), 1 = (UNBOUNDED, 0), 2 = (DET_BOUNDED, monomer)
     __shared__ unsigned s_cnt[3];
     __shared__ unsigned long long s_min[3];
-    __shared__ unsigned s_fill[3];               // this iteration's items per list
-    __shared__ unsigned long long s_base[3];     // where they go in the lists
+    __shared__ unsigned s_fill[6];               // this iteration's items per list
+    __shared__ unsigned long long s_base[6];     // where they go in the lists
     if (threadIdx.x < 3) {
         s_cnt[threadIdx.x] = 0u;
         s_min[threadIdx.x] = ~0ull;
@@ -1106,18 +1106,18 @@ __global__ void __launch_bounds__(256) prefilter_kernel(const LaunchArgs a, int 
     // itself; records without ids: the index): the lowest lane of a warp holds
     // the smallest.  Sampled genotypes and GA genomes need the reduction.
     const bool sid_is_index = a.mode == MODE_RANGE || (a.mode == MODE_RECORDS && !a.ids);
-    const int nlists = a.bucket ? 3 : 2;
+    const int nlists = 6;
     const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
     for (unsigned long long base = (unsigned long long)blockIdx.x * blockDim.x; base < a.count; base += stride) {
         const unsigned long long idx = base + threadIdx.x;
         int key = -1;
         bool grow = false;
-        int klass = 0;  // the list: the item's size class, or (one class) 0 = heavy, 1 = light
+        int klass = 0;  // the list: size class (one class: 0) + 3 for a light item stored from the region's end
         unsigned long long sid = 0;
         if (idx < a.count) {
             const Item it = load_item<true>(a, idx, b_uniform, smax);
             sid = it.sid;
-            if (a.bucket) klass = (it.L <= 8) ? 0 : (it.L <= 16) ? 1 : 2;
+            if (a.bucket) klass = (it.L <= 8) ? 0 : (it.L <= 16) ? 1 : 2;  // (+ 3 below for light items)
             if (!it.ok) {
                 atomicOr(a.err, ERR_INVALID_ITEM);
                 write_result(a, idx, 255, 0, 0u, 0u);
@@ -1134,7 +1134,7 @@ __global__ void __launch_bounds__(256) prefilter_kernel(const LaunchArgs a, int 
                     // site, which finish soon (for calls large enough that every lane
                     // takes many genotypes: in a small call, warps given only heavy
                     // genotypes would set its length)
-                    if (!a.bucket && a.heavy_first) klass = (so <= -2) ? 0 : 1;
+                    if (a.heavy_first && so > -2) klass += 3;
                 } else if (so == 0) {
                     write_result(a, idx, JATAM_DET_BOUNDED, it.k, 1u, mono);
                     key = 2;
@@ -1147,7 +1147,7 @@ __global__ void __launch_bounds__(256) prefilter_kernel(const LaunchArgs a, int 
         // append to the list of the item's lattice size class (one class unless
         // the launch mixes sizes): warp offsets from shared counters, then one
         // global atomic per list and CTA iteration
-        if (threadIdx.x < 3) s_fill[threadIdx.x] = 0u;
+        if (threadIdx.x < 6) s_fill[threadIdx.x] = 0u;
         __syncthreads();
         unsigned my_off = 0;
         for (int kc = 0; kc < nlists; ++kc) {
@@ -1162,9 +1162,10 @@ __global__ void __launch_bounds__(256) prefilter_kernel(const LaunchArgs a, int 
             s_base[threadIdx.x] = atomicAdd(&a.list_count[threadIdx.x], (unsigned long long)s_fill[threadIdx.x]);
         __syncthreads();
         if (grow) {
+            // region klass % 3 of the list buffer: heavy items from its front, light ones from its end
             const unsigned long long pos = s_base[klass] + my_off;
-            if (a.bucket) a.list[(size_t)klass * a.list_stride + pos] = idx;
-            else a.list[klass == 0 ? pos : a.list_stride - 1 - pos] = idx;  // light items from the back
+            const size_t region = (size_t)(klass % 3) * a.list_stride;
+            a.list[region + (klass < 3 ? pos : a.list_stride - 1 - pos)] = idx;
         }
         if (a.use_hist) {
 #pragma unroll
@@ -1542,11 +1543,8 @@ __global__ void __launch_bounds__(MAX_CTA_WARPS * 32, 3) classify_kernel(const L
     hist_begin(H);
     const int warp = threadIdx.x >> 5;
     uint32_t *warp_lanes = smem_lanes + (size_t)warp * Geo<S, NT>::WORDS * 32;
-    if (a.bucket)
-        warp_loop<S, NT, LIFO>(a, warp_lanes, H, a.list + (size_t)a.klass * a.list_stride, a.list_count[a.klass],
-                               0ull, a.work_next + a.klass);
-    else
-        warp_loop<S, NT, LIFO>(a, warp_lanes, H, a.list, a.list_count[0], a.list_count[1], a.work_next);
+    warp_loop<S, NT, LIFO>(a, warp_lanes, H, a.list + (size_t)a.klass * a.list_stride, a.list_count[a.klass],
+                           a.list_count[3 + a.klass], a.work_next + a.klass);
     hist_end(H, a);
 }
 
@@ -1567,16 +1565,16 @@ __global__ void __launch_bounds__(256) classify_mixed_kernel(const LaunchArgs a)
     if (warp < w32) {
         uint32_t *wl = smem_lanes + (size_t)warp * R32;
         for (int c = 2; c >= 0; --c)
-            warp_loop<32, 16, false>(a, wl, H, a.list + (size_t)c * a.list_stride, a.list_count[c], 0ull,
+            warp_loop<32, 16, false>(a, wl, H, a.list + (size_t)c * a.list_stride, a.list_count[c], a.list_count[3 + c],
                                      a.work_next + c);
     } else if (warp < w32 + w16) {
         uint32_t *wl = smem_lanes + (size_t)w32 * R32 + (size_t)(warp - w32) * R16;
         for (int c = 1; c >= 0; --c)
-            warp_loop<16, 16, false>(a, wl, H, a.list + (size_t)c * a.list_stride, a.list_count[c], 0ull,
+            warp_loop<16, 16, false>(a, wl, H, a.list + (size_t)c * a.list_stride, a.list_count[c], a.list_count[3 + c],
                                      a.work_next + c);
     } else {
         uint32_t *wl = smem_lanes + (size_t)w32 * R32 + (size_t)w16 * R16 + (size_t)(warp - w32 - w16) * R8;
-        warp_loop<8, 16, false>(a, wl, H, a.list, a.list_count[0], 0ull, a.work_next);
+        warp_loop<8, 16, false>(a, wl, H, a.list, a.list_count[0], a.list_count[3], a.work_next);
     }
     hist_end(H, a);
 }
@@ -1610,10 +1608,8 @@ __global__ void reset_kernel(unsigned long long *work_next, unsigned *nkeys, uns
                              unsigned long long *crops, unsigned crop_words)
 {
     if (blockIdx.x == 0 && threadIdx.x == 0) {
-        for (int c = 0; c < 3; ++c) {
-            work_next[c] = 0ull;
-            list_count[c] = 0ull;
-        }
+        for (int c = 0; c < 3; ++c) work_next[c] = 0ull;
+        for (int c = 0; c < 6; ++c) list_count[c] = 0ull;
         *nkeys = 0u;
     }
     for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < crop_words; i += gridDim.x * blockDim.x)

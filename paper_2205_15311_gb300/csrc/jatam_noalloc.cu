@@ -113,7 +113,7 @@ extern "C" int jatam_enumerate_noalloc(const jatam_config *cfg, uint64_t first, 
 
     unsigned char *base = d->scratch;
     unsigned long long *work_next = reinterpret_cast<unsigned long long *>(base);        // [3]
-    unsigned long long *list_count = reinterpret_cast<unsigned long long *>(base + 32);  // [3]
+    unsigned long long *list_count = reinterpret_cast<unsigned long long *>(base + 128);  // [6]
     unsigned *err = reinterpret_cast<unsigned *>(base + 64);
     unsigned *nkeys = reinterpret_cast<unsigned *>(base + 68);
     unsigned long long *list = reinterpret_cast<unsigned long long *>(base + NOALLOC_HEADER);
