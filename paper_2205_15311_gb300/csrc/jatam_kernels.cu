@@ -180,11 +180,16 @@ __device__ __forceinline__ uint32_t rot16(uint32_t x, int k)
 //   e = 2: edges 2,1,0,3 -> x * (2^11 + 2^6 + 2 + 1)    >> 9
 //   e = 3: edges 3,2,1,0 -> x * (2^15 + 2^10 + 2^5 + 1) >> 12
 template <int E>
-__device__ __forceinline__ uint32_t plane_byte(uint32_t x)
+__device__ __forceinline__ uint32_t plane_spread(uint32_t x)  // tile 0 at bits 0..3, tile 1 at 16..19
 {
     constexpr uint32_t MUL = E == 0 ? 0xC21u : E == 1 ? 0x861u : E == 2 ? 0x843u : 0x8421u;
     constexpr int K = E == 0 ? 11 : E == 1 ? 10 : E == 2 ? 9 : 12;
-    const uint32_t z = ((x * MUL) >> K) & 0x000F000Fu;
+    return ((x * MUL) >> K) & 0x000F000Fu;
+}
+template <int E>
+__device__ __forceinline__ uint32_t plane_byte(uint32_t x)  // tile 0 at bits 0..3, tile 1 at 4..7
+{
+    const uint32_t z = plane_spread<E>(x);
     return (z | (z >> 12)) & 0xFFu;
 }
 
@@ -403,8 +408,8 @@ __device__ __forceinline__ int seed_outcome_w(W cols, int n, int c, int L)
 // The seed step of replicate 0 for sets of at most two tiles, branch-free: the
 // candidates of side d of the seed are the representative tuples whose side
 // d + 2 carries the partner of the seed's colour on side d, read from the bit
-// planes of the binding tables (lane_tables); two or more is local ambiguity.
-// Same returns as seed_outcome_w.
+// planes of the binding tables (lane_tables), kept here with tile 1's rotations
+// at bits 16..19; two or more is local ambiguity.  Same returns as seed_outcome_w.
 __device__ __forceinline__ int seed_outcome_two(uint32_t cols, int n, int c, int L)
 {
     const uint32_t t0 = cols & 0xFFFFu, t1 = cols >> 16;
@@ -412,7 +417,7 @@ __device__ __forceinline__ int seed_outcome_two(uint32_t cols, int n, int c, int
     if (n == 2) {
         uint32_t m = 1u | (rot16(t1, 4) != t1 ? 2u : 0u) | (rot16(t1, 8) != t1 ? 12u : 0u);
         if (t1 == t0 || t1 == rot16(t0, 4) || t1 == rot16(t0, 8) || t1 == rot16(t0, 12)) m = 0u;
-        reps |= m << 4;
+        reps |= m << 16;
     }
     const int cx = L >> 1;
     bool nd = false, unb = false;
@@ -427,8 +432,8 @@ __device__ __forceinline__ int seed_outcome_two(uint32_t cols, int n, int c, int
 #pragma unroll
         for (int b = 0; b < 3; ++b) {
             const uint32_t x = (cols >> b) & 0x11111111u;
-            const uint32_t P = (d == 0) ? plane_byte<2>(x) : (d == 1) ? plane_byte<3>(x)
-                             : (d == 2) ? plane_byte<0>(x) : plane_byte<1>(x);  // side d + 2
+            const uint32_t P = (d == 0) ? plane_spread<2>(x) : (d == 1) ? plane_spread<3>(x)
+                             : (d == 2) ? plane_spread<0>(x) : plane_spread<1>(x);  // side d + 2
             X &= ~(P ^ (b == 0 ? n0 : b == 1 ? n1 : n2));
         }
         if (X) {
@@ -1151,6 +1156,7 @@ __global__ void __launch_bounds__(256) prefilter_kernel(const LaunchArgs a, int 
         __syncthreads();
         unsigned my_off = 0;
         for (int kc = 0; kc < nlists; ++kc) {
+            if (!a.bucket && kc % 3 != 0) continue;  // one size class: lists 0 and 3
             const unsigned gm = __ballot_sync(FULL, grow && klass == kc);
             unsigned woff = 0;
             if (gm && lane == 0) woff = atomicAdd(&s_fill[kc], (unsigned)__popc(gm));
