@@ -153,6 +153,27 @@ def measured_traffic(kernel_file):
     return traffic
 
 
+def measured_pipes(kernel_file):
+    """ALU-pipe and issue utilisation of the dominant kernel from the committed
+    ncu full capture (2^22 random S_{2,8} genomes), or None when the kernel
+    source changed since."""
+    import hashlib
+    import re
+    path = os.path.join(ROOT, "profiles", "classify_kernel_s28_rand4M_ncu_full.md")
+    try:
+        text = open(path).read()
+        src = open(kernel_file, "rb").read()
+    except OSError:
+        return None
+    m = re.search(r"sha256 prefix ([0-9a-f]+)", text)
+    alu = re.search(r"sm__pipe_alu_cycles_active\.avg\.pct_of_peak_sustained_active` \| ([0-9.]+) %", text)
+    issue = re.search(r"smsp__issue_active\.avg\.pct_of_peak_sustained_active` \| ([0-9.]+) %", text)
+    if not (m and alu and issue) or hashlib.sha256(src).hexdigest()[: len(m.group(1))] != m.group(1):
+        return None
+    return {"alu_pipe_active": round(float(alu.group(1)) / 100, 4), "issue_active": round(float(issue.group(1)) / 100, 4),
+            "source": "profiles/classify_kernel_s28_rand4M_ncu_full.md"}
+
+
 def cpu_sample_plan():
     """Stratified bounded sample of the workload for the oracle: 64 blocks of
     up to 65,536 consecutive genotypes spread evenly over the workload."""
@@ -548,6 +569,10 @@ def main():
                     "lane_utilisation": round((work["placements"] + work["seeds"]) / max(work["lane_slots"], 1), 4),
                     "hbm_gbs": round(count * 8 / (kms / 1e3) / 1e9, 1),
                     "hbm_frac_of_measured": round(count * 8 / (kms / 1e3) / 1e9 / float(peaks.get("hbm_gbs", 6753.1)), 4)}
+        pipes = measured_pipes(os.path.join(ROOT, "paper_2205_15311_gb300", "csrc", "jatam_kernels.cu"))
+        if pipes is not None and n <= 2 and L <= 16 and not args.lifo:
+            # context for the ALU fraction: how busy the kernel keeps the SM (ncu, same source)
+            roofline["ncu_pipes"] = pipes
         if placements is not None:
             # the same rate counted in the work of the process as the paper states it
             # (all k replicates of every genotype, the oracle's placement count)
