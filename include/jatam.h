@@ -33,6 +33,12 @@
  *     stream).  The call returns before the work ends unless a host output
  *     buffer was given or cfg->flags has JATAM_SYNC; in those cases it waits
  *     for the stream and also reports errors found on the device;
+ *   - a classification of at least 2^24 items whose results (or fitness
+ *     values) go to page-locked host memory runs in pieces on two internal
+ *     streams, each piece's results copied on a third while the next piece is
+ *     classified; `stream` waits for all of it before the call returns, and the
+ *     results equal the one-pass call's (not for records without stream ids,
+ *     JATAM_ORBITS, JATAM_LIFO, JATAM_GRAPH or the profiling mode);
  *   - the library owns one workspace per device (the histogram table, counters
  *     and staging buffers); calls on one device are serialised through it, in
  *     the order they were made, whatever their streams.  jatam_shutdown()
