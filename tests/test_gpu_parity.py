@@ -324,6 +324,23 @@ def test_ga_evaluate_fitness():
     assert tuple(res[0].tolist()) == tuple(out[0].tolist())
 
 
+def test_large_genome_batch_matches_oracle():
+    """2^20 random genomes of S_{2,8}: a call large enough that the pre-filter
+    hands out the genotypes with two or more frontier sites first; every result
+    equals the oracle's (stream id = the genome)."""
+    n, c, L, k, seed = 2, 8, 16, 20, 5
+    g = W.random_genomes(1 << 20, n, c, seed=23)
+    cols = np.zeros((g.shape[0], 16), np.uint8)
+    for m in range(4 * n):
+        cols[:, m] = ((g >> np.uint64(3 * (4 * n - 1 - m))) & np.uint64(7)).astype(np.uint8)
+    ref, _ = O.classify_batch(cols, n=n, c=c, L=L, k=k, seed=seed, ids=g)
+    dg = torch.from_numpy(g.view(np.int64)).cuda()
+    fit = torch.empty(g.shape[0], dtype=torch.int32, device="cuda")
+    out = torch.full((g.shape[0] * 8,), 0xEE, dtype=torch.uint8, device="cuda")
+    J.evaluate_genomes(dg, fit, n=n, c=c, L=L, k=k, seed=seed, out=out, sync=True)
+    assert np.array_equal(J.results_view(out), ref)
+
+
 def test_argument_errors():
     with pytest.raises(J.JatamError) as e:
         J.enumerate_space(5, 8, 16, 20, 2, 0, 10, out=np.zeros(10, J.RESULT_DTYPE))
