@@ -501,7 +501,7 @@ def test_orbit_mode_rejects_ranges_not_starting_at_zero():
     assert e.value.code == J.JATAM_EINVAL
 
 
-@pytest.mark.parametrize("case", ["s24_full", "s28_slice", "s38_sample_L32"])
+@pytest.mark.parametrize("case", ["s24_full", "s28_slice", "s38_sample_L32", "s28_large"])
 def test_movelist_process_matches_oracle(case):
     """JATAM_LIFO: the movelist process of Section 2.4 (stack of frontier sites,
     new sites pushed in a drawn order, the top one placed) equals the oracle's
@@ -512,6 +512,9 @@ def test_movelist_process_matches_oracle(case):
     elif case == "s28_slice":
         n, c, L, k, seed, sampled = 2, 8, 16, 20, 2, False
         first, count = 7 * (1 << 20) + 11, 30000
+    elif case == "s28_large":  # large enough for the heavy-first list
+        n, c, L, k, seed, sampled = 2, 8, 16, 20, 2, False
+        first, count = 3 << 20, 1 << 20
     else:
         n, c, L, k, seed, _, _, _ = W.WORKLOADS["s38_sample"]
         first, count, sampled = 4242, 20000, True
