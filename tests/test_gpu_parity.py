@@ -472,7 +472,7 @@ def test_work_counters_count_the_executed_process():
 
 
 @pytest.mark.parametrize("n,c,L,k,seed,count", [(2, 4, 16, 10, 1, 1 << 16), (2, 8, 16, 20, 2, 300000),
-                                                (3, 4, 8, 6, 5, 200000)])
+                                                (3, 4, 8, 6, 5, 200000), (2, 8, 16, 20, 2, 1 << 20)])
 def test_orbit_mode_matches_oracle(n, c, L, k, seed, count):
     """JATAM_ORBITS: every genotype gets its orbit representative's result
     (classified with the representative as stream id), equal to the oracle's
