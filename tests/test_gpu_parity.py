@@ -110,7 +110,7 @@ def test_s38_sample_slice_matches_oracle():
     assert _hist_rows(hist) == _hist_rows(_oracle_hist(ref, ids))
 
 
-@pytest.mark.parametrize("case", ["s24_full", "s28_slice", "s38_sample"])
+@pytest.mark.parametrize("case", ["s24_full", "s28_slice", "s38_sample", "s28_large"])
 def test_c4_hash_variant_matches_oracle(case):
     """The rotation-only hash of Section 2.5: every field but the hash equals
     the default run, the hashes equal the oracle's C4 hashes, and chiral pairs
@@ -121,6 +121,9 @@ def test_c4_hash_variant_matches_oracle(case):
     elif case == "s28_slice":
         n, c, L, k, seed, sampled = 2, 8, 16, 20, 2, False
         first, count = 5 * (1 << 20) + 3, 40000
+    elif case == "s28_large":  # the call's crop table and the heavy-first list at scale
+        n, c, L, k, seed, sampled = 2, 8, 16, 20, 2, False
+        first, count = 9 << 20, 1 << 20
     else:
         n, c, L, k, seed, _, _, _ = W.WORKLOADS["s38_sample"]
         first, count, sampled = 777, 40000, True
