@@ -40,6 +40,8 @@ struct DeviceState {
     bool ready = false;
     unsigned char *scratch = nullptr;  // device address of g_noalloc_scratch on this device
     int num_sms = 0;
+    int warps[3][2] = {};   // [lattice template 8, 16, 32][tuple table 8, 16]: warps per CTA
+    int per_sm[3][2] = {};  // resident CTAs of that launch shape per SM
 };
 DeviceState g_dev[MAX_DEVICES];
 std::mutex g_noalloc_mutex;
@@ -51,14 +53,16 @@ int noalloc_fail(int code, const char *msg)
 }
 
 int lattice_template_of(int L) { return L <= 8 ? 8 : L <= 16 ? 16 : 32; }
+int template_slot(int S) { return S == 8 ? 0 : S == 16 ? 1 : 2; }
 int colour_bits(int c) { return c >= 8 ? 3 : c >= 4 ? 2 : c >= 2 ? 1 : 0; }
 
-// set-up of the calling thread's current device: the scratch address and the
-// launch limits of the classification kernel
-int device_setup(DeviceState **out)
+// Set-up of device `dev` (the calling thread's current device), once: the
+// scratch array's device address, the SM count, and for every lattice template
+// and tuple-table size the launch limits and occupancy of the classification
+// kernel -- so that every kernel a later call launches is already loaded and
+// configured, whatever its L and n.
+int device_setup(int dev, DeviceState **out)
 {
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess) return noalloc_fail(JATAM_ECUDA, "cudaGetDevice failed");
     if (dev < 0 || dev >= MAX_DEVICES) return noalloc_fail(JATAM_EUNSUPPORTED, "device ordinal out of range");
     DeviceState &d = g_dev[dev];
     if (!d.ready) {
@@ -70,6 +74,23 @@ int device_setup(DeviceState **out)
         }
         if (cudaDeviceGetAttribute(&d.num_sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
             return noalloc_fail(JATAM_ECUDA, "cudaDeviceGetAttribute failed");
+        if (load_index_range_kernels() != cudaSuccess) {
+            cudaGetLastError();
+            return noalloc_fail(JATAM_ECUDA, "loading the pre-filter kernel failed");
+        }
+        const int Ss[3] = {8, 16, 32}, nts[2] = {8, 16};
+        for (int i = 0; i < 3; ++i)
+            for (int j = 0; j < 2; ++j) {
+                const int w = default_warps_per_cta(Ss[i], nts[j]);
+                int per_sm = 0;
+                if (classify_set_attributes(Ss[i], nts[j], w) != cudaSuccess ||
+                    classify_occupancy(Ss[i], nts[j], w, &per_sm) != cudaSuccess || per_sm < 1) {
+                    cudaGetLastError();
+                    return noalloc_fail(JATAM_ECUDA, "classification kernel does not fit on an SM");
+                }
+                d.warps[i][j] = w;
+                d.per_sm[i][j] = per_sm;
+            }
         d.scratch = static_cast<unsigned char *>(p);
         d.ready = true;
     }
@@ -78,6 +99,14 @@ int device_setup(DeviceState **out)
 }
 
 }  // namespace
+
+// jatam_shutdown: the next call on each device looks everything up again (a
+// cudaDeviceReset reloads the module, and the array may then sit elsewhere)
+void jatam::noalloc_forget_devices()
+{
+    std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+    for (auto &d : g_dev) d = DeviceState{};
+}
 
 extern "C" int jatam_enumerate_noalloc(const jatam_config *cfg, uint64_t first, uint64_t count, jatam_result *out,
                                        void *stream)
@@ -100,14 +129,18 @@ extern "C" int jatam_enumerate_noalloc(const jatam_config *cfg, uint64_t first, 
         const uint64_t space = bits >= 64 ? ~0ull : (1ull << bits);
         if (first > space || count > space - first) return noalloc_fail(JATAM_EINVAL, "index range exceeds the space");
     }
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return noalloc_fail(JATAM_ECUDA, "cudaGetDevice failed");
+    // out must be memory the current device owns (or managed memory): another
+    // GPU's buffer would be written through a peer pointer
     cudaPointerAttributes at;
     if (cudaPointerGetAttributes(&at, out) != cudaSuccess ||
-        !(at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged)) {
+        !((at.type == cudaMemoryTypeDevice && at.device == dev) || at.type == cudaMemoryTypeManaged)) {
         cudaGetLastError();
-        return noalloc_fail(JATAM_EINVAL, "out must be device memory");
+        return noalloc_fail(JATAM_EINVAL, "out must be device memory of the current device");
     }
     DeviceState *d = nullptr;
-    int rc = device_setup(&d);
+    int rc = device_setup(dev, &d);
     if (rc) return rc;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
 
@@ -140,16 +173,8 @@ extern "C" int jatam_enumerate_noalloc(const jatam_config *cfg, uint64_t first, 
     const int S = lattice_template_of(L);
     a.stop_at = default_stop_at(S);
     const int nt = tuple_table_size(cfg->n);
-    const int warps = default_warps_per_cta(S, nt);
-    if (classify_set_attributes(S, nt, warps) != cudaSuccess) {
-        cudaGetLastError();
-        return noalloc_fail(JATAM_ECUDA, "cudaFuncSetAttribute failed");
-    }
-    int per_sm = 0;
-    if (classify_occupancy(S, nt, warps, &per_sm) != cudaSuccess || per_sm < 1) {
-        cudaGetLastError();
-        return noalloc_fail(JATAM_ECUDA, "classification kernel does not fit on an SM");
-    }
+    const int warps = d->warps[template_slot(S)][nt == 8 ? 0 : 1];
+    const int per_sm = d->per_sm[template_slot(S)][nt == 8 ? 0 : 1];
     long long blocks = (long long)per_sm * d->num_sms;
     const long long needed = (long long)((count + 32ull * warps - 1) / (32ull * warps));
     if (needed < blocks) blocks = needed < 1 ? 1 : needed;
