@@ -152,6 +152,33 @@ int jatam_enumerate(const jatam_config *cfg, uint64_t first, uint64_t count, jat
                     jatam_hist_entry *hist, uint32_t hist_cap, uint32_t *hist_len, void *stream);
 
 /*
+ * jatam_last_shapes -- the exact side table of the phenotype histogram
+ * (Section 2.5: shapes are binned by a 32-bit one-at-a-time hash, and the
+ * paper estimates how likely two distinct shapes are to share one; this
+ * table checks it exactly).  Every call on the current device that builds a
+ * histogram with the canonical-form hash (not JATAM_C4_HASH) records, for
+ * every shape hash of its histogram, the canonical form the hash was computed
+ * from; every later computation of the same hash in that call compares its
+ * own canonical form with the stored one and counts a collision when they
+ * differ.  This call returns that table for the last such call on the device
+ * (it waits for that call to finish).
+ *   shapes : [cap] entries sorted by shape_hash (cap may be 0).
+ *   len    : receives the number of distinct shape hashes.
+ *   collisions : receives the number of canonical forms that differed from
+ *            the form stored under their hash (0: every hash names one shape).
+ * Returns JATAM_EINVAL if the last call on the device recorded no shapes or
+ * cap < *len (the first cap entries are still written), JATAM_ENOMEM if the
+ * table (16,384 hashes) overflowed.
+ */
+typedef struct {
+    uint32_t shape_hash; /* hash of the histogram keys (class 0 or 2) with this shape */
+    uint8_t h, w;        /* height and width of the canonical form */
+    uint16_t size;       /* occupied cells */
+    uint32_t rows[32];   /* row i < h of the canonical form: bit j set = cell (column j, row i) occupied */
+} jatam_shape;           /* 136 bytes */
+int jatam_last_shapes(jatam_shape *shapes, uint32_t cap, uint32_t *len, uint32_t *collisions);
+
+/*
  * jatam_classify_batch -- classify N explicit tile sets (Section 2.6: a batch
  * of assemblies, hashed and binned).
  *   colours    : [N][16] uint8, colour of edge e of tile t at [i][4 t + e]
@@ -407,16 +434,29 @@ int jatam_work_counters(uint64_t counters[4]);
  *           JATAM_EINVAL).
  *   first, count : index range, count <= JATAM_NOALLOC_MAX_COUNT, else
  *           JATAM_EINVAL with a message naming the limit.
- *   out   : [count] results in DEVICE memory (required; host memory is
- *           rejected, as staging it would need an allocation).  No histogram.
+ *   out   : [count] results in device memory of the current device, or
+ *           managed memory (required; host memory is rejected, as staging it
+ *           would need an allocation, and so is another GPU's memory).  No
+ *           histogram.
  *   stream: cudaStream_t or NULL.
  * The first call on each device looks up the scratch array's device address
- * and sets the kernel's launch limits; make that first call before any stream
- * capture.  All calls share the one array and start by clearing its counters:
- * calls whose work overlaps on the GPU (unordered streams) race on it.
+ * and loads and configures every kernel instance the entry point may launch
+ * (all lattice sizes and tile counts); make that first call before any stream
+ * capture.  jatam_shutdown() forgets this set-up; call it before a
+ * cudaDeviceReset, after which the array may sit at another address.  All
+ * calls share the one array and start by clearing its counters: calls whose
+ * work overlaps on the GPU (unordered streams) race on it.
  */
 #define JATAM_NOALLOC_MAX_COUNT 1048576u
 int jatam_enumerate_noalloc(const jatam_config *cfg, uint64_t first, uint64_t count, jatam_result *out, void *stream);
+
+/*
+ * jatam_workspace_bytes -- bytes of device memory the library's workspace
+ * holds on the current device (0 if no call has created one there; the fixed
+ * scratch array of jatam_enumerate_noalloc is not counted).  The paper has no
+ * counterpart: it is a memory-accounting aid.
+ */
+int jatam_workspace_bytes(uint64_t *bytes);
 
 /* Free every device workspace of the library (waits for queued work). */
 void jatam_shutdown(void);

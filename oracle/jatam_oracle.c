@@ -166,6 +166,13 @@ uint64_t orc_sample_genotype(uint64_t i, int n, int c, uint64_t seed)
     return v;
 }
 
+/* The sampled genotypes of indices first .. first+count-1 (one call of
+ * orc_sample_genotype per index). */
+void orc_sample_genotypes(uint64_t first, uint64_t count, int n, int c, uint64_t seed, uint64_t *out)
+{
+    for (uint64_t i = 0; i < count; i++) out[i] = orc_sample_genotype(first + i, n, c, seed);
+}
+
 /* ---------------------------------------------------------------------------
  * Tile set with rotations
  * ------------------------------------------------------------------------- */
@@ -566,6 +573,104 @@ static int g_c4_hash = 0; /* hash mode of the classification calls below (0: D4 
 
 void orc_set_hash_mode(int c4) { g_c4_hash = c4 ? 1 : 0; }
 
+/* ---------------------------------------------------------------------------
+ * Exact side table of the shapes (Section 2.5 estimates the chance that two
+ * distinct shapes share a 32-bit hash; this table settles it): while it is
+ * on, every canonical form hashed by the classification calls is stored under
+ * its hash, and a form that differs from the one already stored under the
+ * same hash counts as a collision.  Row i of a form: bit j = column j.
+ * ------------------------------------------------------------------------- */
+#define ORC_SHAPE_SLOTS (1 << 16)
+typedef struct {
+    int used;
+    uint32_t hash;
+    int h, w;
+    uint32_t rows[ORC_MAXL];
+} orc_shape_entry;
+static orc_shape_entry *g_shape_tab = NULL;
+static int g_shape_on = 0;
+static uint64_t g_shape_collisions = 0, g_shape_overflow = 0;
+static pthread_mutex_t g_shape_mu = PTHREAD_MUTEX_INITIALIZER;
+
+int orc_shape_table_begin(void)
+{
+    if (!g_shape_tab) g_shape_tab = (orc_shape_entry *)malloc(sizeof(orc_shape_entry) * ORC_SHAPE_SLOTS);
+    if (!g_shape_tab) return -2;
+    memset(g_shape_tab, 0, sizeof(orc_shape_entry) * ORC_SHAPE_SLOTS);
+    g_shape_collisions = 0;
+    g_shape_overflow = 0;
+    g_shape_on = 1;
+    return 0;
+}
+
+void orc_shape_table_add(uint32_t hash, const uint8_t *bm, int h, int w)
+{
+    orc_shape_entry e;
+    memset(&e, 0, sizeof e);
+    e.used = 1;
+    e.hash = hash;
+    e.h = h;
+    e.w = w;
+    for (int y = 0; y < h && y < ORC_MAXL; y++)
+        for (int x = 0; x < w && x < 32; x++)
+            if (bm[y * w + x]) e.rows[y] |= (uint32_t)1 << x;
+    pthread_mutex_lock(&g_shape_mu);
+    uint32_t slot = hash & (ORC_SHAPE_SLOTS - 1);
+    int placed = 0;
+    for (int p = 0; p < ORC_SHAPE_SLOTS; p++) {
+        orc_shape_entry *t = &g_shape_tab[slot];
+        if (!t->used) {
+            *t = e;
+            placed = 1;
+            break;
+        }
+        if (t->hash == hash) {
+            if (t->h != h || t->w != w || memcmp(t->rows, e.rows, sizeof e.rows) != 0) g_shape_collisions++;
+            placed = 1;
+            break;
+        }
+        slot = (slot + 1) & (ORC_SHAPE_SLOTS - 1);
+    }
+    if (!placed) g_shape_overflow++;
+    pthread_mutex_unlock(&g_shape_mu);
+}
+
+/* Stop recording; the stored forms, sorted by hash: hashes[i], hw[2 i] = h,
+ * hw[2 i + 1] = w, rows[32 i .. 32 i + 31].  Returns -1 if more than cap. */
+int orc_shape_table_end(uint32_t *hashes, int32_t *hw, uint32_t *rows, int cap, int *len, uint64_t *collisions,
+                        uint64_t *overflow)
+{
+    g_shape_on = 0;
+    int m = 0;
+    if (g_shape_tab) {
+        /* selection of the entries in increasing hash order (plain and slow) */
+        uint64_t last = 0;
+        int first = 1;
+        for (;;) {
+            int best = -1;
+            for (int i = 0; i < ORC_SHAPE_SLOTS; i++) {
+                const orc_shape_entry *t = &g_shape_tab[i];
+                if (!t->used || (!first && (uint64_t)t->hash <= last)) continue;
+                if (best < 0 || t->hash < g_shape_tab[best].hash) best = i;
+            }
+            if (best < 0) break;
+            if (m < cap) {
+                hashes[m] = g_shape_tab[best].hash;
+                hw[2 * m] = g_shape_tab[best].h;
+                hw[2 * m + 1] = g_shape_tab[best].w;
+                for (int r = 0; r < 32; r++) rows[32 * m + r] = r < ORC_MAXL ? g_shape_tab[best].rows[r] : 0u;
+            }
+            m++;
+            last = g_shape_tab[best].hash;
+            first = 0;
+        }
+    }
+    *len = m;
+    *collisions = g_shape_collisions;
+    *overflow = g_shape_overflow;
+    return m > cap ? -1 : 0;
+}
+
 static uint32_t hash_of_grid(const grid *G)
 {
     int32_t xs[ORC_MAXL * ORC_MAXL], ys[ORC_MAXL * ORC_MAXL];
@@ -581,7 +686,9 @@ static uint32_t hash_of_grid(const grid *G)
     if (g_c4_hash) return orc_c4_hash(xs, ys, m);
     int32_t h, w;
     orc_canonical(xs, ys, m, bm, &h, &w);
-    return orc_shape_hash(bm, h, w);
+    uint32_t hash = orc_shape_hash(bm, h, w);
+    if (g_shape_on) orc_shape_table_add(hash, bm, h, w);
+    return hash;
 }
 
 /* ---------------------------------------------------------------------------

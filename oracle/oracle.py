@@ -77,6 +77,16 @@ def lib():
             L.orc_decode.restype = ctypes.c_int
             L.orc_sample_genotype.argtypes = [ctypes.c_uint64, ctypes.c_int, ctypes.c_int, ctypes.c_uint64]
             L.orc_sample_genotype.restype = ctypes.c_uint64
+            L.orc_sample_genotypes.argtypes = [ctypes.c_uint64, ctypes.c_uint64, ctypes.c_int, ctypes.c_int,
+                                               ctypes.c_uint64, ctypes.c_void_p]
+            L.orc_sample_genotypes.restype = None
+            L.orc_shape_table_begin.argtypes = []
+            L.orc_shape_table_begin.restype = ctypes.c_int
+            L.orc_shape_table_end.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int,
+                                              ctypes.POINTER(ctypes.c_int), u64p, u64p]
+            L.orc_shape_table_end.restype = ctypes.c_int
+            L.orc_shape_table_add.argtypes = [ctypes.c_uint32, u8p, ctypes.c_int, ctypes.c_int]
+            L.orc_shape_table_add.restype = None
             L.orc_canonical.argtypes = [i32p, i32p, ctypes.c_int, u8p, i32p, i32p]
             L.orc_canonical.restype = ctypes.c_int
             L.orc_shape_hash.argtypes = [u8p, ctypes.c_int, ctypes.c_int]
@@ -160,6 +170,13 @@ def decode(g: int, n: int, c: int) -> np.ndarray:
 
 def sample_genotype(i: int, n: int, c: int, seed: int) -> int:
     return int(lib().orc_sample_genotype(int(i), int(n), int(c), int(seed)))
+
+
+def sample_genotypes(first: int, count: int, n: int, c: int, seed: int) -> np.ndarray:
+    """The sampled genotypes of indices first .. first+count-1."""
+    out = np.zeros(int(count), np.uint64)
+    lib().orc_sample_genotypes(int(first), int(count), int(n), int(c), int(seed), out.ctypes.data)
+    return out
 
 
 def canonical(cells):
@@ -328,6 +345,43 @@ def c4_hash(cells) -> int:
     ys = np.array([c[1] for c in cells] or [0], np.int32)
     return int(lib().orc_c4_hash(xs.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
                                  ys.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), len(cells)))
+
+
+class shape_table:
+    """Context manager: record the canonical form of every shape the
+    classification calls inside it hash (the exact side table of Section
+    2.5's hash).  After the block: `forms` maps each shape hash to its
+    canonical form (h x w uint8 array) and `collisions` counts the forms that
+    differed from the one already stored under their hash."""
+
+    CAP = 1 << 16
+
+    def __enter__(self):
+        if lib().orc_shape_table_begin() != 0:
+            raise MemoryError("oracle shape table")
+        return self
+
+    def add(self, hash_value, bitmap):
+        """Store one form under a given hash, as the classification does."""
+        bm = np.ascontiguousarray(bitmap, dtype=np.uint8)
+        lib().orc_shape_table_add(int(hash_value), _u8(bm.reshape(-1)), bm.shape[0], bm.shape[1])
+
+    def __exit__(self, *exc):
+        hashes = np.zeros(self.CAP, np.uint32)
+        hw = np.zeros(2 * self.CAP, np.int32)
+        rows = np.zeros(32 * self.CAP, np.uint32)
+        n = ctypes.c_int(0)
+        col = ctypes.c_uint64(0)
+        ovf = ctypes.c_uint64(0)
+        lib().orc_shape_table_end(hashes.ctypes.data, hw.ctypes.data, rows.ctypes.data, self.CAP, ctypes.byref(n),
+                                  ctypes.byref(col), ctypes.byref(ovf))
+        self.collisions = int(col.value)
+        self.overflow = int(ovf.value)
+        self.forms = {}
+        for i in range(min(n.value, self.CAP)):
+            h, w = int(hw[2 * i]), int(hw[2 * i + 1])
+            bm = np.array([[(int(rows[32 * i + y]) >> x) & 1 for x in range(w)] for y in range(h)], np.uint8)
+            self.forms[int(hashes[i])] = bm.reshape(h, w)
 
 
 class hash_mode:

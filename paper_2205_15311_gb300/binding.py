@@ -85,6 +85,10 @@ def lib():
             getattr(L, f).restype = ctypes.c_int
         L.jatam_enumerate_noalloc.argtypes = [_VP, _U64, _U64, _VP, _VP]
         L.jatam_enumerate_noalloc.restype = ctypes.c_int
+        L.jatam_last_shapes.argtypes = [_VP, _U32, ctypes.POINTER(_U32), ctypes.POINTER(_U32)]
+        L.jatam_last_shapes.restype = ctypes.c_int
+        L.jatam_workspace_bytes.argtypes = [ctypes.POINTER(ctypes.c_uint64)]
+        L.jatam_workspace_bytes.restype = ctypes.c_int
         L.jatam_mlp_create.argtypes = [_U64, ctypes.POINTER(_VP)]
         L.jatam_mlp_create.restype = ctypes.c_int
         L.jatam_mlp_destroy.argtypes = [_VP]
@@ -258,6 +262,14 @@ def jatam_work_counters(counters):
     return lib().jatam_work_counters(counters)
 
 
+def jatam_last_shapes(shapes, cap, length, collisions):
+    return lib().jatam_last_shapes(shapes, cap, length, collisions)
+
+
+def jatam_workspace_bytes(nbytes):
+    return lib().jatam_workspace_bytes(nbytes)
+
+
 def jatam_shutdown():
     lib().jatam_shutdown()
 
@@ -308,9 +320,36 @@ def enumerate_space(n, c, L, k, seed, first, count, *, sampled=False, out=None, 
                                  _addr(hist_len), _stream_handle(stream)))
 
 
-def enumerate_noalloc(n, c, L, k, seed, first, count, out, *, sampled=False, stream=None, sync=False):
+SHAPE_DTYPE = np.dtype([("shape_hash", "<u4"), ("h", "u1"), ("w", "u1"), ("size", "<u2"), ("rows", "<u4", (32,))])
+
+
+def last_shapes(cap=1 << 14):
+    """jatam_last_shapes: (entries as a SHAPE_DTYPE array sorted by hash, collisions)."""
+    out = np.zeros(cap, SHAPE_DTYPE)
+    n = _U32(0)
+    col = _U32(0)
+    check(jatam_last_shapes(out.ctypes.data, cap, ctypes.byref(n), ctypes.byref(col)))
+    return out[: n.value], int(col.value)
+
+
+def shape_bitmap(entry):
+    """h x w uint8 array of one jatam_shape entry (column j of row i = bit j)."""
+    h, w = int(entry["h"]), int(entry["w"])
+    return np.array([[(int(entry["rows"][i]) >> j) & 1 for j in range(w)] for i in range(h)], np.uint8)
+
+
+def workspace_bytes() -> int:
+    """Device bytes the library's workspace holds on the current device (0: none)."""
+    v = ctypes.c_uint64(0)
+    check(jatam_workspace_bytes(ctypes.byref(v)))
+    return int(v.value)
+
+
+def enumerate_noalloc(n, c, L, k, seed, first, count, out, *, sampled=False, stream=None, sync=False,
+                      c4_hash=False):
     """jatam_enumerate_noalloc into a device buffer `out` (no library allocation)."""
-    cfg = make_config(n, c, L, k, seed, (JATAM_SAMPLED if sampled else 0) | (JATAM_SYNC if sync else 0))
+    cfg = make_config(n, c, L, k, seed, (JATAM_SAMPLED if sampled else 0) | (JATAM_SYNC if sync else 0)
+                      | (JATAM_C4_HASH if c4_hash else 0))
     return check(jatam_enumerate_noalloc(ctypes.addressof(cfg), first, count, _addr(out), _stream_handle(stream)))
 
 

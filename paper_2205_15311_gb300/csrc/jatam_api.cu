@@ -1,5 +1,6 @@
 // jatam_api.cu -- host side of libjatam.so: argument checks, the per-device
 // workspace, staging of host buffers, launches, and the error state.
+#include <algorithm>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -78,6 +79,7 @@ int fail(int code, const char *fmt, ...)
 
 constexpr unsigned TABLE_LOG2 = 18;  // 262,144 phenotype slots per device
 constexpr unsigned CROPS_LOG2 = 12;  // 4,096 slots of the per-call crop table (64 KB)
+constexpr unsigned SHAPES_LOG2 = 14;  // 16,384 slots of the call's shape side table (2.2 MB)
 // host-buffer calls of at least 2 * PIPE_MIN_ITEMS items run in up to PIPE_MAX_CHUNKS pieces whose
 // results are copied to the host while the next piece is classified
 constexpr size_t PIPE_MIN_ITEMS = size_t(1) << 23;
@@ -92,6 +94,8 @@ struct Workspace {
     unsigned long long *crops = nullptr;  // crop -> shape hash within one call (cleared by its reset)
     unsigned long long *stats = nullptr;  // [4] executed-work counters of the last counted call
     bool stats_valid = false;
+    ShapeTab shapes{};           // canonical form per shape hash of the last call with a histogram
+    bool shapes_valid = false;   // the last call filled `shapes` (a histogram, not the C4 hash)
     unsigned *err = nullptr;
     unsigned *nkeys = nullptr;
     unsigned long long *list_count = nullptr;
@@ -181,6 +185,11 @@ int workspace(Workspace **out)
     CUDA_TRY(cudaMalloc(&w->work_next, 3 * 8));
     CUDA_TRY(cudaMalloc(&w->crops, (size_t(2) << CROPS_LOG2) * 8));
     CUDA_TRY(cudaMalloc(&w->stats, 4 * 8));
+    w->shapes.log2 = SHAPES_LOG2;
+    CUDA_TRY(cudaMalloc(&w->shapes.key, (size_t(8) + 4 + 128) << SHAPES_LOG2));
+    w->shapes.meta = reinterpret_cast<unsigned *>(w->shapes.key + (size_t(1) << SHAPES_LOG2));
+    w->shapes.rows = reinterpret_cast<uint32_t *>(w->shapes.meta + (size_t(1) << SHAPES_LOG2));
+    CUDA_TRY(cudaMalloc(&w->shapes.stats, 4 * 4));
     CUDA_TRY(cudaMalloc(&w->err, 4));
     CUDA_TRY(cudaMalloc(&w->nkeys, 4));
     CUDA_TRY(cudaMalloc(&w->list_count, 6 * 8));
@@ -333,6 +342,9 @@ int run(Workspace *w, LaunchArgs a, int S, jatam_result *out, int32_t *fitness, 
     a.work_next = w->work_next;
     a.crops = w->crops;
     a.crops_log2 = CROPS_LOG2;
+    // the exact shape side table: calls with a histogram and the canonical-form hash
+    const bool record_shapes = hist && !a.c4;
+    a.shape_tab = record_shapes ? w->shapes : ShapeTab{};
     a.stats = (g_profile & 2) ? w->stats : nullptr;
     a.err = w->err;
     const bool mixed = a.mode == MODE_RECORDS && a.shapes;
@@ -408,7 +420,16 @@ int run(Workspace *w, LaunchArgs a, int S, jatam_result *out, int32_t *fitness, 
     const bool timed = (g_profile & 1) || kernel_ms;
 
     // the device work of the call; `events` brackets the growth kernels
+    // the side table starts empty in every call that records shapes (keys and meta words; rows are
+    // always written before their meta word)
+    auto clear_shapes = [&](cudaStream_t s) -> int {
+        if (!record_shapes) return JATAM_OK;
+        CUDA_TRY(cudaMemsetAsync(w->shapes.key, 0, (size_t(8) + 4) << SHAPES_LOG2, s));
+        CUDA_TRY(cudaMemsetAsync(w->shapes.stats, 0, 4 * 4, s));
+        return JATAM_OK;
+    };
     auto enqueue = [&](cudaStream_t s, bool events) -> int {
+        if (int rc = clear_shapes(s)) return rc;
         CUDA_TRY(launch_reset(w->work_next, w->nkeys, w->list_count, s, w->crops, CROPS_LOG2));
         if (a.stats) CUDA_TRY(cudaMemsetAsync(a.stats, 0, 4 * 8, s));
         if (n_items) CUDA_TRY(launch_prefilter(a, S, (int)pblocks, s));
@@ -427,7 +448,7 @@ int run(Workspace *w, LaunchArgs a, int S, jatam_result *out, int32_t *fitness, 
         if (events) CUDA_TRY(cudaEventRecord(w->k_stop, s));
         if (n_items && a.orbits) CUDA_TRY(launch_orbit_fill(a, (int)pblocks, s));
         if (hist) {
-            CUDA_TRY(launch_hist_compact(w->table, w->compact, w->nkeys, 2 * w->num_sms, s));
+            CUDA_TRY(launch_hist_compact(w->table, w->compact, w->nkeys, 2 * w->num_sms, s, a.shape_tab));
             CUDA_TRY(launch_hist_emit(w->compact, w->nkeys, o.hist_dev, hist_cap,
                                       o.host_len ? nullptr : o.hist_len_dev, w->num_sms, s));
         }
@@ -468,6 +489,7 @@ int run(Workspace *w, LaunchArgs a, int S, jatam_result *out, int32_t *fitness, 
             if (rc) return rc;
         }
         if (a.stats) CUDA_TRY(cudaMemsetAsync(a.stats, 0, 4 * 8, s));
+        if (int rc = clear_shapes(s)) return rc;
         CUDA_TRY(cudaEventRecord(w->pipe_start, s));
         CUDA_TRY(cudaStreamWaitEvent(w->aux, w->pipe_start, 0));
         int c = 0;
@@ -527,7 +549,7 @@ int run(Workspace *w, LaunchArgs a, int S, jatam_result *out, int32_t *fitness, 
         CUDA_TRY(cudaEventRecord(w->aux_done, w->aux));
         CUDA_TRY(cudaStreamWaitEvent(s, w->aux_done, 0));
         if (hist) {
-            CUDA_TRY(launch_hist_compact(w->table, w->compact, w->nkeys, 2 * w->num_sms, s));
+            CUDA_TRY(launch_hist_compact(w->table, w->compact, w->nkeys, 2 * w->num_sms, s, a.shape_tab));
             CUDA_TRY(launch_hist_emit(w->compact, w->nkeys, o.hist_dev, hist_cap,
                                       o.host_len ? nullptr : o.hist_len_dev, w->num_sms, s));
         }
@@ -587,6 +609,7 @@ int run(Workspace *w, LaunchArgs a, int S, jatam_result *out, int32_t *fitness, 
     }
     if (timed) w->k_valid = true;
     w->stats_valid = a.stats != nullptr;
+    w->shapes_valid = record_shapes;
     if (o.host_out && n_items && !pipelined)
         CUDA_TRY(cudaMemcpyAsync(out, o.out_dev, n_items * sizeof(jatam_result), cudaMemcpyDeviceToHost, st));
     if (o.host_fit && n_items && !pipelined)
@@ -1561,6 +1584,7 @@ void jatam_shutdown(void)
         cudaFree(w->compact.key); cudaFree(w->compact.count); cudaFree(w->compact.min_id);
         cudaFree(w->compact.size_max); cudaFree(w->compact.size_min);
         cudaFree(w->work_next); cudaFree(w->crops); cudaFree(w->stats); cudaFree(w->err); cudaFree(w->nkeys); cudaFree(w->list_count);
+        cudaFree(w->shapes.key); cudaFree(w->shapes.stats);
         if (w->list) cudaFree(w->list);
         cudaFreeHost(w->host_words);
         if (w->stage_in) cudaFree(w->stage_in);
@@ -1592,6 +1616,83 @@ void jatam_shutdown(void)
     }
     g_ws.clear();
     cudaSetDevice(cur);
+    noalloc_forget_devices();
+}
+
+int jatam_last_shapes(jatam_shape *shapes, uint32_t cap, uint32_t *len, uint32_t *collisions)
+{
+    std::lock_guard<std::mutex> lock(g_mutex);
+    if (!len || !collisions) return fail(JATAM_EINVAL, "len and collisions are required");
+    if (cap && !shapes) return fail(JATAM_EINVAL, "shapes is NULL");
+    int dev = 0;
+    CUDA_TRY(cudaGetDevice(&dev));
+    auto it = g_ws.find(dev);
+    if (it == g_ws.end() || !it->second->shapes_valid)
+        return fail(JATAM_EINVAL, "the last call on this device built no histogram with the canonical-form hash");
+    Workspace *w = it->second;
+    CUDA_TRY(cudaEventSynchronize(w->last));
+    const size_t nslot = size_t(1) << SHAPES_LOG2;
+    std::vector<unsigned long long> keys(nslot);
+    std::vector<unsigned> meta(nslot);
+    std::vector<uint32_t> rows(nslot * 32);
+    unsigned st[4] = {0, 0, 0, 0};
+    CUDA_TRY(cudaMemcpy(keys.data(), w->shapes.key, nslot * 8, cudaMemcpyDeviceToHost));
+    CUDA_TRY(cudaMemcpy(meta.data(), w->shapes.meta, nslot * 4, cudaMemcpyDeviceToHost));
+    CUDA_TRY(cudaMemcpy(rows.data(), w->shapes.rows, nslot * 128, cudaMemcpyDeviceToHost));
+    CUDA_TRY(cudaMemcpy(st, w->shapes.stats, 16, cudaMemcpyDeviceToHost));
+    std::vector<jatam_shape> all;
+    for (size_t i = 0; i < nslot; ++i) {
+        if (!keys[i]) continue;
+        jatam_shape e{};
+        e.shape_hash = (uint32_t)keys[i];
+        const unsigned m = meta[i];
+        e.h = (uint8_t)((m >> 8) & 0xFF);
+        e.w = (uint8_t)(m & 0xFF);
+        unsigned size = 0;
+        for (int r = 0; r < 32; ++r) {
+            // stored with the first cell in bit w - 1; returned with column j in bit j
+            const uint32_t v = rows[i * 32 + r];
+            uint32_t out = 0;
+            for (int j = 0; j < e.w; ++j)
+                if ((v >> (e.w - 1 - j)) & 1u) out |= 1u << j;
+            e.rows[r] = r < e.h ? out : 0u;
+            size += (unsigned)__builtin_popcount(e.rows[r]);
+        }
+        e.size = (uint16_t)size;
+        all.push_back(e);
+    }
+    std::sort(all.begin(), all.end(), [](const jatam_shape &x, const jatam_shape &y) { return x.shape_hash < y.shape_hash; });
+    *len = (uint32_t)all.size();
+    *collisions = st[0];
+    for (size_t i = 0; i < all.size() && i < cap; ++i) shapes[i] = all[i];
+    if (st[1]) return fail(JATAM_ETIMEOUT, "%u shape comparisons gave up waiting for the stored rows", st[1]);
+    if (st[2]) return fail(JATAM_ENOMEM, "the shape side table (%zu slots) overflowed %u times", nslot, st[2]);
+    if (all.size() > cap) return fail(JATAM_EINVAL, "%zu shapes but cap is %u", all.size(), cap);
+    return JATAM_OK;
+}
+
+int jatam_workspace_bytes(uint64_t *bytes)
+{
+    std::lock_guard<std::mutex> lock(g_mutex);
+    if (!bytes) return fail(JATAM_EINVAL, "bytes is NULL");
+    int dev = 0;
+    CUDA_TRY(cudaGetDevice(&dev));
+    auto it = g_ws.find(dev);
+    if (it == g_ws.end()) {
+        *bytes = 0;
+        return JATAM_OK;
+    }
+    const Workspace *w = it->second;
+    const size_t cap = size_t(1) << TABLE_LOG2;
+    size_t b = 2 * cap * (8 + 8 + 8 + 4 + 4);                  // phenotype table and its compacted copy
+    b += 3 * 8 + (size_t(2) << CROPS_LOG2) * 8 + 4 * 8 + 4 + 4 + 6 * 8;  // counters, crop table
+    b += ((size_t(8) + 4 + 128) << SHAPES_LOG2) + 4 * 4;                 // shape side table
+    b += w->list_bytes + w->stage_in_bytes + w->stage_out_bytes + w->stage_aux_bytes +
+         w->stage_hist_cap * sizeof(jatam_hist_entry) + w->lifo_bytes + w->ga_bytes + w->screen_bytes +
+         w->alt.list_bytes;
+    if (w->copy) b += 3 * 8 + 6 * 8 + 4 + (size_t(2) << CROPS_LOG2) * 8;
+    *bytes = b;
+    return JATAM_OK;
 }
 
 const char *jatam_last_error(void) { return g_last_error.c_str(); }

@@ -45,6 +45,22 @@ struct Compact {
     unsigned *size_min;
 };
 
+// Exact side table of one call's shapes: for every shape hash the call
+// computed, the canonical form it was computed from (open addressing by hash,
+// 2^log2 slots).  key: 0 free, else 2^32 | hash; meta: 0 until the inserting
+// warp has written the rows, then 2^31 | h << 8 | w; rows[32 slot + i]: row i
+// of the canonical form, its first cell in bit w - 1.  stats: [0] computed
+// forms that differed from the one stored under their hash (collisions),
+// [1] comparisons given up (a bounded wait for the rows ran out), [2] forms not
+// stored (the table was full).  key == nullptr: no table.
+struct ShapeTab {
+    unsigned long long *key;
+    unsigned *meta;
+    uint32_t *rows;
+    unsigned *stats;
+    unsigned log2;
+};
+
 struct LaunchArgs {
     int mode;
     unsigned long long first;     // first index (MODE_RANGE / MODE_SAMPLED)
@@ -80,6 +96,7 @@ struct LaunchArgs {
     unsigned long long *crops;      // null, or the crop table of the launch: 2^crops_log2 slots of
                                     // {crop bits, valid | h | w | hash}, cleared by the call's reset
     unsigned crops_log2;
+    ShapeTab shape_tab;             // the call's shape side table (key null: none)
 };
 
 // Lattice template: rows of S bits, S in {8, 16, 32}, L <= S; nt = 8 tuple ids
@@ -105,8 +122,15 @@ cudaError_t launch_classify_mixed(const LaunchArgs &a, int blocks, cudaStream_t 
 cudaError_t launch_reset(unsigned long long *work_next, unsigned *nkeys, unsigned long long *list_count,
                          cudaStream_t st, unsigned long long *crops = nullptr, unsigned crops_log2 = 0);
 cudaError_t launch_prefilter(const LaunchArgs &a, int smax, int blocks, cudaStream_t st);
+// load the reset and pre-filter kernels on the current device now (not at their first launch)
+cudaError_t load_index_range_kernels();
+// jatam_shutdown: forget the per-device set-up of jatam_enumerate_noalloc
+void noalloc_forget_devices();
 cudaError_t launch_table_init(Table t, cudaStream_t st);
-cudaError_t launch_hist_compact(Table t, Compact c, unsigned *nkeys, int blocks, cudaStream_t st);
+// also records the single-cell shape in `shapes` when a size-1 key is present
+// (the pre-filter settles those genotypes without computing a canonical form)
+cudaError_t launch_hist_compact(Table t, Compact c, unsigned *nkeys, int blocks, cudaStream_t st,
+                                ShapeTab shapes = ShapeTab{});
 cudaError_t launch_hist_emit(Compact c, const unsigned *nkeys, jatam_hist_entry *hist, unsigned cap,
                              uint32_t *hist_len, int blocks, cudaStream_t st);
 cudaError_t launch_philox(const uint32_t *in, unsigned long long n, uint32_t *out, cudaStream_t st);

@@ -300,11 +300,71 @@ __device__ __forceinline__ uint32_t c4_combine(uint32_t a, uint32_t b, uint32_t 
 }
 
 // ---------------------------------------------------------------------------
+// Exact side table of a call's shapes (Section 2.5 estimates the chance that
+// two distinct shapes share a 32-bit hash; the table settles it exactly): the
+// first warp that computes a hash stores the canonical form under it, every
+// later warp that computes the same hash compares its form with the stored
+// one.  A form is never computed from a cache hit (caches map an exact crop to
+// its hash), so every distinct form the call produces is compared at least
+// once.  All 32 lanes call it; lane i < h holds row i of the form.
+// ---------------------------------------------------------------------------
+constexpr int SHAPE_PROBES = 64;      // slots tried before a form is counted as not stored
+constexpr int SHAPE_WAIT = 1 << 16;   // polls of a slot whose rows are still being written
+
+__device__ __noinline__ void shape_record(const ShapeTab t, uint32_t hash, uint32_t row, int h, int w, int lane)
+{
+    const unsigned mask = (1u << t.log2) - 1u;
+    const unsigned long long key = (1ull << 32) | hash;
+    unsigned slot = (hash * 2654435761u) >> (32 - t.log2);
+    int state = 0;  // 1: stored by this warp, 2: present, 3: table full
+    if (lane == 0) {
+        for (int p = 0; p < SHAPE_PROBES; ++p) {
+            const unsigned long long old = atomicCAS(&t.key[slot], 0ull, key);
+            if (old == 0ull) { state = 1; break; }
+            if (old == key) { state = 2; break; }
+            slot = (slot + 1) & mask;
+        }
+        if (!state) state = 3;
+    }
+    state = __shfl_sync(FULL, state, 0);
+    slot = __shfl_sync(FULL, slot, 0);
+    const uint32_t mine = lane < h ? row : 0u;
+    const unsigned meta = 0x80000000u | ((unsigned)h << 8) | (unsigned)w;
+    if (state == 1) {
+        __stcg(&t.rows[(size_t)slot * 32 + lane], mine);
+        __threadfence();
+        __syncwarp();
+        if (lane == 0) atomicExch(&t.meta[slot], meta);
+    } else if (state == 2) {
+        unsigned m = 0;
+        if (lane == 0) {
+            // the storing warp writes its rows and then the meta word; it waits on
+            // nothing, so this bounded wait ends long before its limit
+            for (int it = 0; it < SHAPE_WAIT && m == 0; ++it) {
+                m = atomicOr(&t.meta[slot], 0u);
+                if (m == 0) __nanosleep(64);
+            }
+        }
+        m = __shfl_sync(FULL, m, 0);
+        if (m == 0) {
+            if (lane == 0) atomicAdd(&t.stats[1], 1u);
+        } else {
+            __threadfence();
+            const uint32_t have = __ldcg(&t.rows[(size_t)slot * 32 + lane]);
+            if (__any_sync(FULL, m != meta || have != mine) && lane == 0) atomicAdd(&t.stats[0], 1u);
+        }
+    } else if (lane == 0) {
+        atomicAdd(&t.stats[2], 1u);
+    }
+    __syncwarp();
+}
+
+// ---------------------------------------------------------------------------
 // warp-cooperative canonical form + hash of owner o's replicate-0 shape
 // ---------------------------------------------------------------------------
 template <int S>
 __device__ __forceinline__ uint32_t coop_shape_hash(int o, const uint32_t *warp_lanes, const Lane &Ls, int lane,
-                                                    bool c4)
+                                                    bool c4, const ShapeTab &tab)
 {
     using G = Geo<S>;
     const int x0 = __shfl_sync(FULL, Ls.x0, o), x1 = __shfl_sync(FULL, Ls.x1, o);
@@ -359,7 +419,9 @@ __device__ __forceinline__ uint32_t coop_shape_hash(int o, const uint32_t *warp_
         const uint32_t h5 = image_hash(v[5], w, h), h6 = image_hash(v[6], w, h);
         return c4_combine(h0, h3, h5, h6);
     }
-    return image_hash(best, hc, wc);
+    const uint32_t hv = image_hash(best, hc, wc);
+    if (tab.key) shape_record(tab, hv, best, hc, wc, lane);
+    return hv;
 }
 
 // W: the unsigned type that holds the colours (32 bits for at most two tiles).
@@ -1478,7 +1540,7 @@ __device__ __forceinline__ void warp_loop(const LaunchArgs &a, uint32_t *warp_la
         while (shp) {
             const int o = __ffs(shp) - 1;
             shp &= shp - 1;
-            const uint32_t hv = coop_shape_hash<S>(o, warp_lanes, Ls, lane, a.c4 != 0);
+            const uint32_t hv = coop_shape_hash<S>(o, warp_lanes, Ls, lane, a.c4 != 0, a.shape_tab);
             if (lane == o) {
                 Ls.hash = hv;
                 Ls.phase = PH_WRITE;
@@ -1634,13 +1696,55 @@ __global__ void table_init_kernel(Table t)
     }
 }
 
+// the single-cell shape (h = w = 1) in the side table, by one thread: the
+// pre-filter settles lone seeds without a warp computing their form
+__device__ void shape_record_cell(const ShapeTab t, uint32_t hash)
+{
+    const unsigned mask = (1u << t.log2) - 1u;
+    const unsigned long long key = (1ull << 32) | hash;
+    const unsigned meta = 0x80000000u | (1u << 8) | 1u;
+    unsigned slot = (hash * 2654435761u) >> (32 - t.log2);
+    for (int p = 0; p < SHAPE_PROBES; ++p) {
+        const unsigned long long old = atomicCAS(&t.key[slot], 0ull, key);
+        if (old == 0ull) {
+            for (int i = 0; i < 32; ++i) __stcg(&t.rows[(size_t)slot * 32 + i], i == 0 ? 1u : 0u);
+            __threadfence();
+            atomicExch(&t.meta[slot], meta);
+            return;
+        }
+        if (old == key) {
+            // the growth warps have finished (this is a later kernel); only a thread of
+            // this kernel storing the same hash may still be writing: a bounded wait
+            unsigned m = 0;
+            for (int it = 0; it < SHAPE_WAIT && m == 0; ++it) {
+                m = atomicOr(&t.meta[slot], 0u);
+                if (m == 0) __nanosleep(64);
+            }
+            if (m == 0) {
+                atomicAdd(&t.stats[1], 1u);
+                return;
+            }
+            __threadfence();
+            bool same = m == meta;
+            for (int i = 0; i < 32 && same; ++i) same = __ldcg(&t.rows[(size_t)slot * 32 + i]) == (i == 0 ? 1u : 0u);
+            if (!same) atomicAdd(&t.stats[0], 1u);
+            return;
+        }
+        slot = (slot + 1) & mask;
+    }
+    atomicAdd(&t.stats[2], 1u);
+}
+
 // move the used slots into a dense list and leave the table empty again
-__global__ void hist_compact_kernel(Table t, Compact c, unsigned *nkeys)
+__global__ void hist_compact_kernel(Table t, Compact c, unsigned *nkeys, ShapeTab shapes)
 {
     const unsigned cap = 1u << t.cap_log2;
     for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < cap; i += gridDim.x * blockDim.x) {
         const unsigned long long k = t.key[i];
         if (k == EMPTY_KEY) continue;
+        const unsigned cls = (unsigned)(k >> 32);
+        if (shapes.key && (cls == JATAM_DET_BOUNDED || cls == JATAM_ND_STERIC) && t.size_min[i] == 1u)
+            shape_record_cell(shapes, (uint32_t)k);
         const unsigned j = atomicAdd(nkeys, 1u);
         c.key[j] = k;
         c.count[j] = t.count[i];
@@ -1843,6 +1947,15 @@ cudaError_t launch_reset(unsigned long long *work_next, unsigned *nkeys, unsigne
     return cudaGetLastError();
 }
 
+cudaError_t load_index_range_kernels()
+{
+    // cudaFuncGetAttributes loads a kernel that lazy module loading has not yet loaded
+    cudaFuncAttributes fa;
+    cudaError_t e = cudaFuncGetAttributes(&fa, reset_kernel);
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, prefilter_kernel);
+    return e;
+}
+
 cudaError_t launch_prefilter(const LaunchArgs &a, int smax, int blocks, cudaStream_t st)
 {
     prefilter_kernel<<<blocks, 256, 0, st>>>(a, smax);
@@ -1855,9 +1968,9 @@ cudaError_t launch_table_init(Table t, cudaStream_t st)
     return cudaGetLastError();
 }
 
-cudaError_t launch_hist_compact(Table t, Compact c, unsigned *nkeys, int blocks, cudaStream_t st)
+cudaError_t launch_hist_compact(Table t, Compact c, unsigned *nkeys, int blocks, cudaStream_t st, ShapeTab shapes)
 {
-    hist_compact_kernel<<<blocks, 256, 0, st>>>(t, c, nkeys);
+    hist_compact_kernel<<<blocks, 256, 0, st>>>(t, c, nkeys, shapes);
     return cudaGetLastError();
 }
 
