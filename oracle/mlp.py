@@ -83,6 +83,37 @@ def forward_backward(params, x, labels, *, bf16=True):
     return loss, {"W1": gW1, "b1": gb1, "W2": gW2, "b2": gb2, "W3": gW3, "b3": gb3}, logits
 
 
+def magnitude_sums(params, x, labels, *, bf16=True):
+    """For every gradient element and every logit, the sum of the absolute
+    values of the terms of the dot product (plus bias) that forms it --
+    sum_i |a_i b_i| -- from the same rounded operands as forward_backward.
+    A floating-point sum of K terms differs from the exact one by at most
+    about K * u * sum_i |a_i b_i| (u the unit roundoff), which is what the
+    element-wise tolerances of the parity tests are built from."""
+    r = bf16_round if bf16 else (lambda a: np.asarray(a, np.float64))
+    W1, b1, W2, b2, W3, b3 = (np.asarray(params[k], np.float64) for k in ("W1", "b1", "W2", "b2", "W3", "b3"))
+    B = x.shape[0]
+    xq = r(x)
+    W1q, W2q, W3q = r(W1), r(W2), r(W3)
+    h1 = r(np.maximum(xq @ W1q + b1, 0.0))
+    h2 = r(np.maximum(h1 @ W2q + b2, 0.0))
+    logits = h2 @ W3q + b3
+    m = logits.max(axis=1, keepdims=True)
+    e = np.exp(logits - m)
+    p = e / e.sum(axis=1, keepdims=True)
+    d = p.copy()
+    d[np.arange(B), labels] -= 1.0
+    d /= B
+    dq = r(d)
+    dh2 = r((dq @ W3q.T) * (h2 > 0))
+    dh1 = r((dh2 @ W2q.T) * (h1 > 0))
+    a = np.abs
+    return {"logits": a(h2) @ a(W3q) + a(b3),
+            "W3": a(h2).T @ a(dq), "b3": a(d).sum(axis=0),
+            "W2": a(h1).T @ a(dh2), "b2": a(dh2).sum(axis=0),
+            "W1": a(xq).T @ a(dh1), "b1": a(dh1).sum(axis=0)}
+
+
 def predict(params, x, *, bf16=True):
     r = bf16_round if bf16 else (lambda a: np.asarray(a, np.float64))
     h1 = r(np.maximum(r(x) @ r(params["W1"]) + params["b1"], 0.0))

@@ -146,3 +146,64 @@ def test_mutation_counts_follow_poisson_per_edge():
     assert abs(p0 - np.exp(-12 * rate)) < 0.02
     none = O.ga_breed(parents, np.zeros(N, np.int32), 5, n=n, c=c, seed=14, tournament=1, mutation_thresholds=NONE)
     assert not none.any()
+
+
+def test_breed_draw_layout_rederived():
+    """Every word a child consumes, re-derived from Triton's Philox with the
+    documented layout -- word k of child i in generation g is word (k mod 4) of
+    Philox4x32-10(ctr = (k >> 2, (2 << 24) | g, i_lo, i_hi), key = seed), in
+    the order: selection of parent A (T words, or one roulette dart), of
+    parent B, the crossover decision, two cut/mask words, one Poisson word per
+    edge, four bit-choice words per edge -- and the operators applied by hand:
+    selection (Section 2.2), one-point / uniform crossover and single-bit
+    mutations of an edge (the appendix listings of the operators)."""
+    from triton_philox import triton_philox
+
+    n, c, b = 3, 8, 3
+    bits = 4 * n * b
+    N, gen, seed = 12, 7, 0x0123456789ABCDEF
+    rng = np.random.default_rng(4)
+    parents = rng.integers(0, 1 << bits, size=N, dtype=np.int64).astype(np.uint64)
+    fitness = rng.integers(0, 20, size=N).astype(np.int32)
+    fitness[[2, 5]] = 0
+    thr = O.poisson_thresholds(0.7)  # many mutation events, up to the cap of 4
+    configs = [(O.TOURNAMENT, 4, O.ONE_POINT), (O.ROULETTE, 1, O.UNIFORM), (O.TOURNAMENT, 2, O.NO_CROSSOVER)]
+    for selection, T, crossover in configs:
+        got = O.ga_breed(parents, fitness, gen, n=n, c=c, seed=seed, selection=selection, tournament=T,
+                         crossover=crossover, crossover_threshold=1 << 31, mutation_thresholds=thr)
+        K = 2 * T + 3 + 4 * n + 4 * 4 * n
+        nblk = (K + 3) // 4
+        for i in range(N):
+            blocks = triton_philox([[q, (2 << 24) | gen, i, 0] for q in range(nblk)],
+                                   [seed & 0xFFFFFFFF, seed >> 32])
+            w = [blocks[k >> 2][k & 3] for k in range(K)]
+
+            def select(k0):
+                if selection == O.TOURNAMENT:
+                    best = None
+                    for j in range(T):
+                        idx = (w[k0 + j] * N) >> 32
+                        if best is None or fitness[idx] > fitness[best]:
+                            best = idx
+                    return best
+                total = int(np.maximum(fitness, 0).sum())
+                if total == 0:
+                    return (w[k0] * N) >> 32
+                dart = (w[k0] * total) >> 32
+                return int(np.argmax(np.cumsum(np.maximum(fitness, 0)) > dart))
+
+            a, bb = int(parents[select(0)]), int(parents[select(T)])
+            child = a
+            if crossover != O.NO_CROSSOVER and w[2 * T] < (1 << 31):
+                if crossover == O.ONE_POINT:
+                    cut = 1 + ((w[2 * T + 1] * (bits - 1)) >> 32)
+                    low = (1 << cut) - 1
+                else:
+                    low = (w[2 * T + 2] << 32) | w[2 * T + 1]
+                child = (a & ~low) | (bb & low)
+            for e in range(4 * n):
+                events = sum(1 for t in thr if w[2 * T + 3 + e] >= t)
+                pos = b * (4 * (n - 1 - e // 4) + (3 - e % 4))
+                for m in range(events):
+                    child ^= 1 << (pos + ((w[2 * T + 3 + 4 * n + 4 * e + m] * b) >> 32))
+            assert int(got[i]) == child & ((1 << bits) - 1), (selection, T, crossover, i)

@@ -67,3 +67,23 @@ def test_class_buckets():
     res["cls"] = [3, 1, 2, 0, 0, 0, 0, 0, 0]
     res["size"] = [0, 0, 9, 1, 3, 4, 15, 16, 200]
     assert M.class_of(res).tolist() == [0, 1, 2, 3, 4, 5, 6, 7, 7]
+
+
+def test_adam_step_matches_torch_optim_adam():
+    """The oracle's Adam (Kingma & Ba 2015, bias-corrected moments, eps outside
+    the square root) equals torch.optim.Adam in float64 over several steps."""
+    torch = pytest.importorskip("torch")
+    rng = np.random.default_rng(8)
+    params = {k: v + 0.01 * rng.standard_normal(v.shape) for k, v in M.init_params(8).items()}
+    tp = {k: torch.tensor(v.copy(), dtype=torch.float64, requires_grad=True) for k, v in params.items()}
+    opt = torch.optim.Adam(list(tp.values()), lr=3e-3, betas=(0.9, 0.999), eps=1e-8)
+    state = {}
+    for step in range(5):
+        grads = {k: rng.standard_normal(v.shape) * 10.0 ** rng.uniform(-9, 1, v.shape) for k, v in params.items()}
+        grads["b3"][0] = 0.0  # a zero gradient leaves the parameter in place on the first step
+        for k in tp:
+            tp[k].grad = torch.tensor(grads[k], dtype=torch.float64)
+        opt.step()
+        M.adam_step(params, grads, state, lr=3e-3)
+        for k in params:
+            assert np.allclose(params[k], tp[k].detach().numpy(), rtol=1e-12, atol=1e-15), (step, k)

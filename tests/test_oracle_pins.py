@@ -11,6 +11,7 @@ import pytest
 
 from oracle import bruteforce as B
 from oracle import oracle as O
+from triton_philox import triton_philox as _triton_philox
 
 N_, E_, S_, W_ = 0, 1, 2, 3
 
@@ -18,35 +19,6 @@ N_, E_, S_, W_ = 0, 1, 2, 3
 # ---------------------------------------------------------------------------
 # Philox4x32-10 (Salmon et al., SC'11) against an independent implementation
 # ---------------------------------------------------------------------------
-def _triton_philox(ctrs, key):
-    """Philox4x32-10 words from Triton's own implementation (run by its CPU
-    interpreter), a library routine written independently of the oracle."""
-    os.environ["TRITON_INTERPRET"] = "1"
-    triton = pytest.importorskip("triton")
-    tl = pytest.importorskip("triton.language")
-    torch = pytest.importorskip("torch")
-
-    @triton.jit
-    def kern(out_ptr, c_ptr, seed, NB: tl.constexpr):
-        i = tl.arange(0, NB)
-        c0 = tl.load(c_ptr + 4 * i + 0)
-        c1 = tl.load(c_ptr + 4 * i + 1)
-        c2 = tl.load(c_ptr + 4 * i + 2)
-        c3 = tl.load(c_ptr + 4 * i + 3)
-        a, b, c, d = tl.philox(seed, c0, c1, c2, c3, 10)
-        tl.store(out_ptr + 4 * i + 0, a)
-        tl.store(out_ptr + 4 * i + 1, b)
-        tl.store(out_ptr + 4 * i + 2, c)
-        tl.store(out_ptr + 4 * i + 3, d)
-
-    nb = len(ctrs)
-    cbuf = torch.tensor(np.array(ctrs, dtype=np.uint32).reshape(-1).view(np.int32))
-    out = torch.zeros(4 * nb, dtype=torch.int32)
-    seed = (int(key[1]) << 32) | int(key[0])
-    kern[(1,)](out, cbuf, seed, NB=nb)
-    return out.numpy().view(np.uint32).reshape(nb, 4).tolist()
-
-
 def test_philox_matches_independent_implementation():
     rng = random.Random(11)
     for key in ([0, 0], [3, 0], [0xFFFFFFFF, 0xFFFFFFFF], [rng.getrandbits(32), rng.getrandbits(32)]):
@@ -54,6 +26,24 @@ def test_philox_matches_independent_implementation():
         want = _triton_philox(ctrs, key)
         got = [O.philox(c, key) for c in ctrs]
         assert got == want
+
+
+def test_sampled_genotypes_rederived_from_triton_philox():
+    """The sampled workload of S_{3,8} (and of other spaces): genotype i is
+    words 0 and 1 of Philox4x32-10(ctr = (0, 1 << 24, i_lo, i_hi), key = seed)
+    as (w1 << 32 | w0), masked to the 4 n log2(c) genome bits -- re-derived
+    here from Triton's Philox, on indices below and above 2^32."""
+    rng = random.Random(5)
+    idx = [0, 1, 2, (1 << 28) - 1, 1 << 32, (1 << 40) + 3] + [rng.getrandbits(36) for _ in range(20)]
+    for (n, c, seed) in ((3, 8, 3), (2, 8, 2), (4, 8, 0xDEADBEEF12345678), (2, 4, 1)):
+        bits = 4 * n * (c.bit_length() - 1)
+        words = _triton_philox([[0, 1 << 24, i & 0xFFFFFFFF, i >> 32] for i in idx],
+                               [seed & 0xFFFFFFFF, seed >> 32])
+        for i, w in zip(idx, words):
+            want = ((w[1] << 32) | w[0]) & ((1 << bits) - 1)
+            assert O.sample_genotype(i, n, c, seed) == want, (n, c, seed, i)
+        assert O.sample_genotypes(idx[0], 3, n, c, seed).tolist() == [O.sample_genotype(i, n, c, seed)
+                                                                     for i in range(3)]
 
 
 # ---------------------------------------------------------------------------
@@ -473,3 +463,46 @@ def test_c4_hash_mode_changes_only_the_hash():
     shaped = (d4["cls"] == O.DET_BOUNDED) | (d4["cls"] == O.ND_STERIC)
     assert shaped.any() and not np.array_equal(d4["shape_hash"][shaped], c4["shape_hash"][shaped])
     assert not c4["shape_hash"][~shaped].any()
+
+
+# ---------------------------------------------------------------------------
+# exact side table of the shape hash (Section 2.5)
+# ---------------------------------------------------------------------------
+def test_shape_table_counts_a_planted_collision():
+    """The side table's collision rule on planted forms: the same hash for the
+    2 x 2 square and the L-tromino is one collision; the same form again is
+    none; a different hash is none."""
+    square = np.ones((2, 2), np.uint8)
+    ltro = np.array([[1, 1], [1, 0]], np.uint8)
+    with O.shape_table() as T:
+        T.add(5, square)
+        T.add(5, square)
+        T.add(6, ltro)
+        T.add(5, ltro)
+    assert T.collisions == 1 and T.overflow == 0
+    assert set(T.forms) == {5, 6}
+    assert np.array_equal(T.forms[5], square) and np.array_equal(T.forms[6], ltro)
+
+
+def test_shape_table_of_s24_holds_canonical_forms_of_every_shaped_key():
+    """All of S_{2,4}: the table holds exactly the hashes of the histogram's
+    shaped keys, each stored form is its own canonical form (invariant under
+    the 8 symmetries: canonical(cells) gives it back) and re-hashes to its key,
+    and no two forms collide; each key's form is the canonical form of its
+    smallest genotype's replicate-0 shape."""
+    n, c, L, k, seed = 2, 4, 16, 10, 1
+    with O.shape_table() as T:
+        res, _ = O.enumerate_space(n, c, L, k, seed, 0, 1 << 16)
+    assert T.collisions == 0 and T.overflow == 0
+    h = O.histogram(res)
+    shaped = h[(h["cls"] == 0) | (h["cls"] == 2)]
+    assert sorted(T.forms) == sorted(set(int(v) for v in shaped["shape_hash"]))
+    for key, bm in T.forms.items():
+        cells = [(x, y) for y in range(bm.shape[0]) for x in range(bm.shape[1]) if bm[y, x]]
+        assert np.array_equal(O.canonical(cells), bm)
+        assert O.shape_hash(bm) == key
+    for row in shaped:
+        g = int(row["min_id"])
+        r = O.classify(n, c, L, k, seed, O.decode(g, n, c), g, want_grid=True)
+        cells = [(x, y) for y in range(L) for x in range(L) if r["grid"][y, x] >= 0]
+        assert np.array_equal(O.canonical(cells), T.forms[int(row["shape_hash"])])
