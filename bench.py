@@ -38,6 +38,7 @@ OPS_PER_PLACEMENT = 62
 OPS_PER_REPLICATE = 37
 OPS_PER_GENOTYPE = 300
 OPS_PER_SHAPED_CELL = 24
+SOAK_S = 1.2  # seconds of back-to-back steps inside the clock record before the timed steps
 
 
 def _env_rank():
@@ -49,7 +50,7 @@ class ClockSampler:
 
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
-              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap,utilization.gpu")
 
     def __init__(self, gpu_index: int):
         self.gpu = gpu_index
@@ -83,7 +84,10 @@ class ClockSampler:
                 self.t.join(timeout=2)
 
     def summary(self):
-        sm, smax, reasons = [], [], set()
+        """Median SM clock over the samples taken under load (GPU utilisation of
+        at least 50 %; all samples if the field is unavailable), the maximum
+        clock, and every throttle reason seen active."""
+        sm, smax, util, reasons = [], [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         for line in self.lines:
             p = [x.strip() for x in line.split(",")]
@@ -94,13 +98,19 @@ class ClockSampler:
                 smax.append(float(p[2]))
             except ValueError:
                 continue
+            try:
+                util.append(float(p[9]) if len(p) > 9 else -1.0)
+            except ValueError:
+                util.append(-1.0)
             for name, v in zip(names, p[5:9]):
                 if v.lower() == "active":
                     reasons.add(name)
         if not sm:
-            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
-        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(smax)), "reasons": sorted(reasons),
-                "samples": len(sm)}
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0,
+                    "samples_under_load": 0}
+        loaded = [c for c, u in zip(sm, util) if u >= 50.0]
+        return {"sm_mhz": float(np.median(loaded if loaded else sm)), "sm_max_mhz": float(max(smax)),
+                "reasons": sorted(reasons), "samples": len(sm), "samples_under_load": len(loaded)}
 
 
 def measured_peaks():
@@ -199,7 +209,27 @@ def WORKLOAD_SPEC():
 MIXED_COUNT = 10_000_000
 
 
-def mixed_arm(args, torch, J, dev):
+def _timed_steps(torch, stream, flush, steps, fn, J=None):
+    """Mean CUDA-event time of `steps` calls of fn on `stream`, a buffer larger
+    than L2 written before each; with J, also the mean growth-kernel time of
+    the profiling mode."""
+    st = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    en = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    kms = []
+    for i in range(steps):
+        with torch.cuda.stream(stream):
+            flush.fill_(i & 255)
+            st[i].record(stream)
+            fn()
+            en[i].record(stream)
+        if J is not None:
+            kms.append(J.last_kernel_ms())
+    torch.cuda.synchronize()
+    ms = float(np.mean([a.elapsed_time(b) for a, b in zip(st, en)]))
+    return ms, (float(np.mean(kms)) if kms else None)
+
+
+def measure_mixed(torch, J, dev, steps, warmup):
     """Batched uneven workload: 10^7 explicit tile sets with n in {2,3,4},
     c in {4,6,8}, L in {8,16,32}, k in {10,20} (seed 4) in one persistent,
     graph-captured launch whose CTA plan the autotuner picks; the per-size
@@ -218,67 +248,58 @@ def mixed_arm(args, torch, J, dev):
     plan = J.get_mixed_plan()
     choice = J.get_mixed_launch()
 
-    def timed(per_shape, graph):
-        for _ in range(args.warmup):
-            J.classify_batch(dc, seed=4, shapes=ds, out=out, hist=hist, hist_len=hlen, hist_cap=hist_cap,
-                             stream=stream, per_shape=per_shape, graph=graph)
-        stream.synchronize()
-        st = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-        en = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-        kms = []
-        for i in range(args.steps):
-            with torch.cuda.stream(stream):
-                flush.fill_(i & 255)
-                st[i].record(stream)
-                J.classify_batch(dc, seed=4, shapes=ds, out=out, hist=hist, hist_len=hlen, hist_cap=hist_cap,
-                                 stream=stream, per_shape=per_shape, graph=graph)
-                en[i].record(stream)
-            kms.append(J.last_kernel_ms())
-        torch.cuda.synchronize()
-        return float(np.mean([a.elapsed_time(b) for a, b in zip(st, en)])), float(np.mean(kms))
+    def call(per_shape, graph):
+        J.classify_batch(dc, seed=4, shapes=ds, out=out, hist=hist, hist_len=hlen, hist_cap=hist_cap,
+                         stream=stream, per_shape=per_shape, graph=graph)
 
     J.jatam_profile(1)
+    res = {}
+    for name, per_shape, graph in (("persistent_graph", False, True), ("per_size_fixed", True, False)):
+        for _ in range(warmup):
+            call(per_shape, graph)
+        stream.synchronize()
+        ms, kms = _timed_steps(torch, stream, flush, steps, lambda: call(per_shape, graph), J)
+        res[name] = {"value": MIXED_COUNT / (ms / 1e3), "ms_per_step": round(ms, 4), "growth_kernels_ms": round(kms, 4)}
+    J.jatam_profile(0)
+    return {"workload": "mixed: 10^7 tile sets, n in {2,3,4}, c in {4,6,8}, L in {8,16,32}, k in {10,20}, seed 4",
+            "unit": UNIT, "value": res["persistent_graph"]["value"], "steps": steps, "warmup": warmup,
+            "persistent_graph": res["persistent_graph"], "per_size_fixed": res["per_size_fixed"],
+            "plan_w32_w16_w8": list(plan), "autotuner_default_launch": "per_size" if choice else "persistent",
+            "distinct_phenotypes": int(hlen.item())}
+
+
+def mixed_arm(args, torch, J, dev):
     with ClockSampler(int(str(dev).split(":")[-1]) if ":" in str(dev) else 0) as clocks:
-        ms, kms = timed(False, True)
-    ms_fixed, kms_fixed = timed(True, False)
+        m = measure_mixed(torch, J, dev, args.steps, args.warmup)
     line = {
-        "metric": METRIC, "value": MIXED_COUNT / (ms / 1e3), "unit": UNIT, "n_gpus": 1, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "u32", "data": "synthetic",
-        "config": {"workload": "mixed: 10^7 tile sets, n in {2,3,4}, c in {4,6,8}, L in {8,16,32}, k in {10,20}, "
-                               "seed 4", "launch": "one persistent launch, CUDA graph replay",
-                   "plan_w32_w16_w8": list(plan), "growth_kernels_ms": round(kms, 4),
-                   "autotuner_default_launch": choice,
-                   "per_shape_fixed_launches": {"ms_per_step": round(ms_fixed, 4),
-                                                "growth_kernels_ms": round(kms_fixed, 4),
-                                                "value": MIXED_COUNT / (ms_fixed / 1e3)},
-                   "distinct_phenotypes": int(hlen.item())},
-        "e2e": None, "gpu_launches": 5 * args.steps, "roofline": None, "cpu_baseline": None,
+        "metric": METRIC, "value": m["value"], "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": m["persistent_graph"]["ms_per_step"], "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+        "config": m, "e2e": None, "gpu_launches": 5 * args.steps, "roofline": None, "cpu_baseline": None,
         "clocks": clocks.summary(),
     }
     print(json.dumps(line), flush=True)
     return 0
 
 
-def ga_arm(args, torch, J, dev):
+def measure_ga(torch, J, dev, seed=5, N=8192, G=500, ratio=4, train_steps=3000):
     """The GA of the fifth configuration (n = 3, c = 8 genomes, population
     8192, 500 generations, per-edge mutation rate 0.01, tournament of 4, shape
-    fitness at L = 16, k = 20, seed 5), plain and with the surrogate network as
-    a pre-screen (trained first on labels the library's classification gives:
+    fitness at L = 16, k = 20), plain and with the surrogate network as a
+    pre-screen (trained first on labels the library's classification gives:
     S_{2,4} in full, a uniform sample of S_{2,8}, and a uniform sample of
-    S_{3,8} at the GA's L and k).  Every reported fitness is simulated; the
-    line gives genomes simulated per second and, per arm, the generation at
-    which the verified best fitness first reached each level."""
+    S_{3,8} at the GA's L and k).  Every reported fitness is simulated; per
+    arm: genomes simulated per second, the best verified fitness, and the
+    generation (and simulations) at which it was first reached."""
     from paper_2205_15311_gb300 import surrogate as S
     from paper_2205_15311_gb300 import workloads as W
-    N, G, ratio, seed = 8192, 500, 4, 5
     genomes, labels = S.build_training_set(torch, dev, s28_sample=1 << 21, s38_sample=1 << 21)
     perm = torch.from_numpy(np.random.default_rng(seed).permutation(genomes.shape[0])).to(dev)
     genomes, labels = genomes[perm].contiguous(), labels[perm].contiguous()
     net = J.Surrogate(max_batch=max(N * ratio, 1 << 15))
     net.set_params(S.initial_params(seed))
     t0 = time.perf_counter()
-    S.train(torch, net, genomes, labels, steps=3000, batch=8192, lr=2e-3)
+    S.train(torch, net, genomes, labels, steps=train_steps, batch=8192, lr=2e-3)
     torch.cuda.synchronize()
     train_s = time.perf_counter() - t0
     trained = net.get_params()
@@ -303,23 +324,81 @@ def ga_arm(args, torch, J, dev):
         ms = a.elapsed_time(b)
         so_far = np.maximum.accumulate(best)
         first = {int(v): int(np.argmax(so_far >= v)) for v in sorted(set(so_far.tolist()))}
+        g_best = first[int(so_far[-1])]
         arms[mode] = {"genomes_per_s": N * G / (ms / 1e3), "ms": round(ms, 1), "best": int(so_far[-1]),
+                      "generation_of_best": g_best, "simulations_to_best": (g_best + 1) * N,
                       "first_generation_reaching": first}
     net.close()
+    return {"workload": f"ga: n=3 c=8, population {N}, {G} generations, per-edge mutation 0.01, tournament 4, "
+                        f"shape fitness L=16 k=20, seed {seed}",
+            "unit": "genomes/s", "value": arms["plain"]["genomes_per_s"],
+            "surrogate": f"36-256-256-8 bf16, {train_steps} Adam steps of 8192 on S_{{2,4}} + 2M S_{{2,8}} + "
+                         f"2M S_{{3,8}} labels ({train_s:.1f} s); screen ratio {ratio}, online lr 1e-3",
+            "plain": arms["plain"], "screened": arms["screened"]}
+
+
+def ga_arm(args, torch, J, dev):
+    m = measure_ga(torch, J, dev)
     line = {
         "metric": "GA genomes simulated/s (every survivor classified; plain vs surrogate-screened)",
-        "value": arms["plain"]["genomes_per_s"], "unit": "genomes/s", "n_gpus": 1, "steps": G, "warmup": 0,
-        "ms_per_step": arms["plain"]["ms"] / G, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "u32", "data": "synthetic",
-        "config": {"workload": "ga: n=3 c=8, population 8192, 500 generations, per-edge mutation 0.01, "
-                               "tournament 4, shape fitness L=16 k=20, seed 5",
-                   "surrogate": f"36-256-256-8 bf16, 3000 Adam steps of 8192 on S_{{2,4}} + 2M S_{{2,8}} + 2M S_{{3,8}} "
-                                f"labels ({train_s:.1f} s); screen ratio {ratio}, online lr 1e-3",
-                   "plain": arms["plain"], "screened": arms["screened"]},
+        "value": m["value"], "unit": "genomes/s", "n_gpus": 1, "steps": 500, "warmup": 0,
+        "ms_per_step": m["plain"]["ms"] / 500, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "u32", "data": "synthetic", "config": m,
         "e2e": None, "gpu_launches": None, "roofline": None, "cpu_baseline": None,
     }
     print(json.dumps(line), flush=True)
     return 0
+
+
+def measure_enumeration(torch, J, dev, name, steps, warmup, top_shapes=0):
+    """One of the enumerated or sampled workloads, timed like the bench line;
+    with top_shapes, the largest deterministic bounded shapes of its histogram
+    (size, hash, genotypes, smallest genotype)."""
+    from paper_2205_15311_gb300 import workloads as W
+    n, c, L, k, seed, first, count, sampled = W.WORKLOADS[name]
+    hist_cap = 1 << 16
+    stream = torch.cuda.Stream(device=dev)
+    out = torch.empty(count * 8, dtype=torch.uint8, device=dev)
+    hist = torch.empty(hist_cap * 32, dtype=torch.uint8, device=dev)
+    hlen = torch.zeros(1, dtype=torch.int32, device=dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+
+    def call():
+        J.enumerate_space(n, c, L, k, seed, first, count, sampled=sampled, out=out, hist=hist, hist_len=hlen,
+                          hist_cap=hist_cap, stream=stream)
+
+    J.jatam_profile(1)
+    with torch.cuda.stream(stream):
+        for _ in range(warmup):
+            call()
+    stream.synchronize()
+    ms, kms = _timed_steps(torch, stream, flush, steps, call, J)
+    J.jatam_profile(0)
+    m = int(hlen.item())
+    r = {"workload": f"{name}: {'sampled' if sampled else 'all'} {count} genotypes of S_{{{n},{c}}}, "
+                     f"L={L} k={k} seed={seed}", "unit": UNIT, "value": count / (ms / 1e3), "ms_per_step": round(ms, 4),
+         "growth_kernels_ms": round(kms, 4), "steps": steps, "warmup": warmup, "distinct_phenotypes": m}
+    if top_shapes:
+        h = J.hist_view(hist, min(m, hist_cap))
+        det = [x for x in h.tolist() if x[0] == 0]
+        det.sort(key=lambda x: (-x[2], -x[4], x[1]))
+        r["largest_det_shapes"] = [{"size": int(x[2]), "shape_hash": int(x[1]), "genotypes": int(x[4]),
+                                    "min_genotype": int(x[5])} for x in det[:top_shapes]]
+    del out
+    return r
+
+
+def measure_configs(torch, J, dev, steps, warmup):
+    """The other configurations, measured in the same run as the bench line."""
+    cfg = {}
+    cfg["c1_s24_full"] = measure_enumeration(torch, J, dev, "s24_full", steps, warmup)
+    cfg["c3_s38_sample"] = measure_enumeration(torch, J, dev, "s38_sample", steps, warmup, top_shapes=8)
+    torch.cuda.empty_cache()
+    cfg["c4_mixed"] = measure_mixed(torch, J, dev, steps, warmup)
+    torch.cuda.empty_cache()
+    cfg["c5_ga"] = measure_ga(torch, J, dev)
+    torch.cuda.empty_cache()
+    return cfg
 
 
 KSWEEP = (1, 2, 4, 8, 16, 20, 32, 64, 128)
@@ -420,6 +499,9 @@ def main():
                     help="orbit mode (JATAM_ORBITS): one classification per orbit of the exact symmetries; "
                          "a measurement, not the bench line")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end leg")
+    ap.add_argument("--no-configs", action="store_true",
+                    help="skip the other configurations (S_{2,4}, the 2^28 S_{3,8} sample, the 10^7 mixed "
+                         "batch, the GA arms) measured after the bench line")
     ap.add_argument("--profile-genomes", type=int, default=0,
                     help="instead of the bench: ga_evaluate on this many uniform random genomes of the "
                          "workload's space (a representative small case for ncu); prints timings only")
@@ -490,6 +572,15 @@ def main():
     work = J.work_counters()
     J.jatam_profile(1)
 
+    # a sustained run of at least SOAK_S seconds of back-to-back steps just before the timed steps, inside
+    # the clock record: the sampler sees the GPU under load even when the timed steps are short
+    est = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    est[0].record(stream)
+    with torch.cuda.stream(stream):
+        step()
+    est[1].record(stream)
+    torch.cuda.synchronize()
+    soak_steps = max(1, int(np.ceil(SOAK_S * 1e3 / max(est[0].elapsed_time(est[1]), 1e-3))))
     starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     stops = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     kernel_ms = []
@@ -497,6 +588,12 @@ def main():
         dist.barrier()
     torch.cuda.synchronize()
     with ClockSampler(local) as clocks:
+        soak = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        soak[0].record(stream)
+        with torch.cuda.stream(stream):
+            for _ in range(soak_steps):
+                step()
+        soak[1].record(stream)
         for i in range(args.steps):
             with torch.cuda.stream(stream):
                 flush.fill_(i & 255)
@@ -507,6 +604,7 @@ def main():
         torch.cuda.synchronize()
     if world > 1:
         dist.barrier()
+    soak_ms = soak[0].elapsed_time(soak[1])
     step_ms = [s.elapsed_time(e) for s, e in zip(starts, stops)]
     ms = float(np.mean(step_ms))
     if world > 1:
@@ -587,6 +685,10 @@ def main():
             units, dt = run_oracle_sample(cores)
             cpu = {"value": units / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
                    "sample": f"{cpu_sample_text()} ({units} genotypes, {dt:.1f} s)"}
+        configs = None
+        if world == 1 and not args.no_configs and WORKLOAD == "s28_full" and not (args.count or args.orbits
+                                                                                  or args.lifo):
+            configs = measure_configs(torch, J, dev, steps=5, warmup=3)
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
@@ -597,7 +699,13 @@ def main():
                                    f"S_{{{n},{c}}}, n={n} c={c} L={L} k={k} seed={seed0}",
                        "global_batch": world * count, "parallelism": f"replicas x{world}",
                        "l2": "256 MB buffer written between timed steps; outputs 134 MB > L2",
-                       "distinct_phenotypes": nk},
+                       "distinct_phenotypes": nk,
+                       "sustained": {"steps": soak_steps, "seconds": round(soak_ms / 1e3, 3),
+                                     "ms_per_step": round(soak_ms / soak_steps, 4),
+                                     "value": world * count / (soak_ms / soak_steps / 1e3),
+                                     "note": "back-to-back steps just before the timed ones, no L2 flush; "
+                                             "the clock record covers them and the timed steps"}},
+            "configs": configs,
             "e2e": None if not e2e_times else {"value": world * count / e2e_s, "unit": UNIT,
                                                "h2d_bytes_per_step": 0,
                                                "d2h_bytes_per_step": count * 8 + nk * 32 + 8},

@@ -1,6 +1,6 @@
 """Write the stored expected values under tests/golden/ -- calls only oracle/.
 
-    python tests/golden/make_golden.py [c1] [c2] [c3]
+    python tests/golden/make_golden.py [c1] [c2] [c3s] [c3] [c4s] [c4]
 
 For each workload it runs the CPU oracle and stores:
   * the SHA-256 of the per-genotype result array (8 bytes per genotype:
@@ -34,7 +34,7 @@ WORKLOADS = {
 }
 
 
-def write_mixed(name, count, seed):
+def write_mixed(name, count, seed, histogram_file=False):
     """Explicit mixed-size tile sets from the seeded input generator (its
     SplitMix64 streams are the inputs; every result comes from the oracle)."""
     from paper_2205_15311_gb300 import workloads as WL  # input generator only
@@ -56,12 +56,102 @@ def write_mixed(name, count, seed):
     with open(os.path.join(HERE, f"{name}_summary.json"), "w") as f:
         json.dump(meta, f, indent=1)
         f.write("\n")
+    if histogram_file:
+        with open(os.path.join(HERE, f"{name}_histogram.txt"), "w") as f:
+            f.write("# cls shape_hash size count min_id\n")
+            for h in hist:
+                f.write(f"{int(h['cls'])} {int(h['shape_hash'])} {int(h['size'])} {int(h['count'])} "
+                        f"{int(h['min_id'])}\n")
+    print(name, meta, flush=True)
+
+
+def largest_shapes(rows, n, c, L, k, seed, top=12):
+    """The largest deterministic bounded shapes of a histogram: (size, hash,
+    count, smallest id) of the DET keys with the most tiles, each with the
+    canonical bitmap of its smallest genotype's replicate-0 shape as text rows
+    ('#' occupied), from the oracle."""
+    det = sorted((r for r in rows if r[0] == O.DET_BOUNDED), key=lambda r: (-r[2], -r[3], r[1]))[:top]
+    out = []
+    for cls, h, size, count, min_id in det:
+        r = O.classify(n, c, L, k, seed, O.decode(min_id, n, c), min_id, want_grid=True)
+        cells = [(x, y) for y in range(L) for x in range(L) if r["grid"][y, x] >= 0]
+        bm = O.canonical(cells)
+        assert r["cls"] == cls and r["shape_hash"] == h and len(cells) == size
+        out.append({"size": size, "shape_hash": h, "count": count, "min_id": min_id,
+                    "canonical": ["".join("#" if v else "." for v in row) for row in bm]})
+    return out
+
+
+def write_sampled_chunked(name, n, c, L, k, seed, count, chunk):
+    """A sampled workload too large to hold at once: classified in chunks of
+    `chunk` indices; the SHA-256 covers the whole result array (and one digest
+    per chunk is kept), the histogram is merged over the chunks."""
+    sha = hashlib.sha256()
+    chunk_sha, cls_counts, placements, keys = [], np.zeros(4, np.int64), 0, {}
+    t0 = time.time()
+    for first in range(0, count, chunk):
+        m = min(chunk, count - first)
+        res, pl = O.enumerate_space(n, c, L, k, seed, first, m, sampled=True)
+        placements += int(pl)
+        b = res.tobytes()
+        sha.update(b)
+        chunk_sha.append(hashlib.sha256(b).hexdigest())
+        cls_counts += np.bincount(res["cls"], minlength=4)
+        ids = O.sample_genotypes(first, m, n, c, seed)
+        sizes = {}
+        for kk in O.size_collisions(res).tolist():
+            sizes[kk] = True
+        for h in O.histogram(res, ids):
+            key = (int(h["cls"]), int(h["shape_hash"]))
+            cur = keys.get(key)
+            sz, cnt, mid = int(h["size"]), int(h["count"]), int(h["min_id"])
+            if cur is None:
+                keys[key] = [sz, sz, cnt, mid]
+            else:
+                cur[0], cur[1] = max(cur[0], sz), min(cur[1], sz)
+                cur[2] += cnt
+                cur[3] = min(cur[3], mid)
+        print(name, first + m, "of", count, round(time.time() - t0, 1), "s", flush=True)
+    dt = time.time() - t0
+    rows = [(kk[0], kk[1], v[0], v[2], v[3]) for kk, v in sorted(keys.items())]
+    collisions = sum(1 for v in keys.values() if v[0] != v[1])
+    meta = {
+        "workload": {"n": n, "c": c, "L": L, "k": k, "seed": seed, "first": 0, "count": count,
+                     "sampled": True},
+        "results_sha256": sha.hexdigest(),
+        "chunk": chunk,
+        "chunk_sha256": chunk_sha,
+        "class_counts": cls_counts.tolist(),
+        "placements": int(placements),
+        "distinct_keys": len(rows),
+        "oracle_seconds": round(dt, 1),
+        "oracle_threads": O.default_threads(),
+        "collisions": int(collisions),
+    }
+    with open(os.path.join(HERE, f"{name}_summary.json"), "w") as f:
+        json.dump(meta, f, indent=1)
+        f.write("\n")
+    with open(os.path.join(HERE, f"{name}_histogram.txt"), "w") as f:
+        f.write("# cls shape_hash size count min_id\n")
+        for r in rows:
+            f.write(" ".join(str(v) for v in r) + "\n")
+    with open(os.path.join(HERE, f"{name}_largest.json"), "w") as f:
+        json.dump(largest_shapes(rows, n, c, L, k, seed), f, indent=1)
+        f.write("\n")
     print(name, meta, flush=True)
 
 
 def write(name):
     if name == "c4s":
         return write_mixed(name, 1_000_000, 4)
+    if name == "c4":
+        return write_mixed(name, 10_000_000, 4, histogram_file=True)
+    if name == "c3":
+        # all 2^28 sampled genotypes of S_{3,8}, 32 x 32 grid, 20 replicates, seed 3
+        return write_sampled_chunked("c3", 3, 8, 32, 20, 3, 1 << 28, 1 << 24)
+    if name == "c3chk":
+        # the chunked writer on the first 2^20 (must reproduce c3s exactly)
+        return write_sampled_chunked("c3chk", 3, 8, 32, 20, 3, 1 << 20, 1 << 18)
     n, c, L, k, seed, first, count, sampled = WORKLOADS[name]
     t0 = time.time()
     res, placements = O.enumerate_space(n, c, L, k, seed, first, count, sampled=sampled)

@@ -1,0 +1,114 @@
+"""Full-size parity of the two largest workloads with the oracle's stored values
+(tests/golden/make_golden.py, which calls only oracle/):
+
+  * 2^28 genotypes sampled uniformly from S_{3,8} (three tile types, eight
+    colours: the space of Section 3.3), 32 x 32 grid, 20 replicates, seed 3:
+    SHA-256 of the 2 GiB result array (and of each 2^24 chunk, to locate a
+    difference), class counts, every histogram row, and the largest
+    deterministic bounded shapes found;
+  * 10^7 explicit tile sets of mixed n, c, L, k (seed 4), in one persistent
+    launch, in one CUDA-graph replay of it, and as per-size fixed launches.
+
+Every comparison is exact."""
+import hashlib
+import json
+import os
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from oracle import oracle as O  # noqa: E402
+from paper_2205_15311_gb300 import binding as J  # noqa: E402
+from paper_2205_15311_gb300 import workloads as W  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    torch.cuda.init()
+    yield
+
+
+def _golden_hist(name):
+    rows = []
+    for line in open(os.path.join(GOLDEN, name)):
+        if not line.startswith("#"):
+            rows.append(tuple(int(v) for v in line.split()))
+    return rows
+
+
+def _hist_rows(h):
+    return [(int(r["cls"]), int(r["shape_hash"]), int(r["size"]), int(r["count"]), int(r["min_id"])) for r in h]
+
+
+def largest_det(rows, top):
+    """The DET keys with the most tiles (ties: more genotypes first, then hash)."""
+    det = sorted((r for r in rows if r[0] == 0), key=lambda r: (-r[2], -r[3], r[1]))
+    return [(r[2], r[1], r[3], r[4]) for r in det[:top]]
+
+
+def test_s38_all_2e28_sampled_genotypes_match_golden():
+    n, c, L, k, seed, first, count, sampled = W.WORKLOADS["s38_sample"]
+    gold = json.load(open(os.path.join(GOLDEN, "c3_summary.json")))
+    assert gold["workload"]["count"] == count and gold["workload"]["L"] == L and gold["workload"]["k"] == k
+    cap = 1 << 16
+    out = torch.full((count * 8,), 0xEE, dtype=torch.uint8, device="cuda")  # poisoned, 2 GiB
+    hist = torch.empty(cap * 32, dtype=torch.uint8, device="cuda")
+    hlen = torch.zeros(1, dtype=torch.int32, device="cuda")
+    J.enumerate_space(n, c, L, k, seed, first, count, sampled=True, out=out, hist=hist, hist_len=hlen,
+                      hist_cap=cap, sync=True)
+    m = int(hlen.item())
+    rows = _hist_rows(J.hist_view(hist, m))
+    assert rows == _golden_hist("c3_histogram.txt")
+    sha = hashlib.sha256()
+    counts = np.zeros(4, np.int64)
+    chunk = gold["chunk"]
+    for i, lo in enumerate(range(0, count, chunk)):
+        part = out[lo * 8:(lo + chunk) * 8].cpu().numpy()
+        b = part.tobytes()
+        assert hashlib.sha256(b).hexdigest() == gold["chunk_sha256"][i], f"chunk {i}"
+        sha.update(b)
+        counts += np.bincount(part.view(J.RESULT_DTYPE)["cls"], minlength=4)
+    assert sha.hexdigest() == gold["results_sha256"]
+    assert counts.tolist() == gold["class_counts"]
+    # the largest deterministic bounded shapes found, as the oracle reported them
+    largest = json.load(open(os.path.join(GOLDEN, "c3_largest.json")))
+    want = [(e["size"], e["shape_hash"], e["count"], e["min_id"]) for e in largest]
+    assert largest_det(rows, len(want)) == want
+    # a few genotypes re-classified one at a time by the oracle
+    res = J.results_view(out)
+    rng = np.random.default_rng(11)
+    for i in rng.integers(0, count, size=64).tolist():
+        g = O.sample_genotype(i, n, c, seed)
+        r = O.classify(n, c, L, k, seed, O.decode(g, n, c), g)
+        assert (r["cls"], r["decided_rep"], r["size"], r["shape_hash"]) == tuple(res[i].tolist())
+
+
+def _mixed(colours, shapes, per_shape, graph=False, hist_cap=1 << 14):
+    N = colours.shape[0]
+    out = torch.full((N * 8,), 0xEE, dtype=torch.uint8, device="cuda")
+    hist = torch.empty(hist_cap * 32, dtype=torch.uint8, device="cuda")
+    hlen = torch.zeros(1, dtype=torch.int32, device="cuda")
+    J.classify_batch(colours, seed=4, shapes=shapes, out=out, hist=hist, hist_len=hlen, hist_cap=hist_cap,
+                     sync=True, per_shape=per_shape, graph=graph)
+    return J.results_view(out), _hist_rows(J.hist_view(hist, int(hlen.item())))
+
+
+def test_mixed_1e7_records_match_golden():
+    gold = json.load(open(os.path.join(GOLDEN, "c4_summary.json")))
+    colours, shapes = W.mixed_records(10_000_000, seed=4)
+    assert hashlib.sha256(colours.tobytes() + shapes.tobytes()).hexdigest() == gold["inputs_sha256"]
+    dc = torch.from_numpy(colours).cuda()
+    ds = torch.from_numpy(shapes).cuda()
+    want_hist = _golden_hist("c4_histogram.txt")
+    for per_shape, graph in ((False, False), (False, True), (False, True), (True, False)):
+        res, rows = _mixed(dc, ds, per_shape, graph)
+        assert np.bincount(res["cls"], minlength=4).tolist() == gold["class_counts"], (per_shape, graph)
+        assert hashlib.sha256(res.tobytes()).hexdigest() == gold["results_sha256"], (per_shape, graph)
+        assert rows == want_hist, (per_shape, graph)
