@@ -214,6 +214,8 @@ typedef struct {
     int ncand[ORC_MAXL][ORC_MAXL]; /* |D(s)| of an empty site, as last evaluated */
     int cand[ORC_MAXL][ORC_MAXL];  /* the single candidate when ncand == 1 */
     int size;
+    int nd_kind; /* local ambiguity found: 1 one neighbour offers two distinct tuples, 2 only different
+                    neighbours disagree (two arms meeting: first-order steric, Section 2.4) */
 } grid;
 
 static int inside(const grid *G, int x, int y) { return x >= 0 && y >= 0 && x < G->L && y < G->L; }
@@ -247,6 +249,30 @@ static int candidates(const tileset *T, const grid *G, int qx, int qy, int *only
         }
     }
     return m;
+}
+
+/* Which kind of local ambiguity the empty site q (with |D(q)| >= 2) shows:
+ * 1 if some single occupied neighbour alone offers two distinct tuples
+ * (trivial non-determinism), 2 if every neighbour offers at most one and
+ * different neighbours offer different tuples (two arms meeting at q: the
+ * first-order steric non-determinism Section 2.4 detects together with the
+ * trivial kind). */
+static int ambiguity_kind(const tileset *T, const grid *G, int qx, int qy)
+{
+    for (int d = 0; d < 4; d++) {
+        int nx = qx + DX[d], ny = qy + DY[d];
+        if (!inside(G, nx, ny) || G->cell[ny][nx] < 0) continue;
+        int u = G->cell[ny][nx];
+        int seen[4 * ORC_MAXN], m = 0;
+        memset(seen, 0, sizeof seen);
+        for (int a = 0; a < 4 * T->n; a++)
+            if (orc_bind(T->side[a][d], T->side[u][(d + 2) % 4]) && !seen[T->rep[a]]) {
+                seen[T->rep[a]] = 1;
+                m++;
+            }
+        if (m >= 2) return 1;
+    }
+    return 2;
 }
 
 static uint32_t draw(const tileset *T, uint64_t stream_id, int rep, int step)
@@ -283,6 +309,7 @@ static int run_replicate(const tileset *T, uint64_t stream_id, int rep, grid *G,
     int px = L / 2, py = L / 2;
     G->cell[py][px] = T->rep[0];
     G->size = 1;
+    G->nd_kind = 0;
     int step = 0;
     int fx[ORC_MAXL * ORC_MAXL], fy[ORC_MAXL * ORC_MAXL];
     for (;;) {
@@ -297,7 +324,11 @@ static int run_replicate(const tileset *T, uint64_t stream_id, int rep, grid *G,
                 G->ncand[qy][qx] = m;
                 G->cand[qy][qx] = (m == 1) ? only : -1;
             }
-            if (m >= 2) nd = 1;
+            if (m >= 2) {
+                nd = 1;
+                int kind = ambiguity_kind(T, G, qx, qy);
+                if (G->nd_kind == 0 || kind < G->nd_kind) G->nd_kind = kind;
+            }
             else if (!in && m >= 1) unb = 1;
         }
         if (nd) return OUT_ND_LOCAL;
@@ -374,6 +405,7 @@ static int run_replicate_lifo(const tileset *T, uint64_t stream_id, int rep, gri
     int px = L / 2, py = L / 2;
     G->cell[py][px] = T->rep[0];
     G->size = 1;
+    G->nd_kind = 0; /* the ambiguity diagnostic covers the row-major process only */
     int placed = 0; /* placements after the seed */
     int sx_stack[ORC_MAXL * ORC_MAXL], sy_stack[ORC_MAXL * ORC_MAXL];
     int sp = 0;
@@ -699,6 +731,12 @@ static int valid_params(int n, int c, int L, int k)
     return n >= 1 && n <= ORC_MAXN && c >= 1 && c <= 8 && L >= 1 && L <= ORC_MAXL && k >= 1 && k <= 255;
 }
 
+/* Diagnostic mode of the classification calls below: ND_LOCAL results carry
+ * the kind of ambiguity that decided them in `size` (1 trivial, 2 first-order
+ * steric; see ambiguity_kind).  Classes and every other field are unchanged. */
+static int g_nd_detail = 0;
+void orc_set_nd_detail(int on) { g_nd_detail = on ? 1 : 0; }
+
 /* Classify one genotype given its colours col[4t + e].  When rep0_cells is not
  * NULL it receives replicate 0's final grid (L*L ints, row-major, -1 empty).
  * When trace is not NULL it receives the steps of replicate trace_rep. */
@@ -733,6 +771,7 @@ int orc_classify_ex(int n, int c, int L, int k, uint64_t seed, const uint8_t col
     res->decided_rep = (uint8_t)decided;
     res->size = 0;
     res->shape_hash = 0;
+    if (cls == ORC_ND_LOCAL && g_nd_detail) res->size = (uint16_t)((decided == 0 ? A0 : Aj)->nd_kind);
     if (cls == ORC_DET_BOUNDED || cls == ORC_ND_STERIC) {
         res->size = (uint16_t)A0->size;
         res->shape_hash = hash_of_grid(A0);

@@ -87,6 +87,8 @@ def lib():
             L.orc_shape_table_end.restype = ctypes.c_int
             L.orc_shape_table_add.argtypes = [ctypes.c_uint32, u8p, ctypes.c_int, ctypes.c_int]
             L.orc_shape_table_add.restype = None
+            L.orc_set_nd_detail.argtypes = [ctypes.c_int]
+            L.orc_set_nd_detail.restype = None
             L.orc_canonical.argtypes = [i32p, i32p, ctypes.c_int, u8p, i32p, i32p]
             L.orc_canonical.restype = ctypes.c_int
             L.orc_shape_hash.argtypes = [u8p, ctypes.c_int, ctypes.c_int]
@@ -382,6 +384,21 @@ class shape_table:
             h, w = int(hw[2 * i]), int(hw[2 * i + 1])
             bm = np.array([[(int(rows[32 * i + y]) >> x) & 1 for x in range(w)] for y in range(h)], np.uint8)
             self.forms[int(hashes[i])] = bm.reshape(h, w)
+
+
+class nd_detail:
+    """Context manager (diagnostic): ND_LOCAL results carry in `size` the kind
+    of ambiguity that decided them -- 1 when one neighbour alone offers two
+    distinct tuples (trivial non-determinism), 2 when only different
+    neighbours disagree (two arms meeting: first-order steric
+    non-determinism, Section 2.4).  Classes and other fields are unchanged."""
+
+    def __enter__(self):
+        lib().orc_set_nd_detail(1)
+        return self
+
+    def __exit__(self, *exc):
+        lib().orc_set_nd_detail(0)
 
 
 class hash_mode:

@@ -1,6 +1,6 @@
 """Write the stored expected values under tests/golden/ -- calls only oracle/.
 
-    python tests/golden/make_golden.py [c1] [c2] [c3s] [c3] [c4s] [c4]
+    python tests/golden/make_golden.py [c1] [c2] [c3s] [c3] [c4s] [c4] [facts]
 
 For each workload it runs the CPU oracle and stores:
   * the SHA-256 of the per-genotype result array (8 bytes per genotype:
@@ -141,7 +141,52 @@ def write_sampled_chunked(name, n, c, L, k, seed, count, chunk):
     print(name, meta, flush=True)
 
 
+def write_paper_facts():
+    """Section 3.1's two remarks on S_{2,8} at the paper's own settings (19 x 19
+    grid, k = 8 replicates, the rotation-only hash of Section 2.5), set beside
+    this model's counts: the ratio of sterically non-deterministic to unbounded
+    genotypes, and which shapes have both deterministic and sterically
+    non-deterministic genotypes.  Local ambiguity is split by the oracle's
+    diagnostic into its trivial kind (one neighbour offers two tuples) and its
+    first-order steric kind (two neighbours disagree), which Section 2.4
+    detects with one check."""
+    n, c, L, k, seed = 2, 8, 19, 8, 2
+    count = 1 << 24
+    t0 = time.time()
+    with O.hash_mode(True), O.nd_detail():
+        res, placements = O.enumerate_space(n, c, L, k, seed, 0, count)
+    dt = time.time() - t0
+    cls = res["cls"]
+    counts = np.bincount(cls, minlength=4).tolist()
+    nd = cls == O.ND_LOCAL
+    kinds = np.bincount(res["size"][nd], minlength=3).tolist()
+    det_keys = set(res["shape_hash"][cls == O.DET_BOUNDED].tolist())
+    steric_keys = set(res["shape_hash"][cls == O.ND_STERIC].tolist())
+    shared = sorted(det_keys & steric_keys)
+    shared_sizes = sorted({int(res["size"][(cls == O.DET_BOUNDED) & (res["shape_hash"] == h)][0]) for h in shared})
+    meta = {
+        "workload": {"n": n, "c": c, "L": L, "k": k, "seed": seed, "count": count, "hash": "C4 (Section 2.5)"},
+        "class_counts": {"det_bounded": counts[0], "nd_local": counts[1], "nd_steric": counts[2],
+                         "unbounded": counts[3]},
+        "nd_local_kinds": {"trivial": kinds[1], "first_order_steric": kinds[2]},
+        "steric_to_unbounded": {
+            "higher_order_only": round(counts[2] / counts[3], 4),
+            "with_first_order": round((counts[2] + kinds[2]) / counts[3], 4),
+            "paper": 2.2},
+        "shapes_with_det_and_nd_steric_genotypes": {"count": len(shared), "sizes": shared_sizes,
+                                                    "paper": "only the 12-mer"},
+        "placements": int(placements),
+        "oracle_seconds": round(dt, 1),
+    }
+    with open(os.path.join(HERE, "s28_paper_facts.json"), "w") as f:
+        json.dump(meta, f, indent=1)
+        f.write("\n")
+    print(meta, flush=True)
+
+
 def write(name):
+    if name == "facts":
+        return write_paper_facts()
     if name == "c4s":
         return write_mixed(name, 1_000_000, 4)
     if name == "c4":

@@ -112,3 +112,27 @@ def test_mixed_1e7_records_match_golden():
         assert np.bincount(res["cls"], minlength=4).tolist() == gold["class_counts"], (per_shape, graph)
         assert hashlib.sha256(res.tobytes()).hexdigest() == gold["results_sha256"], (per_shape, graph)
         assert rows == want_hist, (per_shape, graph)
+
+
+def test_s28_at_the_papers_settings_matches_the_oracle_counts():
+    """All of S_{2,8} at the paper's 19 x 19 grid, k = 8, with its rotation-only
+    hash (Section 2.5): the class counts equal the oracle's (the counts set
+    beside Section 3.1's remarks), and no shape has both deterministic and
+    sterically non-deterministic genotypes under these readings."""
+    facts = json.load(open(os.path.join(GOLDEN, "s28_paper_facts.json")))
+    w = facts["workload"]
+    n, c, L, k, seed, count = w["n"], w["c"], w["L"], w["k"], w["seed"], w["count"]
+    cap = 1 << 12
+    out = torch.empty(count * 8, dtype=torch.uint8, device="cuda")
+    hist = torch.empty(cap * 32, dtype=torch.uint8, device="cuda")
+    hlen = torch.zeros(1, dtype=torch.int32, device="cuda")
+    J.enumerate_space(n, c, L, k, seed, 0, count, out=out, hist=hist, hist_len=hlen, hist_cap=cap, sync=True,
+                      c4_hash=True)
+    cls = J.results_view(out)["cls"]
+    got = np.bincount(cls, minlength=4).tolist()
+    want = facts["class_counts"]
+    assert got == [want["det_bounded"], want["nd_local"], want["nd_steric"], want["unbounded"]]
+    rows = _hist_rows(J.hist_view(hist, int(hlen.item())))
+    det = {r[1] for r in rows if r[0] == 0}
+    steric = {r[1] for r in rows if r[0] == 2}
+    assert len(det & steric) == facts["shapes_with_det_and_nd_steric_genotypes"]["count"]

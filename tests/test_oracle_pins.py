@@ -506,3 +506,44 @@ def test_shape_table_of_s24_holds_canonical_forms_of_every_shaped_key():
         r = O.classify(n, c, L, k, seed, O.decode(g, n, c), g, want_grid=True)
         cells = [(x, y) for y in range(L) for x in range(L) if r["grid"][y, x] >= 0]
         assert np.array_equal(O.canonical(cells), T.forms[int(row["shape_hash"])])
+
+
+def test_ambiguity_kind_diagnostic_hand_cases():
+    """The diagnostic split of local ambiguity (Section 2.4 detects trivial and
+    first-order steric non-determinism with one check):
+      * seed (1, 0, 0, 0) and tile (0, 0, 2, 2): the seed's north side alone
+        offers two distinct rotated tuples (0,0,2,2) and (0,2,2,0) -- trivial,
+        kind 1, at the seed step;
+      * seed (0, 1, 3, 0) and tile (4, 5, 6, 2): the seed's east and south
+        sides each take exactly one tuple of the tile, and the two arms offer
+        the diagonal cell different tuples, (5,6,2,4) from the north and
+        (2,4,5,6) from the west, while no single neighbour ever offers two --
+        first-order steric, kind 2.
+    The mode changes no class, replicate, hash or non-ND size."""
+    with O.nd_detail():
+        r = O.classify(2, 8, 9, 20, 1, [1, 0, 0, 0, 0, 0, 2, 2], 0)
+        assert (r["cls"], r["decided_rep"], r["size"]) == (O.ND_LOCAL, 0, 1)
+        for seed in range(6):
+            r = O.classify(2, 8, 15, 20, seed, [0, 1, 3, 0, 4, 5, 6, 2], seed)
+            assert (r["cls"], r["size"]) == (O.ND_LOCAL, 2), seed
+    a, _ = O.enumerate_space(2, 8, 19, 8, 2, 1 << 22, 1 << 16)
+    with O.nd_detail():
+        b, _ = O.enumerate_space(2, 8, 19, 8, 2, 1 << 22, 1 << 16)
+    same = ["cls", "decided_rep", "shape_hash"]
+    assert all(np.array_equal(a[f], b[f]) for f in same)
+    nd = b["cls"] == O.ND_LOCAL
+    assert np.array_equal(a["size"][~nd], b["size"][~nd])
+    assert set(np.unique(b["size"][nd]).tolist()) <= {1, 2}
+
+
+def test_paper_facts_file_is_consistent():
+    """The stored S_{2,8} counts at the paper's settings add up: the classes
+    cover 8^8 genotypes and the two kinds of local ambiguity cover ND_LOCAL."""
+    import json
+    facts = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "s28_paper_facts.json")))
+    cc = facts["class_counts"]
+    assert sum(cc.values()) == 8 ** 8
+    kinds = facts["nd_local_kinds"]
+    assert kinds["trivial"] + kinds["first_order_steric"] == cc["nd_local"]
+    r = facts["steric_to_unbounded"]
+    assert abs(r["with_first_order"] - (cc["nd_steric"] + kinds["first_order_steric"]) / cc["unbounded"]) < 1e-4
