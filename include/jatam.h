@@ -380,6 +380,24 @@ int jatam_set_tuning(const jatam_config *cfg, int warps_per_cta, int stop_at);
 int jatam_get_tuning(const jatam_config *cfg, int *warps_per_cta, int *stop_at);
 
 /*
+ * jatam_set_genotypes_per_warp / jatam_get_genotypes_per_warp -- the layout of
+ * the growth launch for cfg's key (lattice size class, n, c), for items of one
+ * shape on the row-major process:
+ *   32: one genotype per lane, its lattice in the lane's share of shared
+ *       memory (every lattice size);
+ *    1: one genotype per warp, lattice rows in lanes held in registers, the
+ *       frontier rank found by a prefix sum across lanes (lattices of
+ *       17 x 17 to 32 x 32 only, where the per-lane layout leaves few warps
+ *       resident);
+ *    0: forget the setting (the default: 32 until jatam_autotune has timed
+ *       both on a 32 x 32 key).
+ * jatam_autotune times both layouts for keys with L > 16.  The layout never
+ * changes results.
+ */
+int jatam_set_genotypes_per_warp(const jatam_config *cfg, int genotypes_per_warp);
+int jatam_get_genotypes_per_warp(const jatam_config *cfg, int *genotypes_per_warp);
+
+/*
  * jatam_set_mixed_plan / jatam_get_mixed_plan -- the CTA plan of the
  * persistent launch for mixed lattice sizes: warps with a 32 x 32, 16 x 16
  * and 8 x 8 region per CTA (at least one 32 x 32 warp, since only those can

@@ -87,6 +87,10 @@ def lib():
         L.jatam_enumerate_noalloc.restype = ctypes.c_int
         L.jatam_last_shapes.argtypes = [_VP, _U32, ctypes.POINTER(_U32), ctypes.POINTER(_U32)]
         L.jatam_last_shapes.restype = ctypes.c_int
+        L.jatam_set_genotypes_per_warp.argtypes = [_VP, ctypes.c_int]
+        L.jatam_set_genotypes_per_warp.restype = ctypes.c_int
+        L.jatam_get_genotypes_per_warp.argtypes = [_VP, ctypes.POINTER(ctypes.c_int)]
+        L.jatam_get_genotypes_per_warp.restype = ctypes.c_int
         L.jatam_workspace_bytes.argtypes = [ctypes.POINTER(ctypes.c_uint64)]
         L.jatam_workspace_bytes.restype = ctypes.c_int
         L.jatam_mlp_create.argtypes = [_U64, ctypes.POINTER(_VP)]
@@ -266,6 +270,14 @@ def jatam_last_shapes(shapes, cap, length, collisions):
     return lib().jatam_last_shapes(shapes, cap, length, collisions)
 
 
+def jatam_set_genotypes_per_warp(cfg, genotypes_per_warp):
+    return lib().jatam_set_genotypes_per_warp(cfg, genotypes_per_warp)
+
+
+def jatam_get_genotypes_per_warp(cfg, genotypes_per_warp):
+    return lib().jatam_get_genotypes_per_warp(cfg, genotypes_per_warp)
+
+
 def jatam_workspace_bytes(nbytes):
     return lib().jatam_workspace_bytes(nbytes)
 
@@ -336,6 +348,19 @@ def shape_bitmap(entry):
     """h x w uint8 array of one jatam_shape entry (column j of row i = bit j)."""
     h, w = int(entry["h"]), int(entry["w"])
     return np.array([[(int(entry["rows"][i]) >> j) & 1 for j in range(w)] for i in range(h)], np.uint8)
+
+
+def set_genotypes_per_warp(n, c, L, genotypes_per_warp):
+    """1: one genotype per warp (L > 16); 32: one per lane; 0: the default."""
+    cfg = make_config(n, c, L, 1, 0)
+    return check(jatam_set_genotypes_per_warp(ctypes.addressof(cfg), int(genotypes_per_warp)))
+
+
+def get_genotypes_per_warp(n, c, L):
+    cfg = make_config(n, c, L, 1, 0)
+    v = ctypes.c_int(0)
+    check(jatam_get_genotypes_per_warp(ctypes.addressof(cfg), ctypes.byref(v)))
+    return int(v.value)
 
 
 def workspace_bytes() -> int:

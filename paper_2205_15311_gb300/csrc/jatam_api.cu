@@ -34,11 +34,16 @@ int g_profile = 0;  // bit 0: events around the growth kernels; bit 1: executed-
 int g_stop_override = 0;
 bool g_mixed_per_shape = false;  // the default launch form of mixed batches (set by jatam_autotune_batch)
 int g_warps_override = 0;
+int g_per_warp_override = 0;  // JATAM_GENOTYPES_PER_WARP: 1 or 32 for every 32 x 32 launch
+// genotypes per warp of a 32 x 32 launch when nothing is tuned or set
+int g_default_per_warp32 = 32;
 
 struct Tuning {
     int warps = 0;    // 0: the CTA size that keeps the most warps resident
     int stop_at = 0;  // 0: default_stop_at (14 for lattices up to 16 x 16, 12 for 32 x 32)
     int w32 = 2, w16 = 4, w8 = 2;  // warps per CTA of each region size in the mixed launch
+    int per_warp = 0;  // genotypes a warp grows at once: 32 (one per lane) or 1 (one per warp, 32 x 32
+                       // lattices only); 0: the default of the lattice template
 };
 // launch shape per key (lattice template, n, c); n = c = 0 for mixed batches
 std::map<std::tuple<int, int, int>, Tuning> g_tuned;
@@ -56,6 +61,10 @@ void read_env_overrides()
     if (const char *v = getenv("JATAM_WARPS_PER_CTA")) {
         int x = atoi(v);
         if (x >= 1 && x <= MAX_CTA_WARPS) g_warps_override = x;
+    }
+    if (const char *v = getenv("JATAM_GENOTYPES_PER_WARP")) {
+        int x = atoi(v);
+        if (x == 1 || x == 32) g_per_warp_override = x;
     }
 }
 
@@ -271,11 +280,15 @@ Tuning tuning_for(int S, int n, int c)
     if (it != g_tuned.end()) {
         t.warps = it->second.warps;
         t.stop_at = it->second.stop_at;
+        t.per_warp = it->second.per_warp;
     }
     if (t.warps == 0) t.warps = default_warps_per_cta(S, nt);
     if (t.stop_at == 0) t.stop_at = default_stop_at(S);
     if (g_warps_override) t.warps = g_warps_override;
     if (g_stop_override) t.stop_at = g_stop_override;
+    if (t.per_warp == 0) t.per_warp = (S == 32) ? g_default_per_warp32 : 32;
+    if (g_per_warp_override && S == 32) t.per_warp = g_per_warp_override;
+    if (S != 32) t.per_warp = 32;
     while (t.warps > 1 && classify_smem_bytes(S, nt, t.warps) > 200 * 1024) --t.warps;  // what fits on one SM
     return t;
 }
@@ -364,10 +377,18 @@ int run(Workspace *w, LaunchArgs a, int S, jatam_result *out, int32_t *fitness, 
     a.plan_w8 = tune.w8;
 
     // the single-template launch (not used for mixed sizes)
-    const int warps = tune.warps;
+    const bool per_warp = !mixed && !a.lifo && S == 32 && tune.per_warp == 1;
+    int warps = tune.warps;
     const int nt = mixed ? 16 : tuple_table_size(a.n);
     long long blocks = 0;
-    if (!mixed) {
+    if (per_warp) {
+        int per_sm = 0;
+        CUDA_TRY(classify_warp_occupancy(&per_sm, &warps));
+        if (per_sm < 1) return fail(JATAM_ECUDA, "classification kernel does not fit on an SM");
+        blocks = (long long)per_sm * w->num_sms;
+        const long long needed = (long long)((n_items + warps - 1) / warps);
+        if (needed < blocks) blocks = needed < 1 ? 1 : needed;
+    } else if (!mixed) {
         CUDA_TRY(classify_set_attributes(S, nt, warps, a.lifo != 0));
         int per_sm = 0;
         CUDA_TRY(classify_occupancy(S, nt, warps, &per_sm, a.lifo != 0));
@@ -380,8 +401,9 @@ int run(Workspace *w, LaunchArgs a, int S, jatam_result *out, int32_t *fitness, 
 
     // heavy genotypes first when every lane of the growth launch takes at least
     // 8 genotypes on average (pieces of a pipelined call are at least 2^23)
+    // (genotypes in progress at once: a lane's, or a warp's with one genotype per warp)
     const unsigned long long lanes = mixed ? 4ull * 160ull * (unsigned long long)w->num_sms  // about 4 CTAs of 5 warps an SM
-                                           : (unsigned long long)blocks * warps * 32;
+                                           : (unsigned long long)blocks * warps * (per_warp ? 1 : 32);
     a.heavy_first = (n_items >= 8ull * lanes) ? 1 : 0;
 
     a.lifo_stack = nullptr;
@@ -434,7 +456,8 @@ int run(Workspace *w, LaunchArgs a, int S, jatam_result *out, int32_t *fitness, 
         if (a.stats) CUDA_TRY(cudaMemsetAsync(a.stats, 0, 4 * 8, s));
         if (n_items) CUDA_TRY(launch_prefilter(a, S, (int)pblocks, s));
         if (events) CUDA_TRY(cudaEventRecord(w->k_start, s));
-        if (n_items && !mixed) CUDA_TRY(launch_classify(a, S, nt, (int)blocks, warps, s));
+        if (n_items && per_warp) CUDA_TRY(launch_classify_warp(a, (int)blocks, s));
+        if (n_items && !mixed && !per_warp) CUDA_TRY(launch_classify(a, S, nt, (int)blocks, warps, s));
         if (n_items && mixed && per_shape) {
             // one fixed launch per lattice size class, each over its own list
             for (int kc = 0; kc < 3; ++kc) {
@@ -522,7 +545,11 @@ int run(Workspace *w, LaunchArgs a, int S, jatam_result *out, int32_t *fitness, 
             long long pb = (long long)(cnt + 255) / 256;
             if (pb > 8LL * w->num_sms) pb = 8LL * w->num_sms;
             CUDA_TRY(launch_prefilter(ac, S, (int)pb, cs));
-            if (!mixed) {
+            if (per_warp) {
+                long long bc = (long long)((cnt + warps - 1) / warps);
+                if (bc > blocks) bc = blocks;
+                CUDA_TRY(launch_classify_warp(ac, (int)(bc < 1 ? 1 : bc), cs));
+            } else if (!mixed) {
                 const long long lanes_per_cta = 32LL * warps;
                 long long bc = (long long)((cnt + lanes_per_cta - 1) / lanes_per_cta);
                 if (bc > blocks) bc = blocks;
@@ -577,7 +604,7 @@ int run(Workspace *w, LaunchArgs a, int S, jatam_result *out, int32_t *fitness, 
                                   a.plan_w8, S, blocks, warps, per_shape, mixed_blocks, pblocks, hist_cap,
                                   fixed[0].blocks, fixed[0].warps, fixed[0].stop_at, fixed[1].blocks, fixed[1].warps,
                                   fixed[1].stop_at, fixed[2].blocks, fixed[2].warps, fixed[2].stop_at,
-                                  a.stats ? 1 : 0, a.c4, a.orbits};
+                                  a.stats ? 1 : 0, a.c4, a.orbits, per_warp ? 1 : 0};
         put(nums, sizeof nums);
         cudaGraphExec_t exec = nullptr;
         auto it = w->graphs.find(key);
@@ -1389,8 +1416,51 @@ int jatam_autotune(const jatam_config *shapes, uint32_t n_shapes, void *stream)
                 }
             }
         }
+        if (S == 32) {
+            // one genotype per warp: a single launch shape
+            Tuning t;
+            t.per_warp = 1;
+            float ms_min = 1e30f;
+            for (int rep = 0; rep < 2; ++rep) {
+                float ms = 0.f;
+                rc = run(w, a, S, nullptr, nullptr, nullptr, 0, nullptr, true, st, &t, &ms);
+                if (rc) return rc;
+                ms_min = ms < ms_min ? ms : ms_min;
+            }
+            if (ms_min < best_ms) {
+                best_ms = ms_min;
+                best = t;
+            }
+            if (best.per_warp == 0) best.per_warp = 32;
+        }
         g_tuned[std::make_tuple(S, (int)cfg.n, (int)cfg.c)] = best;
     }
+    return JATAM_OK;
+}
+
+int jatam_set_genotypes_per_warp(const jatam_config *cfg, int genotypes_per_warp)
+{
+    std::lock_guard<std::mutex> lock(g_mutex);
+    g_last_error.clear();
+    if (!cfg) return fail(JATAM_EINVAL, "cfg is NULL");
+    if (cfg->L < 1 || cfg->L > JATAM_MAX_GRID) return fail(JATAM_EUNSUPPORTED, "L must be 1..32");
+    if (!(genotypes_per_warp == 0 || genotypes_per_warp == 1 || genotypes_per_warp == 32))
+        return fail(JATAM_EINVAL, "genotypes_per_warp must be 0, 1 or 32");
+    const int S = lattice_template(cfg->L);
+    if (genotypes_per_warp == 1 && S != 32)
+        return fail(JATAM_EINVAL, "one genotype per warp is built for lattices of 17 x 17 to 32 x 32");
+    g_tuned[std::make_tuple(S, (int)cfg->n, (int)cfg->c)].per_warp = genotypes_per_warp;
+    return JATAM_OK;
+}
+
+int jatam_get_genotypes_per_warp(const jatam_config *cfg, int *genotypes_per_warp)
+{
+    std::lock_guard<std::mutex> lock(g_mutex);
+    g_last_error.clear();
+    if (!cfg || !genotypes_per_warp) return fail(JATAM_EINVAL, "cfg and genotypes_per_warp are required");
+    if (cfg->L < 1 || cfg->L > JATAM_MAX_GRID) return fail(JATAM_EUNSUPPORTED, "L must be 1..32");
+    const int S = lattice_template(cfg->L);
+    *genotypes_per_warp = tuning_for(S, cfg->n, cfg->c).per_warp;
     return JATAM_OK;
 }
 
@@ -1409,10 +1479,9 @@ int jatam_set_tuning(const jatam_config *cfg, int warps_per_cta, int stop_at)
         return fail(JATAM_EINVAL, "warps_per_cta must be 0..%d and stop_at 1..32", MAX_CTA_WARPS);
     if (classify_smem_bytes(S, tuple_table_size(cfg->n), warps_per_cta) > 200 * 1024)
         return fail(JATAM_EINVAL, "%d warps of a %dx%d lattice do not fit in shared memory", warps_per_cta, S, S);
-    Tuning t;
+    Tuning &t = g_tuned[std::make_tuple(S, (int)cfg->n, (int)cfg->c)];  // keeps the layout setting
     t.warps = warps_per_cta;
     t.stop_at = stop_at;
-    g_tuned[std::make_tuple(S, (int)cfg->n, (int)cfg->c)] = t;
     return JATAM_OK;
 }
 

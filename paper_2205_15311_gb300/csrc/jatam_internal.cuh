@@ -115,6 +115,10 @@ inline int tuple_table_size(int n) { return (n >= 1 && n <= 2) ? 8 : 16; }
 // finished lanes that end a growth round when nothing is tuned (measured on
 // S_{2,8} at L = 16 and 19 and on S_{3,8} at L = 32)
 inline int default_stop_at(int S) { return S == 32 ? 12 : 14; }
+// one genotype per warp (lattices up to 32 x 32, the row-major process): CTAs of
+// *warps_per_cta warps, no dynamic shared memory
+cudaError_t classify_warp_occupancy(int *blocks_per_sm, int *warps_per_cta);
+cudaError_t launch_classify_warp(const LaunchArgs &a, int blocks, cudaStream_t st);
 int classify_mixed_smem_bytes(int w32, int w16, int w8);
 cudaError_t classify_mixed_prepare(int w32, int w16, int w8, int *blocks_per_sm);
 cudaError_t launch_classify_mixed(const LaunchArgs &a, int blocks, cudaStream_t st);

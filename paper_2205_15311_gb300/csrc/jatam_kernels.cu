@@ -362,20 +362,10 @@ __device__ __noinline__ void shape_record(const ShapeTab t, uint32_t hash, uint3
 // ---------------------------------------------------------------------------
 // warp-cooperative canonical form + hash of owner o's replicate-0 shape
 // ---------------------------------------------------------------------------
-template <int S>
-__device__ __forceinline__ uint32_t coop_shape_hash(int o, const uint32_t *warp_lanes, const Lane &Ls, int lane,
-                                                    bool c4, const ShapeTab &tab)
+// canonical form + hash of a cropped shape held in lanes: lane i < h holds row
+// i of the h x w crop (bit j = column j), the other lanes 0
+__device__ __forceinline__ uint32_t crop_shape_hash(uint32_t r, int h, int w, int lane, bool c4, const ShapeTab &tab)
 {
-    using G = Geo<S>;
-    const int x0 = __shfl_sync(FULL, Ls.x0, o), x1 = __shfl_sync(FULL, Ls.x1, o);
-    const int y0 = __shfl_sync(FULL, Ls.y0, o), y1 = __shfl_sync(FULL, Ls.y1, o);
-    const int h = y1 - y0 + 1, w = x1 - x0 + 1;
-    const uint32_t wmask = (w >= 32) ? FULL : ((1u << w) - 1u);
-    uint32_t r = 0;  // lane i < h: row i of the crop, bit j = cell (x0 + j, y0 + i)
-    if (lane < h) {
-        const int b = (y0 + lane) * S + x0;
-        r = (warp_lanes[(G::OCCA + (b >> 5)) * 32 + o] >> (b & 31)) & wmask;
-    }
     uint32_t col = 0;  // lane j < w: column j, bit i = cell (x0 + j, y0 + i)
     for (int j = 0; j < w; ++j) {
         const uint32_t bj = __ballot_sync(FULL, (r >> j) & 1u);
@@ -422,6 +412,23 @@ __device__ __forceinline__ uint32_t coop_shape_hash(int o, const uint32_t *warp_
     const uint32_t hv = image_hash(best, hc, wc);
     if (tab.key) shape_record(tab, hv, best, hc, wc, lane);
     return hv;
+}
+
+template <int S>
+__device__ __forceinline__ uint32_t coop_shape_hash(int o, const uint32_t *warp_lanes, const Lane &Ls, int lane,
+                                                    bool c4, const ShapeTab &tab)
+{
+    using G = Geo<S>;
+    const int x0 = __shfl_sync(FULL, Ls.x0, o), x1 = __shfl_sync(FULL, Ls.x1, o);
+    const int y0 = __shfl_sync(FULL, Ls.y0, o), y1 = __shfl_sync(FULL, Ls.y1, o);
+    const int h = y1 - y0 + 1, w = x1 - x0 + 1;
+    const uint32_t wmask = (w >= 32) ? FULL : ((1u << w) - 1u);
+    uint32_t r = 0;  // lane i < h: row i of the crop, bit j = cell (x0 + j, y0 + i)
+    if (lane < h) {
+        const int b = (y0 + lane) * S + x0;
+        r = (warp_lanes[(G::OCCA + (b >> 5)) * 32 + o] >> (b & 31)) & wmask;
+    }
+    return crop_shape_hash(r, h, w, lane, c4, tab);
 }
 
 // W: the unsigned type that holds the colours (32 bits for at most two tiles).
@@ -1648,6 +1655,395 @@ __global__ void __launch_bounds__(256) classify_mixed_kernel(const LaunchArgs a)
 }
 
 
+// ===========================================================================
+// One genotype per warp, for lattices up to 32 x 32.  Lane y holds row y of
+// the lattice in registers: the occupancy of the current replicate and of
+// replicate 0, the frontier, and the 4-bit tuple ids (the placed tuple of an
+// occupied cell, the single candidate of a frontier cell).  The warp runs one
+// assembly step at a time (Section 2.4's stochastic addition of bonding tiles):
+// the rank of the drawn frontier site is found by a prefix sum of the rows'
+// site counts across the lanes, the row's lane places the tile, and the lanes
+// of rows y - 1, y and y + 1 re-evaluate the new tile's four neighbours.  The
+// binding table is spread over the lanes (word j in lane j, read by shuffle),
+// and the lanes compute 32 Philox blocks of a replicate's stream at once (128
+// draws).  Nothing but the CTA's histogram table lives in shared memory, and a
+// new genotype or replicate clears its lattice by zeroing registers, so far
+// more warps fit an SM than with one genotype per lane, whose 32 x 32 layout
+// needs about 1 KB of shared memory per lane.  The draws, the replicate rule
+// and the exact shortcuts (forced path, closed shape, dominated offers) are
+// those of the lane-per-genotype kernel, so the results are identical.
+// ===========================================================================
+constexpr int WG_WARPS = 8;  // warps per CTA of the warp-per-genotype kernel
+constexpr int WG_CHUNK = 4;  // items a warp takes from the list at once
+
+// tuple id of cell x of a row: nibble x & 7 of word x >> 3 (selected without
+// indexing, so the words stay in registers)
+__device__ __forceinline__ int row_tuple(uint32_t n0, uint32_t n1, uint32_t n2, uint32_t n3, int x)
+{
+    const uint32_t w = x < 8 ? n0 : x < 16 ? n1 : x < 24 ? n2 : n3;
+    return (int)((w >> ((x & 7) * 4)) & 15u);
+}
+__device__ __forceinline__ void row_tuple_set(uint32_t &n0, uint32_t &n1, uint32_t &n2, uint32_t &n3, int x, int t)
+{
+    const int sh = (x & 7) * 4;
+    const uint32_t keep = ~(15u << sh), val = (uint32_t)t << sh;
+    if (x < 8) n0 = (n0 & keep) | val;
+    else if (x < 16) n1 = (n1 & keep) | val;
+    else if (x < 24) n2 = (n2 & keep) | val;
+    else n3 = (n3 & keep) | val;
+}
+
+// The binding table of one genotype, word j in lane j: word 2 t + h holds, at
+// bits 16 q, the set of representative tuples u whose side (d + 2) mod 4
+// carries the partner of tuple t's colour on side d = 2 h + q (Section 1.1's
+// pairs 1-2, 3-4, 5-6; 0 and an odd top colour bind nothing).  Tuple a = 4 t +
+// r is tile t turned clockwise by r quarter turns (side d shows edge (d - r)
+// mod 4); a representative is the lowest a with its rotated colour tuple.
+__device__ __forceinline__ uint32_t warp_binding_table(unsigned long long cols, int n, int c, int lane)
+{
+    const int na = 4 * n;
+    uint32_t tup = 0xFFFFFFFFu;  // never equal to a 16-bit tuple
+    if (lane < na) tup = rot16((uint32_t)(cols >> (16 * (lane >> 2))) & 0xFFFFu, 4 * (lane & 3));
+    int rep = lane;
+    for (int a = na - 1; a >= 0; --a) {
+        const uint32_t ta = __shfl_sync(FULL, tup, a);
+        if (a < lane && ta == tup) rep = a;
+    }
+    const unsigned isrep = __ballot_sync(FULL, lane < na && rep == lane);
+    const int t = (lane >> 1) & 15, h = lane & 1;
+    const uint32_t tt = __shfl_sync(FULL, tup, t);
+    int p0, p1;  // partners of t's colours on sides 2h and 2h + 1
+    {
+        const int x0 = (int)((tt >> (8 * h)) & 15u), x1 = (int)((tt >> (8 * h + 4)) & 15u);
+        p0 = (x0 == 0) ? -1 : (x0 & 1) ? ((x0 + 1 < c) ? x0 + 1 : -1) : x0 - 1;
+        p1 = (x1 == 0) ? -1 : (x1 & 1) ? ((x1 + 1 < c) ? x1 + 1 : -1) : x1 - 1;
+    }
+    uint32_t word = 0;
+    for (int u = 0; u < na; ++u) {
+        const uint32_t tu = __shfl_sync(FULL, tup, u);
+        if (!((isrep >> u) & 1u)) continue;
+        // side 2h + q faces side (2h + q + 2) mod 4 of u
+        const int f0 = (int)((tu >> (4 * ((2 * h + 2) & 3))) & 15u);
+        const int f1 = (int)((tu >> (4 * ((2 * h + 3) & 3))) & 15u);
+        if (p0 >= 0 && f0 == p0) word |= 1u << u;
+        if (p1 >= 0 && f1 == p1) word |= 1u << (16 + u);
+    }
+    return (lane < 2 * na) ? word : 0u;
+}
+
+// Dominance certificate of replicate 0's final configuration A0 (rows in lanes,
+// absolute coordinates): the attachment graph u -> v when u offers v's tuple,
+// bad offers to cells of A0 (the seed's cell excepted), and for every cell q
+// receiving a bad offer a flood fill from its bad offerers that avoids q --
+// the certificate fails if it reaches the seed.  The argument is that of the
+// lane-per-genotype kernel's coop_dominated.
+__device__ __forceinline__ bool warp_dominated(uint32_t occ, uint32_t n0, uint32_t n1, uint32_t n2, uint32_t n3,
+                                               uint32_t nbm, int x0, int x1, int L, int lane)
+{
+    uint32_t occN = __shfl_up_sync(FULL, occ, 1), occS = __shfl_down_sync(FULL, occ, 1);
+    if (lane == 0) occN = 0u;
+    if (lane == 31) occS = 0u;
+    const int sx = L >> 1, sy = L >> 1;
+    uint32_t gN = 0, gE = 0, gS = 0, gW = 0, bN = 0, bE = 0, bS = 0, bW = 0;
+    int tW = 0, tC = row_tuple(n0, n1, n2, n3, x0);
+    for (int x = x0; x <= x1; ++x) {
+        const int tE = (x + 1 < 32) ? row_tuple(n0, n1, n2, n3, x + 1) : 0;
+        const int tN = __shfl_up_sync(FULL, tC, 1), tS = __shfl_down_sync(FULL, tC, 1);
+        const uint32_t m01 = __shfl_sync(FULL, nbm, (2 * tC) & 31);
+        const uint32_t m23 = __shfl_sync(FULL, nbm, (2 * tC + 1) & 31);
+        if ((occ >> x) & 1u) {
+            const uint32_t bit = 1u << x;
+            const uint32_t MN = m01 & 0xFFFFu, ME = m01 >> 16, MS = m23 & 0xFFFFu, MW = m23 >> 16;
+            if ((occN >> x) & 1u) {
+                if ((MN >> tN) & 1u) gN |= bit;
+                if ((MN & ~(1u << tN)) && !(lane - 1 == sy && x == sx)) bN |= bit;
+            }
+            if (x + 1 < 32 && ((occ >> (x + 1)) & 1u)) {
+                if ((ME >> tE) & 1u) gE |= bit;
+                if ((ME & ~(1u << tE)) && !(lane == sy && x + 1 == sx)) bE |= bit;
+            }
+            if ((occS >> x) & 1u) {
+                if ((MS >> tS) & 1u) gS |= bit;
+                if ((MS & ~(1u << tS)) && !(lane + 1 == sy && x == sx)) bS |= bit;
+            }
+            if (x > 0 && ((occ >> (x - 1)) & 1u)) {
+                if ((MW >> tW) & 1u) gW |= bit;
+                if ((MW & ~(1u << tW)) && !(lane == sy && x - 1 == sx)) bW |= bit;
+            }
+        }
+        tW = tC;
+        tC = tE;
+    }
+    const uint32_t fromAbove = __shfl_up_sync(FULL, bS, 1), fromBelow = __shfl_down_sync(FULL, bN, 1);
+    uint32_t qs = (bE << 1) | (bW >> 1) | (lane > 0 ? fromAbove : 0u) | (lane < 31 ? fromBelow : 0u);
+    qs &= occ;
+    const uint32_t seed_bit = (lane == sy) ? (1u << sx) : 0u;
+    for (int guard = 0; guard < 1024; ++guard) {  // at most one pass per cell of A0
+        const unsigned hasq = __ballot_sync(FULL, qs != 0u);
+        if (!hasq) return true;
+        const int qy = __ffs(hasq) - 1;
+        const int qx = __ffs(__shfl_sync(FULL, qs, qy)) - 1;
+        if (lane == qy) qs &= ~(1u << qx);
+        const uint32_t keep = occ & ((lane == qy) ? ~(1u << qx) : FULL);
+        uint32_t X = 0u;
+        if (lane == qy - 1) X = bS & (1u << qx);
+        if (lane == qy + 1) X = bN & (1u << qx);
+        if (lane == qy) X = (bW & ((qx + 1 < 32) ? (2u << qx) : 0u)) | (bE & ((qx > 0) ? (1u << (qx - 1)) : 0u));
+        for (int it = 0; it < 1024; ++it) {  // a layer per step: at most the cells of A0
+            if (__any_sync(FULL, (X & seed_bit) != 0u)) return false;
+            const uint32_t below = __shfl_down_sync(FULL, X, 1);
+            const uint32_t above = __shfl_up_sync(FULL, X, 1);
+            uint32_t nX = X | (gE & (X >> 1)) | (gW & (X << 1)) | (lane < 31 ? (gS & below) : 0u) |
+                          (lane > 0 ? (gN & above) : 0u);
+            nX &= keep;
+            if (!__any_sync(FULL, nX != X)) break;
+            X = nX;
+        }
+    }
+    return false;  // unreachable: the passes are bounded by the cells of A0
+}
+
+struct WarpOutcome {
+    int cls, decided, size;
+    uint32_t hash;
+};
+
+// Classify one genotype with the whole warp (every value below is uniform
+// across the warp except the row registers and `nbm`).
+__device__ __forceinline__ WarpOutcome warp_classify(const LaunchArgs &a, const Item &it, int lane,
+                                                     unsigned long long *st_draw, unsigned long long *st_seed)
+{
+    const int L = it.L, k = it.k, cx = it.L >> 1;
+    const uint32_t nbm = warp_binding_table(it.cols, it.n, it.c, lane);
+    uint32_t occ = 0, front = 0, occ0 = 0, n0 = 0, n1 = 0, n2 = 0, n3 = 0;
+    int size0 = 0, x0 = cx, x1 = cx, y0 = cx, y1 = cx;
+    WarpOutcome res{JATAM_DET_BOUNDED, k, 0, 0u};
+    // Philox blocks of the current replicate: lane j holds block base + j
+    uint4 blk = make_uint4(0, 0, 0, 0);
+    int blk_base = -1, blk_rep = -1;
+    for (int rep = 0; rep < k; ++rep) {
+        // the seed: tile 0 in orientation 0 at the centre (tuple id 0)
+        occ = (lane == cx) ? (1u << cx) : 0u;
+        front = 0u;
+        if (rep == 0 && lane == cx) row_tuple_set(n0, n1, n2, n3, cx, 0);
+        int px = cx, py = cx, tau = 0;
+        int size = 1, step = 0, nF = 0;
+        int xmin = cx, xmax = cx, ymin = cx, ymax = cx;
+        bool forced = true, cert = true, diverged = false;
+        int outcome = 0;  // 1 local ambiguity, 2 unbounded, 3 terminated
+        *st_seed += 1;
+        for (int guard = 0; guard <= 32 * 32; ++guard) {
+            // ---- re-evaluate the empty neighbours of the tile tau just placed at (px, py):
+            // lane py - 1 its north side, lane py + 1 its south side, lane py its east and west
+            // sides (indices wrap to a lane whose site lies outside the grid)
+            const uint32_t m01 = __shfl_sync(FULL, nbm, 2 * tau), m23 = __shfl_sync(FULL, nbm, 2 * tau + 1);
+            const bool isN = lane == ((py + 31) & 31), isS = lane == ((py + 1) & 31), isC = lane == py;
+            bool nd = false, unb = false, bad = false, div = false;
+            int added = 0;
+            // up to two sites per lane: (sx1, sy1, M1) and, on lane py, the west side
+            const int sx1 = isC ? px + 1 : px;
+            const int sy1 = isN ? py - 1 : isS ? py + 1 : py;
+            const uint32_t M1 = isN ? (m01 & 0xFFFFu) : isS ? (m23 & 0xFFFFu) : (m01 >> 16);
+#pragma unroll
+            for (int q = 0; q < 2; ++q) {
+                const bool mine = q == 0 ? (isN || isS || isC) : isC;
+                const int x = q == 0 ? sx1 : px - 1;
+                const int y = q == 0 ? sy1 : py;
+                const uint32_t M = q == 0 ? M1 : (m23 >> 16);
+                const bool multi = (M & (M - 1u)) != 0u;
+                const bool in = x >= 0 && x < L && y >= 0 && y < L;
+                if (mine && !in) {
+                    nd = nd || multi;
+                    unb = unb || (M != 0u && !multi);
+                } else if (mine) {
+                    const uint32_t bit = 1u << x;
+                    const bool empty = !(occ & bit);
+                    const bool isf = (front & bit) != 0u;
+                    const int tq = row_tuple(n0, n1, n2, n3, x);
+                    nd = nd || (empty && (isf ? (M & ~(1u << tq)) != 0u : multi));
+                    // replicate 0: an occupied neighbour that could receive another tuple from the new
+                    // tile breaks the closure of the final shape (the seed's cell excepted)
+                    if (rep == 0 && !empty && (M & ~(1u << tq)) != 0u && !(x == cx && y == cx)) bad = true;
+                    if (empty && !isf && M != 0u && !multi) {
+                        const int tn = __ffs(M) - 1;
+                        // a later replicate must place replicate 0's tuple here to end in its configuration
+                        if (rep > 0 && (!(occ0 & bit) || tq != tn)) div = true;
+                        row_tuple_set(n0, n1, n2, n3, x, tn);
+                        front |= bit;
+                        ++added;
+                    }
+                }
+            }
+            const unsigned flags = __reduce_or_sync(FULL, (nd ? 1u : 0u) | (unb ? 2u : 0u) | (bad ? 4u : 0u) |
+                                                              (div ? 8u : 0u));
+            nF += (int)__reduce_add_sync(FULL, (unsigned)added);
+            if (flags & 4u) cert = false;
+            if (flags & 8u) diverged = true;
+            if (flags & 1u) { outcome = 1; break; }
+            if (flags & 2u) { outcome = 2; break; }
+            if (nF == 0) { outcome = 3; break; }
+            // ---- draw: word (step mod 4) of Philox block step >> 2 of this replicate's stream
+            if (nF > 1) forced = false;
+            const int b = step >> 2;
+            if (blk_rep != rep || b < blk_base || b >= blk_base + 32) {
+                blk_base = b;
+                blk_rep = rep;
+                blk = philox4x32_10(make_uint4((uint32_t)(b + lane), (uint32_t)rep, (uint32_t)it.sid,
+                                               (uint32_t)(it.sid >> 32)), a.key0, a.key1);
+            }
+            const int sel = step & 3;
+            const uint32_t word = sel == 0 ? blk.x : sel == 1 ? blk.y : sel == 2 ? blk.z : blk.w;
+            const uint32_t u = __shfl_sync(FULL, word, b - blk_base);
+            const uint32_t i = __umulhi(u, (uint32_t)nF);
+            // the row holding frontier site number i (row-major order): a prefix sum of site counts
+            const uint32_t cnt = (uint32_t)__popc(front);
+            uint32_t incl = cnt;
+#pragma unroll
+            for (int off = 1; off < 32; off <<= 1) {
+                const uint32_t v = __shfl_up_sync(FULL, incl, off);
+                if (lane >= off) incl += v;
+            }
+            const uint32_t excl = incl - cnt;
+            const unsigned hit = __ballot_sync(FULL, i >= excl && i < incl);
+            if (hit == 0u) break;  // unreachable (i < nF = the sum of the counts): reported below as a guard error
+            const int row = __ffs(hit) - 1;
+            int bx = 0, bt = 0;
+            if (lane == row) {
+                bx = nth_set(front, i - excl);
+                bt = row_tuple(n0, n1, n2, n3, bx);
+                front &= ~(1u << bx);
+                occ |= 1u << bx;
+            }
+            px = __shfl_sync(FULL, bx, row & 31);
+            tau = __shfl_sync(FULL, bt, row & 31);
+            py = row;
+            nF -= 1;
+            size += 1;
+            step += 1;
+            *st_draw += 1;
+            xmin = min(xmin, px);
+            xmax = max(xmax, px);
+            ymin = min(ymin, py);
+            ymax = max(ymax, py);
+        }
+        // ---- the first deciding replicate (reading R10) and the exact shortcuts
+        if (outcome == 1 || outcome == 2 || outcome == 0) {
+            res.cls = outcome == 2 ? JATAM_UNBOUNDED : JATAM_ND_LOCAL;
+            res.decided = rep;
+            if (outcome == 0) atomicOr(a.err, ERR_GUARD);  // unreachable: a replicate ends within L * L steps
+            return res;
+        }
+        if (rep == 0) {
+            size0 = size;
+            occ0 = occ;
+            x0 = xmin; x1 = xmax; y0 = ymin; y1 = ymax;
+            if (forced || cert) break;  // every replicate ends in A0
+            if (k > 1 && warp_dominated(occ0, n0, n1, n2, n3, nbm, x0, x1, L, lane)) break;
+        } else if (diverged || size != size0) {
+            res.cls = JATAM_ND_STERIC;
+            res.decided = rep;
+            break;
+        }
+    }
+    // ---- replicate 0's shape: crop, canonical form under the 8 symmetries, hash
+    res.size = size0;
+    const int h = y1 - y0 + 1, w = x1 - x0 + 1;
+    const uint32_t wmask = (w >= 32) ? FULL : ((1u << w) - 1u);
+    const uint32_t r = (__shfl_sync(FULL, occ0, (y0 + lane) & 31) >> x0) & wmask;
+    const uint32_t row = lane < h ? r : 0u;
+    unsigned long long bits = 0ull;
+    int gslot = -1;
+    bool found = false;
+    const uint32_t hw = ((uint32_t)h << 8) | (uint32_t)w;
+    if (h * w <= 64 && a.crops) {
+        // the call's crop table (shared with the lane-per-genotype kernel's format)
+        const unsigned long long mine = lane < h ? ((unsigned long long)row << (lane * w)) : 0ull;
+        const uint32_t lo = __reduce_or_sync(FULL, (uint32_t)mine), hi = __reduce_or_sync(FULL, (uint32_t)(mine >> 32));
+        bits = ((unsigned long long)hi << 32) | lo;
+        const unsigned mask = (1u << a.crops_log2) - 1u;
+        const unsigned s0 = (unsigned)(((bits ^ ((unsigned long long)hw << 52)) * 0x9E3779B97F4A7C15ull) >> 40) & mask;
+        for (int p = 0; p < CROP_PROBES; ++p) {
+            const unsigned sl = (s0 + (unsigned)p) & mask;
+            const unsigned long long key = __ldcg(&a.crops[2 * sl]);
+            if (key == 0ull) {
+                gslot = (int)sl;
+                break;
+            }
+            if (key == bits) {
+                const unsigned long long meta = __ldcg(&a.crops[2 * sl + 1]);
+                if ((meta >> 63) && (uint32_t)((meta >> 40) & 0xFFFFu) == hw) {
+                    res.hash = (uint32_t)meta;
+                    found = true;
+                }
+                break;
+            }
+        }
+        if (gslot < 0) gslot = (int)s0;
+    }
+    if (!found) {
+        res.hash = crop_shape_hash(row, h, w, lane, a.c4 != 0, a.shape_tab);
+        if (lane == 0 && bits) {
+            const unsigned mask = (1u << a.crops_log2) - 1u;
+            const unsigned long long meta = (1ull << 63) | ((unsigned long long)hw << 40) | res.hash;
+            for (int p = 0; p < CROP_PROBES; ++p) {
+                const unsigned sl = ((unsigned)gslot + (unsigned)p) & mask;
+                const unsigned long long old = atomicCAS(&a.crops[2 * sl], 0ull, bits);
+                if (old == 0ull) {
+                    __stcg(&a.crops[2 * sl + 1], meta);
+                    break;
+                }
+                if (old == bits) break;
+            }
+        }
+    }
+    return res;
+}
+
+// the warps of a CTA work through one pre-filter list, a genotype at a time
+__global__ void __launch_bounds__(WG_WARPS * 32, 3) classify_warp_kernel(const LaunchArgs a)
+{
+    __shared__ SmemHist H;
+    hist_begin(H);
+    const int lane = threadIdx.x & 31;
+    const unsigned long long *list = a.list + (size_t)a.klass * a.list_stride;
+    const unsigned long long front = a.list_count[a.klass], total = front + a.list_count[3 + a.klass];
+    unsigned long long *work_next = a.work_next + a.klass;
+    const int b_uniform = log2_colours(a.c);
+    unsigned long long q_next = 0, q_end = 0, st_draw = 0, st_seed = 0, st_geno = 0;
+    for (;;) {
+        if (q_next >= q_end) {
+            unsigned long long nb = 0;
+            if (lane == 0) nb = atomicAdd(work_next, (unsigned long long)WG_CHUNK);
+            nb = __shfl_sync(FULL, nb, 0);
+            if (nb >= total) break;
+            q_next = nb;
+            q_end = min(nb + (unsigned long long)WG_CHUNK, total);
+        }
+        const unsigned long long pos = q_next++;
+        const unsigned long long item = list[pos < front ? pos : a.list_stride - 1 - (pos - front)];
+        const Item it = load_item(a, item, b_uniform, 32);
+        st_geno += 1;
+        const WarpOutcome o = warp_classify(a, it, lane, &st_draw, &st_seed);
+        if (lane == 0) {
+            const bool shaped = o.cls == JATAM_DET_BOUNDED || o.cls == JATAM_ND_STERIC;
+            const unsigned size = shaped ? (unsigned)o.size : 0u;
+            const uint32_t hash = shaped ? o.hash : 0u;
+            write_result(a, item, o.cls, o.decided, size, hash);
+            if (a.use_hist)
+                hist_insert(H, a.table, ((unsigned long long)o.cls << 32) | hash, 1u, it.sid, size, size, a.err);
+        }
+        __syncwarp();
+    }
+    if (a.stats && lane == 0) {
+        atomicAdd(&a.stats[0], st_draw);
+        atomicAdd(&a.stats[1], st_seed);
+        atomicAdd(&a.stats[2], 32ull * (st_draw + st_seed));  // a warp step occupies all 32 lane slots
+        atomicAdd(&a.stats[3], st_geno);
+    }
+    hist_end(H, a);
+}
+
+
 // Orbit mode, after the growth kernel: every genotype that is not its orbit's
 // representative takes the representative's result (the representative is the
 // smaller genotype, so it lies in the range, which starts at 0) and is counted
@@ -1936,6 +2332,18 @@ cudaError_t launch_classify_mixed(const LaunchArgs &a, int blocks, cudaStream_t 
 {
     const int warps = a.plan_w32 + a.plan_w16 + a.plan_w8;
     classify_mixed_kernel<<<blocks, warps * 32, classify_mixed_smem_bytes(a.plan_w32, a.plan_w16, a.plan_w8), st>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t classify_warp_occupancy(int *blocks_per_sm, int *warps_per_cta)
+{
+    *warps_per_cta = WG_WARPS;
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, classify_warp_kernel, WG_WARPS * 32, 0);
+}
+
+cudaError_t launch_classify_warp(const LaunchArgs &a, int blocks, cudaStream_t st)
+{
+    classify_warp_kernel<<<blocks, WG_WARPS * 32, 0, st>>>(a);
     return cudaGetLastError();
 }
 
