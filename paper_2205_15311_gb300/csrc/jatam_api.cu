@@ -35,6 +35,7 @@ int g_stop_override = 0;
 bool g_mixed_per_shape = false;  // the default launch form of mixed batches (set by jatam_autotune_batch)
 int g_warps_override = 0;
 int g_per_warp_override = 0;  // JATAM_GENOTYPES_PER_WARP: 1 or 32 for every 32 x 32 launch
+int g_window = 1;             // lattices of 17..32: grow in a 16 x 16 window first (JATAM_WINDOW=0: off)
 // genotypes per warp of a 32 x 32 launch when nothing is tuned or set
 int g_default_per_warp32 = 32;
 
@@ -62,6 +63,7 @@ void read_env_overrides()
         int x = atoi(v);
         if (x >= 1 && x <= MAX_CTA_WARPS) g_warps_override = x;
     }
+    if (const char *v = getenv("JATAM_WINDOW")) g_window = atoi(v) != 0;
     if (const char *v = getenv("JATAM_GENOTYPES_PER_WARP")) {
         int x = atoi(v);
         if (x == 1 || x == 32) g_per_warp_override = x;
@@ -363,8 +365,12 @@ int run(Workspace *w, LaunchArgs a, int S, jatam_result *out, int32_t *fitness, 
     const bool mixed = a.mode == MODE_RECORDS && a.shapes;
     const Tuning tune = force ? *force : tuning_for(S, mixed ? 0 : a.n, mixed ? 0 : a.c);
     a.stop_at = tune.stop_at;
+    // lattices of 17 to 32: the items first grow in the 16 x 16 window around the seed, where four
+    // times as many warps fit an SM; the few whose growth leaves the window run on the full lattice
+    const bool windowed = !mixed && !a.lifo && S == 32 && tune.per_warp != 1 && g_window;
+    const int regions = mixed ? 3 : windowed ? 2 : 1;
     if (n_items) {
-        int rc = grow(&w->list, &w->list_bytes, n_items * 8 * (mixed ? 3 : 1));
+        int rc = grow(&w->list, &w->list_bytes, n_items * 8 * regions);
         if (rc) return rc;
     }
     a.list = static_cast<unsigned long long *>(w->list);
@@ -399,10 +405,41 @@ int run(Workspace *w, LaunchArgs a, int S, jatam_result *out, int32_t *fitness, 
         if (needed < blocks) blocks = needed < 1 ? 1 : needed;
     }
 
+    // the window launch (S = 16) and the full-lattice launch of the items that leave the window
+    const Tuning tw = tuning_for(16, a.n, a.c);
+    int wblocks = 0;
+    if (windowed) {
+        CUDA_TRY(classify_set_attributes(16, nt, tw.warps));
+        int pw = 0;
+        CUDA_TRY(classify_occupancy(16, nt, tw.warps, &pw));
+        if (pw < 1) return fail(JATAM_ECUDA, "classification kernel does not fit on an SM");
+        wblocks = pw * w->num_sms;
+        const long long need = (long long)((n_items + 32LL * tw.warps - 1) / (32LL * tw.warps));
+        if (need < wblocks) wblocks = need < 1 ? 1 : (int)need;
+    }
+    auto launch_growth = [&](const LaunchArgs &la, long long nb, cudaStream_t s) -> int {
+        if (windowed) {
+            LaunchArgs aw = la;
+            aw.window = 1;
+            aw.stop_at = tw.stop_at;
+            long long wb = (long long)((la.count + 32ull * tw.warps - 1) / (32ull * tw.warps));
+            if (wb > wblocks) wb = wblocks;
+            CUDA_TRY(launch_classify(aw, 16, nt, (int)(wb < 1 ? 1 : wb), tw.warps, s));
+            LaunchArgs af = la;
+            af.window = 0;
+            af.klass = 1;
+            CUDA_TRY(launch_classify(af, 32, nt, (int)nb, warps, s));
+            return JATAM_OK;
+        }
+        CUDA_TRY(launch_classify(la, S, nt, (int)nb, warps, s));
+        return JATAM_OK;
+    };
+
     // heavy genotypes first when every lane of the growth launch takes at least
     // 8 genotypes on average (pieces of a pipelined call are at least 2^23)
     // (genotypes in progress at once: a lane's, or a warp's with one genotype per warp)
     const unsigned long long lanes = mixed ? 4ull * 160ull * (unsigned long long)w->num_sms  // about 4 CTAs of 5 warps an SM
+                                   : windowed ? (unsigned long long)wblocks * tw.warps * 32  // the window launch reads the list
                                            : (unsigned long long)blocks * warps * (per_warp ? 1 : 32);
     a.heavy_first = (n_items >= 8ull * lanes) ? 1 : 0;
 
@@ -457,7 +494,9 @@ int run(Workspace *w, LaunchArgs a, int S, jatam_result *out, int32_t *fitness, 
         if (n_items) CUDA_TRY(launch_prefilter(a, S, (int)pblocks, s));
         if (events) CUDA_TRY(cudaEventRecord(w->k_start, s));
         if (n_items && per_warp) CUDA_TRY(launch_classify_warp(a, (int)blocks, s));
-        if (n_items && !mixed && !per_warp) CUDA_TRY(launch_classify(a, S, nt, (int)blocks, warps, s));
+        if (n_items && !mixed && !per_warp) {
+            if (int rc = launch_growth(a, blocks, s)) return rc;
+        }
         if (n_items && mixed && per_shape) {
             // one fixed launch per lattice size class, each over its own list
             for (int kc = 0; kc < 3; ++kc) {
@@ -508,7 +547,7 @@ int run(Workspace *w, LaunchArgs a, int S, jatam_result *out, int32_t *fitness, 
             CUDA_TRY(cudaMalloc(&alt.crops, (size_t(2) << CROPS_LOG2) * 8));
         }
         {
-            int rc = grow(&alt.list, &alt.list_bytes, per * 8 * (mixed ? 3 : 1));
+            int rc = grow(&alt.list, &alt.list_bytes, per * 8 * regions);
             if (rc) return rc;
         }
         if (a.stats) CUDA_TRY(cudaMemsetAsync(a.stats, 0, 4 * 8, s));
@@ -553,7 +592,7 @@ int run(Workspace *w, LaunchArgs a, int S, jatam_result *out, int32_t *fitness, 
                 const long long lanes_per_cta = 32LL * warps;
                 long long bc = (long long)((cnt + lanes_per_cta - 1) / lanes_per_cta);
                 if (bc > blocks) bc = blocks;
-                CUDA_TRY(launch_classify(ac, S, nt, (int)(bc < 1 ? 1 : bc), warps, cs));
+                if (int rc = launch_growth(ac, bc < 1 ? 1 : bc, cs)) return rc;
             } else if (per_shape) {
                 for (int kc = 0; kc < 3; ++kc) {
                     LaunchArgs ak = ac;
@@ -604,7 +643,8 @@ int run(Workspace *w, LaunchArgs a, int S, jatam_result *out, int32_t *fitness, 
                                   a.plan_w8, S, blocks, warps, per_shape, mixed_blocks, pblocks, hist_cap,
                                   fixed[0].blocks, fixed[0].warps, fixed[0].stop_at, fixed[1].blocks, fixed[1].warps,
                                   fixed[1].stop_at, fixed[2].blocks, fixed[2].warps, fixed[2].stop_at,
-                                  a.stats ? 1 : 0, a.c4, a.orbits, per_warp ? 1 : 0};
+                                  a.stats ? 1 : 0, a.c4, a.orbits, per_warp ? 1 : 0, windowed ? 1 : 0,
+                                  wblocks, tw.warps, tw.stop_at};
         put(nums, sizeof nums);
         cudaGraphExec_t exec = nullptr;
         auto it = w->graphs.find(key);

@@ -97,6 +97,10 @@ struct LaunchArgs {
                                     // {crop bits, valid | h | w | hash}, cleared by the call's reset
     unsigned crops_log2;
     ShapeTab shape_tab;             // the call's shape side table (key null: none)
+    int window;                     // 1: the items' lattice (L > S) is grown in the S x S window around the
+                                    // seed; an item whose growth offers a tile outside the window is not
+                                    // classified here but appended to region 1 of `list` (count at
+                                    // list_count[1]) for a launch on the full lattice
 };
 
 // Lattice template: rows of S bits, S in {8, 16, 32}, L <= S; nt = 8 tuple ids

@@ -57,6 +57,14 @@ constexpr unsigned FULL = 0xffffffffu;
 constexpr int HIST_SLOTS = 256;  // per-CTA phenotype aggregation table
 constexpr int CHUNK = 32;        // items taken from the global counter at once
 constexpr int CROP_PROBES = 4;   // slots of the crop table tried per lookup
+constexpr int CROP_CELLS = 48;   // crops of at most this many cells are kept in the crop table
+
+// key of a crop in the crop table: its h x w bits (row i at bits i * w ..) with h and w above
+// them, so that crops of different dimensions never share a key (h * w <= CROP_CELLS)
+__device__ __forceinline__ unsigned long long crop_key(unsigned long long bits, int h, int w)
+{
+    return bits | ((unsigned long long)h << 48) | ((unsigned long long)w << 56);
+}
 
 enum Phase : int { PH_NEED = 0, PH_INIT, PH_START, PH_GROW, PH_DOM, PH_SHAPE, PH_WRITE, PH_DONE };
 
@@ -311,7 +319,7 @@ __device__ __forceinline__ uint32_t c4_combine(uint32_t a, uint32_t b, uint32_t 
 constexpr int SHAPE_PROBES = 64;      // slots tried before a form is counted as not stored
 constexpr int SHAPE_WAIT = 1 << 16;   // polls of a slot whose rows are still being written
 
-__device__ __noinline__ void shape_record(const ShapeTab t, uint32_t hash, uint32_t row, int h, int w, int lane)
+__device__ __forceinline__ void shape_record(const ShapeTab &t, uint32_t hash, uint32_t row, int h, int w, int lane)
 {
     const unsigned mask = (1u << t.log2) - 1u;
     const unsigned long long key = (1ull << 32) | hash;
@@ -331,10 +339,14 @@ __device__ __noinline__ void shape_record(const ShapeTab t, uint32_t hash, uint3
     const uint32_t mine = lane < h ? row : 0u;
     const unsigned meta = 0x80000000u | ((unsigned)h << 8) | (unsigned)w;
     if (state == 1) {
+        // the rows, then (after the warp barrier, which orders the lanes' stores before lane 0's
+        // fence) the meta word that publishes them
         __stcg(&t.rows[(size_t)slot * 32 + lane], mine);
-        __threadfence();
         __syncwarp();
-        if (lane == 0) atomicExch(&t.meta[slot], meta);
+        if (lane == 0) {
+            __threadfence();
+            atomicExch(&t.meta[slot], meta);
+        }
     } else if (state == 2) {
         unsigned m = 0;
         if (lane == 0) {
@@ -345,11 +357,11 @@ __device__ __noinline__ void shape_record(const ShapeTab t, uint32_t hash, uint3
                 if (m == 0) __nanosleep(64);
             }
         }
+        if (lane == 0) __threadfence();  // the rows are read after the meta word was seen
         m = __shfl_sync(FULL, m, 0);
         if (m == 0) {
             if (lane == 0) atomicAdd(&t.stats[1], 1u);
         } else {
-            __threadfence();
             const uint32_t have = __ldcg(&t.rows[(size_t)slot * 32 + lane]);
             if (__any_sync(FULL, m != meta || have != mine) && lane == 0) atomicAdd(&t.stats[0], 1u);
         }
@@ -1327,6 +1339,23 @@ __device__ __forceinline__ void warp_loop(const LaunchArgs &a, uint32_t *warp_la
         // ---- service: write finished genotypes and hand out new ones from the
         // pre-filter's list (all lanes together)
         for (;;) {
+            if (a.window) {
+                // growth reached past the window: the item goes to the full-lattice launch unclassified
+                // (a site outside the window with two candidates is local ambiguity there too, and an
+                // ambiguity elsewhere in the same step comes first: those results stand)
+                const bool esc = Ls.phase == PH_WRITE && Ls.cls == JATAM_UNBOUNDED;
+                const unsigned em = __ballot_sync(FULL, esc);
+                if (em) {
+                    const int first_lane = __ffs(em) - 1;
+                    unsigned long long base = 0;
+                    if (lane == first_lane) base = atomicAdd(&a.list_count[1], (unsigned long long)__popc(em));
+                    base = __shfl_sync(FULL, base, first_lane);
+                    if (esc) {
+                        a.list[a.list_stride + base + __popc(em & lanemask_lt())] = Ls.item;
+                        Ls.phase = PH_NEED;
+                    }
+                }
+            }
             if (Ls.phase == PH_WRITE) {
                 const bool shaped = Ls.cls == JATAM_DET_BOUNDED || Ls.cls == JATAM_ND_STERIC;
                 const unsigned size = shaped ? (unsigned)Ls.size0 : 0u;
@@ -1363,11 +1392,13 @@ __device__ __forceinline__ void warp_loop(const LaunchArgs &a, uint32_t *warp_la
                 } else {
                     const unsigned long long item =
                         list[my_pos < front ? my_pos : a.list_stride - 1 - (my_pos - front)];
-                    const Item it = load_item(a, item, b_uniform, S);
+                    const Item it = load_item(a, item, b_uniform, a.window ? JATAM_MAX_GRID : S);
                     Ls.item = item;
                     Ls.sid = it.sid;
                     Ls.cols = it.cols;
-                    Ls.n = it.n; Ls.c = it.c; Ls.L = it.L; Ls.k = it.k;
+                    // in a window the lattice is the S x S window itself (its seed cell, S / 2, is the
+                    // lattice's seed cell L / 2 shifted; row-major order is kept by the shift)
+                    Ls.n = it.n; Ls.c = it.c; Ls.L = a.window ? S : it.L; Ls.k = it.k;
                     Ls.phase = PH_INIT;
                 }
             }
@@ -1485,12 +1516,12 @@ __device__ __forceinline__ void warp_loop(const LaunchArgs &a, uint32_t *warp_la
 
         // ---- canonical shapes of finished genotypes: a per-warp cache keyed by
         // the exact crop (when it has at most 32 cells), then the launch's crop
-        // table (at most 64 cells), else one warp-wide job each
+        // table (at most CROP_CELLS cells), else one warp-wide job each
         unsigned long long ckey = 0ull, gbits = 0ull;
         int cslot = -1, gslot = -1;
         if (Ls.phase == PH_SHAPE) {
             const int h = Ls.y1 - Ls.y0 + 1, w = Ls.x1 - Ls.x0 + 1;
-            if (h * w <= 64) {
+            if (h * w <= CROP_CELLS) {
                 const uint32_t wmask = (w >= 32) ? FULL : ((1u << w) - 1u);
                 unsigned long long bits = 0;  // row i of the crop at bits i * w ..
                 for (int i = 0; i < h; ++i) {
@@ -1514,8 +1545,8 @@ __device__ __forceinline__ void warp_loop(const LaunchArgs &a, uint32_t *warp_la
                     // written once per launch (key by compare-and-swap, then the meta
                     // word), so a matching key with a valid meta word is always right
                     const unsigned mask = (1u << a.crops_log2) - 1u;
-                    const unsigned s0 = (unsigned)(((bits ^ ((unsigned long long)hw << 52)) *
-                                                    0x9E3779B97F4A7C15ull) >> 40) & mask;
+                    const unsigned long long key = crop_key(bits, h, w);
+                    const unsigned s0 = (unsigned)((key * 0x9E3779B97F4A7C15ull) >> 40) & mask;
                     for (int p = 0; p < CROP_PROBES; ++p) {
                         const unsigned sl = (s0 + (unsigned)p) & mask;
                         const unsigned long long k = __ldcg(&a.crops[2 * sl]);
@@ -1523,7 +1554,7 @@ __device__ __forceinline__ void warp_loop(const LaunchArgs &a, uint32_t *warp_la
                             gslot = (int)sl;
                             break;
                         }
-                        if (k == bits) {
+                        if (k == key) {
                             const unsigned long long meta = __ldcg(&a.crops[2 * sl + 1]);
                             if ((meta >> 63) && (uint32_t)((meta >> 40) & 0xFFFFu) == hw) {
                                 Ls.hash = (uint32_t)meta;
@@ -1538,16 +1569,42 @@ __device__ __forceinline__ void warp_loop(const LaunchArgs &a, uint32_t *warp_la
                             break;
                         }
                     }
-                    if (Ls.phase == PH_SHAPE) gbits = bits;
+                    if (Ls.phase == PH_SHAPE) gbits = key;
                     if (gslot < 0) gslot = (int)s0;  // the probes start there again on insertion
                 }
             }
         }
         unsigned shp = __ballot_sync(FULL, Ls.phase == PH_SHAPE);
+        const ShapeTab no_tab{};
         while (shp) {
             const int o = __ffs(shp) - 1;
             shp &= shp - 1;
-            const uint32_t hv = coop_shape_hash<S>(o, warp_lanes, Ls, lane, a.c4 != 0, a.shape_tab);
+            // the owner claims its crop's slot of the call's crop table before the form is computed
+            // (the key by compare-and-swap now, the meta word once the hash is known).  The form is
+            // a function of the crop, so the side table of shapes needs it only from the warp that
+            // claims the crop, and from every warp whose crop the table cannot hold
+            int claim = -1;
+            int record = 0;
+            if (lane == o) {
+                record = 1;
+                if (gbits) {
+                    const unsigned mask = (1u << a.crops_log2) - 1u;
+                    for (int p = 0; p < CROP_PROBES; ++p) {
+                        const unsigned sl = ((unsigned)gslot + (unsigned)p) & mask;
+                        const unsigned long long old = atomicCAS(&a.crops[2 * sl], 0ull, gbits);
+                        if (old == 0ull) {
+                            claim = (int)sl;
+                            break;
+                        }
+                        if (old == gbits) {
+                            record = 0;  // another warp claimed this crop and records its form
+                            break;
+                        }
+                    }
+                }
+            }
+            record = __shfl_sync(FULL, record, o);
+            const uint32_t hv = coop_shape_hash<S>(o, warp_lanes, Ls, lane, a.c4 != 0, record ? a.shape_tab : no_tab);
             if (lane == o) {
                 Ls.hash = hv;
                 Ls.phase = PH_WRITE;
@@ -1557,19 +1614,10 @@ __device__ __forceinline__ void warp_loop(const LaunchArgs &a, uint32_t *warp_la
                     ce[(G::CACHE + 1) * 32] = (uint32_t)(ckey >> 32);
                     ce[(G::CACHE + 2) * 32] = hv;
                 }
-                if (gbits) {
-                    const unsigned mask = (1u << a.crops_log2) - 1u;
+                if (claim >= 0) {
                     const unsigned long long meta = (1ull << 63) |
                         ((unsigned long long)(((Ls.y1 - Ls.y0 + 1) << 8) | (Ls.x1 - Ls.x0 + 1)) << 40) | hv;
-                    for (int p = 0; p < CROP_PROBES; ++p) {
-                        const unsigned sl = ((unsigned)gslot + (unsigned)p) & mask;
-                        const unsigned long long old = atomicCAS(&a.crops[2 * sl], 0ull, gbits);
-                        if (old == 0ull) {
-                            __stcg(&a.crops[2 * sl + 1], meta);
-                            break;
-                        }
-                        if (old == gbits) break;
-                    }
+                    __stcg(&a.crops[2 * claim + 1], meta);
                 }
             }
             __syncwarp();
@@ -1955,13 +2003,13 @@ __device__ __forceinline__ WarpOutcome warp_classify(const LaunchArgs &a, const 
     int gslot = -1;
     bool found = false;
     const uint32_t hw = ((uint32_t)h << 8) | (uint32_t)w;
-    if (h * w <= 64 && a.crops) {
+    if (h * w <= CROP_CELLS && a.crops) {
         // the call's crop table (shared with the lane-per-genotype kernel's format)
         const unsigned long long mine = lane < h ? ((unsigned long long)row << (lane * w)) : 0ull;
         const uint32_t lo = __reduce_or_sync(FULL, (uint32_t)mine), hi = __reduce_or_sync(FULL, (uint32_t)(mine >> 32));
-        bits = ((unsigned long long)hi << 32) | lo;
+        bits = crop_key(((unsigned long long)hi << 32) | lo, h, w);
         const unsigned mask = (1u << a.crops_log2) - 1u;
-        const unsigned s0 = (unsigned)(((bits ^ ((unsigned long long)hw << 52)) * 0x9E3779B97F4A7C15ull) >> 40) & mask;
+        const unsigned s0 = (unsigned)((bits * 0x9E3779B97F4A7C15ull) >> 40) & mask;
         for (int p = 0; p < CROP_PROBES; ++p) {
             const unsigned sl = (s0 + (unsigned)p) & mask;
             const unsigned long long key = __ldcg(&a.crops[2 * sl]);
@@ -1981,20 +2029,29 @@ __device__ __forceinline__ WarpOutcome warp_classify(const LaunchArgs &a, const 
         if (gslot < 0) gslot = (int)s0;
     }
     if (!found) {
-        res.hash = crop_shape_hash(row, h, w, lane, a.c4 != 0, a.shape_tab);
+        // claim the crop's slot first: only the claiming warp (or a warp whose crop the table cannot
+        // hold) records the form in the side table of shapes, as in the lane-per-genotype kernel
+        int claim = -1, record = 1;
         if (lane == 0 && bits) {
             const unsigned mask = (1u << a.crops_log2) - 1u;
-            const unsigned long long meta = (1ull << 63) | ((unsigned long long)hw << 40) | res.hash;
             for (int p = 0; p < CROP_PROBES; ++p) {
                 const unsigned sl = ((unsigned)gslot + (unsigned)p) & mask;
                 const unsigned long long old = atomicCAS(&a.crops[2 * sl], 0ull, bits);
                 if (old == 0ull) {
-                    __stcg(&a.crops[2 * sl + 1], meta);
+                    claim = (int)sl;
                     break;
                 }
-                if (old == bits) break;
+                if (old == bits) {
+                    record = 0;
+                    break;
+                }
             }
         }
+        record = __shfl_sync(FULL, record, 0);
+        const ShapeTab no_tab{};
+        res.hash = crop_shape_hash(row, h, w, lane, a.c4 != 0, record ? a.shape_tab : no_tab);
+        if (lane == 0 && claim >= 0)
+            __stcg(&a.crops[2 * claim + 1], (1ull << 63) | ((unsigned long long)hw << 40) | res.hash);
     }
     return res;
 }
