@@ -92,15 +92,16 @@ struct LaunchArgs {
                                     // lane slots of the growth rounds, genotypes grown by warps
     unsigned *err;                  // sticky error bits
     int heavy_first;                // 1: the pre-filter lists the genotypes with two or more frontier
-                                    // sites after the seed first (one size class only)
+                                    // sites after the seed first (one size class only); 2: three levels --
+                                    // three or four sites first, then two (region 1 of the list), then one
     unsigned long long *crops;      // null, or the crop table of the launch: 2^crops_log2 slots of
                                     // {crop bits, valid | h | w | hash}, cleared by the call's reset
     unsigned crops_log2;
     ShapeTab shape_tab;             // the call's shape side table (key null: none)
-    int window;                     // 1: the items' lattice (L > S) is grown in the S x S window around the
-                                    // seed; an item whose growth offers a tile outside the window is not
-                                    // classified here but appended to region 1 of `list` (count at
-                                    // list_count[1]) for a launch on the full lattice
+    unsigned long long *esc_list;   // non-null: window mode -- the items' lattice (L > S) is grown in the
+                                    // S x S window around the seed; an item whose growth offers a tile
+                                    // outside the window is not classified here but appended to esc_list
+    unsigned long long *esc_count;  // (count in *esc_count) for a launch on the full lattice
 };
 
 // Lattice template: rows of S bits, S in {8, 16, 32}, L <= S; nt = 8 tuple ids
@@ -127,8 +128,10 @@ int classify_mixed_smem_bytes(int w32, int w16, int w8);
 cudaError_t classify_mixed_prepare(int w32, int w16, int w8, int *blocks_per_sm);
 cudaError_t launch_classify_mixed(const LaunchArgs &a, int blocks, cudaStream_t st);
 
+// also zeroes extra[0 .. extra_words) when given
 cudaError_t launch_reset(unsigned long long *work_next, unsigned *nkeys, unsigned long long *list_count,
-                         cudaStream_t st, unsigned long long *crops = nullptr, unsigned crops_log2 = 0);
+                         cudaStream_t st, unsigned long long *crops = nullptr, unsigned crops_log2 = 0,
+                         unsigned long long *extra = nullptr, int extra_words = 0);
 cudaError_t launch_prefilter(const LaunchArgs &a, int smax, int blocks, cudaStream_t st);
 // load the reset and pre-filter kernels on the current device now (not at their first launch)
 cudaError_t load_index_range_kernels();

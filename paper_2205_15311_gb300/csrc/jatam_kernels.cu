@@ -1221,6 +1221,7 @@ __global__ void __launch_bounds__(256) prefilter_kernel(const LaunchArgs a, int 
                     // takes many genotypes: in a small call, warps given only heavy
                     // genotypes would set its length)
                     if (a.heavy_first && so > -2) klass += 3;
+                    else if (a.heavy_first == 2 && !a.bucket && so == -2) klass = 1;  // the middle level
                 } else if (so == 0) {
                     write_result(a, idx, JATAM_DET_BOUNDED, it.k, 1u, mono);
                     key = 2;
@@ -1237,7 +1238,8 @@ __global__ void __launch_bounds__(256) prefilter_kernel(const LaunchArgs a, int 
         __syncthreads();
         unsigned my_off = 0;
         for (int kc = 0; kc < nlists; ++kc) {
-            if (!a.bucket && kc % 3 != 0) continue;  // one size class: lists 0 and 3
+            // one size class: lists 0 and 3 (and 1, the middle level of a three-level order)
+            if (!a.bucket && kc % 3 != 0 && !(kc == 1 && a.heavy_first == 2)) continue;
             const unsigned gm = __ballot_sync(FULL, grow && klass == kc);
             unsigned woff = 0;
             if (gm && lane == 0) woff = atomicAdd(&s_fill[kc], (unsigned)__popc(gm));
@@ -1296,11 +1298,14 @@ __global__ void __launch_bounds__(256) prefilter_kernel(const LaunchArgs a, int 
 template <int S, int NT, bool LIFO>
 __device__ __forceinline__ void warp_loop(const LaunchArgs &a, uint32_t *warp_lanes, SmemHist &H,
                                           const unsigned long long *list, unsigned long long front,
-                                          unsigned long long back, unsigned long long *work_next)
+                                          unsigned long long back, unsigned long long *work_next,
+                                          const unsigned long long *mid_list = nullptr,
+                                          unsigned long long mid = 0)
 {
-    // items list[0 .. front) first, then list[a.list_stride - 1], list[a.list_stride - 2], ...
-    // (`back` of them): the pre-filter puts the longest-running genotypes in front
-    const unsigned long long total = front + back;
+    // items list[0 .. front) first, then mid_list[0 .. mid), then list[a.list_stride - 1],
+    // list[a.list_stride - 2], ... (`back` of them): the pre-filter puts the longest-running
+    // genotypes in front
+    const unsigned long long total = front + mid + back;
     using G = Geo<S, NT>;
     const int lane = threadIdx.x & 31;
     uint32_t *my = warp_lanes + lane;
@@ -1339,7 +1344,7 @@ __device__ __forceinline__ void warp_loop(const LaunchArgs &a, uint32_t *warp_la
         // ---- service: write finished genotypes and hand out new ones from the
         // pre-filter's list (all lanes together)
         for (;;) {
-            if (a.window) {
+            if (a.esc_list) {
                 // growth reached past the window: the item goes to the full-lattice launch unclassified
                 // (a site outside the window with two candidates is local ambiguity there too, and an
                 // ambiguity elsewhere in the same step comes first: those results stand)
@@ -1348,10 +1353,10 @@ __device__ __forceinline__ void warp_loop(const LaunchArgs &a, uint32_t *warp_la
                 if (em) {
                     const int first_lane = __ffs(em) - 1;
                     unsigned long long base = 0;
-                    if (lane == first_lane) base = atomicAdd(&a.list_count[1], (unsigned long long)__popc(em));
+                    if (lane == first_lane) base = atomicAdd(a.esc_count, (unsigned long long)__popc(em));
                     base = __shfl_sync(FULL, base, first_lane);
                     if (esc) {
-                        a.list[a.list_stride + base + __popc(em & lanemask_lt())] = Ls.item;
+                        a.esc_list[base + __popc(em & lanemask_lt())] = Ls.item;
                         Ls.phase = PH_NEED;
                     }
                 }
@@ -1391,14 +1396,16 @@ __device__ __forceinline__ void warp_loop(const LaunchArgs &a, uint32_t *warp_la
                     Ls.phase = PH_DONE;
                 } else {
                     const unsigned long long item =
-                        list[my_pos < front ? my_pos : a.list_stride - 1 - (my_pos - front)];
-                    const Item it = load_item(a, item, b_uniform, a.window ? JATAM_MAX_GRID : S);
+                        my_pos < front ? list[my_pos]
+                        : my_pos < front + mid ? mid_list[my_pos - front]
+                                               : list[a.list_stride - 1 - (my_pos - front - mid)];
+                    const Item it = load_item(a, item, b_uniform, a.esc_list ? JATAM_MAX_GRID : S);
                     Ls.item = item;
                     Ls.sid = it.sid;
                     Ls.cols = it.cols;
                     // in a window the lattice is the S x S window itself (its seed cell, S / 2, is the
                     // lattice's seed cell L / 2 shifted; row-major order is kept by the shift)
-                    Ls.n = it.n; Ls.c = it.c; Ls.L = a.window ? S : it.L; Ls.k = it.k;
+                    Ls.n = it.n; Ls.c = it.c; Ls.L = a.esc_list ? S : it.L; Ls.k = it.k;
                     Ls.phase = PH_INIT;
                 }
             }
@@ -1666,8 +1673,10 @@ __global__ void __launch_bounds__(MAX_CTA_WARPS * 32, 3) classify_kernel(const L
     hist_begin(H);
     const int warp = threadIdx.x >> 5;
     uint32_t *warp_lanes = smem_lanes + (size_t)warp * Geo<S, NT>::WORDS * 32;
+    const bool three = a.heavy_first == 2 && !a.bucket && a.klass == 0;
     warp_loop<S, NT, LIFO>(a, warp_lanes, H, a.list + (size_t)a.klass * a.list_stride, a.list_count[a.klass],
-                           a.list_count[3 + a.klass], a.work_next + a.klass);
+                           a.list_count[3 + a.klass], a.work_next + a.klass, three ? a.list + a.list_stride : nullptr,
+                           three ? a.list_count[1] : 0ull);
     hist_end(H, a);
 }
 
@@ -2126,11 +2135,13 @@ __global__ void __launch_bounds__(256) orbit_fill_kernel(const LaunchArgs a)
 }
 
 __global__ void reset_kernel(unsigned long long *work_next, unsigned *nkeys, unsigned long long *list_count,
-                             unsigned long long *crops, unsigned crop_words)
+                             unsigned long long *crops, unsigned crop_words, unsigned long long *extra,
+                             int extra_words)
 {
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         for (int c = 0; c < 3; ++c) work_next[c] = 0ull;
         for (int c = 0; c < 6; ++c) list_count[c] = 0ull;
+        for (int c = 0; c < extra_words; ++c) extra[c] = 0ull;
         *nkeys = 0u;
     }
     for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < crop_words; i += gridDim.x * blockDim.x)
@@ -2405,10 +2416,12 @@ cudaError_t launch_classify_warp(const LaunchArgs &a, int blocks, cudaStream_t s
 }
 
 cudaError_t launch_reset(unsigned long long *work_next, unsigned *nkeys, unsigned long long *list_count,
-                         cudaStream_t st, unsigned long long *crops, unsigned crops_log2)
+                         cudaStream_t st, unsigned long long *crops, unsigned crops_log2, unsigned long long *extra,
+                         int extra_words)
 {
     const unsigned words = crops ? (2u << crops_log2) : 0u;
-    reset_kernel<<<crops ? 16 : 1, 256, 0, st>>>(work_next, nkeys, list_count, crops, words);
+    reset_kernel<<<crops ? 16 : 1, 256, 0, st>>>(work_next, nkeys, list_count, crops, words, extra,
+                                                  extra ? extra_words : 0);
     return cudaGetLastError();
 }
 
