@@ -36,6 +36,7 @@ bool g_mixed_per_shape = false;  // the default launch form of mixed batches (se
 int g_warps_override = 0;
 int g_per_warp_override = 0;  // JATAM_GENOTYPES_PER_WARP: 1 or 32 for every 32 x 32 launch
 int g_window = 1;             // lattices of 17..32: grow in a 16 x 16 window first (JATAM_WINDOW=0: off)
+int g_crop_table = 1;         // the call's crop table of hashes (JATAM_CROP_TABLE=0: every form is computed)
 // levels of the heavy-first order of uniform launches (JATAM_HEAVY_LEVELS=2: two or more frontier
 // sites after the seed, then one).  Three (three or four, then two, then one) measured 1.7 % faster
 // on the S_{2,8} growth kernel (2.182 -> 2.145 ms)
@@ -68,6 +69,7 @@ void read_env_overrides()
         if (x >= 1 && x <= MAX_CTA_WARPS) g_warps_override = x;
     }
     if (const char *v = getenv("JATAM_WINDOW")) g_window = atoi(v) != 0;
+    if (const char *v = getenv("JATAM_CROP_TABLE")) g_crop_table = atoi(v) != 0;
     if (const char *v = getenv("JATAM_HEAVY_LEVELS")) g_heavy_levels = atoi(v) == 2 ? 2 : 3;
     if (const char *v = getenv("JATAM_GENOTYPES_PER_WARP")) {
         int x = atoi(v);
@@ -96,7 +98,10 @@ int fail(int code, const char *fmt, ...)
 constexpr unsigned TABLE_LOG2 = 18;  // 262,144 phenotype slots per device
 constexpr unsigned CROPS_LOG2 = 12;  // 4,096 slots of the per-call crop table (64 KB)
 constexpr unsigned SHAPES_LOG2 = 14;  // 16,384 slots of the call's shape side table (2.2 MB)
-constexpr int ESC_CTL_WORDS = 9;      // window mode: counts [0..5] and work counters [6..8] of the escalation list
+// per call or piece: counts [0..5] and work counters [6..8] of the window's escalation list, and
+// [9] the number of spilled crops
+constexpr int ESC_CTL_WORDS = 10;
+constexpr unsigned SPILL_CAP = 1u << 16;  // crops the crop table cannot hold, per call or piece (8.3 MB)
 // host-buffer calls of at least 2 * PIPE_MIN_ITEMS items run in up to PIPE_MAX_CHUNKS pieces whose
 // results are copied to the host while the next piece is classified
 constexpr size_t PIPE_MIN_ITEMS = size_t(1) << 23;
@@ -123,6 +128,8 @@ struct Workspace {
     void *esc = nullptr;
     size_t esc_bytes = 0;
     unsigned long long *esc_ctl = nullptr;
+    uint32_t *spill_rows = nullptr;  // SPILL_CAP x 32 rows, then SPILL_CAP meta words
+    size_t spill_bytes = 0;
     unsigned *host_words = nullptr;  // pinned: [0] err, [1] nkeys
     void *stage_in = nullptr;
     size_t stage_in_bytes = 0;
@@ -157,6 +164,8 @@ struct Workspace {
         void *esc = nullptr;
         size_t esc_bytes = 0;
         unsigned long long *esc_ctl = nullptr;
+        uint32_t *spill_rows = nullptr;
+        size_t spill_bytes = 0;
     } alt;
     cudaStream_t aux = nullptr, copy = nullptr;
     cudaEvent_t pipe_ev[PIPE_MAX_CHUNKS] = {};  // end of each piece's classification
@@ -371,11 +380,20 @@ int run(Workspace *w, LaunchArgs a, int S, jatam_result *out, int32_t *fitness, 
     a.table = w->table;
     a.use_hist = hist ? 1 : 0;
     a.work_next = w->work_next;
-    a.crops = w->crops;
+    a.crops = g_crop_table ? w->crops : nullptr;
     a.crops_log2 = CROPS_LOG2;
     // the exact shape side table: calls with a histogram and the canonical-form hash
     const bool record_shapes = hist && !a.c4;
-    a.shape_tab = record_shapes ? w->shapes : ShapeTab{};
+    const size_t spill_need = (size_t)SPILL_CAP * (32 * 4 + 4);
+    if (record_shapes) {
+        int rc = grow(reinterpret_cast<void **>(&w->spill_rows), &w->spill_bytes, spill_need);
+        if (rc) return rc;
+    }
+    auto spill_of = [&](uint32_t *rows, unsigned long long *ctl) -> CropSpill {
+        if (!record_shapes) return CropSpill{};
+        return CropSpill{rows, reinterpret_cast<unsigned *>(rows + (size_t)SPILL_CAP * 32), ctl + 9, SPILL_CAP};
+    };
+    a.spill = spill_of(w->spill_rows, w->esc_ctl);
     a.stats = (g_profile & 2) ? w->stats : nullptr;
     a.err = w->err;
     const bool mixed = a.mode == MODE_RECORDS && a.shapes;
@@ -553,9 +571,11 @@ int run(Workspace *w, LaunchArgs a, int S, jatam_result *out, int32_t *fitness, 
         }
         if (n_items && mixed && !per_shape) CUDA_TRY(launch_classify_mixed(a, mixed_blocks, s));
         if (events) CUDA_TRY(cudaEventRecord(w->k_stop, s));
+        if (record_shapes) CUDA_TRY(launch_shape_scan(w->shapes, a.crops, CROPS_LOG2, a.spill, s));
         if (n_items && a.orbits) CUDA_TRY(launch_orbit_fill(a, (int)pblocks, s));
         if (hist) {
-            CUDA_TRY(launch_hist_compact(w->table, w->compact, w->nkeys, 2 * w->num_sms, s, a.shape_tab));
+            CUDA_TRY(launch_hist_compact(w->table, w->compact, w->nkeys, 2 * w->num_sms, s,
+                                         record_shapes ? w->shapes : ShapeTab{}));
             CUDA_TRY(launch_hist_emit(w->compact, w->nkeys, o.hist_dev, hist_cap,
                                       o.host_len ? nullptr : o.hist_len_dev, w->num_sms, s));
         }
@@ -599,6 +619,10 @@ int run(Workspace *w, LaunchArgs a, int S, jatam_result *out, int32_t *fitness, 
                 rc = grow(&alt.esc, &alt.esc_bytes, per * 8);
                 if (rc) return rc;
             }
+            if (record_shapes) {
+                rc = grow(reinterpret_cast<void **>(&alt.spill_rows), &alt.spill_bytes, spill_need);
+                if (rc) return rc;
+            }
         }
         if (a.stats) CUDA_TRY(cudaMemsetAsync(a.stats, 0, 4 * 8, s));
         if (int rc = clear_shapes(s)) return rc;
@@ -619,7 +643,7 @@ int run(Workspace *w, LaunchArgs a, int S, jatam_result *out, int32_t *fitness, 
             LaunchArgs ac = a;
             ac.work_next = wn;
             ac.list_count = lc;
-            ac.crops = cr;
+            ac.crops = g_crop_table ? cr : nullptr;
             ac.list = static_cast<unsigned long long *>(odd ? alt.list : w->list);
             ac.list_stride = per;
             ac.count = cnt;
@@ -632,6 +656,7 @@ int run(Workspace *w, LaunchArgs a, int S, jatam_result *out, int32_t *fitness, 
             }
             if (a.out) ac.out = a.out + start;
             if (a.fitness) ac.fitness = a.fitness + start;
+            ac.spill = spill_of(odd ? alt.spill_rows : w->spill_rows, ectl);
             CUDA_TRY(launch_reset(wn, nk, lc, cs, cr, CROPS_LOG2, ectl, ESC_CTL_WORDS));
             long long pb = (long long)(cnt + 255) / 256;
             if (pb > 8LL * w->num_sms) pb = 8LL * w->num_sms;
@@ -650,6 +675,7 @@ int run(Workspace *w, LaunchArgs a, int S, jatam_result *out, int32_t *fitness, 
             } else {
                 CUDA_TRY(launch_classify_mixed(ac, mixed_blocks, cs));
             }
+            if (record_shapes) CUDA_TRY(launch_shape_scan(w->shapes, ac.crops, CROPS_LOG2, ac.spill, cs));
             CUDA_TRY(cudaEventRecord(w->pipe_ev[c], cs));
             CUDA_TRY(cudaStreamWaitEvent(w->copy, w->pipe_ev[c], 0));
             if (o.host_out)
@@ -662,7 +688,8 @@ int run(Workspace *w, LaunchArgs a, int S, jatam_result *out, int32_t *fitness, 
         CUDA_TRY(cudaEventRecord(w->aux_done, w->aux));
         CUDA_TRY(cudaStreamWaitEvent(s, w->aux_done, 0));
         if (hist) {
-            CUDA_TRY(launch_hist_compact(w->table, w->compact, w->nkeys, 2 * w->num_sms, s, a.shape_tab));
+            CUDA_TRY(launch_hist_compact(w->table, w->compact, w->nkeys, 2 * w->num_sms, s,
+                                         record_shapes ? w->shapes : ShapeTab{}));
             CUDA_TRY(launch_hist_emit(w->compact, w->nkeys, o.hist_dev, hist_cap,
                                       o.host_len ? nullptr : o.hist_len_dev, w->num_sms, s));
         }
@@ -1744,6 +1771,8 @@ void jatam_shutdown(void)
         if (w->esc) cudaFree(w->esc);
         if (w->alt.esc) cudaFree(w->alt.esc);
         if (w->alt.esc_ctl) cudaFree(w->alt.esc_ctl);
+        if (w->spill_rows) cudaFree(w->spill_rows);
+        if (w->alt.spill_rows) cudaFree(w->alt.spill_rows);
         if (w->list) cudaFree(w->list);
         cudaFreeHost(w->host_words);
         if (w->stage_in) cudaFree(w->stage_in);
@@ -1848,7 +1877,8 @@ int jatam_workspace_bytes(uint64_t *bytes)
     b += ((size_t(8) + 4 + 128) << SHAPES_LOG2) + 4 * 4;                 // shape side table
     b += w->list_bytes + w->stage_in_bytes + w->stage_out_bytes + w->stage_aux_bytes +
          w->stage_hist_cap * sizeof(jatam_hist_entry) + w->lifo_bytes + w->ga_bytes + w->screen_bytes +
-         w->alt.list_bytes + w->esc_bytes + w->alt.esc_bytes + ESC_CTL_WORDS * 8;
+         w->alt.list_bytes + w->esc_bytes + w->alt.esc_bytes + ESC_CTL_WORDS * 8 + w->spill_bytes +
+         w->alt.spill_bytes;
     if (w->copy) b += 3 * 8 + 6 * 8 + 4 + (size_t(2) << CROPS_LOG2) * 8;
     *bytes = b;
     return JATAM_OK;

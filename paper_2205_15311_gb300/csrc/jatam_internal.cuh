@@ -61,6 +61,19 @@ struct ShapeTab {
     unsigned log2;
 };
 
+// Crops whose form a growth kernel computed but whose crop the call's crop
+// table does not hold (more than 48 cells, or no free slot): rows[32 i + r] is
+// row r of crop i (bit j = column j), meta[i] = h << 8 | w; *count entries
+// (counted past cap when full).  The side table of shapes takes their forms,
+// and those of every crop in the crop table, in a pass after the growth
+// kernels, so that the growth kernels carry none of its code.
+struct CropSpill {
+    uint32_t *rows;
+    unsigned *meta;
+    unsigned long long *count;
+    unsigned cap;
+};
+
 struct LaunchArgs {
     int mode;
     unsigned long long first;     // first index (MODE_RANGE / MODE_SAMPLED)
@@ -97,7 +110,8 @@ struct LaunchArgs {
     unsigned long long *crops;      // null, or the crop table of the launch: 2^crops_log2 slots of
                                     // {crop bits, valid | h | w | hash}, cleared by the call's reset
     unsigned crops_log2;
-    ShapeTab shape_tab;             // the call's shape side table (key null: none)
+    CropSpill spill;                // uncacheable crops of a call that keeps a side table of shapes (rows
+                                    // null: none)
     unsigned long long *esc_list;   // non-null: window mode -- the items' lattice (L > S) is grown in the
                                     // S x S window around the seed; an item whose growth offers a tile
                                     // outside the window is not classified here but appended to esc_list
@@ -138,6 +152,9 @@ cudaError_t load_index_range_kernels();
 // jatam_shutdown: forget the per-device set-up of jatam_enumerate_noalloc
 void noalloc_forget_devices();
 cudaError_t launch_table_init(Table t, cudaStream_t st);
+// the side table of shapes from the crop table (2^crops_log2 slots) and the spill list of one call or piece
+cudaError_t launch_shape_scan(ShapeTab shapes, const unsigned long long *crops, unsigned crops_log2, CropSpill spill,
+                              cudaStream_t st);
 // also records the single-cell shape in `shapes` when a size-1 key is present
 // (the pre-filter settles those genotypes without computing a canonical form)
 cudaError_t launch_hist_compact(Table t, Compact c, unsigned *nkeys, int blocks, cudaStream_t st,

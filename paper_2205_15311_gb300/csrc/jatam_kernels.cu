@@ -310,11 +310,12 @@ __device__ __forceinline__ uint32_t c4_combine(uint32_t a, uint32_t b, uint32_t 
 // ---------------------------------------------------------------------------
 // Exact side table of a call's shapes (Section 2.5 estimates the chance that
 // two distinct shapes share a 32-bit hash; the table settles it exactly): the
-// first warp that computes a hash stores the canonical form under it, every
-// later warp that computes the same hash compares its form with the stored
-// one.  A form is never computed from a cache hit (caches map an exact crop to
-// its hash), so every distinct form the call produces is compared at least
-// once.  All 32 lanes call it; lane i < h holds row i of the form.
+// first warp that stores a hash keeps the canonical form under it, every later
+// warp with the same hash compares its form with the stored one.  A form is a
+// function of its crop, and every crop of a call is either in the call's crop
+// table or in its spill list, so the pass over both (shape_scan_kernel) sees
+// every distinct form.  All 32 lanes call it; lane i < h holds row i of the
+// form.
 // ---------------------------------------------------------------------------
 constexpr int SHAPE_PROBES = 64;      // slots tried before a form is counted as not stored
 constexpr int SHAPE_WAIT = 1 << 16;   // polls of a slot whose rows are still being written
@@ -426,9 +427,21 @@ __device__ __forceinline__ uint32_t crop_shape_hash(uint32_t r, int h, int w, in
     return hv;
 }
 
+// the crop of a form the crop table does not hold, appended to the call's spill list
+__device__ __forceinline__ void spill_crop(const CropSpill &sp, uint32_t r, int h, int w, int lane)
+{
+    unsigned long long idx = 0;
+    if (lane == 0) idx = atomicAdd(sp.count, 1ull);
+    idx = __shfl_sync(FULL, idx, 0);
+    if (idx < sp.cap) {
+        sp.rows[idx * 32 + lane] = lane < h ? r : 0u;
+        if (lane == 0) sp.meta[idx] = ((unsigned)h << 8) | (unsigned)w;
+    }
+}
+
 template <int S>
 __device__ __forceinline__ uint32_t coop_shape_hash(int o, const uint32_t *warp_lanes, const Lane &Ls, int lane,
-                                                    bool c4, const ShapeTab &tab)
+                                                    bool c4, bool spill, const CropSpill &sp)
 {
     using G = Geo<S>;
     const int x0 = __shfl_sync(FULL, Ls.x0, o), x1 = __shfl_sync(FULL, Ls.x1, o);
@@ -440,7 +453,8 @@ __device__ __forceinline__ uint32_t coop_shape_hash(int o, const uint32_t *warp_
         const int b = (y0 + lane) * S + x0;
         r = (warp_lanes[(G::OCCA + (b >> 5)) * 32 + o] >> (b & 31)) & wmask;
     }
-    return crop_shape_hash(r, h, w, lane, c4, tab);
+    if (spill) spill_crop(sp, r, h, w, lane);
+    return crop_shape_hash(r, h, w, lane, c4, ShapeTab{});
 }
 
 // W: the unsigned type that holds the colours (32 bits for at most two tiles).
@@ -1582,14 +1596,12 @@ __device__ __forceinline__ void warp_loop(const LaunchArgs &a, uint32_t *warp_la
             }
         }
         unsigned shp = __ballot_sync(FULL, Ls.phase == PH_SHAPE);
-        const ShapeTab no_tab{};
         while (shp) {
             const int o = __ffs(shp) - 1;
             shp &= shp - 1;
             // the owner claims its crop's slot of the call's crop table before the form is computed
-            // (the key by compare-and-swap now, the meta word once the hash is known).  The form is
-            // a function of the crop, so the side table of shapes needs it only from the warp that
-            // claims the crop, and from every warp whose crop the table cannot hold
+            // (the key by compare-and-swap now, the meta word once the hash is known); a crop the
+            // table cannot hold goes to the spill list, from which the side table of shapes takes it
             int claim = -1;
             int record = 0;
             if (lane == o) {
@@ -1601,17 +1613,19 @@ __device__ __forceinline__ void warp_loop(const LaunchArgs &a, uint32_t *warp_la
                         const unsigned long long old = atomicCAS(&a.crops[2 * sl], 0ull, gbits);
                         if (old == 0ull) {
                             claim = (int)sl;
+                            record = 0;  // the crop table holds it
                             break;
                         }
                         if (old == gbits) {
-                            record = 0;  // another warp claimed this crop and records its form
+                            record = 0;  // another warp claimed this crop
                             break;
                         }
                     }
                 }
             }
             record = __shfl_sync(FULL, record, o);
-            const uint32_t hv = coop_shape_hash<S>(o, warp_lanes, Ls, lane, a.c4 != 0, record ? a.shape_tab : no_tab);
+            const uint32_t hv = coop_shape_hash<S>(o, warp_lanes, Ls, lane, a.c4 != 0,
+                                                   record != 0 && a.spill.rows != nullptr, a.spill);
             if (lane == o) {
                 Ls.hash = hv;
                 Ls.phase = PH_WRITE;
@@ -2038,8 +2052,8 @@ __device__ __forceinline__ WarpOutcome warp_classify(const LaunchArgs &a, const 
         if (gslot < 0) gslot = (int)s0;
     }
     if (!found) {
-        // claim the crop's slot first: only the claiming warp (or a warp whose crop the table cannot
-        // hold) records the form in the side table of shapes, as in the lane-per-genotype kernel
+        // claim the crop's slot first; a crop the table cannot hold goes to the spill list, as in the
+        // lane-per-genotype kernel
         int claim = -1, record = 1;
         if (lane == 0 && bits) {
             const unsigned mask = (1u << a.crops_log2) - 1u;
@@ -2048,6 +2062,7 @@ __device__ __forceinline__ WarpOutcome warp_classify(const LaunchArgs &a, const 
                 const unsigned long long old = atomicCAS(&a.crops[2 * sl], 0ull, bits);
                 if (old == 0ull) {
                     claim = (int)sl;
+                    record = 0;
                     break;
                 }
                 if (old == bits) {
@@ -2057,8 +2072,8 @@ __device__ __forceinline__ WarpOutcome warp_classify(const LaunchArgs &a, const 
             }
         }
         record = __shfl_sync(FULL, record, 0);
-        const ShapeTab no_tab{};
-        res.hash = crop_shape_hash(row, h, w, lane, a.c4 != 0, record ? a.shape_tab : no_tab);
+        if (record && a.spill.rows) spill_crop(a.spill, row, h, w, lane);
+        res.hash = crop_shape_hash(row, h, w, lane, a.c4 != 0, ShapeTab{});
         if (lane == 0 && claim >= 0)
             __stcg(&a.crops[2 * claim + 1], (1ull << 63) | ((unsigned long long)hw << 40) | res.hash);
     }
@@ -2072,7 +2087,11 @@ __global__ void __launch_bounds__(WG_WARPS * 32, 3) classify_warp_kernel(const L
     hist_begin(H);
     const int lane = threadIdx.x & 31;
     const unsigned long long *list = a.list + (size_t)a.klass * a.list_stride;
-    const unsigned long long front = a.list_count[a.klass], total = front + a.list_count[3 + a.klass];
+    // a three-level heavy-first order keeps its middle level in region 1
+    const bool three = a.heavy_first == 2 && !a.bucket && a.klass == 0;
+    const unsigned long long *mid_list = a.list + a.list_stride;
+    const unsigned long long front = a.list_count[a.klass], mid = three ? a.list_count[1] : 0ull;
+    const unsigned long long total = front + mid + a.list_count[3 + a.klass];
     unsigned long long *work_next = a.work_next + a.klass;
     const int b_uniform = log2_colours(a.c);
     unsigned long long q_next = 0, q_end = 0, st_draw = 0, st_seed = 0, st_geno = 0;
@@ -2086,7 +2105,9 @@ __global__ void __launch_bounds__(WG_WARPS * 32, 3) classify_warp_kernel(const L
             q_end = min(nb + (unsigned long long)WG_CHUNK, total);
         }
         const unsigned long long pos = q_next++;
-        const unsigned long long item = list[pos < front ? pos : a.list_stride - 1 - (pos - front)];
+        const unsigned long long item = pos < front ? list[pos]
+                                        : pos < front + mid ? mid_list[pos - front]
+                                                            : list[a.list_stride - 1 - (pos - front - mid)];
         const Item it = load_item(a, item, b_uniform, 32);
         st_geno += 1;
         const WarpOutcome o = warp_classify(a, it, lane, &st_draw, &st_seed);
@@ -2197,6 +2218,49 @@ __device__ void shape_record_cell(const ShapeTab t, uint32_t hash)
         slot = (slot + 1) & mask;
     }
     atomicAdd(&t.stats[2], 1u);
+}
+
+// The side table of shapes of one call (or piece): a warp per crop of the crop
+// table (key: bits, h, w; meta: valid bit and hash) and per spilled crop
+// computes the crop's canonical form and stores or compares it under its hash.
+// A crop-table hash that differs from the recomputed one is counted as a
+// comparison given up (stats[1]): it cannot happen unless a kernel is wrong.
+__global__ void __launch_bounds__(256) shape_scan_kernel(ShapeTab tab, const unsigned long long *crops,
+                                                        unsigned crops_log2, CropSpill spill)
+{
+    const int lane = threadIdx.x & 31;
+    const unsigned long long warp = (blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x) >> 5;
+    const unsigned long long warps = (gridDim.x * (unsigned long long)blockDim.x) >> 5;
+    const unsigned long long nslots = crops ? (1ull << crops_log2) : 0ull;
+    unsigned long long nspill = spill.rows ? *spill.count : 0ull;
+    if (nspill > spill.cap) nspill = spill.cap;
+    for (unsigned long long i = warp; i < nslots + nspill; i += warps) {
+        uint32_t row = 0;
+        int h = 0, w = 0;
+        uint32_t want = 0;
+        bool check = false;
+        if (i < nslots) {
+            const unsigned long long key = crops[2 * i];
+            const unsigned long long meta = crops[2 * i + 1];
+            if (key == 0ull || !(meta >> 63)) continue;  // free slot, or a claim whose hash was never written
+            h = (int)((key >> 48) & 255u);
+            w = (int)(key >> 56);
+            const unsigned long long bits = key & ((1ull << 48) - 1ull);
+            const uint32_t wmask = (w >= 32) ? FULL : ((1u << w) - 1u);
+            if (lane < h) row = (uint32_t)(bits >> (lane * w)) & wmask;
+            want = (uint32_t)meta;
+            check = true;
+        } else {
+            const unsigned long long j = i - nslots;
+            const unsigned m = spill.meta[j];
+            h = (int)(m >> 8);
+            w = (int)(m & 255u);
+            row = spill.rows[j * 32 + lane];
+        }
+        const uint32_t hv = crop_shape_hash(row, h, w, lane, false, tab);
+        if (check && hv != want && lane == 0) atomicAdd(&tab.stats[1], 1u);
+    }
+    if (spill.rows && blockIdx.x == 0 && threadIdx.x == 0 && *spill.count > spill.cap) atomicAdd(&tab.stats[2], 1u);
 }
 
 // move the used slots into a dense list and leave the table empty again
@@ -2443,6 +2507,13 @@ cudaError_t launch_prefilter(const LaunchArgs &a, int smax, int blocks, cudaStre
 cudaError_t launch_table_init(Table t, cudaStream_t st)
 {
     table_init_kernel<<<256, 256, 0, st>>>(t);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_shape_scan(ShapeTab shapes, const unsigned long long *crops, unsigned crops_log2, CropSpill spill,
+                              cudaStream_t st)
+{
+    shape_scan_kernel<<<128, 256, 0, st>>>(shapes, crops, crops_log2, spill);
     return cudaGetLastError();
 }
 

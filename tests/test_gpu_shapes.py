@@ -2,6 +2,8 @@
 for every shape hash of a call's histogram, the canonical form the GPU stored
 equals the oracle's, and both sides count zero collisions (no two distinct
 canonical forms share a hash)."""
+import os
+
 import numpy as np
 import pytest
 
@@ -102,3 +104,53 @@ def test_pipelined_host_call_records_the_same_shapes():
                       c4_hash=True)
     with pytest.raises(J.JatamError):
         J.last_shapes()
+
+
+_NO_CROP_TABLE = r"""
+import json, sys
+import os
+
+import numpy as np
+import torch
+sys.path.insert(0, sys.argv[1])
+from paper_2205_15311_gb300 import binding as J
+n, c, L, k, seed, first, count, sampled = json.loads(sys.argv[2])
+out = torch.empty(count * 8, dtype=torch.uint8, device="cuda")
+hist = torch.empty((1 << 12) * 32, dtype=torch.uint8, device="cuda")
+hlen = torch.zeros(1, dtype=torch.int32, device="cuda")
+J.enumerate_space(n, c, L, k, seed, first, count, sampled=sampled, out=out, hist=hist, hist_len=hlen,
+                  hist_cap=1 << 12, sync=True)
+entries, collisions = J.last_shapes()
+np.save(sys.argv[3] + "/res.npy", J.results_view(out).copy())
+np.save(sys.argv[3] + "/shapes.npy", entries)
+print(json.dumps({"collisions": collisions}))
+"""
+
+
+@pytest.mark.parametrize("case", [(2, 8, 16, 20, 2, 11 << 20, 1 << 14, False),
+                                  (3, 8, 32, 20, 3, 5 << 20, 1 << 14, True)])
+def test_without_the_crop_table_every_form_reaches_the_side_table(case):
+    """With the crop table switched off (JATAM_CROP_TABLE=0, a fresh process)
+    every computed form goes through the spill list to the side table: the
+    results and the table still equal the oracle's."""
+    import json
+    import subprocess
+    import sys
+    import tempfile
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    env = dict(os.environ, JATAM_CROP_TABLE="0")
+    with tempfile.TemporaryDirectory() as tmp:
+        p = subprocess.run([sys.executable, "-c", _NO_CROP_TABLE, root, json.dumps(list(case)), tmp], env=env,
+                           capture_output=True, text=True, timeout=600)
+        assert p.returncode == 0, p.stderr[-4000:]
+        assert json.loads(p.stdout.strip().splitlines()[-1])["collisions"] == 0
+        res = np.load(os.path.join(tmp, "res.npy"))
+        entries = np.load(os.path.join(tmp, "shapes.npy"))
+    n, c, L, k, seed, first, count, sampled = case
+    with O.shape_table() as T:
+        ref, _ = O.enumerate_space(n, c, L, k, seed, first, count, sampled=sampled)
+    assert np.array_equal(res.view(J.RESULT_DTYPE), ref)
+    forms = {int(e["shape_hash"]): J.shape_bitmap(e) for e in entries.view(J.SHAPE_DTYPE)}
+    assert sorted(forms) == sorted(T.forms)
+    for key, bm in forms.items():
+        assert np.array_equal(bm, T.forms[key])
