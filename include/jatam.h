@@ -33,7 +33,7 @@
  *     stream).  The call returns before the work ends unless a host output
  *     buffer was given or cfg->flags has JATAM_SYNC; in those cases it waits
  *     for the stream and also reports errors found on the device;
- *   - a classification of at least 2^24 items whose results (or fitness
+ *   - a classification of at least 2^23 items whose results (or fitness
  *     values) go to page-locked host memory runs in pieces on two internal
  *     streams, each piece's results copied on a third while the next piece is
  *     classified; `stream` waits for all of it before the call returns, and the
@@ -373,7 +373,7 @@ int jatam_autotune(const jatam_config *shapes, uint32_t n_shapes, void *stream);
  * cfg's key: warps_per_cta 1..6, stop_at 1..32 (lanes that must have finished
  * their genotype before a warp leaves a growth round); warps_per_cta 0 forgets
  * the key's setting.  A key never tuned or set uses the defaults: the CTA size
- * that keeps the most warps resident on an SM, and stop_at 14 (lattices up to
+ * that keeps the most warps resident on an SM, and stop_at 18 (lattices up to
  * 16 x 16) or 12 (32 x 32).
  */
 int jatam_set_tuning(const jatam_config *cfg, int warps_per_cta, int stop_at);

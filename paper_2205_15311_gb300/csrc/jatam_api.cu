@@ -55,6 +55,11 @@ struct Tuning {
 std::map<std::tuple<int, int, int>, Tuning> g_tuned;
 
 // optional overrides of the launch shape (for tuning sweeps)
+// host-buffer calls of at least 2 * PIPE_MIN_ITEMS items run in pieces (JATAM_PIPE_PIECE_LOG2 sets it,
+// 2^20 .. 2^26).  End to end on all of S_{2,8} (results to page-locked memory): 2^23 3.17 ms,
+// 2^22 2.91 ms, 2^21 3.33 ms, 2^24 3.19 ms
+size_t PIPE_MIN_ITEMS = size_t(1) << 22;
+
 void read_env_overrides()
 {
     static bool done = false;
@@ -69,6 +74,10 @@ void read_env_overrides()
         if (x >= 1 && x <= MAX_CTA_WARPS) g_warps_override = x;
     }
     if (const char *v = getenv("JATAM_WINDOW")) g_window = atoi(v) != 0;
+    if (const char *v = getenv("JATAM_PIPE_PIECE_LOG2")) {
+        const int x = atoi(v);
+        if (x >= 20 && x <= 26) PIPE_MIN_ITEMS = size_t(1) << x;
+    }
     if (const char *v = getenv("JATAM_CROP_TABLE")) g_crop_table = atoi(v) != 0;
     if (const char *v = getenv("JATAM_HEAVY_LEVELS")) g_heavy_levels = atoi(v) == 2 ? 2 : 3;
     if (const char *v = getenv("JATAM_GENOTYPES_PER_WARP")) {
@@ -104,7 +113,6 @@ constexpr int ESC_CTL_WORDS = 10;
 constexpr unsigned SPILL_CAP = 1u << 16;  // crops the crop table cannot hold, per call or piece (8.3 MB)
 // host-buffer calls of at least 2 * PIPE_MIN_ITEMS items run in up to PIPE_MAX_CHUNKS pieces whose
 // results are copied to the host while the next piece is classified
-constexpr size_t PIPE_MIN_ITEMS = size_t(1) << 23;
 constexpr int PIPE_MAX_CHUNKS = 8;
 
 struct Workspace {

@@ -132,8 +132,10 @@ int default_warps_per_cta(int S, int nt);
 // tuple-table size of a uniform launch of n-tile sets
 inline int tuple_table_size(int n) { return (n >= 1 && n <= 2) ? 8 : 16; }
 // finished lanes that end a growth round when nothing is tuned (measured on
-// S_{2,8} at L = 16 and 19 and on S_{3,8} at L = 32)
-inline int default_stop_at(int S) { return S == 32 ? 12 : 14; }
+// S_{2,8} at L = 16 and 19 and on S_{3,8} at L = 32; 18 for the 8 x 8 and
+// 16 x 16 templates since the three-level heavy-first order: S_{2,8} growth
+// kernel 2.11 ms at 14, 2.09 at 16, 2.085 at 18, 2.10 at 20, 2.15 at 22)
+inline int default_stop_at(int S) { return S == 32 ? 12 : 18; }
 // one genotype per warp (lattices up to 32 x 32, the row-major process): CTAs of
 // *warps_per_cta warps, no dynamic shared memory
 cudaError_t classify_warp_occupancy(int *blocks_per_sm, int *warps_per_cta);

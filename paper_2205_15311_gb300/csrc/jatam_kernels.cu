@@ -1187,17 +1187,20 @@ __device__ __forceinline__ void write_result(const LaunchArgs &a, unsigned long 
 // result of every item it decides, counts them into the histogram, and appends
 // every other item to the list that the growth kernel consumes.
 // ---------------------------------------------------------------------------
+constexpr int PF_ITEMS = 2;  // items per thread and iteration of the pre-filter (its barriers per item halve)
+
 __global__ void __launch_bounds__(256) prefilter_kernel(const LaunchArgs a, int smax)
 {
     // keys decided here: 0 = (ND_LOCAL, 0), 1 = (UNBOUNDED, 0), 2 = (DET_BOUNDED, monomer)
     __shared__ unsigned s_cnt[3];
     __shared__ unsigned long long s_min[3];
-    __shared__ unsigned s_fill[6];               // this iteration's items per list
+    __shared__ unsigned s_fill[2][6];            // an iteration's items per list (two buffers, alternating)
     __shared__ unsigned long long s_base[6];     // where they go in the lists
     if (threadIdx.x < 3) {
         s_cnt[threadIdx.x] = 0u;
         s_min[threadIdx.x] = ~0ull;
     }
+    if (threadIdx.x < 6) s_fill[0][threadIdx.x] = 0u;
     __syncthreads();
     const int lane = threadIdx.x & 31;
     const int b_uniform = log2_colours(a.c);
@@ -1207,88 +1210,109 @@ __global__ void __launch_bounds__(256) prefilter_kernel(const LaunchArgs a, int 
     // the smallest.  Sampled genotypes and GA genomes need the reduction.
     const bool sid_is_index = a.mode == MODE_RANGE || (a.mode == MODE_RECORDS && !a.ids);
     const int nlists = 6;
-    const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
-    for (unsigned long long base = (unsigned long long)blockIdx.x * blockDim.x; base < a.count; base += stride) {
-        const unsigned long long idx = base + threadIdx.x;
-        int key = -1;
-        bool grow = false;
-        int klass = 0;  // the list: size class (one class: 0) + 3 for a light item stored from the region's end
-        unsigned long long sid = 0;
-        if (idx < a.count) {
-            const Item it = load_item<true>(a, idx, b_uniform, smax);
-            sid = it.sid;
-            if (a.bucket) klass = (it.L <= 8) ? 0 : (it.L <= 16) ? 1 : 2;  // (+ 3 below for light items)
-            if (!it.ok) {
-                atomicOr(a.err, ERR_INVALID_ITEM);
-                write_result(a, idx, 255, 0, 0u, 0u);
-            } else if (a.orbits && orbit_rep(it.sid, it.n, it.c, b_uniform) != it.sid) {
-                // not its orbit's representative: the fill pass copies the representative's result
-            } else {
-                const int so = seed_outcome(it.cols, it.n, it.c, it.L);
-                if (so < 0) {
-                    grow = true;
-                    // two or more frontier sites after the seed: the genotypes that can
-                    // run long (on uniform S_{2,8}, 57 % of those that grow, and every
-                    // one of the slowest 1 % in a sample of 7,777); they are handed out
-                    // first, so that the growth launch ends on genotypes with a single
-                    // site, which finish soon (for calls large enough that every lane
-                    // takes many genotypes: in a small call, warps given only heavy
-                    // genotypes would set its length)
-                    if (a.heavy_first && so > -2) klass += 3;
-                    else if (a.heavy_first == 2 && !a.bucket && so == -2) klass = 1;  // the middle level
-                } else if (so == 0) {
-                    write_result(a, idx, JATAM_DET_BOUNDED, it.k, 1u, mono);
-                    key = 2;
+    const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x * PF_ITEMS;
+    int buf = 0;
+    for (unsigned long long base = (unsigned long long)blockIdx.x * blockDim.x * PF_ITEMS; base < a.count;
+         base += stride, buf ^= 1) {
+        int key[PF_ITEMS];
+        bool grow[PF_ITEMS];
+        int klass[PF_ITEMS];  // the list: size class (one class: 0) + 3 for a light item stored from the region's end
+        unsigned long long sid[PF_ITEMS], idxs[PF_ITEMS];
+#pragma unroll
+        for (int u = 0; u < PF_ITEMS; ++u) {
+            const unsigned long long idx = base + (unsigned long long)u * blockDim.x + threadIdx.x;
+            idxs[u] = idx;
+            key[u] = -1;
+            grow[u] = false;
+            klass[u] = 0;
+            sid[u] = 0;
+            if (idx < a.count) {
+                const Item it = load_item<true>(a, idx, b_uniform, smax);
+                sid[u] = it.sid;
+                if (a.bucket) klass[u] = (it.L <= 8) ? 0 : (it.L <= 16) ? 1 : 2;  // (+ 3 below for light items)
+                if (!it.ok) {
+                    atomicOr(a.err, ERR_INVALID_ITEM);
+                    write_result(a, idx, 255, 0, 0u, 0u);
+                } else if (a.orbits && orbit_rep(it.sid, it.n, it.c, b_uniform) != it.sid) {
+                    // not its orbit's representative: the fill pass copies the representative's result
                 } else {
-                    write_result(a, idx, so, 0, 0u, 0u);
-                    key = (so == JATAM_ND_LOCAL) ? 0 : 1;
+                    const int so = seed_outcome(it.cols, it.n, it.c, it.L);
+                    if (so < 0) {
+                        grow[u] = true;
+                        // two or more frontier sites after the seed: the genotypes that can
+                        // run long (on uniform S_{2,8}, 57 % of those that grow, and every
+                        // one of the slowest 1 % in a sample of 7,777); they are handed out
+                        // first, so that the growth launch ends on genotypes with a single
+                        // site, which finish soon (for calls large enough that every lane
+                        // takes many genotypes: in a small call, warps given only heavy
+                        // genotypes would set its length)
+                        if (a.heavy_first && so > -2) klass[u] += 3;
+                        else if (a.heavy_first == 2 && !a.bucket && so == -2) klass[u] = 1;  // the middle level
+                    } else if (so == 0) {
+                        write_result(a, idx, JATAM_DET_BOUNDED, it.k, 1u, mono);
+                        key[u] = 2;
+                    } else {
+                        write_result(a, idx, so, 0, 0u, 0u);
+                        key[u] = (so == JATAM_ND_LOCAL) ? 0 : 1;
+                    }
                 }
             }
         }
         // append to the list of the item's lattice size class (one class unless
         // the launch mixes sizes): warp offsets from shared counters, then one
         // global atomic per list and CTA iteration
-        if (threadIdx.x < 6) s_fill[threadIdx.x] = 0u;
-        __syncthreads();
-        unsigned my_off = 0;
-        for (int kc = 0; kc < nlists; ++kc) {
-            // one size class: lists 0 and 3 (and 1, the middle level of a three-level order)
-            if (!a.bucket && kc % 3 != 0 && !(kc == 1 && a.heavy_first == 2)) continue;
-            const unsigned gm = __ballot_sync(FULL, grow && klass == kc);
-            unsigned woff = 0;
-            if (gm && lane == 0) woff = atomicAdd(&s_fill[kc], (unsigned)__popc(gm));
-            woff = __shfl_sync(FULL, woff, 0);
-            if (grow && klass == kc) my_off = woff + __popc(gm & lanemask_lt());
+        unsigned my_off[PF_ITEMS];
+#pragma unroll
+        for (int u = 0; u < PF_ITEMS; ++u) {
+            my_off[u] = 0;
+            for (int kc = 0; kc < nlists; ++kc) {
+                // one size class: lists 0 and 3 (and 1, the middle level of a three-level order)
+                if (!a.bucket && kc % 3 != 0 && !(kc == 1 && a.heavy_first == 2)) continue;
+                const unsigned gm = __ballot_sync(FULL, grow[u] && klass[u] == kc);
+                unsigned woff = 0;
+                if (gm && lane == 0) woff = atomicAdd(&s_fill[buf][kc], (unsigned)__popc(gm));
+                woff = __shfl_sync(FULL, woff, 0);
+                if (grow[u] && klass[u] == kc) my_off[u] = woff + __popc(gm & lanemask_lt());
+            }
         }
         __syncthreads();
-        if (threadIdx.x < nlists && s_fill[threadIdx.x])
-            s_base[threadIdx.x] = atomicAdd(&a.list_count[threadIdx.x], (unsigned long long)s_fill[threadIdx.x]);
+        if (threadIdx.x < nlists) {
+            const unsigned f = s_fill[buf][threadIdx.x];
+            if (f) s_base[threadIdx.x] = atomicAdd(&a.list_count[threadIdx.x], (unsigned long long)f);
+            s_fill[buf ^ 1][threadIdx.x] = 0u;  // the next iteration's counters
+        }
         __syncthreads();
-        if (grow) {
-            // region klass % 3 of the list buffer: heavy items from its front, light ones from its end
-            const unsigned long long pos = s_base[klass] + my_off;
-            const size_t region = (size_t)(klass % 3) * a.list_stride;
-            a.list[region + (klass < 3 ? pos : a.list_stride - 1 - pos)] = idx;
+#pragma unroll
+        for (int u = 0; u < PF_ITEMS; ++u) {
+            if (grow[u]) {
+                // region klass % 3 of the list buffer: heavy items from its front, light ones from its end
+                const unsigned long long pos = s_base[klass[u]] + my_off[u];
+                const size_t region = (size_t)(klass[u] % 3) * a.list_stride;
+                a.list[region + (klass[u] < 3 ? pos : a.list_stride - 1 - pos)] = idxs[u];
+            }
         }
         if (a.use_hist) {
 #pragma unroll
-            for (int q = 0; q < 3; ++q) {
-                const unsigned m = __ballot_sync(FULL, key == q);
-                if (m) {
-                    unsigned long long v;
-                    if (sid_is_index) {
-                        v = __shfl_sync(FULL, sid, __ffs(m) - 1);
-                    } else {
-                        v = (key == q) ? sid : ~0ull;
+            for (int u = 0; u < PF_ITEMS; ++u) {
 #pragma unroll
-                        for (int off = 16; off > 0; off >>= 1) {
-                            const unsigned long long o = __shfl_xor_sync(FULL, v, off);
-                            v = o < v ? o : v;
+                for (int q = 0; q < 3; ++q) {
+                    const unsigned m = __ballot_sync(FULL, key[u] == q);
+                    if (m) {
+                        unsigned long long v;
+                        if (sid_is_index) {
+                            v = __shfl_sync(FULL, sid[u], __ffs(m) - 1);
+                        } else {
+                            v = (key[u] == q) ? sid[u] : ~0ull;
+#pragma unroll
+                            for (int off = 16; off > 0; off >>= 1) {
+                                const unsigned long long o = __shfl_xor_sync(FULL, v, off);
+                                v = o < v ? o : v;
+                            }
                         }
-                    }
-                    if (lane == 0) {
-                        atomicAdd(&s_cnt[q], (unsigned)__popc(m));
-                        atomicMin(&s_min[q], v);
+                        if (lane == 0) {
+                            atomicAdd(&s_cnt[q], (unsigned)__popc(m));
+                            atomicMin(&s_min[q], v);
+                        }
                     }
                 }
             }

@@ -253,9 +253,9 @@ def test_host_buffers_equal_device_buffers():
 
 def test_pinned_host_buffers_pipelined_equal_device_buffers():
     """Calls whose results go to page-locked host memory and that hold at least
-    2^24 items run in pieces (of at least 2^23) whose copies overlap the next
-    piece's work; the results, the histogram and the fitness values equal the
-    one-pass device call."""
+    2^23 items run in pieces (of at least 2^22, up to 8) whose copies overlap
+    the next piece's work; the results, the histogram and the fitness values
+    equal the one-pass device call."""
     n, c, L, k, seed = 3, 8, 16, 20, 3
     first, count = 1 << 30, (1 << 24) + 4_000_001  # a ragged last piece
     res, dh, m = _dev_enumerate(n, c, L, k, seed, first, count, sampled=True)
