@@ -38,7 +38,7 @@ OPS_PER_PLACEMENT = 62
 OPS_PER_REPLICATE = 37
 OPS_PER_GENOTYPE = 300
 OPS_PER_SHAPED_CELL = 24
-SOAK_S = 1.2  # seconds of back-to-back steps inside the clock record before the timed steps
+SOAK_S = 2.0  # seconds of back-to-back steps inside the clock record before the timed steps
 
 
 def _env_rank():

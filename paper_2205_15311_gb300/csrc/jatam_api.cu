@@ -36,7 +36,7 @@ bool g_mixed_per_shape = false;  // the default launch form of mixed batches (se
 int g_warps_override = 0;
 int g_per_warp_override = 0;  // JATAM_GENOTYPES_PER_WARP: 1 or 32 for every 32 x 32 launch
 int g_window = 1;             // lattices of 17..32: grow in a 16 x 16 window first (JATAM_WINDOW=0: off)
-int g_crop_table = 1;         // the call's crop table of hashes (JATAM_CROP_TABLE=0: every form is computed)
+int g_crop_table = 1;          // the call's crop table of hashes (JATAM_CROP_TABLE=0: every form is computed)
 // levels of the heavy-first order of uniform launches (JATAM_HEAVY_LEVELS=2: two or more frontier
 // sites after the seed, then one).  Three (three or four, then two, then one) measured 1.7 % faster
 // on the S_{2,8} growth kernel (2.182 -> 2.145 ms)
@@ -597,6 +597,8 @@ int run(Workspace *w, LaunchArgs a, int S, jatam_result *out, int32_t *fitness, 
     // compacted once.  Not for records without stream ids (their stream id is
     // the item's index in the call), the orbit mode (members read their
     // representative's result anywhere in the range), graph replay or timed calls.
+    // (device-output calls in pieces on two streams were measured too, with and without the window:
+    // no faster on S_{3,8}, slower on S_{2,8})
     const bool pipelined = n_items >= 2 * PIPE_MIN_ITEMS && !use_graph && !timed && !a.orbits && !a.lifo &&
                            !(a.mode == MODE_RECORDS && !a.ids) && (o.host_out || o.host_fit) &&
                            (!o.host_out || is_pinned(out)) && (!o.host_fit || is_pinned(fitness));
