@@ -409,7 +409,10 @@ int run(Workspace *w, LaunchArgs a, int S, jatam_result *out, int32_t *fitness, 
     a.stop_at = tune.stop_at;
     // lattices of 17 to 32: the items first grow in the 16 x 16 window around the seed, where four
     // times as many warps fit an SM; the few whose growth leaves the window run on the full lattice
-    const bool windowed = !mixed && !a.lifo && S == 32 && tune.per_warp != 1 && g_window;
+    // (for calls of at least 2^23 items: smaller ones end in a thin escalation launch -- on S_{3,8},
+    // 2^22 items 2.67 ms with the window, 2.41 without; 2^24 5.90 against 7.12; 2^26 19.8 against 26.5)
+    const bool windowed = !mixed && !a.lifo && S == 32 && tune.per_warp != 1 && g_window &&
+                          n_items >= (size_t(1) << 23);
     const int regions = mixed ? 3 : (g_heavy_levels == 3 ? 2 : 1);
     if (n_items) {
         int rc = grow(&w->list, &w->list_bytes, n_items * 8 * regions);

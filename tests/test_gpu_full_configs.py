@@ -77,10 +77,18 @@ def test_s38_all_2e28_sampled_genotypes_match_golden():
         counts += np.bincount(part.view(J.RESULT_DTYPE)["cls"], minlength=4)
     assert sha.hexdigest() == gold["results_sha256"]
     assert counts.tolist() == gold["class_counts"]
-    # the largest deterministic bounded shapes found, as the oracle reported them
+    # the largest deterministic bounded shapes found, as the oracle reported them, with their
+    # canonical forms in the call's side table of shapes (and no hash naming two forms)
     largest = json.load(open(os.path.join(GOLDEN, "c3_largest.json")))
     want = [(e["size"], e["shape_hash"], e["count"], e["min_id"]) for e in largest]
     assert largest_det(rows, len(want)) == want
+    entries, collisions = J.last_shapes()
+    assert collisions == 0
+    forms = {int(e["shape_hash"]): J.shape_bitmap(e) for e in entries}
+    assert sorted(forms) == sorted({r[1] for r in rows if r[0] in (0, 2)})
+    for e in largest:
+        bm = np.array([[1 if ch == "#" else 0 for ch in row] for row in e["canonical"]], np.uint8)
+        assert np.array_equal(forms[e["shape_hash"]], bm), e["shape_hash"]
     # a few genotypes re-classified one at a time by the oracle
     res = J.results_view(out)
     rng = np.random.default_rng(11)
@@ -136,3 +144,31 @@ def test_s28_at_the_papers_settings_matches_the_oracle_counts():
     det = {r[1] for r in rows if r[0] == 0}
     steric = {r[1] for r in rows if r[0] == 2}
     assert len(det & steric) == facts["shapes_with_det_and_nd_steric_genotypes"]["count"]
+
+
+def test_window_on_a_ragged_lattice_matches_the_oracle():
+    """A call large enough for the 16 x 16 window (2^23 genotypes of S_{2,8} on
+    a 25 x 25 lattice, 5 replicates): every result and histogram row equals the
+    oracle's, items that leave the window included."""
+    n, c, L, k, seed, first, count = 2, 8, 25, 5, 9, 1 << 23, 1 << 23
+    cap = 1 << 12
+    out = torch.full((count * 8,), 0xEE, dtype=torch.uint8, device="cuda")
+    hist = torch.empty(cap * 32, dtype=torch.uint8, device="cuda")
+    hlen = torch.zeros(1, dtype=torch.int32, device="cuda")
+    J.enumerate_space(n, c, L, k, seed, first, count, out=out, hist=hist, hist_len=hlen, hist_cap=cap, sync=True)
+    ref, _ = O.enumerate_space(n, c, L, k, seed, first, count)
+    assert np.array_equal(J.results_view(out), ref)
+    ids = np.arange(first, first + count, dtype=np.uint64)
+    assert _hist_rows(J.hist_view(hist, int(hlen.item()))) == _hist_rows(O.histogram(ref, ids))
+    assert J.last_shapes()[1] == 0
+
+
+def test_window_on_the_first_2e24_sampled_genotypes_matches_golden():
+    """The first 2^24 of the S_{3,8} sample through the window: the chunk digest
+    the oracle stored."""
+    n, c, L, k, seed, _, _, _ = W.WORKLOADS["s38_sample"]
+    gold = json.load(open(os.path.join(GOLDEN, "c3_summary.json")))
+    count = gold["chunk"]
+    out = torch.empty(count * 8, dtype=torch.uint8, device="cuda")
+    J.enumerate_space(n, c, L, k, seed, 0, count, sampled=True, out=out, sync=True)
+    assert hashlib.sha256(out.cpu().numpy().tobytes()).hexdigest() == gold["chunk_sha256"][0]
