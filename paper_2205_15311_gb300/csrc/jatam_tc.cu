@@ -181,7 +181,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_gemm_kernel(const TcArgs g)
                          : "memory");
         }
         // every thread waits for the products before the buffers are refilled;
-        // the verdict is made uniform so that all threads leave the loop together
+        // the outcome is made uniform so that all threads leave the loop together
         ok = __syncthreads_and(mbar_wait(mb, phase) ? 1 : 0) != 0;
         phase ^= 1u;
     }
