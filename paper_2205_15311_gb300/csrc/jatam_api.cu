@@ -554,7 +554,7 @@ int run(Workspace *w, LaunchArgs a, int S, jatam_result *out, int32_t *fitness, 
         mixed_blocks = pm * w->num_sms;
     }
     long long pblocks = (long long)(n_items + 255) / 256;
-    if (pblocks > 8LL * w->num_sms) pblocks = 8LL * w->num_sms;
+    if (pblocks > PF_CTAS_PER_SM * w->num_sms) pblocks = PF_CTAS_PER_SM * w->num_sms;
     const bool timed = (g_profile & 1) || kernel_ms;
 
     // the device work of the call; `events` brackets the growth kernels
@@ -673,7 +673,7 @@ int run(Workspace *w, LaunchArgs a, int S, jatam_result *out, int32_t *fitness, 
             ac.spill = spill_of(odd ? alt.spill_rows : w->spill_rows, ectl);
             CUDA_TRY(launch_reset(wn, nk, lc, cs, cr, CROPS_LOG2, ectl, ESC_CTL_WORDS));
             long long pb = (long long)(cnt + 255) / 256;
-            if (pb > 8LL * w->num_sms) pb = 8LL * w->num_sms;
+            if (pb > PF_CTAS_PER_SM * w->num_sms) pb = PF_CTAS_PER_SM * w->num_sms;
             CUDA_TRY(launch_prefilter(ac, S, (int)pb, cs));
             if (per_warp) {
                 long long bc = (long long)((cnt + warps - 1) / warps);

@@ -127,6 +127,9 @@ cudaError_t launch_classify(const LaunchArgs &a, int S, int nt, int blocks, int 
 // largest CTA of classify_kernel (its launch bounds hold it to 113 registers so
 // that three such CTAs fit an SM)
 constexpr int MAX_CTA_WARPS = 6;
+// pre-filter grid: at most this many 256-thread CTAs per SM (five are resident at
+// a time; many short CTAs end the launch with a short last wave)
+constexpr long long PF_CTAS_PER_SM = 48;
 // warps per CTA that keep the most warps resident on an SM
 int default_warps_per_cta(int S, int nt);
 // tuple-table size of a uniform launch of n-tile sets

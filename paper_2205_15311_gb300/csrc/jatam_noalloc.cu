@@ -186,7 +186,7 @@ extern "C" int jatam_enumerate_noalloc(const jatam_config *cfg, uint64_t first, 
     if (cudaMemsetAsync(err, 0, 4, st) != cudaSuccess) return noalloc_fail(JATAM_ECUDA, "cudaMemsetAsync failed");
     if (count) {
         long long pblocks = (long long)((count + 255) / 256);
-        if (pblocks > 8LL * d->num_sms) pblocks = 8LL * d->num_sms;
+        if (pblocks > PF_CTAS_PER_SM * d->num_sms) pblocks = PF_CTAS_PER_SM * d->num_sms;
         if (launch_prefilter(a, S, (int)pblocks, st) != cudaSuccess) return noalloc_fail(JATAM_ECUDA, "launch failed");
         if (launch_classify(a, S, nt, (int)blocks, warps, st) != cudaSuccess)
             return noalloc_fail(JATAM_ECUDA, "launch failed");
