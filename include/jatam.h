@@ -288,7 +288,8 @@ typedef struct jatam_mlp jatam_mlp;
 /* Create a network with capacity for batches of up to max_batch genomes;
  * its parameters start at zero (set them with jatam_mlp_set_params).  Its
  * products with 256 output columns run on tcgen05 (accumulator in tensor
- * memory), the others on mma.sync; the environment variable
+ * memory), the 8-column output layer on the CUDA cores (float32 dot products
+ * of a row), the others on mma.sync; the environment variable
  * JATAM_MLP_PRODUCTS=mma, read here, keeps all of them on mma.sync. */
 int jatam_mlp_create(uint64_t max_batch, jatam_mlp **net);
 void jatam_mlp_destroy(jatam_mlp *net);
@@ -314,6 +315,12 @@ int jatam_mlp_predict(jatam_mlp *net, const uint64_t *genomes, uint64_t N, float
  * bits; an all-zero tile never binds, so the classification is unchanged). */
 int jatam_mlp_labels(const jatam_result *results, uint64_t N, uint8_t *labels, void *stream);
 int jatam_embed_genomes(const uint64_t *genomes, uint64_t N, int n, int c, uint64_t *out, void *stream);
+
+/* The selection step of the pre-screen below, on its own: idx[0 .. keep) receives,
+ * in increasing order, the indices of the keep largest of the n scores (all
+ * non-negative float32; ties: lower index first).  scores and idx are device
+ * memory; n <= 2^26, keep <= n.  Queued on `stream`; no synchronisation. */
+int jatam_select_top(const float *scores, uint64_t n, uint64_t keep, uint64_t *idx, void *stream);
 
 /*
  * ga_run_screened -- ga_run with the network as a pre-screen (shape fitness):

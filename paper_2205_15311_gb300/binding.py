@@ -109,6 +109,8 @@ def lib():
         L.jatam_mlp_labels.restype = ctypes.c_int
         L.jatam_embed_genomes.argtypes = [_VP, _U64, ctypes.c_int, ctypes.c_int, _VP, _VP]
         L.jatam_embed_genomes.restype = ctypes.c_int
+        L.jatam_select_top.argtypes = [_VP, _U64, _U64, _VP, _VP]
+        L.jatam_select_top.restype = ctypes.c_int
         L.ga_run_screened.argtypes = [_VP, _VP, _U64, _U32, _U32, _VP, ctypes.c_float, _VP, _VP, _VP, _VP]
         L.ga_run_screened.restype = ctypes.c_int
         L.ga_breed.argtypes = [_VP, _VP, _VP, _U64, _U32, _VP, _VP]
@@ -224,6 +226,10 @@ def jatam_mlp_labels(results, N, labels, stream):
 
 def jatam_embed_genomes(genomes, N, n, c, out, stream):
     return lib().jatam_embed_genomes(genomes, N, n, c, out, stream)
+
+
+def jatam_select_top(scores, n, keep, idx, stream):
+    return lib().jatam_select_top(scores, n, keep, idx, stream)
 
 
 def ga_run_screened(ga, cls, N, generations, ratio, net, online_lr, population, best, total, stream):
@@ -584,6 +590,12 @@ def labels_of(results, labels, stream=None):
     """Device results (uint8 view, 8 B per genotype) -> device class labels."""
     N = int(results.numel() // 8) if hasattr(results, "numel") else int(results.shape[0])
     return check(jatam_mlp_labels(_addr(results), N, _addr(labels), _stream_handle(stream)))
+
+
+def select_top(scores, keep, idx, stream=None):
+    """Device float32 scores [n] -> idx[0 .. keep) (device int64): indices of the
+    keep largest, ties lower index first, in increasing order."""
+    return check(jatam_select_top(_addr(scores), int(scores.shape[0]), int(keep), _addr(idx), _stream_handle(stream)))
 
 
 def embed(genomes, n, c, out, stream=None):

@@ -1423,6 +1423,22 @@ int jatam_mlp_labels(const jatam_result *results, uint64_t N, uint8_t *labels, v
     return JATAM_OK;
 }
 
+int jatam_select_top(const float *scores, uint64_t n, uint64_t keep, uint64_t *idx, void *stream)
+{
+    std::lock_guard<std::mutex> lock(g_mutex);
+    g_last_error.clear();
+    if (n && (!scores || (keep && !idx))) return fail(JATAM_EINVAL, "scores and idx required");
+    if (n > (1ull << 26) || keep > n) return fail(JATAM_EINVAL, "n <= 2^26 and keep <= n required");
+    int dev = 0;
+    CUDA_TRY(cudaGetDevice(&dev));
+    if (n && (kind_of(scores, dev) != K_DEVICE || (keep && kind_of(idx, dev) != K_DEVICE)))
+        return fail(JATAM_EINVAL, "scores and idx must be device memory");
+    if (keep)
+        CUDA_TRY(launch_topn(scores, (long long)n, (long long)keep, reinterpret_cast<unsigned long long *>(idx),
+                             static_cast<cudaStream_t>(stream)));
+    return JATAM_OK;
+}
+
 int jatam_embed_genomes(const uint64_t *genomes, uint64_t N, int n, int c, uint64_t *out, void *stream)
 {
     std::lock_guard<std::mutex> lock(g_mutex);

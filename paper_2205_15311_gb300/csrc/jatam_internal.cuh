@@ -232,6 +232,8 @@ struct ScreenTable {
 // deterministic bounded shape of >= 8 tiles, plus one for the first occurrence
 // of each distinct genome (repeats rank below every distinct genome); idx = the
 // `keep` best (ties: lower index), chosen = cand[idx]
+// indices of the `keep` largest non-negative scores (ties: lower index first), in increasing order
+cudaError_t launch_topn(const float *score, long long n, long long keep, unsigned long long *idx, cudaStream_t st);
 cudaError_t launch_screen(const float *logits, long long n, long long keep, float *score, unsigned long long *idx,
                           const unsigned long long *cand, unsigned long long *chosen, const ScreenTable &t,
                           cudaStream_t st);

@@ -138,6 +138,41 @@ __global__ void features_kernel(const unsigned long long *genomes, long long n, 
     }
 }
 
+// logits = h2 W3 + b3 for the 8-column output layer on the CUDA cores: one
+// thread per row reads the row's 256 bfloat16 activations in 16-byte pieces
+// and accumulates its 8 dot products in float32, k in increasing order (the
+// products of two bfloat16 values are exact in float32); W3 sits in shared
+// memory as float32.  An 8-column tile would leave 7/8 of an mma tile empty.
+__global__ void __launch_bounds__(256) logits_kernel(const __nv_bfloat16 *h2, long long M, const __nv_bfloat16 *w3,
+                                                     const float *b3, float *logits)
+{
+    __shared__ float w[MLP_H][MLP_OUT];
+    for (int i = threadIdx.x; i < MLP_H * MLP_OUT; i += blockDim.x) w[i / MLP_OUT][i % MLP_OUT] = __bfloat162float(w3[i]);
+    __syncthreads();
+    for (long long row = blockIdx.x * (long long)blockDim.x + threadIdx.x; row < M;
+         row += (long long)gridDim.x * blockDim.x) {
+        float acc[MLP_OUT];
+#pragma unroll
+        for (int c = 0; c < MLP_OUT; ++c) acc[c] = 0.f;
+        const uint4 *src = reinterpret_cast<const uint4 *>(h2 + row * MLP_H);
+#pragma unroll 4
+        for (int q = 0; q < MLP_H / 8; ++q) {
+            const uint4 v = src[q];
+            const uint32_t part[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+            for (int e = 0; e < 8; ++e) {
+                const uint32_t bits = (part[e >> 1] >> (16 * (e & 1))) & 0xFFFFu;
+                const float a = __uint_as_float(bits << 16);
+#pragma unroll
+                for (int c = 0; c < MLP_OUT; ++c) acc[c] = fmaf(a, w[8 * q + e][c], acc[c]);
+            }
+        }
+        float4 *dst = reinterpret_cast<float4 *>(logits + row * MLP_OUT);
+        dst[0] = make_float4(acc[0] + b3[0], acc[1] + b3[1], acc[2] + b3[2], acc[3] + b3[3]);
+        dst[1] = make_float4(acc[4] + b3[4], acc[5] + b3[5], acc[6] + b3[6], acc[7] + b3[7]);
+    }
+}
+
 // softmax cross-entropy on float32 logits: d = (softmax - onehot) / B, as
 // float32 (for the bias gradient) and bfloat16 (for the products); the loss
 // summed into *loss (divided by B)
@@ -267,9 +302,12 @@ __global__ void splitk_sum_kernel(const float *part, int splits, long long n, fl
 cudaError_t gemm(const GemmArgs &g, cudaStream_t st, float *splitk = nullptr, const MlpBuffers *tcb = nullptr)
 {
     // the products with 256 output columns and K a multiple of 16 on tcgen05
-    if (tcb && tcb->tc && g.N == 256 && g.M >= 128 && g.K % 16 == 0 &&
+    // (K-contiguous operands with 16-byte aligned rows, K <= 256)
+    const bool bt = g.Bt != nullptr;
+    const long long bn = bt ? g.K : g.b_n;
+    const bool k_major = g.a_k == 1 && (bt || g.b_k == 1) && g.a_m % 8 == 0 && bn % 8 == 0 && g.K <= 256;
+    if (tcb && tcb->tc && k_major && g.N == 256 && g.M >= 128 && g.K % 16 == 0 &&
         (g.epi == EPI_BIAS_RELU_BF16 || g.epi == EPI_MASK_BF16)) {
-        const bool bt = g.Bt != nullptr;
         return tc_gemm_n256(g.A, g.a_m, g.a_k, bt ? g.Bt : g.B, bt ? 1 : g.b_k, bt ? g.K : g.b_n, g.M, g.K,
                             g.epi == EPI_BIAS_RELU_BF16 ? 0 : 1, g.bias, g.mask, g.Cb, tcb->tc_err, st);
     }
@@ -325,7 +363,13 @@ cudaError_t mlp_forward(const MlpBuffers &b, const unsigned long long *genomes, 
     g = GemmArgs{b.h1, MLP_H, 1, Wq + MLP_OFF_W2, MLP_H, 1, (int)B, MLP_H, MLP_H, EPI_BIAS_RELU_BF16,
                  b.p + MLP_OFF_B2, nullptr, nullptr, b.h2, 0, b.wqt + MLP_PAD * MLP_H};
     if ((e = gemm(g, st, nullptr, &b)) != cudaSuccess) return e;
-    // logits = h2 W3 + b3
+    // logits = h2 W3 + b3 (on mma.sync too when every product is kept there)
+    if (b.tc) {
+        const long long blocks = (B + 255) / 256;
+        logits_kernel<<<(unsigned)(blocks < 4096 ? blocks : 4096), 256, 0, st>>>(b.h2, B, Wq + MLP_OFF_W3,
+                                                                                b.p + MLP_OFF_B3, b.logits);
+        return cudaGetLastError();
+    }
     g = GemmArgs{b.h2, MLP_H, 1, Wq + MLP_OFF_W3, MLP_OUT, 1, (int)B, MLP_OUT, MLP_H, EPI_BIAS_F32,
                  b.p + MLP_OFF_B3, nullptr, b.logits, nullptr};
     return gemm(g, st);
@@ -434,31 +478,74 @@ __global__ void score_kernel(const float *logits, long long n, float *score)
 }
 
 // Indices of the `keep` largest non-negative scores among n (ties: lower index
-// first), in increasing index order; one CTA of 1024 threads, radix select on
-// the float bits (monotone for non-negative floats) then an ordered compaction.
-__global__ void __launch_bounds__(1024) topn_kernel(const float *score, long long n, long long keep,
-                                                    unsigned long long *idx_out)
+// first), in increasing index order; one CTA.  A radix select on the float
+// bits (monotone for non-negative floats) finds the key of the keep-th largest
+// score four bits at a time: every thread counts the digits of the keys that
+// match the prefix so far in its own column of a shared table (no atomics), and
+// one warp per digit sums the columns.  Then every warp owns a contiguous
+// segment of the scores and reads it twice, coalesced: first to count the keys
+// above the threshold key and equal to it, then -- after a scan over the warps
+// of those counts, which ranks the equal keys in index order -- to write the
+// chosen indices, each lane at its rank within the warp's ballot.
+constexpr int TOPN_THREADS = 512;
+constexpr int TOPN_BINS = 16;
+
+__global__ void __launch_bounds__(TOPN_THREADS) topn_kernel(const float *score, long long n, long long keep,
+                                                            unsigned long long *idx_out)
 {
-    __shared__ unsigned hist[256];
+    __shared__ unsigned cnt[TOPN_BINS][TOPN_THREADS];
+    __shared__ unsigned tot[TOPN_BINS];
     __shared__ unsigned prefix_s, want_s;
-    __shared__ unsigned long long scan[1024];
+    __shared__ unsigned long long w_above[32], w_equal[32], w_eq_before[32], w_pos[32];
     const uint32_t *key = reinterpret_cast<const uint32_t *>(score);
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const unsigned lt = (1u << lane) - 1u;
     unsigned prefix = 0, mask = 0;
     unsigned long long want = (unsigned long long)keep;  // rank (from the top) still to place inside the prefix
-    for (int shift = 24; shift >= 0; shift -= 8) {
-        for (int i = threadIdx.x; i < 256; i += blockDim.x) hist[i] = 0;
+    const bool vec = (reinterpret_cast<uintptr_t>(score) & 15) == 0;
+    const long long n4 = vec ? n / 4 : 0;  // keys read four at a time; the rest one by one
+    for (int shift = 28; shift >= 0; shift -= 4) {
+#pragma unroll
+        for (int b = 0; b < TOPN_BINS; ++b) cnt[b][tid] = 0u;
+        auto count = [&](uint32_t k) {
+            if ((k & mask) == prefix) cnt[(k >> shift) & 15u][tid] += 1u;
+        };
+        // eight independent 16-byte loads in flight per thread, then their 32 keys counted
+        constexpr int U = 8;
+        for (long long i0 = tid; i0 < n4; i0 += (long long)TOPN_THREADS * U) {
+            uint4 v[U];
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const long long i = i0 + (long long)u * TOPN_THREADS;
+                v[u] = i < n4 ? reinterpret_cast<const uint4 *>(key)[i] : make_uint4(0u, 0u, 0u, 0u);
+            }
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                if (i0 + (long long)u * TOPN_THREADS < n4) {
+                    count(v[u].x);
+                    count(v[u].y);
+                    count(v[u].z);
+                    count(v[u].w);
+                }
+            }
+        }
+        for (long long i = 4 * n4 + tid; i < n; i += TOPN_THREADS) count(key[i]);
         __syncthreads();
-        for (long long i = threadIdx.x; i < n; i += blockDim.x) {
-            const uint32_t k = key[i];
-            if ((k & mask) == prefix) atomicAdd(&hist[(k >> shift) & 255u], 1u);
+        if (warp < TOPN_BINS) {
+            unsigned v = 0;
+            for (int t = lane; t < TOPN_THREADS; t += 32) v += cnt[warp][t];
+#pragma unroll
+            for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+            if (lane == 0) tot[warp] = v;
         }
         __syncthreads();
-        if (threadIdx.x == 0) {
+        if (tid == 0) {
+            // the highest digit d > 0 at which the count from the top reaches `want`, else digit 0
             unsigned long long acc = 0;
-            int d = 255;
+            int d = TOPN_BINS - 1;
             for (; d > 0; --d) {
-                if (acc + hist[d] >= want) break;
-                acc += hist[d];
+                if (acc + tot[d] >= want) break;
+                acc += tot[d];
             }
             prefix_s = prefix | ((unsigned)d << shift);
             want_s = (unsigned)(want - acc);
@@ -466,45 +553,62 @@ __global__ void __launch_bounds__(1024) topn_kernel(const float *score, long lon
         __syncthreads();
         prefix = prefix_s;
         want = want_s;
-        mask |= 255u << shift;
-        __syncthreads();
+        mask |= 15u << shift;
     }
     // prefix is now the key of the keep-th largest; `want` of its copies are taken, lowest indices first
     const uint32_t thr = prefix;
-    const long long per = (n + blockDim.x - 1) / blockDim.x;
-    const long long lo = threadIdx.x * per, hi = min(n, lo + per);
+    const long long seg = ((n + TOPN_THREADS - 1) / TOPN_THREADS) * 32;  // a warp's segment, whole chunks of 32
+    const long long lo = (long long)warp * seg, hi = min(n, lo + seg);
+    // both passes read a warp's chunks eight at a time, all eight loads in flight together
+    constexpr int CB = 8;
     unsigned long long above = 0, equal = 0;
-    for (long long i = lo; i < hi; ++i) {
-        above += key[i] > thr;
-        equal += key[i] == thr;
+    for (long long c0 = lo; c0 < hi; c0 += 32 * CB) {
+        uint32_t kk[CB];
+#pragma unroll
+        for (int u = 0; u < CB; ++u) {
+            const long long i = c0 + 32 * u + lane;
+            kk[u] = i < hi ? key[i] : 0u;
+        }
+#pragma unroll
+        for (int u = 0; u < CB; ++u) {
+            const long long i = c0 + 32 * u + lane;
+            above += __popc(__ballot_sync(0xffffffffu, i < hi && kk[u] > thr));
+            equal += __popc(__ballot_sync(0xffffffffu, i < hi && kk[u] == thr));
+        }
     }
-    // exclusive scan of (equal) to rank the ties, and of (above + chosen ties) for positions
-    scan[threadIdx.x] = equal;
-    __syncthreads();
-    for (int off = 1; off < (int)blockDim.x; off <<= 1) {
-        const unsigned long long v = threadIdx.x >= (unsigned)off ? scan[threadIdx.x - off] : 0ull;
-        __syncthreads();
-        scan[threadIdx.x] += v;
-        __syncthreads();
+    if (lane == 0) {
+        w_above[warp] = above;
+        w_equal[warp] = equal;
     }
-    const unsigned long long eq_before = scan[threadIdx.x] - equal;
     __syncthreads();
-    const unsigned long long take_eq = eq_before >= want ? 0 : min(equal, want - eq_before);
-    scan[threadIdx.x] = above + take_eq;
-    __syncthreads();
-    for (int off = 1; off < (int)blockDim.x; off <<= 1) {
-        const unsigned long long v = threadIdx.x >= (unsigned)off ? scan[threadIdx.x - off] : 0ull;
-        __syncthreads();
-        scan[threadIdx.x] += v;
-        __syncthreads();
+    if (tid == 0) {
+        unsigned long long eq = 0, pos = 0;
+        for (int w = 0; w < TOPN_THREADS / 32; ++w) {
+            w_eq_before[w] = eq;
+            w_pos[w] = pos;
+            const unsigned long long take = eq >= want ? 0ull : min(w_equal[w], want - eq);
+            eq += w_equal[w];
+            pos += w_above[w] + take;
+        }
     }
-    unsigned long long pos = scan[threadIdx.x] - (above + take_eq);
-    unsigned long long eq_left = take_eq;
-    for (long long i = lo; i < hi; ++i) {
-        const uint32_t k = key[i];
-        if (k > thr || (k == thr && eq_left > 0)) {
-            if (k == thr) --eq_left;
-            idx_out[pos++] = (unsigned long long)i;
+    __syncthreads();
+    unsigned long long r = w_eq_before[warp], pos = w_pos[warp];
+    for (long long c0 = lo; c0 < hi; c0 += 32 * CB) {
+        uint32_t kk[CB];
+#pragma unroll
+        for (int u = 0; u < CB; ++u) {
+            const long long i = c0 + 32 * u + lane;
+            kk[u] = i < hi ? key[i] : 0u;
+        }
+#pragma unroll
+        for (int u = 0; u < CB; ++u) {
+            const long long i = c0 + 32 * u + lane;
+            const unsigned eqm = __ballot_sync(0xffffffffu, i < hi && kk[u] == thr);
+            const bool take = (i < hi && kk[u] > thr) || ((eqm >> lane) & 1u && r + __popc(eqm & lt) < want);
+            const unsigned selm = __ballot_sync(0xffffffffu, take);
+            if (take) idx_out[pos + __popc(selm & lt)] = (unsigned long long)i;
+            pos += __popc(selm);
+            r += __popc(eqm);
         }
     }
 }
@@ -564,6 +668,12 @@ __global__ void dedup_mark_kernel(float *score, long long n, const unsigned *fir
         if (first[slot[i]] == (unsigned)i) score[i] += 1.f;
 }
 
+cudaError_t launch_topn(const float *score, long long n, long long keep, unsigned long long *idx, cudaStream_t st)
+{
+    if (n > 0) topn_kernel<<<1, TOPN_THREADS, 0, st>>>(score, n, keep, idx);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_screen(const float *logits, long long n, long long keep, float *score, unsigned long long *idx,
                           const unsigned long long *cand, unsigned long long *chosen, const ScreenTable &t,
                           cudaStream_t st)
@@ -574,7 +684,7 @@ cudaError_t launch_screen(const float *logits, long long n, long long keep, floa
     if ((e = cudaMemsetAsync(t.first, 0xFF, (size_t)(t.cap_mask + 1) * 4, st)) != cudaSuccess) return e;
     dedup_insert_kernel<<<grid_of(n), 256, 0, st>>>(cand, n, t.keys, t.first, t.cap_mask, t.slot, t.err);
     dedup_mark_kernel<<<grid_of(n), 256, 0, st>>>(score, n, t.first, t.slot);
-    topn_kernel<<<1, 1024, 0, st>>>(score, n, keep, idx);
+    topn_kernel<<<1, TOPN_THREADS, 0, st>>>(score, n, keep, idx);
     gather_kernel<<<grid_of(keep), 256, 0, st>>>(cand, idx, keep, chosen);
     return cudaGetLastError();
 }
