@@ -405,6 +405,22 @@ int jatam_set_genotypes_per_warp(const jatam_config *cfg, int genotypes_per_warp
 int jatam_get_genotypes_per_warp(const jatam_config *cfg, int *genotypes_per_warp);
 
 /*
+ * jatam_set_replicate_lanes / jatam_get_replicate_lanes -- replicate lanes for
+ * small calls (Section 2.4's k independent assemblies of a genotype grown side
+ * by side): a warp takes one genotype and its lane r grows replicate r, so a
+ * genotype takes as long as its longest replicate instead of the sum of its
+ * replicates.  Eligible: items of one shape, lattices up to 16 x 16, k <= 32,
+ * the row-major process, no executed-work counters (jatam_profile(2)).
+ *   0: for eligible calls whose item count times k is at most 2^20 (2^22
+ *      for sets of three or more tiles) -- the default; the environment
+ *      variable JATAM_REPLICATE_LANES, read once, sets the mode;
+ *   1: never;   2: for every eligible call.
+ * Results are the same either way.  The setting is per process.
+ */
+int jatam_set_replicate_lanes(int mode);
+int jatam_get_replicate_lanes(void);
+
+/*
  * jatam_set_mixed_plan / jatam_get_mixed_plan -- the CTA plan of the
  * persistent launch for mixed lattice sizes: warps with a 32 x 32, 16 x 16
  * and 8 x 8 region per CTA (at least one 32 x 32 warp, since only those can

@@ -109,6 +109,10 @@ def lib():
         L.jatam_mlp_labels.restype = ctypes.c_int
         L.jatam_embed_genomes.argtypes = [_VP, _U64, ctypes.c_int, ctypes.c_int, _VP, _VP]
         L.jatam_embed_genomes.restype = ctypes.c_int
+        L.jatam_set_replicate_lanes.argtypes = [ctypes.c_int]
+        L.jatam_set_replicate_lanes.restype = ctypes.c_int
+        L.jatam_get_replicate_lanes.argtypes = []
+        L.jatam_get_replicate_lanes.restype = ctypes.c_int
         L.jatam_select_top.argtypes = [_VP, _U64, _U64, _VP, _VP]
         L.jatam_select_top.restype = ctypes.c_int
         L.ga_run_screened.argtypes = [_VP, _VP, _U64, _U32, _U32, _VP, ctypes.c_float, _VP, _VP, _VP, _VP]
@@ -226,6 +230,19 @@ def jatam_mlp_labels(results, N, labels, stream):
 
 def jatam_embed_genomes(genomes, N, n, c, out, stream):
     return lib().jatam_embed_genomes(genomes, N, n, c, out, stream)
+
+
+def jatam_set_replicate_lanes(mode):
+    return lib().jatam_set_replicate_lanes(int(mode))
+
+
+def jatam_get_replicate_lanes():
+    return lib().jatam_get_replicate_lanes()
+
+
+def set_replicate_lanes(mode):
+    """0: replicate lanes for small calls (default), 1: never, 2: whenever eligible."""
+    return check(jatam_set_replicate_lanes(mode))
 
 
 def jatam_select_top(scores, n, keep, idx, stream):

@@ -43,6 +43,14 @@ int g_crop_table = 1;          // the call's crop table of hashes (JATAM_CROP_TA
 int g_heavy_levels = 3;
 // genotypes per warp of a 32 x 32 launch when nothing is tuned or set
 int g_default_per_warp32 = 32;
+// replicate lanes (one genotype per warp, its k replicates side by side): 0 for calls on lattices
+// up to 16 x 16 with k <= 32 whose items x k is at most REPS_MAX_WORK (four times that for sets of
+// three or more tiles, whose genotypes grow longer), 1 never, 2 whenever eligible
+// (jatam_set_replicate_lanes; JATAM_REPLICATE_LANES).  Measured crossovers, L = 16: S_{2,8} slices
+// (k = 20) 2^15 items 0.203 against 0.222 ms, 2^16 0.287 against 0.221; all of S_{2,4} (k = 10)
+// 0.151 against 0.165; S_{3,8} samples (k = 20) 2^17 0.325 against 0.452, 2^18 0.516 against 0.468
+int g_reps_mode = 0;
+size_t REPS_MAX_WORK = size_t(1) << 20;
 
 struct Tuning {
     int warps = 0;    // 0: the CTA size that keeps the most warps resident
@@ -80,6 +88,14 @@ void read_env_overrides()
     }
     if (const char *v = getenv("JATAM_CROP_TABLE")) g_crop_table = atoi(v) != 0;
     if (const char *v = getenv("JATAM_HEAVY_LEVELS")) g_heavy_levels = atoi(v) == 2 ? 2 : 3;
+    if (const char *v = getenv("JATAM_REPLICATE_LANES")) {
+        const int x = atoi(v);
+        if (x >= 0 && x <= 2) g_reps_mode = x;
+    }
+    if (const char *v = getenv("JATAM_REPLICATE_LANES_MAX_LOG2")) {
+        const int x = atoi(v);
+        if (x >= 8 && x <= 30) REPS_MAX_WORK = size_t(1) << x;
+    }
     if (const char *v = getenv("JATAM_GENOTYPES_PER_WARP")) {
         int x = atoi(v);
         if (x == 1 || x == 32) g_per_warp_override = x;
@@ -433,6 +449,21 @@ int run(Workspace *w, LaunchArgs a, int S, jatam_result *out, int32_t *fitness, 
 
     // the single-template launch (not used for mixed sizes)
     const bool per_warp = !mixed && !a.lifo && S == 32 && tune.per_warp == 1;
+    // replicate lanes for calls too small to fill the GPU one genotype per lane (the executed-work
+    // counters model the one-genotype-per-lane kernel, so profiled calls keep it)
+    const bool reps = !mixed && !a.lifo && !a.stats && S <= 16 && a.k >= 1 && a.k <= 32 &&
+                      (g_reps_mode == 2 ||
+                       (g_reps_mode == 0 && n_items * (size_t)a.k <= REPS_MAX_WORK * (a.n >= 3 ? 4 : 1)));
+    const int rwarps = 4;
+    long long rblocks = 0;
+    if (reps && n_items) {
+        int per_sm = 0;
+        CUDA_TRY(classify_reps_prepare(S, tuple_table_size(a.n), rwarps, &per_sm));
+        if (per_sm < 1) return fail(JATAM_ECUDA, "classification kernel does not fit on an SM");
+        rblocks = (long long)per_sm * w->num_sms;
+        const long long needed = (long long)((n_items + rwarps - 1) / rwarps);
+        if (needed < rblocks) rblocks = needed < 1 ? 1 : needed;
+    }
     int warps = tune.warps;
     const int nt = mixed ? 16 : tuple_table_size(a.n);
     long long blocks = 0;
@@ -493,6 +524,10 @@ int run(Workspace *w, LaunchArgs a, int S, jatam_result *out, int32_t *fitness, 
     };
     auto launch_growth = [&](const LaunchArgs &la, long long nb, cudaStream_t s, void *esc,
                              unsigned long long *ctl) -> int {
+        if (reps) {
+            CUDA_TRY(launch_classify_reps(la, S, nt, (int)rblocks, rwarps, s));
+            return JATAM_OK;
+        }
         if (windowed) {
             long long wb = (long long)((la.count + 32ull * tw.warps - 1) / (32ull * tw.warps));
             if (wb > wblocks) wb = wblocks;
@@ -506,6 +541,7 @@ int run(Workspace *w, LaunchArgs a, int S, jatam_result *out, int32_t *fitness, 
     // 8 genotypes on average (pieces of a pipelined call are at least 2^23)
     // (genotypes in progress at once: a lane's, or a warp's with one genotype per warp)
     const unsigned long long lanes = mixed ? 4ull * 160ull * (unsigned long long)w->num_sms  // about 4 CTAs of 5 warps an SM
+                                   : reps ? (unsigned long long)rblocks * rwarps  // one genotype a warp
                                    : windowed ? (unsigned long long)wblocks * tw.warps * 32  // the window launch reads the list
                                            : (unsigned long long)blocks * warps * (per_warp ? 1 : 32);
     a.heavy_first = (n_items >= 8ull * lanes) ? ((!mixed && g_heavy_levels == 3) ? 2 : 1) : 0;
@@ -732,7 +768,7 @@ int run(Workspace *w, LaunchArgs a, int S, jatam_result *out, int32_t *fitness, 
                                   fixed[0].blocks, fixed[0].warps, fixed[0].stop_at, fixed[1].blocks, fixed[1].warps,
                                   fixed[1].stop_at, fixed[2].blocks, fixed[2].warps, fixed[2].stop_at,
                                   a.stats ? 1 : 0, a.c4, a.orbits, per_warp ? 1 : 0, windowed ? 1 : 0,
-                                  wblocks, tw.warps, tw.stop_at, g_heavy_levels};
+                                  wblocks, tw.warps, tw.stop_at, g_heavy_levels, reps ? 1 : 0, rblocks};
         put(nums, sizeof nums);
         cudaGraphExec_t exec = nullptr;
         auto it = w->graphs.find(key);
@@ -1580,6 +1616,23 @@ int jatam_autotune(const jatam_config *shapes, uint32_t n_shapes, void *stream)
         g_tuned[std::make_tuple(S, (int)cfg.n, (int)cfg.c)] = best;
     }
     return JATAM_OK;
+}
+
+int jatam_set_replicate_lanes(int mode)
+{
+    std::lock_guard<std::mutex> lock(g_mutex);
+    g_last_error.clear();
+    read_env_overrides();
+    if (mode < 0 || mode > 2) return fail(JATAM_EINVAL, "mode must be 0 (by call size), 1 (never) or 2 (whenever eligible)");
+    g_reps_mode = mode;
+    return JATAM_OK;
+}
+
+int jatam_get_replicate_lanes(void)
+{
+    std::lock_guard<std::mutex> lock(g_mutex);
+    read_env_overrides();
+    return g_reps_mode;
 }
 
 int jatam_set_genotypes_per_warp(const jatam_config *cfg, int genotypes_per_warp)

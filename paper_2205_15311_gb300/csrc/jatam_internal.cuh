@@ -124,6 +124,10 @@ int classify_smem_bytes(int S, int nt, int warps_per_cta);
 cudaError_t classify_set_attributes(int S, int nt, int warps_per_cta, bool lifo = false);
 cudaError_t classify_occupancy(int S, int nt, int warps_per_cta, int *blocks_per_sm, bool lifo = false);
 cudaError_t launch_classify(const LaunchArgs &a, int S, int nt, int blocks, int warps_per_cta, cudaStream_t st);
+// replicate lanes (S = 8 or 16, k <= 32): one genotype per warp, lane r grows replicate r;
+// prepare sets the shared-memory limit (grow-only) and returns the CTAs an SM holds
+cudaError_t classify_reps_prepare(int S, int nt, int warps_per_cta, int *blocks_per_sm);
+cudaError_t launch_classify_reps(const LaunchArgs &a, int S, int nt, int blocks, int warps_per_cta, cudaStream_t st);
 // largest CTA of classify_kernel (its launch bounds hold it to 113 registers so
 // that three such CTAs fit an SM)
 constexpr int MAX_CTA_WARPS = 6;

@@ -734,6 +734,15 @@ __device__ __forceinline__ void replicate_end(Lane &Ls, uint32_t *my, bool nd, b
     }
 }
 
+// a replicate lane's replicate has ended: local ambiguity, unbounded growth, or
+// (recorded as DET_BOUNDED) an empty frontier in a configuration the warp then
+// compares with replicate 0's
+__device__ __forceinline__ void replicate_end_par(Lane &Ls, bool nd, bool unb)
+{
+    Ls.cls = nd ? JATAM_ND_LOCAL : unb ? JATAM_UNBOUNDED : JATAM_DET_BOUNDED;
+    Ls.phase = PH_DONE;
+}
+
 // ---------------------------------------------------------------------------
 // one growth step of one lane: seed placement or one drawn placement, then the
 // evaluation of the new tile's empty neighbours and the replicate rule
@@ -753,8 +762,11 @@ __device__ __forceinline__ bool current_word(Lane &Ls, uint32_t s, uint32_t &u)
     return true;
 }
 
-// LIFO: the movelist process; stk: this lane's stack (S * S cells, global memory)
-template <int S, bool LIFO>
+// LIFO: the movelist process; stk: this lane's stack (S * S cells, global memory).
+// PAR: replicate lanes -- the lane grows replicate Ls.rep alone on its own lattice
+// (occupancy in OCCA, no comparison with replicate 0 while it grows, no
+// certificates) and only records how it ended (replicate_end_par)
+template <int S, bool LIFO, bool PAR = false>
 __device__ __forceinline__ void lane_step(Lane &Ls, uint32_t *my, uint32_t k0, uint32_t k1, unsigned *err,
                                           uint16_t *stk)
 {
@@ -764,7 +776,7 @@ __device__ __forceinline__ void lane_step(Lane &Ls, uint32_t *my, uint32_t k0, u
     using G = Geo<S>;
     const bool active = Ls.phase == PH_START || Ls.phase == PH_GROW;
     const bool seed = Ls.phase == PH_START;
-    const int occ = (Ls.rep == 0) ? G::OCCA : G::OCCB;
+    const int occ = (PAR || Ls.rep == 0) ? G::OCCA : G::OCCB;
     int b = 0, tau = 0;
     bool placing = active;
     if (LIFO && active && !seed) {
@@ -867,7 +879,7 @@ __device__ __forceinline__ void lane_step(Lane &Ls, uint32_t *my, uint32_t k0, u
     const uint32_t fw_b = my[(G::FRONT + (b >> 5)) * 32];
     if (placing) {
         my[(occ + (b >> 5)) * 32] = ow_b | (1u << (b & 31));
-        if (seed && Ls.rep == 0) nib_set<S>(my, b, 0);
+        if (seed && (PAR || Ls.rep == 0)) nib_set<S>(my, b, 0);
         Ls.size += 1;
         Ls.ymin = seed ? py : min(Ls.ymin, py);
         Ls.ymax = seed ? py : max(Ls.ymax, py);
@@ -875,7 +887,7 @@ __device__ __forceinline__ void lane_step(Lane &Ls, uint32_t *my, uint32_t k0, u
         Ls.xmax = seed ? px : max(Ls.xmax, px);
         Ls.dlo = min(Ls.dlo, py - 1);
         Ls.dhi = max(Ls.dhi, py + 1);
-        if (Ls.rep > 0) {
+        if (!PAR && Ls.rep > 0) {
             Ls.blo = min(Ls.blo, py);
             Ls.bhi = max(Ls.bhi, py);
         }
@@ -916,12 +928,12 @@ __device__ __forceinline__ void lane_step(Lane &Ls, uint32_t *my, uint32_t k0, u
         // replicate 0: an occupied neighbour that could receive from the new
         // tile a tuple other than its own breaks the closure of the final
         // shape -- unless it is the seed, which every replicate places first
-        if (placing && Ls.rep == 0 && in && (ow & qbit) && (M & ~(1u << tq)) != 0 && qb != seed_cell) Ls.cert = 0;
+        if (!PAR && placing && Ls.rep == 0 && in && (ow & qbit) && (M & ~(1u << tq)) != 0 && qb != seed_cell) Ls.cert = 0;
         if (placing && empty && !isf && M != 0 && !multi) {
             const int tn = __ffs(M) - 1;
             // replicate 0 must hold the same tuple here, or this replicate can
             // no longer end in replicate 0's configuration
-            if (Ls.rep > 0 && !Ls.diverged && (!(my[(G::OCCA + qw) * 32] & qbit) || tq != tn)) Ls.diverged = 1;
+            if (!PAR && Ls.rep > 0 && !Ls.diverged && (!(my[(G::OCCA + qw) * 32] & qbit) || tq != tn)) Ls.diverged = 1;
             my[(G::NIB + (qb >> 3)) * 32] = (nw & ~(15u << sh)) | ((uint32_t)tn << sh);
             // a fresh read: an earlier side of this step may have set a bit of the same word
             my[(G::FRONT + qw) * 32] |= qbit;
@@ -958,7 +970,10 @@ __device__ __forceinline__ void lane_step(Lane &Ls, uint32_t *my, uint32_t k0, u
         }
     }
     __syncwarp();
-    if (placing && (nd || unb || Ls.nF == 0)) replicate_end<S>(Ls, my, nd, unb);
+    if (placing && (nd || unb || Ls.nF == 0)) {
+        if constexpr (PAR) replicate_end_par(Ls, nd, unb);
+        else replicate_end<S>(Ls, my, nd, unb);
+    }
     __syncwarp();
 }
 
@@ -1718,6 +1733,217 @@ __global__ void __launch_bounds__(MAX_CTA_WARPS * 32, 3) classify_kernel(const L
     hist_end(H, a);
 }
 
+// ---------------------------------------------------------------------------
+// Replicate lanes, for calls too small to fill the GPU one genotype per lane: a
+// warp takes one genotype at a time and lane r grows its replicate r (k <= 32)
+// on the lane's own lattice, all k at once.  A replicate's process depends
+// only on the genotype and on r (the draws are keyed by genotype, replicate and
+// step), so each lane follows exactly the path replicate r takes in the
+// sequential process.  Once every lane has ended, the first deciding replicate
+// is the first r whose replicate ended in local ambiguity or unbounded growth,
+// or (r > 0) in a configuration other than replicate 0's -- other cells or
+// another tuple on a cell -- which is steric non-determinism; with none, the
+// genotype is deterministic.  The shape is replicate 0's (lane 0's lattice).
+// The latency of a genotype becomes that of its longest replicate instead of
+// the sum over its replicates, at the cost of the exact shortcuts, which
+// skip replicates that the lanes here run side by side anyway.
+// ---------------------------------------------------------------------------
+// 0xF in nibble i for every set bit i of a byte
+__device__ __forceinline__ uint32_t nibble_mask(uint32_t byte)
+{
+    uint32_t m = byte & 255u;
+    m = (m | (m << 12)) & 0x000F000Fu;
+    m = (m | (m << 6)) & 0x03030303u;
+    m = (m | (m << 3)) & 0x11111111u;
+    return m * 0xFu;
+}
+
+template <int S, int NT>
+__device__ __forceinline__ void reps_loop(const LaunchArgs &a, uint32_t *warp_lanes, SmemHist &H,
+                                          const unsigned long long *list, unsigned long long front,
+                                          unsigned long long back, unsigned long long *work_next,
+                                          const unsigned long long *mid_list, unsigned long long mid)
+{
+    const unsigned long long total = front + mid + back;
+    using G = Geo<S, NT>;
+    const int lane = threadIdx.x & 31;
+    uint32_t *my = warp_lanes + lane;
+    for (int w = 0; w < 3 * G::NW; ++w) my[w * 32] = 0u;
+    __syncwarp();
+    Lane Ls;
+    Ls.phase = PH_DONE;
+    Ls.dlo = S;
+    Ls.dhi = -1;
+    Ls.blo = S;
+    Ls.bhi = -1;
+    Ls.n = a.n; Ls.c = a.c; Ls.L = a.L; Ls.k = a.k;
+    Ls.cls = 0; Ls.decided = 0; Ls.hash = 0; Ls.size0 = 0;
+    Ls.item = 0; Ls.sid = 0; Ls.cols = 0;
+    Ls.rep = Ls.step = Ls.size = Ls.nF = 0;
+    Ls.fc = 0ull;
+    Ls.sp = 0;
+    Ls.x0 = Ls.x1 = Ls.y0 = Ls.y1 = 0;
+    Ls.ymin = Ls.ymax = Ls.xmin = Ls.xmax = 0;
+    Ls.diverged = 0;
+    Ls.forced = 0;
+    Ls.cert = 0;
+    Ls.ka = Ls.kb = NO_BLOCK;
+    Ls.pa = Ls.pb = make_uint4(0, 0, 0, 0);
+    const int b_uniform = log2_colours(a.c);
+    for (;;) {
+        unsigned long long pos = 0;
+        if (lane == 0) pos = atomicAdd(work_next, 1ull);
+        pos = __shfl_sync(FULL, pos, 0);
+        if (pos >= total) break;
+        const unsigned long long item = pos < front ? list[pos]
+                                        : pos < front + mid ? mid_list[pos - front]
+                                                            : list[a.list_stride - 1 - (pos - front - mid)];
+        const Item it = load_item(a, item, b_uniform, S);
+        Ls.item = item;
+        Ls.sid = it.sid;
+        Ls.cols = it.cols;
+        Ls.n = it.n; Ls.c = it.c; Ls.L = it.L; Ls.k = it.k;
+        lane_tables<S, NT>(my, Ls.cols, Ls.n, Ls.c);
+        if (Ls.dlo <= Ls.dhi) {
+            const int lo = max(Ls.dlo, 0), hi = min(Ls.dhi, S - 1);
+            clear_rows<S>(my, G::OCCA, lo, hi);
+            clear_rows<S>(my, G::FRONT, lo, hi);
+        }
+        Ls.dlo = S;
+        Ls.dhi = -1;
+        Ls.rep = lane;
+        Ls.ka = Ls.kb = NO_BLOCK;
+        Ls.cls = JATAM_DET_BOUNDED;  // a lane without a replicate never deviates
+        Ls.phase = lane < Ls.k ? PH_START : PH_DONE;
+        __syncwarp();
+        // every lane one step a round until all replicates have ended; the Philox block of a
+        // lane's draw is computed in the round that first needs it (the lanes move in step,
+        // so they need new blocks in the same rounds)
+        for (;;) {
+            const uint32_t key = (uint32_t)Ls.rep * 512u + ((uint32_t)Ls.step >> 2);
+            const bool need = Ls.phase == PH_GROW && Ls.ka != key;
+            if (__any_sync(FULL, need) && need) {
+                Ls.pa = philox_block(key, Ls.sid, a.key0, a.key1);
+                Ls.ka = key;
+            }
+            lane_step<S, false, true>(Ls, my, a.key0, a.key1, a.err, nullptr);
+            if (!__any_sync(FULL, Ls.phase == PH_START || Ls.phase == PH_GROW)) break;
+        }
+        __syncwarp();
+        // the first replicate that deviates from replicate 0
+        const int size0 = __shfl_sync(FULL, Ls.size, 0);
+        bool dev = false;
+        if (lane < Ls.k) {
+            if (Ls.cls != JATAM_DET_BOUNDED) {
+                dev = true;
+            } else if (lane > 0) {
+                if (Ls.size != size0) dev = true;
+                for (int w = 0; w < G::NW && !dev; ++w) {
+                    const uint32_t o = my[(G::OCCA + w) * 32], o0 = warp_lanes[(G::OCCA + w) * 32];
+                    if (o != o0) {
+                        dev = true;
+                    } else if (o) {
+#pragma unroll
+                        for (int q = 0; q < 4; ++q) {
+                            const uint32_t m = nibble_mask(o >> (8 * q));
+                            const int nw = G::NIB + 4 * w + q;
+                            if ((my[nw * 32] ^ warp_lanes[nw * 32]) & m) dev = true;
+                        }
+                    }
+                }
+            }
+        }
+        const unsigned devm = __ballot_sync(FULL, dev);
+        const int r = devm ? __ffs(devm) - 1 : 0;
+        const int cr = __shfl_sync(FULL, Ls.cls, r);
+        const int cls = !devm ? JATAM_DET_BOUNDED : (cr != JATAM_DET_BOUNDED ? cr : JATAM_ND_STERIC);
+        const int decided = !devm ? Ls.k : r;
+        // replicate 0's shape: the launch's crop table, else one warp-wide job
+        uint32_t hash = 0;
+        const bool shaped = cls == JATAM_DET_BOUNDED || cls == JATAM_ND_STERIC;
+        if (shaped) {
+            int have = 0, record = 0, claim = -1;
+            uint32_t hv = 0;
+            if (lane == 0) {
+                Ls.x0 = Ls.xmin;
+                Ls.x1 = Ls.xmax;
+                Ls.y0 = Ls.ymin;
+                Ls.y1 = Ls.ymax;
+                const int h = Ls.y1 - Ls.y0 + 1, w = Ls.x1 - Ls.x0 + 1;
+                record = 1;
+                if (a.crops && h * w <= CROP_CELLS) {
+                    const uint32_t wmask = (w >= 32) ? FULL : ((1u << w) - 1u);
+                    unsigned long long bits = 0;
+                    for (int i = 0; i < h; ++i) {
+                        const int b = (Ls.y0 + i) * S + Ls.x0;
+                        bits |= (unsigned long long)((my[(G::OCCA + (b >> 5)) * 32] >> (b & 31)) & wmask) << (i * w);
+                    }
+                    const uint32_t hw = ((uint32_t)h << 8) | (uint32_t)w;
+                    const unsigned mask = (1u << a.crops_log2) - 1u;
+                    const unsigned long long key = crop_key(bits, h, w);
+                    const unsigned s0 = (unsigned)((key * 0x9E3779B97F4A7C15ull) >> 40) & mask;
+                    // a few probes: the crop's meta word holds its hash once its claimer has written it;
+                    // a free slot is claimed (key by compare-and-swap) before the form is computed
+                    for (int p = 0; p < CROP_PROBES; ++p) {
+                        const unsigned sl = (s0 + (unsigned)p) & mask;
+                        unsigned long long k = __ldcg(&a.crops[2 * sl]);
+                        if (k == 0ull) {
+                            k = atomicCAS(&a.crops[2 * sl], 0ull, key);
+                            if (k == 0ull) {
+                                claim = (int)sl;
+                                record = 0;
+                                break;
+                            }
+                        }
+                        if (k == key) {
+                            record = 0;
+                            const unsigned long long meta = __ldcg(&a.crops[2 * sl + 1]);
+                            if ((meta >> 63) && (uint32_t)((meta >> 40) & 0xFFFFu) == hw) {
+                                hv = (uint32_t)meta;
+                                have = 1;
+                            }
+                            break;
+                        }
+                    }
+                }
+            }
+            have = __shfl_sync(FULL, have, 0);
+            record = __shfl_sync(FULL, record, 0);
+            if (!have) {
+                hv = coop_shape_hash<S>(0, warp_lanes, Ls, lane, a.c4 != 0, record != 0 && a.spill.rows != nullptr,
+                                        a.spill);
+                if (lane == 0 && claim >= 0) {
+                    const unsigned long long meta = (1ull << 63) |
+                        ((unsigned long long)(((Ls.y1 - Ls.y0 + 1) << 8) | (Ls.x1 - Ls.x0 + 1)) << 40) | hv;
+                    __stcg(&a.crops[2 * claim + 1], meta);
+                }
+            }
+            hash = hv;
+        }
+        if (lane == 0) {
+            const unsigned size = shaped ? (unsigned)size0 : 0u;
+            write_result(a, Ls.item, cls, decided, size, hash);
+            if (a.use_hist) hist_insert(H, a.table, ((unsigned long long)cls << 32) | hash, 1u, Ls.sid, size, size, a.err);
+        }
+        __syncwarp();
+    }
+}
+
+template <int S, int NT>
+__global__ void __launch_bounds__(MAX_CTA_WARPS * 32, 3) classify_reps_kernel(const LaunchArgs a)
+{
+    extern __shared__ uint32_t smem_lanes[];
+    __shared__ SmemHist H;
+    hist_begin(H);
+    const int warp = threadIdx.x >> 5;
+    uint32_t *warp_lanes = smem_lanes + (size_t)warp * Geo<S, NT>::WORDS * 32;
+    const bool three = a.heavy_first == 2 && !a.bucket && a.klass == 0;
+    reps_loop<S, NT>(a, warp_lanes, H, a.list + (size_t)a.klass * a.list_stride, a.list_count[a.klass],
+                     a.list_count[3 + a.klass], a.work_next + a.klass, three ? a.list + a.list_stride : nullptr,
+                     three ? a.list_count[1] : 0ull);
+    hist_end(H, a);
+}
+
 // Mixed lattice sizes in one persistent launch: the first plan_w32 warps of a
 // CTA own 32 x 32 regions, the next plan_w16 16 x 16 regions, the rest 8 x 8.
 // A warp first works through the list of its own size class, then steals from
@@ -2446,6 +2672,53 @@ int default_warps_per_cta(int S, int nt)
     }
     c = best;
     return c;
+}
+
+namespace {
+// the replicate-lanes instance for lattice template S (8 or 16) and tuple-table size nt
+template <typename F>
+auto with_reps_instance(int S, int nt, F f)
+{
+    if (nt == 8) {
+        if (S == 8) return f(classify_reps_kernel<8, 8>, smem_bytes_for<8, 8>);
+        return f(classify_reps_kernel<16, 8>, smem_bytes_for<16, 8>);
+    }
+    if (S == 8) return f(classify_reps_kernel<8, 16>, smem_bytes_for<8, 16>);
+    return f(classify_reps_kernel<16, 16>, smem_bytes_for<16, 16>);
+}
+}  // namespace
+
+cudaError_t classify_reps_prepare(int S, int nt, int warps_per_cta, int *blocks_per_sm)
+{
+    static std::mutex mu;
+    static std::map<std::tuple<int, int, int>, int> limit;  // (device, S, nt) -> bytes set (grow-only)
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    {
+        std::lock_guard<std::mutex> lock(mu);
+        const int bytes = with_reps_instance(S, nt, [&](auto, auto bytes_for) { return bytes_for(warps_per_cta); });
+        int &have = limit[std::make_tuple(dev, S, nt)];
+        if (bytes > have) {
+            e = with_reps_instance(S, nt, [&](auto kernel, auto) {
+                return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+            });
+            if (e != cudaSuccess) return e;
+            have = bytes;
+        }
+    }
+    return with_reps_instance(S, nt, [&](auto kernel, auto bytes_for) {
+        return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, kernel, warps_per_cta * 32,
+                                                             bytes_for(warps_per_cta));
+    });
+}
+
+cudaError_t launch_classify_reps(const LaunchArgs &a, int S, int nt, int blocks, int warps_per_cta, cudaStream_t st)
+{
+    return with_reps_instance(S, nt, [&](auto kernel, auto bytes_for) {
+        kernel<<<dim3(blocks), dim3(warps_per_cta * 32), bytes_for(warps_per_cta), st>>>(a);
+        return cudaGetLastError();
+    });
 }
 
 cudaError_t launch_classify(const LaunchArgs &a, int S, int nt, int blocks, int warps_per_cta, cudaStream_t st)
