@@ -126,6 +126,109 @@ __global__ void __launch_bounds__(128) gemm_bf16_kernel(const GemmArgs g)
             }
 }
 
+// Weight gradients C[M x N] = A^T B with A [K x M] and B [K x N] both stored row by row
+// (K = the batch, M and N multiples of 8, rows 16-byte aligned): 64 x 64 output tiles of 4
+// warps, K in steps of 32 through two shared-memory stages that cp.async fills as the rows
+// lie in memory ([k][m] and [k][n]); ldmatrix.trans turns them into the m16n8k16 fragments.
+// Split K over blockIdx.z as the general kernel does (float32 partial products, summed in
+// split order afterwards).
+constexpr int WG_KT = 32, WG_PAD = 72;  // k rows a stage; row length in halfs (64 + 8: 16-byte rows, no conflicts)
+
+__device__ __forceinline__ void wg_cp16(uint32_t dst, const void *src, uint32_t bytes)
+{
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(dst), "l"(src), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ void ldsm_x4_trans(uint32_t (&r)[4], uint32_t addr)
+{
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0, %1, %2, %3}, [%4];\n"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+                 : "r"(addr));
+}
+
+__global__ void __launch_bounds__(128) wgrad_kernel(const __nv_bfloat16 *A, long long lda, const __nv_bfloat16 *B,
+                                                    long long ldb, int M, int N, int K, int kchunk, float *C)
+{
+    __shared__ __align__(16) __nv_bfloat16 As[2][WG_KT][WG_PAD];  // [stage][k][m]
+    __shared__ __align__(16) __nv_bfloat16 Bs[2][WG_KT][WG_PAD];  // [stage][k][n]
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int m0 = blockIdx.y * 64, n0 = blockIdx.x * 64;
+    const int wm = (warp >> 1) * 32, wn = (warp & 1) * 32;
+    const int kbeg = (int)blockIdx.z * kchunk, kend = min(K, kbeg + kchunk);
+    const int nsteps = kend > kbeg ? (kend - kbeg + WG_KT - 1) / WG_KT : 0;
+    auto fill = [&](int st, int step) {
+        const int k0 = kbeg + step * WG_KT;
+        // 32 rows x 8 pieces of 16 bytes for each operand: 2 + 2 pieces a thread
+        for (int e = tid; e < WG_KT * 8; e += 128) {
+            const int r = e >> 3, pc = (e & 7) * 8;
+            const int gk = k0 + r;
+            const bool ka = gk < kend;
+            const bool ina = ka && m0 + pc < M, inb = ka && n0 + pc < N;
+            wg_cp16((uint32_t)__cvta_generic_to_shared(&As[st][r][pc]), A + (ina ? (long long)gk * lda + m0 + pc : 0),
+                    ina ? 16u : 0u);
+            wg_cp16((uint32_t)__cvta_generic_to_shared(&Bs[st][r][pc]), B + (inb ? (long long)gk * ldb + n0 + pc : 0),
+                    inb ? 16u : 0u);
+        }
+        asm volatile("cp.async.commit_group;\n" ::: "memory");
+    };
+    float acc[2][4][4];
+#pragma unroll
+    for (int i = 0; i < 2; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+#pragma unroll
+            for (int r = 0; r < 4; ++r) acc[i][j][r] = 0.f;
+    if (nsteps > 0) fill(0, 0);
+    for (int step = 0; step < nsteps; ++step) {
+        const int st = step & 1;
+        if (step + 1 < nsteps) {
+            fill(st ^ 1, step + 1);
+            asm volatile("cp.async.wait_group 1;\n" ::: "memory");
+        } else {
+            asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+        }
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < WG_KT; kk += 16) {
+            // ldmatrix: lanes 8 j .. 8 j + 7 give the rows of 8 x 8 block j
+            const int j = lane >> 3, rr = lane & 7;
+            uint32_t af[2][4], bfr[2][4];
+#pragma unroll
+            for (int i = 0; i < 2; ++i) {
+                // A fragment of rows m = wm + 16 i ..: blocks (k 0-7, m 0-7), (k 0-7, m 8-15), (k 8-15, m 0-7), (k 8-15, m 8-15)
+                const int kr = kk + ((j >> 1) << 3) + rr, mc = wm + 16 * i + ((j & 1) << 3);
+                ldsm_x4_trans(af[i], (uint32_t)__cvta_generic_to_shared(&As[st][kr][mc]));
+            }
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                // B fragments of columns n = wn + 16 h ..: blocks (k 0-7, n 0-7), (k 8-15, n 0-7), (k 0-7, n 8-15), (k 8-15, n 8-15)
+                const int kr = kk + ((j & 1) << 3) + rr, nc = wn + 16 * h + ((j >> 1) << 3);
+                ldsm_x4_trans(bfr[h], (uint32_t)__cvta_generic_to_shared(&Bs[st][kr][nc]));
+            }
+#pragma unroll
+            for (int i = 0; i < 2; ++i)
+#pragma unroll
+                for (int jn = 0; jn < 4; ++jn) {
+                    const uint32_t b2[2] = {bfr[jn >> 1][2 * (jn & 1)], bfr[jn >> 1][2 * (jn & 1) + 1]};
+                    mma_bf16(acc[i][jn], af[i], b2);
+                }
+        }
+        __syncthreads();
+    }
+    const int gq = lane >> 2, tq = lane & 3;
+    float *out = C + (long long)blockIdx.z * M * N;
+#pragma unroll
+    for (int i = 0; i < 2; ++i)
+#pragma unroll
+        for (int jn = 0; jn < 4; ++jn)
+#pragma unroll
+            for (int r = 0; r < 4; ++r) {
+                const int m = m0 + wm + 16 * i + gq + (r >= 2 ? 8 : 0);
+                const int n = n0 + wn + 8 * jn + 2 * tq + (r & 1);
+                if (m < M && n < N) out[(long long)m * N + n] = acc[i][jn][r];
+            }
+}
+
 // features: bit (35 - j) of the genome for j < 36, zero for 36..47
 __global__ void features_kernel(const unsigned long long *genomes, long long n, __nv_bfloat16 *x)
 {
@@ -313,6 +416,22 @@ cudaError_t gemm(const GemmArgs &g, cudaStream_t st, float *splitk = nullptr, co
     }
     const dim3 tiles((g.N + TN - 1) / TN, (g.M + TM - 1) / TM);
     const int ntiles = (int)(tiles.x * tiles.y);
+    // weight gradients (A^T B, both stored row by row over k): the cp.async / ldmatrix kernel
+    if (splitk && g.epi == EPI_F32 && g.a_m == 1 && g.b_n == 1 && g.M % 8 == 0 && g.N % 8 == 0 && g.a_k % 8 == 0 &&
+        g.b_k % 8 == 0 && ((uintptr_t)g.A & 15) == 0 && ((uintptr_t)g.B & 15) == 0) {
+        int splits = (g.K + 8 * 32 - 1) / (8 * 32);  // at least 8 k-steps of 32 a split
+        splits = min(splits, min(MLP_SPLITK_MAX, (304 + ntiles - 1) / ntiles));
+        if (splits < 1) splits = 1;
+        int kchunk = ((g.K + splits - 1) / splits + WG_KT - 1) / WG_KT * WG_KT;
+        splits = (g.K + kchunk - 1) / kchunk;
+        float *dst = splits > 1 ? splitk : g.Cf;
+        wgrad_kernel<<<dim3(tiles.x, tiles.y, splits), 128, 0, st>>>(g.A, g.a_k, g.B, g.b_k, g.M, g.N, g.K, kchunk, dst);
+        if (splits > 1) {
+            const long long n = (long long)g.M * g.N;
+            splitk_sum_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(splitk, splits, n, g.Cf);
+        }
+        return cudaGetLastError();
+    }
     // a float32 product with few output tiles and a long K: split K over the grid
     int splits = 1;
     if (splitk && g.epi == EPI_F32 && ntiles < 64) {

@@ -122,9 +122,12 @@ def test_ga_run_shape_fitness_matches_oracle():
 def test_screened_ga_reaches_the_best_shape_with_fewer_simulations():
     """The network as a pre-screen pays: at the same number
     of simulations, 5 generations of N = 2048 survivors (every survivor
-    simulated by the plain classification), the screened GA reaches a verified
+    simulated by the plain classification) screened from 8 candidates each (the
+    screen ratio of the GA configuration), the screened GA reaches a verified
     best fitness of 32 in more of 12 independent runs than the plain GA, and its
-    mean verified best is higher."""
+    mean verified best is higher.  (Over 32 runs on a GB300: 28 against 4, mean
+    best 30.5 against 20.4; at a ratio of 4, 13 against 4 -- a margin that 12
+    runs do not always show.)"""
     from paper_2205_15311_gb300 import surrogate as S
     dev = torch.device("cuda")
     genomes, labels = S.build_training_set(torch, dev, s28_sample=1 << 21, s38_sample=1 << 21)
@@ -134,7 +137,7 @@ def test_screened_ga_reaches_the_best_shape_with_fewer_simulations():
     net.set_params(S.initial_params(0))
     S.train(torch, net, genomes, labels, steps=3000, batch=8192, lr=2e-3)
     trained = net.get_params()
-    N, G, ratio = 2048, 5, 4
+    N, G, ratio = 2048, 5, 8
     thr = J.poisson_thresholds(0.03)
     best_plain, best_screened = [], []
     for sd in range(12):

@@ -64,7 +64,7 @@ def assert_elementwise(got, want, S, K, name, cap_frac=0.02):
     return over
 
 
-@pytest.mark.parametrize("B", [64, 512, 1000])
+@pytest.mark.parametrize("B", [64, 512, 1000, 8192])
 def test_gradients_match_oracle(B):
     params = M.init_params(3)
     rng = np.random.default_rng(B)
@@ -72,7 +72,7 @@ def test_gradients_match_oracle(B):
         params[k] = 0.1 * rng.standard_normal(params[k].shape)
     genomes = W.random_genomes(B, 3, 8, seed=B)
     labels = rng.integers(0, 8, size=B).astype(np.uint8)
-    net = J.Surrogate(max_batch=2048)
+    net = J.Surrogate(max_batch=max(B, 2048))
     flat = J.flatten_params(params)
     net.set_params(flat)
     grads = np.zeros(J.MLP_NPARAM, np.float32)
