@@ -3,7 +3,7 @@ of the keep largest scores, ties broken by the lower index, in increasing
 order -- element by element against numpy's stable sort on the same scores.
 The cases have many equal scores (the threshold value repeated across the
 warps' segments), the screening size of the GA configuration (65,536
-candidates, keep 8,192) with a ragged tail, and the degenerate ends."""
+candidates, keep 8,192) and odd counts around it, and the degenerate ends."""
 import numpy as np
 import pytest
 
@@ -36,8 +36,8 @@ def _got(scores, keep):
 
 
 @pytest.mark.parametrize("n,keep,levels", [(65536, 8192, 0), (65536 + 77, 8192, 0), (65536, 8192, 7),
-                                           (8192, 2048, 3), (1000, 1, 0), (1000, 1000, 2), (33, 5, 1),
-                                           (300000, 4096, 50), (5000, 0, 0)])
+                                           (65535, 8192, 0), (65533, 30000, 4), (8192, 2048, 3), (1000, 1, 0),
+                                           (1000, 1000, 2), (33, 5, 1), (300000, 4096, 50), (5000, 0, 0)])
 def test_select_top_matches_numpy(n, keep, levels):
     rng = np.random.default_rng(n + keep + levels)
     if levels:
