@@ -1237,7 +1237,7 @@ int ga_loop(const jatam_ga_config *ga, const jatam_config *cls, int fitness_kind
             gg.Nc = M;
             gg.children = w->screen_cand;
             CUDA_TRY(launch_ga_breed(gg, st));
-            CUDA_TRY(mlp_forward(net->b, w->screen_cand, (long long)M, st));
+            CUDA_TRY(mlp_forward(net->b, w->screen_cand, (long long)M, st, true));
             CUDA_TRY(launch_screen(net->b.logits, (long long)M, (long long)N, w->screen_score, w->screen_idx,
                                    w->screen_cand, pop, w->screen_table, st));
         }
@@ -1437,7 +1437,7 @@ int jatam_mlp_predict(jatam_mlp *m, const uint64_t *genomes, uint64_t N, float *
         CUDA_TRY(cudaMemcpyAsync(m->stage, genomes, (size_t)N * 8, cudaMemcpyHostToDevice, st));
         dg = static_cast<const unsigned long long *>(m->stage);
     }
-    CUDA_TRY(mlp_forward(m->b, dg, (long long)N, st));
+    CUDA_TRY(mlp_forward(m->b, dg, (long long)N, st, true));
     CUDA_TRY(cudaMemcpyAsync(logits, m->b.logits, (size_t)N * MLP_OUT * 4, cudaMemcpyDefault, st));
     if (kg == K_HOST || ko == K_HOST) {
         CUDA_TRY(cudaStreamSynchronize(st));

@@ -213,12 +213,17 @@ struct MlpBuffers {
     int tc;                      // 1: products with 256 columns on tcgen05; 0: all on mma.sync
 };
 // D[M x 256] = A[M x K] B[K x 256] on tcgen05 (jatam_tc.cu); epi 0: bias + ReLU,
-// 1: ReLU mask; K a multiple of 16
+// 1: ReLU mask; 2: bias + ReLU, then logits[M x 8] = bf16(D) W3 + b3 instead of D;
+// K a multiple of 16, at most 256, both operands K-contiguous
 cudaError_t tc_gemm_n256(const __nv_bfloat16 *A, long long a_m, long long a_k, const __nv_bfloat16 *B, long long b_k,
                          long long b_n, int M, int K, int epi, const float *bias, const __nv_bfloat16 *mask,
-                         __nv_bfloat16 *C, unsigned *err, cudaStream_t st);
+                         __nv_bfloat16 *C, unsigned *err, cudaStream_t st, const __nv_bfloat16 *w3 = nullptr,
+                         const float *b3 = nullptr, float *logits = nullptr);
 constexpr int MLP_SPLITK_MAX = 32;
-cudaError_t mlp_forward(const MlpBuffers &b, const unsigned long long *genomes, long long B, cudaStream_t st);
+// logits_only: the caller needs the logits alone (no backward pass follows), so the second hidden
+// layer is not stored: its tensor-core epilogue computes the logits
+cudaError_t mlp_forward(const MlpBuffers &b, const unsigned long long *genomes, long long B, cudaStream_t st,
+                        bool logits_only = false);
 cudaError_t mlp_backward(const MlpBuffers &b, const uint8_t *labels, long long B, cudaStream_t st);
 cudaError_t mlp_adam(const MlpBuffers &b, float lr, int t, cudaStream_t st);
 cudaError_t mlp_refresh_bf16(const MlpBuffers &b, cudaStream_t st);

@@ -467,7 +467,8 @@ const long long MLP_OFF_W3 = MLP_OFF_B2 + MLP_H;
 const long long MLP_OFF_B3 = MLP_OFF_W3 + (long long)MLP_H * MLP_OUT;
 const long long MLP_NPARAM = MLP_OFF_B3 + MLP_OUT;
 
-cudaError_t mlp_forward(const MlpBuffers &b, const unsigned long long *genomes, long long B, cudaStream_t st)
+cudaError_t mlp_forward(const MlpBuffers &b, const unsigned long long *genomes, long long B, cudaStream_t st,
+                        bool logits_only)
 {
     features_kernel<<<grid_for(B * MLP_PAD), 256, 0, st>>>(genomes, B, b.x);
     cudaError_t e = cudaGetLastError();
@@ -478,6 +479,11 @@ cudaError_t mlp_forward(const MlpBuffers &b, const unsigned long long *genomes, 
     g = GemmArgs{b.x, MLP_PAD, 1, Wq + MLP_OFF_W1, MLP_H, 1, (int)B, MLP_H, MLP_PAD, EPI_BIAS_RELU_BF16,
                  b.p + MLP_OFF_B1, nullptr, nullptr, b.h1, 0, b.wqt};
     if ((e = gemm(g, st, nullptr, &b)) != cudaSuccess) return e;
+    if (logits_only && b.tc) {
+        // logits = bf16(relu(h1 W2 + b2)) W3 + b3 in the epilogue of the second layer's product
+        return tc_gemm_n256(b.h1, MLP_H, 1, b.wqt + MLP_PAD * MLP_H, 1, MLP_H, (int)B, MLP_H, 2, b.p + MLP_OFF_B2,
+                            nullptr, nullptr, b.tc_err, st, Wq + MLP_OFF_W3, b.p + MLP_OFF_B3, b.logits);
+    }
     // h2 = relu(h1 W2 + b2)
     g = GemmArgs{b.h1, MLP_H, 1, Wq + MLP_OFF_W2, MLP_H, 1, (int)B, MLP_H, MLP_H, EPI_BIAS_RELU_BF16,
                  b.p + MLP_OFF_B2, nullptr, nullptr, b.h2, 0, b.wqt + MLP_PAD * MLP_H};

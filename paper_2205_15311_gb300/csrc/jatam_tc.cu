@@ -36,7 +36,7 @@ constexpr int TC_MAX_KCH = 4;                      // K <= 256
 constexpr int TC_MAX_RING = 8;
 constexpr int TC_STAGE_WORDS = 32 * 20;            // a warp's epilogue staging: 32 rows of 16 words, 16-byte padded
 constexpr int TC_CTRL_BYTES = 2048;                // mbarriers (64 B), the TMEM address, the bias (1 KB)
-constexpr int TC_SMEM_BUDGET = 220 * 1024;
+constexpr int TC_SMEM_BUDGET = 226 * 1024;
 constexpr unsigned TC_WAIT_LIMIT = 1u << 20;       // mbarrier polls before giving up (about a second)
 constexpr unsigned TC_ERR_TIMEOUT = 1u;
 
@@ -92,10 +92,14 @@ struct TcArgs {
     long long b_n;       // element (k, n) at B[n * b_n + k]
     int M, K;            // N = 256; K a multiple of 16, at most 256
     int ring;            // A ring slots
-    int epi;             // 0: bias + ReLU -> bf16; 1: ReLU mask -> bf16
+    int epi;             // 0: bias + ReLU -> bf16; 1: ReLU mask -> bf16; 2: bias + ReLU, rounded to bf16,
+                         // then the 8 logits of the row (W3, b3) instead of the row itself
     const float *bias;
     const __nv_bfloat16 *mask;
-    __nv_bfloat16 *C;    // [M x 256] row-major
+    __nv_bfloat16 *C;    // [M x 256] row-major (epi 0, 1)
+    const __nv_bfloat16 *w3;  // epi 2: [256 x 8] row-major
+    const float *b3;          // epi 2: [8]
+    float *logits;            // epi 2: [M x 8] row-major
     unsigned *err;
 };
 
@@ -148,7 +152,13 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_gemm_kernel(const TcArgs g)
             asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(mbar + i)) : "memory");
         asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
     }
-    for (int i = tid; i < TC_N; i += TC_THREADS) sbias[i] = g.epi == 0 ? g.bias[i] : 0.f;
+    for (int i = tid; i < TC_N; i += TC_THREADS) sbias[i] = g.epi != 1 ? g.bias[i] : 0.f;
+    // epi 2: W3 as float32 in the staging area (which that epilogue does not use for rows), and
+    // after it the column halves' partial logits
+    float *w3s = reinterpret_cast<float *>(stage);                 // [256][8]
+    float *xch = reinterpret_cast<float *>(stage) + TC_N * 8;      // [128 rows][8]
+    if (g.epi == 2)
+        for (int i = tid; i < TC_N * 8; i += TC_THREADS) w3s[i] = __bfloat162float(g.w3[i]);
 
     // B, resident: chunk c holds k in [64 c, 64 c + 64) of all 256 columns (zero past K)
     for (int e = tid; e < nkc * TC_N * (TC_KC / 8); e += TC_THREADS) {
@@ -227,6 +237,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_gemm_kernel(const TcArgs g)
             const int wrow = m0 + quarter * 32;
             const uint32_t lane_base = tmem + ((uint32_t)(quarter * 32) << 16);
             uint32_t *st = stage + warp * TC_STAGE_WORDS;
+            float part[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};  // epi 2: this half's logits of the row
             for (int cp = half * (TC_N / 2); cp < (half + 1) * (TC_N / 2); cp += 64) {
                 // two 32-column reads, one wait
                 uint32_t r[64];
@@ -254,25 +265,44 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_gemm_kernel(const TcArgs g)
 #pragma unroll
                 for (int b = 0; b < 2; ++b) {
                     const int c0 = cp + 32 * b;
-                    // this lane's row, 32 columns, rounded to bfloat16 (bias + ReLU first for epi 0);
+                    // this lane's row, 32 columns, rounded to bfloat16 (bias + ReLU first for epi 0 and 2);
                     // the bias of the 32 columns, the same for every lane, read 16 bytes at a time
                     uint32_t w[16];
 #pragma unroll
                     for (int q4 = 0; q4 < 8; ++q4) {
-                        const float4 bb = g.epi == 0 ? *reinterpret_cast<const float4 *>(sbias + c0 + 4 * q4)
+                        const float4 bb = g.epi != 1 ? *reinterpret_cast<const float4 *>(sbias + c0 + 4 * q4)
                                                      : make_float4(0.f, 0.f, 0.f, 0.f);
                         const float bv[4] = {bb.x, bb.y, bb.z, bb.w};
 #pragma unroll
                         for (int h = 0; h < 4; h += 2) {
                             const int j = 4 * q4 + h;
                             float v0 = __uint_as_float(r[32 * b + j]), v1 = __uint_as_float(r[32 * b + j + 1]);
-                            if (g.epi == 0) {
+                            if (g.epi != 1) {
                                 v0 = fmaxf(v0 + bv[h], 0.f);
                                 v1 = fmaxf(v1 + bv[h + 1], 0.f);
                             }
                             const __nv_bfloat162 hv = __floats2bfloat162_rn(v0, v1);
                             w[j >> 1] = *reinterpret_cast<const uint32_t *>(&hv);
                         }
+                    }
+                    if (g.epi == 2) {
+                        // the row's partial logits over these 32 columns, in column order, from the
+                        // rounded activations (the values a stored row would hold)
+#pragma unroll
+                        for (int j = 0; j < 32; ++j) {
+                            const float a = __uint_as_float(j & 1 ? (w[j >> 1] & 0xFFFF0000u) : (w[j >> 1] << 16));
+                            const float4 wa = *reinterpret_cast<const float4 *>(w3s + (c0 + j) * 8);
+                            const float4 wb = *reinterpret_cast<const float4 *>(w3s + (c0 + j) * 8 + 4);
+                            part[0] = fmaf(a, wa.x, part[0]);
+                            part[1] = fmaf(a, wa.y, part[1]);
+                            part[2] = fmaf(a, wa.z, part[2]);
+                            part[3] = fmaf(a, wa.w, part[3]);
+                            part[4] = fmaf(a, wb.x, part[4]);
+                            part[5] = fmaf(a, wb.y, part[5]);
+                            part[6] = fmaf(a, wb.z, part[6]);
+                            part[7] = fmaf(a, wb.w, part[7]);
+                        }
+                        continue;
                     }
 #pragma unroll
                     for (int q4 = 0; q4 < 4; ++q4)
@@ -307,7 +337,26 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_gemm_kernel(const TcArgs g)
                     __syncwarp();
                 }
             }
-            // every warp has read the accumulator before the next tile's products overwrite it
+            if (g.epi == 2) {
+                // the second column half hands its partial logits to the first, which adds them (first
+                // half + second half, then the bias) and stores the row's 8 logits
+                if (half == 1) {
+#pragma unroll
+                    for (int c = 0; c < 8; ++c) xch[(quarter * 32 + lane) * 8 + c] = part[c];
+                }
+                __syncthreads();
+                const int grow = wrow + lane;
+                if (half == 0 && grow < g.M) {
+                    float o[8];
+#pragma unroll
+                    for (int c = 0; c < 8; ++c) o[c] = part[c] + xch[(quarter * 32 + lane) * 8 + c] + g.b3[c];
+                    float4 *dst = reinterpret_cast<float4 *>(g.logits + (long long)grow * 8);
+                    dst[0] = make_float4(o[0], o[1], o[2], o[3]);
+                    dst[1] = make_float4(o[4], o[5], o[6], o[7]);
+                }
+            }
+            // every warp has read the accumulator (and the exchanged logits) before the next tile's
+            // products overwrite it
             asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
             __syncthreads();
             asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
@@ -327,7 +376,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_gemm_kernel(const TcArgs g)
 
 cudaError_t tc_gemm_n256(const __nv_bfloat16 *A, long long a_m, long long a_k, const __nv_bfloat16 *B, long long b_k,
                          long long b_n, int M, int K, int epi, const float *bias, const __nv_bfloat16 *mask,
-                         __nv_bfloat16 *C, unsigned *err, cudaStream_t st)
+                         __nv_bfloat16 *C, unsigned *err, cudaStream_t st, const __nv_bfloat16 *w3, const float *b3,
+                         float *logits)
 {
     static int sms[64] = {};
     int dev = 0;
@@ -346,14 +396,14 @@ cudaError_t tc_gemm_n256(const __nv_bfloat16 *A, long long a_m, long long a_k, c
     // K-contiguous operands with 16-byte aligned rows only (the caller keeps the others on mma.sync)
     if (K <= 0 || K % 16 != 0 || K > TC_MAX_KCH * TC_KC || a_k != 1 || b_k != 1 || a_m % 8 != 0 || b_n % 8 != 0 ||
         ((uintptr_t)A & 15) != 0 || ((uintptr_t)B & 15) != 0 || ((uintptr_t)C & 15) != 0 ||
-        (epi == 1 && ((uintptr_t)mask & 15) != 0))
+        (epi == 1 && ((uintptr_t)mask & 15) != 0) || (epi == 2 && (!w3 || !b3 || ((uintptr_t)logits & 15) != 0)))
         return cudaErrorInvalidValue;
     const int nkc = (K + TC_KC - 1) / TC_KC;
     const int fixed = nkc * TC_B_BYTES + 8 * TC_STAGE_WORDS * 4 + TC_CTRL_BYTES;
     const int ring = min(TC_MAX_RING, (TC_SMEM_BUDGET - fixed) / TC_A_BYTES);
     const int bytes = fixed + ring * TC_A_BYTES;
     const int ntiles = (M + TC_M - 1) / TC_M;
-    TcArgs g{A, a_m, B, b_n, M, K, ring, epi, bias, mask, C, err};
+    TcArgs g{A, a_m, B, b_n, M, K, ring, epi, bias, mask, C, w3, b3, logits, err};
     tc_gemm_kernel<<<(unsigned)min(ntiles, sms[dev]), TC_THREADS, bytes, st>>>(g);
     return cudaGetLastError();
 }

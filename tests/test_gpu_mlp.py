@@ -64,7 +64,7 @@ def assert_elementwise(got, want, S, K, name, cap_frac=0.02):
     return over
 
 
-@pytest.mark.parametrize("B", [64, 512, 1000, 8192])
+@pytest.mark.parametrize("B", [64, 512, 1000, 8192, 40000])
 def test_gradients_match_oracle(B):
     params = M.init_params(3)
     rng = np.random.default_rng(B)
@@ -115,6 +115,29 @@ def test_predict_matches_oracle_and_training_lowers_the_loss():
     assert last < 0.3 * first
     after = J.unflatten_params(net.get_params())
     assert not np.allclose(after["W1"], params["W1"])
+    net.close()
+
+
+def test_predict_at_screening_size_matches_oracle():
+    """A prediction over more rows than the tensor-core product has CTAs (65,613:
+    several 128-row tiles a CTA, a ragged last tile), where the logits come out
+    of the second layer's epilogue without the layer being stored."""
+    params = M.init_params(7)
+    rng = np.random.default_rng(7)
+    for k in ("b1", "b2", "b3"):
+        params[k] = 0.1 * rng.standard_normal(params[k].shape)
+    n = 65613
+    net = J.Surrogate(max_batch=n)
+    net.set_params(J.flatten_params(params))
+    genomes = W.random_genomes(n, 3, 8, seed=21)
+    dg = torch.from_numpy(genomes.view(np.int64)).cuda()
+    logits = torch.empty((n, 8), dtype=torch.float32, device="cuda")
+    net.predict(dg, logits)
+    got = logits.cpu().numpy()
+    p32 = J.unflatten_params(J.flatten_params(params))
+    want = M.predict(p32, M.genome_bits(genomes))
+    S = M.magnitude_sums(p32, M.genome_bits(genomes), np.zeros(n, np.int64))
+    assert_elementwise(got, want, S["logits"], 256, "logits", cap_frac=0.05)
     net.close()
 
 
