@@ -550,6 +550,43 @@ def reference_arm(args):
     return 0
 
 
+def network_profile_case(args, torch, J, dev):
+    """Small cases of the network and pre-screen kernels for ncu: screened GA
+    generations (population 8192, ratio 8, device-side best) or predictions."""
+    from paper_2205_15311_gb300 import surrogate as S
+    from paper_2205_15311_gb300 import workloads as W
+    N, ratio = 8192, 8
+    net = J.Surrogate(max_batch=max(N * ratio, args.profile_predict))
+    net.set_params(S.initial_params(5))
+    if args.profile_predict:
+        n = args.profile_predict
+        g = torch.from_numpy(W.random_genomes(n, 3, 8, seed=3).view(np.int64)).to(dev)
+        logits = torch.empty((n, 8), dtype=torch.float32, device=dev)
+        for i in range(args.warmup + args.steps):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            net.predict(g, logits)
+            b.record()
+            torch.cuda.synchronize()
+            if i >= args.warmup:
+                print(json.dumps({"profile_predict": n, "ms": round(a.elapsed_time(b), 4)}))
+    else:
+        G = args.profile_screen
+        thr = J.poisson_thresholds(0.01)
+        ga = J.make_ga(3, 8, 5, selection=J.TOURNAMENT, tournament=4, crossover=J.NO_CROSSOVER,
+                       mutation_thresholds=thr)
+        pop = torch.from_numpy(W.random_genomes(N, 3, 8, seed=5).view(np.int64)).to(dev)
+        best = torch.zeros(G, dtype=torch.int32, device=dev)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        J.run_ga_screened(ga, pop, G, ratio, net, online_lr=1e-3, L=16, k=20, seed=5, best=best)
+        b.record()
+        torch.cuda.synchronize()
+        print(json.dumps({"profile_screen_generations": G, "ms_per_generation": round(a.elapsed_time(b) / G, 4)}))
+    net.close()
+    return 0
+
+
 def main():
     global WORKLOAD
     ap = argparse.ArgumentParser()
@@ -574,6 +611,13 @@ def main():
     ap.add_argument("--profile-genomes", type=int, default=0,
                     help="instead of the bench: ga_evaluate on this many uniform random genomes of the "
                          "workload's space (a representative small case for ncu); prints timings only")
+    ap.add_argument("--profile-screen", type=int, default=0,
+                    help="instead of the bench: this many screened GA generations (population 8192 of "
+                         "S_{3,8}, screen ratio 8, an untrained network) -- the network and pre-screen "
+                         "kernels for ncu; prints timings only")
+    ap.add_argument("--profile-predict", type=int, default=0,
+                    help="instead of the bench: network predictions of this many S_{3,8} genomes "
+                         "(the warm-up count, then the step count); prints timings only")
     ap.add_argument("--count", type=int, default=0,
                     help="classify only the first COUNT genotypes (small profiling cases; not a bench line)")
     args = ap.parse_args()
@@ -596,6 +640,8 @@ def main():
     import __graft_entry__
     __graft_entry__.build()
     from paper_2205_15311_gb300 import binding as J
+    if args.profile_screen or args.profile_predict:
+        return network_profile_case(args, torch, J, dev)
     if WORKLOAD == "mixed":
         return mixed_arm(args, torch, J, dev)
     if WORKLOAD == "ga":
