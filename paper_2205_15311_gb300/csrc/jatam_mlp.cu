@@ -42,6 +42,8 @@ struct GemmArgs {
     __nv_bfloat16 *Cb;             // [M x N] row-major bfloat16 output
     int kchunk;                    // split-K: CTA z covers k in [z kchunk, (z + 1) kchunk); 0: all of K
     const __nv_bfloat16 *Bt;       // the same B with K contiguous (element (k, n) at Bt[n * K + k]), or null
+    int bias_row;                  // weight gradients: also the column sums of B, as row M of C (the bias
+                                   // gradient, stored right after the weights)
 };
 
 __device__ __forceinline__ void mma_bf16(float (&c)[4], const uint32_t (&a)[4], const uint32_t (&b)[2])
@@ -147,7 +149,8 @@ __device__ __forceinline__ void ldsm_x4_trans(uint32_t (&r)[4], uint32_t addr)
 }
 
 __global__ void __launch_bounds__(128) wgrad_kernel(const __nv_bfloat16 *A, long long lda, const __nv_bfloat16 *B,
-                                                    long long ldb, int M, int N, int K, int kchunk, float *C)
+                                                    long long ldb, int M, int N, int K, int kchunk, float *C,
+                                                    int bias_row)
 {
     __shared__ __align__(16) __nv_bfloat16 As[2][WG_KT][WG_PAD];  // [stage][k][m]
     __shared__ __align__(16) __nv_bfloat16 Bs[2][WG_KT][WG_PAD];  // [stage][k][n]
@@ -178,6 +181,9 @@ __global__ void __launch_bounds__(128) wgrad_kernel(const __nv_bfloat16 *A, long
         for (int j = 0; j < 4; ++j)
 #pragma unroll
             for (int r = 0; r < 4; ++r) acc[i][j][r] = 0.f;
+    // bias_row: the CTAs of the first row of tiles also sum B's columns over their K range (in k order)
+    const bool colsum = bias_row && blockIdx.y == 0 && tid < 64;
+    float bsum = 0.f;
     if (nsteps > 0) fill(0, 0);
     for (int step = 0; step < nsteps; ++step) {
         const int st = step & 1;
@@ -188,6 +194,10 @@ __global__ void __launch_bounds__(128) wgrad_kernel(const __nv_bfloat16 *A, long
             asm volatile("cp.async.wait_group 0;\n" ::: "memory");
         }
         __syncthreads();
+        if (colsum) {
+#pragma unroll 8
+            for (int r = 0; r < WG_KT; ++r) bsum += __bfloat162float(Bs[st][r][tid]);
+        }
 #pragma unroll
         for (int kk = 0; kk < WG_KT; kk += 16) {
             // ldmatrix: lanes 8 j .. 8 j + 7 give the rows of 8 x 8 block j
@@ -216,7 +226,8 @@ __global__ void __launch_bounds__(128) wgrad_kernel(const __nv_bfloat16 *A, long
         __syncthreads();
     }
     const int gq = lane >> 2, tq = lane & 3;
-    float *out = C + (long long)blockIdx.z * M * N;
+    float *out = C + (long long)blockIdx.z * (M + bias_row) * N;
+    if (colsum && n0 + tid < N) out[(long long)M * N + n0 + tid] = bsum;
 #pragma unroll
     for (int i = 0; i < 2; ++i)
 #pragma unroll
@@ -229,15 +240,25 @@ __global__ void __launch_bounds__(128) wgrad_kernel(const __nv_bfloat16 *A, long
             }
 }
 
-// features: bit (35 - j) of the genome for j < 36, zero for 36..47
+// features: bit (35 - j) of the genome for j < 36, zero for 36..47 (bfloat16 1.0 is 0x3F80); a
+// thread per row, the row's 96 bytes in six 16-byte stores
 __global__ void features_kernel(const unsigned long long *genomes, long long n, __nv_bfloat16 *x)
 {
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n * MLP_PAD;
-         i += (long long)gridDim.x * blockDim.x) {
-        const long long r = i / MLP_PAD;
-        const int j = (int)(i % MLP_PAD);
-        const float v = (j < MLP_IN) ? (float)((genomes[r] >> (MLP_IN - 1 - j)) & 1ull) : 0.f;
-        x[i] = __float2bfloat16_rn(v);
+    for (long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x; r < n; r += (long long)gridDim.x * blockDim.x) {
+        const unsigned long long g = genomes[r];
+        uint4 *dst = reinterpret_cast<uint4 *>(x + r * MLP_PAD);
+#pragma unroll
+        for (int q = 0; q < MLP_PAD / 8; ++q) {
+            uint32_t w[4];
+#pragma unroll
+            for (int h = 0; h < 4; ++h) {
+                const int j0 = 8 * q + 2 * h, j1 = j0 + 1;
+                const uint32_t lo = (j0 < MLP_IN && ((g >> (MLP_IN - 1 - j0)) & 1ull)) ? 0x3F80u : 0u;
+                const uint32_t hi = (j1 < MLP_IN && ((g >> (MLP_IN - 1 - j1)) & 1ull)) ? 0x3F80u : 0u;
+                w[h] = lo | (hi << 16);
+            }
+            dst[q] = make_uint4(w[0], w[1], w[2], w[3]);
+        }
     }
 }
 
@@ -402,6 +423,13 @@ __global__ void splitk_sum_kernel(const float *part, int splits, long long n, fl
     }
 }
 
+// the weight-gradient kernel's shapes: A^T B with both operands stored row by row over k
+bool wgrad_ok(const GemmArgs &g, const float *splitk)
+{
+    return splitk && g.epi == EPI_F32 && g.a_m == 1 && g.b_n == 1 && g.M % 8 == 0 && g.N % 8 == 0 && g.a_k % 8 == 0 &&
+           g.b_k % 8 == 0 && ((uintptr_t)g.A & 15) == 0 && ((uintptr_t)g.B & 15) == 0;
+}
+
 cudaError_t gemm(const GemmArgs &g, cudaStream_t st, float *splitk = nullptr, const MlpBuffers *tcb = nullptr)
 {
     // the products with 256 output columns and K a multiple of 16 on tcgen05
@@ -417,17 +445,17 @@ cudaError_t gemm(const GemmArgs &g, cudaStream_t st, float *splitk = nullptr, co
     const dim3 tiles((g.N + TN - 1) / TN, (g.M + TM - 1) / TM);
     const int ntiles = (int)(tiles.x * tiles.y);
     // weight gradients (A^T B, both stored row by row over k): the cp.async / ldmatrix kernel
-    if (splitk && g.epi == EPI_F32 && g.a_m == 1 && g.b_n == 1 && g.M % 8 == 0 && g.N % 8 == 0 && g.a_k % 8 == 0 &&
-        g.b_k % 8 == 0 && ((uintptr_t)g.A & 15) == 0 && ((uintptr_t)g.B & 15) == 0) {
+    if (wgrad_ok(g, splitk)) {
         int splits = (g.K + 8 * 32 - 1) / (8 * 32);  // at least 8 k-steps of 32 a split
         splits = min(splits, min(MLP_SPLITK_MAX, (304 + ntiles - 1) / ntiles));
         if (splits < 1) splits = 1;
         int kchunk = ((g.K + splits - 1) / splits + WG_KT - 1) / WG_KT * WG_KT;
         splits = (g.K + kchunk - 1) / kchunk;
         float *dst = splits > 1 ? splitk : g.Cf;
-        wgrad_kernel<<<dim3(tiles.x, tiles.y, splits), 128, 0, st>>>(g.A, g.a_k, g.B, g.b_k, g.M, g.N, g.K, kchunk, dst);
+        wgrad_kernel<<<dim3(tiles.x, tiles.y, splits), 128, 0, st>>>(g.A, g.a_k, g.B, g.b_k, g.M, g.N, g.K, kchunk, dst,
+                                                                   g.bias_row ? 1 : 0);
         if (splits > 1) {
-            const long long n = (long long)g.M * g.N;
+            const long long n = (long long)(g.M + (g.bias_row ? 1 : 0)) * g.N;
             splitk_sum_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(splitk, splits, n, g.Cf);
         }
         return cudaGetLastError();
@@ -470,7 +498,7 @@ const long long MLP_NPARAM = MLP_OFF_B3 + MLP_OUT;
 cudaError_t mlp_forward(const MlpBuffers &b, const unsigned long long *genomes, long long B, cudaStream_t st,
                         bool logits_only)
 {
-    features_kernel<<<grid_for(B * MLP_PAD), 256, 0, st>>>(genomes, B, b.x);
+    features_kernel<<<grid_for(B), 256, 0, st>>>(genomes, B, b.x);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     const __nv_bfloat16 *Wq = b.wq;
@@ -520,8 +548,10 @@ cudaError_t mlp_backward(const MlpBuffers &b, const uint8_t *labels, long long B
     // dW2 = h1^T dh2  [256 x 256]
     g = GemmArgs{b.h1, 1, MLP_H, b.dh2, MLP_H, 1, MLP_H, MLP_H, (int)B, EPI_F32, nullptr, nullptr, G + MLP_OFF_W2,
                  nullptr};
+    // db2 = column sums of dh2: row 256 of the same product (b2 follows W2 in the parameters)
+    g.bias_row = wgrad_ok(g, b.splitk) ? 1 : 0;
     if ((e = gemm(g, st, b.splitk)) != cudaSuccess) return e;
-    colsum_kernel<__nv_bfloat16><<<MLP_H, 256, 0, st>>>(b.dh2, B, MLP_H, G + MLP_OFF_B2);
+    if (!g.bias_row) colsum_kernel<__nv_bfloat16><<<MLP_H, 256, 0, st>>>(b.dh2, B, MLP_H, G + MLP_OFF_B2);
     // dh1 = (dh2 W2^T) * [h1 > 0]  [B x 256]
     g = GemmArgs{b.dh2, MLP_H, 1, b.wq + MLP_OFF_W2, 1, MLP_H, (int)B, MLP_H, MLP_H, EPI_MASK_BF16, nullptr, b.h1,
                  nullptr, b.dh1};
@@ -529,8 +559,10 @@ cudaError_t mlp_backward(const MlpBuffers &b, const uint8_t *labels, long long B
     // dW1 = x^T dh1  [48 x 256]
     g = GemmArgs{b.x, 1, MLP_PAD, b.dh1, MLP_H, 1, MLP_PAD, MLP_H, (int)B, EPI_F32, nullptr, nullptr, G + MLP_OFF_W1,
                  nullptr};
+    // db1 = column sums of dh1: row 48 of the same product (b1 follows W1 in the parameters)
+    g.bias_row = wgrad_ok(g, b.splitk) ? 1 : 0;
     if ((e = gemm(g, st, b.splitk)) != cudaSuccess) return e;
-    colsum_kernel<__nv_bfloat16><<<MLP_H, 256, 0, st>>>(b.dh1, B, MLP_H, G + MLP_OFF_B1);
+    if (!g.bias_row) colsum_kernel<__nv_bfloat16><<<MLP_H, 256, 0, st>>>(b.dh1, B, MLP_H, G + MLP_OFF_B1);
     return cudaGetLastError();
 }
 
