@@ -319,7 +319,9 @@ int jatam_embed_genomes(const uint64_t *genomes, uint64_t N, int n, int c, uint6
 /* The selection step of the pre-screen below, on its own: idx[0 .. keep) receives,
  * in increasing order, the indices of the keep largest of the n scores (all
  * non-negative float32; ties: lower index first).  scores and idx are device
- * memory; n <= 2^26, keep <= n.  Queued on `stream`; no synchronisation. */
+ * memory; n <= 2^26, keep <= n.  Queued on `stream`; no synchronisation.  Its
+ * 33 KB of scratch is part of the device's workspace, so it is ordered after
+ * the device's previous call that uses the workspace. */
 int jatam_select_top(const float *scores, uint64_t n, uint64_t keep, uint64_t *idx, void *stream);
 
 /*

@@ -171,6 +171,8 @@ struct Workspace {
     size_t lifo_bytes = 0;
     void *ga_buf = nullptr;   // ga_run / ga_breed: fitness, children, cumsum, stats
     size_t ga_bytes = 0;
+    void *topn_buf = nullptr;    // jatam_select_top: the selection's scratch
+    size_t topn_bytes = 0;
     void *screen_buf = nullptr;  // ga_run_screened: candidates, chosen indices, scores
     size_t screen_bytes = 0;
     unsigned long long *screen_cand = nullptr, *screen_idx = nullptr;
@@ -1171,7 +1173,7 @@ int ga_loop(const jatam_ga_config *ga, const jatam_config *cls, int fitness_kind
             unsigned cap = 1;
             while (cap < 2 * M) cap <<= 1;
             const size_t a8 = ((size_t)M * 8 + 255) & ~size_t(255), a4 = ((size_t)M * 4 + 255) & ~size_t(255);
-            const size_t need = 2 * a8 + a4 + (size_t)cap * 12 + a4 + 256 + 1024;
+            const size_t need = 2 * a8 + a4 + (size_t)cap * 12 + a4 + 256 + 1024 + TOPN_SCRATCH_BYTES + 256;
             rc = grow(&w->screen_buf, &w->screen_bytes, need);
             if (rc) return rc;
             char *p = static_cast<char *>(w->screen_buf);
@@ -1183,6 +1185,8 @@ int ga_loop(const jatam_ga_config *ga, const jatam_config *cls, int fitness_kind
             w->screen_table.slot = reinterpret_cast<unsigned *>(p + 2 * a8 + a4 + (size_t)cap * 12);
             w->screen_table.err = reinterpret_cast<unsigned *>(p + 2 * a8 + a4 + (size_t)cap * 12 + a4);
             w->screen_table.cap_mask = cap - 1;
+            w->screen_table.topn = reinterpret_cast<unsigned *>(p + ((2 * a8 + a4 + (size_t)cap * 12 + a4 + 256 + 1024 +
+                                                                      255) & ~size_t(255)));
         }
     }
     cudaStream_t st = static_cast<cudaStream_t>(stream);
@@ -1469,9 +1473,19 @@ int jatam_select_top(const float *scores, uint64_t n, uint64_t keep, uint64_t *i
     CUDA_TRY(cudaGetDevice(&dev));
     if (n && (kind_of(scores, dev) != K_DEVICE || (keep && kind_of(idx, dev) != K_DEVICE)))
         return fail(JATAM_EINVAL, "scores and idx must be device memory");
-    if (keep)
-        CUDA_TRY(launch_topn(scores, (long long)n, (long long)keep, reinterpret_cast<unsigned long long *>(idx),
-                             static_cast<cudaStream_t>(stream)));
+    if (!keep) return JATAM_OK;
+    // the scratch of the selection lives in the device's workspace; like every call that uses the
+    // workspace, this one is ordered after the previous such call on the device
+    Workspace *w = nullptr;
+    int rc = workspace(&w);
+    if (rc) return rc;
+    rc = grow(&w->topn_buf, &w->topn_bytes, TOPN_SCRATCH_BYTES);
+    if (rc) return rc;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    CUDA_TRY(cudaStreamWaitEvent(st, w->last, 0));
+    CUDA_TRY(launch_topn_multi(scores, (long long)n, (long long)keep, reinterpret_cast<unsigned long long *>(idx),
+                               static_cast<unsigned *>(w->topn_buf), st));
+    CUDA_TRY(cudaEventRecord(w->last, st));
     return JATAM_OK;
 }
 
@@ -1864,6 +1878,7 @@ void jatam_shutdown(void)
         if (w->stage_hist) cudaFree(w->stage_hist);
         if (w->ga_buf) cudaFree(w->ga_buf);
         if (w->screen_buf) cudaFree(w->screen_buf);
+        if (w->topn_buf) cudaFree(w->topn_buf);
         if (w->lifo_buf) cudaFree(w->lifo_buf);
         cudaEventDestroy(w->last);
         cudaEventDestroy(w->k_start);
@@ -1959,7 +1974,7 @@ int jatam_workspace_bytes(uint64_t *bytes)
     b += 3 * 8 + (size_t(2) << CROPS_LOG2) * 8 + 4 * 8 + 4 + 4 + 6 * 8;  // counters, crop table
     b += ((size_t(8) + 4 + 128) << SHAPES_LOG2) + 4 * 4;                 // shape side table
     b += w->list_bytes + w->stage_in_bytes + w->stage_out_bytes + w->stage_aux_bytes +
-         w->stage_hist_cap * sizeof(jatam_hist_entry) + w->lifo_bytes + w->ga_bytes + w->screen_bytes +
+         w->stage_hist_cap * sizeof(jatam_hist_entry) + w->lifo_bytes + w->ga_bytes + w->screen_bytes + w->topn_bytes +
          w->alt.list_bytes + w->esc_bytes + w->alt.esc_bytes + ESC_CTL_WORDS * 8 + w->spill_bytes +
          w->alt.spill_bytes;
     if (w->copy) b += 3 * 8 + 6 * 8 + 4 + (size_t(2) << CROPS_LOG2) * 8;

@@ -236,13 +236,18 @@ struct ScreenTable {
     unsigned long long *keys;
     unsigned *first, *slot, *err;
     unsigned cap_mask;
+    unsigned *topn;  // TOPN_SCRATCH_BYTES of scratch for the selection
 };
+// scratch of the many-CTA selection: a 4096-bin histogram, 16 control words, two counts a CTA
+constexpr size_t TOPN_SCRATCH_BYTES = (4096 + 16) * 4 + 2 * 1024 * 8;
+// indices of the `keep` largest non-negative scores (ties: lower index first), in increasing order
+// (scratch: TOPN_SCRATCH_BYTES, 16-byte aligned)
+cudaError_t launch_topn_multi(const float *score, long long n, long long keep, unsigned long long *idx,
+                              unsigned *scratch, cudaStream_t st);
 // scores of n candidates from their logits: the network's probability of a
 // deterministic bounded shape of >= 8 tiles, plus one for the first occurrence
 // of each distinct genome (repeats rank below every distinct genome); idx = the
 // `keep` best (ties: lower index), chosen = cand[idx]
-// indices of the `keep` largest non-negative scores (ties: lower index first), in increasing order
-cudaError_t launch_topn(const float *score, long long n, long long keep, unsigned long long *idx, cudaStream_t st);
 cudaError_t launch_screen(const float *logits, long long n, long long keep, float *score, unsigned long long *idx,
                           const unsigned long long *cand, unsigned long long *chosen, const ScreenTable &t,
                           cudaStream_t st);

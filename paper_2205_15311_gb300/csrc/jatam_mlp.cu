@@ -634,131 +634,231 @@ __global__ void score_kernel(const float *logits, long long n, float *score)
     }
 }
 
-// Indices of the `keep` largest non-negative scores among n (ties: lower index
-// first), in increasing index order; one CTA.  A radix select on the float
-// bits (monotone for non-negative floats) finds the key of the keep-th largest
-// score four bits at a time: every thread counts the digits of the keys that
-// match the prefix so far in its own column of a shared table (no atomics), and
-// one warp per digit sums the columns.  Then every warp owns a contiguous
-// segment of the scores and reads it twice, coalesced: first to count the keys
-// above the threshold key and equal to it, then -- after a scan over the warps
-// of those counts, which ranks the equal keys in index order -- to write the
-// chosen indices, each lane at its rank within the warp's ballot.
-constexpr int TOPN_THREADS = 512;
-constexpr int TOPN_BINS = 16;
+// ---------------------------------------------------------------------------
+// Indices of the `keep` largest non-negative scores among n (ties: lower index first), in
+// increasing index order, by a radix select on the float bits (monotone for non-negative
+// floats), over many CTAs with a scratch area (TOPN_SCRATCH_BYTES): three
+// histogram launches find the threshold key 12, 12 and 8 bits at a time (the last CTA of each
+// launch to finish -- a fence and an atomic ticket, no waiting -- picks the digit from the summed
+// histogram and clears it for the next); a counting launch gives every CTA its keys above and
+// equal to the threshold (its last CTA turns them into output positions and tie ranks), and a
+// writing launch emits each CTA's chosen indices in order.  A warp whose keys share one digit
+// adds them with one atomic.  Scratch: hist[4096] | ctrl[16] | counts[2][TOPN_MAX_CTAS] (u64).
+// ---------------------------------------------------------------------------
+constexpr int TN_THREADS = 256;
+constexpr int TN_HIST = 4096;
+constexpr int TOPN_MAX_CTAS = 1024;
 
-__global__ void __launch_bounds__(TOPN_THREADS) topn_kernel(const float *score, long long n, long long keep,
-                                                            unsigned long long *idx_out)
+__device__ __forceinline__ void tn_level(int lvl, int &shift, unsigned &dmask, unsigned &pmask)
 {
-    __shared__ unsigned cnt[TOPN_BINS][TOPN_THREADS];
-    __shared__ unsigned tot[TOPN_BINS];
-    __shared__ unsigned prefix_s, want_s;
-    __shared__ unsigned long long w_above[32], w_equal[32], w_eq_before[32], w_pos[32];
-    const uint32_t *key = reinterpret_cast<const uint32_t *>(score);
+    shift = lvl == 0 ? 20 : lvl == 1 ? 8 : 0;
+    dmask = lvl < 2 ? 4095u : 255u;
+    pmask = lvl == 0 ? 0u : lvl == 1 ? 0xFFF00000u : 0xFFFFFF00u;
+}
+
+__global__ void __launch_bounds__(TN_THREADS) topn_hist_kernel(const uint32_t *key, long long n, long long keep,
+                                                               int lvl, unsigned *scratch)
+{
+    __shared__ unsigned local[TN_HIST];
+    __shared__ int last_s;
+    unsigned *hist = scratch, *ctrl = scratch + TN_HIST;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const unsigned lt = (1u << lane) - 1u;
-    unsigned prefix = 0, mask = 0;
-    unsigned long long want = (unsigned long long)keep;  // rank (from the top) still to place inside the prefix
-    const bool vec = (reinterpret_cast<uintptr_t>(score) & 15) == 0;
-    const long long n4 = vec ? n / 4 : 0;  // keys read four at a time; the rest one by one
-    for (int shift = 28; shift >= 0; shift -= 4) {
-#pragma unroll
-        for (int b = 0; b < TOPN_BINS; ++b) cnt[b][tid] = 0u;
-        auto count = [&](uint32_t k) {
-            if ((k & mask) == prefix) cnt[(k >> shift) & 15u][tid] += 1u;
-        };
-        // eight independent 16-byte loads in flight per thread, then their 32 keys counted
-        constexpr int U = 8;
-        for (long long i0 = tid; i0 < n4; i0 += (long long)TOPN_THREADS * U) {
-            uint4 v[U];
-#pragma unroll
-            for (int u = 0; u < U; ++u) {
-                const long long i = i0 + (long long)u * TOPN_THREADS;
-                v[u] = i < n4 ? reinterpret_cast<const uint4 *>(key)[i] : make_uint4(0u, 0u, 0u, 0u);
-            }
-#pragma unroll
-            for (int u = 0; u < U; ++u) {
-                if (i0 + (long long)u * TOPN_THREADS < n4) {
-                    count(v[u].x);
-                    count(v[u].y);
-                    count(v[u].z);
-                    count(v[u].w);
-                }
+    int shift;
+    unsigned dmask, pmask;
+    tn_level(lvl, shift, dmask, pmask);
+    const unsigned prefix = lvl == 0 ? 0u : __ldcg(&ctrl[0]);
+    const unsigned long long want = lvl == 0 ? (unsigned long long)keep : __ldcg(&ctrl[1]);
+    for (int i = tid; i <= (int)dmask; i += TN_THREADS) local[i] = 0u;
+    __syncthreads();
+    for (long long base = (long long)blockIdx.x * TN_THREADS; base < n; base += (long long)gridDim.x * TN_THREADS) {
+        const long long i = base + tid;
+        const uint32_t k = i < n ? key[i] : 0u;
+        const bool in = i < n && (k & pmask) == prefix;
+        const unsigned d = (k >> shift) & dmask;
+        const unsigned act = __ballot_sync(0xffffffffu, in);
+        if (act) {
+            const int f = __ffs(act) - 1;
+            const unsigned d0 = __shfl_sync(0xffffffffu, d, f);
+            if (__all_sync(0xffffffffu, !in || d == d0)) {
+                if (lane == f) atomicAdd(&local[d0], (unsigned)__popc(act));
+            } else if (in) {
+                atomicAdd(&local[d], 1u);
             }
         }
-        for (long long i = 4 * n4 + tid; i < n; i += TOPN_THREADS) count(key[i]);
-        __syncthreads();
-        if (warp < TOPN_BINS) {
-            unsigned v = 0;
-            for (int t = lane; t < TOPN_THREADS; t += 32) v += cnt[warp][t];
-#pragma unroll
-            for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
-            if (lane == 0) tot[warp] = v;
-        }
-        __syncthreads();
-        if (tid == 0) {
-            // the highest digit d > 0 at which the count from the top reaches `want`, else digit 0
-            unsigned long long acc = 0;
-            int d = TOPN_BINS - 1;
-            for (; d > 0; --d) {
-                if (acc + tot[d] >= want) break;
-                acc += tot[d];
-            }
-            prefix_s = prefix | ((unsigned)d << shift);
-            want_s = (unsigned)(want - acc);
-        }
-        __syncthreads();
-        prefix = prefix_s;
-        want = want_s;
-        mask |= 15u << shift;
     }
-    // prefix is now the key of the keep-th largest; `want` of its copies are taken, lowest indices first
-    const uint32_t thr = prefix;
-    const long long seg = ((n + TOPN_THREADS - 1) / TOPN_THREADS) * 32;  // a warp's segment, whole chunks of 32
-    const long long lo = (long long)warp * seg, hi = min(n, lo + seg);
-    // both passes read a warp's chunks eight at a time, all eight loads in flight together
-    constexpr int CB = 8;
-    unsigned long long above = 0, equal = 0;
-    for (long long c0 = lo; c0 < hi; c0 += 32 * CB) {
-        uint32_t kk[CB];
+    __syncthreads();
+    for (int i = tid; i <= (int)dmask; i += TN_THREADS)
+        if (local[i]) atomicAdd(&hist[i], local[i]);
+    __threadfence();
+    __syncthreads();
+    if (tid == 0) last_s = atomicAdd(&ctrl[2], 1u) == gridDim.x - 1;
+    __syncthreads();
+    if (!last_s) return;
+    __threadfence();
+    // the last CTA: the summed histogram into shared memory (the global one starts at zero again for
+    // the next launch)
+    for (int i = tid; i <= (int)dmask; i += TN_THREADS) {
+        local[i] = __ldcg(&hist[i]);
+        hist[i] = 0u;
+    }
+    __syncthreads();
+    if (warp == 0) {
+        // lane l holds bins per l .. per l + per - 1; the crossing -- the highest digit d > 0 at which
+        // the count from the top reaches `want`, else digit 0 -- lies in the lane whose bins take the
+        // count from the top across `want`
+        const int per = (int)(dmask + 1) / 32;
+        unsigned sum = 0;
+        for (int j = 0; j < per; ++j) sum += local[per * lane + j];
+        unsigned incl = sum;  // keys in this lane's bins and above
 #pragma unroll
-        for (int u = 0; u < CB; ++u) {
+        for (int off = 1; off < 32; off <<= 1) {
+            const unsigned v = __shfl_down_sync(0xffffffffu, incl, off);
+            if (lane + off < 32) incl += v;
+        }
+        const unsigned above = incl - sum;
+        const bool mine = (unsigned long long)above < want && (unsigned long long)incl >= want;
+        if (mine) {
+            unsigned long long acc = above;
+            int dsel = 0;
+            for (int j = per - 1; j >= 0; --j) {
+                const int d = per * lane + j;
+                if (d == 0) break;
+                const unsigned h = local[d];
+                if (acc + h >= want) {
+                    dsel = d;
+                    break;
+                }
+                acc += h;
+            }
+            ctrl[0] = prefix | ((unsigned)dsel << shift);
+            ctrl[1] = (unsigned)(want - acc);
+        }
+    }
+    if (tid == 0) ctrl[2] = 0u;  // the ticket, for the next launch
+}
+
+// a warp's keys in [lo, hi): counts above and equal to thr, eight chunks of 32 at a time
+__device__ __forceinline__ void tn_warp_count(const uint32_t *key, long long lo, long long hi, uint32_t thr, int lane,
+                                              unsigned long long &above, unsigned long long &equal)
+{
+    above = 0;
+    equal = 0;
+    for (long long c0 = lo; c0 < hi; c0 += 32 * 8) {
+        uint32_t kk[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
             const long long i = c0 + 32 * u + lane;
             kk[u] = i < hi ? key[i] : 0u;
         }
 #pragma unroll
-        for (int u = 0; u < CB; ++u) {
+        for (int u = 0; u < 8; ++u) {
             const long long i = c0 + 32 * u + lane;
             above += __popc(__ballot_sync(0xffffffffu, i < hi && kk[u] > thr));
             equal += __popc(__ballot_sync(0xffffffffu, i < hi && kk[u] == thr));
         }
     }
+}
+
+__global__ void __launch_bounds__(TN_THREADS) topn_count_kernel(const uint32_t *key, long long n, long long seg,
+                                                                unsigned *scratch)
+{
+    __shared__ unsigned long long wa[TN_THREADS / 32], we[TN_THREADS / 32];
+    __shared__ int last_s;
+    unsigned *ctrl = scratch + TN_HIST;
+    unsigned long long *counts = reinterpret_cast<unsigned long long *>(scratch + TN_HIST + 16);
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const uint32_t thr = __ldcg(&ctrl[0]);
+    const unsigned long long want = __ldcg(&ctrl[1]);
+    const long long wseg = seg / (TN_THREADS / 32);
+    const long long lo = (long long)blockIdx.x * seg + warp * wseg, hi = min(n, lo + wseg);
+    unsigned long long above, equal;
+    tn_warp_count(key, lo, hi, thr, lane, above, equal);
     if (lane == 0) {
-        w_above[warp] = above;
-        w_equal[warp] = equal;
+        wa[warp] = above;
+        we[warp] = equal;
     }
     __syncthreads();
     if (tid == 0) {
-        unsigned long long eq = 0, pos = 0;
-        for (int w = 0; w < TOPN_THREADS / 32; ++w) {
-            w_eq_before[w] = eq;
-            w_pos[w] = pos;
-            const unsigned long long take = eq >= want ? 0ull : min(w_equal[w], want - eq);
-            eq += w_equal[w];
-            pos += w_above[w] + take;
+        unsigned long long a = 0, e = 0;
+        for (int w = 0; w < TN_THREADS / 32; ++w) {
+            a += wa[w];
+            e += we[w];
         }
+        counts[blockIdx.x] = a;
+        counts[TOPN_MAX_CTAS + blockIdx.x] = e;
+        __threadfence();
+        last_s = atomicAdd(&ctrl[3], 1u) == gridDim.x - 1;
     }
     __syncthreads();
-    unsigned long long r = w_eq_before[warp], pos = w_pos[warp];
-    for (long long c0 = lo; c0 < hi; c0 += 32 * CB) {
-        uint32_t kk[CB];
+    if (!last_s || warp != 0) return;
+    __threadfence();
+    // the last CTA: output position and equal keys before, per CTA, in CTA order -- exclusive scans
+    // over 32 CTAs at a time (equal keys before, then above + the equal keys taken)
+    unsigned long long eq = 0, pos = 0;
+    for (unsigned b0 = 0; b0 < gridDim.x; b0 += 32) {
+        const unsigned b = b0 + lane;
+        const bool in = b < gridDim.x;
+        const unsigned long long a = in ? __ldcg(&counts[b]) : 0ull, e = in ? __ldcg(&counts[TOPN_MAX_CTAS + b]) : 0ull;
+        unsigned long long se = e;  // inclusive scan of e
 #pragma unroll
-        for (int u = 0; u < CB; ++u) {
+        for (int off = 1; off < 32; off <<= 1) {
+            const unsigned long long v = __shfl_up_sync(0xffffffffu, se, off);
+            if (lane >= off) se += v;
+        }
+        const unsigned long long eb = eq + se - e;  // equal keys before this CTA
+        const unsigned long long take = eb >= want ? 0ull : min(e, want - eb);
+        unsigned long long sp = a + take;  // inclusive scan of above + taken
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            const unsigned long long v = __shfl_up_sync(0xffffffffu, sp, off);
+            if (lane >= off) sp += v;
+        }
+        if (in) {
+            counts[b] = pos + sp - (a + take);
+            counts[TOPN_MAX_CTAS + b] = eb;
+        }
+        eq += __shfl_sync(0xffffffffu, se, 31);
+        pos += __shfl_sync(0xffffffffu, sp, 31);
+    }
+    if (lane == 0) ctrl[3] = 0u;
+}
+
+__global__ void __launch_bounds__(TN_THREADS) topn_write_kernel(const uint32_t *key, long long n, long long seg,
+                                                                const unsigned *scratch,
+                                                                unsigned long long *idx_out)
+{
+    __shared__ unsigned long long wa[TN_THREADS / 32], we[TN_THREADS / 32];
+    const unsigned *ctrl = scratch + TN_HIST;
+    const unsigned long long *counts = reinterpret_cast<const unsigned long long *>(scratch + TN_HIST + 16);
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const unsigned lt = (1u << lane) - 1u;
+    const uint32_t thr = ctrl[0];
+    const unsigned long long want = ctrl[1];
+    const long long wseg = seg / (TN_THREADS / 32);
+    const long long lo = (long long)blockIdx.x * seg + warp * wseg, hi = min(n, lo + wseg);
+    unsigned long long above, equal;
+    tn_warp_count(key, lo, hi, thr, lane, above, equal);
+    if (lane == 0) {
+        wa[warp] = above;
+        we[warp] = equal;
+    }
+    __syncthreads();
+    // this warp's output position and equal keys before it: the CTA's, then the warps before it
+    unsigned long long pos = counts[blockIdx.x], r = counts[TOPN_MAX_CTAS + blockIdx.x];
+    for (int w = 0; w < warp; ++w) {
+        const unsigned long long take = r >= want ? 0ull : min(we[w], want - r);
+        pos += wa[w] + take;
+        r += we[w];
+    }
+    for (long long c0 = lo; c0 < hi; c0 += 32 * 8) {
+        uint32_t kk[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
             const long long i = c0 + 32 * u + lane;
             kk[u] = i < hi ? key[i] : 0u;
         }
 #pragma unroll
-        for (int u = 0; u < CB; ++u) {
+        for (int u = 0; u < 8; ++u) {
             const long long i = c0 + 32 * u + lane;
             const unsigned eqm = __ballot_sync(0xffffffffu, i < hi && kk[u] == thr);
             const bool take = (i < hi && kk[u] > thr) || ((eqm >> lane) & 1u && r + __popc(eqm & lt) < want);
@@ -825,11 +925,28 @@ __global__ void dedup_mark_kernel(float *score, long long n, const unsigned *fir
         if (first[slot[i]] == (unsigned)i) score[i] += 1.f;
 }
 
-cudaError_t launch_topn(const float *score, long long n, long long keep, unsigned long long *idx, cudaStream_t st)
+cudaError_t launch_topn_multi(const float *score, long long n, long long keep, unsigned long long *idx,
+                              unsigned *scratch, cudaStream_t st)
 {
-    if (n > 0) topn_kernel<<<1, TOPN_THREADS, 0, st>>>(score, n, keep, idx);
+    if (n <= 0 || keep <= 0) return cudaSuccess;
+    const uint32_t *key = reinterpret_cast<const uint32_t *>(score);
+    cudaError_t e = cudaMemsetAsync(scratch, 0, (TN_HIST + 16) * 4, st);
+    if (e != cudaSuccess) return e;
+    long long hb = (n + TN_THREADS * 2 - 1) / (TN_THREADS * 2);  // about 2 keys a thread
+    if (hb > TOPN_MAX_CTAS) hb = TOPN_MAX_CTAS;
+    for (int lvl = 0; lvl < 3; ++lvl)
+        topn_hist_kernel<<<(unsigned)hb, TN_THREADS, 0, st>>>(key, n, keep, lvl, scratch);
+    // segments of whole warp chunks: at least 512 keys a CTA, at most TOPN_MAX_CTAS CTAs
+    long long cb = (n + 511) / 512;
+    if (cb > TOPN_MAX_CTAS) cb = TOPN_MAX_CTAS;
+    const long long unit = 32LL * (TN_THREADS / 32);
+    const long long seg = ((n + cb - 1) / cb + unit - 1) / unit * unit;
+    cb = (n + seg - 1) / seg;
+    topn_count_kernel<<<(unsigned)cb, TN_THREADS, 0, st>>>(key, n, seg, scratch);
+    topn_write_kernel<<<(unsigned)cb, TN_THREADS, 0, st>>>(key, n, seg, scratch, idx);
     return cudaGetLastError();
 }
+
 
 cudaError_t launch_screen(const float *logits, long long n, long long keep, float *score, unsigned long long *idx,
                           const unsigned long long *cand, unsigned long long *chosen, const ScreenTable &t,
@@ -841,7 +958,7 @@ cudaError_t launch_screen(const float *logits, long long n, long long keep, floa
     if ((e = cudaMemsetAsync(t.first, 0xFF, (size_t)(t.cap_mask + 1) * 4, st)) != cudaSuccess) return e;
     dedup_insert_kernel<<<grid_of(n), 256, 0, st>>>(cand, n, t.keys, t.first, t.cap_mask, t.slot, t.err);
     dedup_mark_kernel<<<grid_of(n), 256, 0, st>>>(score, n, t.first, t.slot);
-    topn_kernel<<<1, TOPN_THREADS, 0, st>>>(score, n, keep, idx);
+    if ((e = launch_topn_multi(score, n, keep, idx, t.topn, st)) != cudaSuccess) return e;
     gather_kernel<<<grid_of(keep), 256, 0, st>>>(cand, idx, keep, chosen);
     return cudaGetLastError();
 }
