@@ -1317,7 +1317,7 @@ int jatam_mlp_create(uint64_t max_batch, jatam_mlp **net)
     rc |= alloc((void **)&b.h2, Bc * MLP_H * 2); rc |= alloc((void **)&b.dq, Bc * MLP_OUT * 2);
     rc |= alloc((void **)&b.dh1, Bc * MLP_H * 2); rc |= alloc((void **)&b.dh2, Bc * MLP_H * 2);
     rc |= alloc((void **)&b.logits, Bc * MLP_OUT * 4); rc |= alloc((void **)&b.d, Bc * MLP_OUT * 4);
-    rc |= alloc((void **)&b.lrow, Bc * 4);
+    rc |= alloc((void **)&b.lrow, (Bc + 64) * 4);  // 9 partial sums a block of 256 rows
     rc |= alloc((void **)&b.splitk, (size_t)MLP_SPLITK_MAX * MLP_H * MLP_H * 4);
     rc |= alloc((void **)&b.tc_err, 4);
     rc |= alloc((void **)&b.wqt, (size_t)(MLP_PAD * MLP_H + MLP_H * MLP_H) * 2);

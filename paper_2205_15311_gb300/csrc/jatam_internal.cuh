@@ -207,13 +207,14 @@ struct MlpBuffers {
     __nv_bfloat16 *wqt;          // W1 and W2 transposed (K contiguous) for the tcgen05 products: [256 x 48 + 256 x 256]
     long long cap;               // batch capacity of the activation buffers
     __nv_bfloat16 *x, *h1, *h2, *dq, *dh1, *dh2;
-    float *logits, *d, *lrow, *loss;
+    float *logits, *d, *lrow, *loss;  // lrow: the softmax blocks' partial sums (loss, output bias gradient)
     float *splitk;               // [MLP_SPLITK_MAX][256 x 256] partial weight gradients (split-K)
     unsigned *tc_err;            // error bits of the tcgen05 products (a bounded wait that ran out)
     int tc;                      // 1: products with 256 columns on tcgen05; 0: all on mma.sync
 };
 // D[M x 256] = A[M x K] B[K x 256] on tcgen05 (jatam_tc.cu); epi 0: bias + ReLU,
-// 1: ReLU mask; 2: bias + ReLU, then logits[M x 8] = bf16(D) W3 + b3 instead of D;
+// 1: ReLU mask; 2: bias + ReLU, then logits[M x 8] = bf16(D) W3 + b3 instead of D; 3: both D (as 0)
+// and the logits (as 2);
 // K a multiple of 16, at most 256, both operands K-contiguous
 cudaError_t tc_gemm_n256(const __nv_bfloat16 *A, long long a_m, long long a_k, const __nv_bfloat16 *B, long long b_k,
                          long long b_n, int M, int K, int epi, const float *bias, const __nv_bfloat16 *mask,

@@ -262,49 +262,18 @@ __global__ void features_kernel(const unsigned long long *genomes, long long n, 
     }
 }
 
-// logits = h2 W3 + b3 for the 8-column output layer on the CUDA cores: one
-// thread per row reads the row's 256 bfloat16 activations in 16-byte pieces
-// and accumulates its 8 dot products in float32, k in increasing order (the
-// products of two bfloat16 values are exact in float32); W3 sits in shared
-// memory as float32.  An 8-column tile would leave 7/8 of an mma tile empty.
-__global__ void __launch_bounds__(256) logits_kernel(const __nv_bfloat16 *h2, long long M, const __nv_bfloat16 *w3,
-                                                     const float *b3, float *logits)
-{
-    __shared__ float w[MLP_H][MLP_OUT];
-    for (int i = threadIdx.x; i < MLP_H * MLP_OUT; i += blockDim.x) w[i / MLP_OUT][i % MLP_OUT] = __bfloat162float(w3[i]);
-    __syncthreads();
-    for (long long row = blockIdx.x * (long long)blockDim.x + threadIdx.x; row < M;
-         row += (long long)gridDim.x * blockDim.x) {
-        float acc[MLP_OUT];
-#pragma unroll
-        for (int c = 0; c < MLP_OUT; ++c) acc[c] = 0.f;
-        const uint4 *src = reinterpret_cast<const uint4 *>(h2 + row * MLP_H);
-#pragma unroll 4
-        for (int q = 0; q < MLP_H / 8; ++q) {
-            const uint4 v = src[q];
-            const uint32_t part[4] = {v.x, v.y, v.z, v.w};
-#pragma unroll
-            for (int e = 0; e < 8; ++e) {
-                const uint32_t bits = (part[e >> 1] >> (16 * (e & 1))) & 0xFFFFu;
-                const float a = __uint_as_float(bits << 16);
-#pragma unroll
-                for (int c = 0; c < MLP_OUT; ++c) acc[c] = fmaf(a, w[8 * q + e][c], acc[c]);
-            }
-        }
-        float4 *dst = reinterpret_cast<float4 *>(logits + row * MLP_OUT);
-        dst[0] = make_float4(acc[0] + b3[0], acc[1] + b3[1], acc[2] + b3[2], acc[3] + b3[3]);
-        dst[1] = make_float4(acc[4] + b3[4], acc[5] + b3[5], acc[6] + b3[6], acc[7] + b3[7]);
-    }
-}
-
 // softmax cross-entropy on float32 logits: d = (softmax - onehot) / B, as
-// float32 (for the bias gradient) and bfloat16 (for the products); the loss
-// summed into *loss (divided by B)
-__global__ void softmax_ce_kernel(const float *logits, const uint8_t *labels, long long B, float *d,
-                                  __nv_bfloat16 *dq, float *lrow)
+// float32 and bfloat16 (for the products); per block of 256 rows, in a fixed
+// order, the sum of the rows' losses (each divided by B) and of d's 8 columns
+// (the output bias gradient) into part[9 block ..]
+__global__ void __launch_bounds__(256) softmax_ce_kernel(const float *logits, const uint8_t *labels, long long B,
+                                                         float *d, __nv_bfloat16 *dq, float *part)
 {
+    __shared__ float red[9][256];
     const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    float l = 0.f;
+    float l = 0.f, dv[MLP_OUT];
+#pragma unroll
+    for (int c = 0; c < MLP_OUT; ++c) dv[c] = 0.f;
     if (i < B) {
         const float *z = logits + i * MLP_OUT;
         float mx = z[0];
@@ -315,30 +284,90 @@ __global__ void softmax_ce_kernel(const float *logits, const uint8_t *labels, lo
             s += e[c];
         }
         const int y = labels[i];
+#pragma unroll
         for (int c = 0; c < MLP_OUT; ++c) {
             const float v = (e[c] / s - (c == y ? 1.f : 0.f)) / (float)B;
             d[i * MLP_OUT + c] = v;
             dq[i * MLP_OUT + c] = __float2bfloat16_rn(v);
+            dv[c] = v;
         }
         l = (logf(s) + mx - z[y]) / (float)B;
-        lrow[i] = l;
     }
-}
-
-// the loss: the per-row losses summed in a fixed order (one CTA), so repeated
-// runs give the same bits
-__global__ void __launch_bounds__(256) loss_sum_kernel(const float *lrow, long long B, float *loss)
-{
-    __shared__ float red[256];
-    float s = 0.f;
-    for (long long r = threadIdx.x; r < B; r += blockDim.x) s += lrow[r];
-    red[threadIdx.x] = s;
+    red[0][threadIdx.x] = l;
+#pragma unroll
+    for (int c = 0; c < MLP_OUT; ++c) red[1 + c][threadIdx.x] = dv[c];
     __syncthreads();
     for (int off = blockDim.x / 2; off > 0; off >>= 1) {
-        if ((int)threadIdx.x < off) red[threadIdx.x] += red[threadIdx.x + off];
+        if ((int)threadIdx.x < off) {
+#pragma unroll
+            for (int v = 0; v < 9; ++v) red[v][threadIdx.x] += red[v][threadIdx.x + off];
+        }
         __syncthreads();
     }
-    if (threadIdx.x == 0) *loss = red[0];
+    if (threadIdx.x < 9) part[9 * (long long)blockIdx.x + threadIdx.x] = red[threadIdx.x][0];
+}
+
+// the loss and the output bias gradient: the blocks' partial sums added in a fixed order
+__global__ void __launch_bounds__(256) ce_sum_kernel(const float *part, long long blocks, float *loss, float *db3)
+{
+    __shared__ float red[9][256];
+    float acc[9];
+#pragma unroll
+    for (int v = 0; v < 9; ++v) acc[v] = 0.f;
+    for (long long b = threadIdx.x; b < blocks; b += blockDim.x) {
+#pragma unroll
+        for (int v = 0; v < 9; ++v) acc[v] += part[9 * b + v];
+    }
+#pragma unroll
+    for (int v = 0; v < 9; ++v) red[v][threadIdx.x] = acc[v];
+    __syncthreads();
+    for (int off = blockDim.x / 2; off > 0; off >>= 1) {
+        if ((int)threadIdx.x < off) {
+#pragma unroll
+            for (int v = 0; v < 9; ++v) red[v][threadIdx.x] += red[v][threadIdx.x + off];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *loss = red[0][0];
+    if (threadIdx.x >= 1 && threadIdx.x < 9) db3[threadIdx.x - 1] = red[threadIdx.x][0];
+}
+
+// dh2 = (dq W3^T) * [h2 > 0]: a warp per row, 8 columns a lane; each output the float32 sum of its
+// 8 products in k order (products of two bfloat16 values are exact), then rounded to bfloat16
+__global__ void __launch_bounds__(256) dh2_kernel(const __nv_bfloat16 *dq, const __nv_bfloat16 *w3,
+                                                  const __nv_bfloat16 *h2, long long B, __nv_bfloat16 *dh2)
+{
+    __shared__ float w[MLP_H][MLP_OUT];  // W3[n][k]
+    for (int i = threadIdx.x; i < MLP_H * MLP_OUT; i += blockDim.x) w[i / MLP_OUT][i % MLP_OUT] = __bfloat162float(w3[i]);
+    __syncthreads();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (long long row = (long long)blockIdx.x * 8 + warp; row < B; row += (long long)gridDim.x * 8) {
+        const uint4 qv = *reinterpret_cast<const uint4 *>(dq + row * MLP_OUT);
+        const uint32_t qw[4] = {qv.x, qv.y, qv.z, qv.w};
+        float q[MLP_OUT];
+#pragma unroll
+        for (int k = 0; k < MLP_OUT; ++k)
+            q[k] = __uint_as_float(k & 1 ? (qw[k >> 1] & 0xFFFF0000u) : (qw[k >> 1] << 16));
+        const uint4 mv = *reinterpret_cast<const uint4 *>(h2 + row * MLP_H + 8 * lane);
+        const uint32_t mw[4] = {mv.x, mv.y, mv.z, mv.w};
+        uint32_t ow[4];
+#pragma unroll
+        for (int h = 0; h < 4; ++h) {
+            float v[2];
+#pragma unroll
+            for (int e = 0; e < 2; ++e) {
+                const int n = 8 * lane + 2 * h + e;
+                float acc = 0.f;
+#pragma unroll
+                for (int k = 0; k < MLP_OUT; ++k) acc = fmaf(q[k], w[n][k], acc);
+                const float m = __uint_as_float(e ? (mw[h] & 0xFFFF0000u) : (mw[h] << 16));
+                v[e] = m > 0.f ? acc : 0.f;
+            }
+            const __nv_bfloat162 hv = __floats2bfloat162_rn(v[0], v[1]);
+            ow[h] = *reinterpret_cast<const uint32_t *>(&hv);
+        }
+        *reinterpret_cast<uint4 *>(dh2 + row * MLP_H + 8 * lane) = make_uint4(ow[0], ow[1], ow[2], ow[3]);
+    }
 }
 
 // column sums of a [B x N] matrix (float32 or bfloat16) into out[N]
@@ -512,17 +541,16 @@ cudaError_t mlp_forward(const MlpBuffers &b, const unsigned long long *genomes, 
         return tc_gemm_n256(b.h1, MLP_H, 1, b.wqt + MLP_PAD * MLP_H, 1, MLP_H, (int)B, MLP_H, 2, b.p + MLP_OFF_B2,
                             nullptr, nullptr, b.tc_err, st, Wq + MLP_OFF_W3, b.p + MLP_OFF_B3, b.logits);
     }
+    if (b.tc) {
+        // h2 = relu(h1 W2 + b2), stored, and logits = h2 W3 + b3 in the same epilogue
+        return tc_gemm_n256(b.h1, MLP_H, 1, b.wqt + MLP_PAD * MLP_H, 1, MLP_H, (int)B, MLP_H, 3, b.p + MLP_OFF_B2,
+                            nullptr, b.h2, b.tc_err, st, Wq + MLP_OFF_W3, b.p + MLP_OFF_B3, b.logits);
+    }
     // h2 = relu(h1 W2 + b2)
     g = GemmArgs{b.h1, MLP_H, 1, Wq + MLP_OFF_W2, MLP_H, 1, (int)B, MLP_H, MLP_H, EPI_BIAS_RELU_BF16,
                  b.p + MLP_OFF_B2, nullptr, nullptr, b.h2, 0, b.wqt + MLP_PAD * MLP_H};
     if ((e = gemm(g, st, nullptr, &b)) != cudaSuccess) return e;
-    // logits = h2 W3 + b3 (on mma.sync too when every product is kept there)
-    if (b.tc) {
-        const long long blocks = (B + 255) / 256;
-        logits_kernel<<<(unsigned)(blocks < 4096 ? blocks : 4096), 256, 0, st>>>(b.h2, B, Wq + MLP_OFF_W3,
-                                                                                b.p + MLP_OFF_B3, b.logits);
-        return cudaGetLastError();
-    }
+    // logits = h2 W3 + b3 (every product on mma.sync)
     g = GemmArgs{b.h2, MLP_H, 1, Wq + MLP_OFF_W3, MLP_OUT, 1, (int)B, MLP_OUT, MLP_H, EPI_BIAS_F32,
                  b.p + MLP_OFF_B3, nullptr, b.logits, nullptr};
     return gemm(g, st);
@@ -531,20 +559,27 @@ cudaError_t mlp_forward(const MlpBuffers &b, const unsigned long long *genomes, 
 cudaError_t mlp_backward(const MlpBuffers &b, const uint8_t *labels, long long B, cudaStream_t st)
 {
     cudaError_t e;
-    softmax_ce_kernel<<<(unsigned)((B + 255) / 256), 256, 0, st>>>(b.logits, labels, B, b.d, b.dq, b.lrow);
-    loss_sum_kernel<<<1, 256, 0, st>>>(b.lrow, B, b.loss);
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
     float *G = b.grad;
+    // the loss and db3 from per-block partial sums (in lrow: 9 values a block of 256 rows)
+    const long long ceb = (B + 255) / 256;
+    softmax_ce_kernel<<<(unsigned)ceb, 256, 0, st>>>(b.logits, labels, B, b.d, b.dq, b.lrow);
+    ce_sum_kernel<<<1, 256, 0, st>>>(b.lrow, ceb, b.loss, G + MLP_OFF_B3);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
     GemmArgs g{};
     // dW3 = h2^T dq  [256 x 8], K = B
     g = GemmArgs{b.h2, 1, MLP_H, b.dq, MLP_OUT, 1, MLP_H, MLP_OUT, (int)B, EPI_F32, nullptr, nullptr,
                  G + MLP_OFF_W3, nullptr};
     if ((e = gemm(g, st, b.splitk)) != cudaSuccess) return e;
-    colsum_kernel<float><<<MLP_OUT, 256, 0, st>>>(b.d, B, MLP_OUT, G + MLP_OFF_B3);
-    // dh2 = (dq W3^T) * [h2 > 0]  [B x 256], K = 8
-    g = GemmArgs{b.dq, MLP_OUT, 1, b.wq + MLP_OFF_W3, 1, MLP_OUT, (int)B, MLP_H, MLP_OUT, EPI_MASK_BF16, nullptr,
-                 b.h2, nullptr, b.dh2};
-    if ((e = gemm(g, st)) != cudaSuccess) return e;
+    // dh2 = (dq W3^T) * [h2 > 0]  [B x 256], K = 8 (on mma.sync when every product is kept there)
+    if (b.tc) {
+        const long long rb = (B + 7) / 8;
+        dh2_kernel<<<(unsigned)(rb < 4096 ? rb : 4096), 256, 0, st>>>(b.dq, b.wq + MLP_OFF_W3, b.h2, B, b.dh2);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    } else {
+        g = GemmArgs{b.dq, MLP_OUT, 1, b.wq + MLP_OFF_W3, 1, MLP_OUT, (int)B, MLP_H, MLP_OUT, EPI_MASK_BF16, nullptr,
+                     b.h2, nullptr, b.dh2};
+        if ((e = gemm(g, st)) != cudaSuccess) return e;
+    }
     // dW2 = h1^T dh2  [256 x 256]
     g = GemmArgs{b.h1, 1, MLP_H, b.dh2, MLP_H, 1, MLP_H, MLP_H, (int)B, EPI_F32, nullptr, nullptr, G + MLP_OFF_W2,
                  nullptr};

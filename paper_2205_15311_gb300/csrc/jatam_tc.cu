@@ -36,6 +36,7 @@ constexpr int TC_MAX_KCH = 4;                      // K <= 256
 constexpr int TC_MAX_RING = 8;
 constexpr int TC_STAGE_WORDS = 32 * 20;            // a warp's epilogue staging: 32 rows of 16 words, 16-byte padded
 constexpr int TC_CTRL_BYTES = 2048;                // mbarriers (64 B), the TMEM address, the bias (1 KB)
+constexpr int TC_OUT_BYTES = (TC_N * 8 + TC_M * 8) * 4;  // epi 2, 3: W3 as float32, the halves' partial logits
 constexpr int TC_SMEM_BUDGET = 226 * 1024;
 constexpr unsigned TC_WAIT_LIMIT = 1u << 20;       // mbarrier polls before giving up (about a second)
 constexpr unsigned TC_ERR_TIMEOUT = 1u;
@@ -93,7 +94,8 @@ struct TcArgs {
     int M, K;            // N = 256; K a multiple of 16, at most 256
     int ring;            // A ring slots
     int epi;             // 0: bias + ReLU -> bf16; 1: ReLU mask -> bf16; 2: bias + ReLU, rounded to bf16,
-                         // then the 8 logits of the row (W3, b3) instead of the row itself
+                         // then the 8 logits of the row (W3, b3) instead of the row itself; 3: both the
+                         // row (as 0) and its logits (as 2)
     const float *bias;
     const __nv_bfloat16 *mask;
     __nv_bfloat16 *C;    // [M x 256] row-major (epi 0, 1)
@@ -132,7 +134,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_gemm_kernel(const TcArgs g)
     unsigned char *sb = tc_smem;                                      // B: nkc chunks of 32 KB
     unsigned char *sa = tc_smem + nkc * TC_B_BYTES;                   // A ring: g.ring slots of 16 KB
     uint32_t *stage = reinterpret_cast<uint32_t *>(sa + g.ring * TC_A_BYTES);  // 8 x 32 x 20 words
-    unsigned char *ctrl = reinterpret_cast<unsigned char *>(stage + 8 * TC_STAGE_WORDS);
+    float *outl = reinterpret_cast<float *>(stage + 8 * TC_STAGE_WORDS);  // epi 2, 3: W3, partial logits
+    unsigned char *ctrl = reinterpret_cast<unsigned char *>(stage + 8 * TC_STAGE_WORDS) + TC_OUT_BYTES;
     uint64_t *mbar = reinterpret_cast<uint64_t *>(ctrl);             // [TC_MAX_RING]
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(ctrl + 8 * TC_MAX_RING);
     float *sbias = reinterpret_cast<float *>(ctrl + 8 * TC_MAX_RING + 16);  // [256]
@@ -153,11 +156,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_gemm_kernel(const TcArgs g)
         asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
     }
     for (int i = tid; i < TC_N; i += TC_THREADS) sbias[i] = g.epi != 1 ? g.bias[i] : 0.f;
-    // epi 2: W3 as float32 in the staging area (which that epilogue does not use for rows), and
-    // after it the column halves' partial logits
-    float *w3s = reinterpret_cast<float *>(stage);                 // [256][8]
-    float *xch = reinterpret_cast<float *>(stage) + TC_N * 8;      // [128 rows][8]
-    if (g.epi == 2)
+    // epi 2, 3: W3 as float32, and after it the column halves' partial logits
+    float *w3s = outl;               // [256][8]
+    float *xch = outl + TC_N * 8;    // [128 rows][8]
+    if (g.epi >= 2)
         for (int i = tid; i < TC_N * 8; i += TC_THREADS) w3s[i] = __bfloat162float(g.w3[i]);
 
     // B, resident: chunk c holds k in [64 c, 64 c + 64) of all 256 columns (zero past K)
@@ -285,9 +287,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_gemm_kernel(const TcArgs g)
                             w[j >> 1] = *reinterpret_cast<const uint32_t *>(&hv);
                         }
                     }
-                    if (g.epi == 2) {
+                    if (g.epi >= 2) {
                         // the row's partial logits over these 32 columns, in column order, from the
-                        // rounded activations (the values a stored row would hold)
+                        // rounded activations (the values the stored row holds)
 #pragma unroll
                         for (int j = 0; j < 32; ++j) {
                             const float a = __uint_as_float(j & 1 ? (w[j >> 1] & 0xFFFF0000u) : (w[j >> 1] << 16));
@@ -302,7 +304,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_gemm_kernel(const TcArgs g)
                             part[6] = fmaf(a, wb.z, part[6]);
                             part[7] = fmaf(a, wb.w, part[7]);
                         }
-                        continue;
+                        if (g.epi == 2) continue;  // the row itself is not wanted
                     }
 #pragma unroll
                     for (int q4 = 0; q4 < 4; ++q4)
@@ -337,7 +339,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_gemm_kernel(const TcArgs g)
                     __syncwarp();
                 }
             }
-            if (g.epi == 2) {
+            if (g.epi >= 2) {
                 // the second column half hands its partial logits to the first, which adds them (first
                 // half + second half, then the bias) and stores the row's 8 logits
                 if (half == 1) {
@@ -396,10 +398,10 @@ cudaError_t tc_gemm_n256(const __nv_bfloat16 *A, long long a_m, long long a_k, c
     // K-contiguous operands with 16-byte aligned rows only (the caller keeps the others on mma.sync)
     if (K <= 0 || K % 16 != 0 || K > TC_MAX_KCH * TC_KC || a_k != 1 || b_k != 1 || a_m % 8 != 0 || b_n % 8 != 0 ||
         ((uintptr_t)A & 15) != 0 || ((uintptr_t)B & 15) != 0 || ((uintptr_t)C & 15) != 0 ||
-        (epi == 1 && ((uintptr_t)mask & 15) != 0) || (epi == 2 && (!w3 || !b3 || ((uintptr_t)logits & 15) != 0)))
+        (epi == 1 && ((uintptr_t)mask & 15) != 0) || (epi >= 2 && (!w3 || !b3 || ((uintptr_t)logits & 15) != 0)))
         return cudaErrorInvalidValue;
     const int nkc = (K + TC_KC - 1) / TC_KC;
-    const int fixed = nkc * TC_B_BYTES + 8 * TC_STAGE_WORDS * 4 + TC_CTRL_BYTES;
+    const int fixed = nkc * TC_B_BYTES + 8 * TC_STAGE_WORDS * 4 + TC_OUT_BYTES + TC_CTRL_BYTES;
     const int ring = min(TC_MAX_RING, (TC_SMEM_BUDGET - fixed) / TC_A_BYTES);
     const int bytes = fixed + ring * TC_A_BYTES;
     const int ntiles = (M + TC_M - 1) / TC_M;
