@@ -413,7 +413,7 @@ int jatam_get_genotypes_per_warp(const jatam_config *cfg, int *genotypes_per_war
  * genotype takes as long as its longest replicate instead of the sum of its
  * replicates.  Eligible: items of one shape, lattices up to 16 x 16, k <= 32,
  * the row-major process, no executed-work counters (jatam_profile(2)).
- *   0: for eligible calls whose item count times k is at most 2^20 (2^22
+ *   0: for eligible calls whose item count times k is at most 2^21 (2^23
  *      for sets of three or more tiles) -- the default; the environment
  *      variable JATAM_REPLICATE_LANES, read once, sets the mode;
  *   1: never;   2: for every eligible call.

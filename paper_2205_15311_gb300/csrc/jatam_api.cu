@@ -47,10 +47,10 @@ int g_default_per_warp32 = 32;
 // up to 16 x 16 with k <= 32 whose items x k is at most REPS_MAX_WORK (four times that for sets of
 // three or more tiles, whose genotypes grow longer), 1 never, 2 whenever eligible
 // (jatam_set_replicate_lanes; JATAM_REPLICATE_LANES).  Measured crossovers, L = 16: S_{2,8} slices
-// (k = 20) 2^15 items 0.203 against 0.222 ms, 2^16 0.287 against 0.221; all of S_{2,4} (k = 10)
-// 0.151 against 0.165; S_{3,8} samples (k = 20) 2^17 0.325 against 0.452, 2^18 0.516 against 0.468
+// (k = 20) 2^16 items 0.217 against 0.226 ms, 2^17 0.303 against 0.289; all of S_{2,4} (k = 10)
+// 0.153 against 0.172; S_{3,8} samples (k = 20) 2^18 0.414 against 0.471, 2^19 0.735 against 0.664
 int g_reps_mode = 0;
-size_t REPS_MAX_WORK = size_t(1) << 20;
+size_t REPS_MAX_WORK = size_t(1) << 21;
 
 struct Tuning {
     int warps = 0;    // 0: the CTA size that keeps the most warps resident
