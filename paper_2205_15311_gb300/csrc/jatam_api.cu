@@ -456,7 +456,7 @@ int run(Workspace *w, LaunchArgs a, int S, jatam_result *out, int32_t *fitness, 
     const bool reps = !mixed && !a.lifo && !a.stats && S <= 16 && a.k >= 1 && a.k <= 32 &&
                       (g_reps_mode == 2 ||
                        (g_reps_mode == 0 && n_items * (size_t)a.k <= REPS_MAX_WORK * (a.n >= 3 ? 4 : 1)));
-    const int rwarps = 4;
+    const int rwarps = 3;  // with the small CTA histogram: 18 warps an SM (21 for sets of at most two tiles)
     long long rblocks = 0;
     if (reps && n_items) {
         int per_sm = 0;

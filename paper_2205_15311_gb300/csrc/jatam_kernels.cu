@@ -1001,18 +1001,24 @@ __device__ void table_insert(const Table &T, unsigned long long key, unsigned lo
     atomicOr(err, ERR_TABLE_FULL);
 }
 
-struct SmemHist {
-    unsigned long long key[HIST_SLOTS];
-    unsigned long long min_id[HIST_SLOTS];
-    unsigned count[HIST_SLOTS];
-    unsigned smax[HIST_SLOTS];
-    unsigned smin[HIST_SLOTS];
+template <int SLOTS>
+struct SmemHistT {
+    static constexpr int slots = SLOTS;
+    unsigned long long key[SLOTS];
+    unsigned long long min_id[SLOTS];
+    unsigned count[SLOTS];
+    unsigned smax[SLOTS];
+    unsigned smin[SLOTS];
 };
+using SmemHist = SmemHistT<HIST_SLOTS>;
+// replicate lanes: small calls, few phenotypes, and a CTA's shared memory goes to more warps
+using SmemHistSmall = SmemHistT<64>;
 
-__device__ __forceinline__ void hist_insert(SmemHist &H, const Table &T, unsigned long long key, unsigned cnt,
+template <typename HT>
+__device__ __forceinline__ void hist_insert(HT &H, const Table &T, unsigned long long key, unsigned cnt,
                                             unsigned long long id, unsigned smax, unsigned smin, unsigned *err)
 {
-    unsigned slot = table_slot(key, 8);
+    unsigned slot = table_slot(key, HT::slots == 256 ? 8 : HT::slots == 128 ? 7 : 6);
     for (int p = 0; p < 16; ++p) {
         const unsigned long long old = atomicCAS(&H.key[slot], EMPTY_KEY, key);
         if (old == EMPTY_KEY || old == key) {
@@ -1022,7 +1028,7 @@ __device__ __forceinline__ void hist_insert(SmemHist &H, const Table &T, unsigne
             atomicMin(&H.smin[slot], smin);
             return;
         }
-        slot = (slot + 1) & (HIST_SLOTS - 1);
+        slot = (slot + 1) & (HT::slots - 1);
     }
     table_insert(T, key, cnt, id, smax, smin, err);
 }
@@ -1694,9 +1700,10 @@ __device__ __forceinline__ void warp_loop(const LaunchArgs &a, uint32_t *warp_la
     }
 }
 
-__device__ __forceinline__ void hist_begin(SmemHist &H)
+template <typename HT>
+__device__ __forceinline__ void hist_begin(HT &H)
 {
-    for (int i = threadIdx.x; i < HIST_SLOTS; i += blockDim.x) {
+    for (int i = threadIdx.x; i < HT::slots; i += blockDim.x) {
         H.key[i] = EMPTY_KEY;
         H.min_id[i] = ~0ull;
         H.count[i] = 0u;
@@ -1706,11 +1713,12 @@ __device__ __forceinline__ void hist_begin(SmemHist &H)
     __syncthreads();
 }
 
-__device__ __forceinline__ void hist_end(SmemHist &H, const LaunchArgs &a)
+template <typename HT>
+__device__ __forceinline__ void hist_end(HT &H, const LaunchArgs &a)
 {
     __syncthreads();
     if (a.use_hist) {
-        for (int i = threadIdx.x; i < HIST_SLOTS; i += blockDim.x)
+        for (int i = threadIdx.x; i < HT::slots; i += blockDim.x)
             if (H.key[i] != EMPTY_KEY)
                 table_insert(a.table, H.key[i], H.count[i], H.min_id[i], H.smax[i], H.smin[i], a.err);
     }
@@ -1759,7 +1767,7 @@ __device__ __forceinline__ uint32_t nibble_mask(uint32_t byte)
 }
 
 template <int S, int NT>
-__device__ __forceinline__ void reps_loop(const LaunchArgs &a, uint32_t *warp_lanes, SmemHist &H,
+__device__ __forceinline__ void reps_loop(const LaunchArgs &a, uint32_t *warp_lanes, SmemHistSmall &H,
                                           const unsigned long long *list, unsigned long long front,
                                           unsigned long long back, unsigned long long *work_next,
                                           const unsigned long long *mid_list, unsigned long long mid)
@@ -1942,7 +1950,7 @@ template <int S, int NT>
 __global__ void __launch_bounds__(MAX_CTA_WARPS * 32, 3) classify_reps_kernel(const LaunchArgs a)
 {
     extern __shared__ uint32_t smem_lanes[];
-    __shared__ SmemHist H;
+    __shared__ SmemHistSmall H;
     hist_begin(H);
     const int warp = threadIdx.x >> 5;
     uint32_t *warp_lanes = smem_lanes + (size_t)warp * Geo<S, NT>::WORDS * 32;
