@@ -97,6 +97,10 @@ extern "C" {
                                 mixed batches of jatam_classify_batch). */
 #define JATAM_GRAPH 0x8u     /* capture the call's kernel sequence as a CUDA graph the first time a given
                                 set of arguments is seen, and replay it on later calls with the same set */
+#define JATAM_NO_DEDUP 0x100u /* ga_evaluate: classify every genome, also the repeats of a genome (by
+                                default a batch's distinct genomes are classified once each and their
+                                repeats copy the result, which is the same: a genome is its own stream
+                                id); for batches known to hold no repeats, this saves the table pass */
 
 /* Limits of the supported model sizes. */
 #define JATAM_MAX_TILES 4

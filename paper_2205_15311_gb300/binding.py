@@ -32,6 +32,7 @@ JATAM_C4_HASH = 0x10
 JATAM_PERSISTENT = 0x20
 JATAM_ORBITS = 0x40
 JATAM_LIFO = 0x80
+JATAM_NO_DEDUP = 0x100
 JATAM_NOALLOC_MAX_COUNT = 1048576
 
 RESULT_DTYPE = np.dtype([("cls", "u1"), ("decided_rep", "u1"), ("size", "<u2"), ("shape_hash", "<u4")])
@@ -412,8 +413,10 @@ def classify_batch(colours, *, n=0, c=0, L=0, k=0, seed=0, shapes=None, stream_i
                                       _addr(out), _addr(hist), hist_cap, _addr(hist_len), _stream_handle(stream)))
 
 
-def evaluate_genomes(genomes, fitness, *, n, c, L, k, seed, out=None, stream=None, sync=False, graph=False):
-    cfg = make_config(n, c, L, k, seed, (JATAM_SYNC if sync else 0) | (JATAM_GRAPH if graph else 0))
+def evaluate_genomes(genomes, fitness, *, n, c, L, k, seed, out=None, stream=None, sync=False, graph=False,
+                     dedup=True):
+    cfg = make_config(n, c, L, k, seed, (JATAM_SYNC if sync else 0) | (JATAM_GRAPH if graph else 0) |
+                      (0 if dedup else JATAM_NO_DEDUP))
     N = int(genomes.shape[0])
     return check(ga_evaluate(ctypes.addressof(cfg), _addr(genomes), N, _addr(fitness), _addr(out),
                              _stream_handle(stream)))

@@ -51,6 +51,8 @@ int g_default_per_warp32 = 32;
 // 0.153 against 0.172; S_{3,8} samples (k = 20) 2^18 0.414 against 0.471, 2^19 0.735 against 0.664
 int g_reps_mode = 0;
 size_t REPS_MAX_WORK = size_t(1) << 21;
+// genome batches classify each distinct genome once (JATAM_GENOME_DEDUP=0: every item)
+int g_dedup = 1;
 
 struct Tuning {
     int warps = 0;    // 0: the CTA size that keeps the most warps resident
@@ -88,6 +90,7 @@ void read_env_overrides()
     }
     if (const char *v = getenv("JATAM_CROP_TABLE")) g_crop_table = atoi(v) != 0;
     if (const char *v = getenv("JATAM_HEAVY_LEVELS")) g_heavy_levels = atoi(v) == 2 ? 2 : 3;
+    if (const char *v = getenv("JATAM_GENOME_DEDUP")) g_dedup = atoi(v) != 0;
     if (const char *v = getenv("JATAM_REPLICATE_LANES")) {
         const int x = atoi(v);
         if (x >= 0 && x <= 2) g_reps_mode = x;
@@ -173,6 +176,8 @@ struct Workspace {
     size_t ga_bytes = 0;
     void *topn_buf = nullptr;    // jatam_select_top: the selection's scratch
     size_t topn_bytes = 0;
+    void *dedup_buf = nullptr;   // genome deduplication: table keys, first occurrences, item slots
+    size_t dedup_bytes = 0;
     void *screen_buf = nullptr;  // ga_run_screened: candidates, chosen indices, scores
     size_t screen_bytes = 0;
     unsigned long long *screen_cand = nullptr, *screen_idx = nullptr;
@@ -421,6 +426,34 @@ int run(Workspace *w, LaunchArgs a, int S, jatam_result *out, int32_t *fitness, 
     };
     a.spill = spill_of(w->spill_rows, w->esc_ctl);
     a.stats = (g_profile & 2) ? w->stats : nullptr;
+    // genome batches: every distinct genome is classified once, its repeats copy the result (a result
+    // depends only on the genome: it is also the stream id).  Not with the executed-work counters, the
+    // orbit mode, or a call large enough to run in pieces from host buffers
+    const bool dedup = a.mode == MODE_GENOMES && g_dedup && !a.no_dedup && !a.stats && !a.orbits && n_items >= 2 &&
+                       n_items < (size_t(1) << 30) && !(n_items >= 2 * PIPE_MIN_ITEMS && (o.host_out || o.host_fit));
+    a.dup_keys = nullptr;
+    a.dup_owner = nullptr;
+    a.dup_slot = nullptr;
+    a.dup_mask = 0;
+    if (dedup) {
+        // keys of 2^27 slots at most, at the front of the buffer (so that they outlive a regrowth of the
+        // rest); a new buffer is emptied once, every call empties the slots it used
+        size_t cap = 1;
+        while (cap < 2 * n_items) cap <<= 1;
+        const size_t kb = cap * 8, ob = (cap * 4 + 255) & ~size_t(255);
+        const size_t need = kb + ob + n_items * 4 + 256;
+        if (need > w->dedup_bytes) {
+            int rc = grow(&w->dedup_buf, &w->dedup_bytes, need);
+            if (rc) return rc;
+            CUDA_TRY(cudaMemset(w->dedup_buf, 0xFF, w->dedup_bytes));
+            CUDA_TRY(cudaDeviceSynchronize());  // empty before any stream of the call uses it
+        }
+        char *p = static_cast<char *>(w->dedup_buf);
+        a.dup_keys = reinterpret_cast<unsigned long long *>(p);
+        a.dup_owner = reinterpret_cast<unsigned *>(p + kb);
+        a.dup_slot = reinterpret_cast<unsigned *>(p + kb + ob);
+        a.dup_mask = (unsigned)(cap - 1);
+    }
     a.err = w->err;
     const bool mixed = a.mode == MODE_RECORDS && a.shapes;
     const Tuning tune = force ? *force : tuning_for(S, mixed ? 0 : a.n, mixed ? 0 : a.c);
@@ -620,6 +653,7 @@ int run(Workspace *w, LaunchArgs a, int S, jatam_result *out, int32_t *fitness, 
             if (int rc = launch_per_size(a, s)) return rc;
         }
         if (n_items && mixed && !per_shape) CUDA_TRY(launch_classify_mixed(a, mixed_blocks, s));
+        if (n_items && dedup) CUDA_TRY(launch_dup_fill(a, (int)pblocks, s));
         if (events) CUDA_TRY(cudaEventRecord(w->k_stop, s));
         if (record_shapes) CUDA_TRY(launch_shape_scan(w->shapes, a.crops, CROPS_LOG2, a.spill, s));
         if (n_items && a.orbits) CUDA_TRY(launch_orbit_fill(a, (int)pblocks, s));
@@ -762,7 +796,7 @@ int run(Workspace *w, LaunchArgs a, int S, jatam_result *out, int32_t *fitness, 
         std::string key;
         auto put = [&key](const void *p, size_t n) { key.append(static_cast<const char *>(p), n); };
         const void *ptrs[] = {a.colours, a.shapes, a.ids, a.genomes, a.out, a.fitness, a.list, o.hist_dev,
-                              o.host_len ? nullptr : o.hist_len_dev, a.lifo_stack, w->esc};
+                              o.host_len ? nullptr : o.hist_len_dev, a.lifo_stack, w->esc, a.dup_keys, a.dup_owner, a.dup_slot};
         put(ptrs, sizeof ptrs);
         const long long nums[] = {a.mode, (long long)a.first, (long long)a.count, a.n, a.c, a.L, a.k, a.key0, a.key1,
                                   a.use_hist, a.stop_at, (long long)a.list_stride, a.bucket, a.plan_w32, a.plan_w16,
@@ -770,7 +804,8 @@ int run(Workspace *w, LaunchArgs a, int S, jatam_result *out, int32_t *fitness, 
                                   fixed[0].blocks, fixed[0].warps, fixed[0].stop_at, fixed[1].blocks, fixed[1].warps,
                                   fixed[1].stop_at, fixed[2].blocks, fixed[2].warps, fixed[2].stop_at,
                                   a.stats ? 1 : 0, a.c4, a.orbits, per_warp ? 1 : 0, windowed ? 1 : 0,
-                                  wblocks, tw.warps, tw.stop_at, g_heavy_levels, reps ? 1 : 0, rblocks};
+                                  wblocks, tw.warps, tw.stop_at, g_heavy_levels, reps ? 1 : 0, rblocks,
+                                  (long long)a.dup_mask};
         put(nums, sizeof nums);
         cudaGraphExec_t exec = nullptr;
         auto it = w->graphs.find(key);
@@ -987,6 +1022,7 @@ int ga_evaluate(const jatam_config *cfg, const uint64_t *genomes, uint64_t N, in
     a.count = N;
     a.lifo = (cfg->flags & JATAM_LIFO) ? 1 : 0;
     a.c4 = (cfg->flags & JATAM_C4_HASH) ? 1 : 0;
+    a.no_dedup = (cfg->flags & JATAM_NO_DEDUP) ? 1 : 0;
     a.genomes = static_cast<const unsigned long long *>(gdev);
     a.n = cfg->n; a.c = cfg->c; a.L = cfg->L; a.k = cfg->k;
     a.key0 = (uint32_t)cfg->seed;
@@ -1197,7 +1233,9 @@ int ga_loop(const jatam_ga_config *ga, const jatam_config *cls, int fitness_kind
     if (cls) cc = *cls;
     cc.n = ga->n;
     cc.c = ga->c;
-    cc.flags = JATAM_GRAPH;  // the fitness call is the same every generation: replay its graph
+    // the fitness call is the same every generation: replay its graph; a screened population is chosen
+    // distinct (repeats rank last), so it skips the repeat table
+    cc.flags = JATAM_GRAPH | (net ? JATAM_NO_DEDUP : 0u);
     unsigned long long *pop = reinterpret_cast<unsigned long long *>(population);
     for (uint32_t gen = 0; gen < generations; ++gen) {
         GaScratch sc;
@@ -1879,6 +1917,7 @@ void jatam_shutdown(void)
         if (w->ga_buf) cudaFree(w->ga_buf);
         if (w->screen_buf) cudaFree(w->screen_buf);
         if (w->topn_buf) cudaFree(w->topn_buf);
+        if (w->dedup_buf) cudaFree(w->dedup_buf);
         if (w->lifo_buf) cudaFree(w->lifo_buf);
         cudaEventDestroy(w->last);
         cudaEventDestroy(w->k_start);
@@ -1974,7 +2013,7 @@ int jatam_workspace_bytes(uint64_t *bytes)
     b += 3 * 8 + (size_t(2) << CROPS_LOG2) * 8 + 4 * 8 + 4 + 4 + 6 * 8;  // counters, crop table
     b += ((size_t(8) + 4 + 128) << SHAPES_LOG2) + 4 * 4;                 // shape side table
     b += w->list_bytes + w->stage_in_bytes + w->stage_out_bytes + w->stage_aux_bytes +
-         w->stage_hist_cap * sizeof(jatam_hist_entry) + w->lifo_bytes + w->ga_bytes + w->screen_bytes + w->topn_bytes +
+         w->stage_hist_cap * sizeof(jatam_hist_entry) + w->lifo_bytes + w->ga_bytes + w->screen_bytes + w->topn_bytes + w->dedup_bytes +
          w->alt.list_bytes + w->esc_bytes + w->alt.esc_bytes + ESC_CTL_WORDS * 8 + w->spill_bytes +
          w->alt.spill_bytes;
     if (w->copy) b += 3 * 8 + 6 * 8 + 4 + (size_t(2) << CROPS_LOG2) * 8;

@@ -116,6 +116,12 @@ struct LaunchArgs {
                                     // S x S window around the seed; an item whose growth offers a tile
                                     // outside the window is not classified here but appended to esc_list
     unsigned long long *esc_count;  // (count in *esc_count) for a launch on the full lattice
+    unsigned long long *dup_keys;   // non-null: genome deduplication -- an open-addressing table of the
+    unsigned *dup_owner;            // call's genomes (keys ~0 = empty, 2^k >= 2 count slots, dup_mask =
+    unsigned *dup_slot;             // 2^k - 1): the item that claims a genome's slot classifies it
+    unsigned dup_mask;              // (dup_owner), a repeat records its slot with the top bit set
+                                    // (dup_slot) and takes the owner's result in the fill pass
+    int no_dedup;                   // JATAM_NO_DEDUP: every genome classified
 };
 
 // Lattice template: rows of S bits, S in {8, 16, 32}, L <= S; nt = 8 tuple ids
@@ -172,6 +178,10 @@ cudaError_t launch_hist_emit(Compact c, const unsigned *nkeys, jatam_hist_entry 
                              uint32_t *hist_len, int blocks, cudaStream_t st);
 cudaError_t launch_philox(const uint32_t *in, unsigned long long n, uint32_t *out, cudaStream_t st);
 cudaError_t launch_orbit_fill(const LaunchArgs &a, int blocks, cudaStream_t st);
+// genome deduplication (MODE_GENOMES): after the growth kernels, every repeat copies its owner's
+// result, and every used slot of the table is emptied again (the table must be all empty before
+// the first call that uses it)
+cudaError_t launch_dup_fill(const LaunchArgs &a, int blocks, cudaStream_t st);
 
 // genetic algorithm (jatam_ga.cu)
 struct GaArgs {

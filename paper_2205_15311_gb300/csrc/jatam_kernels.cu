@@ -1208,6 +1208,28 @@ __device__ __forceinline__ void write_result(const LaunchArgs &a, unsigned long 
 // result of every item it decides, counts them into the histogram, and appends
 // every other item to the list that the growth kernel consumes.
 // ---------------------------------------------------------------------------
+// genome deduplication: claim the genome's slot of the call's table (the claimer classifies it), or
+// find it claimed and record the slot as a repeat's (the top bit set)
+__device__ __forceinline__ bool genome_repeat(const LaunchArgs &a, unsigned long long g, unsigned long long idx)
+{
+    unsigned h = (unsigned)((g * 0x9E3779B97F4A7C15ull) >> 32) & a.dup_mask;
+    for (unsigned p = 0; p <= a.dup_mask; ++p) {
+        const unsigned long long old = atomicCAS(&a.dup_keys[h], ~0ull, g);
+        if (old == ~0ull) {
+            a.dup_owner[h] = (unsigned)idx;
+            a.dup_slot[idx] = h;
+            return false;
+        }
+        if (old == g) {
+            a.dup_slot[idx] = h | 0x80000000u;
+            return true;
+        }
+        h = (h + 1) & a.dup_mask;
+    }
+    atomicOr(a.err, ERR_GUARD);  // unreachable: the table holds at least 2 count slots
+    return false;
+}
+
 constexpr int PF_ITEMS = 2;  // items per thread and iteration of the pre-filter (its barriers per item halve)
 
 __global__ void __launch_bounds__(256) prefilter_kernel(const LaunchArgs a, int smax)
@@ -1256,6 +1278,9 @@ __global__ void __launch_bounds__(256) prefilter_kernel(const LaunchArgs a, int 
                     write_result(a, idx, 255, 0, 0u, 0u);
                 } else if (a.orbits && orbit_rep(it.sid, it.n, it.c, b_uniform) != it.sid) {
                     // not its orbit's representative: the fill pass copies the representative's result
+                } else if (a.dup_keys && genome_repeat(a, it.sid, idx)) {
+                    // another item owns this genome (same genome, same stream id, same result): the fill
+                    // pass copies its result
                 } else {
                     const int so = seed_outcome(it.cols, it.n, it.c, it.L);
                     if (so < 0) {
@@ -2841,6 +2866,38 @@ cudaError_t launch_hist_emit(Compact c, const unsigned *nkeys, jatam_hist_entry 
                              uint32_t *hist_len, int blocks, cudaStream_t st)
 {
     hist_emit_kernel<<<blocks, 256, 0, st>>>(c, nkeys, hist, cap, hist_len);
+    return cudaGetLastError();
+}
+
+// Genome deduplication: a result depends only on the genome (its stream id is the genome), so a
+// repeat takes the result of the item that owns the genome's slot; every used slot is emptied again
+__global__ void __launch_bounds__(256) dup_fill_kernel(const LaunchArgs a)
+{
+    __shared__ SmemHist H;
+    hist_begin(H);
+    for (unsigned long long idx = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; idx < a.count;
+         idx += (unsigned long long)gridDim.x * blockDim.x) {
+        const unsigned sl = a.dup_slot[idx], h = sl & 0x7FFFFFFFu;
+        if (sl >> 31) {
+            const unsigned f = a.dup_owner[h];
+            if (a.fitness) a.fitness[idx] = a.fitness[f];
+            if (a.out) {
+                const jatam_result res = a.out[f];
+                a.out[idx] = res;
+                if (a.use_hist && res.cls != 255)
+                    hist_insert(H, a.table, ((unsigned long long)res.cls << 32) | res.shape_hash, 1u, a.genomes[idx],
+                                res.size, res.size, a.err);
+            }
+        }
+        a.dup_keys[h] = ~0ull;
+    }
+    hist_end(H, a);
+}
+
+cudaError_t launch_dup_fill(const LaunchArgs &a, int blocks, cudaStream_t st)
+{
+    if (a.count == 0) return cudaSuccess;
+    dup_fill_kernel<<<blocks, 256, 0, st>>>(a);
     return cudaGetLastError();
 }
 
