@@ -556,6 +556,100 @@ __device__ __forceinline__ int seed_outcome(unsigned long long cols, int n, int 
     return seed_outcome_w<unsigned long long>(cols, n, c, L);
 }
 
+// Seed-step table of every tile of 3-bit colours, indexed by its packed value t
+// (12 bits, edge i at bits 3 (3 - i): the genotype's own encoding of one tile).
+// Word k, nibble v (v = 1 .. 7): bit r is set when t turned by r shows colour v on
+// side k, i.e. edge (k - r) mod 4 of t has colour v.  Colour 0 binds nothing and
+// its nibbles hold two other fields: word 0 the turns that give distinct tuples
+// (bit 0; bit 1 unless a quarter turn leaves t unchanged; bits 2 and 3 unless a
+// half turn does, as in lane_tables), words 1 to 3 the smallest packed value of
+// the four turns of t, 4 bits each, lowest first (two tiles are turns of each
+// other exactly when these agree).  Built by the compiler.
+constexpr uint32_t seed_tile_colour(uint32_t t, int i) { return (t >> (3 * (3 - i))) & 7u; }
+constexpr uint32_t seed_tile_turn(uint32_t t, int r)
+{
+    uint32_t v = 0;
+    for (int j = 0; j < 4; ++j) v |= seed_tile_colour(t, (j + 4 - r) & 3) << (3 * (3 - j));
+    return v;
+}
+struct __align__(16) SeedTab {
+    uint32_t w[4096][4];
+};
+constexpr SeedTab make_seed_tab()
+{
+    SeedTab T{};
+    for (uint32_t t = 0; t < 4096; ++t) {
+        for (int k = 0; k < 4; ++k) {
+            uint32_t word = 0;
+            for (int r = 0; r < 4; ++r) word |= 1u << (4 * seed_tile_colour(t, (k + 4 - r) & 3) + r);
+            T.w[t][k] = word & ~15u;
+        }
+        uint32_t low = t;
+        for (int r = 1; r < 4; ++r) low = seed_tile_turn(t, r) < low ? seed_tile_turn(t, r) : low;
+        T.w[t][0] |= 1u | (seed_tile_turn(t, 1) != t ? 2u : 0u) | (seed_tile_turn(t, 2) != t ? 12u : 0u);
+        T.w[t][1] |= low & 15u;
+        T.w[t][2] |= (low >> 4) & 15u;
+        T.w[t][3] |= low >> 8;
+    }
+    return T;
+}
+__device__ constexpr SeedTab g_seed_tab = make_seed_tab();
+
+// nibble a: the colour that binds colour a (Section 2.2: 1-2, 3-4, 5-6; 0 and an
+// odd top colour bind nothing, 0 here), the rule of seed_outcome_two for c <= 8
+__device__ __forceinline__ uint32_t partner_nibbles(int c)
+{
+    uint32_t p = 0;
+#pragma unroll
+    for (int a = 1; a < 8; ++a) {
+        const int pa = (a & 1) ? ((a + 1 < c) ? a + 1 : 0) : a - 1;
+        p |= (uint32_t)pa << (4 * a);
+    }
+    return p;
+}
+
+// The seed step of replicate 0 for one or two tiles of 3-bit colours, from the
+// packed genotype g and the seed table: the same outcome as seed_outcome_two.
+// For side d of the seed the candidates are the distinct tuples whose side d + 2
+// carries the partner pa of the seed's colour there: nibble pa of word d + 2 of
+// each tile's entry, restricted to the tile's distinct turns (and to none of
+// tile 1's when it is a turn of tile 0).
+__device__ __forceinline__ int seed_outcome_tab(unsigned long long g, int n, uint32_t partner, int L)
+{
+    const uint4 *tab = reinterpret_cast<const uint4 *>(g_seed_tab.w);
+    const uint32_t t0 = (uint32_t)(n == 2 ? g >> 12 : g) & 0xFFFu;
+    const uint4 E0 = __ldg(tab + t0);
+    uint4 E1 = make_uint4(0u, 0u, 0u, 0u);
+    uint32_t reps1 = 0u;
+    if (n == 2) {
+        E1 = __ldg(tab + ((uint32_t)g & 0xFFFu));
+        const bool turned = ((E0.y ^ E1.y) & 15u) == 0u && ((E0.z ^ E1.z) & 15u) == 0u && ((E0.w ^ E1.w) & 15u) == 0u;
+        reps1 = turned ? 0u : (E1.x & 15u);
+    }
+    const uint32_t reps0 = E0.x & 15u;
+    const int cx = L >> 1;
+    bool nd = false, unb = false;
+    int sites = 0;
+#pragma unroll
+    for (int d = 0; d < 4; ++d) {
+        const uint32_t pa = (partner >> (4 * ((t0 >> (3 * (3 - d))) & 7u))) & 15u;
+        const int k = (d + 2) & 3;
+        const uint32_t w0 = k == 0 ? E0.x : k == 1 ? E0.y : k == 2 ? E0.z : E0.w;
+        const uint32_t w1 = k == 0 ? E1.x : k == 1 ? E1.y : k == 2 ? E1.z : E1.w;
+        const uint32_t X = pa ? (((w0 >> (4 * pa)) & reps0) | (((w1 >> (4 * pa)) & reps1) << 4)) : 0u;
+        if (X) {
+            const int qx = cx + (d == 1) - (d == 3), qy = cx + (d == 2) - (d == 0);
+            const bool inside = qx >= 0 && qy >= 0 && qx < L && qy < L;
+            if (X & (X - 1)) nd = true;
+            else if (!inside) unb = true;
+            ++sites;
+        }
+    }
+    if (nd) return JATAM_ND_LOCAL;
+    if (unb) return JATAM_UNBOUNDED;
+    return -sites;
+}
+
 // The replicate just ended (local ambiguity, unbounded growth, or an empty
 // frontier): apply the first-deciding-replicate rule.
 // ---------------------------------------------------------------------------
@@ -1140,7 +1234,8 @@ struct Item {
     bool ok;
 };
 
-template <bool UNROLLED = false>
+// COLS = false: the packed genotype only (it.cols is left 0; the pre-filter's table path)
+template <bool UNROLLED = false, bool COLS = true>
 __device__ __forceinline__ Item load_item(const LaunchArgs &a, unsigned long long idx, int b_uniform, int smax)
 {
     Item it;
@@ -1180,7 +1275,7 @@ __device__ __forceinline__ Item load_item(const LaunchArgs &a, unsigned long lon
         const int bits = 4 * a.n * b_uniform;
         if (bits < 64) g &= (1ull << bits) - 1ull;
         it.sid = g;
-        it.cols = unpack_genotype<UNROLLED>(g, a.n, b_uniform);
+        it.cols = COLS ? unpack_genotype<UNROLLED>(g, a.n, b_uniform) : 0ull;
     }
     return it;
 }
@@ -1232,7 +1327,10 @@ __device__ __forceinline__ bool genome_repeat(const LaunchArgs &a, unsigned long
 
 constexpr int PF_ITEMS = 2;  // items per thread and iteration of the pre-filter (its barriers per item halve)
 
-__global__ void __launch_bounds__(256) prefilter_kernel(const LaunchArgs a, int smax)
+// TAB: genotypes (not records) of one or two tiles of 3-bit colours, whose seed
+// step is read from the seed table (seed_outcome_tab); one lattice size class
+template <bool TAB>
+__global__ void __launch_bounds__(256, 5) prefilter_kernel(const LaunchArgs a, int smax)
 {
     // keys decided here: 0 = (ND_LOCAL, 0), 1 = (UNBOUNDED, 0), 2 = (DET_BOUNDED, monomer)
     __shared__ unsigned s_cnt[3];
@@ -1247,12 +1345,12 @@ __global__ void __launch_bounds__(256) prefilter_kernel(const LaunchArgs a, int 
     __syncthreads();
     const int lane = threadIdx.x & 31;
     const int b_uniform = log2_colours(a.c);
+    const uint32_t partner = TAB ? partner_nibbles(a.c) : 0u;
     const uint32_t mono = monomer_shape_hash(a.c4 != 0);
-    // stream ids that grow with the item index (an index range: the genotype
-    // itself; records without ids: the index): the lowest lane of a warp holds
-    // the smallest.  Sampled genotypes and GA genomes need the reduction.
-    const bool sid_is_index = a.mode == MODE_RANGE || (a.mode == MODE_RECORDS && !a.ids);
     const int nlists = 6;
+    // this thread's decided items per key and their smallest stream ids (scalars: registers)
+    unsigned hc0 = 0u, hc1 = 0u, hc2 = 0u;
+    unsigned long long hm0 = ~0ull, hm1 = ~0ull, hm2 = ~0ull;
     const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x * PF_ITEMS;
     int buf = 0;
     for (unsigned long long base = (unsigned long long)blockIdx.x * blockDim.x * PF_ITEMS; base < a.count;
@@ -1270,7 +1368,7 @@ __global__ void __launch_bounds__(256) prefilter_kernel(const LaunchArgs a, int 
             klass[u] = 0;
             sid[u] = 0;
             if (idx < a.count) {
-                const Item it = load_item<true>(a, idx, b_uniform, smax);
+                const Item it = load_item<true, !TAB>(a, idx, b_uniform, smax);
                 sid[u] = it.sid;
                 if (a.bucket) klass[u] = (it.L <= 8) ? 0 : (it.L <= 16) ? 1 : 2;  // (+ 3 below for light items)
                 if (!it.ok) {
@@ -1282,7 +1380,8 @@ __global__ void __launch_bounds__(256) prefilter_kernel(const LaunchArgs a, int 
                     // another item owns this genome (same genome, same stream id, same result): the fill
                     // pass copies its result
                 } else {
-                    const int so = seed_outcome(it.cols, it.n, it.c, it.L);
+                    const int so = TAB ? seed_outcome_tab(it.sid, it.n, partner, it.L)
+                                       : seed_outcome(it.cols, it.n, it.c, it.L);
                     if (so < 0) {
                         grow[u] = true;
                         // two or more frontier sites after the seed: the genotypes that can
@@ -1311,9 +1410,13 @@ __global__ void __launch_bounds__(256) prefilter_kernel(const LaunchArgs a, int 
 #pragma unroll
         for (int u = 0; u < PF_ITEMS; ++u) {
             my_off[u] = 0;
+#pragma unroll
             for (int kc = 0; kc < nlists; ++kc) {
-                // one size class: lists 0 and 3 (and 1, the middle level of a three-level order)
-                if (!a.bucket && kc % 3 != 0 && !(kc == 1 && a.heavy_first == 2)) continue;
+                // one size class: lists 0 and 3 (and 1, the middle level of a three-level order);
+                // the table path has one class
+                if (TAB ? (kc != 0 && kc != 3 && !(kc == 1 && a.heavy_first == 2))
+                        : (!a.bucket && kc % 3 != 0 && !(kc == 1 && a.heavy_first == 2)))
+                    continue;
                 const unsigned gm = __ballot_sync(FULL, grow[u] && klass[u] == kc);
                 unsigned woff = 0;
                 if (gm && lane == 0) woff = atomicAdd(&s_fill[buf][kc], (unsigned)__popc(gm));
@@ -1340,29 +1443,37 @@ __global__ void __launch_bounds__(256) prefilter_kernel(const LaunchArgs a, int 
         if (a.use_hist) {
 #pragma unroll
             for (int u = 0; u < PF_ITEMS; ++u) {
-#pragma unroll
-                for (int q = 0; q < 3; ++q) {
-                    const unsigned m = __ballot_sync(FULL, key[u] == q);
-                    if (m) {
-                        unsigned long long v;
-                        if (sid_is_index) {
-                            v = __shfl_sync(FULL, sid[u], __ffs(m) - 1);
-                        } else {
-                            v = (key[u] == q) ? sid[u] : ~0ull;
-#pragma unroll
-                            for (int off = 16; off > 0; off >>= 1) {
-                                const unsigned long long o = __shfl_xor_sync(FULL, v, off);
-                                v = o < v ? o : v;
-                            }
-                        }
-                        if (lane == 0) {
-                            atomicAdd(&s_cnt[q], (unsigned)__popc(m));
-                            atomicMin(&s_min[q], v);
-                        }
-                    }
+                const unsigned long long v = sid[u];
+                if (key[u] == 0) {
+                    hc0 += 1u;
+                    hm0 = v < hm0 ? v : hm0;
+                } else if (key[u] == 1) {
+                    hc1 += 1u;
+                    hm1 = v < hm1 ? v : hm1;
+                } else if (key[u] == 2) {
+                    hc2 += 1u;
+                    hm2 = v < hm2 ? v : hm2;
                 }
             }
         }
+    }
+    // the thread's counts and smallest stream ids, summed and reduced over the warp
+    if (a.use_hist) {
+        auto flush = [&](int q, unsigned hc, unsigned long long v) {
+            const unsigned cnt = __reduce_add_sync(FULL, hc);
+#pragma unroll
+            for (int off = 16; off > 0; off >>= 1) {
+                const unsigned long long o = __shfl_xor_sync(FULL, v, off);
+                v = o < v ? o : v;
+            }
+            if (lane == 0 && cnt) {
+                atomicAdd(&s_cnt[q], cnt);
+                atomicMin(&s_min[q], v);
+            }
+        };
+        flush(0, hc0, hm0);
+        flush(1, hc1, hm1);
+        flush(2, hc2, hm2);
     }
     __syncthreads();
     if (a.use_hist && threadIdx.x < 3 && s_cnt[threadIdx.x]) {
@@ -2833,13 +2944,18 @@ cudaError_t load_index_range_kernels()
     // cudaFuncGetAttributes loads a kernel that lazy module loading has not yet loaded
     cudaFuncAttributes fa;
     cudaError_t e = cudaFuncGetAttributes(&fa, reset_kernel);
-    if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, prefilter_kernel);
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, prefilter_kernel<false>);
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, prefilter_kernel<true>);
     return e;
 }
 
 cudaError_t launch_prefilter(const LaunchArgs &a, int smax, int blocks, cudaStream_t st)
 {
-    prefilter_kernel<<<blocks, 256, 0, st>>>(a, smax);
+    // the seed table covers genotypes (not records) of one or two tiles of 3-bit colours
+    if (a.mode != MODE_RECORDS && !a.bucket && a.n >= 1 && a.n <= 2 && a.c == 8)
+        prefilter_kernel<true><<<blocks, 256, 0, st>>>(a, smax);
+    else
+        prefilter_kernel<false><<<blocks, 256, 0, st>>>(a, smax);
     return cudaGetLastError();
 }
 
