@@ -1963,23 +1963,25 @@ __device__ __forceinline__ void reps_loop(const LaunchArgs &a, uint32_t *warp_la
         // every lane one step a round until all replicates have ended; the Philox block of a
         // lane's draw is computed in the round that first needs it (the lanes move in step,
         // so they need new blocks in the same rounds)
-        for (;;) {
+        for (int round = 1;; ++round) {
             const uint32_t key = (uint32_t)Ls.rep * 512u + ((uint32_t)Ls.step >> 2);
-            const bool need = Ls.phase == PH_GROW && Ls.ka != key;
-            if (__any_sync(FULL, need) && need) {
+            if (Ls.phase == PH_GROW && Ls.ka != key) {
                 Ls.pa = philox_block(key, Ls.sid, a.key0, a.key1);
                 Ls.ka = key;
             }
             lane_step<S, false, true>(Ls, my, a.key0, a.key1, a.err, nullptr);
             // a replicate known to deviate -- ended in local ambiguity or unbounded growth, or
             // terminated at another size than replicate 0 -- makes every higher replicate
-            // irrelevant (the first deviating one decides): those lanes stop
-            const bool ended = lane < Ls.k && Ls.phase == PH_DONE;
-            const int size0 = __shfl_sync(FULL, Ls.size, 0);
-            const bool term0 = __shfl_sync(FULL, ended && Ls.cls == JATAM_DET_BOUNDED, 0);
-            const bool known = ended && (Ls.cls != JATAM_DET_BOUNDED || (lane > 0 && term0 && Ls.size != size0));
-            const unsigned km = __ballot_sync(FULL, known);
-            if (km && lane > __ffs(km) - 1 && (Ls.phase == PH_START || Ls.phase == PH_GROW)) Ls.phase = PH_DONE;
+            // irrelevant (the first deviating one decides): those lanes stop, checked every
+            // fourth round (a lane that runs on for a few rounds more changes no result)
+            if ((round & 3) == 0) {
+                const bool ended = lane < Ls.k && Ls.phase == PH_DONE;
+                const int size0 = __shfl_sync(FULL, Ls.size, 0);
+                const bool term0 = __shfl_sync(FULL, ended && Ls.cls == JATAM_DET_BOUNDED, 0);
+                const bool known = ended && (Ls.cls != JATAM_DET_BOUNDED || (lane > 0 && term0 && Ls.size != size0));
+                const unsigned km = __ballot_sync(FULL, known);
+                if (km && lane > __ffs(km) - 1 && (Ls.phase == PH_START || Ls.phase == PH_GROW)) Ls.phase = PH_DONE;
+            }
             if (!__any_sync(FULL, Ls.phase == PH_START || Ls.phase == PH_GROW)) break;
         }
         __syncwarp();
