@@ -66,9 +66,21 @@ std::map<std::tuple<int, int, int>, Tuning> g_tuned;
 
 // optional overrides of the launch shape (for tuning sweeps)
 // host-buffer calls of at least 2 * PIPE_MIN_ITEMS items run in pieces (JATAM_PIPE_PIECE_LOG2 sets it,
-// 2^20 .. 2^26).  End to end on all of S_{2,8} (results to page-locked memory): 2^23 3.17 ms,
-// 2^22 2.91 ms, 2^21 3.33 ms, 2^24 3.19 ms
+// 2^20 .. 2^26)
 size_t PIPE_MIN_ITEMS = size_t(1) << 22;
+// The piece schedule of such calls.  Two forms: (a) staggered -- a piece's work waits for the previous
+// piece's pre-filter, so that its growth launch queues behind the previous one and fills that launch's
+// tail, and pieces end one after another: equal pieces and a last one of a quarter, each at least
+// 2 * PIPE_MIN_ITEMS items; (b) paired -- pieces alternate between two streams with no wait, so that
+// two run side by side, their sizes falling geometrically to an eighth: at most 4 pieces.  Measured
+// end to end (results to page-locked memory), S_{2,8} in full: (a) with 2 pieces 2.67 ms, 3 pieces
+// 2.87, 4 pieces 2.85; (b) with 4 pieces 2.75; equal pieces side by side (the earlier schedule) 2.83;
+// the device-output call 2.33.  S_{3,8} sample of 2^28 at L = 32 (window and escalation launches):
+// (b) with 4 pieces 75.7 ms, 8 pieces 78.2; (a) with 2 or 4 pieces 80.4-80.7; the earlier schedule
+// 79.8; the device-output call 73.9.  Calls that use the window take (b), the others (a).
+// JATAM_PIPE_FORM (bit 0 staggered, bit 1 geometric sizes) and JATAM_PIPE_PIECES override it.
+int g_pipe_form = -1;
+int g_pipe_pieces = 0;
 
 void read_env_overrides()
 {
@@ -87,6 +99,11 @@ void read_env_overrides()
     if (const char *v = getenv("JATAM_PIPE_PIECE_LOG2")) {
         const int x = atoi(v);
         if (x >= 20 && x <= 26) PIPE_MIN_ITEMS = size_t(1) << x;
+    }
+    if (const char *v = getenv("JATAM_PIPE_FORM")) g_pipe_form = atoi(v) & 3;
+    if (const char *v = getenv("JATAM_PIPE_PIECES")) {
+        const int x = atoi(v);
+        if (x >= 2 && x <= 8) g_pipe_pieces = x;
     }
     if (const char *v = getenv("JATAM_CROP_TABLE")) g_crop_table = atoi(v) != 0;
     if (const char *v = getenv("JATAM_HEAVY_LEVELS")) g_heavy_levels = atoi(v) == 2 ? 2 : 3;
@@ -200,6 +217,7 @@ struct Workspace {
     } alt;
     cudaStream_t aux = nullptr, copy = nullptr;
     cudaEvent_t pipe_ev[PIPE_MAX_CHUNKS] = {};  // end of each piece's classification
+    cudaEvent_t pf_ev[PIPE_MAX_CHUNKS] = {};    // end of each piece's pre-filter
     cudaEvent_t pipe_start = nullptr, aux_done = nullptr, pipe_done = nullptr;
 };
 
@@ -678,17 +696,49 @@ int run(Workspace *w, LaunchArgs a, int S, jatam_result *out, int32_t *fitness, 
                            !(a.mode == MODE_RECORDS && !a.ids) && (o.host_out || o.host_fit) &&
                            (!o.host_out || is_pinned(out)) && (!o.host_fit || is_pinned(fitness));
     auto enqueue_pieces = [&](cudaStream_t s) -> int {
-        size_t pieces = n_items / PIPE_MIN_ITEMS;
+        const bool stagger = g_pipe_form >= 0 ? (g_pipe_form & 1) != 0 : !windowed;
+        const bool geometric = g_pipe_form >= 0 ? (g_pipe_form & 2) != 0 : windowed;
+        size_t pieces = windowed ? std::min(n_items / PIPE_MIN_ITEMS, size_t(4))
+                                 : std::max(n_items / (2 * PIPE_MIN_ITEMS), size_t(2));
+        if (g_pipe_pieces) pieces = (size_t)g_pipe_pieces;
         if (pieces > (size_t)PIPE_MAX_CHUNKS) pieces = PIPE_MAX_CHUNKS;
         // pieces - 1 of `per` items and a last one of about per / 4: only the last
         // piece's copy is not hidden behind a later piece's classification
-        const size_t per = (size_t)((double)n_items / ((double)pieces - 0.75)) + 1;
+        size_t sizes[PIPE_MAX_CHUNKS] = {};
+        size_t per = (size_t)((double)n_items / ((double)pieces - 0.75)) + 1;
+        if (geometric) {
+            // sizes r^i, the last an eighth of the first (pieces >= 2)
+            const double r = pow(0.125, 1.0 / (double)(pieces - 1));
+            double tot = 0.0, f = 1.0;
+            for (size_t i = 0; i < pieces; ++i, f *= r) tot += f;
+            per = (size_t)((double)n_items / tot) + 1;
+            size_t left = n_items;
+            f = 1.0;
+            for (size_t i = 0; i < pieces; ++i, f *= r) {
+                size_t m = (i + 1 == pieces) ? left : (size_t)((double)n_items * f / tot);
+                if (m > left) m = left;
+                if (m > per) m = per;
+                sizes[i] = m;
+                left -= m;
+            }
+            // the last piece took the rounding remainder: per exceeds every share
+            if (left || sizes[pieces - 1] > per) return fail(JATAM_EINVAL, "internal: piece schedule");
+        } else {
+            size_t left = n_items;
+            for (size_t i = 0; i < pieces && left; ++i) {
+                sizes[i] = left < per ? left : per;
+                left -= sizes[i];
+            }
+            if (left) return fail(JATAM_EINVAL, "internal: too many pieces");
+        }
         Workspace::Scratch &alt = w->alt;
         if (!w->copy) {
             CUDA_TRY(cudaStreamCreateWithFlags(&w->aux, cudaStreamNonBlocking));
             CUDA_TRY(cudaStreamCreateWithFlags(&w->copy, cudaStreamNonBlocking));
-            for (int c = 0; c < PIPE_MAX_CHUNKS; ++c)
+            for (int c = 0; c < PIPE_MAX_CHUNKS; ++c) {
                 CUDA_TRY(cudaEventCreateWithFlags(&w->pipe_ev[c], cudaEventDisableTiming));
+                CUDA_TRY(cudaEventCreateWithFlags(&w->pf_ev[c], cudaEventDisableTiming));
+            }
             CUDA_TRY(cudaEventCreateWithFlags(&w->pipe_start, cudaEventDisableTiming));
             CUDA_TRY(cudaEventCreateWithFlags(&w->aux_done, cudaEventDisableTiming));
             CUDA_TRY(cudaEventCreateWithFlags(&w->pipe_done, cudaEventDisableTiming));
@@ -715,9 +765,9 @@ int run(Workspace *w, LaunchArgs a, int S, jatam_result *out, int32_t *fitness, 
         CUDA_TRY(cudaEventRecord(w->pipe_start, s));
         CUDA_TRY(cudaStreamWaitEvent(w->aux, w->pipe_start, 0));
         int c = 0;
-        for (size_t start = 0; start < n_items; start += per, ++c) {
-            const size_t cnt = (n_items - start < per) ? n_items - start : per;
-            if (c >= PIPE_MAX_CHUNKS) return fail(JATAM_EINVAL, "internal: too many pieces");
+        for (size_t start = 0; start < n_items; start += sizes[c], ++c) {
+            if (c >= PIPE_MAX_CHUNKS || sizes[c] == 0) return fail(JATAM_EINVAL, "internal: too many pieces");
+            const size_t cnt = sizes[c];
             const bool odd = (c & 1) != 0;
             cudaStream_t cs = odd ? w->aux : s;
             unsigned long long *wn = odd ? alt.work_next : w->work_next;
@@ -743,10 +793,12 @@ int run(Workspace *w, LaunchArgs a, int S, jatam_result *out, int32_t *fitness, 
             if (a.out) ac.out = a.out + start;
             if (a.fitness) ac.fitness = a.fitness + start;
             ac.spill = spill_of(odd ? alt.spill_rows : w->spill_rows, ectl);
+            if (stagger && c > 0) CUDA_TRY(cudaStreamWaitEvent(cs, w->pf_ev[c - 1], 0));
             CUDA_TRY(launch_reset(wn, nk, lc, cs, cr, CROPS_LOG2, ectl, ESC_CTL_WORDS));
             long long pb = (long long)(cnt + 255) / 256;
             if (pb > PF_CTAS_PER_SM * w->num_sms) pb = PF_CTAS_PER_SM * w->num_sms;
             CUDA_TRY(launch_prefilter(ac, S, (int)pb, cs));
+            if (stagger) CUDA_TRY(cudaEventRecord(w->pf_ev[c], cs));
             if (per_warp) {
                 long long bc = (long long)((cnt + warps - 1) / warps);
                 if (bc > blocks) bc = blocks;
@@ -1927,7 +1979,10 @@ void jatam_shutdown(void)
         if (w->copy) {
             cudaStreamDestroy(w->copy);
             cudaStreamDestroy(w->aux);
-            for (int c = 0; c < PIPE_MAX_CHUNKS; ++c) cudaEventDestroy(w->pipe_ev[c]);
+            for (int c = 0; c < PIPE_MAX_CHUNKS; ++c) {
+                cudaEventDestroy(w->pipe_ev[c]);
+                cudaEventDestroy(w->pf_ev[c]);
+            }
             cudaEventDestroy(w->pipe_start);
             cudaEventDestroy(w->aux_done);
             cudaEventDestroy(w->pipe_done);

@@ -279,6 +279,24 @@ def test_pinned_host_buffers_pipelined_equal_device_buffers():
     assert torch.equal(fh, fd.cpu()) and torch.equal(oh, od.cpu())
 
 
+def test_pinned_windowed_pipelined_equal_device_buffers():
+    """A call that grows in the 16 x 16 window first (L = 32, at least 2^23
+    items) with results to page-locked memory runs its pieces side by side on
+    two streams, their sizes falling geometrically, each with its own
+    escalation list: results and histogram equal the one-pass device call."""
+    n, c, L, k, seed = 3, 8, 32, 20, 3
+    first, count = 5 << 26, (1 << 23) + 12_345
+    res, dh, m = _dev_enumerate(n, c, L, k, seed, first, count, sampled=True)
+    out = torch.full((count * 8,), 0xEE, dtype=torch.uint8, pin_memory=True)
+    hist = np.zeros(1 << 16, J.HIST_DTYPE)
+    hlen = np.zeros(1, np.uint32)
+    J.enumerate_space(n, c, L, k, seed, first, count, sampled=True, out=out, hist=hist, hist_len=hlen,
+                      hist_cap=1 << 16)
+    assert np.array_equal(J.results_view(out), res)
+    assert int(hlen[0]) == m and np.array_equal(hist[:m], dh)
+    assert (res["cls"] == 3).any() and (res["size"] > 12).any()  # unbounded genotypes and large shapes
+
+
 def test_pinned_records_with_ids_pipelined_equal_device_buffers():
     """Explicit records of mixed shape with stream ids, results and histogram to
     page-locked memory: the pieces offset the colours, the shapes and the ids."""
