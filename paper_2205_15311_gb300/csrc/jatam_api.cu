@@ -78,9 +78,15 @@ size_t PIPE_MIN_ITEMS = size_t(1) << 22;
 // the device-output call 2.33.  S_{3,8} sample of 2^28 at L = 32 (window and escalation launches):
 // (b) with 4 pieces 75.7 ms, 8 pieces 78.2; (a) with 2 or 4 pieces 80.4-80.7; the earlier schedule
 // 79.8; the device-output call 73.9.  Calls that use the window take (b), the others (a).
-// JATAM_PIPE_FORM (bit 0 staggered, bit 1 geometric sizes) and JATAM_PIPE_PIECES override it.
+// Records from page-locked memory (with stream ids) also copy their inputs piece by piece, in two
+// equal pieces: on 10^7 mixed records (28 B in, 8 B out each) 5.60-5.63 ms against 6.16 with the
+// inputs copied at once; 3, 4 and 6 pieces 6.4, 7.1 and 8.7 ms (each piece runs a launch per lattice
+// size, each with its tail); a first piece of 0.3, 0.4 or 0.6 of the call 5.8-6.1 ms.
+// JATAM_PIPE_FORM (bit 0 staggered, bit 1 geometric sizes), JATAM_PIPE_PIECES and JATAM_PIPE_STAGE
+// override it.
 int g_pipe_form = -1;
 int g_pipe_pieces = 0;
+int g_pipe_stage = 1;  // JATAM_PIPE_STAGE=0: host record inputs copied at once even in pipelined calls
 
 void read_env_overrides()
 {
@@ -101,6 +107,7 @@ void read_env_overrides()
         if (x >= 20 && x <= 26) PIPE_MIN_ITEMS = size_t(1) << x;
     }
     if (const char *v = getenv("JATAM_PIPE_FORM")) g_pipe_form = atoi(v) & 3;
+    if (const char *v = getenv("JATAM_PIPE_STAGE")) g_pipe_stage = atoi(v) != 0;
     if (const char *v = getenv("JATAM_PIPE_PIECES")) {
         const int x = atoi(v);
         if (x >= 2 && x <= 8) g_pipe_pieces = x;
@@ -216,6 +223,8 @@ struct Workspace {
         size_t spill_bytes = 0;
     } alt;
     cudaStream_t aux = nullptr, copy = nullptr;
+    cudaStream_t h2d = nullptr;                  // per-piece input copies of pipelined record calls
+    cudaEvent_t in_ev[PIPE_MAX_CHUNKS] = {};     // end of each piece's input copies
     cudaEvent_t pipe_ev[PIPE_MAX_CHUNKS] = {};  // end of each piece's classification
     cudaEvent_t pf_ev[PIPE_MAX_CHUNKS] = {};    // end of each piece's pre-filter
     cudaEvent_t pipe_start = nullptr, aux_done = nullptr, pipe_done = nullptr;
@@ -369,6 +378,20 @@ Tuning tuning_for(int S, int n, int c)
     return t;
 }
 
+// Record inputs that live in host memory: run() copies them into the staging
+// buffer the launch arguments already point at -- all at once before the
+// classification, or, in a call that runs in pieces from page-locked memory, each
+// piece's slice just before that piece (so that the copies overlap the
+// classification of the pieces before it)
+struct HostInputs {
+    const uint8_t *colours = nullptr;            // [N][16], or null: not from the host
+    const uint8_t *shapes = nullptr;             // [N][4]
+    const unsigned long long *ids = nullptr;     // [N]
+    uint8_t *colours_dev = nullptr, *shapes_dev = nullptr;  // their staging copies
+    unsigned long long *ids_dev = nullptr;
+    bool any() const { return colours || shapes || ids; }
+};
+
 struct Outputs {
     jatam_result *out_dev = nullptr;
     int32_t *fit_dev = nullptr;
@@ -381,7 +404,8 @@ struct Outputs {
 // kernels, stage host outputs, and synchronise when needed.
 int run(Workspace *w, LaunchArgs a, int S, jatam_result *out, int32_t *fitness, jatam_hist_entry *hist,
         uint32_t hist_cap, uint32_t *hist_len, bool sync_flag, cudaStream_t st, const Tuning *force = nullptr,
-        float *kernel_ms = nullptr, bool per_shape = false, bool use_graph = false)
+        float *kernel_ms = nullptr, bool per_shape = false, bool use_graph = false,
+        const HostInputs *hin = nullptr)
 {
     Outputs o;
     const Kind ko = kind_of(out, w->device), kf = kind_of(fitness, w->device), kh = kind_of(hist, w->device),
@@ -695,6 +719,9 @@ int run(Workspace *w, LaunchArgs a, int S, jatam_result *out, int32_t *fitness, 
     const bool pipelined = n_items >= 2 * PIPE_MIN_ITEMS && !use_graph && !timed && !a.orbits && !a.lifo &&
                            !(a.mode == MODE_RECORDS && !a.ids) && (o.host_out || o.host_fit) &&
                            (!o.host_out || is_pinned(out)) && (!o.host_fit || is_pinned(fitness));
+    // record inputs in page-locked memory: copied piece by piece on a stream of their own
+    const bool staged_pieces = pipelined && g_pipe_stage && hin && hin->any() && (!hin->colours || is_pinned(hin->colours)) &&
+                               (!hin->shapes || is_pinned(hin->shapes)) && (!hin->ids || is_pinned(hin->ids));
     auto enqueue_pieces = [&](cudaStream_t s) -> int {
         const bool stagger = g_pipe_form >= 0 ? (g_pipe_form & 1) != 0 : !windowed;
         const bool geometric = g_pipe_form >= 0 ? (g_pipe_form & 2) != 0 : windowed;
@@ -706,7 +733,19 @@ int run(Workspace *w, LaunchArgs a, int S, jatam_result *out, int32_t *fitness, 
         // piece's copy is not hidden behind a later piece's classification
         size_t sizes[PIPE_MAX_CHUNKS] = {};
         size_t per = (size_t)((double)n_items / ((double)pieces - 0.75)) + 1;
-        if (geometric) {
+        if (staged_pieces) {
+            // inputs copied piece by piece: equal pieces, two unless overridden -- the second half's
+            // inputs are copied while the first half is classified, the first half's results while
+            // the second is
+            pieces = g_pipe_pieces ? (size_t)g_pipe_pieces : 2;
+            per = (n_items + pieces - 1) / pieces;
+            size_t left = n_items;
+            for (size_t i = 0; i < pieces && left; ++i) {
+                sizes[i] = left < per ? left : per;
+                left -= sizes[i];
+            }
+            if (left) return fail(JATAM_EINVAL, "internal: piece schedule");
+        } else if (geometric) {
             // sizes r^i, the last an eighth of the first (pieces >= 2)
             const double r = pow(0.125, 1.0 / (double)(pieces - 1));
             double tot = 0.0, f = 1.0;
@@ -732,6 +771,11 @@ int run(Workspace *w, LaunchArgs a, int S, jatam_result *out, int32_t *fitness, 
             if (left) return fail(JATAM_EINVAL, "internal: too many pieces");
         }
         Workspace::Scratch &alt = w->alt;
+        if (staged_pieces && !w->h2d) {
+            CUDA_TRY(cudaStreamCreateWithFlags(&w->h2d, cudaStreamNonBlocking));
+            for (int c = 0; c < PIPE_MAX_CHUNKS; ++c)
+                CUDA_TRY(cudaEventCreateWithFlags(&w->in_ev[c], cudaEventDisableTiming));
+        }
         if (!w->copy) {
             CUDA_TRY(cudaStreamCreateWithFlags(&w->aux, cudaStreamNonBlocking));
             CUDA_TRY(cudaStreamCreateWithFlags(&w->copy, cudaStreamNonBlocking));
@@ -793,6 +837,22 @@ int run(Workspace *w, LaunchArgs a, int S, jatam_result *out, int32_t *fitness, 
             if (a.out) ac.out = a.out + start;
             if (a.fitness) ac.fitness = a.fitness + start;
             ac.spill = spill_of(odd ? alt.spill_rows : w->spill_rows, ectl);
+            if (staged_pieces) {
+                // this piece's records, shapes and stream ids; the staging buffer is free once the
+                // previous call has ended (pipe_start follows it on the caller's stream)
+                if (c == 0) CUDA_TRY(cudaStreamWaitEvent(w->h2d, w->pipe_start, 0));
+                if (hin->colours)
+                    CUDA_TRY(cudaMemcpyAsync(hin->colours_dev + 16 * start, hin->colours + 16 * start, 16 * cnt,
+                                             cudaMemcpyHostToDevice, w->h2d));
+                if (hin->shapes)
+                    CUDA_TRY(cudaMemcpyAsync(hin->shapes_dev + 4 * start, hin->shapes + 4 * start, 4 * cnt,
+                                             cudaMemcpyHostToDevice, w->h2d));
+                if (hin->ids)
+                    CUDA_TRY(cudaMemcpyAsync(hin->ids_dev + start, hin->ids + start, 8 * cnt, cudaMemcpyHostToDevice,
+                                             w->h2d));
+                CUDA_TRY(cudaEventRecord(w->in_ev[c], w->h2d));
+                CUDA_TRY(cudaStreamWaitEvent(cs, w->in_ev[c], 0));
+            }
             if (stagger && c > 0) CUDA_TRY(cudaStreamWaitEvent(cs, w->pf_ev[c - 1], 0));
             CUDA_TRY(launch_reset(wn, nk, lc, cs, cr, CROPS_LOG2, ectl, ESC_CTL_WORDS));
             long long pb = (long long)(cnt + 255) / 256;
@@ -837,6 +897,15 @@ int run(Workspace *w, LaunchArgs a, int S, jatam_result *out, int32_t *fitness, 
     };
 
     CUDA_TRY(cudaStreamWaitEvent(st, w->last, 0));
+    if (hin && hin->any() && !staged_pieces && n_items) {
+        // host record inputs staged all at once, before the classification
+        if (hin->colours)
+            CUDA_TRY(cudaMemcpyAsync(hin->colours_dev, hin->colours, 16 * n_items, cudaMemcpyHostToDevice, st));
+        if (hin->shapes)
+            CUDA_TRY(cudaMemcpyAsync(hin->shapes_dev, hin->shapes, 4 * n_items, cudaMemcpyHostToDevice, st));
+        if (hin->ids)
+            CUDA_TRY(cudaMemcpyAsync(hin->ids_dev, hin->ids, 8 * n_items, cudaMemcpyHostToDevice, st));
+    }
     if (pipelined) {
         int rc = enqueue_pieces(st);
         if (rc) return rc;
@@ -1029,25 +1098,30 @@ int jatam_classify_batch(const jatam_config *cfg, const uint8_t *colours, const 
         rc = grow(&w->stage_in, &w->stage_in_bytes, off_i + ib + 256);
         if (rc) return rc;
     }
+    // host inputs: run() copies them into stage_in, at once or piece by piece
     char *base = static_cast<char *>(w->stage_in);
+    HostInputs hin;
     a.colours = colours;
     if (kc == K_HOST && N) {
-        CUDA_TRY(cudaMemcpyAsync(base, colours, cb, cudaMemcpyHostToDevice, st));
-        a.colours = reinterpret_cast<const uint8_t *>(base);
+        hin.colours = colours;
+        hin.colours_dev = reinterpret_cast<uint8_t *>(base);
+        a.colours = hin.colours_dev;
     }
     a.shapes = shapes;
     if (ks == K_HOST && N) {
-        CUDA_TRY(cudaMemcpyAsync(base + off_s, shapes, sb, cudaMemcpyHostToDevice, st));
-        a.shapes = reinterpret_cast<const uint8_t *>(base + off_s);
+        hin.shapes = shapes;
+        hin.shapes_dev = reinterpret_cast<uint8_t *>(base + off_s);
+        a.shapes = hin.shapes_dev;
     }
     a.ids = reinterpret_cast<const unsigned long long *>(stream_ids);
     if (ki == K_HOST && N) {
-        CUDA_TRY(cudaMemcpyAsync(base + off_i, stream_ids, ib, cudaMemcpyHostToDevice, st));
-        a.ids = reinterpret_cast<const unsigned long long *>(base + off_i);
+        hin.ids = reinterpret_cast<const unsigned long long *>(stream_ids);
+        hin.ids_dev = reinterpret_cast<unsigned long long *>(base + off_i);
+        a.ids = hin.ids_dev;
     }
     return run(w, a, S, out, nullptr, hist, hist_cap, hist_len, (cfg->flags & JATAM_SYNC) != 0, st, nullptr, nullptr,
                (cfg->flags & JATAM_PER_SHAPE) != 0 || (!(cfg->flags & JATAM_PERSISTENT) && g_mixed_per_shape),
-               (cfg->flags & JATAM_GRAPH) != 0);
+               (cfg->flags & JATAM_GRAPH) != 0, &hin);
 }
 
 int ga_evaluate(const jatam_config *cfg, const uint64_t *genomes, uint64_t N, int32_t *fitness, jatam_result *out,
@@ -1976,6 +2050,10 @@ void jatam_shutdown(void)
         cudaEventDestroy(w->k_stop);
         for (auto &kv : w->graphs) cudaGraphExecDestroy(kv.second);
         if (w->capture) cudaStreamDestroy(w->capture);
+        if (w->h2d) {
+            cudaStreamDestroy(w->h2d);
+            for (int c = 0; c < PIPE_MAX_CHUNKS; ++c) cudaEventDestroy(w->in_ev[c]);
+        }
         if (w->copy) {
             cudaStreamDestroy(w->copy);
             cudaStreamDestroy(w->aux);
