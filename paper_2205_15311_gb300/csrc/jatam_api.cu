@@ -720,8 +720,9 @@ int run(Workspace *w, LaunchArgs a, int S, jatam_result *out, int32_t *fitness, 
                            !(a.mode == MODE_RECORDS && !a.ids) && (o.host_out || o.host_fit) &&
                            (!o.host_out || is_pinned(out)) && (!o.host_fit || is_pinned(fitness));
     // record inputs in page-locked memory: copied piece by piece on a stream of their own
-    const bool staged_pieces = pipelined && g_pipe_stage && hin && hin->any() && (!hin->colours || is_pinned(hin->colours)) &&
-                               (!hin->shapes || is_pinned(hin->shapes)) && (!hin->ids || is_pinned(hin->ids));
+    const bool staged_pieces = pipelined && g_pipe_stage && hin && hin->any() &&
+                               (!hin->colours || is_pinned(hin->colours)) && (!hin->shapes || is_pinned(hin->shapes)) &&
+                               (!hin->ids || is_pinned(hin->ids));
     auto enqueue_pieces = [&](cudaStream_t s) -> int {
         const bool stagger = g_pipe_form >= 0 ? (g_pipe_form & 1) != 0 : !windowed;
         const bool geometric = g_pipe_form >= 0 ? (g_pipe_form & 2) != 0 : windowed;
