@@ -15,6 +15,7 @@
 #include <cuda_runtime.h>
 
 #include "jatam_internal.cuh"
+#include "jatam_pipe.h"
 
 using namespace jatam;
 
@@ -68,22 +69,17 @@ std::map<std::tuple<int, int, int>, Tuning> g_tuned;
 // host-buffer calls of at least 2 * PIPE_MIN_ITEMS items run in pieces (JATAM_PIPE_PIECE_LOG2 sets it,
 // 2^20 .. 2^26)
 size_t PIPE_MIN_ITEMS = size_t(1) << 22;
-// The piece schedule of such calls.  Two forms: (a) staggered -- a piece's work waits for the previous
-// piece's pre-filter, so that its growth launch queues behind the previous one and fills that launch's
-// tail, and pieces end one after another: equal pieces and a last one of a quarter, each at least
-// 2 * PIPE_MIN_ITEMS items; (b) paired -- pieces alternate between two streams with no wait, so that
-// two run side by side, their sizes falling geometrically to an eighth: at most 4 pieces.  Measured
-// end to end (results to page-locked memory), S_{2,8} in full: (a) with 2 pieces 2.67 ms, 3 pieces
-// 2.87, 4 pieces 2.85; (b) with 4 pieces 2.75; equal pieces side by side (the earlier schedule) 2.83;
-// the device-output call 2.33.  S_{3,8} sample of 2^28 at L = 32 (window and escalation launches):
-// (b) with 4 pieces 75.7 ms, 8 pieces 78.2; (a) with 2 or 4 pieces 80.4-80.7; the earlier schedule
-// 79.8; the device-output call 73.9.  Calls that use the window take (b), the others (a).
-// Records from page-locked memory (with stream ids) also copy their inputs piece by piece, in two
-// equal pieces: on 10^7 mixed records (28 B in, 8 B out each) 5.60-5.63 ms against 6.16 with the
-// inputs copied at once; 3, 4 and 6 pieces 6.4, 7.1 and 8.7 ms (each piece runs a launch per lattice
-// size, each with its tail); a first piece of 0.3, 0.4 or 0.6 of the call 5.8-6.1 ms.
-// JATAM_PIPE_FORM (bit 0 staggered, bit 1 geometric sizes), JATAM_PIPE_PIECES and JATAM_PIPE_STAGE
-// override it.
+// The piece schedule of such calls (pipe_schedule).  Measured end to end (results to page-locked
+// memory), S_{2,8} in full: staggered with 2 pieces 2.67 ms, 3 pieces 2.87, 4 pieces 2.85; paired
+// geometric with 4 pieces 2.75; equal pieces side by side (the earlier schedule) 2.83; the
+// device-output call 2.33.  S_{3,8} sample of 2^28 at L = 32 (window and escalation launches): paired
+// geometric with 4 pieces 75.7 ms, 8 pieces 78.2; staggered with 2 or 4 pieces 80.4-80.7; the earlier
+// schedule 79.8; the device-output call 73.9.  Records from page-locked memory (with stream ids) also
+// copy their inputs piece by piece: on 10^7 mixed records (28 B in, 8 B out each) two equal pieces
+// take 5.60-5.63 ms against 6.16 with the inputs copied at once; 3, 4 and 6 pieces 6.4, 7.1 and 8.7 ms
+// (each piece runs a launch per lattice size, each with its tail); a first piece of 0.3, 0.4 or 0.6
+// of the call 5.8-6.1 ms.  JATAM_PIPE_FORM (bit 0 staggered, bit 1 geometric sizes), JATAM_PIPE_PIECES
+// and JATAM_PIPE_STAGE override it.
 int g_pipe_form = -1;
 int g_pipe_pieces = 0;
 int g_pipe_stage = 1;  // JATAM_PIPE_STAGE=0: host record inputs copied at once even in pipelined calls
@@ -154,9 +150,6 @@ constexpr unsigned SHAPES_LOG2 = 14;  // 16,384 slots of the call's shape side t
 // [9] the number of spilled crops
 constexpr int ESC_CTL_WORDS = 10;
 constexpr unsigned SPILL_CAP = 1u << 16;  // crops the crop table cannot hold, per call or piece (8.3 MB)
-// host-buffer calls of at least 2 * PIPE_MIN_ITEMS items run in up to PIPE_MAX_CHUNKS pieces whose
-// results are copied to the host while the next piece is classified
-constexpr int PIPE_MAX_CHUNKS = 8;
 
 struct Workspace {
     int device = -1;
@@ -724,53 +717,12 @@ int run(Workspace *w, LaunchArgs a, int S, jatam_result *out, int32_t *fitness, 
                                (!hin->colours || is_pinned(hin->colours)) && (!hin->shapes || is_pinned(hin->shapes)) &&
                                (!hin->ids || is_pinned(hin->ids));
     auto enqueue_pieces = [&](cudaStream_t s) -> int {
-        const bool stagger = g_pipe_form >= 0 ? (g_pipe_form & 1) != 0 : !windowed;
-        const bool geometric = g_pipe_form >= 0 ? (g_pipe_form & 2) != 0 : windowed;
-        size_t pieces = windowed ? std::min(n_items / PIPE_MIN_ITEMS, size_t(4))
-                                 : std::max(n_items / (2 * PIPE_MIN_ITEMS), size_t(2));
-        if (g_pipe_pieces) pieces = (size_t)g_pipe_pieces;
-        if (pieces > (size_t)PIPE_MAX_CHUNKS) pieces = PIPE_MAX_CHUNKS;
-        // pieces - 1 of `per` items and a last one of about per / 4: only the last
-        // piece's copy is not hidden behind a later piece's classification
-        size_t sizes[PIPE_MAX_CHUNKS] = {};
-        size_t per = (size_t)((double)n_items / ((double)pieces - 0.75)) + 1;
-        if (staged_pieces) {
-            // inputs copied piece by piece: equal pieces, two unless overridden -- the second half's
-            // inputs are copied while the first half is classified, the first half's results while
-            // the second is
-            pieces = g_pipe_pieces ? (size_t)g_pipe_pieces : 2;
-            per = (n_items + pieces - 1) / pieces;
-            size_t left = n_items;
-            for (size_t i = 0; i < pieces && left; ++i) {
-                sizes[i] = left < per ? left : per;
-                left -= sizes[i];
-            }
-            if (left) return fail(JATAM_EINVAL, "internal: piece schedule");
-        } else if (geometric) {
-            // sizes r^i, the last an eighth of the first (pieces >= 2)
-            const double r = pow(0.125, 1.0 / (double)(pieces - 1));
-            double tot = 0.0, f = 1.0;
-            for (size_t i = 0; i < pieces; ++i, f *= r) tot += f;
-            per = (size_t)((double)n_items / tot) + 1;
-            size_t left = n_items;
-            f = 1.0;
-            for (size_t i = 0; i < pieces; ++i, f *= r) {
-                size_t m = (i + 1 == pieces) ? left : (size_t)((double)n_items * f / tot);
-                if (m > left) m = left;
-                if (m > per) m = per;
-                sizes[i] = m;
-                left -= m;
-            }
-            // the last piece took the rounding remainder: per exceeds every share
-            if (left || sizes[pieces - 1] > per) return fail(JATAM_EINVAL, "internal: piece schedule");
-        } else {
-            size_t left = n_items;
-            for (size_t i = 0; i < pieces && left; ++i) {
-                sizes[i] = left < per ? left : per;
-                left -= sizes[i];
-            }
-            if (left) return fail(JATAM_EINVAL, "internal: too many pieces");
-        }
+        PipeSchedule ps;
+        if (!pipe_schedule(n_items, PIPE_MIN_ITEMS, windowed, staged_pieces, g_pipe_form, g_pipe_pieces, &ps))
+            return fail(JATAM_EINVAL, "internal: piece schedule");
+        const bool stagger = ps.stagger;
+        const size_t *sizes = ps.sizes;
+        const size_t per = ps.per;
         Workspace::Scratch &alt = w->alt;
         if (staged_pieces && !w->h2d) {
             CUDA_TRY(cudaStreamCreateWithFlags(&w->h2d, cudaStreamNonBlocking));
